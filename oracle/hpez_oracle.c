@@ -1,0 +1,1144 @@
+/*
+ * hpez_oracle.c -- plain, slow, single-threaded CPU oracle of the HPEZ
+ * interpolation predict-and-quantize path (arXiv 2311.12133).
+ *
+ * TEST INFRASTRUCTURE ONLY: only tests/, __graft_entry__.smoke() and the
+ * benchmark's CPU-baseline leg may call it.  It shares no code with the CUDA
+ * path; the two agree only on the compressed stream layout, which each side
+ * writes on its own.
+ *
+ * What it follows, step by step:
+ *   Sec. 4 (Steps 2-4)     prediction, linear quantization, Huffman coding
+ *   Sec. 5.1               anchor grid + level-wise interpolation, strides
+ *                          A/2 .. 1, the grid doubling at every level
+ *   Sec. 5.2 Eq. 2, 4, 6   linear, not-a-knot cubic, natural cubic stencils
+ *   Sec. 5.3 Eq. 8, 14     multi-dimensional interpolation, weights
+ *                          alpha_i proportional to 1/sigma_i^2
+ *   Sec. 5.4.2 Eq. 10, 11  same-level cubic interpolation (two halves)
+ *   Sec. 6.3               dimension freezing (anchor stride 1 on one dim)
+ *   Sec. 6.4 Eq. 15        level error bounds e_l = e / min(alpha^(l-1), beta)
+ *   Sec. 6.6               block-wise interpolator choice (block map)
+ *   Sec. 7.1.3             value-range relative bound e = eps * (max - min)
+ *
+ * Readings where the paper is silent (each listed in the design notes):
+ * boundary fallbacks of the stencils, the quantizer's exact rounding steps,
+ * the outlier escape (code 0), the canonical Huffman tie-breaks and the
+ * chunked bit layout, and the stream container.
+ *
+ * Every binary32 operation below is one correctly rounded IEEE operation in
+ * the order written (compiled with -ffp-contract=off, no fast-math).
+ */
+#include "hpez_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* little-endian byte access                                           */
+/* ------------------------------------------------------------------ */
+static void put_u8(uint8_t* b, uint64_t o, uint8_t v) { b[o] = v; }
+static void put_u16(uint8_t* b, uint64_t o, uint16_t v) {
+  b[o] = (uint8_t)(v & 0xff);
+  b[o + 1] = (uint8_t)(v >> 8);
+}
+static void put_u32(uint8_t* b, uint64_t o, uint32_t v) {
+  for (int i = 0; i < 4; ++i) b[o + i] = (uint8_t)(v >> (8 * i));
+}
+static void put_u64(uint8_t* b, uint64_t o, uint64_t v) {
+  for (int i = 0; i < 8; ++i) b[o + i] = (uint8_t)(v >> (8 * i));
+}
+static void put_f32(uint8_t* b, uint64_t o, float v) {
+  uint32_t u;
+  memcpy(&u, &v, 4);
+  put_u32(b, o, u);
+}
+static void put_f64(uint8_t* b, uint64_t o, double v) {
+  uint64_t u;
+  memcpy(&u, &v, 8);
+  put_u64(b, o, u);
+}
+static uint16_t get_u16(const uint8_t* b, uint64_t o) {
+  return (uint16_t)(b[o] | ((uint16_t)b[o + 1] << 8));
+}
+static uint32_t get_u32(const uint8_t* b, uint64_t o) {
+  uint32_t v = 0;
+  for (int i = 0; i < 4; ++i) v |= (uint32_t)b[o + i] << (8 * i);
+  return v;
+}
+static uint64_t get_u64(const uint8_t* b, uint64_t o) {
+  uint64_t v = 0;
+  for (int i = 0; i < 8; ++i) v |= (uint64_t)b[o + i] << (8 * i);
+  return v;
+}
+static float get_f32(const uint8_t* b, uint64_t o) {
+  uint32_t u = get_u32(b, o);
+  float v;
+  memcpy(&v, &u, 4);
+  return v;
+}
+static double get_f64(const uint8_t* b, uint64_t o) {
+  uint64_t u = get_u64(b, o);
+  double v;
+  memcpy(&v, &u, 8);
+  return v;
+}
+static uint64_t align16(uint64_t v) { return (v + 15) & ~(uint64_t)15; }
+
+/* ------------------------------------------------------------------ */
+/* stream container layout (byte offsets inside the 512-byte header)   */
+/* ------------------------------------------------------------------ */
+#define H_MAGIC 0
+#define H_VERSION 4
+#define H_FLAGS 8
+#define H_NDIM 12
+#define H_DIMS 16
+#define H_EBMODE 40
+#define H_ANCHOR 44
+#define H_EBVALUE 48
+#define H_E 56
+#define H_CONST 60
+#define H_FROZEN 64
+#define H_CHUNK 68
+#define H_ALPHA 72
+#define H_BETA 80
+#define H_MDIV 88
+#define H_INTERP 112
+#define H_PARADIGM 128
+#define H_SAME 144
+#define H_ORDER 160
+#define H_PREDICTOR 208
+#define H_BLOCKWISE 212
+#define H_NANCHORS 216
+#define H_NOUTLIERS 224
+#define H_NUSED 232
+#define H_BLOCKSIZE 236
+#define H_NCHUNKS 240
+#define H_TOTALWORDS 248
+#define H_OFF_ANCHORS 256
+#define H_OFF_CHUNKW 264
+#define H_OFF_TABLE 272
+#define H_OFF_OUTLIERS 280
+#define H_OFF_BITS 288
+#define H_OFF_BLOCKMAP 296
+#define H_TOTAL 304
+#define H_NBLOCKS 312
+#define MAGIC 0x5A455048u /* "HPEZ" */
+#define VERSION 1u
+#define FLAG_CONST 1u
+
+/* ------------------------------------------------------------------ */
+/* field geometry: every field is held as 3 slots, the real dimensions  */
+/* in the last ndim slots; padded slots have extent 1 and are never     */
+/* interpolated.                                                        */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  int ndim, off;
+  uint64_t n[3], st[3], N;
+  int interp[3];
+  int k, A, L;
+} geom;
+
+static int ilog2(uint64_t v) {
+  int l = 0;
+  while (((uint64_t)1 << l) < v) ++l;
+  return l;
+}
+static int is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+static int geom_init(geom* g, int ndim, const uint64_t* dims, int A,
+                     int frozen) {
+  if (ndim < 1 || ndim > 3) return ORA_ERR_INVALID_ARG;
+  if (frozen < -1 || frozen >= ndim || (ndim == 1 && frozen != -1))
+    return ORA_ERR_INVALID_ARG;
+  if (!is_pow2(A) || A < 2 || A > 32768) return ORA_ERR_INVALID_ARG;
+  g->ndim = ndim;
+  g->off = 3 - ndim;
+  g->N = 1;
+  for (int s = 0; s < 3; ++s) {
+    g->n[s] = 1;
+    g->interp[s] = 0;
+  }
+  for (int d = 0; d < ndim; ++d) {
+    if (dims[d] == 0) return ORA_ERR_INVALID_ARG;
+    g->n[d + g->off] = dims[d];
+    g->interp[d + g->off] = (d != frozen);
+    g->N *= dims[d];
+    if (g->N > 0xFFFFFFFFull) return ORA_ERR_INVALID_ARG;
+  }
+  g->st[2] = 1;
+  g->st[1] = g->n[2];
+  g->st[0] = g->n[1] * g->n[2];
+  g->k = 0;
+  for (int s = 0; s < 3; ++s) g->k += g->interp[s];
+  g->A = A;
+  g->L = ilog2((uint64_t)A);
+  return ORA_OK;
+}
+
+void ora_default_config(int ndim, ora_config* c) {
+  memset(c, 0, sizeof(*c));
+  c->anchor_stride = ndim == 1 ? 128 : (ndim == 2 ? 64 : 32);
+  c->frozen_dim = -1;
+  c->chunk_syms = 4096;
+  c->blockwise = 0;
+  c->block_size = 32;
+  c->alpha = 1.0;
+  c->beta = 1.0;
+  for (int d = 0; d < 3; ++d) c->md_inv_var[d] = 1.0;
+  for (int l = 0; l < ORA_MAX_LEVELS; ++l) {
+    c->interp[l] = ORA_CUBIC_NAK;
+    c->paradigm[l] = ORA_1D;
+    c->same_level[l] = 0;
+    for (int j = 0; j < 3; ++j) c->order[l][j] = (uint8_t)(j < ndim ? j : 255);
+  }
+  c->blockmap = NULL;
+}
+
+/* Checks a config against the field shape; fills the per-level 1D-style
+ * order as slots.  Returns 0 or ORA_ERR_INVALID_ARG. */
+static int check_config(const geom* g, const ora_config* c) {
+  if (!is_pow2(c->chunk_syms) || c->chunk_syms < 256 || c->chunk_syms > 32768)
+    return ORA_ERR_INVALID_ARG;
+  if (!(c->alpha >= 1.0) || !(c->beta >= 1.0) || !isfinite(c->alpha) ||
+      !isfinite(c->beta))
+    return ORA_ERR_INVALID_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (!(c->md_inv_var[d] > 0.0) || !isfinite(c->md_inv_var[d]))
+      return ORA_ERR_INVALID_ARG;
+  if (c->blockwise) {
+    if (!c->blockmap || c->block_size < 1) return ORA_ERR_INVALID_ARG;
+  }
+  for (int l = 0; l < g->L; ++l) {
+    if (c->interp[l] > ORA_CUBIC_NAT || c->paradigm[l] > ORA_MD ||
+        c->same_level[l] > 1)
+      return ORA_ERR_INVALID_ARG;
+    /* the 1D-style order lists each interpolation dimension exactly once */
+    int seen[3] = {0, 0, 0};
+    for (int j = 0; j < g->k; ++j) {
+      int d = c->order[l][j];
+      if (d >= g->ndim || !g->interp[d + g->off] || seen[d])
+        return ORA_ERR_INVALID_ARG;
+      seen[d] = 1;
+    }
+  }
+  return ORA_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Eq. 15 level error bounds + quantizer constants                     */
+/* ------------------------------------------------------------------ */
+int ora_level_params(float e, double alpha, double beta, int L, float* el,
+                     float* inv2, float* twoe) {
+  for (int l = 1; l <= L; ++l) {
+    double ap = 1.0; /* alpha^(l-1) by repeated multiplication */
+    for (int i = 1; i < l; ++i) ap = ap * alpha;
+    double m = ap < beta ? ap : beta;
+    float e_l = (float)((double)e / m);
+    if (!(e_l > 0.0f) || !isfinite(e_l)) return ORA_ERR_INVALID_ARG;
+    float t = 2.0f * e_l;
+    if (!isfinite(t)) return ORA_ERR_INVALID_ARG;
+    el[l - 1] = e_l;
+    twoe[l - 1] = t;
+    inv2[l - 1] = (float)(1.0 / (2.0 * (double)e_l));
+  }
+  return ORA_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 5.2 / 5.4.2 stencils along one line                            */
+/* ------------------------------------------------------------------ */
+/* formula ids, chosen from which neighbours exist */
+enum {
+  F_COPY, F_EXTRAP, F_LIN, F_NAK4, F_NAT4, F_NAK3L, F_NAK3R, F_NAT3L,
+  F_NAT3R, F_SL_NAK, F_SL_NAT
+};
+
+/* have[j+3]: neighbour at offset j*s lies inside the line (j = -3..3).
+ * The offset -1 neighbour always exists (the point is at an odd multiple
+ * of s >= s). */
+static int choose_formula(int kind, int half_b, const int have[7]) {
+  const int hm3 = have[0], hm2 = have[1], hp1 = have[4], hp2 = have[5],
+            hp3 = have[6];
+  if (half_b) {
+    /* Eq. 10 (as printed: neighbours +-s, +-2s) and Eq. 11 */
+    if (kind == ORA_CUBIC_NAK && hp1 && hm2 && hp2) return F_SL_NAK;
+    if (kind == ORA_CUBIC_NAT && hp1 && hm2 && hp2 && hm3 && hp3)
+      return F_SL_NAT;
+  }
+  if (!hp1) return hm3 ? F_EXTRAP : F_COPY;
+  if (kind == ORA_LINEAR) return F_LIN;
+  if (hm3 && hp3) return kind == ORA_CUBIC_NAK ? F_NAK4 : F_NAT4;
+  if (hm3) return kind == ORA_CUBIC_NAK ? F_NAK3L : F_NAT3L;
+  if (hp3) return kind == ORA_CUBIC_NAK ? F_NAK3R : F_NAT3R;
+  return F_LIN;
+}
+
+/* which offsets (-3..3 -> bit j+3) a formula reads */
+static unsigned formula_reads(int f) {
+  switch (f) {
+    case F_COPY: return 1u << 2;
+    case F_EXTRAP: return (1u << 0) | (1u << 2);
+    case F_LIN: return (1u << 2) | (1u << 4);
+    case F_NAK4: case F_NAT4: return (1u << 0) | (1u << 2) | (1u << 4) | (1u << 6);
+    case F_NAK3L: case F_NAT3L: return (1u << 0) | (1u << 2) | (1u << 4);
+    case F_NAK3R: case F_NAT3R: return (1u << 2) | (1u << 4) | (1u << 6);
+    case F_SL_NAK: return (1u << 1) | (1u << 2) | (1u << 4) | (1u << 5);
+    case F_SL_NAT: return 0x77u; /* all but the centre */
+  }
+  return 0;
+}
+
+/* v[j+3] = neighbour value at offset j*s (only the ones read are set) */
+static float eval_formula(int f, const float v[7]) {
+  const float m3 = v[0], m2 = v[1], m1 = v[2], p1 = v[4], p2 = v[5],
+              p3 = v[6];
+  switch (f) {
+    case F_COPY: /* no right neighbour and no d-3: repeat d-1 */
+      return m1;
+    case F_EXTRAP: /* line through d-3, d-1 evaluated at 0 */
+      return (m1 * 3.0f - m3) / 2.0f;
+    case F_LIN: /* Eq. 2 */
+      return (m1 + p1) * 0.5f;
+    case F_NAK4: /* Eq. 4: (-1, 9, 9, -1) / 16 */
+      return ((m1 + p1) * 9.0f - (m3 + p3)) / 16.0f;
+    case F_NAT4: /* Eq. 6: (-3, 23, 23, -3) / 40 */
+      return ((m1 + p1) * 23.0f - (m3 + p3) * 3.0f) / 40.0f;
+    case F_NAK3L: /* quadratic through d-3, d-1, d+1: (-1, 6, 3) / 8 */
+      return ((m1 * 6.0f + p1 * 3.0f) - m3) / 8.0f;
+    case F_NAK3R: /* mirror: (3, 6, -1) / 8 on d-1, d+1, d+3 */
+      return ((m1 * 3.0f + p1 * 6.0f) - p3) / 8.0f;
+    case F_NAT3L: /* natural spline on knots -3, -1, 1: (-3, 22, 13) / 32 */
+      return ((m1 * 22.0f + p1 * 13.0f) - m3 * 3.0f) / 32.0f;
+    case F_NAT3R: /* mirror: (13, 22, -3) / 32 on d-1, d+1, d+3 */
+      return ((m1 * 13.0f + p1 * 22.0f) - p3 * 3.0f) / 32.0f;
+    case F_SL_NAK: /* Eq. 10: (-1, 4, 4, -1) / 6 on d-2, d-1, d+1, d+2 */
+      return ((m1 + p1) * 4.0f - (m2 + p2)) / 6.0f;
+    case F_SL_NAT: /* Eq. 11: (3, -18, 46, 46, -18, 3) / 62 */
+      return (((m1 + p1) * 46.0f - (m2 + p2) * 18.0f) + (m3 + p3) * 3.0f) /
+             62.0f;
+  }
+  return 0.0f;
+}
+
+static void line_have(uint64_t c, uint64_t n, uint64_t s, int have[7]) {
+  for (int j = -3; j <= 3; ++j) {
+    if (j == 0) {
+      have[3] = 1;
+      continue;
+    }
+    uint64_t a = (uint64_t)(j < 0 ? -j : j) * s;
+    have[j + 3] = j < 0 ? (c >= a) : (c + a <= n - 1);
+  }
+}
+
+float ora_predict_1d(int kind, int half_b, const float* line, uint64_t n,
+                     uint64_t pos, uint64_t s) {
+  int have[7];
+  float v[7] = {0, 0, 0, 0, 0, 0, 0};
+  line_have(pos, n, s, have);
+  int f = choose_formula(kind, half_b, have);
+  unsigned rd = formula_reads(f);
+  for (int j = 0; j < 7; ++j)
+    if (rd & (1u << j)) v[j] = line[pos + (uint64_t)(j - 3) * s];
+  return eval_formula(f, v);
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 4 Step 3: linear quantization with an exact bound check        */
+/* ------------------------------------------------------------------ */
+/* |r - x| <= e decided exactly: d = rn(r - x) plus its TwoSum residual. */
+static int within_bound(float r, float x, float e) {
+  float nx = -x;
+  float d = r + nx;
+  float bb = d - r;
+  float res = (r - (d - bb)) + (nx - bb);
+  float ad = fabsf(d);
+  if (ad < e) return 1;
+  if (ad == e) {
+    if (d > 0.0f) return res <= 0.0f;
+    if (d < 0.0f) return res >= 0.0f;
+  }
+  return 0; /* also NaN */
+}
+
+uint16_t ora_quantize(float x, float p, float el, float inv2, float twoe,
+                      float* recon) {
+  float diff = x - p;
+  float m = fabsf(diff) * inv2 + 0.5f;
+  if (m < 32768.0f) { /* false for NaN */
+    int k = (int)m;
+    int q = diff < 0.0f ? -k : k;
+    float r = p + (float)q * twoe;
+    if (within_bound(r, x, el)) {
+      *recon = r;
+      return (uint16_t)(q + ORA_RADIUS);
+    }
+  }
+  *recon = x; /* unpredictable: stored verbatim in the outlier list */
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Eq. 14 weights                                                      */
+/* ------------------------------------------------------------------ */
+float ora_md_weight(const double* inv_var, unsigned mask, int d) {
+  double sum = 0.0;
+  for (int j = 0; j < 3; ++j)
+    if (mask & (1u << j)) sum = sum + inv_var[j];
+  return (float)(inv_var[d] / sum);
+}
+
+/* ------------------------------------------------------------------ */
+/* the level-wise sweep                                                */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  const geom* g;
+  const ora_config* c;
+  const float* x;      /* compress: input; decompress: NULL */
+  float* recon;        /* N */
+  uint16_t* codes;     /* N */
+  uint32_t* stamp;     /* N: 0 unknown, else the sub-pass that set it */
+  uint32_t cur;        /* current sub-pass stamp */
+  float el[ORA_MAX_LEVELS], inv2[ORA_MAX_LEVELS], twoe[ORA_MAX_LEVELS];
+  uint64_t bad_reads, double_visits, predicted;
+  int decompress;
+  uint64_t nb[3];      /* blocks per real dim (block map) */
+} sweep;
+
+static float load_known(sweep* w, uint64_t idx) {
+  uint32_t st = w->stamp[idx];
+  if (st == 0 || st >= w->cur) w->bad_reads++;
+  return w->recon[idx];
+}
+
+/* per-point interpolator kind and same-level flag */
+static void point_cfg(const sweep* w, int l, const uint64_t c[3], int* kind,
+                      int* same) {
+  const geom* g = w->g;
+  if (w->c->blockwise) {
+    uint64_t b = 0;
+    for (int d = 0; d < g->ndim; ++d) {
+      uint64_t bd = c[d + g->off] / (uint64_t)w->c->block_size;
+      b = b * w->nb[d] + bd;
+    }
+    uint8_t v = w->c->blockmap[b];
+    *kind = v & 3;
+    *same = (v >> 2) & 1;
+  } else {
+    *kind = w->c->interp[l - 1];
+    *same = w->c->same_level[l - 1];
+  }
+  if (*kind > ORA_CUBIC_NAT) *kind = ORA_CUBIC_NAT;
+  if (*kind == ORA_LINEAR) *same = 0;
+}
+
+/* prediction along slot d for the point at linear index i */
+static float predict_dim(sweep* w, uint64_t i, const uint64_t c[3], int d,
+                         uint64_t s, int kind, int half_b) {
+  const geom* g = w->g;
+  int have[7];
+  float v[7] = {0, 0, 0, 0, 0, 0, 0};
+  line_have(c[d], g->n[d], s, have);
+  int f = choose_formula(kind, half_b, have);
+  unsigned rd = formula_reads(f);
+  for (int j = 0; j < 7; ++j) {
+    if (!(rd & (1u << j))) continue;
+    int64_t o = (int64_t)(j - 3) * (int64_t)s * (int64_t)g->st[d];
+    v[j] = load_known(w, (uint64_t)((int64_t)i + o));
+  }
+  return eval_formula(f, v);
+}
+
+static void process_point(sweep* w, int l, uint64_t i, const uint64_t c[3],
+                          int md, int pass_slot, unsigned odd_mask,
+                          int half_b, int kind) {
+  const geom* g = w->g;
+  uint64_t s = (uint64_t)1 << (l - 1);
+  float p;
+  if (!md) {
+    p = predict_dim(w, i, c, pass_slot, s, kind, half_b);
+  } else {
+    /* Eq. 8: weighted sum over all odd dimensions, ascending, with the
+     * Eq. 14 weights of this odd-dimension set */
+    unsigned real_mask = 0;
+    for (int d = 0; d < 3; ++d)
+      if (odd_mask & (1u << d)) real_mask |= 1u << (d - g->off);
+    float acc = 0.0f;
+    int first = 1;
+    for (int d = 0; d < 3; ++d) {
+      if (!(odd_mask & (1u << d))) continue;
+      float pd = predict_dim(w, i, c, d, s, kind, half_b);
+      float wd = ora_md_weight(w->c->md_inv_var, real_mask, d - g->off);
+      float t = wd * pd;
+      if (first) {
+        acc = t;
+        first = 0;
+      } else {
+        acc = acc + t;
+      }
+    }
+    p = acc;
+  }
+  if (w->stamp[i] != 0) w->double_visits++;
+  w->predicted++;
+  if (!w->decompress) {
+    float r;
+    w->codes[i] = ora_quantize(w->x[i], p, w->el[l - 1], w->inv2[l - 1],
+                               w->twoe[l - 1], &r);
+    w->recon[i] = r;
+  } else {
+    uint16_t code = w->codes[i];
+    if (code != 0) {
+      int q = (int)code - ORA_RADIUS;
+      w->recon[i] = p + (float)q * w->twoe[l - 1];
+    } /* else: the outlier value is already in recon[i] */
+  }
+  w->stamp[i] = w->cur;
+}
+
+/* One level (stride s = 2^(l-1)), Sec. 5.1: the new points are the points
+ * of the stride-s grid that are not on the stride-2s grid. */
+static void run_level(sweep* w, int l) {
+  const geom* g = w->g;
+  const ora_config* c = w->c;
+  uint64_t s = (uint64_t)1 << (l - 1);
+  uint64_t step[3];
+  for (int d = 0; d < 3; ++d) step[d] = g->interp[d] ? s : 1;
+  int md = c->paradigm[l - 1] == ORA_MD;
+  int npass = g->k;
+  for (int pj = 0; pj < npass; ++pj) {
+    int pass_slot = -1;
+    if (!md) pass_slot = c->order[l - 1][pj] + g->off;
+    for (int half = 0; half < 2; ++half) {
+      w->cur++;
+      uint64_t cc[3];
+      for (cc[0] = 0; cc[0] < g->n[0]; cc[0] += step[0])
+        for (cc[1] = 0; cc[1] < g->n[1]; cc[1] += step[1])
+          for (cc[2] = 0; cc[2] < g->n[2]; cc[2] += step[2]) {
+            /* classify: u_d = c_d / s on interpolation slots */
+            unsigned odd = 0;
+            int nodd = 0;
+            for (int d = 0; d < 3; ++d)
+              if (g->interp[d] && ((cc[d] / s) & 1)) {
+                odd |= 1u << d;
+                nodd++;
+              }
+            if (nodd == 0) continue; /* on the stride-2s grid: known */
+            unsigned S;
+            if (!md) {
+              /* 1D-style pass j along order[j]: odd on that dim, any
+               * parity on earlier dims of the order, even on later ones */
+              if (!(odd & (1u << pass_slot))) continue;
+              int ok = 1;
+              for (int m = pj + 1; m < g->k; ++m) {
+                int sl = c->order[l - 1][m] + g->off;
+                if (odd & (1u << sl)) ok = 0;
+              }
+              if (!ok) continue;
+              S = 1u << pass_slot;
+            } else {
+              /* MD sub-pass pj+1: exactly pj+1 odd coordinates */
+              if (nodd != pj + 1) continue;
+              S = odd;
+            }
+            int kind, same;
+            point_cfg(w, l, cc, &kind, &same);
+            /* same-level split (Sec. 5.4.2): parity of sum (u_d - 1)/2 */
+            unsigned par = 0;
+            for (int d = 0; d < 3; ++d)
+              if (S & (1u << d)) par += (unsigned)(((cc[d] / s) - 1) / 2);
+            int in_b = same && (par & 1u);
+            if (in_b != half) continue;
+            uint64_t i = cc[0] * g->st[0] + cc[1] * g->st[1] + cc[2];
+            process_point(w, l, i, cc, md, pass_slot, S, in_b, kind);
+          }
+    }
+  }
+}
+
+static int is_anchor(const geom* g, const uint64_t c[3]) {
+  for (int d = 0; d < 3; ++d)
+    if (g->interp[d] && (c[d] % (uint64_t)g->A) != 0) return 0;
+  return 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* Huffman (Sec. 4 Step 4)                                             */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  uint64_t f;
+  uint32_t sym;
+} leaf_t;
+
+static int leaf_cmp(const void* a, const void* b) {
+  const leaf_t* x = (const leaf_t*)a;
+  const leaf_t* y = (const leaf_t*)b;
+  if (x->f != y->f) return x->f < y->f ? -1 : 1;
+  return x->sym < y->sym ? -1 : (x->sym > y->sym ? 1 : 0);
+}
+
+/* Two-queue Huffman merge: leaves sorted by (frequency, symbol); the
+ * internal nodes form a FIFO in creation order; each pick takes the
+ * smaller weight and, on a tie, the leaf.  Lengths are leaf depths. */
+int ora_huffman_lengths(const uint64_t* freq, int nsym, uint8_t* lens) {
+  int n = 0;
+  for (int i = 0; i < nsym; ++i) {
+    lens[i] = 0;
+    if (freq[i]) n++;
+  }
+  if (n <= 1) return ORA_OK; /* a lone symbol gets the empty code */
+  leaf_t* lv = (leaf_t*)malloc(sizeof(leaf_t) * (size_t)n);
+  uint64_t* iw = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)n);
+  uint32_t* parent = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(2 * n));
+  uint32_t* depth = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(2 * n));
+  if (!lv || !iw || !parent || !depth) {
+    free(lv); free(iw); free(parent); free(depth);
+    return ORA_ERR_NO_MEMORY;
+  }
+  int j = 0;
+  for (int i = 0; i < nsym; ++i)
+    if (freq[i]) {
+      lv[j].f = freq[i];
+      lv[j].sym = (uint32_t)i;
+      j++;
+    }
+  qsort(lv, (size_t)n, sizeof(leaf_t), leaf_cmp);
+  int a = 0, b = 0, m = 0; /* leaf head, internal head, internal count */
+  for (int t = 0; t < n - 1; ++t) {
+    uint32_t pick[2];
+    uint64_t wsum = 0;
+    for (int r = 0; r < 2; ++r) {
+      if (a < n && (b >= m || lv[a].f <= iw[b])) {
+        pick[r] = (uint32_t)a;
+        wsum += lv[a].f;
+        a++;
+      } else {
+        pick[r] = (uint32_t)(n + b);
+        wsum += iw[b];
+        b++;
+      }
+    }
+    iw[m] = wsum;
+    parent[pick[0]] = (uint32_t)(n + m);
+    parent[pick[1]] = (uint32_t)(n + m);
+    m++;
+  }
+  int root = 2 * n - 2;
+  depth[root] = 0;
+  for (int id = root - 1; id >= 0; --id) depth[id] = depth[parent[id]] + 1;
+  int rc = ORA_OK;
+  for (int i = 0; i < n; ++i) {
+    if (depth[i] > 63) rc = ORA_ERR_INVALID_ARG;
+    lens[lv[i].sym] = (uint8_t)depth[i];
+  }
+  free(lv); free(iw); free(parent); free(depth);
+  return rc;
+}
+
+/* Canonical codes: symbols ordered by (length, symbol); the first code is
+ * 0 and each next code is (previous + 1) shifted left by the length step. */
+int ora_canonical_codes(const uint8_t* lens, int nsym, uint64_t* codes) {
+  uint64_t bl_count[65] = {0};
+  uint64_t next[65] = {0};
+  int maxlen = 0;
+  for (int i = 0; i < nsym; ++i) {
+    codes[i] = 0;
+    if (lens[i] > 63) return ORA_ERR_INVALID_ARG;
+    if (lens[i]) {
+      bl_count[lens[i]]++;
+      if (lens[i] > maxlen) maxlen = lens[i];
+    }
+  }
+  uint64_t code = 0;
+  for (int bits = 1; bits <= maxlen; ++bits) {
+    code = (code + bl_count[bits - 1]) << 1;
+    next[bits] = code;
+  }
+  for (int i = 0; i < nsym; ++i)
+    if (lens[i]) codes[i] = next[lens[i]]++;
+  return ORA_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* compress                                                            */
+/* ------------------------------------------------------------------ */
+static uint64_t count_anchors(const geom* g) {
+  uint64_t na = 1;
+  for (int d = 0; d < 3; ++d)
+    na *= g->interp[d] ? (g->n[d] + (uint64_t)g->A - 1) / (uint64_t)g->A
+                       : g->n[d];
+  return na;
+}
+
+static uint64_t count_blocks(const geom* g, int bs, uint64_t nb[3]) {
+  uint64_t t = 1;
+  for (int d = 0; d < g->ndim; ++d) {
+    nb[d] = (g->n[d + g->off] + (uint64_t)bs - 1) / (uint64_t)bs;
+    t *= nb[d];
+  }
+  return t;
+}
+
+uint64_t ora_compress_bound(int ndim, const uint64_t* dims) {
+  uint64_t N = 1;
+  for (int d = 0; d < ndim; ++d) N *= dims[d];
+  uint64_t nch = (N + 255) / 256;
+  /* header + anchors/outliers (<= N floats each) + block map + chunk
+   * words + table + bitstream (<= 17 bits per symbol + one pad word per
+   * chunk) */
+  return 512 + 16 * 8 + 4 * N + 4 * N + N + 4 * nch + 3 * 65536 + 4 +
+         (17 * N) / 8 + 4 * nch + 64;
+}
+
+static int write_const(uint8_t* out, uint64_t cap, uint64_t* out_size,
+                       int ndim, const uint64_t* dims, int eb_mode, double eb,
+                       float v, const ora_config* c) {
+  if (cap < ORA_HEADER_BYTES) return ORA_ERR_OUT_TOO_SMALL;
+  memset(out, 0, ORA_HEADER_BYTES);
+  put_u32(out, H_MAGIC, MAGIC);
+  put_u32(out, H_VERSION, VERSION);
+  put_u32(out, H_FLAGS, FLAG_CONST);
+  put_u32(out, H_NDIM, (uint32_t)ndim);
+  for (int d = 0; d < 3; ++d) put_u64(out, H_DIMS + 8 * d, d < ndim ? dims[d] : 1);
+  put_u32(out, H_EBMODE, (uint32_t)eb_mode);
+  put_u32(out, H_ANCHOR, (uint32_t)c->anchor_stride);
+  put_f64(out, H_EBVALUE, eb);
+  put_f32(out, H_E, 0.0f);
+  put_f32(out, H_CONST, v);
+  put_u32(out, H_FROZEN, (uint32_t)(int32_t)-1);
+  put_u32(out, H_CHUNK, (uint32_t)c->chunk_syms);
+  for (int s = H_OFF_ANCHORS; s <= H_OFF_BLOCKMAP; s += 8)
+    put_u64(out, (uint64_t)s, ORA_HEADER_BYTES);
+  put_u64(out, H_TOTAL, ORA_HEADER_BYTES);
+  *out_size = ORA_HEADER_BYTES;
+  return ORA_OK;
+}
+
+int ora_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode,
+                 double eb, const ora_config* cfg_in, uint8_t* out,
+                 uint64_t cap, uint64_t* out_size, uint16_t* codes_out,
+                 float* recon_out, ora_stats* stats) {
+  ora_config defc;
+  if (!x || !dims || !out || !out_size) return ORA_ERR_INVALID_ARG;
+  if (ndim < 1 || ndim > 3) return ORA_ERR_INVALID_ARG;
+  if (!cfg_in) {
+    ora_default_config(ndim, &defc);
+    cfg_in = &defc;
+  }
+  const ora_config* c = cfg_in;
+  geom g;
+  int rc = geom_init(&g, ndim, dims, c->anchor_stride, c->frozen_dim);
+  if (rc) return rc;
+  rc = check_config(&g, c);
+  if (rc) return rc;
+  if (eb_mode != ORA_EB_ABS && eb_mode != ORA_EB_REL) return ORA_ERR_INVALID_ARG;
+  if (!(eb > 0.0) || !isfinite(eb)) return ORA_ERR_INVALID_ARG;
+  const uint64_t N = g.N;
+  if (stats) memset(stats, 0, sizeof(*stats));
+
+  /* error bound: absolute, or eps * value range (Sec. 7.1.3) */
+  float e;
+  float vmin = x[0], vmax = x[0];
+  if (eb_mode == ORA_EB_REL) {
+    for (uint64_t i = 0; i < N; ++i) {
+      float v = x[i];
+      if (!isfinite(v)) return ORA_ERR_NONFINITE;
+      if (v < vmin) vmin = v;
+      if (v > vmax) vmax = v;
+    }
+    double range = (double)vmax - (double)vmin;
+    if (range == 0.0)
+      return write_const(out, cap, out_size, ndim, dims, eb_mode, eb, x[0], c);
+    e = (float)(eb * range);
+  } else {
+    e = (float)eb;
+  }
+  if (!(e > 0.0f) || !isfinite(e)) return ORA_ERR_INVALID_ARG;
+
+  sweep w;
+  memset(&w, 0, sizeof(w));
+  w.g = &g;
+  w.c = c;
+  rc = ora_level_params(e, c->alpha, c->beta, g.L, w.el, w.inv2, w.twoe);
+  if (rc) return rc;
+  uint64_t nblocks = 0;
+  if (c->blockwise) nblocks = count_blocks(&g, c->block_size, w.nb);
+
+  w.x = x;
+  w.recon = (float*)malloc(sizeof(float) * N);
+  w.codes = (uint16_t*)malloc(sizeof(uint16_t) * N);
+  w.stamp = (uint32_t*)calloc(N, sizeof(uint32_t));
+  if (!w.recon || !w.codes || !w.stamp) {
+    free(w.recon); free(w.codes); free(w.stamp);
+    return ORA_ERR_NO_MEMORY;
+  }
+
+  /* anchors (Sec. 5.1): stored losslessly, code = radius (zero error) */
+  uint64_t na = count_anchors(&g);
+  float* anchors = (float*)malloc(sizeof(float) * (na ? na : 1));
+  uint64_t ai = 0;
+  {
+    uint64_t cc[3];
+    for (cc[0] = 0; cc[0] < g.n[0]; ++cc[0])
+      for (cc[1] = 0; cc[1] < g.n[1]; ++cc[1])
+        for (cc[2] = 0; cc[2] < g.n[2]; ++cc[2]) {
+          uint64_t i = cc[0] * g.st[0] + cc[1] * g.st[1] + cc[2];
+          if (is_anchor(&g, cc)) {
+            anchors[ai++] = x[i];
+            w.recon[i] = x[i];
+            w.codes[i] = ORA_RADIUS;
+            w.stamp[i] = 1;
+          }
+        }
+  }
+  w.cur = 1;
+
+  /* the level sweep, coarse to fine */
+  for (int l = g.L; l >= 1; --l) run_level(&w, l);
+
+  /* every point is either an anchor or predicted exactly once */
+  uint64_t missing = 0;
+  for (uint64_t i = 0; i < N; ++i)
+    if (w.stamp[i] == 0) missing++;
+
+  /* outliers in row-major order */
+  uint64_t nout = 0;
+  for (uint64_t i = 0; i < N; ++i)
+    if (w.codes[i] == 0) nout++;
+  float* outl = (float*)malloc(sizeof(float) * (nout ? nout : 1));
+  {
+    uint64_t k = 0;
+    for (uint64_t i = 0; i < N; ++i)
+      if (w.codes[i] == 0) outl[k++] = x[i];
+  }
+
+  /* Huffman over the row-major code array */
+  uint64_t* hist = (uint64_t*)calloc(65536, sizeof(uint64_t));
+  uint8_t* lens = (uint8_t*)malloc(65536);
+  uint64_t* code64 = (uint64_t*)malloc(sizeof(uint64_t) * 65536);
+  for (uint64_t i = 0; i < N; ++i) hist[w.codes[i]]++;
+  rc = ora_huffman_lengths(hist, 65536, lens);
+  if (!rc) rc = ora_canonical_codes(lens, 65536, code64);
+  uint32_t nused = 0;
+  for (int i = 0; i < 65536; ++i)
+    if (hist[i]) nused++;
+  const uint64_t C = (uint64_t)c->chunk_syms;
+  const uint64_t nch = (N + C - 1) / C;
+  uint32_t* chw = (uint32_t*)calloc(nch, sizeof(uint32_t));
+  uint64_t sumlen = 0;
+  for (uint64_t i = 0; i < N; ++i) sumlen += lens[w.codes[i]];
+  uint64_t maxwords = sumlen / 32 + nch + 1;
+  uint32_t* bits = (uint32_t*)calloc(maxwords, sizeof(uint32_t));
+  uint64_t wpos = 0;
+  for (uint64_t ch = 0; ch < nch && !rc; ++ch) {
+    uint64_t w0 = wpos;
+    uint32_t cur = 0;
+    int nb = 0;
+    uint64_t e_ = (ch + 1) * C < N ? (ch + 1) * C : N;
+    for (uint64_t i = ch * C; i < e_; ++i) {
+      uint16_t sy = w.codes[i];
+      int L_ = lens[sy];
+      uint64_t cw = code64[sy];
+      for (int b = L_ - 1; b >= 0; --b) { /* MSB first */
+        cur = (cur << 1) | (uint32_t)((cw >> b) & 1u);
+        nb++;
+        if (nb == 32) {
+          bits[wpos++] = cur;
+          cur = 0;
+          nb = 0;
+        }
+      }
+    }
+    if (nb) bits[wpos++] = cur << (32 - nb);
+    chw[ch] = (uint32_t)(wpos - w0);
+  }
+
+  /* container */
+  uint64_t off_anchors = ORA_HEADER_BYTES;
+  uint64_t off_blockmap = align16(off_anchors + 4 * na);
+  uint64_t off_chunkw = align16(off_blockmap + nblocks);
+  uint64_t off_table = align16(off_chunkw + 4 * nch);
+  uint64_t off_outl = align16(off_table + 3 * (uint64_t)nused);
+  uint64_t off_bits = align16(off_outl + 4 * nout);
+  uint64_t total = off_bits + 4 * wpos;
+  if (!rc && total > cap) rc = ORA_ERR_OUT_TOO_SMALL;
+  if (!rc && (missing || w.bad_reads || w.double_visits)) rc = ORA_ERR_SELFCHECK;
+  if (!rc) {
+    memset(out, 0, total);
+    put_u32(out, H_MAGIC, MAGIC);
+    put_u32(out, H_VERSION, VERSION);
+    put_u32(out, H_FLAGS, 0);
+    put_u32(out, H_NDIM, (uint32_t)ndim);
+    for (int d = 0; d < 3; ++d) put_u64(out, H_DIMS + 8 * d, d < ndim ? dims[d] : 1);
+    put_u32(out, H_EBMODE, (uint32_t)eb_mode);
+    put_u32(out, H_ANCHOR, (uint32_t)c->anchor_stride);
+    put_f64(out, H_EBVALUE, eb);
+    put_f32(out, H_E, e);
+    put_f32(out, H_CONST, 0.0f);
+    put_u32(out, H_FROZEN, (uint32_t)c->frozen_dim);
+    put_u32(out, H_CHUNK, (uint32_t)c->chunk_syms);
+    put_f64(out, H_ALPHA, c->alpha);
+    put_f64(out, H_BETA, c->beta);
+    for (int d = 0; d < 3; ++d) put_f64(out, H_MDIV + 8 * d, c->md_inv_var[d]);
+    for (int l = 0; l < ORA_MAX_LEVELS; ++l) {
+      int used = l < g.L;
+      put_u8(out, H_INTERP + l, used ? c->interp[l] : 0);
+      put_u8(out, H_PARADIGM + l, used ? c->paradigm[l] : 0);
+      put_u8(out, H_SAME + l, used ? c->same_level[l] : 0);
+      for (int j = 0; j < 3; ++j)
+        put_u8(out, H_ORDER + 3 * l + j,
+               (used && j < g.k) ? c->order[l][j] : 255);
+    }
+    put_u32(out, H_PREDICTOR, 0);
+    put_u32(out, H_BLOCKWISE, (uint32_t)c->blockwise);
+    put_u64(out, H_NANCHORS, na);
+    put_u64(out, H_NOUTLIERS, nout);
+    put_u32(out, H_NUSED, nused);
+    put_u32(out, H_BLOCKSIZE, (uint32_t)c->block_size);
+    put_u64(out, H_NCHUNKS, nch);
+    put_u64(out, H_TOTALWORDS, wpos);
+    put_u64(out, H_OFF_ANCHORS, off_anchors);
+    put_u64(out, H_OFF_CHUNKW, off_chunkw);
+    put_u64(out, H_OFF_TABLE, off_table);
+    put_u64(out, H_OFF_OUTLIERS, off_outl);
+    put_u64(out, H_OFF_BITS, off_bits);
+    put_u64(out, H_OFF_BLOCKMAP, off_blockmap);
+    put_u64(out, H_TOTAL, total);
+    put_u64(out, H_NBLOCKS, nblocks);
+    for (uint64_t i = 0; i < na; ++i) put_f32(out, off_anchors + 4 * i, anchors[i]);
+    for (uint64_t i = 0; i < nblocks; ++i) put_u8(out, off_blockmap + i, c->blockmap[i]);
+    for (uint64_t i = 0; i < nch; ++i) put_u32(out, off_chunkw + 4 * i, chw[i]);
+    {
+      uint64_t k = 0;
+      for (int sy = 0; sy < 65536; ++sy)
+        if (hist[sy]) {
+          put_u16(out, off_table + 2 * k, (uint16_t)sy);
+          put_u8(out, off_table + 2 * (uint64_t)nused + k, lens[sy]);
+          k++;
+        }
+    }
+    for (uint64_t i = 0; i < nout; ++i) put_f32(out, off_outl + 4 * i, outl[i]);
+    for (uint64_t i = 0; i < wpos; ++i) put_u32(out, off_bits + 4 * i, bits[i]);
+    *out_size = total;
+  }
+  if (stats) {
+    stats->n_points = N;
+    stats->n_anchors = na;
+    stats->n_outliers = nout;
+    stats->n_used = nused;
+    stats->total_words = wpos;
+    stats->n_chunks = nch;
+    stats->predicted = w.predicted;
+    stats->bad_reads = w.bad_reads + missing;
+    stats->double_visits = w.double_visits;
+    stats->sum_len_bits = sumlen;
+    stats->e = e;
+    stats->vmin = vmin;
+    stats->vmax = vmax;
+  }
+  if (codes_out) memcpy(codes_out, w.codes, sizeof(uint16_t) * N);
+  if (recon_out) memcpy(recon_out, w.recon, sizeof(float) * N);
+  free(w.recon); free(w.codes); free(w.stamp); free(anchors); free(outl);
+  free(hist); free(lens); free(code64); free(chw); free(bits);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* decompress                                                          */
+/* ------------------------------------------------------------------ */
+int ora_inspect(const uint8_t* in, uint64_t size, int* ndim, uint64_t* dims,
+                double* abs_eb) {
+  if (!in || size < ORA_HEADER_BYTES) return ORA_ERR_CORRUPT;
+  if (get_u32(in, H_MAGIC) != MAGIC || get_u32(in, H_VERSION) != VERSION)
+    return ORA_ERR_CORRUPT;
+  int nd = (int)get_u32(in, H_NDIM);
+  if (nd < 1 || nd > 3) return ORA_ERR_CORRUPT;
+  if (ndim) *ndim = nd;
+  if (dims)
+    for (int d = 0; d < nd; ++d) dims[d] = get_u64(in, H_DIMS + 8 * d);
+  if (abs_eb) *abs_eb = (double)get_f32(in, H_E);
+  return ORA_OK;
+}
+
+int ora_decompress(const uint8_t* in, uint64_t size, float* out,
+                   uint64_t cap_elems) {
+  int ndim;
+  uint64_t dims[3];
+  int rc = ora_inspect(in, size, &ndim, dims, NULL);
+  if (rc) return rc;
+  if (!out) return ORA_ERR_INVALID_ARG;
+  uint64_t N = 1;
+  for (int d = 0; d < ndim; ++d) {
+    if (dims[d] == 0) return ORA_ERR_CORRUPT;
+    N *= dims[d];
+    if (N > 0xFFFFFFFFull) return ORA_ERR_CORRUPT;
+  }
+  if (N > cap_elems) return ORA_ERR_OUT_TOO_SMALL;
+  if (get_u64(in, H_TOTAL) > size) return ORA_ERR_CORRUPT;
+  if (get_u32(in, H_FLAGS) & FLAG_CONST) {
+    float v = get_f32(in, H_CONST);
+    for (uint64_t i = 0; i < N; ++i) out[i] = v;
+    return ORA_OK;
+  }
+  ora_config c;
+  memset(&c, 0, sizeof(c));
+  c.anchor_stride = (int32_t)get_u32(in, H_ANCHOR);
+  c.frozen_dim = (int32_t)get_u32(in, H_FROZEN);
+  c.chunk_syms = (int32_t)get_u32(in, H_CHUNK);
+  c.alpha = get_f64(in, H_ALPHA);
+  c.beta = get_f64(in, H_BETA);
+  for (int d = 0; d < 3; ++d) c.md_inv_var[d] = get_f64(in, H_MDIV + 8 * d);
+  for (int l = 0; l < ORA_MAX_LEVELS; ++l) {
+    c.interp[l] = in[H_INTERP + l];
+    c.paradigm[l] = in[H_PARADIGM + l];
+    c.same_level[l] = in[H_SAME + l];
+    for (int j = 0; j < 3; ++j) c.order[l][j] = in[H_ORDER + 3 * l + j];
+  }
+  c.blockwise = (int32_t)get_u32(in, H_BLOCKWISE);
+  c.block_size = (int32_t)get_u32(in, H_BLOCKSIZE);
+  geom g;
+  rc = geom_init(&g, ndim, dims, c.anchor_stride, c.frozen_dim);
+  if (rc) return ORA_ERR_CORRUPT;
+  uint64_t nb[3] = {1, 1, 1};
+  uint64_t nblocks = 0;
+  if (c.blockwise) {
+    if (c.block_size < 1) return ORA_ERR_CORRUPT;
+    nblocks = count_blocks(&g, c.block_size, nb);
+    if (get_u64(in, H_NBLOCKS) != nblocks) return ORA_ERR_CORRUPT;
+    uint64_t ob = get_u64(in, H_OFF_BLOCKMAP);
+    if (ob + nblocks > size) return ORA_ERR_CORRUPT;
+    c.blockmap = in + ob;
+  }
+  if (check_config(&g, &c)) return ORA_ERR_CORRUPT;
+  float e = get_f32(in, H_E);
+  if (!(e > 0.0f) || !isfinite(e)) return ORA_ERR_CORRUPT;
+
+  sweep w;
+  memset(&w, 0, sizeof(w));
+  w.g = &g;
+  w.c = &c;
+  w.decompress = 1;
+  for (int d = 0; d < 3; ++d) w.nb[d] = nb[d];
+  if (ora_level_params(e, c.alpha, c.beta, g.L, w.el, w.inv2, w.twoe))
+    return ORA_ERR_CORRUPT;
+
+  uint64_t na = get_u64(in, H_NANCHORS);
+  uint64_t nout = get_u64(in, H_NOUTLIERS);
+  uint32_t nused = get_u32(in, H_NUSED);
+  uint64_t nch = get_u64(in, H_NCHUNKS);
+  uint64_t twords = get_u64(in, H_TOTALWORDS);
+  const uint64_t C = (uint64_t)c.chunk_syms;
+  if (na != count_anchors(&g) || nch != (N + C - 1) / C || nused == 0 ||
+      nused > 65536 || nout > N)
+    return ORA_ERR_CORRUPT;
+  uint64_t oa = get_u64(in, H_OFF_ANCHORS), ocw = get_u64(in, H_OFF_CHUNKW),
+           ot = get_u64(in, H_OFF_TABLE), oo = get_u64(in, H_OFF_OUTLIERS),
+           obits = get_u64(in, H_OFF_BITS);
+  if (oa + 4 * na > size || ocw + 4 * nch > size ||
+      ot + 3 * (uint64_t)nused > size || oo + 4 * nout > size ||
+      obits + 4 * twords > size)
+    return ORA_ERR_CORRUPT;
+
+  /* canonical decode tables */
+  uint16_t* syms = (uint16_t*)malloc(sizeof(uint16_t) * nused);
+  uint8_t* lns = (uint8_t*)malloc(nused);
+  uint64_t cnt[65] = {0};
+  int maxlen = 0;
+  for (uint32_t k = 0; k < nused; ++k) {
+    syms[k] = get_u16(in, ot + 2 * (uint64_t)k);
+    lns[k] = in[ot + 2 * (uint64_t)nused + k];
+    if ((k > 0 && syms[k] <= syms[k - 1]) || lns[k] > 63 ||
+        (nused > 1 && lns[k] == 0) || (nused == 1 && lns[k] != 0)) {
+      free(syms); free(lns);
+      return ORA_ERR_CORRUPT;
+    }
+    cnt[lns[k]]++;
+    if (lns[k] > maxlen) maxlen = lns[k];
+  }
+  /* symbols sorted by (length, symbol): stable counting order */
+  uint64_t first[65] = {0}, offs[65] = {0};
+  uint16_t* sorted = (uint16_t*)malloc(sizeof(uint16_t) * nused);
+  {
+    uint64_t code = 0, pos = 0;
+    for (int b = 1; b <= maxlen; ++b) {
+      code = (code + cnt[b - 1]) << 1;
+      first[b] = code;
+      offs[b] = pos;
+      pos += cnt[b];
+    }
+    uint64_t fill[65];
+    memcpy(fill, offs, sizeof(fill));
+    for (uint32_t k = 0; k < nused; ++k)
+      if (lns[k]) sorted[fill[lns[k]]++] = syms[k];
+  }
+  uint16_t* codes = (uint16_t*)malloc(sizeof(uint16_t) * N);
+  w.codes = codes;
+  w.recon = out;
+  w.stamp = (uint32_t*)calloc(N, sizeof(uint32_t));
+  rc = ORA_OK;
+  uint64_t wbase = 0;
+  for (uint64_t ch = 0; ch < nch && !rc; ++ch) {
+    uint64_t nw = get_u32(in, ocw + 4 * ch);
+    if (wbase + nw > twords) {
+      rc = ORA_ERR_CORRUPT;
+      break;
+    }
+    uint64_t e_ = (ch + 1) * C < N ? (ch + 1) * C : N;
+    uint64_t bitpos = 0, nbits = nw * 32;
+    for (uint64_t i = ch * C; i < e_; ++i) {
+      if (nused == 1) {
+        codes[i] = syms[0];
+        continue;
+      }
+      uint64_t code = 0;
+      int len = 0, found = 0;
+      while (len < maxlen) {
+        if (bitpos >= nbits) break;
+        uint32_t word = get_u32(in, obits + 4 * (wbase + bitpos / 32));
+        uint32_t bit = (word >> (31 - (bitpos % 32))) & 1u;
+        bitpos++;
+        code = (code << 1) | bit;
+        len++;
+        if (cnt[len] && code >= first[len] && code - first[len] < cnt[len]) {
+          codes[i] = sorted[offs[len] + (code - first[len])];
+          found = 1;
+          break;
+        }
+      }
+      if (!found) {
+        rc = ORA_ERR_CORRUPT;
+        break;
+      }
+    }
+    wbase += nw;
+  }
+  if (!rc && wbase != twords) rc = ORA_ERR_CORRUPT;
+
+  if (!rc) {
+    /* anchors, then outliers scattered in row-major order */
+    uint64_t ai = 0, oi = 0;
+    uint64_t cc[3];
+    for (cc[0] = 0; cc[0] < g.n[0]; ++cc[0])
+      for (cc[1] = 0; cc[1] < g.n[1]; ++cc[1])
+        for (cc[2] = 0; cc[2] < g.n[2]; ++cc[2]) {
+          uint64_t i = cc[0] * g.st[0] + cc[1] * g.st[1] + cc[2];
+          if (is_anchor(&g, cc)) {
+            out[i] = get_f32(in, oa + 4 * ai);
+            ai++;
+            w.stamp[i] = 1;
+          } else if (codes[i] == 0) {
+            if (oi < nout) out[i] = get_f32(in, oo + 4 * oi);
+            oi++;
+          }
+        }
+    if (oi != nout) rc = ORA_ERR_CORRUPT;
+  }
+  if (!rc) {
+    w.cur = 1;
+    for (int l = g.L; l >= 1; --l) run_level(&w, l);
+    if (w.bad_reads || w.double_visits) rc = ORA_ERR_SELFCHECK;
+  }
+  free(syms); free(lns); free(sorted); free(codes); free(w.stamp);
+  return rc;
+}

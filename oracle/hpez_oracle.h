@@ -1,0 +1,117 @@
+/*
+ * hpez_oracle.h -- plain single-threaded CPU oracle of HPEZ (arXiv 2311.12133).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or helper with the CUDA path; the two meet only through the
+ * compressed byte stream, whose layout each side writes independently.
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math (strict IEEE
+ * binary32: one correctly rounded operation per source operator, no FMA).
+ */
+#ifndef HPEZ_ORACLE_H
+#define HPEZ_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORA_MAX_LEVELS 16
+#define ORA_RADIUS 32768
+#define ORA_HEADER_BYTES 512
+
+/* interpolator kinds (Sec. 5.2): Eq. 2 linear, Eq. 4 not-a-knot cubic,
+ * Eq. 6 natural cubic */
+enum { ORA_LINEAR = 0, ORA_CUBIC_NAK = 1, ORA_CUBIC_NAT = 2 };
+/* paradigms (Sec. 5.3): 1D-style (one direction per pass) or
+ * multi-dimensional (Eq. 8) */
+enum { ORA_1D = 0, ORA_MD = 1 };
+enum { ORA_EB_ABS = 0, ORA_EB_REL = 1 };
+
+enum {
+  ORA_OK = 0,
+  ORA_ERR_INVALID_ARG = -1,
+  ORA_ERR_NONFINITE = -2,
+  ORA_ERR_OUT_TOO_SMALL = -3,
+  ORA_ERR_CORRUPT = -4,
+  ORA_ERR_NO_MEMORY = -5,
+  ORA_ERR_SELFCHECK = -6
+};
+
+typedef struct {
+  int32_t anchor_stride; /* A: power of two in [2, 32768] (Sec. 5.1) */
+  int32_t frozen_dim;    /* -1 or the frozen dimension (Sec. 6.3) */
+  int32_t chunk_syms;    /* Huffman chunk length, power of two in [256, 32768] */
+  int32_t blockwise;     /* 1: per-block interpolator from blockmap (Sec. 6.6) */
+  int32_t block_size;    /* block side for the block map (Sec. 6.6: 32) */
+  int32_t pad_;
+  double alpha, beta;    /* Eq. 15 */
+  double md_inv_var[3];  /* 1/sigma_i^2 per dimension for Eq. 14 weights */
+  uint8_t interp[ORA_MAX_LEVELS];     /* per level l (index l-1) */
+  uint8_t paradigm[ORA_MAX_LEVELS];
+  uint8_t same_level[ORA_MAX_LEVELS]; /* Sec. 5.4.2, cubic only */
+  uint8_t order[ORA_MAX_LEVELS][3];   /* 1D-style dimension order */
+  const uint8_t* blockmap; /* per block: bits0-1 interp kind, bit2 same-level */
+} ora_config;
+
+/* Statistics of the last compress call (diagnostics for the tests). */
+typedef struct {
+  uint64_t n_points, n_anchors, n_outliers, n_used, total_words, n_chunks;
+  uint64_t predicted;    /* points predicted by the level sweep */
+  uint64_t bad_reads;    /* neighbour reads of points not known before the sub-pass */
+  uint64_t double_visits;/* points predicted more than once */
+  uint64_t sum_len_bits; /* sum over symbols of the Huffman code length */
+  float e;               /* absolute error bound in use */
+  float vmin, vmax;
+} ora_stats;
+
+uint64_t ora_compress_bound(int ndim, const uint64_t* dims);
+
+/* Compress x (row-major, dims slowest first).  eb_mode 0 = absolute error
+ * bound eb, 1 = value-range relative (e = eb * (max - min), Sec. 7.1.3).
+ * cfg == NULL uses ora_default_config(ndim).  codes_out (N entries) and
+ * recon_out (N entries) are optional.  Returns 0 or a negative ORA_ERR_*. */
+int ora_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode,
+                 double eb, const ora_config* cfg, uint8_t* out, uint64_t cap,
+                 uint64_t* out_size, uint16_t* codes_out, float* recon_out,
+                 ora_stats* stats);
+
+/* Decompress a stream into out (cap_elems floats). */
+int ora_decompress(const uint8_t* in, uint64_t size, float* out,
+                   uint64_t cap_elems);
+
+/* Read ndim/dims/abs eb from a header. */
+int ora_inspect(const uint8_t* in, uint64_t size, int* ndim, uint64_t* dims,
+                double* abs_eb);
+
+void ora_default_config(int ndim, ora_config* cfg);
+
+/* ---- building blocks exposed for the pin tests ---- */
+
+/* Prediction of line[pos] along a 1D line of n values spaced 1 apart with
+ * stride s (neighbours at pos +- s, +-2s, +-3s).  half_b selects the
+ * same-level formula (Eq. 10 / Eq. 11). */
+float ora_predict_1d(int kind, int half_b, const float* line, uint64_t n,
+                     uint64_t pos, uint64_t s);
+
+/* Linear quantization of x against prediction p (Sec. 4 Step 3). */
+uint16_t ora_quantize(float x, float p, float el, float inv2, float twoe,
+                      float* recon);
+
+/* Level error bounds (Eq. 15) and the derived quantizer constants. */
+int ora_level_params(float e, double alpha, double beta, int L, float* el,
+                     float* inv2, float* twoe);
+
+/* Huffman code lengths by the two-queue merge and canonical codes. */
+int ora_huffman_lengths(const uint64_t* freq, int nsym, uint8_t* lens);
+int ora_canonical_codes(const uint8_t* lens, int nsym, uint64_t* codes);
+
+/* MD weight of dimension d within the odd-dimension set `mask` (Eq. 14). */
+float ora_md_weight(const double* inv_var, unsigned mask, int d);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,204 @@
+"""Seeded synthetic float32 fields shaped like the paper's workloads.
+
+This module holds no compressor arithmetic: it only draws inputs, and both
+the CUDA path and the oracle consume the same arrays.  The paper evaluates
+on real datasets (Table 1: RTM, SEGSalt, Miranda, SCALE-LetKF, CESM-ATM,
+JHTDB); none are available here, so these stand-ins reproduce their shapes
+and broad statistics:
+
+* ``bumps``      sum of Gaussian bumps + low-frequency sinusoids + white noise
+* ``grf``        Gaussian random field with power spectrum ~ k^slope
+                 (slope -5/3: turbulence-like, JHTDB/Miranda stand-in)
+* ``lognormal``  exp of a GRF with variance 2 (density-like variant)
+* ``aniso``      k^-3 spectrum in the two long dims, white along the short
+                 one (SCALE-LetKF stand-in, 98x1200x1200)
+* ``climate2d``  latitude-banded mean + k^-3 noise + 5 % constant-fill
+                 masked rectangles (CESM-ATM 2D slice stand-in, 1800x3600)
+
+Every generator takes an integer seed and is deterministic (numpy PCG64).
+"""
+from __future__ import annotations
+
+import hashlib
+
+import numpy as np
+
+try:  # multi-threaded FFT when scipy is present
+    import scipy.fft as _fft
+
+    def _rfftn(a, axes=None):
+        return _fft.rfftn(a, axes=axes, workers=-1)
+
+    def _irfftn(a, s, axes=None):
+        return _fft.irfftn(a, s=s, axes=axes, workers=-1)
+except Exception:  # pragma: no cover - numpy fallback
+    def _rfftn(a, axes=None):
+        return np.fft.rfftn(a, axes=axes)
+
+    def _irfftn(a, s, axes=None):
+        return np.fft.irfftn(a, s=s, axes=axes)
+
+
+def seed_of(*parts) -> int:
+    """Stable 63-bit seed from arbitrary printable parts."""
+    h = hashlib.sha256("/".join(str(p) for p in parts).encode()).digest()
+    return int.from_bytes(h[:8], "little") >> 1
+
+
+def bumps(shape=(128, 128, 128), seed=0, n_bumps=32, noise=1e-4):
+    """Sum of ``n_bumps`` Gaussian bumps (amplitude U(-1,1), width U(4,24)
+    cells, centre uniform in the box) + 3 sinusoids (integer wave numbers
+    1..3 per axis, random phase, amplitude 0.1) + N(0, noise^2) noise."""
+    rng = np.random.default_rng(seed)
+    shape = tuple(int(s) for s in shape)
+    nd = len(shape)
+    axes = [np.arange(s, dtype=np.float64) for s in shape]
+    out = np.zeros(shape, dtype=np.float64)
+    for _ in range(n_bumps):
+        amp = rng.uniform(-1, 1)
+        width = rng.uniform(4, 24)
+        ctr = [rng.uniform(0, s) for s in shape]
+        g = None
+        for d in range(nd):
+            gd = np.exp(-0.5 * ((axes[d] - ctr[d]) / width) ** 2)
+            sh = [1] * nd
+            sh[d] = shape[d]
+            gd = gd.reshape(sh)
+            g = gd if g is None else g * gd
+        out += amp * g
+    for _ in range(3):
+        k = rng.integers(1, 4, size=nd)
+        ph = rng.uniform(0, 2 * np.pi)
+        arg = None
+        for d in range(nd):
+            sh = [1] * nd
+            sh[d] = shape[d]
+            a = (2 * np.pi * k[d] * axes[d] / shape[d]).reshape(sh)
+            arg = a if arg is None else arg + a
+        out += 0.1 * np.sin(arg + ph)
+    out += rng.normal(0.0, noise, size=shape)
+    return out.astype(np.float32)
+
+
+def _spectral_filter(shape, slope, axes):
+    """|k|^(slope/2) amplitude filter over the given axes (rfft layout on
+    the last of them); the k=0 mode is removed."""
+    ks = []
+    for j, ax in enumerate(axes):
+        n = shape[ax]
+        if j == len(axes) - 1:
+            k = np.fft.rfftfreq(n) * n
+        else:
+            k = np.fft.fftfreq(n) * n
+        sh = [1] * len(axes)
+        sh[j] = k.size
+        ks.append((k.reshape(sh)) ** 2)
+    k2 = ks[0]
+    for t in ks[1:]:
+        k2 = k2 + t
+    with np.errstate(divide="ignore"):
+        filt = np.where(k2 > 0, k2 ** (slope / 4.0), 0.0)
+    return filt
+
+
+def grf(shape=(128, 128, 128), seed=0, slope=-5.0 / 3.0):
+    """Gaussian random field, power spectrum ~ |k|^slope, unit variance."""
+    rng = np.random.default_rng(seed)
+    shape = tuple(int(s) for s in shape)
+    w = rng.standard_normal(shape, dtype=np.float32)
+    axes = tuple(range(len(shape)))
+    W = _rfftn(w, axes=axes)
+    del w
+    filt = _spectral_filter(shape, slope, axes).astype(np.float32)
+    W *= filt
+    g = _irfftn(W, s=shape, axes=axes).astype(np.float32, copy=False)
+    del W
+    g -= g.mean(dtype=np.float64)
+    g /= np.float32(g.std(dtype=np.float64))
+    return np.ascontiguousarray(g, dtype=np.float32)
+
+
+def lognormal(shape=(128, 128, 128), seed=0, slope=-5.0 / 3.0, var=2.0):
+    """exp(g), g the GRF above scaled to variance ``var``."""
+    g = grf(shape, seed, slope)
+    g *= np.float32(np.sqrt(var))
+    np.exp(g, out=g)
+    return g
+
+
+def aniso(shape=(98, 1200, 1200), seed=0, slope=-3.0):
+    """Planes along dim 0 are independent 2D fields with spectrum
+    ~ |k|^slope over dims (1, 2): smooth in the long dims, white along the
+    short one."""
+    rng = np.random.default_rng(seed)
+    shape = tuple(int(s) for s in shape)
+    w = rng.standard_normal(shape, dtype=np.float32)
+    W = _rfftn(w, axes=(1, 2))
+    del w
+    filt = _spectral_filter(shape, slope, (1, 2)).astype(np.float32)
+    W *= filt[None]
+    g = _irfftn(W, s=shape[1:], axes=(1, 2)).astype(np.float32, copy=False)
+    g -= g.mean(dtype=np.float64)
+    g /= np.float32(g.std(dtype=np.float64))
+    return np.ascontiguousarray(g, dtype=np.float32)
+
+
+def climate2d(shape=(1800, 3600), seed=0, mask_frac=0.05):
+    """Latitude-banded mean (cos of latitude plus bands) + k^-3 noise, with
+    rectangular regions covering ~``mask_frac`` of the area set to a constant
+    fill (the field minimum), like land masks in ocean fields."""
+    rng = np.random.default_rng(seed)
+    ny, nx = int(shape[0]), int(shape[1])
+    lat = np.linspace(-np.pi / 2, np.pi / 2, ny)
+    mean = (30.0 * np.cos(lat) + 3.0 * np.cos(6 * lat)).astype(np.float32)
+    noise = grf((ny, nx), seed=seed + 1, slope=-3.0)
+    f = mean[:, None] + 2.0 * noise
+    fill = np.float32(f.min())
+    area = 0
+    target = mask_frac * ny * nx
+    while area < target:
+        h = int(rng.integers(ny // 40, ny // 8))
+        w = int(rng.integers(nx // 40, nx // 8))
+        y0 = int(rng.integers(0, ny - h))
+        x0 = int(rng.integers(0, nx - w))
+        f[y0:y0 + h, x0:x0 + w] = fill
+        area += h * w
+    return np.ascontiguousarray(f, dtype=np.float32)
+
+
+GENERATORS = {
+    "bumps": bumps,
+    "grf": grf,
+    "lognormal": lognormal,
+    "aniso": aniso,
+    "climate2d": climate2d,
+}
+
+
+def make(kind: str, shape, seed: int) -> np.ndarray:
+    return GENERATORS[kind](tuple(shape), seed)
+
+
+def batch_mix(n_fields=64, seed=0, lo=32 ** 3, hi=256 * 384 * 384):
+    """Per-field (kind, shape, seed, rel eb) for the batched workload: sizes
+    log-uniform in [lo, hi] points, about 1/3 2D; generators from the plain
+    workloads; relative eb per field from {1e-2, 1e-3, 1e-4}."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_fields):
+        npts = float(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+        if rng.uniform() < 1.0 / 3.0:
+            a = rng.uniform(0.5, 2.0)
+            ny = max(8, int(round(np.sqrt(npts / a))))
+            nx = max(8, int(round(npts / ny)))
+            shape = (ny, nx)
+            kind = ["climate2d", "grf"][int(rng.integers(0, 2))]
+        else:
+            r = rng.uniform(0.5, 2.0, size=3)
+            r = r / np.prod(r) ** (1 / 3)
+            side = npts ** (1 / 3)
+            shape = tuple(max(8, int(round(side * v))) for v in r)
+            kind = ["bumps", "grf", "lognormal", "aniso"][int(rng.integers(0, 4))]
+        eb = [1e-2, 1e-3, 1e-4][int(rng.integers(0, 3))]
+        out.append((kind, shape, seed_of("batch", seed, i), eb))
+    return out
