@@ -1,0 +1,145 @@
+/*
+ * hpez.h -- C-ABI of libhpez.so: the HPEZ interpolation predict-and-quantize
+ * path (arXiv 2311.12133) as hand-written sm_103a CUDA kernels.
+ *
+ * Conventions for every entry point:
+ *  - Plain pointers and sizes only.  "d_" pointers are CUDA device pointers,
+ *    "h_" pointers are host pointers.  `stream` is a cudaStream_t passed as
+ *    void* (NULL = the legacy default stream).
+ *  - The caller owns every input and output buffer; the context owns the
+ *    device scratch it allocates (grown on demand, freed by hpez_destroy).
+ *  - Return value: HPEZ_OK (0) or a negative HPEZ_ERR_* code; nothing is
+ *    written to an output on error except where stated.  Errors that the
+ *    kernels detect (non-finite input, corrupt stream, capacity) are read
+ *    back at the end of the call, which synchronizes `stream` once.
+ *  - A context is not thread-safe; use one per host thread.
+ *  - Output streams must start at a 16-byte aligned device address
+ *    (cudaMalloc gives 256).
+ *
+ * Field layout: float32, row-major, dims[0] slowest, 1 <= ndim <= 3,
+ * every dim >= 1, total points < 2^32.
+ */
+#ifndef HPEZ_H
+#define HPEZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define HPEZ_API __attribute__((visibility("default")))
+#else
+#define HPEZ_API
+#endif
+
+#define HPEZ_MAX_LEVELS 16
+#define HPEZ_HEADER_BYTES 512
+
+/* error codes */
+#define HPEZ_OK 0
+#define HPEZ_ERR_INVALID_ARG (-1)    /* bad ndim/dims/eb/config/pointer */
+#define HPEZ_ERR_NONFINITE_INPUT (-2)/* NaN/Inf with a relative bound */
+#define HPEZ_ERR_OUT_TOO_SMALL (-3)  /* output capacity too small */
+#define HPEZ_ERR_CORRUPT_STREAM (-4) /* stream fails validation */
+#define HPEZ_ERR_NO_MEMORY (-5)      /* device allocation failed */
+#define HPEZ_ERR_CUDA (-7)           /* a CUDA runtime call failed */
+#define HPEZ_ERR_UNSUPPORTED (-8)    /* valid but not implemented */
+#define HPEZ_ERR_TIMEOUT (-9)        /* a bounded device wait gave up */
+
+/* error-bound modes: Sec. 3.1 Eq. 1 (absolute e) and Sec. 7.1.3
+ * (value-range relative eps, e = eps * (max - min)) */
+#define HPEZ_EB_ABS 0
+#define HPEZ_EB_REL 1
+
+/* interpolators, Sec. 5.2: Eq. 2 linear, Eq. 4 not-a-knot cubic, Eq. 6
+ * natural cubic (same-level forms Eq. 10 / Eq. 11, Sec. 5.4.2) */
+#define HPEZ_LINEAR 0
+#define HPEZ_CUBIC_NAK 1
+#define HPEZ_CUBIC_NAT 2
+/* paradigms, Sec. 5.3: 1D-style passes or multi-dimensional (Eq. 8) */
+#define HPEZ_PARADIGM_1D 0
+#define HPEZ_PARADIGM_MD 1
+
+/* Predictor configuration theta (Sec. 6.2-6.6).  Per-level arrays are
+ * indexed by l-1, l = 1 the finest level (stride 1). */
+typedef struct {
+  int32_t anchor_stride; /* A, power of two in [2, 32768] (Sec. 5.1) */
+  int32_t frozen_dim;    /* -1, or a dim never interpolated (Sec. 6.3) */
+  int32_t chunk_syms;    /* Huffman chunk, power of two in [256, 32768] */
+  int32_t blockwise;     /* 1: per-block interpolator map (Sec. 6.6) */
+  int32_t block_size;    /* block side of the map (Sec. 6.6 default 32) */
+  int32_t reserved;
+  double alpha, beta;    /* Eq. 15 level bounds, both >= 1 */
+  double md_inv_var[3];  /* 1/sigma_d^2 for the Eq. 14 weights, > 0 */
+  uint8_t interp[HPEZ_MAX_LEVELS];     /* HPEZ_LINEAR / _CUBIC_NAK / _NAT */
+  uint8_t paradigm[HPEZ_MAX_LEVELS];   /* HPEZ_PARADIGM_* */
+  uint8_t same_level[HPEZ_MAX_LEVELS]; /* Sec. 5.4.2, cubic only */
+  uint8_t order[HPEZ_MAX_LEVELS][3];   /* 1D-style dim order (interp dims) */
+  const uint8_t* h_blockmap; /* host; per block: bits 0-1 interp, bit 2
+                                same-level; row-major over ceil(n/bs) */
+} hpez_config;
+
+typedef struct hpez_ctx hpez_ctx;
+
+/* Create a context on CUDA device `device` (made current for the call).
+ * *out receives the handle.  Errors: INVALID_ARG, CUDA. */
+HPEZ_API int hpez_create(hpez_ctx** out, int device);
+
+/* Free the context and its device scratch.  NULL is accepted. */
+HPEZ_API int hpez_destroy(hpez_ctx* ctx);
+
+/* Default theta for ndim: A = 128/64/32 for 1D/2D/3D, not-a-knot cubic
+ * (Eq. 4) at every level, 1D-style order 0..ndim-1, alpha = beta = 1,
+ * chunk 4096, no freezing, no block map. */
+HPEZ_API int hpez_default_config(int ndim, hpez_config* out);
+
+/* Upper bound of the compressed size in bytes for a field of these dims. */
+HPEZ_API int hpez_compress_bound(int ndim, const uint64_t* dims, uint64_t* out_bytes);
+
+/* Compress (Sec. 4 Steps 2-4): anchors, level-wise interpolation
+ * prediction, linear quantization with outlier escape, Huffman coding.
+ *   d_in      device, N float32 (not modified)
+ *   eb_mode   HPEZ_EB_ABS (eb = e) or HPEZ_EB_REL (eb = eps)
+ *   cfg       host pointer, NULL = hpez_default_config(ndim)
+ *   d_out     device, out_cap bytes, 16-byte aligned
+ *   h_out_size host, receives the stream size
+ * Errors: INVALID_ARG, NONFINITE_INPUT (REL mode only), OUT_TOO_SMALL,
+ * NO_MEMORY, CUDA.  Synchronizes `stream` once at the end. */
+HPEZ_API int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
+                  const uint64_t* dims, int eb_mode, double eb,
+                  const hpez_config* cfg, void* d_out, uint64_t out_cap,
+                  uint64_t* h_out_size, void* stream);
+
+/* Decompress a stream made by hpez_compress (the mirror of the level
+ * sweep: x' = prediction + 2 e_l q, or the stored outlier).
+ *   d_in      device, in_size bytes, 16-byte aligned
+ *   d_out     device, out_cap_elems float32 (>= N)
+ * Reads the 512-byte header to the host first (one synchronization).
+ * Errors: CORRUPT_STREAM, OUT_TOO_SMALL, INVALID_ARG, NO_MEMORY, CUDA. */
+HPEZ_API int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
+                    float* d_out, uint64_t out_cap_elems, void* stream);
+
+/* Host-buffer forms of the two calls above: copy h_in to the device, run
+ * the call, copy the result back (all on `stream`, synchronous). */
+HPEZ_API int hpez_compress_host(hpez_ctx* ctx, const float* h_in, int ndim,
+                       const uint64_t* dims, int eb_mode, double eb,
+                       const hpez_config* cfg, void* h_out, uint64_t out_cap,
+                       uint64_t* h_out_size, void* stream);
+HPEZ_API int hpez_decompress_host(hpez_ctx* ctx, const void* h_in, uint64_t in_size,
+                         float* h_out, uint64_t out_cap_elems, void* stream);
+
+/* Parse a host copy of the header (>= 512 bytes): ndim, dims[3] and the
+ * absolute error bound in use.  Errors: CORRUPT_STREAM, INVALID_ARG. */
+HPEZ_API int hpez_inspect(const void* h_header, uint64_t n, int* ndim, uint64_t* dims,
+                 double* abs_eb);
+
+/* Static text for an error code. */
+HPEZ_API const char* hpez_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPEZ_H */

@@ -1,0 +1,864 @@
+// hpez_capi.cu -- the C-ABI entry points of libhpez.so (declared in
+// include/hpez.h): argument validation, the level/pass schedule, the device
+// scratch arena, and the launch sequence of compress and decompress.
+#include "hpez.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "hpez_internal.cuh"
+#include "hpez_launch.h"
+
+using namespace hpez;
+
+struct hpez_ctx {
+  int device = 0;
+  int num_sms = 152;
+  char* scratch = nullptr;
+  size_t scratch_cap = 0;
+  Ctl* h_ctl = nullptr;        // pinned
+  uint8_t* h_hdr = nullptr;    // pinned, 512 bytes
+  void* io_in = nullptr;       // device staging for the *_host calls
+  size_t io_in_cap = 0;
+  void* io_out = nullptr;
+  size_t io_out_cap = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------
+// header layout (byte offsets)
+// ---------------------------------------------------------------------
+enum : int {
+  H_MAGIC = 0, H_VERSION = 4, H_FLAGS = 8, H_NDIM = 12, H_DIMS = 16,
+  H_EBMODE = 40, H_ANCHOR = 44, H_EBVALUE = 48, H_E = 56, H_CONST = 60,
+  H_FROZEN = 64, H_CHUNK = 68, H_ALPHA = 72, H_BETA = 80, H_MDIV = 88,
+  H_INTERP = 112, H_PARADIGM = 128, H_SAME = 144, H_ORDER = 160,
+  H_PREDICTOR = 208, H_BLOCKWISE = 212, H_NANCHORS = 216, H_NOUTLIERS = 224,
+  H_NUSED = 232, H_BLOCKSIZE = 236, H_NCHUNKS = 240, H_TOTALWORDS = 248,
+  H_OFF_ANCHORS = 256, H_OFF_CHUNKW = 264, H_OFF_TABLE = 272,
+  H_OFF_OUTLIERS = 280, H_OFF_BITS = 288, H_OFF_BLOCKMAP = 296,
+  H_TOTAL = 304, H_NBLOCKS = 312
+};
+constexpr uint32_t kMagic = 0x5A455048u;  // "HPEZ"
+constexpr uint32_t kVersion = 1u;
+
+void wr32(uint8_t* b, int o, uint32_t v) { std::memcpy(b + o, &v, 4); }
+void wr64(uint8_t* b, int o, uint64_t v) { std::memcpy(b + o, &v, 8); }
+void wrf64(uint8_t* b, int o, double v) { std::memcpy(b + o, &v, 8); }
+uint32_t rd32(const uint8_t* b, int o) {
+  uint32_t v;
+  std::memcpy(&v, b + o, 4);
+  return v;
+}
+uint64_t rd64(const uint8_t* b, int o) {
+  uint64_t v;
+  std::memcpy(&v, b + o, 8);
+  return v;
+}
+double rdf64(const uint8_t* b, int o) {
+  double v;
+  std::memcpy(&v, b + o, 8);
+  return v;
+}
+float rdf32(const uint8_t* b, int o) {
+  float v;
+  std::memcpy(&v, b + o, 4);
+  return v;
+}
+
+uint64_t a16(uint64_t v) { return (v + 15) & ~(uint64_t)15; }
+bool pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// ---------------------------------------------------------------------
+// geometry plan
+// ---------------------------------------------------------------------
+struct Plan {
+  int ndim = 0, off = 0;
+  uint32_t n[3] = {1, 1, 1};
+  uint32_t fst[3] = {0, 0, 1};
+  uint32_t N = 1;
+  bool interp[3] = {false, false, false};
+  int k = 0, A = 0, L = 0;
+  LevelGeom grid[kMaxLevels + 1];  // grid[g]: stride 2^g (g = L: anchors)
+  uint32_t gsize[kMaxLevels + 1];
+  uint32_t C = 4096, nch = 0;
+  uint32_t nb[3] = {1, 1, 1};
+  uint32_t nblocks = 0;
+};
+
+int plan_geometry(Plan& p, int ndim, const uint64_t* dims, int A,
+                  int frozen) {
+  if (ndim < 1 || ndim > 3 || !dims) return HPEZ_ERR_INVALID_ARG;
+  if (frozen < -1 || frozen >= ndim || (ndim == 1 && frozen != -1))
+    return HPEZ_ERR_INVALID_ARG;
+  if (!pow2(A) || A < 2 || A > 32768) return HPEZ_ERR_INVALID_ARG;
+  p.ndim = ndim;
+  p.off = 3 - ndim;
+  uint64_t N = 1;
+  for (int d = 0; d < ndim; ++d) {
+    if (dims[d] == 0) return HPEZ_ERR_INVALID_ARG;
+    N *= dims[d];
+    if (N > 0xFFFFFFFFull) return HPEZ_ERR_INVALID_ARG;
+    p.n[d + p.off] = (uint32_t)dims[d];
+    p.interp[d + p.off] = d != frozen;
+  }
+  p.N = (uint32_t)N;
+  p.fst[2] = 1;
+  p.fst[1] = p.n[2];
+  p.fst[0] = p.n[1] * p.n[2];
+  p.k = 0;
+  for (int s = 0; s < 3; ++s) p.k += p.interp[s];
+  p.A = A;
+  p.L = 0;
+  while ((1 << p.L) < A) ++p.L;
+  for (int g = 0; g <= p.L; ++g) {
+    const uint32_t S = 1u << g;
+    LevelGeom& lg = p.grid[g];
+    for (int s = 0; s < 3; ++s) {
+      lg.m[s] = p.interp[s] ? (p.n[s] + S - 1) / S : p.n[s];
+      lg.step[s] = p.interp[s] ? S : 1u;
+      lg.fst[s] = p.fst[s];
+    }
+    lg.gst[2] = 1;
+    lg.gst[1] = lg.m[2];
+    lg.gst[0] = lg.m[1] * lg.m[2];
+    p.gsize[g] = lg.m[0] * lg.m[1] * lg.m[2];
+  }
+  return HPEZ_OK;
+}
+
+int check_config(const Plan& p, const hpez_config& c) {
+  if (!pow2(c.chunk_syms) || c.chunk_syms < 256 || c.chunk_syms > 32768)
+    return HPEZ_ERR_INVALID_ARG;
+  if (!(c.alpha >= 1.0) || !(c.beta >= 1.0) || !std::isfinite(c.alpha) ||
+      !std::isfinite(c.beta))
+    return HPEZ_ERR_INVALID_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (!(c.md_inv_var[d] > 0.0) || !std::isfinite(c.md_inv_var[d]))
+      return HPEZ_ERR_INVALID_ARG;
+  if (c.blockwise && c.block_size < 1) return HPEZ_ERR_INVALID_ARG;
+  for (int l = 0; l < p.L; ++l) {
+    if (c.interp[l] > HPEZ_CUBIC_NAT || c.paradigm[l] > HPEZ_PARADIGM_MD ||
+        c.same_level[l] > 1)
+      return HPEZ_ERR_INVALID_ARG;
+    bool seen[3] = {false, false, false};
+    for (int j = 0; j < p.k; ++j) {
+      const int d = c.order[l][j];
+      if (d >= p.ndim || !p.interp[d + p.off] || seen[d])
+        return HPEZ_ERR_INVALID_ARG;
+      seen[d] = true;
+    }
+  }
+  return HPEZ_OK;
+}
+
+void plan_chunks_blocks(Plan& p, const hpez_config& c) {
+  p.C = (uint32_t)c.chunk_syms;
+  p.nch = (uint32_t)(((uint64_t)p.N + p.C - 1) / p.C);
+  p.nblocks = 0;
+  for (int s = 0; s < 3; ++s) p.nb[s] = 1;
+  if (c.blockwise) {
+    uint64_t t = 1;
+    for (int s = 0; s < 3; ++s) {
+      p.nb[s] = (p.n[s] + (uint32_t)c.block_size - 1) / (uint32_t)c.block_size;
+      t *= p.nb[s];
+    }
+    p.nblocks = (uint32_t)t;
+  }
+}
+
+// Eq. 14 weight of slot d within the slot mask S (sum over ascending dims
+// in double, one rounding)
+float md_weight(const Plan& p, const hpez_config& c, unsigned S, int slot) {
+  double sum = 0.0;
+  for (int s = 0; s < 3; ++s)
+    if (S & (1u << s)) sum = sum + c.md_inv_var[s - p.off];
+  return (float)(c.md_inv_var[slot - p.off] / sum);
+}
+
+// The launches of one level: for the 1D-style paradigm one box per pass
+// (order pi: odd on pi_j, any parity on earlier dims, even on later ones);
+// for the multi-dimensional paradigm one box per odd-slot set S, grouped by
+// |S|.  Each (pass, half) is a launch; launches run in list order.
+struct Launch {
+  PassBox pb;
+  int group;  // launches of the same group are independent
+};
+
+std::vector<Launch> level_schedule(const Plan& p, const hpez_config& c,
+                                   int l) {
+  std::vector<Launch> out;
+  const LevelGeom& g = p.grid[l - 1];
+  const bool halves =
+      c.blockwise || (c.interp[l - 1] != HPEZ_LINEAR && c.same_level[l - 1]);
+  const bool md = c.paradigm[l - 1] == HPEZ_PARADIGM_MD;
+  std::vector<std::vector<unsigned>> groups;  // odd-slot masks per group
+  if (!md) {
+    for (int j = 0; j < p.k; ++j) groups.push_back({1u << (c.order[l - 1][j] + p.off)});
+  } else {
+    for (int kp = 1; kp <= p.k; ++kp) {
+      std::vector<unsigned> gs;
+      for (unsigned S = 1; S < 8; ++S) {
+        bool ok = true;
+        int cnt = 0;
+        for (int s = 0; s < 3; ++s)
+          if (S & (1u << s)) {
+            if (!p.interp[s]) ok = false;
+            ++cnt;
+          }
+        if (ok && cnt == kp) gs.push_back(S);
+      }
+      groups.push_back(gs);
+    }
+  }
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    for (int half = 0; half < (halves ? 2 : 1); ++half) {
+      for (unsigned S : groups[gi]) {
+        PassBox pb;
+        std::memset(&pb, 0, sizeof(pb));
+        uint64_t tot = 1;
+        for (int s = 0; s < 3; ++s) {
+          const uint32_t m = g.m[s];
+          int kind;  // 0 any, 1 odd, 2 even
+          if (!p.interp[s]) {
+            kind = 0;
+          } else if (S & (1u << s)) {
+            kind = 1;
+          } else if (md) {
+            kind = 2;
+          } else {
+            // 1D-style: earlier dims of the order any, later ones even
+            int pos_s = -1, pos_j = -1;
+            for (int j = 0; j < p.k; ++j) {
+              if (c.order[l - 1][j] + p.off == s) pos_s = j;
+              if ((1u << (c.order[l - 1][j] + p.off)) == S) pos_j = j;
+            }
+            kind = pos_s < pos_j ? 0 : 2;
+          }
+          if (kind == 0) {
+            pb.a[s] = 0; pb.b[s] = 1; pb.cnt[s] = m;
+          } else if (kind == 1) {
+            pb.a[s] = 1; pb.b[s] = 2; pb.cnt[s] = m / 2;
+          } else {
+            pb.a[s] = 0; pb.b[s] = 2; pb.cnt[s] = (m + 1) / 2;
+          }
+          tot *= pb.cnt[s];
+        }
+        pb.total = (uint32_t)tot;
+        pb.S = S;
+        pb.md = md ? 1 : 0;
+        for (int s = 0; s < 3; ++s)
+          pb.w[s] = (md && (S & (1u << s))) ? md_weight(p, c, S, s) : 0.0f;
+        pb.half = half;
+        pb.level = l;
+        pb.write_recon = 1;
+        out.push_back({pb, (int)(gi * 2 + half)});
+      }
+    }
+  }
+  if (l == 1 && !out.empty()) {
+    // the last group of the finest level is never read again
+    const int last = out.back().group;
+    for (auto& L : out)
+      if (L.group == last) L.pb.write_recon = 0;
+  }
+  return out;
+}
+
+// ---------------------------------------------------------------------
+// scratch arena
+// ---------------------------------------------------------------------
+struct Arena {
+  size_t off = 0;
+  template <class T>
+  size_t take(size_t count) {
+    const size_t o = (off + 255) & ~(size_t)255;
+    off = o + count * sizeof(T);
+    return o;
+  }
+};
+
+int ensure_scratch(hpez_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->scratch_cap) return HPEZ_OK;
+  if (ctx->scratch) {
+    cudaDeviceSynchronize();
+    cudaFree(ctx->scratch);
+    ctx->scratch = nullptr;
+    ctx->scratch_cap = 0;
+  }
+  size_t want = bytes + bytes / 8;
+  if (cudaMalloc(&ctx->scratch, want) != cudaSuccess) {
+    cudaGetLastError();
+    if (cudaMalloc(&ctx->scratch, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->scratch = nullptr;
+      return HPEZ_ERR_NO_MEMORY;
+    }
+    want = bytes;
+  }
+  ctx->scratch_cap = want;
+  return HPEZ_OK;
+}
+
+int map_status(int st) {
+  switch (st) {
+    case ST_OK: return HPEZ_OK;
+    case ST_INVALID: return HPEZ_ERR_INVALID_ARG;
+    case ST_NONFINITE: return HPEZ_ERR_NONFINITE_INPUT;
+    case ST_OUT_TOO_SMALL: return HPEZ_ERR_OUT_TOO_SMALL;
+    case ST_CORRUPT: return HPEZ_ERR_CORRUPT_STREAM;
+  }
+  return HPEZ_ERR_CUDA;
+}
+
+int cuda_check(cudaError_t e) {
+  if (e == cudaSuccess) return HPEZ_OK;
+  if (e == cudaErrorMemoryAllocation) return HPEZ_ERR_NO_MEMORY;
+  return HPEZ_ERR_CUDA;
+}
+
+void default_config(int ndim, hpez_config* c) {
+  std::memset(c, 0, sizeof(*c));
+  c->anchor_stride = ndim == 1 ? 128 : (ndim == 2 ? 64 : 32);
+  c->frozen_dim = -1;
+  c->chunk_syms = 4096;
+  c->blockwise = 0;
+  c->block_size = 32;
+  c->alpha = 1.0;
+  c->beta = 1.0;
+  for (int d = 0; d < 3; ++d) c->md_inv_var[d] = 1.0;
+  for (int l = 0; l < HPEZ_MAX_LEVELS; ++l) {
+    c->interp[l] = HPEZ_CUBIC_NAK;
+    c->paradigm[l] = HPEZ_PARADIGM_1D;
+    c->same_level[l] = 0;
+    for (int j = 0; j < 3; ++j) c->order[l][j] = (uint8_t)(j < ndim ? j : 255);
+  }
+}
+
+uint64_t n_anchors(const Plan& p) { return p.gsize[p.L]; }
+
+void header_templates(const Plan& p, const hpez_config& c, int eb_mode,
+                      double eb, uint64_t off_anchors, uint64_t off_bmap,
+                      uint64_t off_chw, uint8_t* h, uint8_t* hc) {
+  std::memset(h, 0, kHeaderBytes);
+  std::memset(hc, 0, kHeaderBytes);
+  for (uint8_t* b : {h, hc}) {
+    wr32(b, H_MAGIC, kMagic);
+    wr32(b, H_VERSION, kVersion);
+    wr32(b, H_NDIM, (uint32_t)p.ndim);
+    for (int d = 0; d < 3; ++d)
+      wr64(b, H_DIMS + 8 * d, d < p.ndim ? p.n[d + p.off] : 1);
+    wr32(b, H_EBMODE, (uint32_t)eb_mode);
+    wr32(b, H_ANCHOR, (uint32_t)c.anchor_stride);
+    wrf64(b, H_EBVALUE, eb);
+    wr32(b, H_CHUNK, (uint32_t)c.chunk_syms);
+  }
+  // constant field: no sections
+  wr32(hc, H_FLAGS, 1u);
+  wr32(hc, H_FROZEN, 0xFFFFFFFFu);
+  for (int o = H_OFF_ANCHORS; o <= H_OFF_BLOCKMAP; o += 8) wr64(hc, o, kHeaderBytes);
+  wr64(hc, H_TOTAL, kHeaderBytes);
+  // regular stream: static fields (the device patches e, counts, offsets)
+  wr32(h, H_FROZEN, (uint32_t)c.frozen_dim);
+  wrf64(h, H_ALPHA, c.alpha);
+  wrf64(h, H_BETA, c.beta);
+  for (int d = 0; d < 3; ++d) wrf64(h, H_MDIV + 8 * d, c.md_inv_var[d]);
+  for (int l = 0; l < kMaxLevels; ++l) {
+    const bool used = l < p.L;
+    h[H_INTERP + l] = used ? c.interp[l] : 0;
+    h[H_PARADIGM + l] = used ? c.paradigm[l] : 0;
+    h[H_SAME + l] = used ? c.same_level[l] : 0;
+    for (int j = 0; j < 3; ++j)
+      h[H_ORDER + 3 * l + j] = (used && j < p.k) ? c.order[l][j] : 255;
+  }
+  wr32(h, H_PREDICTOR, 0);
+  wr32(h, H_BLOCKWISE, (uint32_t)c.blockwise);
+  wr64(h, H_NANCHORS, n_anchors(p));
+  wr32(h, H_BLOCKSIZE, (uint32_t)c.block_size);
+  wr64(h, H_NCHUNKS, p.nch);
+  wr64(h, H_OFF_ANCHORS, off_anchors);
+  wr64(h, H_OFF_CHUNKW, off_chw);
+  wr64(h, H_OFF_BLOCKMAP, off_bmap);
+  wr64(h, H_NBLOCKS, p.nblocks);
+}
+
+struct CompressBufs {
+  Ctl* ctl;
+  uint32_t* hist;
+  unsigned long long* enc;
+  uint16_t* tsyms;
+  uint8_t* tlens;
+  uint8_t* lens_by_sym;
+  unsigned long long* gkeys;
+  unsigned long long* giw;
+  uint32_t* gpar;
+  float* R[kMaxLevels + 1];
+  uint16_t* Cg[kMaxLevels + 1];
+  uint32_t* zc;
+  unsigned long long* zoff;
+  uint32_t* chw;
+  unsigned long long* woff;
+  uint8_t* bmap;
+};
+
+}  // namespace
+
+// =====================================================================
+// C-ABI
+// =====================================================================
+extern "C" {
+
+const char* hpez_strerror(int code) {
+  switch (code) {
+    case HPEZ_OK: return "ok";
+    case HPEZ_ERR_INVALID_ARG: return "invalid argument";
+    case HPEZ_ERR_NONFINITE_INPUT: return "non-finite input with a relative bound";
+    case HPEZ_ERR_OUT_TOO_SMALL: return "output buffer too small";
+    case HPEZ_ERR_CORRUPT_STREAM: return "corrupt or unsupported stream";
+    case HPEZ_ERR_NO_MEMORY: return "device allocation failed";
+    case HPEZ_ERR_CUDA: return "CUDA runtime error";
+    case HPEZ_ERR_UNSUPPORTED: return "unsupported configuration";
+    case HPEZ_ERR_TIMEOUT: return "bounded device wait timed out";
+  }
+  return "unknown error";
+}
+
+int hpez_default_config(int ndim, hpez_config* out) {
+  if (!out || ndim < 1 || ndim > 3) return HPEZ_ERR_INVALID_ARG;
+  default_config(ndim, out);
+  return HPEZ_OK;
+}
+
+int hpez_create(hpez_ctx** out, int device) {
+  if (!out) return HPEZ_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return HPEZ_ERR_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return HPEZ_ERR_CUDA;
+  hpez_ctx* c = new hpez_ctx();
+  c->device = device;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMallocHost(&c->h_ctl, sizeof(Ctl)) != cudaSuccess ||
+      cudaMallocHost(&c->h_hdr, kHeaderBytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return HPEZ_ERR_NO_MEMORY;
+  }
+  *out = c;
+  return HPEZ_OK;
+}
+
+int hpez_destroy(hpez_ctx* ctx) {
+  if (!ctx) return HPEZ_OK;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->io_in) cudaFree(ctx->io_in);
+  if (ctx->io_out) cudaFree(ctx->io_out);
+  if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
+  if (ctx->h_hdr) cudaFreeHost(ctx->h_hdr);
+  delete ctx;
+  return HPEZ_OK;
+}
+
+int hpez_compress_bound(int ndim, const uint64_t* dims, uint64_t* out_bytes) {
+  if (!dims || !out_bytes || ndim < 1 || ndim > 3) return HPEZ_ERR_INVALID_ARG;
+  uint64_t N = 1;
+  for (int d = 0; d < ndim; ++d) {
+    if (dims[d] == 0) return HPEZ_ERR_INVALID_ARG;
+    N *= dims[d];
+  }
+  const uint64_t nch = (N + 255) / 256;
+  *out_bytes = 512 + 16 * 8 + 4 * N + 4 * N + N + 4 * nch + 3 * 65536 + 4 +
+               (17 * N) / 8 + 4 * nch + 64;
+  return HPEZ_OK;
+}
+
+int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
+                  const uint64_t* dims, int eb_mode, double eb,
+                  const hpez_config* cfg_in, void* d_out, uint64_t out_cap,
+                  uint64_t* h_out_size, void* stream) {
+  if (!ctx || !d_in || !d_out || !h_out_size) return HPEZ_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_out) & 15u) != 0) return HPEZ_ERR_INVALID_ARG;
+  if (eb_mode != HPEZ_EB_ABS && eb_mode != HPEZ_EB_REL) return HPEZ_ERR_INVALID_ARG;
+  if (!(eb > 0.0) || !std::isfinite(eb)) return HPEZ_ERR_INVALID_ARG;
+  hpez_config cfg;
+  if (cfg_in)
+    cfg = *cfg_in;
+  else if (ndim >= 1 && ndim <= 3)
+    default_config(ndim, &cfg);
+  else
+    return HPEZ_ERR_INVALID_ARG;
+  Plan p;
+  int rc = plan_geometry(p, ndim, dims, cfg.anchor_stride, cfg.frozen_dim);
+  if (rc) return rc;
+  rc = check_config(p, cfg);
+  if (rc) return rc;
+  if (cfg.blockwise && !cfg.h_blockmap) return HPEZ_ERR_INVALID_ARG;
+  plan_chunks_blocks(p, cfg);
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  // scratch layout
+  Arena ar;
+  const size_t o_ctl = ar.take<Ctl>(1);
+  const size_t o_hist = ar.take<uint32_t>(65536);
+  const size_t o_enc = ar.take<unsigned long long>(65536);
+  const size_t o_tsyms = ar.take<uint16_t>(65536);
+  const size_t o_tlens = ar.take<uint8_t>(65536);
+  const size_t o_lbs = ar.take<uint8_t>(65536);
+  const size_t o_gkeys = ar.take<unsigned long long>(65536);
+  const size_t o_giw = ar.take<unsigned long long>(65536);
+  const size_t o_gpar = ar.take<uint32_t>(131072);
+  size_t o_R[kMaxLevels + 1], o_C[kMaxLevels + 1];
+  for (int g = 0; g <= p.L; ++g) {
+    o_R[g] = ar.take<float>(p.gsize[g]);
+    o_C[g] = ar.take<uint16_t>(p.gsize[g]);
+  }
+  const size_t o_zc = ar.take<uint32_t>(p.nch);
+  const size_t o_zoff = ar.take<unsigned long long>(p.nch);
+  const size_t o_chw = ar.take<uint32_t>(p.nch);
+  const size_t o_woff = ar.take<unsigned long long>(p.nch);
+  const size_t o_bmap = ar.take<uint8_t>(p.nblocks + 1);
+  rc = ensure_scratch(ctx, ar.off);
+  if (rc) return rc;
+  char* S = ctx->scratch;
+  CompressBufs b;
+  b.ctl = reinterpret_cast<Ctl*>(S + o_ctl);
+  b.hist = reinterpret_cast<uint32_t*>(S + o_hist);
+  b.enc = reinterpret_cast<unsigned long long*>(S + o_enc);
+  b.tsyms = reinterpret_cast<uint16_t*>(S + o_tsyms);
+  b.tlens = reinterpret_cast<uint8_t*>(S + o_tlens);
+  b.lens_by_sym = reinterpret_cast<uint8_t*>(S + o_lbs);
+  b.gkeys = reinterpret_cast<unsigned long long*>(S + o_gkeys);
+  b.giw = reinterpret_cast<unsigned long long*>(S + o_giw);
+  b.gpar = reinterpret_cast<uint32_t*>(S + o_gpar);
+  for (int g = 0; g <= p.L; ++g) {
+    b.R[g] = reinterpret_cast<float*>(S + o_R[g]);
+    b.Cg[g] = reinterpret_cast<uint16_t*>(S + o_C[g]);
+  }
+  b.zc = reinterpret_cast<uint32_t*>(S + o_zc);
+  b.zoff = reinterpret_cast<unsigned long long*>(S + o_zoff);
+  b.chw = reinterpret_cast<uint32_t*>(S + o_chw);
+  b.woff = reinterpret_cast<unsigned long long*>(S + o_woff);
+  b.bmap = reinterpret_cast<uint8_t*>(S + o_bmap);
+
+  // stream layout (static part)
+  const uint64_t na = n_anchors(p);
+  const uint64_t off_anchors = kHeaderBytes;
+  const uint64_t off_bmap = a16(off_anchors + 4 * na);
+  const uint64_t off_chw = a16(off_bmap + p.nblocks);
+  const uint64_t off_table = a16(off_chw + 4ull * p.nch);
+  uint8_t hdr[kHeaderBytes], hdrc[kHeaderBytes];
+  header_templates(p, cfg, eb_mode, eb, off_anchors, off_bmap, off_chw, hdr, hdrc);
+
+  // ---- launch sequence ----
+  launch_init_ctl(b.ctl, s);
+  if (eb_mode == HPEZ_EB_REL) launch_range(d_in, p.N, b.ctl, ctx->num_sms, s);
+  launch_params(b.ctl, eb_mode, eb, cfg.alpha, cfg.beta, p.L, d_in, s);
+  if (cfg.blockwise)
+    cudaMemcpyAsync(b.bmap, cfg.h_blockmap, p.nblocks, cudaMemcpyHostToDevice, s);
+  launch_anchor_gather(d_in, p.grid[p.L], p.gsize[p.L], b.R[p.L], b.Cg[p.L],
+                       b.ctl, s);
+  SweepBufs sb;
+  std::memset(&sb, 0, sizeof(sb));
+  sb.x = d_in;
+  sb.blockmap = cfg.blockwise ? b.bmap : nullptr;
+  sb.bs = (uint32_t)(cfg.block_size > 0 ? cfg.block_size : 1);
+  for (int s3 = 0; s3 < 3; ++s3) sb.nb[s3] = p.nb[s3];
+  sb.ctl = b.ctl;
+  for (int l = p.L; l >= 1; --l) {
+    const int g = l - 1;
+    launch_upsample(p.grid[l], p.gsize[l], p.grid[g], b.R[l], b.Cg[l], b.R[g],
+                    b.Cg[g], b.ctl, s);
+    sb.R = b.R[g];
+    sb.C = b.Cg[g];
+    sb.kind = cfg.interp[l - 1];
+    sb.same = cfg.same_level[l - 1];
+    for (const Launch& L : level_schedule(p, cfg, l))
+      launch_pass(false, p.grid[g], L.pb, sb, ctx->num_sms, s);
+  }
+  uint16_t* codes = b.Cg[0];
+  cudaMemsetAsync(b.hist, 0, 65536 * sizeof(uint32_t), s);
+  launch_hist(codes, p.N, p.C, p.nch, b.hist, b.zc, b.ctl, ctx->num_sms, s);
+  launch_scan(b.zc, b.zoff, p.nch, &b.ctl->n_out, b.ctl, s);
+  launch_codebook(b.hist, b.enc, b.tsyms, b.tlens, b.gkeys, b.giw, b.gpar,
+                  b.lens_by_sym, b.ctl, s);
+  launch_enc_len(codes, p.N, p.C, p.nch, b.enc, b.chw, b.ctl, ctx->num_sms, s);
+  launch_scan(b.chw, b.woff, p.nch, &b.ctl->total_words, b.ctl, s);
+  launch_layout(b.ctl, off_table, out_cap, s);
+  uint8_t* out = static_cast<uint8_t*>(d_out);
+  launch_pack(codes, p.N, p.C, p.nch, b.enc, b.chw, b.woff, out, b.ctl,
+              ctx->num_sms, s);
+  launch_outliers(true, codes, p.N, p.C, p.nch, b.zc, b.zoff, d_in, nullptr,
+                  out, ~0ull, b.ctl, ctx->num_sms, s);
+  launch_finalize(hdr, hdrc, out, b.R[p.L], (uint32_t)na, off_anchors, b.bmap,
+                  p.nblocks, off_bmap, b.chw, p.nch, off_chw, b.tsyms, b.tlens,
+                  b.ctl, ctx->num_sms, s);
+  rc = cuda_check(cudaGetLastError());
+  if (rc) return rc;
+  rc = cuda_check(cudaMemcpyAsync(ctx->h_ctl, b.ctl, sizeof(Ctl),
+                                  cudaMemcpyDeviceToHost, s));
+  if (rc) return rc;
+  rc = cuda_check(cudaStreamSynchronize(s));
+  if (rc) return rc;
+  if (ctx->h_ctl->status) return map_status(ctx->h_ctl->status);
+  *h_out_size = ctx->h_ctl->total_size;
+  return HPEZ_OK;
+}
+
+int hpez_inspect(const void* h_header, uint64_t n, int* ndim, uint64_t* dims,
+                 double* abs_eb) {
+  if (!h_header || n < (uint64_t)kHeaderBytes) return HPEZ_ERR_INVALID_ARG;
+  const uint8_t* h = static_cast<const uint8_t*>(h_header);
+  if (rd32(h, H_MAGIC) != kMagic || rd32(h, H_VERSION) != kVersion)
+    return HPEZ_ERR_CORRUPT_STREAM;
+  const int nd = (int)rd32(h, H_NDIM);
+  if (nd < 1 || nd > 3) return HPEZ_ERR_CORRUPT_STREAM;
+  if (ndim) *ndim = nd;
+  if (dims)
+    for (int d = 0; d < 3; ++d) dims[d] = d < nd ? rd64(h, H_DIMS + 8 * d) : 1;
+  if (abs_eb) *abs_eb = (double)rdf32(h, H_E);
+  return HPEZ_OK;
+}
+
+int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
+                    float* d_out, uint64_t out_cap_elems, void* stream) {
+  if (!ctx || !d_in || !d_out) return HPEZ_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_in) & 15u) != 0) return HPEZ_ERR_INVALID_ARG;
+  if (in_size < (uint64_t)kHeaderBytes) return HPEZ_ERR_CORRUPT_STREAM;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = cuda_check(cudaMemcpyAsync(ctx->h_hdr, d_in, kHeaderBytes,
+                                      cudaMemcpyDeviceToHost, s));
+  if (rc) return rc;
+  rc = cuda_check(cudaStreamSynchronize(s));
+  if (rc) return rc;
+  const uint8_t* h = ctx->h_hdr;
+  int nd;
+  uint64_t dims[3];
+  rc = hpez_inspect(h, kHeaderBytes, &nd, dims, nullptr);
+  if (rc) return rc;
+  if (rd64(h, H_TOTAL) > in_size) return HPEZ_ERR_CORRUPT_STREAM;
+  uint64_t N = 1;
+  for (int d = 0; d < nd; ++d) {
+    if (dims[d] == 0) return HPEZ_ERR_CORRUPT_STREAM;
+    N *= dims[d];
+    if (N > 0xFFFFFFFFull) return HPEZ_ERR_CORRUPT_STREAM;
+  }
+  if (N > out_cap_elems) return HPEZ_ERR_OUT_TOO_SMALL;
+  const uint8_t* in = static_cast<const uint8_t*>(d_in);
+
+  hpez_config cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.anchor_stride = (int32_t)rd32(h, H_ANCHOR);
+  cfg.frozen_dim = (int32_t)rd32(h, H_FROZEN);
+  cfg.chunk_syms = (int32_t)rd32(h, H_CHUNK);
+  cfg.blockwise = (int32_t)rd32(h, H_BLOCKWISE);
+  cfg.block_size = (int32_t)rd32(h, H_BLOCKSIZE);
+  cfg.alpha = rdf64(h, H_ALPHA);
+  cfg.beta = rdf64(h, H_BETA);
+  for (int d = 0; d < 3; ++d) cfg.md_inv_var[d] = rdf64(h, H_MDIV + 8 * d);
+  for (int l = 0; l < HPEZ_MAX_LEVELS; ++l) {
+    cfg.interp[l] = h[H_INTERP + l];
+    cfg.paradigm[l] = h[H_PARADIGM + l];
+    cfg.same_level[l] = h[H_SAME + l];
+    for (int j = 0; j < 3; ++j) cfg.order[l][j] = h[H_ORDER + 3 * l + j];
+  }
+  if (rd32(h, H_FLAGS) & 1u) {
+    // constant field
+    Plan p;
+    if (plan_geometry(p, nd, dims, 2, -1)) return HPEZ_ERR_CORRUPT_STREAM;
+    launch_fill(d_out, p.N, rdf32(h, H_CONST), ctx->num_sms, s);
+    rc = cuda_check(cudaGetLastError());
+    if (rc) return rc;
+    return cuda_check(cudaStreamSynchronize(s));
+  }
+  Plan p;
+  if (plan_geometry(p, nd, dims, cfg.anchor_stride, cfg.frozen_dim))
+    return HPEZ_ERR_CORRUPT_STREAM;
+  if (check_config(p, cfg)) return HPEZ_ERR_CORRUPT_STREAM;
+  plan_chunks_blocks(p, cfg);
+  const float e = rdf32(h, H_E);
+  if (!(e > 0.0f) || !std::isfinite(e)) return HPEZ_ERR_CORRUPT_STREAM;
+  const uint64_t na = rd64(h, H_NANCHORS), nout = rd64(h, H_NOUTLIERS),
+                 nch = rd64(h, H_NCHUNKS), twords = rd64(h, H_TOTALWORDS);
+  const uint32_t nused = rd32(h, H_NUSED);
+  const uint64_t oa = rd64(h, H_OFF_ANCHORS), ocw = rd64(h, H_OFF_CHUNKW),
+                 ot = rd64(h, H_OFF_TABLE), oo = rd64(h, H_OFF_OUTLIERS),
+                 ob = rd64(h, H_OFF_BITS), obm = rd64(h, H_OFF_BLOCKMAP);
+  if (na != n_anchors(p) || nch != p.nch || nused == 0 || nused > 65536 ||
+      nout > N || (cfg.blockwise && rd64(h, H_NBLOCKS) != p.nblocks))
+    return HPEZ_ERR_CORRUPT_STREAM;
+  if (oa + 4 * na > in_size || ocw + 4 * nch > in_size ||
+      ot + 3ull * nused > in_size || oo + 4 * nout > in_size ||
+      ob + 4 * twords > in_size || (cfg.blockwise && obm + p.nblocks > in_size) ||
+      (oa & 15) || (ocw & 15) || (oo & 15) || (ob & 15))
+    return HPEZ_ERR_CORRUPT_STREAM;
+  uint16_t single_sym = 0;
+  if (nused == 1) {
+    // the lone symbol of a single-symbol code table
+    rc = cuda_check(cudaMemcpyAsync(ctx->h_hdr, in + ot, 2,
+                                    cudaMemcpyDeviceToHost, s));
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(s));
+    if (rc) return rc;
+    single_sym = (uint16_t)(ctx->h_hdr[0] | (ctx->h_hdr[1] << 8));
+  }
+
+  Arena ar;
+  const size_t o_ctl = ar.take<Ctl>(1);
+  const size_t o_lut = ar.take<uint32_t>(4096);
+  const size_t o_cnt = ar.take<uint32_t>(64);
+  const size_t o_first = ar.take<unsigned long long>(64);
+  const size_t o_offs = ar.take<uint32_t>(64);
+  const size_t o_sorted = ar.take<uint16_t>(65536);
+  const size_t o_gkeys = ar.take<unsigned long long>(65536);
+  size_t o_R[kMaxLevels + 1];
+  for (int g = 1; g < p.L; ++g) o_R[g] = ar.take<float>(p.gsize[g]);
+  const size_t o_codes = ar.take<uint16_t>(N);
+  const size_t o_zc = ar.take<uint32_t>(p.nch);
+  const size_t o_zoff = ar.take<unsigned long long>(p.nch);
+  const size_t o_woff = ar.take<unsigned long long>(p.nch);
+  const size_t o_tot = ar.take<unsigned long long>(2);
+  rc = ensure_scratch(ctx, ar.off);
+  if (rc) return rc;
+  char* S = ctx->scratch;
+  Ctl* ctl = reinterpret_cast<Ctl*>(S + o_ctl);
+  uint32_t* lut = reinterpret_cast<uint32_t*>(S + o_lut);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(S + o_cnt);
+  unsigned long long* first = reinterpret_cast<unsigned long long*>(S + o_first);
+  uint32_t* offs = reinterpret_cast<uint32_t*>(S + o_offs);
+  uint16_t* sorted = reinterpret_cast<uint16_t*>(S + o_sorted);
+  unsigned long long* gkeys = reinterpret_cast<unsigned long long*>(S + o_gkeys);
+  uint16_t* codes = reinterpret_cast<uint16_t*>(S + o_codes);
+  uint32_t* zc = reinterpret_cast<uint32_t*>(S + o_zc);
+  unsigned long long* zoff = reinterpret_cast<unsigned long long*>(S + o_zoff);
+  unsigned long long* woff = reinterpret_cast<unsigned long long*>(S + o_woff);
+  unsigned long long* tot = reinterpret_cast<unsigned long long*>(S + o_tot);
+  float* R[kMaxLevels + 1];
+  for (int g = 1; g < p.L; ++g) R[g] = reinterpret_cast<float*>(S + o_R[g]);
+  R[0] = d_out;
+  R[p.L] = const_cast<float*>(reinterpret_cast<const float*>(in + oa));
+
+  launch_init_ctl(ctl, s);
+  launch_params(ctl, HPEZ_EB_ABS, (double)e, cfg.alpha, cfg.beta, p.L, d_out, s);
+  const uint32_t* chw_stream = reinterpret_cast<const uint32_t*>(in + ocw);
+  launch_scan(chw_stream, woff, p.nch, &tot[0], ctl, s);
+  launch_dec_tables(in, nused, ot, lut, cnt, first, offs, sorted, gkeys, ctl, s);
+  launch_decode(in, ob, twords, chw_stream, woff, p.N, p.C, p.nch, nused,
+                single_sym, lut, cnt, first, offs, sorted, codes, zc, ctl, s);
+  launch_scan(zc, zoff, p.nch, &tot[1], ctl, s);
+  launch_outliers(false, codes, p.N, p.C, p.nch, zc, zoff, nullptr, d_out,
+                  const_cast<uint8_t*>(in) + oo, nout, ctl, ctx->num_sms, s);
+  SweepBufs sb;
+  std::memset(&sb, 0, sizeof(sb));
+  sb.codes_full = codes;
+  sb.outl_full = d_out;
+  sb.blockmap = cfg.blockwise ? in + obm : nullptr;
+  sb.bs = (uint32_t)(cfg.block_size > 0 ? cfg.block_size : 1);
+  for (int s3 = 0; s3 < 3; ++s3) sb.nb[s3] = p.nb[s3];
+  sb.ctl = ctl;
+  for (int l = p.L; l >= 1; --l) {
+    const int g = l - 1;
+    launch_upsample(p.grid[l], p.gsize[l], p.grid[g], R[l], nullptr, R[g],
+                    nullptr, ctl, s);
+    sb.R = R[g];
+    sb.kind = cfg.interp[l - 1];
+    sb.same = cfg.same_level[l - 1];
+    for (const Launch& L : level_schedule(p, cfg, l))
+      launch_pass(true, p.grid[g], L.pb, sb, ctx->num_sms, s);
+  }
+  rc = cuda_check(cudaGetLastError());
+  if (rc) return rc;
+  unsigned long long h_tot[2];
+  rc = cuda_check(cudaMemcpyAsync(ctx->h_ctl, ctl, sizeof(Ctl),
+                                  cudaMemcpyDeviceToHost, s));
+  if (rc) return rc;
+  rc = cuda_check(cudaMemcpyAsync(h_tot, tot, sizeof(h_tot),
+                                  cudaMemcpyDeviceToHost, s));
+  if (rc) return rc;
+  rc = cuda_check(cudaStreamSynchronize(s));
+  if (rc) return rc;
+  if (ctx->h_ctl->status) return map_status(ctx->h_ctl->status);
+  if (h_tot[0] != twords || h_tot[1] != nout) return HPEZ_ERR_CORRUPT_STREAM;
+  return HPEZ_OK;
+}
+
+static int ensure_io(void** buf, size_t* cap, size_t bytes) {
+  if (bytes <= *cap) return HPEZ_OK;
+  if (*buf) {
+    cudaDeviceSynchronize();
+    cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+  }
+  if (cudaMalloc(buf, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *buf = nullptr;
+    return HPEZ_ERR_NO_MEMORY;
+  }
+  *cap = bytes;
+  return HPEZ_OK;
+}
+
+int hpez_compress_host(hpez_ctx* ctx, const float* h_in, int ndim,
+                       const uint64_t* dims, int eb_mode, double eb,
+                       const hpez_config* cfg, void* h_out, uint64_t out_cap,
+                       uint64_t* h_out_size, void* stream) {
+  if (!ctx || !h_in || !h_out || !h_out_size || !dims || ndim < 1 || ndim > 3)
+    return HPEZ_ERR_INVALID_ARG;
+  uint64_t N = 1;
+  for (int d = 0; d < ndim; ++d) N *= dims[d];
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = ensure_io(&ctx->io_in, &ctx->io_in_cap, N * sizeof(float));
+  if (rc) return rc;
+  rc = ensure_io(&ctx->io_out, &ctx->io_out_cap, out_cap);
+  if (rc) return rc;
+  rc = cuda_check(cudaMemcpyAsync(ctx->io_in, h_in, N * sizeof(float),
+                                  cudaMemcpyHostToDevice, s));
+  if (rc) return rc;
+  rc = hpez_compress(ctx, static_cast<const float*>(ctx->io_in), ndim, dims,
+                     eb_mode, eb, cfg, ctx->io_out, out_cap, h_out_size, stream);
+  if (rc) return rc;
+  rc = cuda_check(cudaMemcpyAsync(h_out, ctx->io_out, *h_out_size,
+                                  cudaMemcpyDeviceToHost, s));
+  if (rc) return rc;
+  return cuda_check(cudaStreamSynchronize(s));
+}
+
+int hpez_decompress_host(hpez_ctx* ctx, const void* h_in, uint64_t in_size,
+                         float* h_out, uint64_t out_cap_elems, void* stream) {
+  if (!ctx || !h_in || !h_out) return HPEZ_ERR_INVALID_ARG;
+  int nd;
+  uint64_t dims[3];
+  int rc = hpez_inspect(h_in, in_size, &nd, dims, nullptr);
+  if (rc) return rc;
+  uint64_t N = 1;
+  for (int d = 0; d < nd; ++d) N *= dims[d];
+  if (N > out_cap_elems) return HPEZ_ERR_OUT_TOO_SMALL;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = ensure_io(&ctx->io_in, &ctx->io_in_cap, in_size);
+  if (rc) return rc;
+  rc = ensure_io(&ctx->io_out, &ctx->io_out_cap, N * sizeof(float));
+  if (rc) return rc;
+  rc = cuda_check(cudaMemcpyAsync(ctx->io_in, h_in, in_size,
+                                  cudaMemcpyHostToDevice, s));
+  if (rc) return rc;
+  rc = hpez_decompress(ctx, ctx->io_in, in_size, static_cast<float*>(ctx->io_out),
+                       N, stream);
+  if (rc) return rc;
+  rc = cuda_check(cudaMemcpyAsync(h_out, ctx->io_out, N * sizeof(float),
+                                  cudaMemcpyDeviceToHost, s));
+  if (rc) return rc;
+  return cuda_check(cudaStreamSynchronize(s));
+}
+
+}  // extern "C"

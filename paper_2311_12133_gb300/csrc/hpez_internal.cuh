@@ -1,0 +1,275 @@
+// hpez_internal.cuh -- device-side building blocks of the HPEZ sweep.
+//
+// Every binary32 operation of the prediction and quantization runs through
+// an explicit round-to-nearest intrinsic (__fadd_rn, __fmul_rn, ...), which
+// the compiler never contracts into FMA, so the results are reproducible
+// bit for bit on any IEEE-754 machine that performs the same operations in
+// the same order.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hpez {
+
+constexpr int kMaxLevels = 16;
+constexpr int kRadius = 32768;
+constexpr int kHeaderBytes = 512;
+
+enum Interp { LINEAR = 0, CUBIC_NAK = 1, CUBIC_NAT = 2 };
+
+// status codes written by kernels (mirror the C-ABI error codes)
+enum DevStatus {
+  ST_OK = 0,
+  ST_INVALID = -1,
+  ST_NONFINITE = -2,
+  ST_OUT_TOO_SMALL = -3,
+  ST_CORRUPT = -4,
+};
+
+// Per-call control block in device memory.
+struct Ctl {
+  unsigned int vmin_key, vmax_key;  // order-preserving float keys
+  int nonfinite;
+  int is_const;
+  int status;
+  int pad0;
+  float e;
+  float const_value;
+  float el[kMaxLevels], inv2[kMaxLevels], twoe[kMaxLevels];
+  unsigned long long n_out;
+  unsigned long long total_words;
+  unsigned long long off_table, off_outliers, off_bits, total_size;
+  unsigned int n_used;
+  unsigned int max_len;
+  unsigned long long dbg[4];
+};
+
+// ---------------------------------------------------------------------
+// order-preserving float <-> uint key (for atomic min/max)
+// ---------------------------------------------------------------------
+__device__ __forceinline__ unsigned int f2key(float f) {
+  unsigned int u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key2f(unsigned int k) {
+  unsigned int u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  return __uint_as_float(u);
+}
+
+// ---------------------------------------------------------------------
+// Stencils along one line (Sec. 5.2 Eq. 2/4/6, Sec. 5.4.2 Eq. 10/11) and
+// the boundary fallbacks (spline through the available knots, linear
+// extrapolation with no right neighbour, copy as the last resort).
+// Neighbour offsets are in units of the level stride; slot j+3 of the
+// value array holds offset j.
+// ---------------------------------------------------------------------
+enum Formula {
+  F_COPY, F_EXTRAP, F_LIN, F_NAK4, F_NAT4, F_NAK3L, F_NAK3R, F_NAT3L,
+  F_NAT3R, F_SL_NAK, F_SL_NAT
+};
+
+// Chooses the stencil from which neighbours exist along the line.
+// u: position (in stride units) of the point, m: number of grid points on
+// the line, so offset j exists iff 0 <= u + j <= m - 1.  u is odd >= 1,
+// hence offset -1 always exists.
+__device__ __forceinline__ int choose_formula(int kind, bool half_b, int u,
+                                              int m) {
+  const bool hm3 = u >= 3, hm2 = u >= 2;
+  const bool hp1 = u + 1 <= m - 1, hp2 = u + 2 <= m - 1,
+             hp3 = u + 3 <= m - 1;
+  if (half_b) {
+    if (kind == CUBIC_NAK && hp1 && hm2 && hp2) return F_SL_NAK;
+    if (kind == CUBIC_NAT && hp1 && hm2 && hp2 && hm3 && hp3) return F_SL_NAT;
+  }
+  if (!hp1) return hm3 ? F_EXTRAP : F_COPY;
+  if (kind == LINEAR) return F_LIN;
+  if (hm3 && hp3) return kind == CUBIC_NAK ? F_NAK4 : F_NAT4;
+  if (hm3) return kind == CUBIC_NAK ? F_NAK3L : F_NAT3L;
+  if (hp3) return kind == CUBIC_NAK ? F_NAK3R : F_NAT3R;
+  return F_LIN;
+}
+
+// Division by a power of two is exact scaling, so multiplying by the exact
+// reciprocal rounds to the same value as the division.
+__device__ __forceinline__ float eval_formula(int f, float m3, float m2,
+                                              float m1, float p1, float p2,
+                                              float p3) {
+  switch (f) {
+    case F_COPY:
+      return m1;
+    case F_EXTRAP:  // (3 d-1 - d-3) / 2
+      return __fmul_rn(__fsub_rn(__fmul_rn(m1, 3.0f), m3), 0.5f);
+    case F_LIN:  // Eq. 2
+      return __fmul_rn(__fadd_rn(m1, p1), 0.5f);
+    case F_NAK4:  // Eq. 4
+      return __fmul_rn(
+          __fsub_rn(__fmul_rn(__fadd_rn(m1, p1), 9.0f), __fadd_rn(m3, p3)),
+          0.0625f);
+    case F_NAT4:  // Eq. 6
+      return __fdiv_rn(__fsub_rn(__fmul_rn(__fadd_rn(m1, p1), 23.0f),
+                                 __fmul_rn(__fadd_rn(m3, p3), 3.0f)),
+                       40.0f);
+    case F_NAK3L:  // (-1, 6, 3) / 8
+      return __fmul_rn(
+          __fsub_rn(__fadd_rn(__fmul_rn(m1, 6.0f), __fmul_rn(p1, 3.0f)), m3),
+          0.125f);
+    case F_NAK3R:  // (3, 6, -1) / 8
+      return __fmul_rn(
+          __fsub_rn(__fadd_rn(__fmul_rn(m1, 3.0f), __fmul_rn(p1, 6.0f)), p3),
+          0.125f);
+    case F_NAT3L:  // (-3, 22, 13) / 32
+      return __fmul_rn(
+          __fsub_rn(__fadd_rn(__fmul_rn(m1, 22.0f), __fmul_rn(p1, 13.0f)),
+                    __fmul_rn(m3, 3.0f)),
+          0.03125f);
+    case F_NAT3R:  // (13, 22, -3) / 32
+      return __fmul_rn(
+          __fsub_rn(__fadd_rn(__fmul_rn(m1, 13.0f), __fmul_rn(p1, 22.0f)),
+                    __fmul_rn(p3, 3.0f)),
+          0.03125f);
+    case F_SL_NAK:  // Eq. 10
+      return __fdiv_rn(
+          __fsub_rn(__fmul_rn(__fadd_rn(m1, p1), 4.0f), __fadd_rn(m2, p2)),
+          6.0f);
+    case F_SL_NAT:  // Eq. 11
+      return __fdiv_rn(
+          __fadd_rn(__fsub_rn(__fmul_rn(__fadd_rn(m1, p1), 46.0f),
+                              __fmul_rn(__fadd_rn(m2, p2), 18.0f)),
+                    __fmul_rn(__fadd_rn(m3, p3), 3.0f)),
+          62.0f);
+  }
+  return 0.0f;
+}
+
+// Prediction along one line of a compact grid: `base` points at the
+// point's own entry, `st` is the stride of the line in elements.
+__device__ __forceinline__ float predict_line(const float* __restrict__ base,
+                                              long long st, int u, int m,
+                                              int kind, bool half_b) {
+  const int f = choose_formula(kind, half_b, u, m);
+  float m3 = 0.f, m2 = 0.f, m1 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+  m1 = __ldg(base - st);
+  switch (f) {
+    case F_COPY:
+      break;
+    case F_EXTRAP:
+      m3 = __ldg(base - 3 * st);
+      break;
+    case F_LIN:
+      p1 = __ldg(base + st);
+      break;
+    case F_NAK4:
+    case F_NAT4:
+      m3 = __ldg(base - 3 * st);
+      p1 = __ldg(base + st);
+      p3 = __ldg(base + 3 * st);
+      break;
+    case F_NAK3L:
+    case F_NAT3L:
+      m3 = __ldg(base - 3 * st);
+      p1 = __ldg(base + st);
+      break;
+    case F_NAK3R:
+    case F_NAT3R:
+      p1 = __ldg(base + st);
+      p3 = __ldg(base + 3 * st);
+      break;
+    case F_SL_NAK:
+      m2 = __ldg(base - 2 * st);
+      p1 = __ldg(base + st);
+      p2 = __ldg(base + 2 * st);
+      break;
+    case F_SL_NAT:
+      m3 = __ldg(base - 3 * st);
+      m2 = __ldg(base - 2 * st);
+      p1 = __ldg(base + st);
+      p2 = __ldg(base + 2 * st);
+      p3 = __ldg(base + 3 * st);
+      break;
+  }
+  return eval_formula(f, m3, m2, m1, p1, p2, p3);
+}
+
+// ---------------------------------------------------------------------
+// Linear quantization (Sec. 4 Step 3) with the exact bound check:
+// |r - x| <= e decided from rn(r - x) and its TwoSum residual.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ bool within_bound(float r, float x, float e) {
+  const float nx = -x;
+  const float d = __fadd_rn(r, nx);
+  const float bb = __fsub_rn(d, r);
+  const float res = __fadd_rn(__fsub_rn(r, __fsub_rn(d, bb)), __fsub_rn(nx, bb));
+  const float ad = fabsf(d);
+  if (ad < e) return true;
+  if (ad == e) {
+    if (d > 0.0f) return res <= 0.0f;
+    if (d < 0.0f) return res >= 0.0f;
+  }
+  return false;
+}
+
+// Returns the code word (q + radius, or 0 = unpredictable) and the
+// reconstructed value.
+__device__ __forceinline__ unsigned quantize(float x, float p, float el,
+                                             float inv2, float twoe,
+                                             float& recon) {
+  const float diff = __fsub_rn(x, p);
+  const float m = __fadd_rn(__fmul_rn(fabsf(diff), inv2), 0.5f);
+  if (m < 32768.0f) {
+    const int k = __float2int_rz(m);
+    const int q = diff < 0.0f ? -k : k;
+    const float r = __fadd_rn(p, __fmul_rn(__int2float_rn(q), twoe));
+    if (within_bound(r, x, el)) {
+      recon = r;
+      return (unsigned)(q + kRadius);
+    }
+  }
+  recon = x;
+  return 0u;
+}
+
+__device__ __forceinline__ float dequantize(unsigned code, float p,
+                                            float twoe) {
+  const int q = (int)code - kRadius;
+  return __fadd_rn(p, __fmul_rn(__int2float_rn(q), twoe));
+}
+
+// ---------------------------------------------------------------------
+// Sweep geometry: every field is 3 slots (real dims in the last ndim
+// slots).  A level's compact grid G_s keeps the points whose coordinate is
+// a multiple of s on every interpolation slot.
+// ---------------------------------------------------------------------
+struct LevelGeom {
+  uint32_t m[3];     // G_s extent per slot
+  uint32_t gst[3];   // G_s element strides
+  uint32_t step[3];  // full-field coordinate step per G_s index (s or 1)
+  uint32_t fst[3];   // full-field element strides
+};
+
+// One launch of the sweep: a box of G_s indices u_d = a_d + b_d * t_d.
+struct PassBox {
+  uint32_t a[3], b[3], cnt[3];
+  uint32_t total;
+  uint32_t S;        // slots predicted along (bit per slot)
+  float w[3];        // multi-dimensional weights per slot (Eq. 8 / Eq. 14)
+  int md;            // 1: weighted sum over S, 0: single slot in S
+  int half;          // same-level half processed by this launch
+  int level;         // l >= 1
+  int write_recon;   // compress: store the reconstruction
+};
+
+struct SweepBufs {
+  const float* x;              // compress: full input
+  float* R;                    // G_s reconstruction
+  uint16_t* C;                 // compress: G_s codes
+  const uint16_t* codes_full;  // decompress: full-field codes
+  const float* outl_full;      // decompress: outliers scattered (full)
+  const uint8_t* blockmap;     // per-block interpolator (or null)
+  uint32_t bs;                 // block side
+  uint32_t nb[3];              // blocks per slot
+  int kind, same;              // level interpolator when no block map
+  const Ctl* ctl;
+};
+
+}  // namespace hpez

@@ -1,0 +1,76 @@
+// hpez_launch.h -- host-side launchers of the HPEZ kernels (internal).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hpez_internal.cuh"
+
+namespace hpez {
+
+// k_sweep.cu
+void launch_init_ctl(Ctl* ctl, cudaStream_t s);
+void launch_fill(float* out, uint32_t N, float v, int num_sms,
+                 cudaStream_t s);
+void launch_range(const float* x, uint32_t N, Ctl* ctl, int num_sms,
+                  cudaStream_t s);
+void launch_params(Ctl* ctl, int eb_mode, double eb, double alpha,
+                   double beta, int L, const float* x, cudaStream_t s);
+void launch_anchor_gather(const float* x, const LevelGeom& ga, uint32_t total,
+                          float* RA, uint16_t* CA, const Ctl* ctl,
+                          cudaStream_t s);
+void launch_upsample(const LevelGeom& gc, uint32_t total_c,
+                     const LevelGeom& gs, const float* Rc, const uint16_t* Cc,
+                     float* Rs, uint16_t* Cs, const Ctl* ctl, cudaStream_t s);
+void launch_pass(bool decomp, const LevelGeom& g, const PassBox& pb,
+                 const SweepBufs& B, int num_sms, cudaStream_t s);
+
+// k_huffman.cu
+void launch_hist(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,
+                 uint32_t* hist, uint32_t* zc, const Ctl* ctl, int num_sms,
+                 cudaStream_t s);
+void launch_codebook(const uint32_t* hist, unsigned long long* enc,
+                     uint16_t* tsyms, uint8_t* tlens, unsigned long long* gkeys,
+                     unsigned long long* giw, uint32_t* gpar,
+                     uint8_t* lens_by_sym, Ctl* ctl, cudaStream_t s);
+void launch_enc_len(const uint16_t* codes, uint32_t N, uint32_t C,
+                    uint32_t nch, const unsigned long long* enc, uint32_t* chw,
+                    const Ctl* ctl, int num_sms, cudaStream_t s);
+void launch_pack(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,
+                 const unsigned long long* enc, const uint32_t* chw,
+                 const unsigned long long* woff, uint8_t* out, const Ctl* ctl,
+                 int num_sms, cudaStream_t s);
+void launch_outliers(bool gather, const uint16_t* codes, uint32_t N,
+                     uint32_t C, uint32_t nch, const uint32_t* zc,
+                     const unsigned long long* zoff, const float* src,
+                     float* dst, uint8_t* stream, unsigned long long max_out,
+                     Ctl* ctl, int num_sms, cudaStream_t s);
+void launch_dec_tables(const uint8_t* stream, uint32_t n_used,
+                       uint64_t off_table, uint32_t* lut, uint32_t* cnt,
+                       unsigned long long* first, uint32_t* offs,
+                       uint16_t* sorted, unsigned long long* gkeys, Ctl* ctl,
+                       cudaStream_t s);
+void launch_decode(const uint8_t* stream, uint64_t off_bits,
+                   uint64_t total_words, const uint32_t* chw_stream,
+                   const unsigned long long* woff, uint32_t N, uint32_t C,
+                   uint32_t nch, uint32_t n_used, uint16_t single_sym,
+                   const uint32_t* lut, const uint32_t* cnt,
+                   const unsigned long long* first, const uint32_t* offs,
+                   const uint16_t* sorted, uint16_t* codes, uint32_t* zc,
+                   Ctl* ctl, cudaStream_t s);
+
+// k_stream.cu
+void launch_scan(const uint32_t* in, unsigned long long* out, uint32_t n,
+                 unsigned long long* total, const Ctl* ctl, cudaStream_t s);
+void launch_layout(Ctl* ctl, unsigned long long off_table,
+                   unsigned long long cap, cudaStream_t s);
+void launch_finalize(const uint8_t* hdr, const uint8_t* hdr_const,
+                     uint8_t* out, const float* RA, uint32_t na,
+                     unsigned long long off_anchors, const uint8_t* bmap,
+                     uint32_t nblocks, unsigned long long off_bmap,
+                     const uint32_t* chw, uint32_t nch,
+                     unsigned long long off_chw, const uint16_t* tsyms,
+                     const uint8_t* tlens, const Ctl* ctl, int num_sms,
+                     cudaStream_t s);
+
+}  // namespace hpez

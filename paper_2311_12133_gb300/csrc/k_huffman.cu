@@ -1,0 +1,718 @@
+// k_huffman.cu -- code histogram, canonical Huffman codebook, chunked
+// encode and decode of the quantization codes (Sec. 4 Step 4).
+//
+// Stream convention (shared with the decoder): the row-major code array is
+// cut into chunks of C symbols; each chunk's codes are packed MSB-first
+// into 32-bit words starting at a fresh word; the per-chunk word counts are
+// stored so chunks decode independently.  Codebook: two-queue Huffman merge
+// over leaves sorted by (frequency, symbol), ties taking the leaf; lengths
+// are leaf depths; canonical codes ordered by (length, symbol).
+#include "hpez_internal.cuh"
+#include "hpez_launch.h"
+
+namespace hpez {
+
+constexpr int kHistLo = kRadius - 4096;  // shared-memory window of bins
+constexpr int kHistWin = 8192;
+
+// ---------------------------------------------------------------------
+// histogram of the 65536 code symbols + per-chunk count of code 0
+// ---------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+    k_hist(const uint16_t* __restrict__ codes, uint32_t N, uint32_t C,
+           uint32_t nch, uint32_t* __restrict__ hist, uint32_t* __restrict__ zc,
+           const Ctl* __restrict__ ctl) {
+  if (ctl->status || ctl->is_const) return;
+  __shared__ uint32_t sh[kHistWin];
+  for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  uint32_t cm1 = 0, c0 = 0, cp1 = 0;  // the three central bins in registers
+  auto add = [&](unsigned v) {
+    cm1 += (v == kRadius - 1);
+    c0 += (v == kRadius);
+    cp1 += (v == kRadius + 1);
+    if (v < kRadius - 1 || v > kRadius + 1) {
+      const int o = (int)v - kHistLo;
+      if (o >= 0 && o < kHistWin)
+        atomicAdd(&sh[o], 1u);
+      else
+        atomicAdd(&hist[v], 1u);
+    }
+  };
+  for (uint32_t c = warp; c < nch; c += nwarps) {
+    const uint32_t beg = c * C;
+    const uint32_t end = min(beg + C, N);
+    uint32_t zeros = 0;
+    if (end - beg == C) {
+      const uint4* p = reinterpret_cast<const uint4*>(codes + beg);
+      for (uint32_t i = lane; i < C / 8; i += 32) {
+        uint4 v = __ldcs(p + i);
+        const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const unsigned lo = w[k] & 0xFFFFu, hi = w[k] >> 16;
+          add(lo);
+          add(hi);
+          zeros += (lo == 0) + (hi == 0);
+        }
+      }
+    } else {
+      for (uint32_t i = beg + lane; i < end; i += 32) {
+        const unsigned v = codes[i];
+        add(v);
+        zeros += (v == 0);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) zeros += __shfl_xor_sync(0xffffffffu, zeros, o);
+    if (lane == 0) zc[c] = zeros;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    cm1 += __shfl_xor_sync(0xffffffffu, cm1, o);
+    c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+    cp1 += __shfl_xor_sync(0xffffffffu, cp1, o);
+  }
+  if (lane == 0) {
+    if (cm1) atomicAdd(&sh[kRadius - 1 - kHistLo], cm1);
+    if (c0) atomicAdd(&sh[kRadius - kHistLo], c0);
+    if (cp1) atomicAdd(&sh[kRadius + 1 - kHistLo], cp1);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kHistWin; i += blockDim.x)
+    if (sh[i]) atomicAdd(&hist[kHistLo + i], sh[i]);
+}
+
+// ---------------------------------------------------------------------
+// single-CTA helpers
+// ---------------------------------------------------------------------
+// exclusive scan of one value per thread over the block (blockDim <= 1024)
+__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t warp_sums[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    uint32_t s = lane < nw ? warp_sums[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) warp_sums[lane] = s;
+  }
+  __syncthreads();
+  const uint32_t before = (w ? warp_sums[w - 1] : 0) + x - v;
+  if (total) *total = warp_sums[((blockDim.x + 31) >> 5) - 1];
+  __syncthreads();
+  return before;
+}
+
+// ascending bitonic sort of P (power of two) u64 keys, whole block
+__device__ void bitonic_sort(unsigned long long* a, uint32_t P) {
+  for (uint32_t k = 2; k <= P; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+        const uint32_t ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long x = a[i], y = a[ixj];
+          const bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            a[i] = y;
+            a[ixj] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__host__ __device__ inline uint32_t next_pow2(uint32_t v) {
+  uint32_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+constexpr uint32_t kSmemLeaves = 8192;  // codebook fits shared memory
+constexpr size_t kCodebookSmem =
+    (size_t)kSmemLeaves * 8 + (size_t)kSmemLeaves * 8 + (size_t)kSmemLeaves * 8;
+
+// ---------------------------------------------------------------------
+// codebook: one CTA of 1024 threads
+//   hist[65536] -> enc[sym] = (len << 56) | code, table (syms asc, lens),
+//   ctl->n_used, ctl->max_len
+// scratch (global): gkeys u64[65536], giw u64[65536], gpar u32[131072],
+//                   lens_by_sym u8[65536]
+// ---------------------------------------------------------------------
+__global__ void __launch_bounds__(1024)
+    k_codebook(const uint32_t* __restrict__ hist, unsigned long long* enc,
+               uint16_t* tsyms, uint8_t* tlens, unsigned long long* gkeys,
+               unsigned long long* giw, uint32_t* gpar, uint8_t* lens_by_sym,
+               Ctl* ctl) {
+  if (ctl->status || ctl->is_const) return;
+  extern __shared__ unsigned long long smem[];
+  __shared__ uint32_t s_n;
+  __shared__ uint32_t bl_count[64];
+  __shared__ unsigned long long first_code[64];
+  __shared__ uint32_t start_pos[64];
+  __shared__ uint32_t s_maxlen;
+
+  const int tid = threadIdx.x;
+  // 1. compaction of used symbols, ascending
+  uint32_t cnt = 0;
+  const uint32_t b0 = tid * 64;
+  for (uint32_t i = 0; i < 64; ++i) cnt += hist[b0 + i] != 0;
+  uint32_t total;
+  uint32_t pos = block_exclusive_scan(cnt, &total);
+  if (tid == 0) s_n = total;
+  for (int i = tid; i < 64; i += blockDim.x) bl_count[i] = 0;
+  if (tid == 0) s_maxlen = 0;
+  __syncthreads();
+  const uint32_t n = s_n;
+  const bool in_smem = n <= kSmemLeaves;
+  const uint32_t P = next_pow2(n);
+  unsigned long long* keys = in_smem ? smem : gkeys;
+  unsigned long long* iw = in_smem ? smem + kSmemLeaves : giw;
+  uint32_t* par = in_smem ? reinterpret_cast<uint32_t*>(smem + 2 * kSmemLeaves)
+                          : gpar;
+  for (uint32_t i = 0; i < 64; ++i) {
+    const uint32_t f = hist[b0 + i];
+    if (f) {
+      keys[pos] = ((unsigned long long)f << 16) | (b0 + i);
+      tsyms[pos] = (uint16_t)(b0 + i);
+      ++pos;
+    }
+  }
+  for (uint32_t i = n + tid; i < P; i += blockDim.x) keys[i] = ~0ull;
+  __syncthreads();
+  if (n == 1) {
+    if (tid == 0) {
+      const uint32_t sym = (uint32_t)(keys[0] & 0xFFFFu);
+      enc[sym] = 0ull;  // the empty code
+      tlens[0] = 0;
+      ctl->n_used = 1;
+      ctl->max_len = 0;
+    }
+    return;
+  }
+  // 2. leaves by (frequency, symbol)
+  bitonic_sort(keys, P);
+  // 3. two-queue merge (sequential by nature)
+  if (tid == 0) {
+    uint32_t a = 0, b = 0, m = 0;
+    unsigned long long la = keys[0] >> 16;
+    unsigned long long ib = ~0ull;
+    for (uint32_t t = 0; t + 1 < n; ++t) {
+      uint32_t node[2];
+      unsigned long long wsum = 0;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        if (a < n && (b >= m || la <= ib)) {
+          node[r] = a;
+          wsum += la;
+          ++a;
+          la = a < n ? (keys[a] >> 16) : ~0ull;
+        } else {
+          node[r] = n + b;
+          wsum += ib;
+          ++b;
+          ib = b < m ? iw[b] : ~0ull;
+        }
+      }
+      iw[m] = wsum;
+      par[node[0]] = n + m;
+      par[node[1]] = n + m;
+      if (b == m) ib = wsum;
+      ++m;
+    }
+  }
+  __syncthreads();
+  // 4. leaf depths by walking to the root (one walk per leaf)
+  const uint32_t root = 2 * n - 2;
+  uint32_t my_max = 0;
+  for (uint32_t i = tid; i < n; i += blockDim.x) {
+    uint32_t d = 0, v = i;
+    while (v != root && d < 64) {  // depth <= 63 for any valid tree
+      v = par[v];
+      ++d;
+    }
+    const uint32_t sym = (uint32_t)(keys[i] & 0xFFFFu);
+    lens_by_sym[sym] = (uint8_t)d;
+    my_max = max(my_max, d);
+    atomicAdd(&bl_count[d < 63 ? d : 63], 1u);
+  }
+  atomicMax(&s_maxlen, my_max);
+  __syncthreads();
+  const uint32_t maxlen = s_maxlen;
+  if (maxlen > 56) {
+    if (tid == 0) ctl->status = ST_INVALID;
+    return;
+  }
+  // 5. canonical order (length, symbol)
+  for (uint32_t i = tid; i < n; i += blockDim.x) {
+    const uint32_t sym = (uint32_t)(keys[i] & 0xFFFFu);
+    keys[i] = ((unsigned long long)lens_by_sym[sym] << 16) | sym;
+  }
+  __syncthreads();
+  bitonic_sort(keys, P);
+  if (tid == 0) {
+    unsigned long long code = 0;
+    uint32_t p = 0;
+    bl_count[0] = 0;
+    for (uint32_t bits = 1; bits <= maxlen; ++bits) {
+      code = (code + bl_count[bits - 1]) << 1;
+      first_code[bits] = code;
+      start_pos[bits] = p;
+      p += bl_count[bits];
+    }
+    ctl->n_used = n;
+    ctl->max_len = maxlen;
+  }
+  __syncthreads();
+  for (uint32_t i = tid; i < n; i += blockDim.x) {
+    const uint32_t len = (uint32_t)(keys[i] >> 16);
+    const uint32_t sym = (uint32_t)(keys[i] & 0xFFFFu);
+    const unsigned long long code = first_code[len] + (i - start_pos[len]);
+    enc[sym] = ((unsigned long long)len << 56) | code;
+  }
+  for (uint32_t k = tid; k < n; k += blockDim.x) tlens[k] = lens_by_sym[tsyms[k]];
+}
+
+// ---------------------------------------------------------------------
+// encode: per-chunk word counts
+// ---------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+    k_enc_len(const uint16_t* __restrict__ codes, uint32_t N, uint32_t C,
+              uint32_t nch, const unsigned long long* __restrict__ enc,
+              uint32_t* __restrict__ chw, const Ctl* __restrict__ ctl) {
+  if (ctl->status || ctl->is_const) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t c = warp; c < nch; c += nwarps) {
+    const uint32_t beg = c * C, end = min(beg + C, N);
+    unsigned long long bits = 0;
+    if (end - beg == C) {
+      const uint4* p = reinterpret_cast<const uint4*>(codes + beg);
+      for (uint32_t i = lane; i < C / 8; i += 32) {
+        const uint4 v = p[i];
+        const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          bits += (enc[w[k] & 0xFFFFu] >> 56) + (enc[w[k] >> 16] >> 56);
+      }
+    } else {
+      for (uint32_t i = beg + lane; i < end; i += 32) bits += enc[codes[i]] >> 56;
+    }
+    for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
+    if (lane == 0) chw[c] = (uint32_t)((bits + 31) >> 5);
+  }
+}
+
+// ---------------------------------------------------------------------
+// encode: packing (one warp per chunk, contiguous symbol range per lane)
+// ---------------------------------------------------------------------
+struct BitWriter {
+  uint32_t* words;   // chunk base
+  uint32_t wi;       // current word index
+  unsigned long long acc;
+  int nacc;
+  bool shared_first;
+  __device__ void emit(uint32_t w) {
+    if (shared_first) {
+      atomicOr(words + wi, w);
+      shared_first = false;
+    } else {
+      words[wi] = w;
+    }
+    ++wi;
+  }
+  __device__ void put(uint32_t v, int n) {  // n <= 32, nacc < 32
+    if (n == 0) return;
+    acc |= (unsigned long long)v << (64 - nacc - n);
+    nacc += n;
+    if (nacc >= 32) {
+      emit((uint32_t)(acc >> 32));
+      acc <<= 32;
+      nacc -= 32;
+    }
+  }
+  __device__ void put_code(unsigned long long e) {
+    const int len = (int)(e >> 56);
+    const unsigned long long code = e & ((1ull << 56) - 1);
+    if (len > 32) {
+      put((uint32_t)(code >> 32), len - 32);
+      put((uint32_t)code, 32);
+    } else {
+      put((uint32_t)code, len);
+    }
+  }
+  __device__ void flush() {
+    if (nacc > 0) atomicOr(words + wi, (uint32_t)(acc >> 32));
+  }
+};
+
+__global__ void __launch_bounds__(256)
+    k_pack(const uint16_t* __restrict__ codes, uint32_t N, uint32_t C,
+           uint32_t nch, const unsigned long long* __restrict__ enc,
+           const uint32_t* __restrict__ chw,
+           const unsigned long long* __restrict__ woff, uint8_t* out,
+           const Ctl* __restrict__ ctl) {
+  if (ctl->status || ctl->is_const) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  uint32_t* bits = reinterpret_cast<uint32_t*>(out + ctl->off_bits);
+  for (uint32_t c = warp; c < nch; c += nwarps) {
+    const uint32_t beg = c * C, end = min(beg + C, N);
+    uint32_t* words = bits + woff[c];
+    const uint32_t nw = chw[c];
+    for (uint32_t i = lane; i < nw; i += 32) words[i] = 0u;
+    __syncwarp();
+    const uint32_t per = C / 32;
+    const uint32_t lb = min(beg + lane * per, end), le = min(lb + per, end);
+    unsigned long long mybits = 0;
+    for (uint32_t i = lb; i < le; ++i) mybits += enc[codes[i]] >> 56;
+    unsigned long long off = mybits;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, off, o);
+      if (lane >= o) off += y;
+    }
+    off -= mybits;
+    BitWriter bw;
+    bw.words = words;
+    bw.wi = (uint32_t)(off >> 5);
+    bw.nacc = (int)(off & 31);
+    bw.acc = 0;
+    bw.shared_first = bw.nacc != 0;
+    for (uint32_t i = lb; i < le; ++i) bw.put_code(enc[codes[i]]);
+    bw.flush();
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------
+// outlier gather (compress) / scatter (decompress), row-major order
+// ---------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+    k_outliers(bool gather, const uint16_t* __restrict__ codes, uint32_t N,
+               uint32_t C, uint32_t nch, const uint32_t* __restrict__ zc,
+               const unsigned long long* __restrict__ zoff, const float* src,
+               float* dst, uint8_t* stream, unsigned long long max_out,
+               Ctl* ctl) {
+  if (ctl->status || ctl->is_const) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  float* outl = reinterpret_cast<float*>(stream + ctl->off_outliers);
+  for (uint32_t c = warp; c < nch; c += nwarps) {
+    if (zc[c] == 0) continue;
+    const uint32_t beg = c * C, end = min(beg + C, N);
+    unsigned long long base = zoff[c];
+    for (uint32_t i0 = beg; i0 < end; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      const bool z = i < end && codes[i] == 0;
+      const unsigned mask = __ballot_sync(0xffffffffu, z);
+      if (z) {
+        const unsigned long long k = base + __popc(mask & ((1u << lane) - 1u));
+        if (k >= max_out)  // more escapes than stored outliers: corrupt
+          atomicExch(&ctl->status, ST_CORRUPT);
+        else if (gather)
+          outl[k] = src[i];
+        else
+          dst[i] = outl[k];
+      }
+      base += __popc(mask);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------
+// decode tables from the stream's (symbol, length) table
+//   dec: [0,4096) LUT (len << 16 | sym, 0 = longer than 12 bits)
+//        then count[64], first[64] (u64), offs[64], sorted syms
+// ---------------------------------------------------------------------
+constexpr int kLutBits = 12;
+
+__global__ void __launch_bounds__(1024)
+    k_dec_tables(const uint8_t* __restrict__ stream, uint32_t n_used,
+                 uint64_t off_table, uint32_t* lut, uint32_t* cnt,
+                 unsigned long long* first, uint32_t* offs, uint16_t* sorted,
+                 unsigned long long* gkeys, Ctl* ctl) {
+  extern __shared__ unsigned long long smem[];
+  __shared__ uint32_t s_bad;
+  __shared__ uint32_t s_cnt[64];
+  const int tid = threadIdx.x;
+  const uint8_t* tab = stream + off_table;
+  if (tid == 0) s_bad = 0;
+  for (int i = tid; i < 64; i += blockDim.x) s_cnt[i] = 0;
+  for (int i = tid; i < (1 << kLutBits); i += blockDim.x) lut[i] = 0;
+  __syncthreads();
+  const uint32_t P = next_pow2(n_used);
+  unsigned long long* keys = n_used <= kSmemLeaves ? smem : gkeys;
+  for (uint32_t k = tid; k < P; k += blockDim.x) {
+    if (k < n_used) {
+      const uint32_t sym = (uint32_t)tab[2 * k] | ((uint32_t)tab[2 * k + 1] << 8);
+      const uint32_t len = tab[2 * (size_t)n_used + k];
+      if (k > 0) {
+        const uint32_t prev =
+            (uint32_t)tab[2 * k - 2] | ((uint32_t)tab[2 * k - 1] << 8);
+        if (sym <= prev) s_bad = 1;
+      }
+      if (len > 56 || (n_used > 1 && len == 0) || (n_used == 1 && len != 0))
+        s_bad = 1;
+      keys[k] = ((unsigned long long)len << 16) | sym;
+      atomicAdd(&s_cnt[len & 63], 1u);
+    } else {
+      keys[k] = ~0ull;
+    }
+  }
+  __syncthreads();
+  if (s_bad) {
+    if (tid == 0) ctl->status = ST_CORRUPT;
+    return;
+  }
+  bitonic_sort(keys, P);
+  if (tid == 0) {
+    unsigned long long code = 0;
+    uint32_t p = 0;
+    unsigned long long kraft = 0;
+    for (int b = 0; b < 64; ++b) {
+      cnt[b] = s_cnt[b];
+      first[b] = 0;
+      offs[b] = 0;
+    }
+    for (int b = 1; b < 64; ++b) {
+      code = (code + (b - 1 >= 1 ? s_cnt[b - 1] : 0)) << 1;
+      first[b] = code;
+      offs[b] = p;
+      p += s_cnt[b];
+      if (b <= 56) kraft += (unsigned long long)s_cnt[b] << (56 - b);
+    }
+    if (n_used > 1 && kraft != (1ull << 56)) ctl->status = ST_CORRUPT;
+  }
+  __syncthreads();
+  for (uint32_t i = tid; i < n_used; i += blockDim.x) {
+    const uint32_t len = (uint32_t)(keys[i] >> 16);
+    const uint32_t sym = (uint32_t)(keys[i] & 0xFFFFu);
+    sorted[i] = (uint16_t)sym;
+    if (len >= 1 && len <= kLutBits) {
+      // code = first[len] + rank within its length
+      uint32_t lo_pos = 0;
+      unsigned long long fc = 0;
+      {
+        unsigned long long c2 = 0;
+        uint32_t p2 = 0;
+        for (uint32_t b = 1; b <= len; ++b) {
+          c2 = (c2 + (b - 1 >= 1 ? s_cnt[b - 1] : 0)) << 1;
+          if (b == len) {
+            fc = c2;
+            lo_pos = p2;
+          }
+          p2 += s_cnt[b];
+        }
+      }
+      const unsigned long long code = fc + (i - lo_pos);
+      const uint32_t a = (uint32_t)(code << (kLutBits - len));
+      const uint32_t e = (uint32_t)((code + 1) << (kLutBits - len));
+      for (uint32_t j = a; j < e && j < (1u << kLutBits); ++j)
+        lut[j] = (len << 16) | sym;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------
+// decode: one thread per chunk
+// ---------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+    k_decode(const uint8_t* __restrict__ stream, uint64_t off_bits,
+             uint64_t total_words, const uint32_t* __restrict__ chw_stream,
+             const unsigned long long* __restrict__ woff, uint32_t N,
+             uint32_t C, uint32_t nch, uint32_t n_used, uint16_t single_sym,
+             const uint32_t* __restrict__ g_lut,
+             const uint32_t* __restrict__ g_cnt,
+             const unsigned long long* __restrict__ g_first,
+             const uint32_t* __restrict__ g_offs,
+             const uint16_t* __restrict__ sorted, uint16_t* __restrict__ codes,
+             uint32_t* __restrict__ zc, Ctl* ctl) {
+  __shared__ uint32_t lut[1 << kLutBits];
+  __shared__ uint32_t cnt[64], offs[64];
+  __shared__ unsigned long long first[64];
+  for (int i = threadIdx.x; i < (1 << kLutBits); i += blockDim.x) lut[i] = g_lut[i];
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+    cnt[i] = g_cnt[i];
+    offs[i] = g_offs[i];
+    first[i] = g_first[i];
+  }
+  __syncthreads();
+  if (ctl->status) return;
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nch) return;
+  const uint32_t beg = c * C, end = min(beg + C, N);
+  uint32_t zeros = 0;
+  if (n_used == 1) {
+    for (uint32_t i = beg; i < end; ++i) codes[i] = single_sym;
+    zc[c] = single_sym == 0 ? end - beg : 0;
+    return;
+  }
+  const uint32_t nw = chw_stream[c];
+  const unsigned long long w0 = woff[c];
+  if (w0 + nw > total_words) {
+    atomicExch(&ctl->status, ST_CORRUPT);
+    return;
+  }
+  const uint32_t* words = reinterpret_cast<const uint32_t*>(stream + off_bits) + w0;
+  uint32_t wi = 0;
+  unsigned long long buf = 0;
+  int nbuf = 0;
+  auto refill = [&]() {
+    while (nbuf <= 32 && wi < nw) {
+      buf |= (unsigned long long)__ldg(words + wi) << (32 - nbuf);
+      nbuf += 32;
+      ++wi;
+    }
+  };
+  uint32_t pack[4];
+  int np = 0;
+  const bool vec = (end - beg) == C;
+  for (uint32_t i = beg; i < end; ++i) {
+    refill();
+    const uint32_t e = lut[(uint32_t)(buf >> (64 - kLutBits))];
+    uint32_t sym, len;
+    if (e != 0) {
+      len = e >> 16;
+      sym = e & 0xFFFFu;
+    } else {
+      sym = 0;
+      len = 0;
+      for (uint32_t L = kLutBits + 1; L < 57; ++L) {
+        const unsigned long long v = buf >> (64 - L);
+        if (cnt[L] && v >= first[L] && v - first[L] < cnt[L]) {
+          sym = sorted[offs[L] + (uint32_t)(v - first[L])];
+          len = L;
+          break;
+        }
+      }
+    }
+    if (len == 0 || (int)len > nbuf) {
+      atomicExch(&ctl->status, ST_CORRUPT);
+      return;
+    }
+    buf <<= len;
+    nbuf -= (int)len;
+    zeros += sym == 0;
+    if (vec) {
+      if (np & 1)
+        pack[np >> 1] |= sym << 16;
+      else
+        pack[np >> 1] = sym;
+      if (++np == 8) {
+        *reinterpret_cast<uint4*>(codes + i - 7) =
+            make_uint4(pack[0], pack[1], pack[2], pack[3]);
+        np = 0;
+      }
+    } else {
+      codes[i] = (uint16_t)sym;
+    }
+  }
+  zc[c] = zeros;
+}
+
+// ---------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------
+static inline unsigned warps_grid(uint32_t nch, int num_sms) {
+  uint64_t g = ((uint64_t)nch + 7) / 8;
+  const uint64_t cap = (uint64_t)num_sms * 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+void launch_hist(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,
+                 uint32_t* hist, uint32_t* zc, const Ctl* ctl, int num_sms,
+                 cudaStream_t s) {
+  k_hist<<<warps_grid(nch, num_sms), 256, 0, s>>>(codes, N, C, nch, hist, zc,
+                                                  ctl);
+}
+
+void launch_codebook(const uint32_t* hist, unsigned long long* enc,
+                     uint16_t* tsyms, uint8_t* tlens, unsigned long long* gkeys,
+                     unsigned long long* giw, uint32_t* gpar,
+                     uint8_t* lens_by_sym, Ctl* ctl, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kCodebookSmem);
+    cudaFuncSetAttribute(k_dec_tables,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(kSmemLeaves * 8));
+    attr = true;
+  }
+  k_codebook<<<1, 1024, kCodebookSmem, s>>>(hist, enc, tsyms, tlens, gkeys, giw,
+                                            gpar, lens_by_sym, ctl);
+}
+
+void launch_enc_len(const uint16_t* codes, uint32_t N, uint32_t C,
+                    uint32_t nch, const unsigned long long* enc, uint32_t* chw,
+                    const Ctl* ctl, int num_sms, cudaStream_t s) {
+  k_enc_len<<<warps_grid(nch, num_sms), 256, 0, s>>>(codes, N, C, nch, enc, chw,
+                                                     ctl);
+}
+
+void launch_pack(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,
+                 const unsigned long long* enc, const uint32_t* chw,
+                 const unsigned long long* woff, uint8_t* out, const Ctl* ctl,
+                 int num_sms, cudaStream_t s) {
+  k_pack<<<warps_grid(nch, num_sms), 256, 0, s>>>(codes, N, C, nch, enc, chw,
+                                                  woff, out, ctl);
+}
+
+void launch_outliers(bool gather, const uint16_t* codes, uint32_t N,
+                     uint32_t C, uint32_t nch, const uint32_t* zc,
+                     const unsigned long long* zoff, const float* src,
+                     float* dst, uint8_t* stream, unsigned long long max_out,
+                     Ctl* ctl, int num_sms, cudaStream_t s) {
+  k_outliers<<<warps_grid(nch, num_sms), 256, 0, s>>>(
+      gather, codes, N, C, nch, zc, zoff, src, dst, stream, max_out, ctl);
+}
+
+void launch_dec_tables(const uint8_t* stream, uint32_t n_used,
+                       uint64_t off_table, uint32_t* lut, uint32_t* cnt,
+                       unsigned long long* first, uint32_t* offs,
+                       uint16_t* sorted, unsigned long long* gkeys, Ctl* ctl,
+                       cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_dec_tables,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(kSmemLeaves * 8));
+    attr = true;
+  }
+  k_dec_tables<<<1, 1024, kSmemLeaves * 8, s>>>(stream, n_used, off_table, lut,
+                                                cnt, first, offs, sorted, gkeys,
+                                                ctl);
+}
+
+void launch_decode(const uint8_t* stream, uint64_t off_bits,
+                   uint64_t total_words, const uint32_t* chw_stream,
+                   const unsigned long long* woff, uint32_t N, uint32_t C,
+                   uint32_t nch, uint32_t n_used, uint16_t single_sym,
+                   const uint32_t* lut, const uint32_t* cnt,
+                   const unsigned long long* first, const uint32_t* offs,
+                   const uint16_t* sorted, uint16_t* codes, uint32_t* zc,
+                   Ctl* ctl, cudaStream_t s) {
+  const unsigned grid = (nch + 127) / 128;
+  k_decode<<<grid, 128, 0, s>>>(stream, off_bits, total_words, chw_stream,
+                                woff, N, C, nch, n_used, single_sym, lut, cnt,
+                                first, offs, sorted, codes, zc, ctl);
+}
+
+}  // namespace hpez

@@ -1,0 +1,203 @@
+// k_stream.cu -- prefix scans and assembly of the compressed container.
+//
+// Container (little-endian): a 512-byte header, then 16-byte aligned
+// sections: anchors (f32, compact anchor grid in row-major order), block
+// map (u8 per block, optional), chunk word counts (u32 per chunk), code
+// table (u16 symbols ascending, then u8 lengths), outliers (f32, row-major
+// order of their points), bitstream (u32 words).  Padding bytes are zero.
+#include "hpez_internal.cuh"
+#include "hpez_launch.h"
+
+namespace hpez {
+
+// exclusive scan of n u32 values into u64, single CTA of 1024 threads;
+// *total receives the sum
+__global__ void __launch_bounds__(1024)
+    k_scan(const uint32_t* __restrict__ in, unsigned long long* __restrict__ out,
+           uint32_t n, unsigned long long* total, const Ctl* __restrict__ ctl) {
+  if (ctl->status || ctl->is_const) return;
+  __shared__ unsigned long long warp_sums[32];
+  __shared__ unsigned long long carry;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < n; base += blockDim.x * 8u) {
+    // each thread owns 8 consecutive values of this tile
+    unsigned long long v[8], s = 0;
+    const uint32_t i0 = base + tid * 8u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      v[k] = (i0 + k < n) ? in[i0 + k] : 0u;
+      s += v[k];
+    }
+    unsigned long long x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      unsigned long long t = warp_sums[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      warp_sums[lane] = t;
+    }
+    __syncthreads();
+    unsigned long long run = carry + (w ? warp_sums[w - 1] : 0) + x - s;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (i0 + k < n) out[i0 + k] = run;
+      run += v[k];
+    }
+    __syncthreads();
+    if (tid == 0) carry += warp_sums[31];
+    __syncthreads();
+  }
+  if (tid == 0) *total = carry;
+}
+
+__host__ __device__ inline unsigned long long align16(unsigned long long v) {
+  return (v + 15ull) & ~15ull;
+}
+
+// dynamic section offsets + capacity check
+__global__ void k_layout(Ctl* ctl, unsigned long long off_table,
+                         unsigned long long cap) {
+  if (threadIdx.x != 0 || ctl->status) return;
+  if (ctl->is_const) {
+    ctl->total_size = kHeaderBytes;
+    if (cap < (unsigned long long)kHeaderBytes) ctl->status = ST_OUT_TOO_SMALL;
+    return;
+  }
+  ctl->off_table = off_table;
+  ctl->off_outliers = align16(off_table + 3ull * ctl->n_used);
+  ctl->off_bits = align16(ctl->off_outliers + 4ull * ctl->n_out);
+  ctl->total_size = ctl->off_bits + 4ull * ctl->total_words;
+  if (ctl->total_size > cap) ctl->status = ST_OUT_TOO_SMALL;
+}
+
+struct HeaderImage {
+  uint8_t b[kHeaderBytes];
+};
+
+__device__ inline void put_u32(uint8_t* p, uint32_t v) {
+  p[0] = (uint8_t)v;
+  p[1] = (uint8_t)(v >> 8);
+  p[2] = (uint8_t)(v >> 16);
+  p[3] = (uint8_t)(v >> 24);
+}
+__device__ inline void put_u64(uint8_t* p, unsigned long long v) {
+  for (int i = 0; i < 8; ++i) p[i] = (uint8_t)(v >> (8 * i));
+}
+
+// header byte offsets patched on the device
+constexpr int kHE = 56, kHConst = 60, kHNOut = 224, kHNUsed = 232,
+              kHTotalWords = 248, kHOffTable = 272, kHOffOutliers = 280,
+              kHOffBits = 288, kHTotal = 304;
+
+// Writes the header and the static-size sections; pads every section end
+// with zeros up to the next 16-byte boundary.
+__global__ void k_finalize(HeaderImage hdr, HeaderImage hdr_const,
+                           uint8_t* __restrict__ out,
+                           const float* __restrict__ RA, uint32_t na,
+                           unsigned long long off_anchors,
+                           const uint8_t* __restrict__ bmap, uint32_t nblocks,
+                           unsigned long long off_bmap,
+                           const uint32_t* __restrict__ chw, uint32_t nch,
+                           unsigned long long off_chw,
+                           const uint16_t* __restrict__ tsyms,
+                           const uint8_t* __restrict__ tlens,
+                           const Ctl* __restrict__ ctl) {
+  if (ctl->status) return;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nthr = gridDim.x * blockDim.x;
+  if (ctl->is_const) {
+    for (uint32_t i = tid; i < (uint32_t)kHeaderBytes; i += nthr) {
+      uint8_t v = hdr_const.b[i];
+      if (i >= kHConst && i < kHConst + 4)
+        v = (uint8_t)(__float_as_uint(ctl->const_value) >> (8 * (i - kHConst)));
+      out[i] = v;
+    }
+    return;
+  }
+  if (tid == 0) {
+    uint8_t h[kHeaderBytes];
+    for (int i = 0; i < kHeaderBytes; ++i) h[i] = hdr.b[i];
+    put_u32(h + kHE, __float_as_uint(ctl->e));
+    put_u64(h + kHNOut, ctl->n_out);
+    put_u32(h + kHNUsed, ctl->n_used);
+    put_u64(h + kHTotalWords, ctl->total_words);
+    put_u64(h + kHOffTable, ctl->off_table);
+    put_u64(h + kHOffOutliers, ctl->off_outliers);
+    put_u64(h + kHOffBits, ctl->off_bits);
+    put_u64(h + kHTotal, ctl->total_size);
+    for (int i = 0; i < kHeaderBytes; i += 4)
+      *reinterpret_cast<uint32_t*>(out + i) =
+          (uint32_t)h[i] | ((uint32_t)h[i + 1] << 8) |
+          ((uint32_t)h[i + 2] << 16) | ((uint32_t)h[i + 3] << 24);
+  }
+  // anchors
+  float* fa = reinterpret_cast<float*>(out + off_anchors);
+  for (uint32_t i = tid; i < na; i += nthr) fa[i] = RA[i];
+  // block map
+  for (uint32_t i = tid; i < nblocks; i += nthr) out[off_bmap + i] = bmap[i];
+  // chunk word counts
+  uint32_t* fc = reinterpret_cast<uint32_t*>(out + off_chw);
+  for (uint32_t i = tid; i < nch; i += nthr) fc[i] = chw[i];
+  // code table: symbols then lengths
+  const uint32_t nu = ctl->n_used;
+  const unsigned long long ot = ctl->off_table;
+  for (uint32_t k = tid; k < nu; k += nthr) {
+    const uint16_t sy = tsyms[k];
+    out[ot + 2ull * k] = (uint8_t)sy;
+    out[ot + 2ull * k + 1] = (uint8_t)(sy >> 8);
+    out[ot + 2ull * nu + k] = tlens[k];
+  }
+  // zero padding at the end of each section
+  const unsigned long long ends[5] = {off_anchors + 4ull * na,
+                                      off_bmap + nblocks, off_chw + 4ull * nch,
+                                      ot + 3ull * nu,
+                                      ctl->off_outliers + 4ull * ctl->n_out};
+  if (tid < 5) {
+    for (unsigned long long p = ends[tid]; p < align16(ends[tid]); ++p) out[p] = 0;
+  }
+}
+
+// ---------------------------------------------------------------------
+void launch_scan(const uint32_t* in, unsigned long long* out, uint32_t n,
+                 unsigned long long* total, const Ctl* ctl, cudaStream_t s) {
+  k_scan<<<1, 1024, 0, s>>>(in, out, n, total, ctl);
+}
+
+void launch_layout(Ctl* ctl, unsigned long long off_table,
+                   unsigned long long cap, cudaStream_t s) {
+  k_layout<<<1, 32, 0, s>>>(ctl, off_table, cap);
+}
+
+void launch_finalize(const uint8_t* hdr, const uint8_t* hdr_const,
+                     uint8_t* out, const float* RA, uint32_t na,
+                     unsigned long long off_anchors, const uint8_t* bmap,
+                     uint32_t nblocks, unsigned long long off_bmap,
+                     const uint32_t* chw, uint32_t nch,
+                     unsigned long long off_chw, const uint16_t* tsyms,
+                     const uint8_t* tlens, const Ctl* ctl, int num_sms,
+                     cudaStream_t s) {
+  HeaderImage h, hc;
+  for (int i = 0; i < kHeaderBytes; ++i) {
+    h.b[i] = hdr[i];
+    hc.b[i] = hdr_const[i];
+  }
+  uint64_t work = na;
+  if (nch > work) work = nch;
+  unsigned grid = (unsigned)((work + 255) / 256);
+  if (grid < 1) grid = 1;
+  if (grid > (unsigned)num_sms * 4) grid = num_sms * 4;
+  k_finalize<<<grid, 256, 0, s>>>(h, hc, out, RA, na, off_anchors, bmap,
+                                  nblocks, off_bmap, chw, nch, off_chw, tsyms,
+                                  tlens, ctl);
+}
+
+}  // namespace hpez

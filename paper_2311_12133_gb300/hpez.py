@@ -1,0 +1,286 @@
+"""Thin ctypes binding of ``libhpez.so`` (the C-ABI of ``include/hpez.h``).
+
+Argument marshalling only: every step of compress/decompress runs in the
+library's CUDA kernels.  If the library has not been built this module
+raises on use; there is no CPU fallback.  PyTorch is used only to hold
+device memory and to name the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib",
+                         "libhpez.so")
+
+HPEZ_MAX_LEVELS = 16
+HPEZ_HEADER_BYTES = 512
+HPEZ_OK = 0
+HPEZ_EB_ABS, HPEZ_EB_REL = 0, 1
+HPEZ_LINEAR, HPEZ_CUBIC_NAK, HPEZ_CUBIC_NAT = 0, 1, 2
+HPEZ_PARADIGM_1D, HPEZ_PARADIGM_MD = 0, 1
+
+
+class HpezError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        msg = hpez_strerror(code) if _lib is not None else str(code)
+        super().__init__(f"{what}: hpez error {code} ({msg})")
+        self.code = code
+
+
+class hpez_config(ctypes.Structure):
+    _fields_ = [
+        ("anchor_stride", ctypes.c_int32),
+        ("frozen_dim", ctypes.c_int32),
+        ("chunk_syms", ctypes.c_int32),
+        ("blockwise", ctypes.c_int32),
+        ("block_size", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("alpha", ctypes.c_double),
+        ("beta", ctypes.c_double),
+        ("md_inv_var", ctypes.c_double * 3),
+        ("interp", ctypes.c_uint8 * HPEZ_MAX_LEVELS),
+        ("paradigm", ctypes.c_uint8 * HPEZ_MAX_LEVELS),
+        ("same_level", ctypes.c_uint8 * HPEZ_MAX_LEVELS),
+        ("order", (ctypes.c_uint8 * 3) * HPEZ_MAX_LEVELS),
+        ("h_blockmap", ctypes.c_void_p),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(
+                f"{_LIB_PATH} is missing: build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'` "
+                "(there is no fallback implementation)")
+        L = ctypes.CDLL(_LIB_PATH)
+        vp, u64, u64p = ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)
+        cfgp = ctypes.POINTER(hpez_config)
+        sig = {
+            "hpez_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int]),
+            "hpez_destroy": (ctypes.c_int, [vp]),
+            "hpez_default_config": (ctypes.c_int, [ctypes.c_int, cfgp]),
+            "hpez_compress_bound": (ctypes.c_int, [ctypes.c_int, u64p, u64p]),
+            "hpez_compress": (ctypes.c_int, [vp, vp, ctypes.c_int, u64p,
+                                             ctypes.c_int, ctypes.c_double,
+                                             cfgp, vp, u64, u64p, vp]),
+            "hpez_decompress": (ctypes.c_int, [vp, vp, u64, vp, u64, vp]),
+            "hpez_compress_host": (ctypes.c_int, [vp, vp, ctypes.c_int, u64p,
+                                                  ctypes.c_int, ctypes.c_double,
+                                                  cfgp, vp, u64, u64p, vp]),
+            "hpez_decompress_host": (ctypes.c_int, [vp, vp, u64, vp, u64, vp]),
+            "hpez_inspect": (ctypes.c_int, [vp, u64, ctypes.POINTER(ctypes.c_int),
+                                            u64p, ctypes.POINTER(ctypes.c_double)]),
+            "hpez_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def exported_symbols() -> list[str]:
+    """Names of the C-ABI entry points this binding expects."""
+    return ["hpez_create", "hpez_destroy", "hpez_default_config",
+            "hpez_compress_bound", "hpez_compress", "hpez_decompress",
+            "hpez_compress_host", "hpez_decompress_host", "hpez_inspect",
+            "hpez_strerror"]
+
+
+def _check(rc: int, what: str):
+    if rc != HPEZ_OK:
+        raise HpezError(rc, what)
+
+
+def _dims(shape):
+    return (ctypes.c_uint64 * 3)(*([int(v) for v in shape] + [1] * (3 - len(shape))))
+
+
+# --------------------------------------------------------------------------
+# the C-ABI, name for name
+# --------------------------------------------------------------------------
+def hpez_strerror(code: int) -> str:
+    return _load().hpez_strerror(code).decode()
+
+
+def hpez_create(device: int = 0) -> int:
+    h = ctypes.c_void_p(0)
+    _check(_load().hpez_create(ctypes.byref(h), device), "hpez_create")
+    return h.value
+
+
+def hpez_destroy(ctx: int) -> None:
+    _check(_load().hpez_destroy(ctx), "hpez_destroy")
+
+
+def hpez_default_config(ndim: int) -> hpez_config:
+    c = hpez_config()
+    _check(_load().hpez_default_config(ndim, ctypes.byref(c)), "hpez_default_config")
+    return c
+
+
+def hpez_compress_bound(shape) -> int:
+    out = ctypes.c_uint64(0)
+    _check(_load().hpez_compress_bound(len(shape), _dims(shape), ctypes.byref(out)),
+           "hpez_compress_bound")
+    return out.value
+
+
+def hpez_compress(ctx, d_in: int, shape, eb_mode: int, eb: float,
+                  cfg: hpez_config | None, d_out: int, out_cap: int,
+                  stream: int = 0) -> int:
+    size = ctypes.c_uint64(0)
+    _check(_load().hpez_compress(ctx, d_in, len(shape), _dims(shape), eb_mode,
+                                 float(eb), ctypes.byref(cfg) if cfg is not None else None,
+                                 d_out, out_cap, ctypes.byref(size), stream or None),
+           "hpez_compress")
+    return size.value
+
+
+def hpez_decompress(ctx, d_in: int, in_size: int, d_out: int,
+                    out_cap_elems: int, stream: int = 0) -> None:
+    _check(_load().hpez_decompress(ctx, d_in, in_size, d_out, out_cap_elems,
+                                   stream or None), "hpez_decompress")
+
+
+def hpez_compress_host(ctx, h_in: np.ndarray, eb_mode: int, eb: float,
+                       cfg: hpez_config | None, h_out: np.ndarray,
+                       stream: int = 0) -> int:
+    assert h_in.dtype == np.float32 and h_in.flags.c_contiguous
+    size = ctypes.c_uint64(0)
+    _check(_load().hpez_compress_host(
+        ctx, h_in.ctypes.data, h_in.ndim, _dims(h_in.shape), eb_mode, float(eb),
+        ctypes.byref(cfg) if cfg is not None else None, h_out.ctypes.data,
+        h_out.nbytes, ctypes.byref(size), stream or None), "hpez_compress_host")
+    return size.value
+
+
+def hpez_decompress_host(ctx, h_in: np.ndarray, in_size: int,
+                         h_out: np.ndarray, stream: int = 0) -> None:
+    assert h_out.dtype == np.float32 and h_out.flags.c_contiguous
+    _check(_load().hpez_decompress_host(ctx, h_in.ctypes.data, in_size,
+                                        h_out.ctypes.data, h_out.size,
+                                        stream or None), "hpez_decompress_host")
+
+
+def hpez_inspect(header: bytes):
+    buf = np.frombuffer(header, dtype=np.uint8)
+    nd = ctypes.c_int(0)
+    dims = (ctypes.c_uint64 * 3)()
+    eb = ctypes.c_double(0)
+    _check(_load().hpez_inspect(buf.ctypes.data, buf.size, ctypes.byref(nd), dims,
+                                ctypes.byref(eb)), "hpez_inspect")
+    return nd.value, tuple(int(dims[i]) for i in range(nd.value)), eb.value
+
+
+# --------------------------------------------------------------------------
+# config helper
+# --------------------------------------------------------------------------
+def make_config(ndim: int, *, anchor_stride=None, frozen_dim=-1, chunk_syms=4096,
+                alpha=1.0, beta=1.0, md_inv_var=(1, 1, 1), interp=HPEZ_CUBIC_NAK,
+                paradigm=HPEZ_PARADIGM_1D, same_level=0, order=None,
+                blockmap=None, block_size=32) -> hpez_config:
+    """Config with one setting for all levels unless per-level lists are
+    given (index l-1); ``order`` may be one order or a per-level list."""
+    c = hpez_default_config(ndim)
+    if anchor_stride is not None:
+        c.anchor_stride = anchor_stride
+    c.frozen_dim = frozen_dim
+    c.chunk_syms = chunk_syms
+    c.alpha, c.beta = float(alpha), float(beta)
+    for d in range(3):
+        c.md_inv_var[d] = float(md_inv_var[d])
+    dims = [d for d in range(ndim) if d != frozen_dim]
+    for l in range(HPEZ_MAX_LEVELS):
+        c.interp[l] = interp[l] if isinstance(interp, (list, tuple)) else interp
+        c.paradigm[l] = paradigm[l] if isinstance(paradigm, (list, tuple)) else paradigm
+        c.same_level[l] = (same_level[l] if isinstance(same_level, (list, tuple))
+                           else same_level)
+        if order is None:
+            o = dims
+        elif isinstance(order[0], (list, tuple)):
+            o = order[l] if l < len(order) else order[-1]
+        else:
+            o = order
+        for j in range(3):
+            c.order[l][j] = o[j] if j < len(o) else 255
+    c.block_size = block_size
+    c.blockwise = 0
+    c._blockmap_ref = None
+    if blockmap is not None:
+        bm = np.ascontiguousarray(blockmap, dtype=np.uint8)
+        c._blockmap_ref = bm
+        c.h_blockmap = bm.ctypes.data
+        c.blockwise = 1
+    return c
+
+
+# --------------------------------------------------------------------------
+# torch convenience layer (device memory + streams only)
+# --------------------------------------------------------------------------
+class Context:
+    """Owns one hpez_ctx on a CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        self.handle = hpez_create(device)
+
+    def close(self):
+        if self.handle:
+            hpez_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _stream(stream):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        return stream.cuda_stream
+
+    def compress(self, x, eb: float, eb_mode: int = HPEZ_EB_REL,
+                 config: hpez_config | None = None, out=None, stream=None):
+        """x: contiguous float32 CUDA tensor.  Returns (uint8 tensor, size)."""
+        import torch
+        assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+        cap = hpez_compress_bound(tuple(x.shape))
+        if out is None or out.numel() < cap:
+            out = torch.empty(cap, dtype=torch.uint8, device=x.device)
+        size = hpez_compress(self.handle, x.data_ptr(), tuple(x.shape), eb_mode, eb,
+                             config, out.data_ptr(), out.numel(), self._stream(stream))
+        return out, size
+
+    def decompress(self, stream_buf, size: int, out=None, shape=None, stream=None):
+        """stream_buf: uint8 CUDA tensor holding `size` bytes."""
+        import torch
+        if shape is None:
+            hdr = stream_buf[:HPEZ_HEADER_BYTES].cpu().numpy().tobytes()
+            _, shape, _ = hpez_inspect(hdr)
+        n = int(np.prod(shape))
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=stream_buf.device)
+        hpez_decompress(self.handle, stream_buf.data_ptr(), size, out.data_ptr(), n,
+                        self._stream(stream))
+        return out

@@ -1,0 +1,204 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+The bar is bit-exact: compressed bytes (codes, outliers, Huffman tables and
+bitstream, header) and decompressed fields must equal the oracle's, a
+floating-point tolerance of 0 ULP, because both sides perform the same IEEE
+binary32 operations in the same order.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_12133_gb300 import build as B
+    B.build()
+    from paper_2311_12133_gb300 import hpez
+    ctx = hpez.Context(0)
+    yield ctx
+    ctx.close()
+
+
+def _gpu_roundtrip(ctx, x, eb, mode, cfg=None):
+    import torch
+    from paper_2311_12133_gb300 import hpez
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    buf, size = ctx.compress(xd, eb, mode, cfg)
+    stream = buf[:size].cpu().numpy().tobytes()
+    y = ctx.decompress(buf, size).cpu().numpy()
+    return stream, y
+
+
+def _pair_configs(nd, **kw):
+    from oracle import oracle as O
+    from paper_2311_12133_gb300 import hpez
+    return O.make_config(nd, **kw), hpez.make_config(nd, **kw)
+
+
+def _check(ctx, oracle, x, eb=1e-3, mode=1, **kw):
+    ocfg, gcfg = _pair_configs(x.ndim, **kw)
+    want, st, _, recon = oracle.compress(x, eb, mode, ocfg, want_recon=True)
+    got, y = _gpu_roundtrip(ctx, x, eb, mode, gcfg)
+    assert len(got) == len(want), (len(got), len(want))
+    if got != want:
+        a = np.frombuffer(got, np.uint8)
+        b = np.frombuffer(want, np.uint8)
+        first = int(np.nonzero(a != b)[0][0])
+        raise AssertionError(f"stream differs first at byte {first} of {len(want)}")
+    assert y.tobytes() == oracle.decompress(want).tobytes()
+    if not (mode == 1 and x.max() == x.min()):
+        assert y.tobytes() == recon.tobytes()
+        assert np.all(np.abs(y.astype(np.float64) - x) <= st.e)
+    return st
+
+
+def test_bumps_128_default(gpu, oracle):
+    """The plain workload: 128^3 Gaussian bumps, rel eb 1e-3, cubic
+    not-a-knot, fixed dimension order, no tuning."""
+    from paper_2311_12133_gb300 import fields
+    x = fields.bumps((128, 128, 128), seed=1)
+    st = _check(gpu, oracle, x, 1e-3, 1)
+    assert st.n_used > 2
+
+
+@pytest.mark.parametrize("interp", [0, 1, 2])
+@pytest.mark.parametrize("paradigm", [0, 1])
+@pytest.mark.parametrize("same", [0, 1])
+def test_interpolators_3d(gpu, oracle, interp, paradigm, same):
+    from paper_2311_12133_gb300 import fields
+    x = fields.grf((37, 50, 67), seed=interp * 4 + paradigm * 2 + same)
+    _check(gpu, oracle, x, 1e-3, 1, interp=interp, paradigm=paradigm,
+           same_level=same, anchor_stride=16)
+
+
+@pytest.mark.parametrize("shape", [(1,), (2,), (5,), (1000,), (129,), (7, 5),
+                                   (1, 300), (65, 129), (100, 3), (3, 4, 5),
+                                   (1, 1, 77), (33, 1, 20), (17, 19, 23)])
+def test_shapes_ragged(gpu, oracle, shape):
+    rng = np.random.default_rng(len(shape) * 100 + shape[-1])
+    x = rng.standard_normal(shape).cumsum(axis=-1).astype(np.float32)
+    if x.size > 1 and x.max() == x.min():
+        x.flat[0] += 1
+    for A in (2, 8, 64):
+        _check(gpu, oracle, x, 1e-2, 1, anchor_stride=A)
+        _check(gpu, oracle, x, 0.05, 0, anchor_stride=A, interp=2, same_level=1)
+
+
+@pytest.mark.parametrize("order", [(0, 1, 2), (2, 1, 0), (1, 2, 0), (2, 0, 1)])
+def test_dim_orders(gpu, oracle, order):
+    from paper_2311_12133_gb300 import fields
+    x = fields.bumps((40, 33, 50), seed=7)
+    _check(gpu, oracle, x, 1e-3, 1, order=order)
+    # per-level orders and interpolators
+    _check(gpu, oracle, x, 1e-4, 1, order=[order, (0, 1, 2), (1, 0, 2), order, order],
+           interp=[2, 1, 0, 1, 2], same_level=[1, 0, 0, 1, 1], paradigm=[0, 1, 0, 1, 0])
+
+
+@pytest.mark.parametrize("frozen", [0, 1, 2])
+def test_frozen_dimension(gpu, oracle, frozen):
+    from paper_2311_12133_gb300 import fields
+    x = fields.aniso((12, 80, 96), seed=frozen)
+    _check(gpu, oracle, x, 1e-3, 1, frozen_dim=frozen, paradigm=1,
+           md_inv_var=(1.0, 3.0, 0.25))
+    _check(gpu, oracle, x, 1e-3, 1, frozen_dim=frozen)
+
+
+def test_alpha_beta_level_bounds(gpu, oracle):
+    from paper_2311_12133_gb300 import fields
+    x = fields.grf((64, 64, 64), seed=3)
+    for a, b in ((1.5, 4.0), (2.0, 2.0), (1.25, 8.0)):
+        _check(gpu, oracle, x, 1e-3, 1, alpha=a, beta=b)
+
+
+def test_blockwise_map(gpu, oracle):
+    from paper_2311_12133_gb300 import fields
+    x = fields.grf((70, 64, 45), seed=5)
+    rng = np.random.default_rng(9)
+    nb = 3 * 2 * 2
+    bm = rng.choice(np.array([0, 1, 2, 5, 6], np.uint8), size=nb)
+    _check(gpu, oracle, x, 1e-3, 1, blockmap=bm)
+
+
+def test_2d_and_1d_workloads(gpu, oracle):
+    from paper_2311_12133_gb300 import fields
+    x = fields.climate2d((180, 360), seed=2)
+    _check(gpu, oracle, x, 1e-3, 1)
+    _check(gpu, oracle, x, 1e-4, 1, paradigm=1, same_level=1, interp=2)
+    y = fields.grf((5000,), seed=4)
+    _check(gpu, oracle, y, 1e-3, 1)
+
+
+def test_chunk_sizes_and_outliers(gpu, oracle):
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((33, 40, 41)).astype(np.float32)
+    for C in (256, 1024, 32768):
+        _check(gpu, oracle, x, 1e-3, 1, chunk_syms=C)
+    # white noise with a tiny bound: many outliers and a wide alphabet
+    st = _check(gpu, oracle, x, 1e-6, 1)
+    assert st.n_outliers > 0
+    # alphabet larger than the shared-memory codebook (global-memory path)
+    st = _check(gpu, oracle, x, 2e-5, 1)
+    assert st.n_used > 8192
+
+
+def test_degenerate_fields(gpu, oracle):
+    c = np.full((20, 30), 1.25, np.float32)
+    _check(gpu, oracle, c, 1e-3, 1)  # constant: header-only stream
+    _check(gpu, oracle, c, 1e-3, 0)  # absolute bound: a regular stream
+    one = np.array([3.5], np.float32)
+    _check(gpu, oracle, one, 0.1, 0)
+    lin = np.arange(4096, dtype=np.float32).reshape(16, 256)
+    st = _check(gpu, oracle, lin, 0.25, 0, anchor_stride=16)
+    assert st.n_used == 1  # every code is the zero-error code
+
+
+def test_error_codes(gpu):
+    import torch
+    from paper_2311_12133_gb300 import hpez
+    x = torch.zeros(1000, device="cuda")
+    x[5] = float("nan")
+    with pytest.raises(hpez.HpezError) as e:
+        gpu.compress(x, 1e-3, hpez.HPEZ_EB_REL)
+    assert e.value.code == -2
+    x = torch.randn(64, 64, device="cuda")
+    out = torch.empty(600, dtype=torch.uint8, device="cuda")
+    with pytest.raises(hpez.HpezError) as e:
+        hpez.hpez_compress(gpu.handle, x.data_ptr(), (64, 64), 1, 1e-3, None,
+                           out.data_ptr(), 600, 0)
+    assert e.value.code == -3
+    buf, size = gpu.compress(x, 1e-3)
+    bad = buf.clone()
+    bad[0] ^= 0xFF
+    with pytest.raises(hpez.HpezError):
+        gpu.decompress(bad, size, shape=(64, 64))
+    with pytest.raises(hpez.HpezError):
+        gpu.decompress(buf, 300, shape=(64, 64))
+
+
+def test_host_buffer_entry_points(gpu, oracle):
+    from paper_2311_12133_gb300 import fields, hpez
+    x = fields.bumps((30, 40, 50), seed=2)
+    out = np.zeros(hpez.hpez_compress_bound(x.shape), np.uint8)
+    size = hpez.hpez_compress_host(gpu.handle, x, 1, 1e-3, None, out)
+    want, _, _, recon = oracle.compress(x, 1e-3, 1, want_recon=True)
+    assert out[:size].tobytes() == want
+    y = np.zeros(x.size, np.float32)
+    hpez.hpez_decompress_host(gpu.handle, out, size, y)
+    assert y.tobytes() == recon.tobytes()
+
+
+def test_determinism_repeated(gpu):
+    import torch
+    from paper_2311_12133_gb300 import fields
+    x = torch.from_numpy(fields.lognormal((64, 64, 64), seed=1)).cuda()
+    ref = None
+    for _ in range(5):
+        buf, size = gpu.compress(x, 1e-4)
+        b = buf[:size].cpu().numpy().tobytes()
+        ref = ref or b
+        assert b == ref
