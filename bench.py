@@ -1,0 +1,400 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the HPEZ compress + decompress path on GB300.
+
+One step = compress then decompress one 512x512x512 float32 Gaussian random
+field with a k^-5/3 power spectrum (turbulence-like stand-in for the
+paper's JHTDB field, which is not available) at value-range relative error
+bound 1e-3, with the default predictor (cubic not-a-knot, 1D-style order
+0,1,2, anchor stride 32), through the C-ABI (libhpez.so).
+
+value     input GB/s of the round trip: sum over ranks of 4 N bytes per step
+          divided by the max-over-ranks time per step (CUDA events)
+e2e       the same metric through the host-buffer entry points, host<->device
+          copies inside the timed region
+roofline  the dominant phase's algorithmic bytes / its CUDA-event time,
+          against the measured HBM copy bandwidth
+cpu_baseline  the single-threaded CPU oracle on a slab of the same field
+
+``--impl reference`` times that CPU oracle instead (rank 0 only).
+Multi-GPU: one process per GPU (torchrun); every rank compresses its own
+field, no collective on the data path (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6800.0
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--shape", default="512,512,512")
+    ap.add_argument("--eb", type=float, default=1e-3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="run warm-up + timed steps only (for ncu captures)")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clk", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            if self.uuid and self.uuid not in f[0]:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown",
+                                "sw_thermal_slowdown", "sw_power_cap"), f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per phase (minimum traffic the step must move)
+# ---------------------------------------------------------------------------
+def grid_sizes(shape, A):
+    import math
+    out = []
+    S = 1
+    while S <= A:
+        out.append(math.prod(-(-n // S) for n in shape))
+        S *= 2
+    return out  # out[g]: points of the stride-2^g grid
+
+
+def phase_bytes(name: str, shape, A, comp_size: int) -> int:
+    import math
+    N = math.prod(shape)
+    gs = grid_sizes(shape, A)
+    if name == "range":
+        return 4 * N
+    if name.startswith("level"):  # compress level l
+        l = int(name[5:])
+        n_s, n_c = gs[l - 1], gs[l]
+        new = n_s - n_c
+        b = 4 * new + 4 * n_c + 2 * n_s + 2 * n_c  # x, coarse recon, codes out, coarse codes
+        if l > 1:
+            b += 4 * n_s  # reconstruction read again by the next level
+        return b
+    if name.startswith("dlevel"):
+        l = int(name[6:])
+        n_s, n_c = gs[l - 1], gs[l]
+        return 2 * (n_s - n_c) + 4 * n_c + 4 * n_s
+    if name in ("hist", "encode_len"):
+        return 2 * N
+    if name == "pack":
+        return 2 * N + comp_size
+    if name == "decode":
+        return comp_size + 2 * N
+    if name == "outliers" or name == "scatter":
+        return 0
+    return 0
+
+
+def src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2311_12133_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(phase: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+        if d.get("src_hash") != src_hash():
+            return None
+        return d.get("phases", {}).get(phase)
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (rank 0, N = 1)
+# ---------------------------------------------------------------------------
+def cpu_oracle_sample(x_slab, eb, rounds=1):
+    """Compress + decompress the slab with the CPU oracle; returns
+    (bytes processed, seconds)."""
+    from oracle import oracle as O
+    O.build()
+    t0 = time.perf_counter()
+    nbytes = 0
+    for _ in range(rounds):
+        s, _, _, _ = O.compress(x_slab, eb, O.EB_REL)
+        O.decompress(s)
+        nbytes += x_slab.nbytes
+    return nbytes, time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    from paper_2311_12133_gb300 import fields
+    shape = tuple(int(v) for v in args.shape.split(","))
+    slab = (16,) + shape[1:]
+    x = fields.grf(slab, seed=fields.seed_of("bench-ref", 0))
+    for _ in range(args.warmup):
+        cpu_oracle_sample(x, args.eb)
+    times = []
+    for _ in range(args.steps):
+        nb, t = cpu_oracle_sample(x, args.eb)
+        times.append(t)
+    ms = 1e3 * sum(times) / len(times)
+    value = x.nbytes / (ms / 1e3) / 1e9
+    line = {
+        "impl": "reference",
+        "metric": "compress+decompress input GB/s (rel eb 1e-3)",
+        "value": round(value, 6), "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"grf k^-5/3 float32 slab {'x'.join(map(str, slab))} of the "
+                               f"{'x'.join(map(str, shape))} workload, rel eb {args.eb}, "
+                               "compress+decompress by the single-threaded CPU oracle"},
+        "cpu_baseline": {"value": round(value, 6), "unit": "GB/s", "cores": 1,
+                         "kind": "oracle",
+                         "sample": f"{'x'.join(map(str, slab))} slab per step"},
+        "e2e": {"value": round(value, 6), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    from paper_2311_12133_gb300 import build as B
+    from paper_2311_12133_gb300 import fields, hpez
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    B.build()
+    shape = tuple(int(v) for v in args.shape.split(","))
+    N = int(np.prod(shape))
+    A = 32 if len(shape) == 3 else (64 if len(shape) == 2 else 128)
+    x = fields.grf_torch(shape, seed=fields.seed_of("bench", rank), device=f"cuda:{local}")
+    ctx = hpez.Context(local)
+    cap = hpez.hpez_compress_bound(shape)
+    cbuf = torch.empty(cap, dtype=torch.uint8, device=x.device)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+
+    def step():
+        size = hpez.hpez_compress(ctx.handle, x.data_ptr(), shape, hpez.HPEZ_EB_REL,
+                                  args.eb, None, cbuf.data_ptr(), cap, sptr)
+        hpez.hpez_decompress(ctx.handle, cbuf.data_ptr(), size, y.data_ptr(), N, sptr)
+        return size
+
+    for _ in range(max(3, args.warmup)):
+        size = step()
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    hpez.hpez_profile_enable(ctx.handle, True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
+    ev[0].record(stream)
+    for k in range(args.steps):
+        size = hpez.hpez_compress(ctx.handle, x.data_ptr(), shape, hpez.HPEZ_EB_REL,
+                                  args.eb, None, cbuf.data_ptr(), cap, sptr)
+        ev[2 * k + 1].record(stream)
+        hpez.hpez_decompress(ctx.handle, cbuf.data_ptr(), size, y.data_ptr(), N, sptr)
+        ev[2 * k + 2].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = ev[0].elapsed_time(ev[-1])
+    comp_ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps))
+    dec_ms = sum(ev[2 * k + 1].elapsed_time(ev[2 * k + 2]) for k in range(args.steps))
+    launches = hpez.hpez_launch_count(ctx.handle)
+    phases = {}
+    for ph in range(hpez.HPEZ_PROFILE_PHASES):
+        ms, cnt = hpez.hpez_profile_get(ctx.handle, ph)
+        if cnt:
+            phases[hpez.hpez_profile_phase_name(ph)] = (ms, cnt)
+    hpez.hpez_profile_enable(ctx.handle, False)
+    if args.profile_only:
+        return
+
+    t = torch.tensor([total_ms, comp_ms, dec_ms], dtype=torch.float64, device=x.device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms, comp_ms, dec_ms = [float(v) for v in t.tolist()]
+    ms_per_step = total_ms / args.steps
+    value = world * 4 * N / (ms_per_step / 1e3) / 1e9
+
+    # correctness of what was timed: bound held at every point
+    e_abs = hpez.hpez_inspect(cbuf[:512].cpu().numpy().tobytes())[2]
+    err = (y.double() - x.double()).abs().max().item()
+    assert err <= e_abs, f"error bound violated: {err} > {e_abs}"
+
+    peak, peak_kind = measured_peaks()
+    dom = max(phases.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_cnt) = dom
+    dom_bytes = phase_bytes(dom_name, shape, A, size)
+    achieved = dom_bytes / (dom_ms / dom_cnt / 1e3) / 1e9 if dom_bytes else None
+    roofline = {"bound": "hbm", "phase": dom_name,
+                "achieved": round(achieved, 1) if achieved else None,
+                "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": round(achieved / peak, 4) if achieved else None,
+                "traffic": ncu_traffic(dom_name),
+                "algorithmic_bytes": dom_bytes,
+                "launch_ms": round(dom_ms / dom_cnt, 4)}
+    phase_report = {k: {"ms": round(v[0] / v[1], 4), "n": v[1],
+                        "GBps": round(phase_bytes(k, shape, A, size) / (v[0] / v[1] / 1e3) / 1e9, 1)
+                        if phase_bytes(k, shape, A, size) else None}
+                    for k, v in sorted(phases.items(), key=lambda kv: -kv[1][0])}
+
+    # end to end through the host-buffer entry points
+    e2e = None
+    if not args.no_e2e:
+        hx = x.cpu().pin_memory().numpy()
+        hout = torch.empty(cap, dtype=torch.uint8).pin_memory().numpy()
+        hy = torch.empty(N, dtype=torch.float32).pin_memory().numpy()
+        for _ in range(2):
+            sz = hpez.hpez_compress_host(ctx.handle, hx, hpez.HPEZ_EB_REL, args.eb, None, hout, sptr)
+            hpez.hpez_decompress_host(ctx.handle, hout, sz, hy, sptr)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sz = hpez.hpez_compress_host(ctx.handle, hx, hpez.HPEZ_EB_REL, args.eb, None, hout, sptr)
+            hpez.hpez_decompress_host(ctx.handle, hout, sz, hy, sptr)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        te = torch.tensor([e2e_s], dtype=torch.float64, device=x.device)
+        if dist:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_s = float(te.item())
+        e2e = {"value": round(world * 4 * N / e2e_s / 1e9, 3), "unit": "GB/s",
+               "h2d_bytes_per_step": 4 * N + sz, "d2h_bytes_per_step": sz + 4 * N}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        slab = x[:64].cpu().numpy()
+        nb, secs = cpu_oracle_sample(slab, args.eb, rounds=2)
+        cpu = {"value": round(nb / secs / 1e9, 6), "unit": "GB/s", "cores": 1,
+               "kind": "oracle",
+               "sample": f"2 compress+decompress round trips of the first 64 planes "
+                         f"({'x'.join(map(str, slab.shape))}) of the same field, {secs:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": "compress+decompress input GB/s (rel eb 1e-3)",
+            "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"grf k^-5/3 float32 {'x'.join(map(str, shape))} per GPU, "
+                                   f"rel eb {args.eb}, compress+decompress, default predictor "
+                                   "(cubic not-a-knot, 1D-style order 0,1,2, A=32)",
+                       "global_batch": world, "parallelism": f"replicas{world}",
+                       "l2": f"input {4 * N / 1e6:.0f} MB > L2 {L2_BYTES / 1e6:.0f} MB, no flush"},
+            "compress_gbps": round(world * 4 * N / (comp_ms / args.steps / 1e3) / 1e9, 3),
+            "decompress_gbps": round(world * 4 * N / (dec_ms / args.steps / 1e3) / 1e9, 3),
+            "compression_ratio": round(4 * N / size, 3),
+            "max_abs_err": err, "abs_eb": e_abs,
+            "roofline": roofline, "phases": phase_report,
+            "gpu_launches": int(launches),
+            "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -68,7 +68,7 @@ extern "C" {
 typedef struct {
   int32_t anchor_stride; /* A, power of two in [2, 32768] (Sec. 5.1) */
   int32_t frozen_dim;    /* -1, or a dim never interpolated (Sec. 6.3) */
-  int32_t chunk_syms;    /* Huffman chunk, power of two in [256, 32768] */
+  int32_t chunk_syms;    /* Huffman chunk of 32 lanes, 2^k in [256, 32768] */
   int32_t blockwise;     /* 1: per-block interpolator map (Sec. 6.6) */
   int32_t block_size;    /* block side of the map (Sec. 6.6 default 32) */
   int32_t reserved;
@@ -93,7 +93,7 @@ HPEZ_API int hpez_destroy(hpez_ctx* ctx);
 
 /* Default theta for ndim: A = 128/64/32 for 1D/2D/3D, not-a-knot cubic
  * (Eq. 4) at every level, 1D-style order 0..ndim-1, alpha = beta = 1,
- * chunk 4096, no freezing, no block map. */
+ * chunk 16384, no freezing, no block map. */
 HPEZ_API int hpez_default_config(int ndim, hpez_config* out);
 
 /* Upper bound of the compressed size in bytes for a field of these dims. */
@@ -138,6 +138,37 @@ HPEZ_API int hpez_inspect(const void* h_header, uint64_t n, int* ndim, uint64_t*
 
 /* Static text for an error code. */
 HPEZ_API const char* hpez_strerror(int code);
+
+/* ---- measurement hooks (not part of the paper's method) ----
+ * Phase timing: with profiling enabled, compress/decompress record a CUDA
+ * event pair on the call's stream around each phase and accumulate the
+ * elapsed times once the call has synchronized.  Phase ids: */
+#define HPEZ_PH_RANGE 0     /* value range (relative bound) */
+#define HPEZ_PH_ANCHORS 1   /* anchor gather */
+#define HPEZ_PH_HIST 2      /* code histogram + outlier counts */
+#define HPEZ_PH_CODEBOOK 3  /* canonical Huffman codebook */
+#define HPEZ_PH_ENCODE 4    /* chunk lengths + offsets */
+#define HPEZ_PH_PACK 5      /* bit packing */
+#define HPEZ_PH_OUTLIERS 6  /* outlier gather */
+#define HPEZ_PH_FINALIZE 7  /* header + static sections */
+#define HPEZ_PH_DEC_PREP 8  /* chunk offsets + decode tables */
+#define HPEZ_PH_DECODE 9    /* Huffman decode */
+#define HPEZ_PH_SCATTER 10  /* outlier scatter */
+#define HPEZ_PH_LEVEL 11    /* + (l-1): compress level l, l = 1..16 */
+#define HPEZ_PH_DLEVEL 27   /* + (l-1): decompress level l */
+#define HPEZ_PROFILE_PHASES 43
+
+/* Enable (1) or disable (0) phase timing; resets the accumulators and the
+ * launch counter.  Errors: INVALID_ARG. */
+HPEZ_API int hpez_profile_enable(hpez_ctx* ctx, int enable);
+/* Accumulated milliseconds and number of timed occurrences of a phase. */
+HPEZ_API int hpez_profile_get(hpez_ctx* ctx, int phase, double* total_ms,
+                              uint64_t* count);
+/* Static name of a phase id ("" if out of range). */
+HPEZ_API const char* hpez_profile_phase_name(int phase);
+/* Number of kernels this context launched since creation or the last
+ * hpez_profile_enable call. */
+HPEZ_API int hpez_launch_count(hpez_ctx* ctx, uint64_t* launches);
 
 #ifdef __cplusplus
 }

@@ -180,7 +180,7 @@ void ora_default_config(int ndim, ora_config* c) {
   memset(c, 0, sizeof(*c));
   c->anchor_stride = ndim == 1 ? 128 : (ndim == 2 ? 64 : 32);
   c->frozen_dim = -1;
-  c->chunk_syms = 4096;
+  c->chunk_syms = 16384;
   c->blockwise = 0;
   c->block_size = 32;
   c->alpha = 1.0;
@@ -684,10 +684,10 @@ uint64_t ora_compress_bound(int ndim, const uint64_t* dims) {
   uint64_t N = 1;
   for (int d = 0; d < ndim; ++d) N *= dims[d];
   uint64_t nch = (N + 255) / 256;
-  /* header + anchors/outliers (<= N floats each) + block map + chunk
-   * words + table + bitstream (<= 17 bits per symbol + one pad word per
+  /* header + anchors/outliers (<= N floats each) + block map + lane bit
+   * counts + table + bitstream (<= 17 bits per symbol + one pad word per
    * chunk) */
-  return 512 + 16 * 8 + 4 * N + 4 * N + N + 4 * nch + 3 * 65536 + 4 +
+  return 512 + 16 * 8 + 4 * N + 4 * N + N + 64 * nch + 3 * 65536 + 4 +
          (17 * N) / 8 + 4 * nch + 64;
 }
 
@@ -823,42 +823,50 @@ int ora_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode,
   uint32_t nused = 0;
   for (int i = 0; i < 65536; ++i)
     if (hist[i]) nused++;
+  /* chunked bit layout: a chunk of C symbols is coded as 32 lanes, lane l
+   * holding the chunk's symbols l, l+32, l+64, ... in order; the lanes'
+   * bits follow one another (lane 0 first), MSB first in 32-bit words;
+   * each chunk starts on a word; the bit count of every lane is stored */
   const uint64_t C = (uint64_t)c->chunk_syms;
   const uint64_t nch = (N + C - 1) / C;
-  uint32_t* chw = (uint32_t*)calloc(nch, sizeof(uint32_t));
+  uint16_t* lanebits = (uint16_t*)calloc(nch * 32, sizeof(uint16_t));
   uint64_t sumlen = 0;
   for (uint64_t i = 0; i < N; ++i) sumlen += lens[w.codes[i]];
   uint64_t maxwords = sumlen / 32 + nch + 1;
   uint32_t* bits = (uint32_t*)calloc(maxwords, sizeof(uint32_t));
   uint64_t wpos = 0;
   for (uint64_t ch = 0; ch < nch && !rc; ++ch) {
-    uint64_t w0 = wpos;
     uint32_t cur = 0;
     int nb = 0;
-    uint64_t e_ = (ch + 1) * C < N ? (ch + 1) * C : N;
-    for (uint64_t i = ch * C; i < e_; ++i) {
-      uint16_t sy = w.codes[i];
-      int L_ = lens[sy];
-      uint64_t cw = code64[sy];
-      for (int b = L_ - 1; b >= 0; --b) { /* MSB first */
-        cur = (cur << 1) | (uint32_t)((cw >> b) & 1u);
-        nb++;
-        if (nb == 32) {
-          bits[wpos++] = cur;
-          cur = 0;
-          nb = 0;
+    const uint64_t beg = ch * C;
+    const uint64_t nc = (beg + C < N ? beg + C : N) - beg;
+    for (uint64_t lane = 0; lane < 32; ++lane) {
+      uint64_t lb = 0;
+      for (uint64_t j = lane; j < nc; j += 32) {
+        uint16_t sy = w.codes[beg + j];
+        int L_ = lens[sy];
+        uint64_t cw = code64[sy];
+        lb += (uint64_t)L_;
+        for (int b = L_ - 1; b >= 0; --b) { /* MSB first */
+          cur = (cur << 1) | (uint32_t)((cw >> b) & 1u);
+          nb++;
+          if (nb == 32) {
+            bits[wpos++] = cur;
+            cur = 0;
+            nb = 0;
+          }
         }
       }
+      lanebits[ch * 32 + lane] = (uint16_t)lb;
     }
     if (nb) bits[wpos++] = cur << (32 - nb);
-    chw[ch] = (uint32_t)(wpos - w0);
   }
 
   /* container */
   uint64_t off_anchors = ORA_HEADER_BYTES;
   uint64_t off_blockmap = align16(off_anchors + 4 * na);
   uint64_t off_chunkw = align16(off_blockmap + nblocks);
-  uint64_t off_table = align16(off_chunkw + 4 * nch);
+  uint64_t off_table = align16(off_chunkw + 64 * nch);
   uint64_t off_outl = align16(off_table + 3 * (uint64_t)nused);
   uint64_t off_bits = align16(off_outl + 4 * nout);
   uint64_t total = off_bits + 4 * wpos;
@@ -908,7 +916,7 @@ int ora_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode,
     put_u64(out, H_NBLOCKS, nblocks);
     for (uint64_t i = 0; i < na; ++i) put_f32(out, off_anchors + 4 * i, anchors[i]);
     for (uint64_t i = 0; i < nblocks; ++i) put_u8(out, off_blockmap + i, c->blockmap[i]);
-    for (uint64_t i = 0; i < nch; ++i) put_u32(out, off_chunkw + 4 * i, chw[i]);
+    for (uint64_t i = 0; i < 32 * nch; ++i) put_u16(out, off_chunkw + 2 * i, lanebits[i]);
     {
       uint64_t k = 0;
       for (int sy = 0; sy < 65536; ++sy)
@@ -940,7 +948,7 @@ int ora_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode,
   if (codes_out) memcpy(codes_out, w.codes, sizeof(uint16_t) * N);
   if (recon_out) memcpy(recon_out, w.recon, sizeof(float) * N);
   free(w.recon); free(w.codes); free(w.stamp); free(anchors); free(outl);
-  free(hist); free(lens); free(code64); free(chw); free(bits);
+  free(hist); free(lens); free(code64); free(lanebits); free(bits);
   return rc;
 }
 
@@ -1035,7 +1043,7 @@ int ora_decompress(const uint8_t* in, uint64_t size, float* out,
   uint64_t oa = get_u64(in, H_OFF_ANCHORS), ocw = get_u64(in, H_OFF_CHUNKW),
            ot = get_u64(in, H_OFF_TABLE), oo = get_u64(in, H_OFF_OUTLIERS),
            obits = get_u64(in, H_OFF_BITS);
-  if (oa + 4 * na > size || ocw + 4 * nch > size ||
+  if (oa + 4 * na > size || ocw + 64 * nch > size ||
       ot + 3 * (uint64_t)nused > size || oo + 4 * nout > size ||
       obits + 4 * twords > size)
     return ORA_ERR_CORRUPT;
@@ -1079,37 +1087,46 @@ int ora_decompress(const uint8_t* in, uint64_t size, float* out,
   rc = ORA_OK;
   uint64_t wbase = 0;
   for (uint64_t ch = 0; ch < nch && !rc; ++ch) {
-    uint64_t nw = get_u32(in, ocw + 4 * ch);
+    uint64_t lb[32], sum = 0;
+    for (int l = 0; l < 32; ++l) {
+      lb[l] = get_u16(in, ocw + 64 * ch + 2 * (uint64_t)l);
+      sum += lb[l];
+    }
+    const uint64_t nw = (sum + 31) / 32;
     if (wbase + nw > twords) {
       rc = ORA_ERR_CORRUPT;
       break;
     }
-    uint64_t e_ = (ch + 1) * C < N ? (ch + 1) * C : N;
-    uint64_t bitpos = 0, nbits = nw * 32;
-    for (uint64_t i = ch * C; i < e_; ++i) {
-      if (nused == 1) {
-        codes[i] = syms[0];
-        continue;
-      }
-      uint64_t code = 0;
-      int len = 0, found = 0;
-      while (len < maxlen) {
-        if (bitpos >= nbits) break;
-        uint32_t word = get_u32(in, obits + 4 * (wbase + bitpos / 32));
-        uint32_t bit = (word >> (31 - (bitpos % 32))) & 1u;
-        bitpos++;
-        code = (code << 1) | bit;
-        len++;
-        if (cnt[len] && code >= first[len] && code - first[len] < cnt[len]) {
-          codes[i] = sorted[offs[len] + (code - first[len])];
-          found = 1;
+    const uint64_t beg = ch * C;
+    const uint64_t nc = (beg + C < N ? beg + C : N) - beg;
+    uint64_t bitpos = 0;
+    for (int lane = 0; lane < 32 && !rc; ++lane) {
+      const uint64_t lane_end = bitpos + lb[lane];
+      for (uint64_t j = (uint64_t)lane; j < nc; j += 32) {
+        if (nused == 1) {
+          codes[beg + j] = syms[0];
+          continue;
+        }
+        uint64_t code = 0;
+        int len = 0, found = 0;
+        while (len < maxlen && bitpos < lane_end) {
+          uint32_t word = get_u32(in, obits + 4 * (wbase + bitpos / 32));
+          uint32_t bit = (word >> (31 - (bitpos % 32))) & 1u;
+          bitpos++;
+          code = (code << 1) | bit;
+          len++;
+          if (cnt[len] && code >= first[len] && code - first[len] < cnt[len]) {
+            codes[beg + j] = sorted[offs[len] + (code - first[len])];
+            found = 1;
+            break;
+          }
+        }
+        if (!found) {
+          rc = ORA_ERR_CORRUPT;
           break;
         }
       }
-      if (!found) {
-        rc = ORA_ERR_CORRUPT;
-        break;
-      }
+      if (bitpos != lane_end) rc = ORA_ERR_CORRUPT;
     }
     wbase += nw;
   }

@@ -142,7 +142,7 @@ def default_config(ndim: int) -> Config:
 
 
 def make_config(ndim: int, *, anchor_stride=None, frozen_dim=-1,
-                chunk_syms=4096, alpha=1.0, beta=1.0, md_inv_var=(1, 1, 1),
+                chunk_syms=16384, alpha=1.0, beta=1.0, md_inv_var=(1, 1, 1),
                 interp=CUBIC_NAK, paradigm=P1D, same_level=0, order=None,
                 blockmap=None, block_size=32) -> Config:
     """Config with one setting for every level unless per-level lists are
@@ -158,16 +158,15 @@ def make_config(ndim: int, *, anchor_stride=None, frozen_dim=-1,
     dims = [d for d in range(ndim) if d != frozen_dim]
 
     def per(v, l):
-        return v[l] if isinstance(v, (list, tuple)) and not (
-            len(v) and isinstance(v[0], int) and v is order) else v
+        # per-level lists shorter than the level count repeat their last entry
+        if isinstance(v, (list, tuple)):
+            return v[l] if l < len(v) else v[-1]
+        return v
 
     for l in range(MAX_LEVELS):
-        c.interp[l] = interp[l] if isinstance(interp, (list, tuple)) else interp
-        c.paradigm[l] = (paradigm[l] if isinstance(paradigm, (list, tuple))
-                         else paradigm)
-        c.same_level[l] = (same_level[l] if isinstance(same_level,
-                                                       (list, tuple))
-                           else same_level)
+        c.interp[l] = per(interp, l)
+        c.paradigm[l] = per(paradigm, l)
+        c.same_level[l] = per(same_level, l)
         if order is None:
             o = dims
         elif isinstance(order[0], (list, tuple)):

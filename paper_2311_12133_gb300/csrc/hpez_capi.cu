@@ -13,7 +13,65 @@
 
 using namespace hpez;
 
+// Opt-in phase timer: CUDA events recorded on the call's stream around
+// each phase, read after the call's final synchronization.
+struct PhaseProfiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+  double total_ms[HPEZ_PROFILE_PHASES] = {};
+  uint64_t count[HPEZ_PROFILE_PHASES] = {};
+  cudaEvent_t take() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  void begin(int ph, cudaStream_t s) {
+    if (!on) return;
+    cudaEvent_t e = take();
+    cudaEventRecord(e, s);
+    marks.push_back({ph, {e, nullptr}});
+  }
+  void end(cudaStream_t s) {
+    if (!on || marks.empty()) return;
+    cudaEvent_t e = take();
+    cudaEventRecord(e, s);
+    marks.back().second.second = e;
+  }
+  // after the stream has been synchronized
+  void collect() {
+    for (auto& m : marks) {
+      float ms = 0.f;
+      if (m.second.second &&
+          cudaEventElapsedTime(&ms, m.second.first, m.second.second) == cudaSuccess) {
+        total_ms[m.first] += ms;
+        count[m.first] += 1;
+      }
+    }
+    marks.clear();
+    used = 0;
+    cudaGetLastError();
+  }
+  void reset() {
+    marks.clear();
+    used = 0;
+    for (int i = 0; i < HPEZ_PROFILE_PHASES; ++i) {
+      total_ms[i] = 0;
+      count[i] = 0;
+    }
+  }
+  ~PhaseProfiler() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
 struct hpez_ctx {
+  PhaseProfiler prof;
+  uint64_t launches = 0;
   int device = 0;
   int num_sms = 152;
   char* scratch = nullptr;
@@ -324,7 +382,7 @@ void default_config(int ndim, hpez_config* c) {
   std::memset(c, 0, sizeof(*c));
   c->anchor_stride = ndim == 1 ? 128 : (ndim == 2 ? 64 : 32);
   c->frozen_dim = -1;
-  c->chunk_syms = 4096;
+  c->chunk_syms = 16384;
   c->blockwise = 0;
   c->block_size = 32;
   c->alpha = 1.0;
@@ -401,6 +459,7 @@ struct CompressBufs {
   unsigned long long* zoff;
   uint32_t* chw;
   unsigned long long* woff;
+  uint16_t* lbits;
   uint8_t* bmap;
 };
 
@@ -424,6 +483,42 @@ const char* hpez_strerror(int code) {
     case HPEZ_ERR_TIMEOUT: return "bounded device wait timed out";
   }
   return "unknown error";
+}
+
+int hpez_profile_enable(hpez_ctx* ctx, int enable) {
+  if (!ctx) return HPEZ_ERR_INVALID_ARG;
+  ctx->prof.reset();
+  ctx->prof.on = enable != 0;
+  ctx->launches = 0;
+  return HPEZ_OK;
+}
+
+int hpez_profile_get(hpez_ctx* ctx, int phase, double* total_ms,
+                     uint64_t* count) {
+  if (!ctx || phase < 0 || phase >= HPEZ_PROFILE_PHASES) return HPEZ_ERR_INVALID_ARG;
+  if (total_ms) *total_ms = ctx->prof.total_ms[phase];
+  if (count) *count = ctx->prof.count[phase];
+  return HPEZ_OK;
+}
+
+int hpez_launch_count(hpez_ctx* ctx, uint64_t* launches) {
+  if (!ctx || !launches) return HPEZ_ERR_INVALID_ARG;
+  *launches = ctx->launches;
+  return HPEZ_OK;
+}
+
+const char* hpez_profile_phase_name(int phase) {
+  static const char* fixed[] = {"range", "anchors", "hist", "codebook",
+                                "encode_len", "pack", "outliers", "finalize",
+                                "dec_prep", "decode", "scatter"};
+  static char names[HPEZ_PROFILE_PHASES][24];
+  if (phase < 0 || phase >= HPEZ_PROFILE_PHASES) return "";
+  if (phase < HPEZ_PH_LEVEL) return fixed[phase];
+  if (phase < HPEZ_PH_DLEVEL)
+    std::snprintf(names[phase], 24, "level%d", phase - HPEZ_PH_LEVEL + 1);
+  else
+    std::snprintf(names[phase], 24, "dlevel%d", phase - HPEZ_PH_DLEVEL + 1);
+  return names[phase];
 }
 
 int hpez_default_config(int ndim, hpez_config* out) {
@@ -475,7 +570,7 @@ int hpez_compress_bound(int ndim, const uint64_t* dims, uint64_t* out_bytes) {
     N *= dims[d];
   }
   const uint64_t nch = (N + 255) / 256;
-  *out_bytes = 512 + 16 * 8 + 4 * N + 4 * N + N + 4 * nch + 3 * 65536 + 4 +
+  *out_bytes = 512 + 16 * 8 + 4 * N + 4 * N + N + 64 * nch + 3 * 65536 + 4 +
                (17 * N) / 8 + 4 * nch + 64;
   return HPEZ_OK;
 }
@@ -525,6 +620,7 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   const size_t o_zoff = ar.take<unsigned long long>(p.nch);
   const size_t o_chw = ar.take<uint32_t>(p.nch);
   const size_t o_woff = ar.take<unsigned long long>(p.nch);
+  const size_t o_lbits = ar.take<uint16_t>((size_t)p.nch * 32);
   const size_t o_bmap = ar.take<uint8_t>(p.nblocks + 1);
   rc = ensure_scratch(ctx, ar.off);
   if (rc) return rc;
@@ -547,6 +643,7 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   b.zoff = reinterpret_cast<unsigned long long*>(S + o_zoff);
   b.chw = reinterpret_cast<uint32_t*>(S + o_chw);
   b.woff = reinterpret_cast<unsigned long long*>(S + o_woff);
+  b.lbits = reinterpret_cast<uint16_t*>(S + o_lbits);
   b.bmap = reinterpret_cast<uint8_t*>(S + o_bmap);
 
   // stream layout (static part)
@@ -554,18 +651,30 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   const uint64_t off_anchors = kHeaderBytes;
   const uint64_t off_bmap = a16(off_anchors + 4 * na);
   const uint64_t off_chw = a16(off_bmap + p.nblocks);
-  const uint64_t off_table = a16(off_chw + 4ull * p.nch);
+  const uint64_t off_table = a16(off_chw + 64ull * p.nch);
   uint8_t hdr[kHeaderBytes], hdrc[kHeaderBytes];
   header_templates(p, cfg, eb_mode, eb, off_anchors, off_bmap, off_chw, hdr, hdrc);
 
   // ---- launch sequence ----
+  PhaseProfiler& pf = ctx->prof;
+  uint64_t& nl = ctx->launches;
   launch_init_ctl(b.ctl, s);
-  if (eb_mode == HPEZ_EB_REL) launch_range(d_in, p.N, b.ctl, ctx->num_sms, s);
+  ++nl;
+  if (eb_mode == HPEZ_EB_REL) {
+    pf.begin(HPEZ_PH_RANGE, s);
+    launch_range(d_in, p.N, b.ctl, ctx->num_sms, s);
+    pf.end(s);
+    ++nl;
+  }
   launch_params(b.ctl, eb_mode, eb, cfg.alpha, cfg.beta, p.L, d_in, s);
+  ++nl;
   if (cfg.blockwise)
     cudaMemcpyAsync(b.bmap, cfg.h_blockmap, p.nblocks, cudaMemcpyHostToDevice, s);
+  pf.begin(HPEZ_PH_ANCHORS, s);
   launch_anchor_gather(d_in, p.grid[p.L], p.gsize[p.L], b.R[p.L], b.Cg[p.L],
                        b.ctl, s);
+  pf.end(s);
+  ++nl;
   SweepBufs sb;
   std::memset(&sb, 0, sizeof(sb));
   sb.x = d_in;
@@ -575,32 +684,51 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   sb.ctl = b.ctl;
   for (int l = p.L; l >= 1; --l) {
     const int g = l - 1;
+    pf.begin(HPEZ_PH_LEVEL + g, s);
     launch_upsample(p.grid[l], p.gsize[l], p.grid[g], b.R[l], b.Cg[l], b.R[g],
                     b.Cg[g], b.ctl, s);
+    ++nl;
     sb.R = b.R[g];
     sb.C = b.Cg[g];
     sb.kind = cfg.interp[l - 1];
     sb.same = cfg.same_level[l - 1];
-    for (const Launch& L : level_schedule(p, cfg, l))
+    for (const Launch& L : level_schedule(p, cfg, l)) {
       launch_pass(false, p.grid[g], L.pb, sb, ctx->num_sms, s);
+      nl += L.pb.total ? 1 : 0;
+    }
+    pf.end(s);
   }
   uint16_t* codes = b.Cg[0];
+  pf.begin(HPEZ_PH_HIST, s);
   cudaMemsetAsync(b.hist, 0, 65536 * sizeof(uint32_t), s);
   launch_hist(codes, p.N, p.C, p.nch, b.hist, b.zc, b.ctl, ctx->num_sms, s);
   launch_scan(b.zc, b.zoff, p.nch, &b.ctl->n_out, b.ctl, s);
+  pf.end(s);
+  pf.begin(HPEZ_PH_CODEBOOK, s);
   launch_codebook(b.hist, b.enc, b.tsyms, b.tlens, b.gkeys, b.giw, b.gpar,
                   b.lens_by_sym, b.ctl, s);
-  launch_enc_len(codes, p.N, p.C, p.nch, b.enc, b.chw, b.ctl, ctx->num_sms, s);
+  pf.end(s);
+  pf.begin(HPEZ_PH_ENCODE, s);
+  launch_enc_len(codes, p.N, p.C, p.nch, b.enc, b.lbits, b.chw, b.ctl,
+                 ctx->num_sms, s);
   launch_scan(b.chw, b.woff, p.nch, &b.ctl->total_words, b.ctl, s);
   launch_layout(b.ctl, off_table, out_cap, s);
+  pf.end(s);
   uint8_t* out = static_cast<uint8_t*>(d_out);
-  launch_pack(codes, p.N, p.C, p.nch, b.enc, b.chw, b.woff, out, b.ctl,
-              ctx->num_sms, s);
+  pf.begin(HPEZ_PH_PACK, s);
+  launch_pack(codes, p.N, p.C, p.nch, b.enc, b.lbits, b.chw, b.woff, out,
+              b.ctl, ctx->num_sms, s);
+  pf.end(s);
+  pf.begin(HPEZ_PH_OUTLIERS, s);
   launch_outliers(true, codes, p.N, p.C, p.nch, b.zc, b.zoff, d_in, nullptr,
                   out, ~0ull, b.ctl, ctx->num_sms, s);
+  pf.end(s);
+  pf.begin(HPEZ_PH_FINALIZE, s);
   launch_finalize(hdr, hdrc, out, b.R[p.L], (uint32_t)na, off_anchors, b.bmap,
-                  p.nblocks, off_bmap, b.chw, p.nch, off_chw, b.tsyms, b.tlens,
+                  p.nblocks, off_bmap, b.lbits, p.nch, off_chw, b.tsyms, b.tlens,
                   b.ctl, ctx->num_sms, s);
+  pf.end(s);
+  nl += 10;
   rc = cuda_check(cudaGetLastError());
   if (rc) return rc;
   rc = cuda_check(cudaMemcpyAsync(ctx->h_ctl, b.ctl, sizeof(Ctl),
@@ -608,6 +736,7 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   if (rc) return rc;
   rc = cuda_check(cudaStreamSynchronize(s));
   if (rc) return rc;
+  ctx->prof.collect();
   if (ctx->h_ctl->status) return map_status(ctx->h_ctl->status);
   *h_out_size = ctx->h_ctl->total_size;
   return HPEZ_OK;
@@ -696,7 +825,7 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   if (na != n_anchors(p) || nch != p.nch || nused == 0 || nused > 65536 ||
       nout > N || (cfg.blockwise && rd64(h, H_NBLOCKS) != p.nblocks))
     return HPEZ_ERR_CORRUPT_STREAM;
-  if (oa + 4 * na > in_size || ocw + 4 * nch > in_size ||
+  if (oa + 4 * na > in_size || ocw + 64 * nch > in_size ||
       ot + 3ull * nused > in_size || oo + 4 * nout > in_size ||
       ob + 4 * twords > in_size || (cfg.blockwise && obm + p.nblocks > in_size) ||
       (oa & 15) || (ocw & 15) || (oo & 15) || (ob & 15))
@@ -725,6 +854,7 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   const size_t o_zc = ar.take<uint32_t>(p.nch);
   const size_t o_zoff = ar.take<unsigned long long>(p.nch);
   const size_t o_woff = ar.take<unsigned long long>(p.nch);
+  const size_t o_dchw = ar.take<uint32_t>(p.nch);
   const size_t o_tot = ar.take<unsigned long long>(2);
   rc = ensure_scratch(ctx, ar.off);
   if (rc) return rc;
@@ -741,21 +871,33 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   unsigned long long* zoff = reinterpret_cast<unsigned long long*>(S + o_zoff);
   unsigned long long* woff = reinterpret_cast<unsigned long long*>(S + o_woff);
   unsigned long long* tot = reinterpret_cast<unsigned long long*>(S + o_tot);
+  uint32_t* dchw = reinterpret_cast<uint32_t*>(S + o_dchw);
   float* R[kMaxLevels + 1];
   for (int g = 1; g < p.L; ++g) R[g] = reinterpret_cast<float*>(S + o_R[g]);
   R[0] = d_out;
   R[p.L] = const_cast<float*>(reinterpret_cast<const float*>(in + oa));
 
+  PhaseProfiler& pf = ctx->prof;
+  uint64_t& nl = ctx->launches;
   launch_init_ctl(ctl, s);
   launch_params(ctl, HPEZ_EB_ABS, (double)e, cfg.alpha, cfg.beta, p.L, d_out, s);
-  const uint32_t* chw_stream = reinterpret_cast<const uint32_t*>(in + ocw);
-  launch_scan(chw_stream, woff, p.nch, &tot[0], ctl, s);
+  const uint8_t* lbits_stream = in + ocw;
+  pf.begin(HPEZ_PH_DEC_PREP, s);
+  launch_chunk_words(lbits_stream, p.nch, dchw, ctx->num_sms, s);
+  launch_scan(dchw, woff, p.nch, &tot[0], ctl, s);
   launch_dec_tables(in, nused, ot, lut, cnt, first, offs, sorted, gkeys, ctl, s);
-  launch_decode(in, ob, twords, chw_stream, woff, p.N, p.C, p.nch, nused,
-                single_sym, lut, cnt, first, offs, sorted, codes, zc, ctl, s);
+  pf.end(s);
+  pf.begin(HPEZ_PH_DECODE, s);
+  launch_decode(in, ob, twords, lbits_stream, woff, p.N, p.C, p.nch, nused,
+                single_sym, lut, cnt, first, offs, sorted, codes, zc, ctl,
+                ctx->num_sms, s);
+  pf.end(s);
+  pf.begin(HPEZ_PH_SCATTER, s);
   launch_scan(zc, zoff, p.nch, &tot[1], ctl, s);
   launch_outliers(false, codes, p.N, p.C, p.nch, zc, zoff, nullptr, d_out,
                   const_cast<uint8_t*>(in) + oo, nout, ctl, ctx->num_sms, s);
+  pf.end(s);
+  nl += 8;
   SweepBufs sb;
   std::memset(&sb, 0, sizeof(sb));
   sb.codes_full = codes;
@@ -766,13 +908,18 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   sb.ctl = ctl;
   for (int l = p.L; l >= 1; --l) {
     const int g = l - 1;
+    pf.begin(HPEZ_PH_DLEVEL + g, s);
     launch_upsample(p.grid[l], p.gsize[l], p.grid[g], R[l], nullptr, R[g],
                     nullptr, ctl, s);
+    ++nl;
     sb.R = R[g];
     sb.kind = cfg.interp[l - 1];
     sb.same = cfg.same_level[l - 1];
-    for (const Launch& L : level_schedule(p, cfg, l))
+    for (const Launch& L : level_schedule(p, cfg, l)) {
       launch_pass(true, p.grid[g], L.pb, sb, ctx->num_sms, s);
+      nl += L.pb.total ? 1 : 0;
+    }
+    pf.end(s);
   }
   rc = cuda_check(cudaGetLastError());
   if (rc) return rc;
@@ -785,6 +932,7 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   if (rc) return rc;
   rc = cuda_check(cudaStreamSynchronize(s));
   if (rc) return rc;
+  ctx->prof.collect();
   if (ctx->h_ctl->status) return map_status(ctx->h_ctl->status);
   if (h_tot[0] != twords || h_tot[1] != nout) return HPEZ_ERR_CORRUPT_STREAM;
   return HPEZ_OK;

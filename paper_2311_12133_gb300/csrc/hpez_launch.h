@@ -34,12 +34,15 @@ void launch_codebook(const uint32_t* hist, unsigned long long* enc,
                      unsigned long long* giw, uint32_t* gpar,
                      uint8_t* lens_by_sym, Ctl* ctl, cudaStream_t s);
 void launch_enc_len(const uint16_t* codes, uint32_t N, uint32_t C,
-                    uint32_t nch, const unsigned long long* enc, uint32_t* chw,
-                    const Ctl* ctl, int num_sms, cudaStream_t s);
+                    uint32_t nch, const unsigned long long* enc,
+                    uint16_t* lanebits, uint32_t* chw, const Ctl* ctl,
+                    int num_sms, cudaStream_t s);
 void launch_pack(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,
-                 const unsigned long long* enc, const uint32_t* chw,
-                 const unsigned long long* woff, uint8_t* out, const Ctl* ctl,
-                 int num_sms, cudaStream_t s);
+                 const unsigned long long* enc, const uint16_t* lanebits,
+                 const uint32_t* chw, const unsigned long long* woff,
+                 uint8_t* out, const Ctl* ctl, int num_sms, cudaStream_t s);
+void launch_chunk_words(const uint8_t* lanebits_bytes, uint32_t nch,
+                        uint32_t* chw, int num_sms, cudaStream_t s);
 void launch_outliers(bool gather, const uint16_t* codes, uint32_t N,
                      uint32_t C, uint32_t nch, const uint32_t* zc,
                      const unsigned long long* zoff, const float* src,
@@ -51,13 +54,13 @@ void launch_dec_tables(const uint8_t* stream, uint32_t n_used,
                        uint16_t* sorted, unsigned long long* gkeys, Ctl* ctl,
                        cudaStream_t s);
 void launch_decode(const uint8_t* stream, uint64_t off_bits,
-                   uint64_t total_words, const uint32_t* chw_stream,
+                   uint64_t total_words, const uint8_t* lanebits_bytes,
                    const unsigned long long* woff, uint32_t N, uint32_t C,
                    uint32_t nch, uint32_t n_used, uint16_t single_sym,
                    const uint32_t* lut, const uint32_t* cnt,
                    const unsigned long long* first, const uint32_t* offs,
                    const uint16_t* sorted, uint16_t* codes, uint32_t* zc,
-                   Ctl* ctl, cudaStream_t s);
+                   Ctl* ctl, int num_sms, cudaStream_t s);
 
 // k_stream.cu
 void launch_scan(const uint32_t* in, unsigned long long* out, uint32_t n,
@@ -68,7 +71,7 @@ void launch_finalize(const uint8_t* hdr, const uint8_t* hdr_const,
                      uint8_t* out, const float* RA, uint32_t na,
                      unsigned long long off_anchors, const uint8_t* bmap,
                      uint32_t nblocks, unsigned long long off_bmap,
-                     const uint32_t* chw, uint32_t nch,
+                     const uint16_t* lanebits, uint32_t nch,
                      unsigned long long off_chw, const uint16_t* tsyms,
                      const uint8_t* tlens, const Ctl* ctl, int num_sms,
                      cudaStream_t s);

@@ -2,9 +2,11 @@
 // encode and decode of the quantization codes (Sec. 4 Step 4).
 //
 // Stream convention (shared with the decoder): the row-major code array is
-// cut into chunks of C symbols; each chunk's codes are packed MSB-first
-// into 32-bit words starting at a fresh word; the per-chunk word counts are
-// stored so chunks decode independently.  Codebook: two-queue Huffman merge
+// cut into chunks of C symbols; a chunk is coded as 32 lanes, lane l holding
+// the chunk's symbols l, l+32, l+64, ...; the lanes' bits follow one another
+// MSB-first in 32-bit words, each chunk starting on a fresh word, and every
+// lane's bit count is stored (u16), so one warp encodes or decodes a chunk
+// with coalesced symbol access and no atomics inside a lane's words.  Codebook: two-queue Huffman merge
 // over leaves sorted by (frequency, symbol), ties taking the leaf; lengths
 // are leaf depths; canonical codes ordered by (length, symbol).
 #include "hpez_internal.cuh"
@@ -286,38 +288,30 @@ __global__ void __launch_bounds__(1024)
 }
 
 // ---------------------------------------------------------------------
-// encode: per-chunk word counts
+// encode: lane bit counts and chunk word counts
 // ---------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
     k_enc_len(const uint16_t* __restrict__ codes, uint32_t N, uint32_t C,
               uint32_t nch, const unsigned long long* __restrict__ enc,
-              uint32_t* __restrict__ chw, const Ctl* __restrict__ ctl) {
+              uint16_t* __restrict__ lanebits, uint32_t* __restrict__ chw,
+              const Ctl* __restrict__ ctl) {
   if (ctl->status || ctl->is_const) return;
   const int lane = threadIdx.x & 31;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t c = warp; c < nch; c += nwarps) {
-    const uint32_t beg = c * C, end = min(beg + C, N);
-    unsigned long long bits = 0;
-    if (end - beg == C) {
-      const uint4* p = reinterpret_cast<const uint4*>(codes + beg);
-      for (uint32_t i = lane; i < C / 8; i += 32) {
-        const uint4 v = p[i];
-        const unsigned w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          bits += (enc[w[k] & 0xFFFFu] >> 56) + (enc[w[k] >> 16] >> 56);
-      }
-    } else {
-      for (uint32_t i = beg + lane; i < end; i += 32) bits += enc[codes[i]] >> 56;
-    }
-    for (int o = 16; o > 0; o >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, o);
-    if (lane == 0) chw[c] = (uint32_t)((bits + 31) >> 5);
+    const uint32_t beg = c * C, nc = min(C, N - beg);
+    uint32_t bits = 0;
+    for (uint32_t j = lane; j < nc; j += 32) bits += (uint32_t)(enc[codes[beg + j]] >> 56);
+    lanebits[(size_t)c * 32 + lane] = (uint16_t)bits;
+    uint32_t tot = bits;
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0) chw[c] = (tot + 31) >> 5;
   }
 }
 
 // ---------------------------------------------------------------------
-// encode: packing (one warp per chunk, contiguous symbol range per lane)
+// encode: packing, one warp per chunk, lane l writes its own bit range
 // ---------------------------------------------------------------------
 struct BitWriter {
   uint32_t* words;   // chunk base
@@ -362,6 +356,7 @@ struct BitWriter {
 __global__ void __launch_bounds__(256)
     k_pack(const uint16_t* __restrict__ codes, uint32_t N, uint32_t C,
            uint32_t nch, const unsigned long long* __restrict__ enc,
+           const uint16_t* __restrict__ lanebits,
            const uint32_t* __restrict__ chw,
            const unsigned long long* __restrict__ woff, uint8_t* out,
            const Ctl* __restrict__ ctl) {
@@ -371,30 +366,39 @@ __global__ void __launch_bounds__(256)
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   uint32_t* bits = reinterpret_cast<uint32_t*>(out + ctl->off_bits);
   for (uint32_t c = warp; c < nch; c += nwarps) {
-    const uint32_t beg = c * C, end = min(beg + C, N);
+    const uint32_t beg = c * C, nc = min(C, N - beg);
     uint32_t* words = bits + woff[c];
     const uint32_t nw = chw[c];
     for (uint32_t i = lane; i < nw; i += 32) words[i] = 0u;
     __syncwarp();
-    const uint32_t per = C / 32;
-    const uint32_t lb = min(beg + lane * per, end), le = min(lb + per, end);
-    unsigned long long mybits = 0;
-    for (uint32_t i = lb; i < le; ++i) mybits += enc[codes[i]] >> 56;
-    unsigned long long off = mybits;
+    const uint32_t mybits = lanebits[(size_t)c * 32 + lane];
+    uint32_t off = mybits;
     for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(0xffffffffu, off, o);
+      const uint32_t y = __shfl_up_sync(0xffffffffu, off, o);
       if (lane >= o) off += y;
     }
     off -= mybits;
     BitWriter bw;
     bw.words = words;
-    bw.wi = (uint32_t)(off >> 5);
+    bw.wi = off >> 5;
     bw.nacc = (int)(off & 31);
     bw.acc = 0;
     bw.shared_first = bw.nacc != 0;
-    for (uint32_t i = lb; i < le; ++i) bw.put_code(enc[codes[i]]);
+    for (uint32_t j = lane; j < nc; j += 32) bw.put_code(enc[codes[beg + j]]);
     bw.flush();
     __syncwarp();
+  }
+}
+
+// chunk word counts from the stored lane bit counts (decompress)
+__global__ void k_chunk_words(const uint8_t* __restrict__ lanebits_bytes,
+                              uint32_t nch, uint32_t* __restrict__ chw) {
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nch;
+       c += gridDim.x * blockDim.x) {
+    const uint8_t* p = lanebits_bytes + (size_t)c * 64;
+    uint32_t s = 0;
+    for (int l = 0; l < 32; ++l) s += (uint32_t)p[2 * l] | ((uint32_t)p[2 * l + 1] << 8);
+    chw[c] = (s + 31) >> 5;
   }
 }
 
@@ -529,11 +533,11 @@ __global__ void __launch_bounds__(1024)
 }
 
 // ---------------------------------------------------------------------
-// decode: one thread per chunk
+// decode: one warp per chunk, lane l decodes its own bit range
 // ---------------------------------------------------------------------
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
     k_decode(const uint8_t* __restrict__ stream, uint64_t off_bits,
-             uint64_t total_words, const uint32_t* __restrict__ chw_stream,
+             uint64_t total_words, const uint8_t* __restrict__ lanebits_bytes,
              const unsigned long long* __restrict__ woff, uint32_t N,
              uint32_t C, uint32_t nch, uint32_t n_used, uint16_t single_sym,
              const uint32_t* __restrict__ g_lut,
@@ -553,76 +557,81 @@ __global__ void __launch_bounds__(128)
   }
   __syncthreads();
   if (ctl->status) return;
-  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nch) return;
-  const uint32_t beg = c * C, end = min(beg + C, N);
-  uint32_t zeros = 0;
-  if (n_used == 1) {
-    for (uint32_t i = beg; i < end; ++i) codes[i] = single_sym;
-    zc[c] = single_sym == 0 ? end - beg : 0;
-    return;
-  }
-  const uint32_t nw = chw_stream[c];
-  const unsigned long long w0 = woff[c];
-  if (w0 + nw > total_words) {
-    atomicExch(&ctl->status, ST_CORRUPT);
-    return;
-  }
-  const uint32_t* words = reinterpret_cast<const uint32_t*>(stream + off_bits) + w0;
-  uint32_t wi = 0;
-  unsigned long long buf = 0;
-  int nbuf = 0;
-  auto refill = [&]() {
-    while (nbuf <= 32 && wi < nw) {
-      buf |= (unsigned long long)__ldg(words + wi) << (32 - nbuf);
-      nbuf += 32;
-      ++wi;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t* allw = reinterpret_cast<const uint32_t*>(stream + off_bits);
+  for (uint32_t c = warp; c < nch; c += nwarps) {
+    const uint32_t beg = c * C, nc = min(C, N - beg);
+    const uint8_t* lb = lanebits_bytes + (size_t)c * 64;
+    const uint32_t mybits = (uint32_t)lb[2 * lane] | ((uint32_t)lb[2 * lane + 1] << 8);
+    uint32_t start = mybits, tot;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, start, o);
+      if (lane >= o) start += y;
     }
-  };
-  uint32_t pack[4];
-  int np = 0;
-  const bool vec = (end - beg) == C;
-  for (uint32_t i = beg; i < end; ++i) {
-    refill();
-    const uint32_t e = lut[(uint32_t)(buf >> (64 - kLutBits))];
-    uint32_t sym, len;
-    if (e != 0) {
-      len = e >> 16;
-      sym = e & 0xFFFFu;
-    } else {
-      sym = 0;
-      len = 0;
-      for (uint32_t L = kLutBits + 1; L < 57; ++L) {
-        const unsigned long long v = buf >> (64 - L);
-        if (cnt[L] && v >= first[L] && v - first[L] < cnt[L]) {
-          sym = sorted[offs[L] + (uint32_t)(v - first[L])];
-          len = L;
+    tot = __shfl_sync(0xffffffffu, start, 31);
+    start -= mybits;
+    const uint32_t nw = (tot + 31) >> 5;
+    const unsigned long long w0 = woff[c];
+    uint32_t zeros = 0;
+    bool bad = w0 + nw > total_words;
+    if (n_used == 1) {
+      bad |= mybits != 0;
+      if (!bad)
+        for (uint32_t j = lane; j < nc; j += 32) codes[beg + j] = single_sym;
+      zeros = single_sym == 0 ? (nc + 31 - lane) / 32 : 0;
+    } else if (!bad) {
+      const uint32_t* words = allw + w0;
+      uint32_t wi = start >> 5;
+      unsigned long long buf = 0;
+      int nbuf = 0;
+      {
+        const uint32_t w = wi < nw ? __ldg(words + wi) : 0u;
+        const int sh = (int)(start & 31);
+        buf = ((unsigned long long)w << 32) << sh;
+        nbuf = 32 - sh;
+        ++wi;
+      }
+      uint32_t left = mybits;  // bits of this lane not consumed yet
+      for (uint32_t j = lane; j < nc; j += 32) {
+        while (nbuf <= 32) {
+          const uint32_t w = wi < nw ? __ldg(words + wi) : 0u;
+          buf |= (unsigned long long)w << (32 - nbuf);
+          nbuf += 32;
+          ++wi;
+        }
+        const uint32_t e = lut[(uint32_t)(buf >> (64 - kLutBits))];
+        uint32_t sym = 0, len = 0;
+        if (e != 0) {
+          len = e >> 16;
+          sym = e & 0xFFFFu;
+        } else {
+          for (uint32_t L = kLutBits + 1; L < 57; ++L) {
+            const unsigned long long v = buf >> (64 - L);
+            if (cnt[L] && v >= first[L] && v - first[L] < cnt[L]) {
+              sym = sorted[offs[L] + (uint32_t)(v - first[L])];
+              len = L;
+              break;
+            }
+          }
+        }
+        if (len == 0 || len > left) {
+          bad = true;
           break;
         }
+        left -= len;
+        buf <<= len;
+        nbuf -= (int)len;
+        zeros += sym == 0;
+        codes[beg + j] = (uint16_t)sym;
       }
+      bad |= left != 0;
     }
-    if (len == 0 || (int)len > nbuf) {
-      atomicExch(&ctl->status, ST_CORRUPT);
-      return;
-    }
-    buf <<= len;
-    nbuf -= (int)len;
-    zeros += sym == 0;
-    if (vec) {
-      if (np & 1)
-        pack[np >> 1] |= sym << 16;
-      else
-        pack[np >> 1] = sym;
-      if (++np == 8) {
-        *reinterpret_cast<uint4*>(codes + i - 7) =
-            make_uint4(pack[0], pack[1], pack[2], pack[3]);
-        np = 0;
-      }
-    } else {
-      codes[i] = (uint16_t)sym;
-    }
+    if (bad) atomicExch(&ctl->status, ST_CORRUPT);
+    for (int o = 16; o > 0; o >>= 1) zeros += __shfl_xor_sync(0xffffffffu, zeros, o);
+    if (lane == 0) zc[c] = zeros;
   }
-  zc[c] = zeros;
 }
 
 // ---------------------------------------------------------------------
@@ -661,18 +670,27 @@ void launch_codebook(const uint32_t* hist, unsigned long long* enc,
 }
 
 void launch_enc_len(const uint16_t* codes, uint32_t N, uint32_t C,
-                    uint32_t nch, const unsigned long long* enc, uint32_t* chw,
-                    const Ctl* ctl, int num_sms, cudaStream_t s) {
-  k_enc_len<<<warps_grid(nch, num_sms), 256, 0, s>>>(codes, N, C, nch, enc, chw,
-                                                     ctl);
+                    uint32_t nch, const unsigned long long* enc,
+                    uint16_t* lanebits, uint32_t* chw, const Ctl* ctl,
+                    int num_sms, cudaStream_t s) {
+  k_enc_len<<<warps_grid(nch, num_sms), 256, 0, s>>>(codes, N, C, nch, enc,
+                                                     lanebits, chw, ctl);
 }
 
 void launch_pack(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,
-                 const unsigned long long* enc, const uint32_t* chw,
-                 const unsigned long long* woff, uint8_t* out, const Ctl* ctl,
-                 int num_sms, cudaStream_t s) {
-  k_pack<<<warps_grid(nch, num_sms), 256, 0, s>>>(codes, N, C, nch, enc, chw,
-                                                  woff, out, ctl);
+                 const unsigned long long* enc, const uint16_t* lanebits,
+                 const uint32_t* chw, const unsigned long long* woff,
+                 uint8_t* out, const Ctl* ctl, int num_sms, cudaStream_t s) {
+  k_pack<<<warps_grid(nch, num_sms), 256, 0, s>>>(codes, N, C, nch, enc,
+                                                  lanebits, chw, woff, out, ctl);
+}
+
+void launch_chunk_words(const uint8_t* lanebits_bytes, uint32_t nch,
+                        uint32_t* chw, int num_sms, cudaStream_t s) {
+  unsigned g = (nch + 255) / 256;
+  if (g < 1) g = 1;
+  if (g > (unsigned)num_sms * 8) g = num_sms * 8;
+  k_chunk_words<<<g, 256, 0, s>>>(lanebits_bytes, nch, chw);
 }
 
 void launch_outliers(bool gather, const uint16_t* codes, uint32_t N,
@@ -702,17 +720,16 @@ void launch_dec_tables(const uint8_t* stream, uint32_t n_used,
 }
 
 void launch_decode(const uint8_t* stream, uint64_t off_bits,
-                   uint64_t total_words, const uint32_t* chw_stream,
+                   uint64_t total_words, const uint8_t* lanebits_bytes,
                    const unsigned long long* woff, uint32_t N, uint32_t C,
                    uint32_t nch, uint32_t n_used, uint16_t single_sym,
                    const uint32_t* lut, const uint32_t* cnt,
                    const unsigned long long* first, const uint32_t* offs,
                    const uint16_t* sorted, uint16_t* codes, uint32_t* zc,
-                   Ctl* ctl, cudaStream_t s) {
-  const unsigned grid = (nch + 127) / 128;
-  k_decode<<<grid, 128, 0, s>>>(stream, off_bits, total_words, chw_stream,
-                                woff, N, C, nch, n_used, single_sym, lut, cnt,
-                                first, offs, sorted, codes, zc, ctl);
+                   Ctl* ctl, int num_sms, cudaStream_t s) {
+  k_decode<<<warps_grid(nch, num_sms * 2), 256, 0, s>>>(
+      stream, off_bits, total_words, lanebits_bytes, woff, N, C, nch, n_used,
+      single_sym, lut, cnt, first, offs, sorted, codes, zc, ctl);
 }
 
 }  // namespace hpez

@@ -2,9 +2,10 @@
 //
 // Container (little-endian): a 512-byte header, then 16-byte aligned
 // sections: anchors (f32, compact anchor grid in row-major order), block
-// map (u8 per block, optional), chunk word counts (u32 per chunk), code
-// table (u16 symbols ascending, then u8 lengths), outliers (f32, row-major
-// order of their points), bitstream (u32 words).  Padding bytes are zero.
+// map (u8 per block, optional),
+// lane bit counts (u16, 32 per chunk), code table (u16 symbols ascending,
+// then u8 lengths), outliers (f32, row-major order of their points),
+// bitstream (u32 words).  Padding bytes are zero.
 #include "hpez_internal.cuh"
 #include "hpez_launch.h"
 
@@ -106,8 +107,8 @@ __global__ void k_finalize(HeaderImage hdr, HeaderImage hdr_const,
                            unsigned long long off_anchors,
                            const uint8_t* __restrict__ bmap, uint32_t nblocks,
                            unsigned long long off_bmap,
-                           const uint32_t* __restrict__ chw, uint32_t nch,
-                           unsigned long long off_chw,
+                           const uint16_t* __restrict__ lanebits,
+                           uint32_t nch, unsigned long long off_chw,
                            const uint16_t* __restrict__ tsyms,
                            const uint8_t* __restrict__ tlens,
                            const Ctl* __restrict__ ctl) {
@@ -144,9 +145,10 @@ __global__ void k_finalize(HeaderImage hdr, HeaderImage hdr_const,
   for (uint32_t i = tid; i < na; i += nthr) fa[i] = RA[i];
   // block map
   for (uint32_t i = tid; i < nblocks; i += nthr) out[off_bmap + i] = bmap[i];
-  // chunk word counts
+  // lane bit counts (32 per chunk)
   uint32_t* fc = reinterpret_cast<uint32_t*>(out + off_chw);
-  for (uint32_t i = tid; i < nch; i += nthr) fc[i] = chw[i];
+  const uint32_t* lb32 = reinterpret_cast<const uint32_t*>(lanebits);
+  for (uint32_t i = tid; i < 16u * nch; i += nthr) fc[i] = lb32[i];
   // code table: symbols then lengths
   const uint32_t nu = ctl->n_used;
   const unsigned long long ot = ctl->off_table;
@@ -158,7 +160,7 @@ __global__ void k_finalize(HeaderImage hdr, HeaderImage hdr_const,
   }
   // zero padding at the end of each section
   const unsigned long long ends[5] = {off_anchors + 4ull * na,
-                                      off_bmap + nblocks, off_chw + 4ull * nch,
+                                      off_bmap + nblocks, off_chw + 64ull * nch,
                                       ot + 3ull * nu,
                                       ctl->off_outliers + 4ull * ctl->n_out};
   if (tid < 5) {
@@ -181,7 +183,7 @@ void launch_finalize(const uint8_t* hdr, const uint8_t* hdr_const,
                      uint8_t* out, const float* RA, uint32_t na,
                      unsigned long long off_anchors, const uint8_t* bmap,
                      uint32_t nblocks, unsigned long long off_bmap,
-                     const uint32_t* chw, uint32_t nch,
+                     const uint16_t* lanebits, uint32_t nch,
                      unsigned long long off_chw, const uint16_t* tsyms,
                      const uint8_t* tlens, const Ctl* ctl, int num_sms,
                      cudaStream_t s) {
@@ -191,12 +193,12 @@ void launch_finalize(const uint8_t* hdr, const uint8_t* hdr_const,
     hc.b[i] = hdr_const[i];
   }
   uint64_t work = na;
-  if (nch > work) work = nch;
+  if (16ull * nch > work) work = 16ull * nch;
   unsigned grid = (unsigned)((work + 255) / 256);
   if (grid < 1) grid = 1;
   if (grid > (unsigned)num_sms * 4) grid = num_sms * 4;
   k_finalize<<<grid, 256, 0, s>>>(h, hc, out, RA, na, off_anchors, bmap,
-                                  nblocks, off_bmap, chw, nch, off_chw, tsyms,
+                                  nblocks, off_bmap, lanebits, nch, off_chw, tsyms,
                                   tlens, ctl);
 }
 

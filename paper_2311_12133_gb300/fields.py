@@ -166,6 +166,29 @@ def climate2d(shape=(1800, 3600), seed=0, mask_frac=0.05):
     return np.ascontiguousarray(f, dtype=np.float32)
 
 
+def grf_torch(shape=(512, 512, 512), seed=0, slope=-5.0 / 3.0, device="cuda"):
+    """The ``grf`` recipe drawn on the GPU with torch (same spectrum and
+    normalization, different random stream): for large benchmark inputs
+    whose host generation would take minutes.  Returns a float32 tensor."""
+    import torch
+    shape = tuple(int(s) for s in shape)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
+    w = torch.randn(shape, generator=g, device=device, dtype=torch.float32)
+    W = torch.fft.rfftn(w)
+    del w
+    filt = torch.from_numpy(_spectral_filter(shape, slope,
+                                             tuple(range(len(shape))))
+                            .astype(np.float32)).to(device)
+    W *= filt
+    del filt
+    f = torch.fft.irfftn(W, s=shape)
+    del W
+    f -= f.mean(dtype=torch.float64).float()
+    f /= f.std().float()
+    return f.contiguous()
+
+
 GENERATORS = {
     "bumps": bumps,
     "grf": grf,

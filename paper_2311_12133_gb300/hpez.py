@@ -87,6 +87,11 @@ def _load():
             "hpez_inspect": (ctypes.c_int, [vp, u64, ctypes.POINTER(ctypes.c_int),
                                             u64p, ctypes.POINTER(ctypes.c_double)]),
             "hpez_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+            "hpez_profile_enable": (ctypes.c_int, [vp, ctypes.c_int]),
+            "hpez_profile_get": (ctypes.c_int, [vp, ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_double), u64p]),
+            "hpez_profile_phase_name": (ctypes.c_char_p, [ctypes.c_int]),
+            "hpez_launch_count": (ctypes.c_int, [vp, u64p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -101,7 +106,8 @@ def exported_symbols() -> list[str]:
     return ["hpez_create", "hpez_destroy", "hpez_default_config",
             "hpez_compress_bound", "hpez_compress", "hpez_decompress",
             "hpez_compress_host", "hpez_decompress_host", "hpez_inspect",
-            "hpez_strerror"]
+            "hpez_strerror", "hpez_profile_enable", "hpez_profile_get",
+            "hpez_profile_phase_name", "hpez_launch_count"]
 
 
 def _check(rc: int, what: str):
@@ -190,10 +196,38 @@ def hpez_inspect(header: bytes):
     return nd.value, tuple(int(dims[i]) for i in range(nd.value)), eb.value
 
 
+HPEZ_PH_RANGE, HPEZ_PH_ANCHORS, HPEZ_PH_HIST, HPEZ_PH_CODEBOOK = 0, 1, 2, 3
+HPEZ_PH_ENCODE, HPEZ_PH_PACK, HPEZ_PH_OUTLIERS, HPEZ_PH_FINALIZE = 4, 5, 6, 7
+HPEZ_PH_DEC_PREP, HPEZ_PH_DECODE, HPEZ_PH_SCATTER = 8, 9, 10
+HPEZ_PH_LEVEL, HPEZ_PH_DLEVEL, HPEZ_PROFILE_PHASES = 11, 27, 43
+
+
+def hpez_profile_enable(ctx, enable: bool) -> None:
+    _check(_load().hpez_profile_enable(ctx, 1 if enable else 0), "hpez_profile_enable")
+
+
+def hpez_profile_get(ctx, phase: int):
+    ms = ctypes.c_double(0)
+    cnt = ctypes.c_uint64(0)
+    _check(_load().hpez_profile_get(ctx, phase, ctypes.byref(ms), ctypes.byref(cnt)),
+           "hpez_profile_get")
+    return ms.value, cnt.value
+
+
+def hpez_profile_phase_name(phase: int) -> str:
+    return _load().hpez_profile_phase_name(phase).decode()
+
+
+def hpez_launch_count(ctx) -> int:
+    n = ctypes.c_uint64(0)
+    _check(_load().hpez_launch_count(ctx, ctypes.byref(n)), "hpez_launch_count")
+    return n.value
+
+
 # --------------------------------------------------------------------------
 # config helper
 # --------------------------------------------------------------------------
-def make_config(ndim: int, *, anchor_stride=None, frozen_dim=-1, chunk_syms=4096,
+def make_config(ndim: int, *, anchor_stride=None, frozen_dim=-1, chunk_syms=16384,
                 alpha=1.0, beta=1.0, md_inv_var=(1, 1, 1), interp=HPEZ_CUBIC_NAK,
                 paradigm=HPEZ_PARADIGM_1D, same_level=0, order=None,
                 blockmap=None, block_size=32) -> hpez_config:
@@ -208,11 +242,16 @@ def make_config(ndim: int, *, anchor_stride=None, frozen_dim=-1, chunk_syms=4096
     for d in range(3):
         c.md_inv_var[d] = float(md_inv_var[d])
     dims = [d for d in range(ndim) if d != frozen_dim]
+    def per(v, l):
+        # per-level lists shorter than the level count repeat their last entry
+        if isinstance(v, (list, tuple)):
+            return v[l] if l < len(v) else v[-1]
+        return v
+
     for l in range(HPEZ_MAX_LEVELS):
-        c.interp[l] = interp[l] if isinstance(interp, (list, tuple)) else interp
-        c.paradigm[l] = paradigm[l] if isinstance(paradigm, (list, tuple)) else paradigm
-        c.same_level[l] = (same_level[l] if isinstance(same_level, (list, tuple))
-                           else same_level)
+        c.interp[l] = per(interp, l)
+        c.paradigm[l] = per(paradigm, l)
+        c.same_level[l] = per(same_level, l)
         if order is None:
             o = dims
         elif isinstance(order[0], (list, tuple)):

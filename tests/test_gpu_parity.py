@@ -152,9 +152,11 @@ def test_degenerate_fields(gpu, oracle):
     _check(gpu, oracle, c, 1e-3, 0)  # absolute bound: a regular stream
     one = np.array([3.5], np.float32)
     _check(gpu, oracle, one, 0.1, 0)
-    lin = np.arange(4096, dtype=np.float32).reshape(16, 256)
+    # a linear ramp on a grid that ends on anchor lines: every code is the
+    # zero-error code, so the code table has a single symbol
+    lin = np.arange(17 * 257, dtype=np.float32).reshape(17, 257)
     st = _check(gpu, oracle, lin, 0.25, 0, anchor_stride=16)
-    assert st.n_used == 1  # every code is the zero-error code
+    assert st.n_used == 1
 
 
 def test_error_codes(gpu):
