@@ -139,6 +139,20 @@ HPEZ_API int hpez_inspect(const void* h_header, uint64_t n, int* ndim, uint64_t*
 /* Static text for an error code. */
 HPEZ_API const char* hpez_strerror(int code);
 
+/* Execution options of a context (the results never depend on them):
+ *  HPEZ_OPT_FUSED_LEVELS  1 (default): a level of the 1D-style paradigm
+ *                         runs as one tiled kernel; 0: one kernel per pass
+ *  HPEZ_OPT_TILE_E0..2    tile extent of that slot of the level grid for
+ *                         the fused kernel (0 = built-in heuristic)
+ *  HPEZ_OPT_FUSED_SMEM    shared-memory cap in bytes for a fused tile
+ * Errors: INVALID_ARG for an unknown option or an out-of-range value. */
+#define HPEZ_OPT_FUSED_LEVELS 1
+#define HPEZ_OPT_TILE_E0 2
+#define HPEZ_OPT_TILE_E1 3
+#define HPEZ_OPT_TILE_E2 4
+#define HPEZ_OPT_FUSED_SMEM 5
+HPEZ_API int hpez_set_option(hpez_ctx* ctx, int option, int64_t value);
+
 /* ---- measurement hooks (not part of the paper's method) ----
  * Phase timing: with profiling enabled, compress/decompress record a CUDA
  * event pair on the call's stream around each phase and accumulate the

@@ -72,6 +72,9 @@ struct PhaseProfiler {
 struct hpez_ctx {
   PhaseProfiler prof;
   uint64_t launches = 0;
+  int fused_levels = 1;        // HPEZ_OPT_FUSED_LEVELS
+  int tile_e[3] = {0, 0, 0};   // HPEZ_OPT_TILE_E0..2 (0 = heuristic)
+  size_t fused_smem_cap = 96 * 1024;
   int device = 0;
   int num_sms = 152;
   char* scratch = nullptr;
@@ -327,6 +330,97 @@ std::vector<Launch> level_schedule(const Plan& p, const hpez_config& c,
 }
 
 // ---------------------------------------------------------------------
+// fused level plan (1D-style paradigm): tile extents and, per pass and
+// half, the box of points to compute relative to the tile.  Working back
+// from the last pass: pass j's half B is needed on R_B(j), its half A on
+// R_A(j) = R_B(j) grown by 2 along pi_j (same-level neighbours at +-2s),
+// and every earlier pass on R_B(j-1) = R_A(j) grown by 3 along pi_j
+// (neighbours at +-s, +-3s).
+// ---------------------------------------------------------------------
+bool plan_fused(const hpez_ctx* ctx, const Plan& p, const hpez_config& c,
+                int l, bool decomp, FusedLevel& F) {
+  if (c.paradigm[l - 1] == HPEZ_PARADIGM_MD || p.k == 0) return false;
+  std::memset(&F, 0, sizeof(F));
+  F.g = p.grid[l - 1];
+  F.gc = p.grid[l];
+  const bool sl =
+      c.blockwise || (c.interp[l - 1] != HPEZ_LINEAR && c.same_level[l - 1]);
+  int pi[3];
+  for (int j = 0; j < p.k; ++j) pi[j] = c.order[l - 1][j] + p.off;
+  int hA[3][3], hB[3][3];  // halo per pass j and slot
+  for (int s = 0; s < 3; ++s) hB[p.k - 1][s] = 0;
+  for (int j = p.k - 1; j >= 0; --j) {
+    for (int s = 0; s < 3; ++s) hA[j][s] = hB[j][s];
+    if (sl) hA[j][pi[j]] += 2;
+    if (j > 0) {
+      for (int s = 0; s < 3; ++s) hB[j - 1][s] = hA[j][s];
+      hB[j - 1][pi[j]] += 3;
+    }
+  }
+  const uint32_t* m = F.g.m;
+  for (int s = 0; s < 3; ++s) F.interp[s] = p.interp[s] ? 1 : 0;
+  // tile extents: long along the fastest slot, thin along the slowest
+  uint32_t E[3];
+  const bool one_d = m[0] == 1 && m[1] == 1;
+  E[2] = one_d ? std::min<uint32_t>(m[2], 2048) : (m[2] <= 256 ? m[2] : 128);
+  E[1] = std::min<uint32_t>(m[1], 16);
+  E[0] = std::min<uint32_t>(m[0], 2);
+  for (int s = 0; s < 3; ++s)
+    if (ctx->tile_e[s] > 0) E[s] = std::min<uint32_t>(m[s], (uint32_t)ctx->tile_e[s]);
+  auto fix_even = [&](int s) {
+    if (p.interp[s] && E[s] < m[s] && (E[s] & 1)) E[s] += 1;
+    if (E[s] < 1) E[s] = 1;
+  };
+  for (int s = 0; s < 3; ++s) fix_even(s);
+  auto smem = [&]() {
+    size_t b = 4;
+    for (int s = 0; s < 3; ++s) b *= (size_t)(E[s] + 2 * hA[0][s]);
+    if (!decomp) b += 2ull * E[0] * E[1] * E[2];
+    return b;
+  };
+  while (smem() > ctx->fused_smem_cap) {
+    int big = 2;
+    for (int s = 0; s < 3; ++s)
+      if (E[s] > E[big]) big = s;
+    if (E[big] <= 2) return false;
+    E[big] = (E[big] / 2) & ~1u;
+    if (E[big] < 2) E[big] = 2;
+    fix_even(big);
+  }
+  uint64_t nt = 1;
+  for (int s = 0; s < 3; ++s) {
+    F.E[s] = E[s];
+    F.rlo[s] = -hA[0][s];
+    F.rhi[s] = (int)E[s] + hA[0][s];
+    F.RX[s] = (uint32_t)(F.rhi[s] - F.rlo[s]);
+    F.ntile[s] = (m[s] + E[s] - 1) / E[s];
+    nt *= F.ntile[s];
+  }
+  if (nt > 0x7FFFFFFFull) return false;
+  F.ntiles = (uint32_t)nt;
+  F.nsteps = 0;
+  for (int j = 0; j < p.k; ++j) {
+    for (int half = 0; half < (sl ? 2 : 1); ++half) {
+      FusedStep& S = F.st[F.nsteps++];
+      std::memset(&S, 0, sizeof(S));
+      S.dim = (int8_t)pi[j];
+      S.half = (int8_t)half;
+      for (int s = 0; s < 3; ++s) {
+        const int h = half == 0 ? hA[j][s] : hB[j][s];
+        S.lo[s] = (int16_t)(-h);
+        S.hi[s] = (int16_t)((int)E[s] + h);
+        S.par[s] = 0;  // non-interpolation slots and earlier directions
+      }
+      S.par[pi[j]] = 1;
+      for (int m2 = j + 1; m2 < p.k; ++m2) S.par[pi[m2]] = 2;
+    }
+  }
+  F.level = l;
+  F.write_recon = (decomp || l > 1) ? 1 : 0;
+  return true;
+}
+
+// ---------------------------------------------------------------------
 // scratch arena
 // ---------------------------------------------------------------------
 struct Arena {
@@ -499,6 +593,26 @@ int hpez_profile_get(hpez_ctx* ctx, int phase, double* total_ms,
   if (total_ms) *total_ms = ctx->prof.total_ms[phase];
   if (count) *count = ctx->prof.count[phase];
   return HPEZ_OK;
+}
+
+int hpez_set_option(hpez_ctx* ctx, int option, int64_t value) {
+  if (!ctx) return HPEZ_ERR_INVALID_ARG;
+  switch (option) {
+    case HPEZ_OPT_FUSED_LEVELS:
+      ctx->fused_levels = value != 0;
+      return HPEZ_OK;
+    case HPEZ_OPT_TILE_E0:
+    case HPEZ_OPT_TILE_E1:
+    case HPEZ_OPT_TILE_E2:
+      if (value < 0 || value > 4096) return HPEZ_ERR_INVALID_ARG;
+      ctx->tile_e[option - HPEZ_OPT_TILE_E0] = (int)value;
+      return HPEZ_OK;
+    case HPEZ_OPT_FUSED_SMEM:
+      if (value < 4096 || value > 200 * 1024) return HPEZ_ERR_INVALID_ARG;
+      ctx->fused_smem_cap = (size_t)value;
+      return HPEZ_OK;
+  }
+  return HPEZ_ERR_INVALID_ARG;
 }
 
 int hpez_launch_count(hpez_ctx* ctx, uint64_t* launches) {
@@ -685,16 +799,22 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   for (int l = p.L; l >= 1; --l) {
     const int g = l - 1;
     pf.begin(HPEZ_PH_LEVEL + g, s);
-    launch_upsample(p.grid[l], p.gsize[l], p.grid[g], b.R[l], b.Cg[l], b.R[g],
-                    b.Cg[g], b.ctl, s);
-    ++nl;
     sb.R = b.R[g];
     sb.C = b.Cg[g];
     sb.kind = cfg.interp[l - 1];
     sb.same = cfg.same_level[l - 1];
-    for (const Launch& L : level_schedule(p, cfg, l)) {
-      launch_pass(false, p.grid[g], L.pb, sb, ctx->num_sms, s);
-      nl += L.pb.total ? 1 : 0;
+    FusedLevel F;
+    if (ctx->fused_levels && plan_fused(ctx, p, cfg, l, false, F)) {
+      launch_level(false, F, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g], s);
+      ++nl;
+    } else {
+      launch_upsample(p.grid[l], p.gsize[l], p.grid[g], b.R[l], b.Cg[l], b.R[g],
+                      b.Cg[g], b.ctl, s);
+      ++nl;
+      for (const Launch& L : level_schedule(p, cfg, l)) {
+        launch_pass(false, p.grid[g], L.pb, sb, ctx->num_sms, s);
+        nl += L.pb.total ? 1 : 0;
+      }
     }
     pf.end(s);
   }
@@ -909,15 +1029,21 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   for (int l = p.L; l >= 1; --l) {
     const int g = l - 1;
     pf.begin(HPEZ_PH_DLEVEL + g, s);
-    launch_upsample(p.grid[l], p.gsize[l], p.grid[g], R[l], nullptr, R[g],
-                    nullptr, ctl, s);
-    ++nl;
     sb.R = R[g];
     sb.kind = cfg.interp[l - 1];
     sb.same = cfg.same_level[l - 1];
-    for (const Launch& L : level_schedule(p, cfg, l)) {
-      launch_pass(true, p.grid[g], L.pb, sb, ctx->num_sms, s);
-      nl += L.pb.total ? 1 : 0;
+    FusedLevel F;
+    if (ctx->fused_levels && plan_fused(ctx, p, cfg, l, true, F)) {
+      launch_level(true, F, sb, R[l], nullptr, R[g], nullptr, s);
+      ++nl;
+    } else {
+      launch_upsample(p.grid[l], p.gsize[l], p.grid[g], R[l], nullptr, R[g],
+                      nullptr, ctl, s);
+      ++nl;
+      for (const Launch& L : level_schedule(p, cfg, l)) {
+        launch_pass(true, p.grid[g], L.pb, sb, ctx->num_sms, s);
+        nl += L.pb.total ? 1 : 0;
+      }
     }
     pf.end(s);
   }

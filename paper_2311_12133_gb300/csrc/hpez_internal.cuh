@@ -272,4 +272,28 @@ struct SweepBufs {
   const Ctl* ctl;
 };
 
+// One step of the fused level kernel: a pass (or one same-level half of
+// it) over a box of the level grid given relative to the tile origin.
+struct FusedStep {
+  int8_t par[3];   // per slot: 0 any parity, 1 odd, 2 even
+  int8_t dim;      // slot predicted along
+  int8_t half;     // same-level half processed
+  int8_t pad_[3];
+  int16_t lo[3], hi[3];
+};
+
+struct FusedLevel {
+  LevelGeom g, gc;      // this level's grid and the coarse grid
+  uint32_t E[3];        // tile extents
+  int32_t rlo[3], rhi[3];  // shared-memory region relative to the tile
+  uint32_t RX[3];       // region extents (rhi - rlo)
+  uint32_t ntile[3];
+  uint32_t ntiles;
+  int interp[3];        // slot is an interpolation dimension
+  int nsteps;
+  FusedStep st[6];
+  int level;
+  int write_recon;
+};
+
 }  // namespace hpez

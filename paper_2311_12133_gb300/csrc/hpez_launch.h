@@ -25,6 +25,12 @@ void launch_upsample(const LevelGeom& gc, uint32_t total_c,
 void launch_pass(bool decomp, const LevelGeom& g, const PassBox& pb,
                  const SweepBufs& B, int num_sms, cudaStream_t s);
 
+// k_level.cu
+size_t fused_smem_bytes(const FusedLevel& P, bool decomp);
+void launch_level(bool decomp, const FusedLevel& P, const SweepBufs& B,
+                  const float* Rc, const uint16_t* Cc, float* Rs, uint16_t* Cs,
+                  cudaStream_t s);
+
 // k_huffman.cu
 void launch_hist(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,
                  uint32_t* hist, uint32_t* zc, const Ctl* ctl, int num_sms,

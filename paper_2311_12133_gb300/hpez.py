@@ -92,6 +92,7 @@ def _load():
                                                 ctypes.POINTER(ctypes.c_double), u64p]),
             "hpez_profile_phase_name": (ctypes.c_char_p, [ctypes.c_int]),
             "hpez_launch_count": (ctypes.c_int, [vp, u64p]),
+            "hpez_set_option": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -107,7 +108,7 @@ def exported_symbols() -> list[str]:
             "hpez_compress_bound", "hpez_compress", "hpez_decompress",
             "hpez_compress_host", "hpez_decompress_host", "hpez_inspect",
             "hpez_strerror", "hpez_profile_enable", "hpez_profile_get",
-            "hpez_profile_phase_name", "hpez_launch_count"]
+            "hpez_profile_phase_name", "hpez_launch_count", "hpez_set_option"]
 
 
 def _check(rc: int, what: str):
@@ -216,6 +217,14 @@ def hpez_profile_get(ctx, phase: int):
 
 def hpez_profile_phase_name(phase: int) -> str:
     return _load().hpez_profile_phase_name(phase).decode()
+
+
+HPEZ_OPT_FUSED_LEVELS, HPEZ_OPT_TILE_E0, HPEZ_OPT_TILE_E1 = 1, 2, 3
+HPEZ_OPT_TILE_E2, HPEZ_OPT_FUSED_SMEM = 4, 5
+
+
+def hpez_set_option(ctx, option: int, value: int) -> None:
+    _check(_load().hpez_set_option(ctx, option, int(value)), "hpez_set_option")
 
 
 def hpez_launch_count(ctx) -> int:

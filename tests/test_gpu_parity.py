@@ -204,3 +204,50 @@ def test_determinism_repeated(gpu):
         b = buf[:size].cpu().numpy().tobytes()
         ref = ref or b
         assert b == ref
+
+
+@pytest.fixture
+def opts(gpu):
+    """Restore the context's execution options after a test."""
+    from paper_2311_12133_gb300 import hpez
+    yield gpu
+    hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_FUSED_LEVELS, 1)
+    for o in (hpez.HPEZ_OPT_TILE_E0, hpez.HPEZ_OPT_TILE_E1, hpez.HPEZ_OPT_TILE_E2):
+        hpez.hpez_set_option(gpu.handle, o, 0)
+
+
+@pytest.mark.parametrize("tile", [(2, 4, 8), (2, 2, 2), (4, 6, 10), (6, 2, 4)])
+@pytest.mark.parametrize("order,same,interp", [((0, 1, 2), 0, 1), ((2, 1, 0), 1, 1),
+                                               ((1, 0, 2), 1, 2), ((0, 2, 1), 0, 0)])
+def test_fused_level_tiles(opts, oracle, tile, order, same, interp):
+    """Small tiles make most of every tile halo: the recomputed halo points
+    must equal the neighbouring tiles' own results bit for bit."""
+    from paper_2311_12133_gb300 import fields, hpez
+    for o, e in zip((hpez.HPEZ_OPT_TILE_E0, hpez.HPEZ_OPT_TILE_E1, hpez.HPEZ_OPT_TILE_E2), tile):
+        hpez.hpez_set_option(opts.handle, o, e)
+    x = fields.grf((29, 36, 43), seed=sum(tile) + same)
+    _check(opts, oracle, x, 1e-3, 1, order=order, same_level=same, interp=interp,
+           anchor_stride=16)
+
+
+def test_fused_tiles_blockwise_frozen_2d(opts, oracle):
+    from paper_2311_12133_gb300 import fields, hpez
+    hpez.hpez_set_option(opts.handle, hpez.HPEZ_OPT_TILE_E1, 4)
+    hpez.hpez_set_option(opts.handle, hpez.HPEZ_OPT_TILE_E2, 6)
+    x = fields.grf((70, 64, 45), seed=5)
+    bm = np.random.default_rng(3).choice(np.array([0, 1, 2, 5, 6], np.uint8), size=12)
+    _check(opts, oracle, x, 1e-3, 1, blockmap=bm, order=(1, 2, 0))
+    y = fields.aniso((10, 50, 60), seed=1)
+    _check(opts, oracle, y, 1e-3, 1, frozen_dim=0, same_level=1)
+    z = fields.climate2d((90, 150), seed=4)
+    _check(opts, oracle, z, 1e-3, 1, same_level=1, order=(1, 0))
+
+
+def test_per_pass_path_still_exact(opts, oracle):
+    """The one-kernel-per-pass path (used for multi-dimensional levels)
+    forced on for 1D-style levels too."""
+    from paper_2311_12133_gb300 import fields, hpez
+    hpez.hpez_set_option(opts.handle, hpez.HPEZ_OPT_FUSED_LEVELS, 0)
+    x = fields.grf((40, 41, 42), seed=8)
+    _check(opts, oracle, x, 1e-3, 1)
+    _check(opts, oracle, x, 1e-3, 1, same_level=1, interp=2, order=(2, 0, 1))
