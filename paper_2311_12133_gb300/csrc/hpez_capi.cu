@@ -413,6 +413,9 @@ bool plan_fused(const hpez_ctx* ctx, const Plan& p, const hpez_config& c,
       }
       S.par[pi[j]] = 1;
       for (int m2 = j + 1; m2 < p.k; ++m2) S.par[pi[m2]] = 2;
+      // passes after the first read only points computed in the region;
+      // the first pass's +-s, +-3s neighbours may be coarse points outside
+      S.pad_[0] = (int8_t)(j > 0 ? 1 : 0);
     }
   }
   F.level = l;

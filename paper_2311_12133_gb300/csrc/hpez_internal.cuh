@@ -278,7 +278,7 @@ struct FusedStep {
   int8_t par[3];   // per slot: 0 any parity, 1 odd, 2 even
   int8_t dim;      // slot predicted along
   int8_t half;     // same-level half processed
-  int8_t pad_[3];
+  int8_t pad_[3];  // pad_[0]: every neighbour read lies in the region
   int16_t lo[3], hi[3];
 };
 

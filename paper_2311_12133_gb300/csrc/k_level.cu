@@ -17,71 +17,102 @@
 
 namespace hpez {
 
-// fetch of a neighbour along slot d at offset j: from shared memory when
-// it lies inside the CTA's region, else from the compact coarse grid (only
-// happens for the first pass, whose neighbours are all coarse points)
-struct NeighbourCtx {
-  const float* sm;        // region values
-  const float* Rc;        // compact coarse grid
-  int idx;                // the point's region index
-  int st;                 // region stride along d
-  int u;                  // the point's grid coordinate along d
-  int lo, hi;             // region bounds along d (grid coordinates)
-  uint32_t cbase;         // coarse index of the point with u_d removed
-  uint32_t cst;           // coarse stride along d
-  __device__ float at(int j) const {
+// Exact bound test with a fast accept: rn(r - x) strictly inside the bound
+// implies the exact difference is inside too (rounding is monotonic), so
+// the TwoSum residual is only needed near the bound.
+__device__ __forceinline__ unsigned quantize_fast(float x, float p, float el,
+                                                  float inv2, float twoe,
+                                                  float& recon) {
+  const float diff = __fsub_rn(x, p);
+  const float m = __fadd_rn(__fmul_rn(fabsf(diff), inv2), 0.5f);
+  if (m < 32768.0f) {
+    const int k = __float2int_rz(m);
+    const int q = diff < 0.0f ? -k : k;
+    const float r = __fadd_rn(p, __fmul_rn(__int2float_rn(q), twoe));
+    if (fabsf(__fsub_rn(r, x)) < el || within_bound(r, x, el)) {
+      recon = r;
+      return (unsigned)(q + kRadius);
+    }
+  }
+  recon = x;
+  return 0u;
+}
+
+// Prediction at a point from neighbours along one slot: smem[idx + j*st]
+// when the neighbour lies in the CTA's region, else (first pass only) the
+// compact coarse grid.
+struct Line {
+  const float* sm;
+  int idx, st;     // region index of the point, region stride along the slot
+  int u, lo, hi;   // grid coordinate along the slot, region bounds
+  bool in_smem;    // every existing neighbour is in the region
+  const float* Rc;
+  uint32_t cbase, cst;
+  __device__ __forceinline__ float at(int j) const {
+    if (in_smem) return sm[idx + j * st];
     const int v = u + j;
     if (v >= lo && v < hi) return sm[idx + j * st];
     return __ldg(Rc + cbase + (uint32_t)(v >> 1) * cst);
   }
 };
 
-__device__ __forceinline__ float predict_fused(const NeighbourCtx& n, int m,
-                                               int kind, bool half_b) {
-  const int f = choose_formula(kind, half_b, n.u, m);
+__device__ __forceinline__ float predict_at(const Line& L, int m, int kind,
+                                            bool half_b) {
+  const int u = L.u;
+  // interior fast path: all four inter-level knots present
+  if (!half_b && u >= 3 && u + 3 <= m - 1) {
+    const float m1 = L.at(-1), p1 = L.at(1);
+    if (kind == LINEAR) return eval_formula(F_LIN, 0.f, 0.f, m1, p1, 0.f, 0.f);
+    const float m3 = L.at(-3), p3 = L.at(3);
+    return eval_formula(kind == CUBIC_NAK ? F_NAK4 : F_NAT4, m3, 0.f, m1, p1,
+                        0.f, p3);
+  }
+  const int f = choose_formula(kind, half_b, u, m);
   float m3 = 0.f, m2 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
-  const float m1 = n.at(-1);
+  const float m1 = L.at(-1);
   switch (f) {
     case F_COPY:
       break;
     case F_EXTRAP:
-      m3 = n.at(-3);
+      m3 = L.at(-3);
       break;
     case F_LIN:
-      p1 = n.at(1);
+      p1 = L.at(1);
       break;
     case F_NAK4:
     case F_NAT4:
-      m3 = n.at(-3);
-      p1 = n.at(1);
-      p3 = n.at(3);
+      m3 = L.at(-3);
+      p1 = L.at(1);
+      p3 = L.at(3);
       break;
     case F_NAK3L:
     case F_NAT3L:
-      m3 = n.at(-3);
-      p1 = n.at(1);
+      m3 = L.at(-3);
+      p1 = L.at(1);
       break;
     case F_NAK3R:
     case F_NAT3R:
-      p1 = n.at(1);
-      p3 = n.at(3);
+      p1 = L.at(1);
+      p3 = L.at(3);
       break;
     case F_SL_NAK:
-      m2 = n.at(-2);
-      p1 = n.at(1);
-      p2 = n.at(2);
+      m2 = L.at(-2);
+      p1 = L.at(1);
+      p2 = L.at(2);
       break;
     case F_SL_NAT:
-      m3 = n.at(-3);
-      m2 = n.at(-2);
-      p1 = n.at(1);
-      p2 = n.at(2);
-      p3 = n.at(3);
+      m3 = L.at(-3);
+      m2 = L.at(-2);
+      p1 = L.at(1);
+      p2 = L.at(2);
+      p3 = L.at(3);
       break;
   }
   return eval_formula(f, m3, m2, m1, p1, p2, p3);
 }
 
+// Rows of a box are (slot 0, slot 1) index pairs handed to warps; lanes
+// walk the fastest slot.  One division per row, none per point.
 template <bool kDecomp>
 __global__ void __launch_bounds__(256)
     k_level(FusedLevel P, SweepBufs B, const float* __restrict__ Rc,
@@ -92,7 +123,8 @@ __global__ void __launch_bounds__(256)
   extern __shared__ float sm[];
   const LevelGeom& g = P.g;
   const LevelGeom& gc = P.gc;
-  // tile origin and region bounds (grid coordinates)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
   uint32_t tb = blockIdx.x;
   int o[3];
   {
@@ -110,7 +142,7 @@ __global__ void __launch_bounds__(256)
     base[d] = o[d] + P.rlo[d];
     lo[d] = max(base[d], 0);
     hi[d] = min(o[d] + P.rhi[d], (int)g.m[d]);
-    te[d] = min(o[d] + (int)P.E[d], (int)g.m[d]);  // tile end
+    te[d] = min(o[d] + (int)P.E[d], (int)g.m[d]);
   }
   const int RX1 = (int)P.RX[1], RX2 = (int)P.RX[2];
   const int sst[3] = {RX1 * RX2, RX2, 1};
@@ -118,8 +150,10 @@ __global__ void __launch_bounds__(256)
   const int E1 = (int)P.E[1], E2 = (int)P.E[2];
   const int li = P.level - 1;
   const float el = ctl->el[li], inv2 = ctl->inv2[li], twoe = ctl->twoe[li];
+  const uint32_t fst0 = g.step[0] * g.fst[0], fst1 = g.step[1] * g.fst[1],
+                 fst2 = g.step[2];
 
-  // 1. coarse points of the region (every interpolation coordinate even)
+  // 1. coarse points of the region
   {
     int st0[3], cn[3], stp[3];
 #pragma unroll
@@ -128,19 +162,17 @@ __global__ void __launch_bounds__(256)
       st0[d] = P.interp[d] ? ((lo[d] + 1) & ~1) : lo[d];
       cn[d] = hi[d] > st0[d] ? (hi[d] - st0[d] + stp[d] - 1) / stp[d] : 0;
     }
-    const uint32_t tot = (uint32_t)(cn[0] * cn[1] * cn[2]);
-    for (uint32_t t = threadIdx.x; t < tot; t += blockDim.x) {
-      const int a2 = (int)(t % (uint32_t)cn[2]);
-      const uint32_t r = t / (uint32_t)cn[2];
-      const int a1 = (int)(r % (uint32_t)cn[1]);
-      const int a0 = (int)(r / (uint32_t)cn[1]);
-      const int u0 = st0[0] + a0 * stp[0], u1 = st0[1] + a1 * stp[1],
-                u2 = st0[2] + a2 * stp[2];
-      const uint32_t ci = (uint32_t)(u0 / stp[0]) * gc.gst[0] +
-                          (uint32_t)(u1 / stp[1]) * gc.gst[1] +
-                          (uint32_t)(u2 / stp[2]);
-      sm[(u0 - base[0]) * sst[0] + (u1 - base[1]) * RX2 + (u2 - base[2])] =
-          __ldg(Rc + ci);
+    const int rows = cn[0] * cn[1];
+    for (int r = warp; r < rows; r += nwarps) {
+      const int a0 = r / cn[1], a1 = r - a0 * cn[1];
+      const int u0 = st0[0] + a0 * stp[0], u1 = st0[1] + a1 * stp[1];
+      const uint32_t crow = (uint32_t)(u0 / stp[0]) * gc.gst[0] +
+                            (uint32_t)(u1 / stp[1]) * gc.gst[1] +
+                            (uint32_t)(st0[2] / stp[2]);
+      float* srow = sm + (u0 - base[0]) * sst[0] + (u1 - base[1]) * RX2 +
+                    (st0[2] - base[2]);
+      for (int a2 = lane; a2 < cn[2]; a2 += 32)
+        srow[a2 * stp[2]] = __ldg(Rc + crow + a2);
     }
   }
   __syncthreads();
@@ -164,96 +196,93 @@ __global__ void __launch_bounds__(256)
       cn[d] = b > st0[d] ? (b - st0[d] + stp[d] - 1) / stp[d] : 0;
     }
     const int d = S.dim;
-    const uint32_t tot = (uint32_t)(cn[0] * cn[1] * cn[2]);
-    for (uint32_t t = threadIdx.x; t < tot; t += blockDim.x) {
-      const int a2 = (int)(t % (uint32_t)cn[2]);
-      const uint32_t r = t / (uint32_t)cn[2];
-      const int a1 = (int)(r % (uint32_t)cn[1]);
-      const int a0 = (int)(r / (uint32_t)cn[1]);
-      const int u[3] = {st0[0] + a0 * stp[0], st0[1] + a1 * stp[1],
-                        st0[2] + a2 * stp[2]};
-      int kind = B.kind, same = B.same;
-      if (B.blockmap) {
-        uint32_t bi = 0;
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-          bi = bi * B.nb[q] + ((uint32_t)u[q] * g.step[q]) / B.bs;
-        const unsigned v = B.blockmap[bi];
-        kind = (int)(v & 3u);
-        if (kind > CUBIC_NAT) kind = CUBIC_NAT;
-        same = (int)((v >> 2) & 1u);
+    const bool in_smem = S.pad_[0] != 0;
+    const int md = (int)g.m[d];
+    const int rows = cn[0] * cn[1];
+    for (int r = warp; r < rows; r += nwarps) {
+      const int a0 = r / cn[1], a1 = r - a0 * cn[1];
+      const int u0 = st0[0] + a0 * stp[0], u1 = st0[1] + a1 * stp[1];
+      const int rsm = (u0 - base[0]) * sst[0] + (u1 - base[1]) * RX2 - base[2];
+      const uint32_t rfull = (uint32_t)u0 * fst0 + (uint32_t)u1 * fst1;
+      const bool row_in_tile = u0 >= o[0] && u0 < te[0] && u1 >= o[1] && u1 < te[1];
+      const int rtile = ((u0 - o[0]) * E1 + (u1 - o[1])) * E2 - o[2];
+      uint32_t brow = 0;
+      if (B.blockmap)
+        brow = (((uint32_t)u0 * g.step[0]) / B.bs * B.nb[1] +
+                ((uint32_t)u1 * g.step[1]) / B.bs) * B.nb[2];
+      // coarse index of the row with slot d left out (first pass only)
+      uint32_t cb_row = 0;
+      if (!in_smem) {
+        if (d != 0) cb_row += (uint32_t)(P.interp[0] ? (u0 >> 1) : u0) * gc.gst[0];
+        if (d != 1) cb_row += (uint32_t)(P.interp[1] ? (u1 >> 1) : u1) * gc.gst[1];
       }
-      if (kind == LINEAR) same = 0;
-      const int in_b = same && (((u[d] - 1) >> 1) & 1);
-      if (in_b != S.half) continue;
-      const int idx = (u[0] - base[0]) * sst[0] + (u[1] - base[1]) * RX2 +
-                      (u[2] - base[2]);
-      NeighbourCtx nc;
-      nc.sm = sm;
-      nc.Rc = Rc;
-      nc.idx = idx;
-      nc.st = sst[d];
-      nc.u = u[d];
-      nc.lo = lo[d];
-      nc.hi = hi[d];
-      {
-        // coarse index with slot d left out (only used by the first pass)
-        uint32_t cb = 0;
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-          if (q != d) cb += (uint32_t)(P.interp[q] ? (u[q] >> 1) : u[q]) * gc.gst[q];
-        nc.cbase = cb;
-        nc.cst = gc.gst[d];
+      for (int a2 = lane; a2 < cn[2]; a2 += 32) {
+        const int u2 = st0[2] + a2 * stp[2];
+        int kind = B.kind, same = B.same;
+        if (B.blockmap) {
+          const unsigned v = B.blockmap[brow + ((uint32_t)u2 * g.step[2]) / B.bs];
+          kind = (int)(v & 3u);
+          if (kind > CUBIC_NAT) kind = CUBIC_NAT;
+          same = (int)((v >> 2) & 1u);
+        }
+        if (kind == LINEAR) same = 0;
+        const int ud = d == 0 ? u0 : (d == 1 ? u1 : u2);
+        const int in_b = same && (((ud - 1) >> 1) & 1);
+        if (in_b != S.half) continue;
+        const int idx = rsm + u2;
+        Line L;
+        L.sm = sm;
+        L.idx = idx;
+        L.st = sst[d];
+        L.u = ud;
+        L.lo = lo[d];
+        L.hi = hi[d];
+        L.in_smem = in_smem;
+        L.Rc = Rc;
+        L.cbase = cb_row + (d != 2 ? (uint32_t)(P.interp[2] ? (u2 >> 1) : u2) : 0u);
+        L.cst = gc.gst[d];
+        const float p = predict_at(L, md, kind, in_b);
+        const uint32_t fi = rfull + (uint32_t)u2 * fst2;
+        float rec;
+        if (!kDecomp) {
+          const unsigned code = quantize_fast(__ldg(B.x + fi), p, el, inv2, twoe, rec);
+          if (row_in_tile && u2 >= o[2] && u2 < te[2]) ctile[rtile + u2] = (uint16_t)code;
+        } else {
+          const unsigned code = B.codes_full[fi];
+          rec = code ? dequantize(code, p, twoe) : B.outl_full[fi];
+        }
+        sm[idx] = rec;
       }
-      const float p = predict_fused(nc, (int)g.m[d], kind, in_b);
-      const uint32_t fi = (uint32_t)u[0] * g.step[0] * g.fst[0] +
-                          (uint32_t)u[1] * g.step[1] * g.fst[1] +
-                          (uint32_t)u[2] * g.step[2];
-      float rec;
-      if (!kDecomp) {
-        const unsigned code = quantize(__ldg(B.x + fi), p, el, inv2, twoe, rec);
-        if (u[0] >= o[0] && u[0] < te[0] && u[1] >= o[1] && u[1] < te[1] &&
-            u[2] >= o[2] && u[2] < te[2])
-          ctile[((u[0] - o[0]) * E1 + (u[1] - o[1])) * E2 + (u[2] - o[2])] =
-              (uint16_t)code;
-      } else {
-        const unsigned code = B.codes_full[fi];
-        rec = code ? dequantize(code, p, twoe) : B.outl_full[fi];
-      }
-      sm[idx] = rec;
     }
     __syncthreads();
   }
 
-  // 3. write the tile: codes (coarse ones copied from the coarse grid) and
-  //    the reconstruction when the next level reads it
+  // 3. write the tile out, rows to warps, consecutive elements to lanes
   {
     const int n0 = te[0] - o[0], n1 = te[1] - o[1], n2 = te[2] - o[2];
-    const uint32_t tot = (uint32_t)(n0 * n1 * n2);
-    for (uint32_t t = threadIdx.x; t < tot; t += blockDim.x) {
-      const int a2 = (int)(t % (uint32_t)n2);
-      const uint32_t r = t / (uint32_t)n2;
-      const int a1 = (int)(r % (uint32_t)n1);
-      const int a0 = (int)(r / (uint32_t)n1);
-      const int u0 = o[0] + a0, u1 = o[1] + a1, u2 = o[2] + a2;
-      const uint32_t gi = (uint32_t)u0 * g.gst[0] + (uint32_t)u1 * g.gst[1] + (uint32_t)u2;
-      const int idx = (u0 - base[0]) * sst[0] + (u1 - base[1]) * RX2 + (u2 - base[2]);
+    const int rows = n0 * n1;
+    for (int r = warp; r < rows; r += nwarps) {
+      const int a0 = r / n1, a1 = r - a0 * n1;
+      const int u0 = o[0] + a0, u1 = o[1] + a1;
+      const uint32_t grow = (uint32_t)u0 * g.gst[0] + (uint32_t)u1 * g.gst[1] + (uint32_t)o[2];
+      const float* srow = sm + (u0 - base[0]) * sst[0] + (u1 - base[1]) * RX2 + (o[2] - base[2]);
       if (!kDecomp) {
-        const bool coarse = (!P.interp[0] || !(u0 & 1)) && (!P.interp[1] || !(u1 & 1)) &&
-                            (!P.interp[2] || !(u2 & 1));
-        uint16_t code;
-        if (coarse) {
-          const uint32_t ci = (uint32_t)(P.interp[0] ? u0 >> 1 : u0) * gc.gst[0] +
-                              (uint32_t)(P.interp[1] ? u1 >> 1 : u1) * gc.gst[1] +
-                              (uint32_t)(P.interp[2] ? u2 >> 1 : u2);
-          code = Cc[ci];
-        } else {
-          code = ctile[(a0 * E1 + a1) * E2 + a2];
+        const bool crow = (!P.interp[0] || !(u0 & 1)) && (!P.interp[1] || !(u1 & 1));
+        const uint32_t ccrow = (uint32_t)(P.interp[0] ? u0 >> 1 : u0) * gc.gst[0] +
+                               (uint32_t)(P.interp[1] ? u1 >> 1 : u1) * gc.gst[1];
+        const uint16_t* trow = ctile + (a0 * E1 + a1) * E2;
+        for (int a2 = lane; a2 < n2; a2 += 32) {
+          const int u2 = o[2] + a2;
+          uint16_t code;
+          if (crow && (!P.interp[2] || !(u2 & 1)))
+            code = Cc[ccrow + (uint32_t)(P.interp[2] ? u2 >> 1 : u2)];
+          else
+            code = trow[a2];
+          Cs[grow + a2] = code;
+          if (P.write_recon) Rs[grow + a2] = srow[a2];
         }
-        Cs[gi] = code;
-        if (P.write_recon) Rs[gi] = sm[idx];
       } else {
-        Rs[gi] = sm[idx];
+        for (int a2 = lane; a2 < n2; a2 += 32) Rs[grow + a2] = srow[a2];
       }
     }
   }
