@@ -32,7 +32,7 @@ def test_host_side_calls_without_gpu():
     """Pure host entry points work without a device."""
     from paper_2311_12133_gb300 import hpez
     cfg = hpez.hpez_default_config(3)
-    assert cfg.anchor_stride == 32 and cfg.chunk_syms == 4096
+    assert cfg.anchor_stride == 32 and cfg.chunk_syms == 16384
     assert hpez.hpez_compress_bound((128, 128, 128)) > 4 * 128 ** 3
     assert hpez.hpez_strerror(-4).startswith("corrupt")
     import pytest
