@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--eb", type=float, default=1e-3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fused", type=int, default=1,
+                    help="1: one kernel per level (1D-style); 0: one per pass")
+    ap.add_argument("--tile", default="",
+                    help="fused tile extents e0,e1,e2 (0 = heuristic)")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warm-up + timed steps only (for ncu captures)")
     return ap.parse_args()
@@ -256,6 +260,11 @@ def main():
     A = 32 if len(shape) == 3 else (64 if len(shape) == 2 else 128)
     x = fields.grf_torch(shape, seed=fields.seed_of("bench", rank), device=f"cuda:{local}")
     ctx = hpez.Context(local)
+    hpez.hpez_set_option(ctx.handle, hpez.HPEZ_OPT_FUSED_LEVELS, args.fused)
+    if args.tile:
+        for o, e in zip((hpez.HPEZ_OPT_TILE_E0, hpez.HPEZ_OPT_TILE_E1,
+                         hpez.HPEZ_OPT_TILE_E2), args.tile.split(",")):
+            hpez.hpez_set_option(ctx.handle, o, int(e))
     cap = hpez.hpez_compress_bound(shape)
     cbuf = torch.empty(cap, dtype=torch.uint8, device=x.device)
     y = torch.empty_like(x)

@@ -362,8 +362,8 @@ bool plan_fused(const hpez_ctx* ctx, const Plan& p, const hpez_config& c,
   // tile extents: long along the fastest slot, thin along the slowest
   uint32_t E[3];
   const bool one_d = m[0] == 1 && m[1] == 1;
-  E[2] = one_d ? std::min<uint32_t>(m[2], 2048) : (m[2] <= 256 ? m[2] : 128);
-  E[1] = std::min<uint32_t>(m[1], 16);
+  E[2] = one_d ? std::min<uint32_t>(m[2], 4096) : (m[2] <= 512 ? m[2] : 256);
+  E[1] = std::min<uint32_t>(m[1], 8);
   E[0] = std::min<uint32_t>(m[0], 2);
   for (int s = 0; s < 3; ++s)
     if (ctx->tile_e[s] > 0) E[s] = std::min<uint32_t>(m[s], (uint32_t)ctx->tile_e[s]);
@@ -372,10 +372,12 @@ bool plan_fused(const hpez_ctx* ctx, const Plan& p, const hpez_config& c,
     if (E[s] < 1) E[s] = 1;
   };
   for (int s = 0; s < 3; ++s) fix_even(s);
+  // a slot the tile covers whole needs no halo
+  auto halo = [&](int s) { return E[s] >= m[s] ? 0 : hA[0][s]; };
   auto smem = [&]() {
     size_t b = 4;
-    for (int s = 0; s < 3; ++s) b *= (size_t)(E[s] + 2 * hA[0][s]);
-    if (!decomp) b += 2ull * E[0] * E[1] * E[2];
+    for (int s = 0; s < 3; ++s)
+      b *= (size_t)(E[s] + 2 * halo(s) + (s == 2 ? 3 : 0));
     return b;
   };
   while (smem() > ctx->fused_smem_cap) {
@@ -390,8 +392,12 @@ bool plan_fused(const hpez_ctx* ctx, const Plan& p, const hpez_config& c,
   uint64_t nt = 1;
   for (int s = 0; s < 3; ++s) {
     F.E[s] = E[s];
-    F.rlo[s] = -hA[0][s];
-    F.rhi[s] = (int)E[s] + hA[0][s];
+    // along the fastest slot the region starts on an even column and has
+    // an even length (the shared-memory rows split even and odd columns)
+    const int h = s == 2 ? ((halo(s) + 1) & ~1) : halo(s);
+    F.rlo[s] = -h;
+    F.rhi[s] = (int)E[s] + h;
+    if (s == 2 && ((F.rhi[s] - F.rlo[s]) & 1)) F.rhi[s] += 1;
     F.RX[s] = (uint32_t)(F.rhi[s] - F.rlo[s]);
     F.ntile[s] = (m[s] + E[s] - 1) / E[s];
     nt *= F.ntile[s];

@@ -38,82 +38,245 @@ __device__ __forceinline__ unsigned quantize_fast(float x, float p, float el,
   return 0u;
 }
 
-// Prediction at a point from neighbours along one slot: smem[idx + j*st]
-// when the neighbour lies in the CTA's region, else (first pass only) the
-// compact coarse grid.
-struct Line {
-  const float* sm;
-  int idx, st;     // region index of the point, region stride along the slot
-  int u, lo, hi;   // grid coordinate along the slot, region bounds
-  bool in_smem;    // every existing neighbour is in the region
-  const float* Rc;
-  uint32_t cbase, cst;
-  __device__ __forceinline__ float at(int j) const {
-    if (in_smem) return sm[idx + j * st];
-    const int v = u + j;
-    if (v >= lo && v < hi) return sm[idx + j * st];
-    return __ldg(Rc + cbase + (uint32_t)(v >> 1) * cst);
+// ---------------------------------------------------------------------
+// Shared-memory layout of the CTA's region: rows (slot 0, slot 1) of RX2
+// columns; along the fastest slot the even and odd grid columns are kept
+// in separate halves of the row (the region starts on an even column), so
+// a pass along that slot -- odd points, even neighbours -- and every other
+// pass read consecutive words across a warp.
+// ---------------------------------------------------------------------
+struct Region {
+  int o[3], base[3], lo[3], hi[3], te[3];
+  int RX1, RX2, HX;        // row length, half-row length
+  int rst0, rst1;          // element stride of a step along slot 0 / 1
+  __device__ __forceinline__ int col(int u2) const {
+    const int c = u2 - base[2];
+    return (c & 1) * HX + (c >> 1);
+  }
+  __device__ __forceinline__ int row(int u0, int u1) const {
+    return (u0 - base[0]) * rst0 + (u1 - base[1]) * rst1;
   }
 };
 
-__device__ __forceinline__ float predict_at(const Line& L, int m, int kind,
-                                            bool half_b) {
-  const int u = L.u;
-  // interior fast path: all four inter-level knots present
+template <int KIND>
+__device__ __forceinline__ float interior_k(float m3, float m1, float p1,
+                                            float p3) {
+  if (KIND == LINEAR) return eval_formula(F_LIN, 0.f, 0.f, m1, p1, 0.f, 0.f);
+  if (KIND == CUBIC_NAK) return eval_formula(F_NAK4, m3, 0.f, m1, p1, 0.f, p3);
+  return eval_formula(F_NAT4, m3, 0.f, m1, p1, 0.f, p3);
+}
+
+// Neighbour access along slot D of the point (u0, u1, u2): shared memory
+// inside the region, the compact coarse grid outside (first pass only).
+template <int D>
+struct Nbr {
+  const float* sm;
+  const Region* R;
+  int r, u0, u1, u2;   // row offset and coordinates of the point
+  bool in_smem;
+  const float* Rc;
+  uint32_t cbase, cst;
+  __device__ __forceinline__ float at(int j) const {
+    const int u = D == 0 ? u0 : (D == 1 ? u1 : u2);
+    const int v = u + j;
+    if (!in_smem && (v < R->lo[D] || v >= R->hi[D]))
+      return __ldg(Rc + cbase + (uint32_t)(v >> 1) * cst);
+    if (D == 2) return sm[r + R->col(v)];
+    if (D == 1) return sm[r + j * R->rst1 + R->col(u2)];
+    return sm[r + j * R->rst0 + R->col(u2)];
+  }
+};
+
+template <int KIND, int D>
+__device__ __forceinline__ float predict_nbr(const Nbr<D>& n, int u, int m,
+                                             int kind, bool half_b) {
   if (!half_b && u >= 3 && u + 3 <= m - 1) {
-    const float m1 = L.at(-1), p1 = L.at(1);
-    if (kind == LINEAR) return eval_formula(F_LIN, 0.f, 0.f, m1, p1, 0.f, 0.f);
-    const float m3 = L.at(-3), p3 = L.at(3);
-    return eval_formula(kind == CUBIC_NAK ? F_NAK4 : F_NAT4, m3, 0.f, m1, p1,
-                        0.f, p3);
+    const float m1 = n.at(-1), p1 = n.at(1);
+    if (KIND != 3) {
+      if (KIND == LINEAR) return interior_k<LINEAR>(0.f, m1, p1, 0.f);
+      return interior_k<KIND>(n.at(-3), m1, p1, n.at(3));
+    }
+    if (kind == LINEAR) return interior_k<LINEAR>(0.f, m1, p1, 0.f);
+    const float m3 = n.at(-3), p3 = n.at(3);
+    return kind == CUBIC_NAK ? interior_k<CUBIC_NAK>(m3, m1, p1, p3)
+                             : interior_k<CUBIC_NAT>(m3, m1, p1, p3);
   }
   const int f = choose_formula(kind, half_b, u, m);
   float m3 = 0.f, m2 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
-  const float m1 = L.at(-1);
+  const float m1 = n.at(-1);
   switch (f) {
     case F_COPY:
       break;
     case F_EXTRAP:
-      m3 = L.at(-3);
+      m3 = n.at(-3);
       break;
     case F_LIN:
-      p1 = L.at(1);
+      p1 = n.at(1);
       break;
     case F_NAK4:
     case F_NAT4:
-      m3 = L.at(-3);
-      p1 = L.at(1);
-      p3 = L.at(3);
+      m3 = n.at(-3);
+      p1 = n.at(1);
+      p3 = n.at(3);
       break;
     case F_NAK3L:
     case F_NAT3L:
-      m3 = L.at(-3);
-      p1 = L.at(1);
+      m3 = n.at(-3);
+      p1 = n.at(1);
       break;
     case F_NAK3R:
     case F_NAT3R:
-      p1 = L.at(1);
-      p3 = L.at(3);
+      p1 = n.at(1);
+      p3 = n.at(3);
       break;
     case F_SL_NAK:
-      m2 = L.at(-2);
-      p1 = L.at(1);
-      p2 = L.at(2);
+      m2 = n.at(-2);
+      p1 = n.at(1);
+      p2 = n.at(2);
       break;
     case F_SL_NAT:
-      m3 = L.at(-3);
-      m2 = L.at(-2);
-      p1 = L.at(1);
-      p2 = L.at(2);
-      p3 = L.at(3);
+      m3 = n.at(-3);
+      m2 = n.at(-2);
+      p1 = n.at(1);
+      p2 = n.at(2);
+      p3 = n.at(3);
       break;
   }
   return eval_formula(f, m3, m2, m1, p1, p2, p3);
 }
 
-// Rows of a box are (slot 0, slot 1) index pairs handed to warps; lanes
-// walk the fastest slot.  One division per row, none per point.
-template <bool kDecomp>
+struct LevelConsts {
+  float el, inv2, twoe;
+  uint32_t fst0, fst1, fst2;
+};
+
+// One pass half over its box: rows to warps, the fastest slot to lanes.
+// Interior points of a fixed interpolator whose neighbours are all in
+// shared memory take a straight-line path with precomputed indices; all
+// other points (boundaries, same-level halves, block map, first pass)
+// take the general one.  Codes (and reconstructions the next level reads)
+// of points inside the tile go straight to global memory.
+template <bool kDecomp, int KIND, int D>
+__device__ __forceinline__ void run_step(const FusedLevel& P, const SweepBufs& B,
+                                         const FusedStep& S, const Region& R,
+                                         const LevelConsts& K, float* sm,
+                                         const float* __restrict__ Rc,
+                                         float* __restrict__ Rs,
+                                         uint16_t* __restrict__ Cs) {
+  const LevelGeom& g = P.g;
+  const LevelGeom& gc = P.gc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  int st0[3], cn[3], stp[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int a = max(R.o[d] + S.lo[d], R.lo[d]);
+    const int b = min(R.o[d] + S.hi[d], R.hi[d]);
+    if (S.par[d] == 0) {
+      st0[d] = a;
+      stp[d] = 1;
+    } else {
+      const int want = S.par[d] == 1 ? 1 : 0;
+      st0[d] = a + ((a & 1) != want ? 1 : 0);
+      stp[d] = 2;
+    }
+    cn[d] = b > st0[d] ? (b - st0[d] + stp[d] - 1) / stp[d] : 0;
+  }
+  const bool in_smem = S.pad_[0] != 0;
+  const bool fast_ok = in_smem && KIND != 3;
+  const int md = (int)g.m[D];
+  const int rows = cn[0] * cn[1];
+  const int nst = D == 2 ? 0 : (D == 1 ? R.rst1 : R.rst0);  // neighbour stride
+  for (int rr = warp; rr < rows; rr += nwarps) {
+    const int a0 = rr / cn[1], a1 = rr - a0 * cn[1];
+    const int u0 = st0[0] + a0 * stp[0], u1 = st0[1] + a1 * stp[1];
+    const int rsm = R.row(u0, u1);
+    const uint32_t rfull = (uint32_t)u0 * K.fst0 + (uint32_t)u1 * K.fst1;
+    const uint32_t rgrid = (uint32_t)u0 * g.gst[0] + (uint32_t)u1 * g.gst[1];
+    const bool row_in_tile =
+        u0 >= R.o[0] && u0 < R.te[0] && u1 >= R.o[1] && u1 < R.te[1];
+    // along slot 0/1 the stencil depends on the row only
+    const int urow = D == 0 ? u0 : u1;
+    const bool row_interior = D == 2 || (urow >= 3 && urow + 3 <= md - 1);
+    uint32_t brow = 0;
+    if (KIND == 3 && B.blockmap)
+      brow = (((uint32_t)u0 * g.step[0]) / B.bs * B.nb[1] +
+              ((uint32_t)u1 * g.step[1]) / B.bs) * B.nb[2];
+    uint32_t cb_row = 0;
+    if (!in_smem) {
+      if (D != 0) cb_row += (uint32_t)(P.interp[0] ? (u0 >> 1) : u0) * gc.gst[0];
+      if (D != 1) cb_row += (uint32_t)(P.interp[1] ? (u1 >> 1) : u1) * gc.gst[1];
+    }
+    for (int a2 = lane; a2 < cn[2]; a2 += 32) {
+      const int u2 = st0[2] + a2 * stp[2];
+      const int c = u2 - R.base[2];
+      const int sidx = rsm + (c & 1) * R.HX + (c >> 1);
+      float p;
+      int in_b = 0;
+      const bool interior =
+          fast_ok && !B.same && row_interior && (D != 2 || (u2 >= 3 && u2 + 3 <= md - 1));
+      if (interior) {
+        float m3, m1, p1, p3;
+        if (D == 2) {
+          // odd column: even neighbours e-1 .. e+2 of the even half-row
+          const int e = rsm + (c >> 1);
+          m3 = sm[e - 1];
+          m1 = sm[e];
+          p1 = sm[e + 1];
+          p3 = sm[e + 2];
+        } else {
+          m3 = sm[sidx - 3 * nst];
+          m1 = sm[sidx - nst];
+          p1 = sm[sidx + nst];
+          p3 = sm[sidx + 3 * nst];
+        }
+        p = interior_k<KIND>(m3, m1, p1, p3);
+      } else {
+        int kind = KIND == 3 ? B.kind : KIND, same = B.same;
+        if (KIND == 3 && B.blockmap) {
+          const unsigned v = B.blockmap[brow + ((uint32_t)u2 * g.step[2]) / B.bs];
+          kind = (int)(v & 3u);
+          if (kind > CUBIC_NAT) kind = CUBIC_NAT;
+          same = (int)((v >> 2) & 1u);
+        }
+        if (kind == LINEAR) same = 0;
+        const int ud = D == 0 ? u0 : (D == 1 ? u1 : u2);
+        in_b = same && (((ud - 1) >> 1) & 1);
+        if (in_b != S.half) continue;
+        Nbr<D> n;
+        n.sm = sm;
+        n.R = &R;
+        n.r = rsm;
+        n.u0 = u0;
+        n.u1 = u1;
+        n.u2 = u2;
+        n.in_smem = in_smem;
+        n.Rc = Rc;
+        n.cbase = cb_row + (D != 2 ? (uint32_t)(P.interp[2] ? (u2 >> 1) : u2) : 0u);
+        n.cst = gc.gst[D];
+        p = predict_nbr<KIND, D>(n, ud, md, kind, in_b);
+      }
+      if (interior && S.half != 0) continue;  // fixed interpolator: no half B
+      const uint32_t fi = rfull + (uint32_t)u2 * K.fst2;
+      const bool in_tile = row_in_tile && u2 >= R.o[2] && u2 < R.te[2];
+      float rec;
+      if (!kDecomp) {
+        const unsigned code = quantize_fast(__ldg(B.x + fi), p, K.el, K.inv2, K.twoe, rec);
+        if (in_tile) {
+          Cs[rgrid + (uint32_t)u2] = (uint16_t)code;
+          if (P.write_recon) Rs[rgrid + (uint32_t)u2] = rec;
+        }
+      } else {
+        const unsigned code = B.codes_full[fi];
+        rec = code ? dequantize(code, p, K.twoe) : B.outl_full[fi];
+        if (in_tile) Rs[rgrid + (uint32_t)u2] = rec;
+      }
+      sm[sidx] = rec;
+    }
+  }
+}
+
+template <bool kDecomp, int KIND>
 __global__ void __launch_bounds__(256)
     k_level(FusedLevel P, SweepBufs B, const float* __restrict__ Rc,
             const uint16_t* __restrict__ Cc, float* __restrict__ Rs,
@@ -125,42 +288,46 @@ __global__ void __launch_bounds__(256)
   const LevelGeom& gc = P.gc;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  uint32_t tb = blockIdx.x;
-  int o[3];
+  Region R;
   {
+    uint32_t tb = blockIdx.x;
     const uint32_t t2 = tb % P.ntile[2];
     tb /= P.ntile[2];
     const uint32_t t1 = tb % P.ntile[1];
     const uint32_t t0 = tb / P.ntile[1];
-    o[0] = (int)(t0 * P.E[0]);
-    o[1] = (int)(t1 * P.E[1]);
-    o[2] = (int)(t2 * P.E[2]);
+    R.o[0] = (int)(t0 * P.E[0]);
+    R.o[1] = (int)(t1 * P.E[1]);
+    R.o[2] = (int)(t2 * P.E[2]);
   }
-  int base[3], lo[3], hi[3], te[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    base[d] = o[d] + P.rlo[d];
-    lo[d] = max(base[d], 0);
-    hi[d] = min(o[d] + P.rhi[d], (int)g.m[d]);
-    te[d] = min(o[d] + (int)P.E[d], (int)g.m[d]);
+    R.base[d] = R.o[d] + P.rlo[d];
+    R.lo[d] = max(R.base[d], 0);
+    R.hi[d] = min(R.o[d] + P.rhi[d], (int)g.m[d]);
+    R.te[d] = min(R.o[d] + (int)P.E[d], (int)g.m[d]);
   }
-  const int RX1 = (int)P.RX[1], RX2 = (int)P.RX[2];
-  const int sst[3] = {RX1 * RX2, RX2, 1};
-  uint16_t* ctile = reinterpret_cast<uint16_t*>(sm + P.RX[0] * P.RX[1] * P.RX[2]);
-  const int E1 = (int)P.E[1], E2 = (int)P.E[2];
+  R.RX1 = (int)P.RX[1];
+  R.RX2 = (int)P.RX[2];
+  R.HX = R.RX2 >> 1;
+  R.rst1 = R.RX2;
+  R.rst0 = R.RX1 * R.RX2;
   const int li = P.level - 1;
-  const float el = ctl->el[li], inv2 = ctl->inv2[li], twoe = ctl->twoe[li];
-  const uint32_t fst0 = g.step[0] * g.fst[0], fst1 = g.step[1] * g.fst[1],
-                 fst2 = g.step[2];
+  LevelConsts K;
+  K.el = ctl->el[li];
+  K.inv2 = ctl->inv2[li];
+  K.twoe = ctl->twoe[li];
+  K.fst0 = g.step[0] * g.fst[0];
+  K.fst1 = g.step[1] * g.fst[1];
+  K.fst2 = g.step[2];
 
-  // 1. coarse points of the region
+  // 1. coarse points of the region (all interpolation coordinates even)
   {
     int st0[3], cn[3], stp[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       stp[d] = P.interp[d] ? 2 : 1;
-      st0[d] = P.interp[d] ? ((lo[d] + 1) & ~1) : lo[d];
-      cn[d] = hi[d] > st0[d] ? (hi[d] - st0[d] + stp[d] - 1) / stp[d] : 0;
+      st0[d] = P.interp[d] ? ((R.lo[d] + 1) & ~1) : R.lo[d];
+      cn[d] = R.hi[d] > st0[d] ? (R.hi[d] - st0[d] + stp[d] - 1) / stp[d] : 0;
     }
     const int rows = cn[0] * cn[1];
     for (int r = warp; r < rows; r += nwarps) {
@@ -169,10 +336,9 @@ __global__ void __launch_bounds__(256)
       const uint32_t crow = (uint32_t)(u0 / stp[0]) * gc.gst[0] +
                             (uint32_t)(u1 / stp[1]) * gc.gst[1] +
                             (uint32_t)(st0[2] / stp[2]);
-      float* srow = sm + (u0 - base[0]) * sst[0] + (u1 - base[1]) * RX2 +
-                    (st0[2] - base[2]);
+      const int rsm = R.row(u0, u1);
       for (int a2 = lane; a2 < cn[2]; a2 += 32)
-        srow[a2 * stp[2]] = __ldg(Rc + crow + a2);
+        sm[rsm + R.col(st0[2] + a2 * stp[2])] = __ldg(Rc + crow + a2);
     }
   }
   __syncthreads();
@@ -180,136 +346,83 @@ __global__ void __launch_bounds__(256)
   // 2. the passes, each half a step
   for (int si = 0; si < P.nsteps; ++si) {
     const FusedStep& S = P.st[si];
+    if (S.dim == 2)
+      run_step<kDecomp, KIND, 2>(P, B, S, R, K, sm, Rc, Rs, Cs);
+    else if (S.dim == 1)
+      run_step<kDecomp, KIND, 1>(P, B, S, R, K, sm, Rc, Rs, Cs);
+    else
+      run_step<kDecomp, KIND, 0>(P, B, S, R, K, sm, Rc, Rs, Cs);
+    __syncthreads();
+  }
+
+  // 3. the tile's coarse points: codes copied from the coarse grid, and the
+  //    reconstruction where this level's output is read again
+  {
     int st0[3], cn[3], stp[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const int a = max(o[d] + S.lo[d], lo[d]);
-      const int b = min(o[d] + S.hi[d], hi[d]);
-      if (S.par[d] == 0) {
-        st0[d] = a;
-        stp[d] = 1;
-      } else {
-        const int want = S.par[d] == 1 ? 1 : 0;
-        st0[d] = a + ((a & 1) != want ? 1 : 0);
-        stp[d] = 2;
-      }
-      cn[d] = b > st0[d] ? (b - st0[d] + stp[d] - 1) / stp[d] : 0;
+      stp[d] = P.interp[d] ? 2 : 1;
+      st0[d] = P.interp[d] ? ((R.o[d] + 1) & ~1) : R.o[d];
+      cn[d] = R.te[d] > st0[d] ? (R.te[d] - st0[d] + stp[d] - 1) / stp[d] : 0;
     }
-    const int d = S.dim;
-    const bool in_smem = S.pad_[0] != 0;
-    const int md = (int)g.m[d];
     const int rows = cn[0] * cn[1];
     for (int r = warp; r < rows; r += nwarps) {
       const int a0 = r / cn[1], a1 = r - a0 * cn[1];
       const int u0 = st0[0] + a0 * stp[0], u1 = st0[1] + a1 * stp[1];
-      const int rsm = (u0 - base[0]) * sst[0] + (u1 - base[1]) * RX2 - base[2];
-      const uint32_t rfull = (uint32_t)u0 * fst0 + (uint32_t)u1 * fst1;
-      const bool row_in_tile = u0 >= o[0] && u0 < te[0] && u1 >= o[1] && u1 < te[1];
-      const int rtile = ((u0 - o[0]) * E1 + (u1 - o[1])) * E2 - o[2];
-      uint32_t brow = 0;
-      if (B.blockmap)
-        brow = (((uint32_t)u0 * g.step[0]) / B.bs * B.nb[1] +
-                ((uint32_t)u1 * g.step[1]) / B.bs) * B.nb[2];
-      // coarse index of the row with slot d left out (first pass only)
-      uint32_t cb_row = 0;
-      if (!in_smem) {
-        if (d != 0) cb_row += (uint32_t)(P.interp[0] ? (u0 >> 1) : u0) * gc.gst[0];
-        if (d != 1) cb_row += (uint32_t)(P.interp[1] ? (u1 >> 1) : u1) * gc.gst[1];
-      }
+      const uint32_t grow = (uint32_t)u0 * g.gst[0] + (uint32_t)u1 * g.gst[1];
+      const uint32_t crow = (uint32_t)(u0 / stp[0]) * gc.gst[0] +
+                            (uint32_t)(u1 / stp[1]) * gc.gst[1] +
+                            (uint32_t)(st0[2] / stp[2]);
+      const int rsm = R.row(u0, u1);
       for (int a2 = lane; a2 < cn[2]; a2 += 32) {
         const int u2 = st0[2] + a2 * stp[2];
-        int kind = B.kind, same = B.same;
-        if (B.blockmap) {
-          const unsigned v = B.blockmap[brow + ((uint32_t)u2 * g.step[2]) / B.bs];
-          kind = (int)(v & 3u);
-          if (kind > CUBIC_NAT) kind = CUBIC_NAT;
-          same = (int)((v >> 2) & 1u);
-        }
-        if (kind == LINEAR) same = 0;
-        const int ud = d == 0 ? u0 : (d == 1 ? u1 : u2);
-        const int in_b = same && (((ud - 1) >> 1) & 1);
-        if (in_b != S.half) continue;
-        const int idx = rsm + u2;
-        Line L;
-        L.sm = sm;
-        L.idx = idx;
-        L.st = sst[d];
-        L.u = ud;
-        L.lo = lo[d];
-        L.hi = hi[d];
-        L.in_smem = in_smem;
-        L.Rc = Rc;
-        L.cbase = cb_row + (d != 2 ? (uint32_t)(P.interp[2] ? (u2 >> 1) : u2) : 0u);
-        L.cst = gc.gst[d];
-        const float p = predict_at(L, md, kind, in_b);
-        const uint32_t fi = rfull + (uint32_t)u2 * fst2;
-        float rec;
         if (!kDecomp) {
-          const unsigned code = quantize_fast(__ldg(B.x + fi), p, el, inv2, twoe, rec);
-          if (row_in_tile && u2 >= o[2] && u2 < te[2]) ctile[rtile + u2] = (uint16_t)code;
+          Cs[grow + (uint32_t)u2] = Cc[crow + a2];
+          if (P.write_recon) Rs[grow + (uint32_t)u2] = sm[rsm + R.col(u2)];
         } else {
-          const unsigned code = B.codes_full[fi];
-          rec = code ? dequantize(code, p, twoe) : B.outl_full[fi];
+          Rs[grow + (uint32_t)u2] = sm[rsm + R.col(u2)];
         }
-        sm[idx] = rec;
-      }
-    }
-    __syncthreads();
-  }
-
-  // 3. write the tile out, rows to warps, consecutive elements to lanes
-  {
-    const int n0 = te[0] - o[0], n1 = te[1] - o[1], n2 = te[2] - o[2];
-    const int rows = n0 * n1;
-    for (int r = warp; r < rows; r += nwarps) {
-      const int a0 = r / n1, a1 = r - a0 * n1;
-      const int u0 = o[0] + a0, u1 = o[1] + a1;
-      const uint32_t grow = (uint32_t)u0 * g.gst[0] + (uint32_t)u1 * g.gst[1] + (uint32_t)o[2];
-      const float* srow = sm + (u0 - base[0]) * sst[0] + (u1 - base[1]) * RX2 + (o[2] - base[2]);
-      if (!kDecomp) {
-        const bool crow = (!P.interp[0] || !(u0 & 1)) && (!P.interp[1] || !(u1 & 1));
-        const uint32_t ccrow = (uint32_t)(P.interp[0] ? u0 >> 1 : u0) * gc.gst[0] +
-                               (uint32_t)(P.interp[1] ? u1 >> 1 : u1) * gc.gst[1];
-        const uint16_t* trow = ctile + (a0 * E1 + a1) * E2;
-        for (int a2 = lane; a2 < n2; a2 += 32) {
-          const int u2 = o[2] + a2;
-          uint16_t code;
-          if (crow && (!P.interp[2] || !(u2 & 1)))
-            code = Cc[ccrow + (uint32_t)(P.interp[2] ? u2 >> 1 : u2)];
-          else
-            code = trow[a2];
-          Cs[grow + a2] = code;
-          if (P.write_recon) Rs[grow + a2] = srow[a2];
-        }
-      } else {
-        for (int a2 = lane; a2 < n2; a2 += 32) Rs[grow + a2] = srow[a2];
       }
     }
   }
 }
 
-size_t fused_smem_bytes(const FusedLevel& P, bool decomp) {
-  size_t b = (size_t)P.RX[0] * P.RX[1] * P.RX[2] * sizeof(float);
-  if (!decomp) b += (size_t)P.E[0] * P.E[1] * P.E[2] * sizeof(uint16_t);
-  return b;
+template <bool kDecomp, int KIND>
+static void launch_kind(const FusedLevel& P, const SweepBufs& B, size_t smem,
+                        const float* Rc, const uint16_t* Cc, float* Rs,
+                        uint16_t* Cs, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_level<kDecomp, KIND>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_level<kDecomp, KIND><<<P.ntiles, 256, smem, s>>>(P, B, Rc, Cc, Rs, Cs);
+}
+
+template <bool kDecomp>
+static void launch_dec(const FusedLevel& P, const SweepBufs& B, size_t smem,
+                       const float* Rc, const uint16_t* Cc, float* Rs,
+                       uint16_t* Cs, cudaStream_t s) {
+  // a fixed interpolator compiles to straight-line code; a block map (or
+  // a same-level level) takes the per-point path
+  const int kind = (B.blockmap || B.same) ? 3 : B.kind;
+  switch (kind) {
+    case LINEAR: launch_kind<kDecomp, LINEAR>(P, B, smem, Rc, Cc, Rs, Cs, s); break;
+    case CUBIC_NAK: launch_kind<kDecomp, CUBIC_NAK>(P, B, smem, Rc, Cc, Rs, Cs, s); break;
+    case CUBIC_NAT: launch_kind<kDecomp, CUBIC_NAT>(P, B, smem, Rc, Cc, Rs, Cs, s); break;
+    default: launch_kind<kDecomp, 3>(P, B, smem, Rc, Cc, Rs, Cs, s); break;
+  }
 }
 
 void launch_level(bool decomp, const FusedLevel& P, const SweepBufs& B,
                   const float* Rc, const uint16_t* Cc, float* Rs, uint16_t* Cs,
                   cudaStream_t s) {
   const size_t smem = fused_smem_bytes(P, decomp);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_level<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    cudaFuncSetAttribute(k_level<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    attr = true;
-  }
   if (decomp)
-    k_level<true><<<P.ntiles, 256, smem, s>>>(P, B, Rc, Cc, Rs, Cs);
+    launch_dec<true>(P, B, smem, Rc, Cc, Rs, Cs, s);
   else
-    k_level<false><<<P.ntiles, 256, smem, s>>>(P, B, Rc, Cc, Rs, Cs);
+    launch_dec<false>(P, B, smem, Rc, Cc, Rs, Cs, s);
 }
 
 }  // namespace hpez
