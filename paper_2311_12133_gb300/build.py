@@ -72,6 +72,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}{r.stderr}")
+    # every symbol must resolve (a missing device-side definition would
+    # otherwise only show when the library is loaded on the GPU machine)
+    import ctypes
+    ctypes.CDLL(tmp, mode=os.RTLD_NOW)
     os.replace(tmp, LIB)
     return LIB
 

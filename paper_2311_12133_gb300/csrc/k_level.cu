@@ -387,6 +387,11 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+size_t fused_smem_bytes(const FusedLevel& P, bool decomp) {
+  (void)decomp;
+  return (size_t)P.RX[0] * P.RX[1] * P.RX[2] * sizeof(float);
+}
+
 template <bool kDecomp, int KIND>
 static void launch_kind(const FusedLevel& P, const SweepBufs& B, size_t smem,
                         const float* Rc, const uint16_t* Cc, float* Rs,
