@@ -207,71 +207,93 @@ __device__ __forceinline__ void run_step(const FusedLevel& P, const SweepBufs& B
       if (D != 0) cb_row += (uint32_t)(P.interp[0] ? (u0 >> 1) : u0) * gc.gst[0];
       if (D != 1) cb_row += (uint32_t)(P.interp[1] ? (u1 >> 1) : u1) * gc.gst[1];
     }
-    for (int a2 = lane; a2 < cn[2]; a2 += 32) {
-      const int u2 = st0[2] + a2 * stp[2];
-      const int c = u2 - R.base[2];
-      const int sidx = rsm + (c & 1) * R.HX + (c >> 1);
-      float p;
-      int in_b = 0;
-      const bool interior =
-          fast_ok && !B.same && row_interior && (D != 2 || (u2 >= 3 && u2 + 3 <= md - 1));
-      if (interior) {
-        float m3, m1, p1, p3;
-        if (D == 2) {
-          // odd column: even neighbours e-1 .. e+2 of the even half-row
-          const int e = rsm + (c >> 1);
-          m3 = sm[e - 1];
-          m1 = sm[e];
-          p1 = sm[e + 1];
-          p3 = sm[e + 2];
+    // batches of kBatch points per lane: all their global loads (input
+    // value or code) are issued before any of them is computed, so each
+    // lane keeps several memory requests in flight
+    constexpr int kBatch = 4;
+    for (int a2b = lane; a2b < cn[2]; a2b += 32 * kBatch) {
+      float xin[kBatch];
+      unsigned cin[kBatch];
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k) {
+        const int a2 = a2b + 32 * k;
+        xin[k] = 0.f;
+        cin[k] = 0u;
+        if (a2 < cn[2]) {
+          const uint32_t fi = rfull + (uint32_t)(st0[2] + a2 * stp[2]) * K.fst2;
+          if (!kDecomp)
+            xin[k] = __ldg(B.x + fi);
+          else
+            cin[k] = B.codes_full[fi];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k) {
+        const int a2 = a2b + 32 * k;
+        if (a2 >= cn[2]) break;
+        const int u2 = st0[2] + a2 * stp[2];
+        const int c = u2 - R.base[2];
+        const int sidx = rsm + (c & 1) * R.HX + (c >> 1);
+        float p;
+        const bool interior =
+            fast_ok && !B.same && row_interior && (D != 2 || (u2 >= 3 && u2 + 3 <= md - 1));
+        if (interior) {
+          float m3, m1, p1, p3;
+          if (D == 2) {
+            // odd column: even neighbours e-1 .. e+2 of the even half-row
+            const int e = rsm + (c >> 1);
+            m3 = sm[e - 1];
+            m1 = sm[e];
+            p1 = sm[e + 1];
+            p3 = sm[e + 2];
+          } else {
+            m3 = sm[sidx - 3 * nst];
+            m1 = sm[sidx - nst];
+            p1 = sm[sidx + nst];
+            p3 = sm[sidx + 3 * nst];
+          }
+          p = interior_k<KIND>(m3, m1, p1, p3);
         } else {
-          m3 = sm[sidx - 3 * nst];
-          m1 = sm[sidx - nst];
-          p1 = sm[sidx + nst];
-          p3 = sm[sidx + 3 * nst];
+          int kind = KIND == 3 ? B.kind : KIND, same = B.same;
+          if (KIND == 3 && B.blockmap) {
+            const unsigned v = B.blockmap[brow + ((uint32_t)u2 * g.step[2]) / B.bs];
+            kind = (int)(v & 3u);
+            if (kind > CUBIC_NAT) kind = CUBIC_NAT;
+            same = (int)((v >> 2) & 1u);
+          }
+          if (kind == LINEAR) same = 0;
+          const int ud = D == 0 ? u0 : (D == 1 ? u1 : u2);
+          const int in_b = same && (((ud - 1) >> 1) & 1);
+          if (in_b != S.half) continue;
+          Nbr<D> n;
+          n.sm = sm;
+          n.R = &R;
+          n.r = rsm;
+          n.u0 = u0;
+          n.u1 = u1;
+          n.u2 = u2;
+          n.in_smem = in_smem;
+          n.Rc = Rc;
+          n.cbase = cb_row + (D != 2 ? (uint32_t)(P.interp[2] ? (u2 >> 1) : u2) : 0u);
+          n.cst = gc.gst[D];
+          p = predict_nbr<KIND, D>(n, ud, md, kind, in_b);
         }
-        p = interior_k<KIND>(m3, m1, p1, p3);
-      } else {
-        int kind = KIND == 3 ? B.kind : KIND, same = B.same;
-        if (KIND == 3 && B.blockmap) {
-          const unsigned v = B.blockmap[brow + ((uint32_t)u2 * g.step[2]) / B.bs];
-          kind = (int)(v & 3u);
-          if (kind > CUBIC_NAT) kind = CUBIC_NAT;
-          same = (int)((v >> 2) & 1u);
+        const bool in_tile = row_in_tile && u2 >= R.o[2] && u2 < R.te[2];
+        float rec;
+        if (!kDecomp) {
+          const unsigned code = quantize_fast(xin[k], p, K.el, K.inv2, K.twoe, rec);
+          if (in_tile) {
+            Cs[rgrid + (uint32_t)u2] = (uint16_t)code;
+            if (P.write_recon) Rs[rgrid + (uint32_t)u2] = rec;
+          }
+        } else {
+          const unsigned code = cin[k];
+          rec = code ? dequantize(code, p, K.twoe)
+                     : B.outl_full[rfull + (uint32_t)u2 * K.fst2];
+          if (in_tile) Rs[rgrid + (uint32_t)u2] = rec;
         }
-        if (kind == LINEAR) same = 0;
-        const int ud = D == 0 ? u0 : (D == 1 ? u1 : u2);
-        in_b = same && (((ud - 1) >> 1) & 1);
-        if (in_b != S.half) continue;
-        Nbr<D> n;
-        n.sm = sm;
-        n.R = &R;
-        n.r = rsm;
-        n.u0 = u0;
-        n.u1 = u1;
-        n.u2 = u2;
-        n.in_smem = in_smem;
-        n.Rc = Rc;
-        n.cbase = cb_row + (D != 2 ? (uint32_t)(P.interp[2] ? (u2 >> 1) : u2) : 0u);
-        n.cst = gc.gst[D];
-        p = predict_nbr<KIND, D>(n, ud, md, kind, in_b);
+        sm[sidx] = rec;
       }
-      if (interior && S.half != 0) continue;  // fixed interpolator: no half B
-      const uint32_t fi = rfull + (uint32_t)u2 * K.fst2;
-      const bool in_tile = row_in_tile && u2 >= R.o[2] && u2 < R.te[2];
-      float rec;
-      if (!kDecomp) {
-        const unsigned code = quantize_fast(__ldg(B.x + fi), p, K.el, K.inv2, K.twoe, rec);
-        if (in_tile) {
-          Cs[rgrid + (uint32_t)u2] = (uint16_t)code;
-          if (P.write_recon) Rs[rgrid + (uint32_t)u2] = rec;
-        }
-      } else {
-        const unsigned code = B.codes_full[fi];
-        rec = code ? dequantize(code, p, K.twoe) : B.outl_full[fi];
-        if (in_tile) Rs[rgrid + (uint32_t)u2] = rec;
-      }
-      sm[sidx] = rec;
     }
   }
 }
@@ -337,6 +359,7 @@ __global__ void __launch_bounds__(256)
                             (uint32_t)(u1 / stp[1]) * gc.gst[1] +
                             (uint32_t)(st0[2] / stp[2]);
       const int rsm = R.row(u0, u1);
+#pragma unroll 4
       for (int a2 = lane; a2 < cn[2]; a2 += 32)
         sm[rsm + R.col(st0[2] + a2 * stp[2])] = __ldg(Rc + crow + a2);
     }
@@ -374,6 +397,7 @@ __global__ void __launch_bounds__(256)
                             (uint32_t)(u1 / stp[1]) * gc.gst[1] +
                             (uint32_t)(st0[2] / stp[2]);
       const int rsm = R.row(u0, u1);
+#pragma unroll 4
       for (int a2 = lane; a2 < cn[2]; a2 += 32) {
         const int u2 = st0[2] + a2 * stp[2];
         if (!kDecomp) {
