@@ -73,6 +73,8 @@ struct hpez_ctx {
   PhaseProfiler prof;
   uint64_t launches = 0;
   int fused_levels = 1;        // HPEZ_OPT_FUSED_LEVELS
+  bool x_aligned16 = true;     // per call: input pointer 16-byte aligned
+  bool codes_aligned16 = true;
   int tile_e[3] = {0, 0, 0};   // HPEZ_OPT_TILE_E0..2 (0 = heuristic)
   size_t fused_smem_cap = 96 * 1024;
   int device = 0;
@@ -375,9 +377,9 @@ bool plan_fused(const hpez_ctx* ctx, const Plan& p, const hpez_config& c,
   // a slot the tile covers whole needs no halo
   auto halo = [&](int s) { return E[s] >= m[s] ? 0 : hA[0][s]; };
   auto smem = [&]() {
-    size_t b = 4;
+    size_t b = decomp ? 6 : 4;  // decompress stages the codes as well
     for (int s = 0; s < 3; ++s)
-      b *= (size_t)(E[s] + 2 * halo(s) + (s == 2 ? 3 : 0));
+      b *= (size_t)(E[s] + 2 * halo(s) + (s == 2 ? 14 : 0));
     return b;
   };
   while (smem() > ctx->fused_smem_cap) {
@@ -392,12 +394,12 @@ bool plan_fused(const hpez_ctx* ctx, const Plan& p, const hpez_config& c,
   uint64_t nt = 1;
   for (int s = 0; s < 3; ++s) {
     F.E[s] = E[s];
-    // along the fastest slot the region starts on an even column and has
-    // an even length (the shared-memory rows split even and odd columns)
-    const int h = s == 2 ? ((halo(s) + 1) & ~1) : halo(s);
+    // along the fastest slot the region is padded to multiples of 8
+    // columns, so staged rows start on 16-byte (8-code) boundaries
+    const int h = s == 2 ? ((halo(s) + 7) & ~7) : halo(s);
     F.rlo[s] = -h;
     F.rhi[s] = (int)E[s] + h;
-    if (s == 2 && ((F.rhi[s] - F.rlo[s]) & 1)) F.rhi[s] += 1;
+    if (s == 2) F.rhi[s] = F.rlo[s] + (((F.rhi[s] - F.rlo[s]) + 7) & ~7);
     F.RX[s] = (uint32_t)(F.rhi[s] - F.rlo[s]);
     F.ntile[s] = (m[s] + E[s] - 1) / E[s];
     nt *= F.ntile[s];
@@ -426,6 +428,18 @@ bool plan_fused(const hpez_ctx* ctx, const Plan& p, const hpez_config& c,
   }
   F.level = l;
   F.write_recon = (decomp || l > 1) ? 1 : 0;
+  // staging: rows of the level grid are contiguous in the full field only
+  // at stride 1 along the fastest slot; 16-byte copies need rows, the tile
+  // and the region to start on 16-byte boundaries
+  F.stage_x = 0;
+  const bool contig = F.g.step[2] == 1;
+  const bool al4 = (p.n[2] % 4 == 0) && (F.g.m[2] == p.n[2]) && (F.E[2] % 4 == 0 || F.E[2] >= m[2]);
+  const bool al8 = (p.n[2] % 8 == 0) && (F.g.m[2] == p.n[2]) && (F.E[2] % 8 == 0 || F.E[2] >= m[2]);
+  if (!decomp) {
+    F.stage_x = (contig && al4 && ctx->x_aligned16) ? 2 : 1;
+  } else {
+    F.stage_x = (contig && al8 && ctx->codes_aligned16) ? 1 : 0;
+  }
   return true;
 }
 
@@ -722,6 +736,7 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   plan_chunks_blocks(p, cfg);
   cudaSetDevice(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ctx->x_aligned16 = (reinterpret_cast<uintptr_t>(d_in) & 15u) == 0;
 
   // scratch layout
   Arena ar;

@@ -294,6 +294,8 @@ struct FusedLevel {
   FusedStep st[6];
   int level;
   int write_recon;
+  int stage_x;   // compress: 1 = 4-byte async copies of the input, 2 = 16-byte;
+                 // decompress: 1 = 16-byte async copies of the codes; 0 = none
 };
 
 }  // namespace hpez

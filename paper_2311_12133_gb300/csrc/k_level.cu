@@ -40,19 +40,28 @@ __device__ __forceinline__ unsigned quantize_fast(float x, float p, float el,
 
 // ---------------------------------------------------------------------
 // Shared-memory layout of the CTA's region: rows (slot 0, slot 1) of RX2
-// columns; along the fastest slot the even and odd grid columns are kept
-// in separate halves of the row (the region starts on an even column), so
-// a pass along that slot -- odd points, even neighbours -- and every other
-// pass read consecutive words across a warp.
+// columns in grid order.  Before the passes the region holds the input
+// values (staged with asynchronous copies); the coarse points are then
+// overwritten with their reconstruction, and each pass replaces a point's
+// input value by its reconstruction, which later passes read.
 // ---------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::);
+}
 struct Region {
   int o[3], base[3], lo[3], hi[3], te[3];
   int RX1, RX2, HX;        // row length, half-row length
   int rst0, rst1;          // element stride of a step along slot 0 / 1
-  __device__ __forceinline__ int col(int u2) const {
-    const int c = u2 - base[2];
-    return (c & 1) * HX + (c >> 1);
-  }
+  __device__ __forceinline__ int col(int u2) const { return u2 - base[2]; }
   __device__ __forceinline__ int row(int u0, int u1) const {
     return (u0 - base[0]) * rst0 + (u1 - base[1]) * rst1;
   }
@@ -160,6 +169,7 @@ template <bool kDecomp, int KIND, int D>
 __device__ __forceinline__ void run_step(const FusedLevel& P, const SweepBufs& B,
                                          const FusedStep& S, const Region& R,
                                          const LevelConsts& K, float* sm,
+                                         const uint16_t* scodes,
                                          const float* __restrict__ Rc,
                                          float* __restrict__ Rs,
                                          uint16_t* __restrict__ Cs) {
@@ -220,11 +230,14 @@ __device__ __forceinline__ void run_step(const FusedLevel& P, const SweepBufs& B
         xin[k] = 0.f;
         cin[k] = 0u;
         if (a2 < cn[2]) {
-          const uint32_t fi = rfull + (uint32_t)(st0[2] + a2 * stp[2]) * K.fst2;
-          if (!kDecomp)
-            xin[k] = __ldg(B.x + fi);
-          else
-            cin[k] = B.codes_full[fi];
+          const int u2 = st0[2] + a2 * stp[2];
+          if (!kDecomp) {
+            xin[k] = P.stage_x ? sm[rsm + (u2 - R.base[2])]
+                               : __ldg(B.x + rfull + (uint32_t)u2 * K.fst2);
+          } else {
+            cin[k] = P.stage_x ? scodes[rsm + (u2 - R.base[2])]
+                               : B.codes_full[rfull + (uint32_t)u2 * K.fst2];
+          }
         }
       }
 #pragma unroll
@@ -232,20 +245,17 @@ __device__ __forceinline__ void run_step(const FusedLevel& P, const SweepBufs& B
         const int a2 = a2b + 32 * k;
         if (a2 >= cn[2]) break;
         const int u2 = st0[2] + a2 * stp[2];
-        const int c = u2 - R.base[2];
-        const int sidx = rsm + (c & 1) * R.HX + (c >> 1);
+        const int sidx = rsm + (u2 - R.base[2]);
         float p;
         const bool interior =
             fast_ok && !B.same && row_interior && (D != 2 || (u2 >= 3 && u2 + 3 <= md - 1));
         if (interior) {
           float m3, m1, p1, p3;
           if (D == 2) {
-            // odd column: even neighbours e-1 .. e+2 of the even half-row
-            const int e = rsm + (c >> 1);
-            m3 = sm[e - 1];
-            m1 = sm[e];
-            p1 = sm[e + 1];
-            p3 = sm[e + 2];
+            m3 = sm[sidx - 3];
+            m1 = sm[sidx - 1];
+            p1 = sm[sidx + 1];
+            p3 = sm[sidx + 3];
           } else {
             m3 = sm[sidx - 3 * nst];
             m1 = sm[sidx - nst];
@@ -342,6 +352,34 @@ __global__ void __launch_bounds__(256)
   K.fst1 = g.step[1] * g.fst[1];
   K.fst2 = g.step[2];
 
+  // 0. stage the region's input values (compress) or codes (decompress)
+  uint16_t* scodes = reinterpret_cast<uint16_t*>(sm + P.RX[0] * P.RX[1] * P.RX[2]);
+  if (P.stage_x) {
+    const int ncol = R.hi[2] - R.lo[2];
+    const int rows = (R.hi[0] - R.lo[0]) * (R.hi[1] - R.lo[1]);
+    const int n1 = R.hi[1] - R.lo[1];
+    for (int r = warp; r < rows; r += nwarps) {
+      const int u0 = R.lo[0] + r / n1, u1 = R.lo[1] + r % n1;
+      const int rsm = R.row(u0, u1) + (R.lo[2] - R.base[2]);
+      const uint32_t rfull = (uint32_t)u0 * K.fst0 + (uint32_t)u1 * K.fst1 +
+                             (uint32_t)R.lo[2] * K.fst2;
+      if (!kDecomp) {
+        if (P.stage_x == 2) {  // 16-byte copies, rows 16-byte aligned
+          for (int c4 = lane * 4; c4 < ncol; c4 += 128)
+            cp_async16(sm + rsm + c4, B.x + rfull + c4);
+        } else {
+          for (int c = lane; c < ncol; c += 32)
+            cp_async4(sm + rsm + c, B.x + rfull + (uint32_t)c * K.fst2);
+        }
+      } else {
+        for (int c8 = lane * 8; c8 < ncol; c8 += 256)
+          cp_async16(scodes + rsm + c8, B.codes_full + rfull + c8);
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+  }
+
   // 1. coarse points of the region (all interpolation coordinates even)
   {
     int st0[3], cn[3], stp[3];
@@ -370,11 +408,11 @@ __global__ void __launch_bounds__(256)
   for (int si = 0; si < P.nsteps; ++si) {
     const FusedStep& S = P.st[si];
     if (S.dim == 2)
-      run_step<kDecomp, KIND, 2>(P, B, S, R, K, sm, Rc, Rs, Cs);
+      run_step<kDecomp, KIND, 2>(P, B, S, R, K, sm, scodes, Rc, Rs, Cs);
     else if (S.dim == 1)
-      run_step<kDecomp, KIND, 1>(P, B, S, R, K, sm, Rc, Rs, Cs);
+      run_step<kDecomp, KIND, 1>(P, B, S, R, K, sm, scodes, Rc, Rs, Cs);
     else
-      run_step<kDecomp, KIND, 0>(P, B, S, R, K, sm, Rc, Rs, Cs);
+      run_step<kDecomp, KIND, 0>(P, B, S, R, K, sm, scodes, Rc, Rs, Cs);
     __syncthreads();
   }
 
@@ -412,8 +450,9 @@ __global__ void __launch_bounds__(256)
 }
 
 size_t fused_smem_bytes(const FusedLevel& P, bool decomp) {
-  (void)decomp;
-  return (size_t)P.RX[0] * P.RX[1] * P.RX[2] * sizeof(float);
+  size_t b = (size_t)P.RX[0] * P.RX[1] * P.RX[2] * sizeof(float);
+  if (decomp && P.stage_x) b += (size_t)P.RX[0] * P.RX[1] * P.RX[2] * sizeof(uint16_t);
+  return b;
 }
 
 template <bool kDecomp, int KIND>
