@@ -145,12 +145,15 @@ HPEZ_API const char* hpez_strerror(int code);
  *  HPEZ_OPT_TILE_E0..2    tile extent of that slot of the level grid for
  *                         the fused kernel (0 = built-in heuristic)
  *  HPEZ_OPT_FUSED_SMEM    shared-memory cap in bytes for a fused tile
+ *  HPEZ_OPT_LEVEL3D       1 (default): 3D levels in direction order 0,1,2
+ *                         with one interpolator use the dedicated kernel
  * Errors: INVALID_ARG for an unknown option or an out-of-range value. */
 #define HPEZ_OPT_FUSED_LEVELS 1
 #define HPEZ_OPT_TILE_E0 2
 #define HPEZ_OPT_TILE_E1 3
 #define HPEZ_OPT_TILE_E2 4
 #define HPEZ_OPT_FUSED_SMEM 5
+#define HPEZ_OPT_LEVEL3D 6
 HPEZ_API int hpez_set_option(hpez_ctx* ctx, int option, int64_t value);
 
 /* ---- measurement hooks (not part of the paper's method) ----

@@ -21,8 +21,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libhpez.so")
-SOURCES = ["hpez_capi.cu", "k_sweep.cu", "k_level.cu", "k_huffman.cu",
-           "k_stream.cu"]
+SOURCES = ["hpez_capi.cu", "k_sweep.cu", "k_level.cu", "k_level3d.cu",
+           "k_huffman.cu", "k_stream.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

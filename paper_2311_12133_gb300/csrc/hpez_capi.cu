@@ -73,6 +73,7 @@ struct hpez_ctx {
   PhaseProfiler prof;
   uint64_t launches = 0;
   int fused_levels = 1;        // HPEZ_OPT_FUSED_LEVELS
+  int level3d = 1;             // HPEZ_OPT_LEVEL3D
   bool x_aligned16 = true;     // per call: input pointer 16-byte aligned
   bool codes_aligned16 = true;
   int tile_e[3] = {0, 0, 0};   // HPEZ_OPT_TILE_E0..2 (0 = heuristic)
@@ -443,6 +444,41 @@ bool plan_fused(const hpez_ctx* ctx, const Plan& p, const hpez_config& c,
   return true;
 }
 
+// The dedicated 3D kernel applies to levels of a 3D field with no frozen
+// dimension, the 1D-style order (0, 1, 2), one interpolator and no
+// same-level halves; whole rows along dim 2 must fit shared memory.
+bool plan_level3d(const hpez_ctx* ctx, const Plan& p, const hpez_config& c,
+                  int l, bool decomp, Level3D& F) {
+  if (!ctx->level3d || p.ndim != 3 || p.k != 3 || c.blockwise) return false;
+  if (c.paradigm[l - 1] != HPEZ_PARADIGM_1D) return false;
+  if (c.order[l - 1][0] != 0 || c.order[l - 1][1] != 1 || c.order[l - 1][2] != 2)
+    return false;
+  if (c.interp[l - 1] != HPEZ_LINEAR && c.same_level[l - 1]) return false;
+  const LevelGeom& g = p.grid[l - 1];
+  const LevelGeom& gc = p.grid[l];
+  std::memset(&F, 0, sizeof(F));
+  for (int s = 0; s < 3; ++s) F.m[s] = (int)g.m[s];
+  F.E1 = ctx->tile_e[1] > 0 ? ctx->tile_e[1] : 8;
+  if (F.E1 & 1) F.E1 += 1;
+  F.W = (F.m[2] + 7) & ~7;
+  F.fs0 = g.step[0] * g.fst[0];
+  F.fs1 = g.step[1] * g.fst[1];
+  F.fs2 = g.step[2];
+  F.cst0 = gc.gst[0];
+  F.cst1 = gc.gst[1];
+  F.level = l;
+  F.write_recon = (decomp || l > 1) ? 1 : 0;
+  const bool contig = g.step[2] == 1;
+  F.stage16 = (!decomp && contig && (p.n[2] % 4 == 0) && ctx->x_aligned16) ? 1 : 0;
+  F.stage_codes = (decomp && contig && (p.n[2] % 8 == 0) && ctx->codes_aligned16) ? 1 : 0;
+  while (level3d_smem_bytes(F, decomp) > ctx->fused_smem_cap && F.E1 > 2) F.E1 -= 2;
+  if (level3d_smem_bytes(F, decomp) > ctx->fused_smem_cap) return false;
+  F.nt0 = (F.m[0] + 1) / 2;
+  F.nt1 = (F.m[1] + F.E1 - 1) / F.E1;
+  if ((uint64_t)F.nt0 * (uint64_t)F.nt1 > 0x7FFFFFFFull) return false;
+  return true;
+}
+
 // ---------------------------------------------------------------------
 // scratch arena
 // ---------------------------------------------------------------------
@@ -629,6 +665,9 @@ int hpez_set_option(hpez_ctx* ctx, int option, int64_t value) {
     case HPEZ_OPT_TILE_E2:
       if (value < 0 || value > 4096) return HPEZ_ERR_INVALID_ARG;
       ctx->tile_e[option - HPEZ_OPT_TILE_E0] = (int)value;
+      return HPEZ_OK;
+    case HPEZ_OPT_LEVEL3D:
+      ctx->level3d = value != 0;
       return HPEZ_OK;
     case HPEZ_OPT_FUSED_SMEM:
       if (value < 4096 || value > 200 * 1024) return HPEZ_ERR_INVALID_ARG;
@@ -828,7 +867,11 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
     sb.kind = cfg.interp[l - 1];
     sb.same = cfg.same_level[l - 1];
     FusedLevel F;
-    if (ctx->fused_levels && plan_fused(ctx, p, cfg, l, false, F)) {
+    Level3D F3;
+    if (ctx->fused_levels && plan_level3d(ctx, p, cfg, l, false, F3)) {
+      launch_level3d(false, F3, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g], s);
+      ++nl;
+    } else if (ctx->fused_levels && plan_fused(ctx, p, cfg, l, false, F)) {
       launch_level(false, F, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g], s);
       ++nl;
     } else {
@@ -1057,7 +1100,11 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
     sb.kind = cfg.interp[l - 1];
     sb.same = cfg.same_level[l - 1];
     FusedLevel F;
-    if (ctx->fused_levels && plan_fused(ctx, p, cfg, l, true, F)) {
+    Level3D F3;
+    if (ctx->fused_levels && plan_level3d(ctx, p, cfg, l, true, F3)) {
+      launch_level3d(true, F3, sb, R[l], nullptr, R[g], nullptr, s);
+      ++nl;
+    } else if (ctx->fused_levels && plan_fused(ctx, p, cfg, l, true, F)) {
       launch_level(true, F, sb, R[l], nullptr, R[g], nullptr, s);
       ++nl;
     } else {

@@ -298,4 +298,19 @@ struct FusedLevel {
                  // decompress: 1 = 16-byte async copies of the codes; 0 = none
 };
 
+// The dedicated 3D level kernel (direction order 0,1,2, one interpolator,
+// no same-level halves): tiles of 2 planes x E1 rows x whole rows.
+struct Level3D {
+  int m[3];          // level grid extents
+  int E1;            // tile rows
+  int W;             // shared-memory row length (m[2] rounded up to 8)
+  int nt0, nt1;      // tiles along dims 0 and 1
+  uint32_t fs0, fs1, fs2;  // full-field element strides of level-grid steps
+  uint32_t cst0, cst1;     // coarse-grid strides
+  int level;
+  int write_recon;
+  int stage16;       // compress: input rows staged with 16-byte copies
+  int stage_codes;   // decompress: code rows staged (16-byte copies)
+};
+
 }  // namespace hpez
