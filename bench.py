@@ -326,7 +326,10 @@ def main():
     value = world * 4 * N / (ms_per_step / 1e3) / 1e9
 
     # correctness of what was timed: bound held at every point
-    e_abs = hpez.hpez_inspect(cbuf[:512].cpu().numpy().tobytes())[2]
+    hdr = cbuf[:512].cpu().numpy().tobytes()
+    e_abs = hpez.hpez_inspect(hdr)[2]
+    n_out = int.from_bytes(hdr[224:232], "little")
+    n_used = int.from_bytes(hdr[232:236], "little")
     err = (y.double() - x.double()).abs().max().item()
     assert err <= e_abs, f"error bound violated: {err} > {e_abs}"
 
@@ -395,7 +398,8 @@ def main():
             "compress_gbps": round(world * 4 * N / (comp_ms / args.steps / 1e3) / 1e9, 3),
             "decompress_gbps": round(world * 4 * N / (dec_ms / args.steps / 1e3) / 1e9, 3),
             "compression_ratio": round(4 * N / size, 3),
-            "max_abs_err": err, "abs_eb": e_abs,
+            "max_abs_err": err, "abs_eb": e_abs, "n_outliers": n_out,
+            "n_symbols": n_used,
             "roofline": roofline, "phases": phase_report,
             "gpu_launches": int(launches),
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,

@@ -403,7 +403,11 @@ __global__ void k_chunk_words(const uint8_t* __restrict__ lanebits_bytes,
 }
 
 // ---------------------------------------------------------------------
-// outlier gather (compress) / scatter (decompress), row-major order
+// outlier gather (compress) / scatter (decompress), row-major order.
+// One CTA per chunk; CTAs of chunks without an outlier leave at once.
+// Each thread counts the escapes (code 0) in a contiguous run of the
+// chunk, a block scan turns the counts into ranks, and the thread moves
+// its outliers in order.
 // ---------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
     k_outliers(bool gather, const uint16_t* __restrict__ codes, uint32_t N,
@@ -412,29 +416,40 @@ __global__ void __launch_bounds__(256)
                float* dst, uint8_t* stream, unsigned long long max_out,
                Ctl* ctl) {
   if (ctl->status || ctl->is_const) return;
-  const int lane = threadIdx.x & 31;
-  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t c = blockIdx.x;
+  if (c >= nch || zc[c] == 0) return;
   float* outl = reinterpret_cast<float*>(stream + ctl->off_outliers);
-  for (uint32_t c = warp; c < nch; c += nwarps) {
-    if (zc[c] == 0) continue;
-    const uint32_t beg = c * C, end = min(beg + C, N);
-    unsigned long long base = zoff[c];
-    for (uint32_t i0 = beg; i0 < end; i0 += 32) {
-      const uint32_t i = i0 + lane;
-      const bool z = i < end && codes[i] == 0;
-      const unsigned mask = __ballot_sync(0xffffffffu, z);
-      if (z) {
-        const unsigned long long k = base + __popc(mask & ((1u << lane) - 1u));
-        if (k >= max_out)  // more escapes than stored outliers: corrupt
-          atomicExch(&ctl->status, ST_CORRUPT);
-        else if (gather)
-          outl[k] = src[i];
-        else
-          dst[i] = outl[k];
-      }
-      base += __popc(mask);
+  const uint32_t beg = c * C, end = min(beg + C, N);
+  const uint32_t per = (C + blockDim.x - 1) / blockDim.x;
+  const uint32_t tb = min(beg + threadIdx.x * per, end), te = min(tb + per, end);
+  uint32_t mine = 0;
+  const bool vec = (per % 8 == 0) && (te - tb == per);
+  if (vec) {
+    const uint4* p = reinterpret_cast<const uint4*>(codes + tb);
+    for (uint32_t k = 0; k < per / 8; ++k) {
+      const uint4 v = p[k];
+      const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) mine += ((w[q] & 0xFFFFu) == 0) + ((w[q] >> 16) == 0);
     }
+  } else {
+    for (uint32_t i = tb; i < te; ++i) mine += codes[i] == 0;
+  }
+  uint32_t total;
+  uint32_t rank = block_exclusive_scan(mine, &total);
+  if (mine == 0) return;
+  unsigned long long k = zoff[c] + rank;
+  for (uint32_t i = tb; i < te; ++i) {
+    if (codes[i] != 0) continue;
+    if (k >= max_out) {  // more escapes than stored outliers: corrupt
+      atomicExch(&ctl->status, ST_CORRUPT);
+      return;
+    }
+    if (gather)
+      outl[k] = src[i];
+    else
+      dst[i] = outl[k];
+    ++k;
   }
 }
 
@@ -698,8 +713,8 @@ void launch_outliers(bool gather, const uint16_t* codes, uint32_t N,
                      const unsigned long long* zoff, const float* src,
                      float* dst, uint8_t* stream, unsigned long long max_out,
                      Ctl* ctl, int num_sms, cudaStream_t s) {
-  k_outliers<<<warps_grid(nch, num_sms), 256, 0, s>>>(
-      gather, codes, N, C, nch, zc, zoff, src, dst, stream, max_out, ctl);
+  k_outliers<<<nch, 256, 0, s>>>(gather, codes, N, C, nch, zc, zoff, src, dst,
+                                 stream, max_out, ctl);
 }
 
 void launch_dec_tables(const uint8_t* stream, uint32_t n_used,
