@@ -76,6 +76,7 @@ struct hpez_ctx {
   int level3d = 1;             // HPEZ_OPT_LEVEL3D
   bool x_aligned16 = true;     // per call: input pointer 16-byte aligned
   bool codes_aligned16 = true;
+  bool out_aligned16 = true;   // per call: decompress output 16-byte aligned
   int tile_e[3] = {0, 0, 0};   // HPEZ_OPT_TILE_E0..2 (0 = heuristic)
   size_t fused_smem_cap = 96 * 1024;
   int device = 0;
@@ -456,8 +457,12 @@ bool plan_level3d(const hpez_ctx* ctx, const Plan& p, const hpez_config& c,
   if (c.interp[l - 1] != HPEZ_LINEAR && c.same_level[l - 1]) return false;
   const LevelGeom& g = p.grid[l - 1];
   const LevelGeom& gc = p.grid[l];
+  if (g.m[2] < 8) return false;
   std::memset(&F, 0, sizeof(F));
   for (int s = 0; s < 3; ++s) F.m[s] = (int)g.m[s];
+  // whole rows of the level grids start on 16-byte boundaries when the
+  // row length is a multiple of 4 (the arena aligns every grid to 256 B)
+  F.vec_out = (g.m[2] % 4 == 0 && (l > 1 || !decomp || ctx->out_aligned16)) ? 1 : 0;
   F.E1 = ctx->tile_e[1] > 0 ? ctx->tile_e[1] : 8;
   if (F.E1 & 1) F.E1 += 1;
   F.W = (F.m[2] + 7) & ~7;
@@ -949,6 +954,8 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   if (!ctx || !d_in || !d_out) return HPEZ_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(d_in) & 15u) != 0) return HPEZ_ERR_INVALID_ARG;
   if (in_size < (uint64_t)kHeaderBytes) return HPEZ_ERR_CORRUPT_STREAM;
+  if ((reinterpret_cast<uintptr_t>(d_out) & 3u) != 0) return HPEZ_ERR_INVALID_ARG;
+  ctx->out_aligned16 = (reinterpret_cast<uintptr_t>(d_out) & 15u) == 0;
   cudaSetDevice(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int rc = cuda_check(cudaMemcpyAsync(ctx->h_hdr, d_in, kHeaderBytes,

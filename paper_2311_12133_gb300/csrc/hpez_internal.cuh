@@ -311,6 +311,7 @@ struct Level3D {
   int write_recon;
   int stage16;       // compress: input rows staged with 16-byte copies
   int stage_codes;   // decompress: code rows staged (16-byte copies)
+  int vec_out;       // rows of the output grids start 16-byte aligned
 };
 
 }  // namespace hpez

@@ -65,6 +65,22 @@ __device__ __forceinline__ unsigned quant(float x, float p, float el, float inv2
 
 }  // namespace
 
+// The stencil of a point from which neighbours exist along its line.
+template <int KIND>
+__device__ __forceinline__ int edge_formula(bool hm3, bool hp1, bool hp3) {
+  if (!hp1) return hm3 ? F_EXTRAP : F_COPY;
+  if (KIND == LINEAR) return F_LIN;
+  if (hm3 && hp3) return KIND == CUBIC_NAK ? F_NAK4 : F_NAT4;
+  if (hm3) return KIND == CUBIC_NAK ? F_NAK3L : F_NAT3L;
+  if (hp3) return KIND == CUBIC_NAK ? F_NAK3R : F_NAT3R;
+  return F_LIN;
+}
+
+// Shared-memory layout: region values [2 planes][RR rows][W] (input values
+// first, reconstructions once computed); compress adds the tile's codes
+// [2][E1][W]; decompress stages the region's codes [2][RR][W].  A lane
+// works on 4 consecutive columns through float4 accesses (conflict-free),
+// and pass 3 writes whole rows of codes / reconstructions to global memory.
 template <bool kDecomp, int KIND>
 __global__ void __launch_bounds__(256)
     k_level3d(Level3D P, const float* __restrict__ X,
@@ -73,12 +89,13 @@ __global__ void __launch_bounds__(256)
               const uint16_t* __restrict__ Cc, float* __restrict__ Rs,
               uint16_t* __restrict__ Cs, const Ctl* __restrict__ ctl) {
   if (ctl->status || ctl->is_const) return;
-  extern __shared__ float sm[];
+  extern __shared__ float4 sm4[];
+  float* sm = reinterpret_cast<float*>(sm4);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = 8;
   const int m0 = P.m[0], m1 = P.m[1], m2 = P.m[2];
-  const int RR = P.E1 + 6;          // region rows: tile rows + 3 on each side
-  const int W = P.W;                // shared-memory row length (>= m2)
+  const int RR = P.E1 + 6;
+  const int W = P.W, W4 = W >> 2;
   const int t1 = blockIdx.x % P.nt1;
   const int t0 = blockIdx.x / P.nt1;
   const int P0 = 2 * t0;
@@ -88,14 +105,18 @@ __global__ void __launch_bounds__(256)
   const int Tlo = R0, Thi = min(R0 + P.E1, m1);
   const int li = P.level - 1;
   const float el = ctl->el[li], inv2 = ctl->inv2[li], twoe = ctl->twoe[li];
-  uint16_t* scode = reinterpret_cast<uint16_t*>(sm + 2 * RR * W);
-  auto srow = [&](int plane, int row) { return plane * RR * W + (row - (R0 - 3)) * W; };
+  // region row (plane, row) starts at float index srow(); code tile rows
+  auto srow = [&](int plane, int row) { return (plane * RR + (row - (R0 - 3))) * W; };
+  uint16_t* ctile = reinterpret_cast<uint16_t*>(sm + 2 * RR * W);  // compress
+  uint16_t* scode = ctile;                                            // decompress
+  auto trow = [&](int plane, int row) { return (plane * P.E1 + (row - R0)) * W; };
   const uint32_t gst0 = (uint32_t)m1 * (uint32_t)m2, gst1 = (uint32_t)m2;
+  const int nc4 = (m2 + 3) >> 2;  // float4 groups per row
 
   // 0. stage the region rows: input values (compress) or codes (decompress)
   {
-    const int nrows = (Rhi - Rlo) * (odd_plane ? 2 : 1);
     const int nr = Rhi - Rlo;
+    const int nrows = nr * (odd_plane ? 2 : 1);
     for (int r = warp; r < nrows; r += NW) {
       const int pl = r / nr, row = Rlo + (r - pl * nr);
       const uint32_t fr = (uint32_t)(P0 + pl) * P.fs0 + (uint32_t)row * P.fs1;
@@ -110,10 +131,11 @@ __global__ void __launch_bounds__(256)
       }
     }
     cp_wait();
-    __syncthreads();
   }
+  __syncthreads();
 
-  // 1. coarse points: plane P0, even rows, even columns
+  // 1. coarse points of plane P0 (even rows, even columns): reconstruction
+  //    for the region, codes for the tile
   {
     const int r0 = (Rlo + 1) & ~1;
     const int nr = (Rhi - r0 + 1) >> 1, nc = (m2 + 1) >> 1;
@@ -121,56 +143,63 @@ __global__ void __launch_bounds__(256)
       const int row = r0 + 2 * r;
       const uint32_t crow = (uint32_t)(P0 >> 1) * P.cst0 + (uint32_t)(row >> 1) * P.cst1;
       const int so = srow(0, row);
+      const bool in_tile = row >= Tlo && row < Thi;
+      const int to = in_tile ? trow(0, row) : 0;
 #pragma unroll 4
-      for (int c = lane; c < nc; c += 32) sm[so + 2 * c] = __ldg(Rc + crow + c);
+      for (int c = lane; c < nc; c += 32) {
+        sm[so + 2 * c] = __ldg(Rc + crow + c);
+        if (!kDecomp && in_tile) ctile[to + 2 * c] = Cc[crow + c];
+      }
     }
   }
   __syncthreads();
 
-  // 2. pass 1 (along dim 0): odd plane, even rows of the region, even columns
+  // 2. pass 1 (along dim 0): the odd plane's even rows (region), even columns
   if (odd_plane) {
     const int u0 = P0 + 1;
     const bool hm3 = u0 >= 3, hp1 = u0 + 1 <= m0 - 1, hp3 = u0 + 3 <= m0 - 1;
-    int f;  // the same stencil for the whole plane
-    if (!hp1) f = hm3 ? F_EXTRAP : F_COPY;
-    else if (KIND == LINEAR) f = F_LIN;
-    else if (hm3 && hp3) f = KIND == CUBIC_NAK ? F_NAK4 : F_NAT4;
-    else if (hm3) f = KIND == CUBIC_NAK ? F_NAK3L : F_NAT3L;
-    else if (hp3) f = KIND == CUBIC_NAK ? F_NAK3R : F_NAT3R;
-    else f = F_LIN;
+    const int f = edge_formula<KIND>(hm3, hp1, hp3);  // one stencil per plane
     const int k0 = P0 >> 1;  // coarse plane of u0 - 1
     const int r0 = (Rlo + 1) & ~1;
-    const int nr = (Rhi - r0 + 1) >> 1, nc = (m2 + 1) >> 1;
+    const int nr = (Rhi - r0 + 1) >> 1;
     for (int r = warp; r < nr; r += NW) {
       const int row = r0 + 2 * r;
       const bool in_tile = row >= Tlo && row < Thi;
       const uint32_t crow = (uint32_t)(row >> 1) * P.cst1;
       const int so = srow(1, row);
-      const uint32_t grow = (uint32_t)u0 * gst0 + (uint32_t)row * gst1;
+      const int to = in_tile ? trow(1, row) : 0;
       const uint32_t fr = (uint32_t)u0 * P.fs0 + (uint32_t)row * P.fs1;
-#pragma unroll 2
-      for (int c = lane; c < nc; c += 32) {
-        const int col = 2 * c;
-        const uint32_t cc = crow + (uint32_t)c;
-        const float m1v = __ldg(Rc + (uint32_t)k0 * P.cst0 + cc);
-        const float p1v = hp1 ? __ldg(Rc + (uint32_t)(k0 + 1) * P.cst0 + cc) : 0.f;
-        const float m3v = hm3 ? __ldg(Rc + (uint32_t)(k0 - 1) * P.cst0 + cc) : 0.f;
-        const float p3v = hp3 ? __ldg(Rc + (uint32_t)(k0 + 2) * P.cst0 + cc) : 0.f;
-        const float p = eval_formula(f, m3v, 0.f, m1v, p1v, 0.f, p3v);
-        float rec;
-        if (!kDecomp) {
-          const unsigned code = quant(sm[so + col], p, el, inv2, twoe, rec);
-          if (in_tile) {
-            Cs[grow + (uint32_t)col] = (uint16_t)code;
-            if (P.write_recon) Rs[grow + (uint32_t)col] = rec;
-          }
-        } else {
-          const unsigned code = P.stage_codes ? scode[so + col]
+      for (int g = lane; g < nc4; g += 32) {
+        float4 v = sm4[(so >> 2) + g];
+        const int col0 = 4 * g;
+        float vin[2] = {v.x, v.z};
+        float rec[2];
+        unsigned code[2] = {0u, 0u};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int col = col0 + 2 * h;
+          if (col >= m2) break;
+          const uint32_t cc = crow + (uint32_t)(col >> 1);
+          const float m1v = __ldg(Rc + (uint32_t)k0 * P.cst0 + cc);
+          const float p1v = hp1 ? __ldg(Rc + (uint32_t)(k0 + 1) * P.cst0 + cc) : 0.f;
+          const float m3v = hm3 ? __ldg(Rc + (uint32_t)(k0 - 1) * P.cst0 + cc) : 0.f;
+          const float p3v = hp3 ? __ldg(Rc + (uint32_t)(k0 + 2) * P.cst0 + cc) : 0.f;
+          const float p = eval_formula(f, m3v, 0.f, m1v, p1v, 0.f, p3v);
+          if (!kDecomp) {
+            code[h] = quant(vin[h], p, el, inv2, twoe, rec[h]);
+          } else {
+            const unsigned cd = P.stage_codes ? scode[so + col]
                                               : codes_full[fr + (uint32_t)col * P.fs2];
-          rec = code ? dequantize(code, p, twoe) : outl_full[fr + (uint32_t)col * P.fs2];
-          if (in_tile) Rs[grow + (uint32_t)col] = rec;
+            rec[h] = cd ? dequantize(cd, p, twoe) : outl_full[fr + (uint32_t)col * P.fs2];
+          }
         }
-        sm[so + col] = rec;
+        v.x = rec[0];
+        if (col0 + 2 < m2) v.z = rec[1];
+        sm4[(so >> 2) + g] = v;
+        if (!kDecomp && in_tile) {
+          ctile[to + col0] = (uint16_t)code[0];
+          if (col0 + 2 < m2) ctile[to + col0 + 2] = (uint16_t)code[1];
+        }
       }
     }
   }
@@ -180,123 +209,118 @@ __global__ void __launch_bounds__(256)
   {
     const int np = odd_plane ? 2 : 1;
     const int r0 = Tlo | 1;
-    const int nr = Thi > r0 ? (Thi - r0 + 1) >> 1 : 0, nc = (m2 + 1) >> 1;
+    const int nr = Thi > r0 ? (Thi - r0 + 1) >> 1 : 0;
     for (int r = warp; r < nr * np; r += NW) {
       const int pl = r / nr, row = r0 + 2 * (r - pl * nr);
-      const int u0 = P0 + pl;
       const bool hm3 = row >= 3, hp1 = row + 1 <= m1 - 1, hp3 = row + 3 <= m1 - 1;
-      int f;
-      if (!hp1) f = hm3 ? F_EXTRAP : F_COPY;
-      else if (KIND == LINEAR) f = F_LIN;
-      else if (hm3 && hp3) f = KIND == CUBIC_NAK ? F_NAK4 : F_NAT4;
-      else if (hm3) f = KIND == CUBIC_NAK ? F_NAK3L : F_NAT3L;
-      else if (hp3) f = KIND == CUBIC_NAK ? F_NAK3R : F_NAT3R;
-      else f = F_LIN;
-      const int so = srow(pl, row);
-      const uint32_t grow = (uint32_t)u0 * gst0 + (uint32_t)row * gst1;
-      const uint32_t fr = (uint32_t)u0 * P.fs0 + (uint32_t)row * P.fs1;
-      const bool interior = KIND == LINEAR ? f == F_LIN : (f == F_NAK4 || f == F_NAT4);
-#pragma unroll 2
-      for (int c = lane; c < nc; c += 32) {
-        const int col = 2 * c;
-        const int s = so + col;
-        float p;
-        if (interior) {
-          // only the knots the stencil uses are read (rows +-3 may not exist
-          // for the linear stencil)
-          if (KIND == LINEAR)
-            p = eval_formula(F_LIN, 0.f, 0.f, sm[s - W], sm[s + W], 0.f, 0.f);
-          else
-            p = stencil4<KIND>(sm[s - 3 * W], sm[s - W], sm[s + W], sm[s + 3 * W]);
-        } else {
-          const float m1v = sm[s - W];
-          const float p1v = hp1 ? sm[s + W] : 0.f;
-          const float m3v = hm3 ? sm[s - 3 * W] : 0.f;
-          const float p3v = hp3 ? sm[s + 3 * W] : 0.f;
-          p = eval_formula(f, m3v, 0.f, m1v, p1v, 0.f, p3v);
-        }
-        float rec;
-        if (!kDecomp) {
-          const unsigned code = quant(sm[s], p, el, inv2, twoe, rec);
-          Cs[grow + (uint32_t)col] = (uint16_t)code;
-          if (P.write_recon) Rs[grow + (uint32_t)col] = rec;
-        } else {
-          const unsigned code = P.stage_codes ? scode[s]
+      const int f = edge_formula<KIND>(hm3, hp1, hp3);  // one stencil per row
+      const int so = srow(pl, row) >> 2, W4r = W4;
+      const int to = trow(pl, row);
+      const uint32_t fr = (uint32_t)(P0 + pl) * P.fs0 + (uint32_t)row * P.fs1;
+      for (int g = lane; g < nc4; g += 32) {
+        float4 v = sm4[so + g];
+        const float4 a1 = sm4[so - W4r + g];
+        const float4 b1 = hp1 ? sm4[so + W4r + g] : a1;
+        const float4 a3 = hm3 ? sm4[so - 3 * W4r + g] : a1;
+        const float4 b3 = hp3 ? sm4[so + 3 * W4r + g] : a1;
+        const int col0 = 4 * g;
+        float vin[2] = {v.x, v.z};
+        float m3s[2] = {a3.x, a3.z}, m1s[2] = {a1.x, a1.z}, p1s[2] = {b1.x, b1.z},
+              p3s[2] = {b3.x, b3.z};
+        float rec[2];
+        unsigned code[2] = {0u, 0u};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int col = col0 + 2 * h;
+          if (col >= m2) break;
+          const float p = eval_formula(f, m3s[h], 0.f, m1s[h], p1s[h], 0.f, p3s[h]);
+          if (!kDecomp) {
+            code[h] = quant(vin[h], p, el, inv2, twoe, rec[h]);
+          } else {
+            const unsigned cd = P.stage_codes ? scode[4 * so + col]
                                               : codes_full[fr + (uint32_t)col * P.fs2];
-          rec = code ? dequantize(code, p, twoe) : outl_full[fr + (uint32_t)col * P.fs2];
-          Rs[grow + (uint32_t)col] = rec;
+            rec[h] = cd ? dequantize(cd, p, twoe) : outl_full[fr + (uint32_t)col * P.fs2];
+          }
         }
-        sm[s] = rec;
+        v.x = rec[0];
+        if (col0 + 2 < m2) v.z = rec[1];
+        sm4[so + g] = v;
+        if (!kDecomp) {
+          ctile[to + col0] = (uint16_t)code[0];
+          if (col0 + 2 < m2) ctile[to + col0 + 2] = (uint16_t)code[1];
+        }
       }
     }
   }
   __syncthreads();
 
-  // 4. pass 3 (along dim 2): both planes, every row of the tile, odd columns
+  // 4. pass 3 (along dim 2): both planes, every tile row, odd columns; the
+  //    finished rows (codes, reconstruction) go to global memory
   {
     const int np = odd_plane ? 2 : 1;
-    const int nr = Thi - Tlo, nc = m2 >> 1;
+    const int nr = Thi - Tlo;
     for (int r = warp; r < nr * np; r += NW) {
       const int pl = r / nr, row = Tlo + (r - pl * nr);
       const int u0 = P0 + pl;
-      const int so = srow(pl, row);
+      const int so = srow(pl, row) >> 2;
+      const int to = trow(pl, row);
       const uint32_t grow = (uint32_t)u0 * gst0 + (uint32_t)row * gst1;
       const uint32_t fr = (uint32_t)u0 * P.fs0 + (uint32_t)row * P.fs1;
-#pragma unroll 4
-      for (int c = lane; c < nc; c += 32) {
-        const int col = 2 * c + 1;
-        const int s = so + col;
-        float p;
-        if (col >= 3 && col + 3 <= m2 - 1) {
-          if (KIND == LINEAR)
-            p = eval_formula(F_LIN, 0.f, 0.f, sm[s - 1], sm[s + 1], 0.f, 0.f);
-          else
-            p = stencil4<KIND>(sm[s - 3], sm[s - 1], sm[s + 1], sm[s + 3]);
-        } else {
-          const bool hm3 = col >= 3, hp1 = col + 1 <= m2 - 1, hp3 = col + 3 <= m2 - 1;
-          int f;
-          if (!hp1) f = hm3 ? F_EXTRAP : F_COPY;
-          else if (KIND == LINEAR) f = F_LIN;
-          else if (hm3) f = KIND == CUBIC_NAK ? F_NAK3L : F_NAT3L;
-          else if (hp3) f = KIND == CUBIC_NAK ? F_NAK3R : F_NAT3R;
-          else f = F_LIN;
-          const float m1v = sm[s - 1];
-          const float p1v = hp1 ? sm[s + 1] : 0.f;
-          const float m3v = hm3 ? sm[s - 3] : 0.f;
-          const float p3v = hp3 ? sm[s + 3] : 0.f;
-          p = eval_formula(f, m3v, 0.f, m1v, p1v, 0.f, p3v);
-        }
-        float rec;
-        if (!kDecomp) {
-          const unsigned code = quant(sm[s], p, el, inv2, twoe, rec);
-          Cs[grow + (uint32_t)col] = (uint16_t)code;
-          if (P.write_recon) Rs[grow + (uint32_t)col] = rec;
-        } else {
-          const unsigned code = P.stage_codes ? scode[s]
+      for (int g = lane; g < nc4; g += 32) {
+        const float4 v = sm4[so + g];
+        const float4 prev = g > 0 ? sm4[so + g - 1] : v;
+        const float4 next = g + 1 < W4 ? sm4[so + g + 1] : v;
+        const int col0 = 4 * g;
+        // odd columns col0+1 and col0+3
+        const float vin[2] = {v.y, v.w};
+        const float m3s[2] = {prev.z, v.x}, m1s[2] = {v.x, v.z}, p1s[2] = {v.z, next.x},
+                    p3s[2] = {next.x, next.z};
+        float rec[2] = {v.y, v.w};
+        unsigned code[2] = {0u, 0u};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int col = col0 + 1 + 2 * h;
+          if (col >= m2) break;
+          float p;
+          if (col >= 3 && col + 3 <= m2 - 1) {
+            p = KIND == LINEAR ? eval_formula(F_LIN, 0.f, 0.f, m1s[h], p1s[h], 0.f, 0.f)
+                               : stencil4<KIND>(m3s[h], m1s[h], p1s[h], p3s[h]);
+          } else {
+            const int f = edge_formula<KIND>(col >= 3, col + 1 <= m2 - 1, col + 3 <= m2 - 1);
+            p = eval_formula(f, m3s[h], 0.f, m1s[h], p1s[h], 0.f, p3s[h]);
+          }
+          if (!kDecomp) {
+            code[h] = quant(vin[h], p, el, inv2, twoe, rec[h]);
+          } else {
+            const unsigned cd = P.stage_codes ? scode[4 * so + col]
                                               : codes_full[fr + (uint32_t)col * P.fs2];
-          rec = code ? dequantize(code, p, twoe) : outl_full[fr + (uint32_t)col * P.fs2];
-          Rs[grow + (uint32_t)col] = rec;
+            rec[h] = cd ? dequantize(cd, p, twoe) : outl_full[fr + (uint32_t)col * P.fs2];
+          }
         }
-      }
-    }
-  }
-
-  // 5. the tile's coarse points: codes from the coarse grid, reconstruction
-  {
-    const int r0 = (Tlo + 1) & ~1;
-    const int nr = Thi > r0 ? (Thi - r0 + 1) >> 1 : 0, nc = (m2 + 1) >> 1;
-    for (int r = warp; r < nr; r += NW) {
-      const int row = r0 + 2 * r;
-      const uint32_t grow = (uint32_t)P0 * gst0 + (uint32_t)row * gst1;
-      const uint32_t crow = (uint32_t)(P0 >> 1) * P.cst0 + (uint32_t)(row >> 1) * P.cst1;
-      const int so = srow(0, row);
-#pragma unroll 4
-      for (int c = lane; c < nc; c += 32) {
+        const float4 out = make_float4(v.x, rec[0], v.z, rec[1]);
+        const bool full = col0 + 4 <= m2 && P.vec_out;
         if (!kDecomp) {
-          Cs[grow + 2u * c] = Cc[crow + c];
-          if (P.write_recon) Rs[grow + 2u * c] = sm[so + 2 * c];
+          const uint16_t c0 = ctile[to + col0];
+          const uint16_t c2 = col0 + 2 < m2 ? ctile[to + col0 + 2] : 0;
+          if (full) {
+            *reinterpret_cast<uint2*>(Cs + grow + col0) =
+                make_uint2((uint32_t)c0 | (code[0] << 16), (uint32_t)c2 | (code[1] << 16));
+            if (P.write_recon) *reinterpret_cast<float4*>(Rs + grow + col0) = out;
+          } else {
+            const uint16_t cv[4] = {c0, (uint16_t)code[0], c2, (uint16_t)code[1]};
+            const float ov[4] = {out.x, out.y, out.z, out.w};
+            for (int q = 0; q < 4 && col0 + q < m2; ++q) {
+              Cs[grow + col0 + q] = cv[q];
+              if (P.write_recon) Rs[grow + col0 + q] = ov[q];
+            }
+          }
         } else {
-          Rs[grow + 2u * c] = sm[so + 2 * c];
+          if (full) {
+            *reinterpret_cast<float4*>(Rs + grow + col0) = out;
+          } else {
+            const float ov[4] = {out.x, out.y, out.z, out.w};
+            for (int q = 0; q < 4 && col0 + q < m2; ++q) Rs[grow + col0 + q] = ov[q];
+          }
         }
       }
     }
@@ -306,6 +330,7 @@ __global__ void __launch_bounds__(256)
 size_t level3d_smem_bytes(const Level3D& P, bool decomp) {
   size_t b = 2ull * (P.E1 + 6) * P.W * sizeof(float);
   if (decomp && P.stage_codes) b += 2ull * (P.E1 + 6) * P.W * sizeof(uint16_t);
+  if (!decomp) b += 2ull * P.E1 * P.W * sizeof(uint16_t);
   return b;
 }
 
