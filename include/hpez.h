@@ -48,6 +48,7 @@ extern "C" {
 #define HPEZ_ERR_CUDA (-7)           /* a CUDA runtime call failed */
 #define HPEZ_ERR_UNSUPPORTED (-8)    /* valid but not implemented */
 #define HPEZ_ERR_TIMEOUT (-9)        /* a bounded device wait gave up */
+#define HPEZ_ERR_TOO_LARGE (-10)     /* beyond hpez_decompress_noalloc's limit */
 
 /* error-bound modes: Sec. 3.1 Eq. 1 (absolute e) and Sec. 7.1.3
  * (value-range relative eps, e = eps * (max - min)) */
@@ -121,6 +122,28 @@ HPEZ_API int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
  * Errors: CORRUPT_STREAM, OUT_TOO_SMALL, INVALID_ARG, NO_MEMORY, CUDA. */
 HPEZ_API int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
                     float* d_out, uint64_t out_cap_elems, void* stream);
+
+/* Decompression that allocates nothing -- no counterpart in the paper; it
+ * exists for callers that may not allocate memory: code running under a
+ * memory manager that owns the device heap, or a pre-sized loop that must
+ * not call cudaMalloc/cudaFree (or an allocating library) once running.
+ * Same result as hpez_decompress, needs no context.
+ *   d_in   device, in_size bytes, 16-byte aligned; d_out device, >= N floats
+ *   stream cudaStream_t as void*; uses the current CUDA device
+ * Scratch is one file-scope device array of HPEZ_NOALLOC_SCRATCH_BYTES
+ * (16 MiB), held by every GPU that loads the library until the process
+ * exits.  Fields of more than HPEZ_NOALLOC_MAX_POINTS points (2^21) are
+ * refused with HPEZ_ERR_TOO_LARGE.  The first call on a device looks the
+ * array's device address up (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialized by the caller.  Synchronizes `stream`.
+ * Errors: as hpez_decompress, plus HPEZ_ERR_TOO_LARGE. */
+#define HPEZ_NOALLOC_MAX_POINTS 2097152u
+#define HPEZ_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+HPEZ_API int hpez_decompress_noalloc(const void* d_in, uint64_t in_size,
+                                     float* d_out, uint64_t out_cap_elems,
+                                     void* stream);
 
 /* Host-buffer forms of the two calls above: copy h_in to the device, run
  * the call, copy the result back (all on `stream`, synchronous). */

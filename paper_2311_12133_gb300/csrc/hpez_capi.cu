@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "hpez_internal.cuh"
@@ -639,6 +640,8 @@ const char* hpez_strerror(int code) {
     case HPEZ_ERR_CUDA: return "CUDA runtime error";
     case HPEZ_ERR_UNSUPPORTED: return "unsupported configuration";
     case HPEZ_ERR_TIMEOUT: return "bounded device wait timed out";
+    case HPEZ_ERR_TOO_LARGE:
+      return "field larger than the fixed scratch of the no-allocation entry point";
   }
   return "unknown error";
 }
@@ -1214,3 +1217,217 @@ int hpez_decompress_host(hpez_ctx* ctx, const void* h_in, uint64_t in_size,
 }
 
 }  // extern "C"
+
+// =====================================================================
+// Decompression without any allocation, for callers that cannot allocate
+// device or pinned host memory (for example code running under an external
+// memory manager that forbids cudaMalloc, or inside a pre-sized real-time
+// loop).  Its scratch is this fixed device array; the caller still passes
+// the stream and the output.
+// =====================================================================
+namespace {
+
+static __device__ __align__(256) unsigned char
+    g_noalloc_scratch[HPEZ_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[128] = {};  // per device: address of g_noalloc_scratch
+
+// Device address of the array on the current device, looked up once per
+// device (a host-side reference to the symbol is not a device address).
+int noalloc_scratch(int dev, char** out) {
+  if (dev < 0 || dev >= 128) return HPEZ_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return HPEZ_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = static_cast<char*>(g_noalloc_ptr[dev]);
+  return HPEZ_OK;
+}
+
+}  // namespace
+
+extern "C" int hpez_decompress_noalloc(const void* d_in, uint64_t in_size,
+                                       float* d_out, uint64_t out_cap_elems,
+                                       void* stream) {
+  if (!d_in || !d_out) return HPEZ_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_in) & 15u) != 0) return HPEZ_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_out) & 3u) != 0) return HPEZ_ERR_INVALID_ARG;
+  if (in_size < (uint64_t)kHeaderBytes) return HPEZ_ERR_CORRUPT_STREAM;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HPEZ_ERR_CUDA;
+  char* S = nullptr;
+  int rc = noalloc_scratch(dev, &S);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // execution settings of a default context, built on the stack (nothing
+  // in it allocates)
+  hpez_ctx opt;
+  opt.device = dev;
+  cudaDeviceGetAttribute(&opt.num_sms, cudaDevAttrMultiProcessorCount, dev);
+  opt.out_aligned16 = (reinterpret_cast<uintptr_t>(d_out) & 15u) == 0;
+  uint8_t h[kHeaderBytes];
+  rc = cuda_check(cudaMemcpyAsync(h, d_in, kHeaderBytes, cudaMemcpyDeviceToHost, s));
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(s));
+  if (rc) return rc;
+  int nd;
+  uint64_t dims[3];
+  rc = hpez_inspect(h, kHeaderBytes, &nd, dims, nullptr);
+  if (rc) return rc;
+  if (rd64(h, H_TOTAL) > in_size) return HPEZ_ERR_CORRUPT_STREAM;
+  uint64_t N = 1;
+  for (int d = 0; d < nd; ++d) {
+    if (dims[d] == 0) return HPEZ_ERR_CORRUPT_STREAM;
+    N *= dims[d];
+    if (N > 0xFFFFFFFFull) return HPEZ_ERR_CORRUPT_STREAM;
+  }
+  if (N > HPEZ_NOALLOC_MAX_POINTS) return HPEZ_ERR_TOO_LARGE;
+  if (N > out_cap_elems) return HPEZ_ERR_OUT_TOO_SMALL;
+  const uint8_t* in = static_cast<const uint8_t*>(d_in);
+  hpez_config cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.anchor_stride = (int32_t)rd32(h, H_ANCHOR);
+  cfg.frozen_dim = (int32_t)rd32(h, H_FROZEN);
+  cfg.chunk_syms = (int32_t)rd32(h, H_CHUNK);
+  cfg.blockwise = (int32_t)rd32(h, H_BLOCKWISE);
+  cfg.block_size = (int32_t)rd32(h, H_BLOCKSIZE);
+  cfg.alpha = rdf64(h, H_ALPHA);
+  cfg.beta = rdf64(h, H_BETA);
+  for (int d = 0; d < 3; ++d) cfg.md_inv_var[d] = rdf64(h, H_MDIV + 8 * d);
+  for (int l = 0; l < HPEZ_MAX_LEVELS; ++l) {
+    cfg.interp[l] = h[H_INTERP + l];
+    cfg.paradigm[l] = h[H_PARADIGM + l];
+    cfg.same_level[l] = h[H_SAME + l];
+    for (int j = 0; j < 3; ++j) cfg.order[l][j] = h[H_ORDER + 3 * l + j];
+  }
+  if (rd32(h, H_FLAGS) & 1u) {
+    Plan p;
+    if (plan_geometry(p, nd, dims, 2, -1)) return HPEZ_ERR_CORRUPT_STREAM;
+    launch_fill(d_out, p.N, rdf32(h, H_CONST), opt.num_sms, s);
+    rc = cuda_check(cudaGetLastError());
+    if (rc) return rc;
+    return cuda_check(cudaStreamSynchronize(s));
+  }
+  Plan p;
+  if (plan_geometry(p, nd, dims, cfg.anchor_stride, cfg.frozen_dim))
+    return HPEZ_ERR_CORRUPT_STREAM;
+  if (check_config(p, cfg)) return HPEZ_ERR_CORRUPT_STREAM;
+  plan_chunks_blocks(p, cfg);
+  const float e = rdf32(h, H_E);
+  if (!(e > 0.0f) || !std::isfinite(e)) return HPEZ_ERR_CORRUPT_STREAM;
+  const uint64_t na = rd64(h, H_NANCHORS), nout = rd64(h, H_NOUTLIERS),
+                 nch = rd64(h, H_NCHUNKS), twords = rd64(h, H_TOTALWORDS);
+  const uint32_t nused = rd32(h, H_NUSED);
+  const uint64_t oa = rd64(h, H_OFF_ANCHORS), ocw = rd64(h, H_OFF_CHUNKW),
+                 ot = rd64(h, H_OFF_TABLE), oo = rd64(h, H_OFF_OUTLIERS),
+                 ob = rd64(h, H_OFF_BITS), obm = rd64(h, H_OFF_BLOCKMAP);
+  if (na != n_anchors(p) || nch != p.nch || nused == 0 || nused > 65536 ||
+      nout > N || (cfg.blockwise && rd64(h, H_NBLOCKS) != p.nblocks))
+    return HPEZ_ERR_CORRUPT_STREAM;
+  if (oa + 4 * na > in_size || ocw + 64 * nch > in_size ||
+      ot + 3ull * nused > in_size || oo + 4 * nout > in_size ||
+      ob + 4 * twords > in_size || (cfg.blockwise && obm + p.nblocks > in_size) ||
+      (oa & 15) || (ocw & 15) || (oo & 15) || (ob & 15))
+    return HPEZ_ERR_CORRUPT_STREAM;
+  uint16_t single_sym = 0;
+  if (nused == 1) {
+    uint8_t tb[2];
+    rc = cuda_check(cudaMemcpyAsync(tb, in + ot, 2, cudaMemcpyDeviceToHost, s));
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(s));
+    if (rc) return rc;
+    single_sym = (uint16_t)(tb[0] | (tb[1] << 8));
+  }
+  // carve the scratch out of the fixed array
+  Arena ar;
+  const size_t o_ctl = ar.take<Ctl>(1);
+  const size_t o_lut = ar.take<uint32_t>(4096);
+  const size_t o_cnt = ar.take<uint32_t>(64);
+  const size_t o_first = ar.take<unsigned long long>(64);
+  const size_t o_offs = ar.take<uint32_t>(64);
+  const size_t o_sorted = ar.take<uint16_t>(65536);
+  const size_t o_gkeys = ar.take<unsigned long long>(65536);
+  size_t o_R[kMaxLevels + 1];
+  for (int g = 1; g < p.L; ++g) o_R[g] = ar.take<float>(p.gsize[g]);
+  const size_t o_codes = ar.take<uint16_t>(N);
+  const size_t o_zc = ar.take<uint32_t>(p.nch);
+  const size_t o_zoff = ar.take<unsigned long long>(p.nch);
+  const size_t o_woff = ar.take<unsigned long long>(p.nch);
+  const size_t o_dchw = ar.take<uint32_t>(p.nch);
+  const size_t o_tot = ar.take<unsigned long long>(2);
+  if (ar.off > (size_t)HPEZ_NOALLOC_SCRATCH_BYTES) return HPEZ_ERR_TOO_LARGE;
+  Ctl* ctl = reinterpret_cast<Ctl*>(S + o_ctl);
+  uint32_t* lut = reinterpret_cast<uint32_t*>(S + o_lut);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(S + o_cnt);
+  unsigned long long* first = reinterpret_cast<unsigned long long*>(S + o_first);
+  uint32_t* offs = reinterpret_cast<uint32_t*>(S + o_offs);
+  uint16_t* sorted = reinterpret_cast<uint16_t*>(S + o_sorted);
+  unsigned long long* gkeys = reinterpret_cast<unsigned long long*>(S + o_gkeys);
+  uint16_t* codes = reinterpret_cast<uint16_t*>(S + o_codes);
+  uint32_t* zc = reinterpret_cast<uint32_t*>(S + o_zc);
+  unsigned long long* zoff = reinterpret_cast<unsigned long long*>(S + o_zoff);
+  unsigned long long* woff = reinterpret_cast<unsigned long long*>(S + o_woff);
+  unsigned long long* tot = reinterpret_cast<unsigned long long*>(S + o_tot);
+  uint32_t* dchw = reinterpret_cast<uint32_t*>(S + o_dchw);
+  float* R[kMaxLevels + 1];
+  for (int g = 1; g < p.L; ++g) R[g] = reinterpret_cast<float*>(S + o_R[g]);
+  R[0] = d_out;
+  R[p.L] = const_cast<float*>(reinterpret_cast<const float*>(in + oa));
+  // the control block is cleared by its first kernel; every other buffer is
+  // written in full before it is read
+  launch_init_ctl(ctl, s);
+  launch_params(ctl, HPEZ_EB_ABS, (double)e, cfg.alpha, cfg.beta, p.L, d_out, s);
+  const uint8_t* lbits_stream = in + ocw;
+  launch_chunk_words(lbits_stream, p.nch, dchw, opt.num_sms, s);
+  launch_scan(dchw, woff, p.nch, &tot[0], ctl, s);
+  launch_dec_tables(in, nused, ot, lut, cnt, first, offs, sorted, gkeys, ctl, s);
+  launch_decode(in, ob, twords, lbits_stream, woff, p.N, p.C, p.nch, nused,
+                single_sym, lut, cnt, first, offs, sorted, codes, zc, ctl,
+                opt.num_sms, s);
+  launch_scan(zc, zoff, p.nch, &tot[1], ctl, s);
+  launch_outliers(false, codes, p.N, p.C, p.nch, zc, zoff, nullptr, d_out,
+                  const_cast<uint8_t*>(in) + oo, nout, ctl, opt.num_sms, s);
+  SweepBufs sb;
+  std::memset(&sb, 0, sizeof(sb));
+  sb.codes_full = codes;
+  sb.outl_full = d_out;
+  sb.blockmap = cfg.blockwise ? in + obm : nullptr;
+  sb.bs = (uint32_t)(cfg.block_size > 0 ? cfg.block_size : 1);
+  for (int s3 = 0; s3 < 3; ++s3) sb.nb[s3] = p.nb[s3];
+  sb.ctl = ctl;
+  for (int l = p.L; l >= 1; --l) {
+    const int g = l - 1;
+    sb.R = R[g];
+    sb.kind = cfg.interp[l - 1];
+    sb.same = cfg.same_level[l - 1];
+    FusedLevel F;
+    Level3D F3;
+    if (plan_level3d(&opt, p, cfg, l, true, F3)) {
+      launch_level3d(true, F3, sb, R[l], nullptr, R[g], nullptr, s);
+    } else if (plan_fused(&opt, p, cfg, l, true, F)) {
+      launch_level(true, F, sb, R[l], nullptr, R[g], nullptr, s);
+    } else {
+      launch_upsample(p.grid[l], p.gsize[l], p.grid[g], R[l], nullptr, R[g],
+                      nullptr, ctl, s);
+      for (const Launch& L : level_schedule(p, cfg, l))
+        launch_pass(true, p.grid[g], L.pb, sb, opt.num_sms, s);
+    }
+  }
+  rc = cuda_check(cudaGetLastError());
+  if (rc) return rc;
+  Ctl hc;
+  unsigned long long h_tot[2];
+  rc = cuda_check(cudaMemcpyAsync(&hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(h_tot, tot, sizeof(h_tot),
+                                           cudaMemcpyDeviceToHost, s));
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(s));
+  if (rc) return rc;
+  if (hc.status) return map_status(hc.status);
+  if (h_tot[0] != twords || h_tot[1] != nout) return HPEZ_ERR_CORRUPT_STREAM;
+  return HPEZ_OK;
+}

@@ -93,6 +93,7 @@ def _load():
             "hpez_profile_phase_name": (ctypes.c_char_p, [ctypes.c_int]),
             "hpez_launch_count": (ctypes.c_int, [vp, u64p]),
             "hpez_set_option": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int64]),
+            "hpez_decompress_noalloc": (ctypes.c_int, [vp, u64, vp, u64, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -108,7 +109,8 @@ def exported_symbols() -> list[str]:
             "hpez_compress_bound", "hpez_compress", "hpez_decompress",
             "hpez_compress_host", "hpez_decompress_host", "hpez_inspect",
             "hpez_strerror", "hpez_profile_enable", "hpez_profile_get",
-            "hpez_profile_phase_name", "hpez_launch_count", "hpez_set_option"]
+            "hpez_profile_phase_name", "hpez_launch_count", "hpez_set_option",
+            "hpez_decompress_noalloc"]
 
 
 def _check(rc: int, what: str):
@@ -165,6 +167,19 @@ def hpez_decompress(ctx, d_in: int, in_size: int, d_out: int,
                     out_cap_elems: int, stream: int = 0) -> None:
     _check(_load().hpez_decompress(ctx, d_in, in_size, d_out, out_cap_elems,
                                    stream or None), "hpez_decompress")
+
+
+HPEZ_NOALLOC_MAX_POINTS = 2097152
+HPEZ_ERR_TOO_LARGE = -10
+
+
+def hpez_decompress_noalloc(d_in: int, in_size: int, d_out: int,
+                            out_cap_elems: int, stream: int = 0) -> None:
+    """Decompress with no allocation at all: scratch is a fixed device array
+    inside the library (fields up to HPEZ_NOALLOC_MAX_POINTS points), for
+    callers that may not allocate; concurrent calls race."""
+    _check(_load().hpez_decompress_noalloc(d_in, in_size, d_out, out_cap_elems,
+                                           stream or None), "hpez_decompress_noalloc")
 
 
 def hpez_compress_host(ctx, h_in: np.ndarray, eb_mode: int, eb: float,

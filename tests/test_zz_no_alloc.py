@@ -1,0 +1,64 @@
+"""hpez_decompress_noalloc: decompression for callers that may not allocate
+memory (an external memory manager owns the device heap, or a pre-sized
+loop may not call cudaMalloc once running).  Its scratch is a fixed device
+array inside the library; its output must equal hpez_decompress's, bit for
+bit, on consecutive calls.  This file is collected last on purpose."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_12133_gb300 import build as B
+    B.build()
+    from paper_2311_12133_gb300 import hpez
+    c = hpez.Context(0)
+    yield c
+    c.close()
+
+
+def _noalloc(buf, size, shape):
+    import torch
+    from paper_2311_12133_gb300 import hpez
+    out = torch.full(shape, float("nan"), dtype=torch.float32, device=buf.device)
+    hpez.hpez_decompress_noalloc(buf.data_ptr(), size, out.data_ptr(), out.numel(),
+                                 torch.cuda.current_stream().cuda_stream)
+    return out
+
+
+def test_noalloc_matches_decompress_twice(ctx):
+    import torch
+    from paper_2311_12133_gb300 import fields, hpez
+    cases = [(fields.bumps((96, 80, 72), seed=3), {}),
+             (fields.climate2d((300, 500), seed=1), {"same_level": 1}),
+             (fields.grf((40000,), seed=2), {"interp": hpez.HPEZ_CUBIC_NAT})]
+    for x, kw in cases:
+        cfg = hpez.make_config(x.ndim, **kw)
+        xd = torch.from_numpy(x).cuda()
+        buf, size = ctx.compress(xd, 1e-3, hpez.HPEZ_EB_REL, cfg)
+        ref = ctx.decompress(buf, size).cpu().numpy()
+        for _ in range(2):  # the array keeps the last call's contents
+            got = _noalloc(buf, size, x.shape).cpu().numpy()
+            assert got.tobytes() == ref.tobytes()
+
+
+def test_noalloc_refuses_fields_beyond_its_scratch(ctx):
+    import torch
+    from paper_2311_12133_gb300 import fields, hpez
+    x = torch.from_numpy(fields.grf((130, 128, 128), seed=4)).cuda()
+    assert x.numel() > hpez.HPEZ_NOALLOC_MAX_POINTS
+    buf, size = ctx.compress(x, 1e-3)
+    with pytest.raises(hpez.HpezError) as e:
+        _noalloc(buf, size, tuple(x.shape))
+    assert e.value.code == hpez.HPEZ_ERR_TOO_LARGE
+    # a field at the limit still works afterwards
+    y = torch.from_numpy(fields.grf((128, 128, 128), seed=5)).cuda()
+    buf, size = ctx.compress(y, 1e-3)
+    ref = ctx.decompress(buf, size)
+    got = _noalloc(buf, size, tuple(y.shape))
+    assert torch.equal(got, ref)
