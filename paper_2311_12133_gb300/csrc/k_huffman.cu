@@ -143,6 +143,7 @@ __host__ __device__ inline uint32_t next_pow2(uint32_t v) {
 }
 
 constexpr uint32_t kSmemLeaves = 8192;  // codebook fits shared memory
+constexpr uint32_t kRankSort = 2048;    // alphabets sorted by rank counting
 constexpr size_t kCodebookSmem =
     (size_t)kSmemLeaves * 8 + (size_t)kSmemLeaves * 8 + (size_t)kSmemLeaves * 8;
 
@@ -167,15 +168,34 @@ __global__ void __launch_bounds__(1024)
   __shared__ uint32_t s_maxlen;
 
   const int tid = threadIdx.x;
-  // 1. compaction of used symbols, ascending
-  uint32_t cnt = 0;
-  const uint32_t b0 = tid * 64;
-  for (uint32_t i = 0; i < 64; ++i) cnt += hist[b0 + i] != 0;
-  uint32_t total;
-  uint32_t pos = block_exclusive_scan(cnt, &total);
-  if (tid == 0) s_n = total;
-  for (int i = tid; i < 64; i += blockDim.x) bl_count[i] = 0;
+  const int lane = tid & 31, wid = tid >> 5;
+  // 1. compaction of used symbols, ascending: warp w owns bins
+  //    [2048 w, 2048 (w+1)), read 32 at a time (coalesced); the ballot masks
+  //    give every used bin its position
+  __shared__ uint32_t masks[32][64];
+  __shared__ uint32_t wtot[32];
+  {
+    uint32_t c = 0;
+    for (int it = 0; it < 64; ++it) {
+      const uint32_t f = hist[wid * 2048 + it * 32 + lane];
+      const uint32_t m = __ballot_sync(0xffffffffu, f != 0);
+      if (lane == 0) masks[wid][it] = m;
+      c += __popc(m);
+    }
+    if (lane == 0) wtot[wid] = c;
+  }
   if (tid == 0) s_maxlen = 0;
+  for (int i = tid; i < 64; i += blockDim.x) bl_count[i] = 0;
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t run = 0;
+    for (int w = 0; w < 32; ++w) {
+      const uint32_t t = wtot[w];
+      wtot[w] = run;
+      run += t;
+    }
+    s_n = run;
+  }
   __syncthreads();
   const uint32_t n = s_n;
   const bool in_smem = n <= kSmemLeaves;
@@ -184,12 +204,17 @@ __global__ void __launch_bounds__(1024)
   unsigned long long* iw = in_smem ? smem + kSmemLeaves : giw;
   uint32_t* par = in_smem ? reinterpret_cast<uint32_t*>(smem + 2 * kSmemLeaves)
                           : gpar;
-  for (uint32_t i = 0; i < 64; ++i) {
-    const uint32_t f = hist[b0 + i];
-    if (f) {
-      keys[pos] = ((unsigned long long)f << 16) | (b0 + i);
-      tsyms[pos] = (uint16_t)(b0 + i);
-      ++pos;
+  {
+    uint32_t pos = wtot[wid];
+    for (int it = 0; it < 64; ++it) {
+      const uint32_t m = masks[wid][it];
+      const uint32_t b = wid * 2048 + it * 32 + lane;
+      if (m & (1u << lane)) {
+        const uint32_t k = pos + __popc(m & ((1u << lane) - 1u));
+        keys[k] = ((unsigned long long)hist[b] << 16) | b;
+        tsyms[k] = (uint16_t)b;
+      }
+      pos += __popc(m);
     }
   }
   for (uint32_t i = n + tid; i < P; i += blockDim.x) keys[i] = ~0ull;
@@ -204,8 +229,23 @@ __global__ void __launch_bounds__(1024)
     }
     return;
   }
-  // 2. leaves by (frequency, symbol)
-  bitonic_sort(keys, P);
+  // 2. leaves by (frequency, symbol): small alphabets by rank counting
+  //    (keys are distinct), large ones by a bitonic sort
+  const bool small = n <= kRankSort;
+  if (small) {
+    unsigned long long* tmp = smem + 3 * kSmemLeaves / 2;  // scratch half of par
+    for (uint32_t i = tid; i < n; i += blockDim.x) tmp[i] = keys[i];
+    __syncthreads();
+    for (uint32_t i = tid; i < n; i += blockDim.x) {
+      const unsigned long long k = tmp[i];
+      uint32_t r = 0;
+      for (uint32_t j = 0; j < n; ++j) r += tmp[j] < k;
+      keys[r] = k;
+    }
+    __syncthreads();
+  } else {
+    bitonic_sort(keys, P);
+  }
   // 3. two-queue merge (sequential by nature)
   if (tid == 0) {
     uint32_t a = 0, b = 0, m = 0;
@@ -258,6 +298,33 @@ __global__ void __launch_bounds__(1024)
     return;
   }
   // 5. canonical order (length, symbol)
+  if (small) {
+    // rank of a symbol among the symbols of its length = number of smaller
+    // symbols of that length; symbols are ascending in tsyms
+    uint8_t* lsym = reinterpret_cast<uint8_t*>(smem + 3 * kSmemLeaves / 2);
+    for (uint32_t k = tid; k < n; k += blockDim.x) lsym[k] = lens_by_sym[tsyms[k]];
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long code = 0;
+      bl_count[0] = 0;
+      for (uint32_t bits = 1; bits <= maxlen; ++bits) {
+        code = (code + bl_count[bits - 1]) << 1;
+        first_code[bits] = code;
+      }
+      ctl->n_used = n;
+      ctl->max_len = maxlen;
+    }
+    __syncthreads();
+    for (uint32_t k = tid; k < n; k += blockDim.x) {
+      const uint8_t L = lsym[k];
+      uint32_t r = 0;
+      for (uint32_t j = 0; j < k; ++j) r += lsym[j] == L;
+      const uint32_t sym = tsyms[k];
+      enc[sym] = ((unsigned long long)L << 56) | (first_code[L] + r);
+      tlens[k] = L;
+    }
+    return;
+  }
   for (uint32_t i = tid; i < n; i += blockDim.x) {
     const uint32_t sym = (uint32_t)(keys[i] & 0xFFFFu);
     keys[i] = ((unsigned long long)lens_by_sym[sym] << 16) | sym;
@@ -302,7 +369,19 @@ __global__ void __launch_bounds__(256)
   for (uint32_t c = warp; c < nch; c += nwarps) {
     const uint32_t beg = c * C, nc = min(C, N - beg);
     uint32_t bits = 0;
-    for (uint32_t j = lane; j < nc; j += 32) bits += (uint32_t)(enc[codes[beg + j]] >> 56);
+    // batches of 8: all code loads, then all table lookups, in flight
+    uint32_t j = lane;
+    for (; j + 7 * 32 < nc; j += 8 * 32) {
+      unsigned cd[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) cd[k] = codes[beg + j + 32 * k];
+      unsigned long long e[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) e[k] = __ldg(enc + cd[k]);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) bits += (uint32_t)(e[k] >> 56);
+    }
+    for (; j < nc; j += 32) bits += (uint32_t)(enc[codes[beg + j]] >> 56);
     lanebits[(size_t)c * 32 + lane] = (uint16_t)bits;
     uint32_t tot = bits;
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
@@ -384,7 +463,18 @@ __global__ void __launch_bounds__(256)
     bw.nacc = (int)(off & 31);
     bw.acc = 0;
     bw.shared_first = bw.nacc != 0;
-    for (uint32_t j = lane; j < nc; j += 32) bw.put_code(enc[codes[beg + j]]);
+    uint32_t j = lane;
+    for (; j + 7 * 32 < nc; j += 8 * 32) {
+      unsigned cd[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) cd[k] = codes[beg + j + 32 * k];
+      unsigned long long e[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) e[k] = __ldg(enc + cd[k]);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) bw.put_code(e[k]);
+    }
+    for (; j < nc; j += 32) bw.put_code(enc[codes[beg + j]]);
     bw.flush();
     __syncwarp();
   }
