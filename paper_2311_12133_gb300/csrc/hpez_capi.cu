@@ -477,8 +477,6 @@ bool plan_level3d(const hpez_ctx* ctx, const Plan& p, const hpez_config& c,
   const bool contig = g.step[2] == 1;
   F.stage16 = (!decomp && contig && (p.n[2] % 4 == 0) && ctx->x_aligned16) ? 1 : 0;
   F.stage_codes = (decomp && contig && (p.n[2] % 8 == 0) && ctx->codes_aligned16) ? 1 : 0;
-  F.hist = (!decomp && l == 1) ? 1 : 0;
-  F.C = p.C;
   while (level3d_smem_bytes(F, decomp) > ctx->fused_smem_cap && F.E1 > 2) F.E1 -= 2;
   if (level3d_smem_bytes(F, decomp) > ctx->fused_smem_cap) return false;
   F.nt0 = (F.m[0] + 1) / 2;
@@ -869,13 +867,6 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   sb.bs = (uint32_t)(cfg.block_size > 0 ? cfg.block_size : 1);
   for (int s3 = 0; s3 < 3; ++s3) sb.nb[s3] = p.nb[s3];
   sb.ctl = b.ctl;
-  // the finest level may accumulate the histogram itself
-  Level3D F3l1;
-  const bool hist_fused = ctx->fused_levels && plan_level3d(ctx, p, cfg, 1, false, F3l1);
-  if (hist_fused) {
-    cudaMemsetAsync(b.hist, 0, 65536 * sizeof(uint32_t), s);
-    cudaMemsetAsync(b.zc, 0, (size_t)p.nch * sizeof(uint32_t), s);
-  }
   for (int l = p.L; l >= 1; --l) {
     const int g = l - 1;
     pf.begin(HPEZ_PH_LEVEL + g, s);
@@ -886,7 +877,7 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
     FusedLevel F;
     Level3D F3;
     if (ctx->fused_levels && plan_level3d(ctx, p, cfg, l, false, F3)) {
-      launch_level3d(false, F3, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g], b.hist, b.zc, s);
+      launch_level3d(false, F3, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g], s);
       ++nl;
     } else if (ctx->fused_levels && plan_fused(ctx, p, cfg, l, false, F)) {
       launch_level(false, F, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g], s);
@@ -904,10 +895,8 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   }
   uint16_t* codes = b.Cg[0];
   pf.begin(HPEZ_PH_HIST, s);
-  if (!hist_fused) {
-    cudaMemsetAsync(b.hist, 0, 65536 * sizeof(uint32_t), s);
-    launch_hist(codes, p.N, p.C, p.nch, b.hist, b.zc, b.ctl, ctx->num_sms, s);
-  }
+  cudaMemsetAsync(b.hist, 0, 65536 * sizeof(uint32_t), s);
+  launch_hist(codes, p.N, p.C, p.nch, b.hist, b.zc, b.ctl, ctx->num_sms, s);
   launch_scan(b.zc, b.zoff, p.nch, &b.ctl->n_out, b.ctl, s);
   pf.end(s);
   pf.begin(HPEZ_PH_CODEBOOK, s);
@@ -1123,7 +1112,7 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
     FusedLevel F;
     Level3D F3;
     if (ctx->fused_levels && plan_level3d(ctx, p, cfg, l, true, F3)) {
-      launch_level3d(true, F3, sb, R[l], nullptr, R[g], nullptr, nullptr, nullptr, s);
+      launch_level3d(true, F3, sb, R[l], nullptr, R[g], nullptr, s);
       ++nl;
     } else if (ctx->fused_levels && plan_fused(ctx, p, cfg, l, true, F)) {
       launch_level(true, F, sb, R[l], nullptr, R[g], nullptr, s);
@@ -1419,7 +1408,7 @@ extern "C" int hpez_decompress_noalloc(const void* d_in, uint64_t in_size,
     FusedLevel F;
     Level3D F3;
     if (plan_level3d(&opt, p, cfg, l, true, F3)) {
-      launch_level3d(true, F3, sb, R[l], nullptr, R[g], nullptr, nullptr, nullptr, s);
+      launch_level3d(true, F3, sb, R[l], nullptr, R[g], nullptr, s);
     } else if (plan_fused(&opt, p, cfg, l, true, F)) {
       launch_level(true, F, sb, R[l], nullptr, R[g], nullptr, s);
     } else {

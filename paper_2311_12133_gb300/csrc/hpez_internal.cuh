@@ -312,8 +312,6 @@ struct Level3D {
   int stage16;       // compress: input rows staged with 16-byte copies
   int stage_codes;   // decompress: code rows staged (16-byte copies)
   int vec_out;       // rows of the output grids start 16-byte aligned
-  int hist;          // compress, finest level: accumulate the code histogram
-  uint32_t C;        // Huffman chunk length (per-chunk escape counts)
 };
 
 }  // namespace hpez

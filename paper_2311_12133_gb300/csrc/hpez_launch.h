@@ -35,7 +35,7 @@ void launch_level(bool decomp, const FusedLevel& P, const SweepBufs& B,
 size_t level3d_smem_bytes(const Level3D& P, bool decomp);
 void launch_level3d(bool decomp, const Level3D& P, const SweepBufs& B,
                     const float* Rc, const uint16_t* Cc, float* Rs, uint16_t* Cs,
-                    uint32_t* hist, uint32_t* zc, cudaStream_t s);
+                    cudaStream_t s);
 
 // k_huffman.cu
 void launch_hist(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,

@@ -14,21 +14,26 @@
 
 namespace hpez {
 
-constexpr int kHistLo = kRadius - 4096;  // shared-memory window of bins
-constexpr int kHistWin = 8192;
+constexpr int kHistWin = 2048;              // bins per warp-private window
+constexpr int kHistLo = kRadius - kHistWin / 2;
+constexpr int kHistWarps = 8;
 
 // ---------------------------------------------------------------------
-// histogram of the 65536 code symbols + per-chunk count of code 0
+// histogram of the 65536 code symbols + per-chunk count of code 0.  Each
+// warp owns a private window of bins in shared memory (contention only
+// between lanes of one warp); the three central bins are counted in
+// registers; bins outside the window go straight to global atomics.
 // ---------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
     k_hist(const uint16_t* __restrict__ codes, uint32_t N, uint32_t C,
            uint32_t nch, uint32_t* __restrict__ hist, uint32_t* __restrict__ zc,
            const Ctl* __restrict__ ctl) {
   if (ctl->status || ctl->is_const) return;
-  __shared__ uint32_t sh[kHistWin];
-  for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) sh[i] = 0;
+  extern __shared__ uint32_t shw[];  // [kHistWarps][kHistWin]
+  for (int i = threadIdx.x; i < kHistWarps * kHistWin; i += blockDim.x) shw[i] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
+  uint32_t* sh = shw + (threadIdx.x >> 5) * kHistWin;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   uint32_t cm1 = 0, c0 = 0, cp1 = 0;  // the three central bins in registers
@@ -50,15 +55,22 @@ __global__ void __launch_bounds__(256)
     uint32_t zeros = 0;
     if (end - beg == C) {
       const uint4* p = reinterpret_cast<const uint4*>(codes + beg);
-      for (uint32_t i = lane; i < C / 8; i += 32) {
-        uint4 v = __ldcs(p + i);
-        const unsigned w[4] = {v.x, v.y, v.z, v.w};
+      for (uint32_t i = lane; i < C / 8; i += 64) {
+        uint4 v[2];
+        v[0] = __ldcs(p + i);
+        v[1] = i + 32 < C / 8 ? __ldcs(p + i + 32) : make_uint4(kRadius | (kRadius << 16), kRadius | (kRadius << 16), kRadius | (kRadius << 16), kRadius | (kRadius << 16));
+        const bool two = i + 32 < C / 8;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const unsigned lo = w[k] & 0xFFFFu, hi = w[k] >> 16;
-          add(lo);
-          add(hi);
-          zeros += (lo == 0) + (hi == 0);
+        for (int h = 0; h < 2; ++h) {
+          if (h == 1 && !two) break;
+          const unsigned w[4] = {v[h].x, v[h].y, v[h].z, v[h].w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const unsigned lo = w[k] & 0xFFFFu, hi = w[k] >> 16;
+            add(lo);
+            add(hi);
+            zeros += (lo == 0) + (hi == 0);
+          }
         }
       }
     } else {
@@ -77,13 +89,17 @@ __global__ void __launch_bounds__(256)
     cp1 += __shfl_xor_sync(0xffffffffu, cp1, o);
   }
   if (lane == 0) {
-    if (cm1) atomicAdd(&sh[kRadius - 1 - kHistLo], cm1);
-    if (c0) atomicAdd(&sh[kRadius - kHistLo], c0);
-    if (cp1) atomicAdd(&sh[kRadius + 1 - kHistLo], cp1);
+    sh[kRadius - 1 - kHistLo] += cm1;
+    sh[kRadius - kHistLo] += c0;
+    sh[kRadius + 1 - kHistLo] += cp1;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < kHistWin; i += blockDim.x)
-    if (sh[i]) atomicAdd(&hist[kHistLo + i], sh[i]);
+  for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int w = 0; w < kHistWarps; ++w) t += shw[w * kHistWin + i];
+    if (t) atomicAdd(&hist[kHistLo + i], t);
+  }
 }
 
 // ---------------------------------------------------------------------
@@ -753,8 +769,14 @@ static inline unsigned warps_grid(uint32_t nch, int num_sms) {
 void launch_hist(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,
                  uint32_t* hist, uint32_t* zc, const Ctl* ctl, int num_sms,
                  cudaStream_t s) {
-  k_hist<<<warps_grid(nch, num_sms), 256, 0, s>>>(codes, N, C, nch, hist, zc,
-                                                  ctl);
+  static bool attr = false;
+  const int smem = kHistWarps * kHistWin * (int)sizeof(uint32_t);
+  if (!attr) {
+    cudaFuncSetAttribute(k_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  k_hist<<<warps_grid(nch, num_sms), 256, smem, s>>>(codes, N, C, nch, hist, zc,
+                                                     ctl);
 }
 
 void launch_codebook(const uint32_t* hist, unsigned long long* enc,

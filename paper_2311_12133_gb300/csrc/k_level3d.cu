@@ -81,17 +81,13 @@ __device__ __forceinline__ int edge_formula(bool hm3, bool hp1, bool hp3) {
 // [2][E1][W]; decompress stages the region's codes [2][RR][W].  A lane
 // works on 4 consecutive columns through float4 accesses (conflict-free),
 // and pass 3 writes whole rows of codes / reconstructions to global memory.
-constexpr int kHWin = 1024;  // histogram bins kept in shared memory
-constexpr int kHLo = kRadius - kHWin / 2;
-
 template <bool kDecomp, int KIND>
 __global__ void __launch_bounds__(256)
     k_level3d(Level3D P, const float* __restrict__ X,
               const uint16_t* __restrict__ codes_full,
               const float* __restrict__ outl_full, const float* __restrict__ Rc,
               const uint16_t* __restrict__ Cc, float* __restrict__ Rs,
-              uint16_t* __restrict__ Cs, uint32_t* __restrict__ hist,
-              uint32_t* __restrict__ zc, const Ctl* __restrict__ ctl) {
+              uint16_t* __restrict__ Cs, const Ctl* __restrict__ ctl) {
   if (ctl->status || ctl->is_const) return;
   extern __shared__ float4 sm4[];
   float* sm = reinterpret_cast<float*>(sm4);
@@ -114,13 +110,6 @@ __global__ void __launch_bounds__(256)
   uint16_t* ctile = reinterpret_cast<uint16_t*>(sm + 2 * RR * W);  // compress
   uint16_t* scode = ctile;                                            // decompress
   auto trow = [&](int plane, int row) { return (plane * P.E1 + (row - R0)) * W; };
-  // compress, finest level: histogram of the final codes (a window of bins
-  // in shared memory, the three central bins in registers) and per-chunk
-  // counts of the escape code
-  uint32_t* shist = reinterpret_cast<uint32_t*>(ctile + 2 * P.E1 * W);
-  uint32_t hm1 = 0, h0 = 0, hp1c = 0;
-  if (!kDecomp && P.hist)
-    for (int i = threadIdx.x; i < kHWin; i += blockDim.x) shist[i] = 0;
   const uint32_t gst0 = (uint32_t)m1 * (uint32_t)m2, gst1 = (uint32_t)m2;
   const int nc4 = (m2 + 3) >> 2;  // float4 groups per row
 
@@ -313,25 +302,6 @@ __global__ void __launch_bounds__(256)
         if (!kDecomp) {
           const uint16_t c0 = ctile[to + col0];
           const uint16_t c2 = col0 + 2 < m2 ? ctile[to + col0 + 2] : 0;
-          if (P.hist) {
-            const unsigned cv4[4] = {c0, code[0], c2, code[1]};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              if (col0 + q >= m2) break;
-              const unsigned v = cv4[q];
-              hm1 += v == kRadius - 1;
-              h0 += v == kRadius;
-              hp1c += v == kRadius + 1;
-              if (v < kRadius - 1 || v > kRadius + 1) {
-                const int o = (int)v - kHLo;
-                if (o >= 0 && o < kHWin)
-                  atomicAdd(&shist[o], 1u);
-                else
-                  atomicAdd(&hist[v], 1u);
-                if (v == 0) atomicAdd(&zc[(grow + (uint32_t)(col0 + q)) / P.C], 1u);
-              }
-            }
-          }
           if (full) {
             *reinterpret_cast<uint2*>(Cs + grow + col0) =
                 make_uint2((uint32_t)c0 | (code[0] << 16), (uint32_t)c2 | (code[1] << 16));
@@ -355,34 +325,18 @@ __global__ void __launch_bounds__(256)
       }
     }
   }
-  if (!kDecomp && P.hist) {
-    for (int o = 16; o > 0; o >>= 1) {
-      hm1 += __shfl_xor_sync(0xffffffffu, hm1, o);
-      h0 += __shfl_xor_sync(0xffffffffu, h0, o);
-      hp1c += __shfl_xor_sync(0xffffffffu, hp1c, o);
-    }
-    if (lane == 0) {
-      if (hm1) atomicAdd(&shist[kRadius - 1 - kHLo], hm1);
-      if (h0) atomicAdd(&shist[kRadius - kHLo], h0);
-      if (hp1c) atomicAdd(&shist[kRadius + 1 - kHLo], hp1c);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kHWin; i += blockDim.x)
-      if (shist[i]) atomicAdd(&hist[kHLo + i], shist[i]);
-  }
 }
 
 size_t level3d_smem_bytes(const Level3D& P, bool decomp) {
   size_t b = 2ull * (P.E1 + 6) * P.W * sizeof(float);
   if (decomp && P.stage_codes) b += 2ull * (P.E1 + 6) * P.W * sizeof(uint16_t);
-  if (!decomp) b += 2ull * P.E1 * P.W * sizeof(uint16_t) + (P.hist ? kHWin * 4 : 0);
+  if (!decomp) b += 2ull * P.E1 * P.W * sizeof(uint16_t);
   return b;
 }
 
 template <bool kDecomp, int KIND>
 static void launch3(const Level3D& P, const SweepBufs& B, const float* Rc,
-                    const uint16_t* Cc, float* Rs, uint16_t* Cs, uint32_t* hist,
-                    uint32_t* zc, cudaStream_t s) {
+                    const uint16_t* Cc, float* Rs, uint16_t* Cs, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_level3d<kDecomp, KIND>,
@@ -391,20 +345,20 @@ static void launch3(const Level3D& P, const SweepBufs& B, const float* Rc,
   }
   const unsigned grid = (unsigned)(P.nt0 * P.nt1);
   k_level3d<kDecomp, KIND><<<grid, 256, level3d_smem_bytes(P, kDecomp), s>>>(
-      P, B.x, B.codes_full, B.outl_full, Rc, Cc, Rs, Cs, hist, zc, B.ctl);
+      P, B.x, B.codes_full, B.outl_full, Rc, Cc, Rs, Cs, B.ctl);
 }
 
 void launch_level3d(bool decomp, const Level3D& P, const SweepBufs& B,
                     const float* Rc, const uint16_t* Cc, float* Rs, uint16_t* Cs,
-                    uint32_t* hist, uint32_t* zc, cudaStream_t s) {
+                    cudaStream_t s) {
   if (decomp) {
-    if (B.kind == LINEAR) launch3<true, LINEAR>(P, B, Rc, Cc, Rs, Cs, hist, zc, s);
-    else if (B.kind == CUBIC_NAK) launch3<true, CUBIC_NAK>(P, B, Rc, Cc, Rs, Cs, hist, zc, s);
-    else launch3<true, CUBIC_NAT>(P, B, Rc, Cc, Rs, Cs, hist, zc, s);
+    if (B.kind == LINEAR) launch3<true, LINEAR>(P, B, Rc, Cc, Rs, Cs, s);
+    else if (B.kind == CUBIC_NAK) launch3<true, CUBIC_NAK>(P, B, Rc, Cc, Rs, Cs, s);
+    else launch3<true, CUBIC_NAT>(P, B, Rc, Cc, Rs, Cs, s);
   } else {
-    if (B.kind == LINEAR) launch3<false, LINEAR>(P, B, Rc, Cc, Rs, Cs, hist, zc, s);
-    else if (B.kind == CUBIC_NAK) launch3<false, CUBIC_NAK>(P, B, Rc, Cc, Rs, Cs, hist, zc, s);
-    else launch3<false, CUBIC_NAT>(P, B, Rc, Cc, Rs, Cs, hist, zc, s);
+    if (B.kind == LINEAR) launch3<false, LINEAR>(P, B, Rc, Cc, Rs, Cs, s);
+    else if (B.kind == CUBIC_NAK) launch3<false, CUBIC_NAK>(P, B, Rc, Cc, Rs, Cs, s);
+    else launch3<false, CUBIC_NAT>(P, B, Rc, Cc, Rs, Cs, s);
   }
 }
 
