@@ -404,7 +404,20 @@ typedef struct {
   uint64_t bad_reads, double_visits, predicted;
   int decompress;
   uint64_t nb[3];      /* blocks per real dim (block map) */
+  /* tuning hooks (compress only; NULL when unused) */
+  uint64_t* score;     /* [level]: sum of fixed-point |x - p| / e_l */
+  uint64_t* chist;     /* [65536]: codes of predicted points */
+  uint64_t nout;       /* escapes among predicted points */
 } sweep;
+
+/* Fixed-point error measure of the tuner: |d| / e_l as an IEEE double,
+ * capped at 2^24, in units of 1/256, floored.  Integer sums of it do not
+ * depend on the summation order. */
+static uint64_t err_fixed(float d, double inv_el) {
+  double v = fabs((double)d) * inv_el;
+  v = fmin(v, 16777216.0);
+  return (uint64_t)floor(v * 256.0);
+}
 
 static float load_known(sweep* w, uint64_t idx) {
   uint32_t st = w->stamp[idx];
@@ -487,6 +500,10 @@ static void process_point(sweep* w, int l, uint64_t i, const uint64_t c[3],
     w->codes[i] = ora_quantize(w->x[i], p, w->el[l - 1], w->inv2[l - 1],
                                w->twoe[l - 1], &r);
     w->recon[i] = r;
+    if (w->score)
+      w->score[l - 1] += err_fixed(w->x[i] - p, 1.0 / (double)w->el[l - 1]);
+    if (w->chist) w->chist[w->codes[i]]++;
+    if (w->codes[i] == 0) w->nout++;
   } else {
     uint16_t code = w->codes[i];
     if (code != 0) {
@@ -1158,4 +1175,571 @@ int ora_decompress(const uint8_t* in, uint64_t size, float* out,
   }
   free(syms); free(lns); free(sorted); free(codes); free(w.stamp);
   return rc;
+}
+
+/* ================================================================== */
+/* Auto-tuning (Sec. 6): statistics on a sample (6.1), per-level global  */
+/* interpolation tuning on sampled blocks (6.2), level error bounds      */
+/* alpha/beta (6.4), dimension freezing (6.3), Lorenzo test (6.5),       */
+/* block-wise interpolator choice (6.6).  Every score is an integer     */
+/* (fixed-point errors, Huffman bit counts), so decisions do not depend  */
+/* on summation order.                                                   */
+/* ================================================================== */
+
+void ora_default_tune_params(ora_tune_params* t) {
+  memset(t, 0, sizeof(*t));
+  t->sample_rate = 0.002;
+  t->block_rate = 0.01;
+  t->sub_frac = 0.04;
+  t->lorenzo_coef = 1.0;
+  t->block_size = 32;
+  t->tune_levels = 1;
+  t->tune_eb = 1;
+  t->tune_freeze = 1;
+  t->tune_lorenzo = 1;
+  t->tune_blockwise = 1;
+  t->allow_natural = 1;
+  t->allow_same_level = 1;
+  t->anchor_stride = 0;
+}
+
+/* squared error in units of e^2 / 256 (|d| / e capped at 2^16) */
+static uint64_t sq_fixed(float d, double inv_e) {
+  double v = fabs((double)d) * inv_e;
+  v = fmin(v, 65536.0);
+  return (uint64_t)floor(v * v * 256.0);
+}
+
+/* number of bits of a Huffman code for these counts (sum of freq * len) */
+static uint64_t huff_cost(const uint64_t* hist) {
+  uint8_t* lens = (uint8_t*)malloc(65536);
+  uint64_t c = 0;
+  if (ora_huffman_lengths(hist, 65536, lens) == ORA_OK)
+    for (int i = 0; i < 65536; ++i) c += hist[i] * (uint64_t)lens[i];
+  free(lens);
+  return c;
+}
+
+/* Runs the sweep on an extracted sub-field from the coarsest level down to
+ * level l_stop: per-level scores, code histogram and escapes of the
+ * predicted points.  *n_anchors receives the anchor count. */
+int ora_subfield_test(const float* xs, int ndim, const uint64_t* ds,
+                         const ora_config* c, float e, int l_stop,
+                         uint64_t* score, uint64_t* chist, uint64_t* nout,
+                         uint64_t* n_anchors) {
+  geom g;
+  int rc = geom_init(&g, ndim, ds, c->anchor_stride, c->frozen_dim);
+  if (rc) return rc;
+  sweep w;
+  memset(&w, 0, sizeof(w));
+  w.g = &g;
+  w.c = c;
+  if (ora_level_params(e, c->alpha, c->beta, g.L, w.el, w.inv2, w.twoe))
+    return ORA_ERR_INVALID_ARG;
+  const uint64_t N = g.N;
+  w.x = xs;
+  w.recon = (float*)malloc(sizeof(float) * N);
+  w.codes = (uint16_t*)malloc(sizeof(uint16_t) * N);
+  w.stamp = (uint32_t*)calloc(N, sizeof(uint32_t));
+  w.score = score;
+  w.chist = chist;
+  uint64_t na = 0;
+  uint64_t cc[3];
+  for (cc[0] = 0; cc[0] < g.n[0]; ++cc[0])
+    for (cc[1] = 0; cc[1] < g.n[1]; ++cc[1])
+      for (cc[2] = 0; cc[2] < g.n[2]; ++cc[2]) {
+        uint64_t i = cc[0] * g.st[0] + cc[1] * g.st[1] + cc[2];
+        if (is_anchor(&g, cc)) {
+          w.recon[i] = xs[i];
+          w.codes[i] = ORA_RADIUS;
+          w.stamp[i] = 1;
+          na++;
+        }
+      }
+  w.cur = 1;
+  for (int l = g.L; l >= l_stop && l >= 1; --l) run_level(&w, l);
+  if (nout) *nout += w.nout;
+  if (n_anchors) *n_anchors += na;
+  free(w.recon);
+  free(w.codes);
+  free(w.stamp);
+  return ORA_OK;
+}
+
+/* region [start, start + ext) of the field, row-major */
+static float* extract(const float* x, int ndim, const uint64_t* dims,
+                      const uint64_t* start, const uint64_t* ext) {
+  uint64_t n[3] = {1, 1, 1}, st[3] = {0, 0, 0}, e3[3] = {1, 1, 1};
+  int off = 3 - ndim;
+  for (int d = 0; d < ndim; ++d) {
+    n[d + off] = dims[d];
+    st[d + off] = start[d];
+    e3[d + off] = ext[d];
+  }
+  float* out = (float*)malloc(sizeof(float) * e3[0] * e3[1] * e3[2]);
+  uint64_t k = 0;
+  for (uint64_t a = 0; a < e3[0]; ++a)
+    for (uint64_t b = 0; b < e3[1]; ++b)
+      for (uint64_t c = 0; c < e3[2]; ++c)
+        out[k++] = x[((st[0] + a) * n[1] + (st[1] + b)) * n[2] + st[2] + c];
+  return out;
+}
+
+/* Candidate j of the global per-level tuning (Sec. 6.2): interpolator
+ * (linear, not-a-knot, natural) x paradigm (each 1D-style order of the
+ * interpolation dims in lexicographic order, then multi-dimensional) x
+ * same-level (cubic only).  Returns 0 past the end of the list. */
+int ora_tune_candidate(const ora_tune_params* tp, int ndim, int frozen, int j,
+                       int* kind, int* paradigm, uint8_t order[3], int* same) {
+  int dims[3], k = 0;
+  for (int d = 0; d < ndim; ++d)
+    if (d != frozen) dims[k++] = d;
+  /* orders of the k dims, lexicographic */
+  int perms[6][3], np = 0;
+  for (int a = 0; a < k; ++a)
+    for (int b = 0; b < k; ++b)
+      for (int c = 0; c < k; ++c) {
+        if (k >= 2 && b == a) continue;
+        if (k >= 3 && (c == a || c == b)) continue;
+        if (k < 2 && b != 0) continue;
+        if (k < 3 && c != 0) continue;
+        perms[np][0] = dims[a];
+        perms[np][1] = k > 1 ? dims[b] : 255;
+        perms[np][2] = k > 2 ? dims[c] : 255;
+        np++;
+      }
+  const int nvar = np + (k >= 2 ? 1 : 0);
+  int idx = 0;
+  for (int kd = 0; kd < 3; ++kd) {
+    if (kd == ORA_CUBIC_NAT && !tp->allow_natural) continue;
+    const int nsl = (kd == ORA_LINEAR || !tp->allow_same_level) ? 1 : 2;
+    for (int v = 0; v < nvar; ++v)
+      for (int sl = 0; sl < nsl; ++sl) {
+        if (idx == j) {
+          *kind = kd;
+          *same = sl;
+          if (v < np) {
+            *paradigm = ORA_1D;
+            for (int q = 0; q < 3; ++q) order[q] = (uint8_t)perms[v][q];
+          } else {
+            *paradigm = ORA_MD;
+            for (int q = 0; q < 3; ++q) order[q] = (uint8_t)(q < k ? dims[q] : 255);
+          }
+          return 1;
+        }
+        idx++;
+      }
+  }
+  return 0;
+}
+
+static void set_level(ora_config* c, int l, int kind, int paradigm,
+                      const uint8_t order[3], int same) {
+  c->interp[l - 1] = (uint8_t)kind;
+  c->paradigm[l - 1] = (uint8_t)paradigm;
+  c->same_level[l - 1] = (uint8_t)same;
+  for (int q = 0; q < 3; ++q) c->order[l - 1][q] = order[q];
+}
+
+typedef struct {
+  int nblk;
+  float** xs;
+  uint64_t (*ds)[3];
+} blockset;
+
+/* Sample blocks of the global tuning: blocks of B + 1 points (B = the
+ * anchor stride) on a lattice of block indices, every tau-th block per
+ * dim, tau the smallest stride giving at most block_rate * N / B^ndim
+ * blocks (at least one). */
+static void sample_blocks(const float* x, int ndim, const uint64_t* dims,
+                          int B, double rate, blockset* bs) {
+  uint64_t nb[3], N = 1, vol = 1;
+  for (int d = 0; d < ndim; ++d) {
+    nb[d] = (dims[d] - 1) / (uint64_t)B;
+    N *= dims[d];
+    vol *= (uint64_t)B;
+  }
+  double tgt = floor(rate * (double)N / (double)vol + 0.5);
+  uint64_t target = tgt < 1.0 ? 1 : (uint64_t)tgt;
+  uint64_t tau = 1;
+  for (;;) {
+    uint64_t cnt = 1;
+    for (int d = 0; d < ndim; ++d) {
+      uint64_t m = nb[d] ? nb[d] : 1;
+      cnt *= (m + tau - 1) / tau;
+    }
+    if (cnt <= target) break;
+    tau++;
+  }
+  uint64_t cntd[3] = {1, 1, 1};
+  int total = 1;
+  for (int d = 0; d < ndim; ++d) {
+    uint64_t m = nb[d] ? nb[d] : 1;
+    cntd[d] = (m + tau - 1) / tau;
+    total *= (int)cntd[d];
+  }
+  bs->nblk = total;
+  bs->xs = (float**)malloc(sizeof(float*) * (size_t)total);
+  bs->ds = (uint64_t(*)[3])malloc(sizeof(uint64_t[3]) * (size_t)total);
+  for (int t = 0; t < total; ++t) {
+    uint64_t r = (uint64_t)t, start[3], ext[3];
+    for (int d = ndim - 1; d >= 0; --d) {
+      uint64_t j = r % cntd[d];
+      r /= cntd[d];
+      if (nb[d]) {
+        start[d] = j * tau * (uint64_t)B;
+        ext[d] = (uint64_t)B + 1;
+      } else {
+        start[d] = 0;
+        ext[d] = dims[d];
+      }
+      bs->ds[t][d] = ext[d];
+    }
+    bs->xs[t] = extract(x, ndim, dims, start, ext);
+  }
+}
+
+static void free_blocks(blockset* bs) {
+  for (int t = 0; t < bs->nblk; ++t) free(bs->xs[t]);
+  free(bs->xs);
+  free(bs->ds);
+}
+
+/* bits of compressing the sample blocks with c: Huffman bits of the codes
+ * + 32 per escape + 32 per anchor */
+static uint64_t blocks_bits(const blockset* bs, int ndim, const ora_config* c,
+                            float e, uint64_t* anchors_out) {
+  uint64_t* hist = (uint64_t*)calloc(65536, sizeof(uint64_t));
+  uint64_t nout = 0, na = 0;
+  for (int t = 0; t < bs->nblk; ++t)
+    ora_subfield_test(bs->xs[t], ndim, bs->ds[t], c, e, 1, NULL, hist, &nout, &na);
+  uint64_t bits = huff_cost(hist) + 32 * nout + 32 * na;
+  free(hist);
+  if (anchors_out) *anchors_out = na;
+  return bits;
+}
+
+static const double kAlpha[5] = {1.0, 1.25, 1.5, 1.75, 2.0};
+static const double kBeta[4] = {2.0, 4.0, 8.0, 16.0};
+
+/* a12 + a13 for one frozen-dim choice; returns the sample bits estimate */
+static uint64_t tune_global(const float* x, int ndim, const uint64_t* dims,
+                            float e, const ora_tune_params* tp, int frozen,
+                            const double* inv_var, ora_config* cfg,
+                            ora_tune_report* rep, int slot) {
+  ora_default_config(ndim, cfg);
+  if (tp->anchor_stride) cfg->anchor_stride = tp->anchor_stride;
+  cfg->frozen_dim = frozen;
+  for (int d = 0; d < 3; ++d) cfg->md_inv_var[d] = inv_var[d];
+  const int A = cfg->anchor_stride;
+  const int L = ilog2((uint64_t)A);
+  /* default order lists the interpolation dims only */
+  for (int l = 0; l < ORA_MAX_LEVELS; ++l) {
+    int k = 0;
+    for (int d = 0; d < ndim; ++d)
+      if (d != frozen) cfg->order[l][k++] = (uint8_t)d;
+    for (; k < 3; ++k) cfg->order[l][k] = 255;
+  }
+  blockset bs;
+  sample_blocks(x, ndim, dims, A, tp->block_rate, &bs);
+  if (rep && slot == 0) rep->n_sample_blocks = (uint32_t)bs.nblk;
+  if (tp->tune_levels) {
+    for (int l = L; l >= 1; --l) {
+      uint64_t best = UINT64_MAX;
+      int bj = 0;
+      int kind, par, same;
+      uint8_t ord[3];
+      for (int j = 0; ora_tune_candidate(tp, ndim, frozen, j, &kind, &par, ord, &same); ++j) {
+        ora_config c2 = *cfg;
+        set_level(&c2, l, kind, par, ord, same);
+        uint64_t sc[ORA_MAX_LEVELS] = {0};
+        for (int t = 0; t < bs.nblk; ++t)
+          ora_subfield_test(bs.xs[t], ndim, bs.ds[t], &c2, e, l, sc, NULL, NULL, NULL);
+        if (sc[l - 1] < best) {
+          best = sc[l - 1];
+          bj = j;
+        }
+      }
+      ora_tune_candidate(tp, ndim, frozen, bj, &kind, &par, ord, &same);
+      set_level(cfg, l, kind, par, ord, same);
+      if (rep) {
+        rep->level_choice[slot][l - 1] = (uint8_t)bj;
+        rep->level_score[slot][l - 1] = best;
+      }
+    }
+  }
+  if (tp->tune_eb) {
+    uint64_t best = UINT64_MAX;
+    double ba = 1.0, bb = 1.0;
+    for (int ia = 0; ia < 5; ++ia)
+      for (int ib = 0; ib < (ia == 0 ? 1 : 4); ++ib) {
+        ora_config c2 = *cfg;
+        c2.alpha = kAlpha[ia];
+        c2.beta = ia == 0 ? 1.0 : kBeta[ib];
+        uint64_t bits = blocks_bits(&bs, ndim, &c2, e, NULL);
+        if (bits < best) {
+          best = bits;
+          ba = c2.alpha;
+          bb = c2.beta;
+        }
+      }
+    cfg->alpha = ba;
+    cfg->beta = bb;
+  }
+  uint64_t na = 0;
+  uint64_t bits = blocks_bits(&bs, ndim, cfg, e, &na);
+  if (rep) rep->bits[slot] = bits;
+  free_blocks(&bs);
+  return bits;
+}
+
+/* Lorenzo prediction test on a sub-field (Sec. 6.5): order 1 or 2,
+ * neighbours outside the block read as 0, quantized with the global bound */
+static void lorenzo_test(const float* xs, int ndim, const uint64_t* ds, int order,
+                         float e, uint64_t* hist, uint64_t* nout) {
+  uint64_t n[3] = {1, 1, 1};
+  int off = 3 - ndim;
+  for (int d = 0; d < ndim; ++d) n[d + off] = ds[d];
+  const uint64_t N = n[0] * n[1] * n[2];
+  float* r = (float*)malloc(sizeof(float) * N);
+  const float inv2 = (float)(1.0 / (2.0 * (double)e));
+  const float twoe = 2.0f * e;
+  const float co[2][3] = {{1.0f, -1.0f, 0.0f}, {1.0f, -2.0f, 1.0f}};
+  const int lim[3] = {off > 0 ? 0 : order, off > 1 ? 0 : order, order};
+  for (uint64_t i0 = 0; i0 < n[0]; ++i0)
+    for (uint64_t i1 = 0; i1 < n[1]; ++i1)
+      for (uint64_t i2 = 0; i2 < n[2]; ++i2) {
+        float acc = 0.0f;
+        for (int a = 0; a <= lim[0]; ++a)
+          for (int b = 0; b <= lim[1]; ++b)
+            for (int c = 0; c <= lim[2]; ++c) {
+              if (a == 0 && b == 0 && c == 0) continue;
+              const float wgt = -(co[order - 1][a] * co[order - 1][b] * co[order - 1][c]);
+              float v = 0.0f;
+              if ((uint64_t)a <= i0 && (uint64_t)b <= i1 && (uint64_t)c <= i2)
+                v = r[((i0 - a) * n[1] + (i1 - b)) * n[2] + (i2 - c)];
+              acc = acc + wgt * v;
+            }
+        const uint64_t i = (i0 * n[1] + i1) * n[2] + i2;
+        float rec;
+        uint16_t code = ora_quantize(xs[i], acc, e, inv2, twoe, &rec);
+        r[i] = rec;
+        hist[code]++;
+        if (code == 0) (*nout)++;
+      }
+  free(r);
+}
+
+uint64_t ora_blockmap_size(int ndim, const uint64_t* dims, int bs) {
+  if (bs < 1 || ndim < 1 || ndim > 3) return 0;
+  uint64_t t = 1;
+  for (int d = 0; d < ndim; ++d) t *= (dims[d] + (uint64_t)bs - 1) / (uint64_t)bs;
+  return t;
+}
+
+int ora_tune(const float* x, int ndim, const uint64_t* dims, int eb_mode,
+             double eb, const ora_tune_params* tp_in, ora_config* out,
+             uint8_t* blockmap, uint64_t blockmap_cap, ora_tune_report* rep) {
+  ora_tune_params tpd;
+  if (!tp_in) {
+    ora_default_tune_params(&tpd);
+    tp_in = &tpd;
+  }
+  const ora_tune_params* tp = tp_in;
+  if (!x || !dims || !out || ndim < 1 || ndim > 3) return ORA_ERR_INVALID_ARG;
+  if (eb_mode != ORA_EB_ABS && eb_mode != ORA_EB_REL) return ORA_ERR_INVALID_ARG;
+  if (!(eb > 0.0) || !isfinite(eb)) return ORA_ERR_INVALID_ARG;
+  if (tp->block_size < 1 || !(tp->sample_rate > 0.0) || !(tp->block_rate > 0.0) ||
+      !(tp->sub_frac > 0.0) || tp->sub_frac > 1.0)
+    return ORA_ERR_INVALID_ARG;
+  if (tp->tune_blockwise &&
+      (!blockmap || blockmap_cap < ora_blockmap_size(ndim, dims, tp->block_size)))
+    return ORA_ERR_OUT_TOO_SMALL;
+  if (rep) memset(rep, 0, sizeof(*rep));
+  ora_default_config(ndim, out);
+  if (tp->anchor_stride) out->anchor_stride = tp->anchor_stride;
+  geom g0;
+  int rc = geom_init(&g0, ndim, dims, out->anchor_stride, -1);
+  if (rc) return rc;
+  const uint64_t N = g0.N;
+  /* absolute bound exactly as compress derives it */
+  float e;
+  if (eb_mode == ORA_EB_REL) {
+    float vmin = x[0], vmax = x[0];
+    for (uint64_t i = 0; i < N; ++i) {
+      if (!isfinite(x[i])) return ORA_ERR_NONFINITE;
+      if (x[i] < vmin) vmin = x[i];
+      if (x[i] > vmax) vmax = x[i];
+    }
+    double range = (double)vmax - (double)vmin;
+    if (range == 0.0) return ORA_OK; /* constant field: nothing to tune */
+    e = (float)(eb * range);
+  } else {
+    e = (float)eb;
+  }
+  if (!(e > 0.0f) || !isfinite(e)) return ORA_ERR_INVALID_ARG;
+  const double inv_e = 1.0 / (double)e;
+
+  /* a11: statistics on a uniform lattice (Sec. 6.1): MSE of linear and
+   * cubic interpolation along every dim at points with all +-3 neighbours */
+  int t = 1;
+  for (;;) {
+    double p = 1.0;
+    for (int d = 0; d < ndim; ++d) p *= (double)t;
+    if (p * tp->sample_rate >= 1.0) break;
+    t++;
+  }
+  uint64_t cnt = 0, lin[3] = {0, 0, 0}, cub[3] = {0, 0, 0};
+  {
+    uint64_t n[3] = {1, 1, 1}, st[3];
+    const int off = 3 - ndim;
+    for (int d = 0; d < ndim; ++d) n[d + off] = dims[d];
+    st[2] = 1;
+    st[1] = n[2];
+    st[0] = n[1] * n[2];
+    int ok = 1;
+    for (int d = 0; d < ndim; ++d)
+      if (dims[d] < 7) ok = 0;
+    if (ok) {
+      uint64_t c[3];
+      uint64_t lo[3], step[3];
+      for (int sl = 0; sl < 3; ++sl) {
+        lo[sl] = sl < off ? 0 : 3;
+        step[sl] = sl < off ? 1 : (uint64_t)t;
+      }
+      for (c[0] = lo[0]; c[0] + (off > 0 ? 0 : 3) < n[0]; c[0] += step[0])
+        for (c[1] = lo[1]; c[1] + (off > 1 ? 0 : 3) < n[1]; c[1] += step[1])
+          for (c[2] = lo[2]; c[2] + 3 < n[2]; c[2] += step[2]) {
+            const uint64_t i = c[0] * st[0] + c[1] * st[1] + c[2];
+            cnt++;
+            for (int d = 0; d < ndim; ++d) {
+              const uint64_t s = st[d + off];
+              float v[7] = {0, 0, 0, 0, 0, 0, 0};
+              v[0] = x[i - 3 * s];
+              v[2] = x[i - s];
+              v[4] = x[i + s];
+              v[6] = x[i + 3 * s];
+              const float pc = eval_formula(F_NAK4, v);
+              const float pl = eval_formula(F_LIN, v);
+              cub[d] += sq_fixed(x[i] - pc, inv_e);
+              lin[d] += sq_fixed(x[i] - pl, inv_e);
+            }
+          }
+    }
+  }
+  double inv_var[3] = {1.0, 1.0, 1.0};
+  int nonsmooth = -1;
+  if (cnt) {
+    uint64_t mx = 0;
+    for (int d = 0; d < ndim; ++d) {
+      inv_var[d] = (double)cnt * 256.0 / (double)(cub[d] ? cub[d] : 1);
+      if (nonsmooth < 0 || cub[d] > mx) {
+        mx = cub[d];
+        nonsmooth = d;
+      }
+    }
+  }
+  if (rep) {
+    rep->stats_count = cnt;
+    for (int d = 0; d < 3; ++d) {
+      rep->mse_lin[d] = lin[d];
+      rep->mse_cub[d] = cub[d];
+    }
+    rep->nonsmooth_dim = nonsmooth;
+    rep->froze = 0;
+  }
+
+  /* a12 + a13 without freezing, and (a14) with the most non-smooth dim
+   * frozen; the smaller sample estimate wins */
+  ora_config cfg_nf, cfg_f;
+  uint64_t bits_nf = tune_global(x, ndim, dims, e, tp, -1, inv_var, &cfg_nf, rep, 0);
+  *out = cfg_nf;
+  uint64_t bits_best = bits_nf;
+  if (tp->tune_freeze && cnt && ndim >= 2) {
+    uint64_t bits_f = tune_global(x, ndim, dims, e, tp, nonsmooth, inv_var, &cfg_f, rep, 1);
+    if (bits_f < bits_nf) {
+      *out = cfg_f;
+      bits_best = bits_f;
+      if (rep) rep->froze = 1;
+    }
+  }
+
+  /* a15: Lorenzo test on the same sample blocks */
+  if (tp->tune_lorenzo) {
+    blockset bs;
+    sample_blocks(x, ndim, dims, out->anchor_stride, tp->block_rate, &bs);
+    uint64_t lb[2];
+    for (int o = 1; o <= 2; ++o) {
+      uint64_t* hist = (uint64_t*)calloc(65536, sizeof(uint64_t));
+      uint64_t nout = 0;
+      for (int b = 0; b < bs.nblk; ++b)
+        lorenzo_test(bs.xs[b], ndim, bs.ds[b], o, e, hist, &nout);
+      lb[o - 1] = huff_cost(hist) + 32 * nout;
+      free(hist);
+    }
+    free_blocks(&bs);
+    if (rep) {
+      rep->lorenzo_bits[0] = lb[0];
+      rep->lorenzo_bits[1] = lb[1];
+      const uint64_t m = lb[0] < lb[1] ? lb[0] : lb[1];
+      rep->lorenzo_better = (double)m * tp->lorenzo_coef < (double)bits_best;
+    }
+  }
+
+  /* a16: block-wise interpolator choice on a centred sub-block per block */
+  if (tp->tune_blockwise) {
+    const int bsz = tp->block_size;
+    const uint64_t nbt = ora_blockmap_size(ndim, dims, bsz);
+    double q0 = 32.0 * pow(tp->sub_frac, 1.0 / (double)ndim);
+    int Q = (int)floor((double)bsz / 32.0 * q0 + 0.5);
+    if (Q < 5) Q = 5;
+    uint64_t nb[3];
+    for (int d = 0; d < ndim; ++d) nb[d] = (dims[d] + (uint64_t)bsz - 1) / (uint64_t)bsz;
+    static const uint8_t cand_code[5] = {0, 1, 5, 2, 6};
+    for (uint64_t b = 0; b < nbt; ++b) {
+      uint64_t r = b, start[3], ext[3];
+      uint64_t qmin = UINT64_MAX;
+      for (int d = ndim - 1; d >= 0; --d) {
+        const uint64_t j = r % nb[d];
+        r /= nb[d];
+        const uint64_t bstart = j * (uint64_t)bsz;
+        const uint64_t bext = dims[d] - bstart < (uint64_t)bsz ? dims[d] - bstart : (uint64_t)bsz;
+        const uint64_t q = bext < (uint64_t)Q ? bext : (uint64_t)Q;
+        start[d] = bstart + (bext - q) / 2;
+        ext[d] = q;
+        if (d != out->frozen_dim && q < qmin) qmin = q;
+      }
+      int As = 2;
+      while ((uint64_t)(As * 2) <= (qmin > 1 ? qmin - 1 : 1)) As *= 2;
+      float* xs = extract(x, ndim, dims, start, ext);
+      uint64_t best = UINT64_MAX;
+      int bj = 0;
+      for (int j = 0; j < 5; ++j) {
+        const uint8_t v = cand_code[j];
+        if ((v & 3) == ORA_CUBIC_NAT && !tp->allow_natural) continue;
+        if ((v & 4) && !tp->allow_same_level) continue;
+        ora_config c2 = *out;
+        c2.anchor_stride = As;
+        c2.blockwise = 0;
+        for (int l = 0; l < ORA_MAX_LEVELS; ++l) {
+          c2.interp[l] = v & 3;
+          c2.same_level[l] = (v >> 2) & 1;
+        }
+        uint64_t sc[ORA_MAX_LEVELS] = {0};
+        ora_subfield_test(xs, ndim, ext, &c2, e, 1, sc, NULL, NULL, NULL);
+        uint64_t tot = 0;
+        for (int l = 0; l < ORA_MAX_LEVELS; ++l) tot += sc[l];
+        if (tot < best) {
+          best = tot;
+          bj = j;
+        }
+      }
+      blockmap[b] = cand_code[bj];
+      free(xs);
+    }
+    out->blockwise = 1;
+    out->block_size = bsz;
+    out->blockmap = blockmap;
+  }
+  return ORA_OK;
 }

@@ -108,6 +108,47 @@ int ora_level_params(float e, double alpha, double beta, int L, float* el,
 int ora_huffman_lengths(const uint64_t* freq, int nsym, uint8_t* lens);
 int ora_canonical_codes(const uint8_t* lens, int nsym, uint64_t* codes);
 
+/* ---- auto-tuning (Sec. 6) ---- */
+typedef struct {
+  double sample_rate;   /* statistics lattice density (Sec. 6.1: 0.2 %) */
+  double block_rate;    /* global tuning: sampled volume fraction (1 %) */
+  double sub_frac;      /* block-wise tuning: sub-block fraction (4 %) */
+  double lorenzo_coef;  /* multiplier of the Lorenzo bit estimate */
+  int32_t block_size;   /* block-wise tuning block side (Sec. 6.6: 32) */
+  int32_t tune_levels, tune_eb, tune_freeze, tune_lorenzo, tune_blockwise;
+  int32_t allow_natural, allow_same_level;
+  int32_t anchor_stride; /* 0: default for ndim */
+} ora_tune_params;
+
+typedef struct {
+  uint64_t stats_count, mse_lin[3], mse_cub[3]; /* fixed-point sums */
+  int32_t nonsmooth_dim, froze, lorenzo_better;
+  uint32_t n_sample_blocks;
+  uint64_t bits[2];          /* sample estimate without / with freezing */
+  uint64_t lorenzo_bits[2];  /* order 1, order 2 */
+  uint8_t level_choice[2][ORA_MAX_LEVELS];
+  uint64_t level_score[2][ORA_MAX_LEVELS];
+} ora_tune_report;
+
+void ora_default_tune_params(ora_tune_params* t);
+/* Candidate j of the per-level global tuning; returns 0 past the end. */
+int ora_tune_candidate(const ora_tune_params* tp, int ndim, int frozen, int j,
+                       int* kind, int* paradigm, uint8_t order[3], int* same);
+/* Compression test on a sub-field: anchors, then levels L .. l_stop with
+ * config c and absolute bound e.  Adds the per-level error scores, the code
+ * histogram (65536 bins), the escapes and the anchors to the non-NULL
+ * accumulators. */
+int ora_subfield_test(const float* xs, int ndim, const uint64_t* ds,
+                      const ora_config* c, float e, int l_stop,
+                      uint64_t* score, uint64_t* hist, uint64_t* nout,
+                      uint64_t* n_anchors);
+uint64_t ora_blockmap_size(int ndim, const uint64_t* dims, int block_size);
+/* Tunes theta for x; out->blockmap points at `blockmap` when the block-wise
+ * map is produced.  Returns 0 or a negative ORA_ERR_*. */
+int ora_tune(const float* x, int ndim, const uint64_t* dims, int eb_mode,
+             double eb, const ora_tune_params* tp, ora_config* out,
+             uint8_t* blockmap, uint64_t blockmap_cap, ora_tune_report* rep);
+
 /* MD weight of dimension d within the odd-dimension set `mask` (Eq. 14). */
 float ora_md_weight(const double* inv_var, unsigned mask, int d);
 

@@ -71,6 +71,40 @@ class Stats(ctypes.Structure):
                             ("vmax", ctypes.c_float)]
 
 
+class TuneParams(ctypes.Structure):
+    _fields_ = [
+        ("sample_rate", ctypes.c_double),
+        ("block_rate", ctypes.c_double),
+        ("sub_frac", ctypes.c_double),
+        ("lorenzo_coef", ctypes.c_double),
+        ("block_size", ctypes.c_int32),
+        ("tune_levels", ctypes.c_int32),
+        ("tune_eb", ctypes.c_int32),
+        ("tune_freeze", ctypes.c_int32),
+        ("tune_lorenzo", ctypes.c_int32),
+        ("tune_blockwise", ctypes.c_int32),
+        ("allow_natural", ctypes.c_int32),
+        ("allow_same_level", ctypes.c_int32),
+        ("anchor_stride", ctypes.c_int32),
+    ]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [
+        ("stats_count", ctypes.c_uint64),
+        ("mse_lin", ctypes.c_uint64 * 3),
+        ("mse_cub", ctypes.c_uint64 * 3),
+        ("nonsmooth_dim", ctypes.c_int32),
+        ("froze", ctypes.c_int32),
+        ("lorenzo_better", ctypes.c_int32),
+        ("n_sample_blocks", ctypes.c_uint32),
+        ("bits", ctypes.c_uint64 * 2),
+        ("lorenzo_bits", ctypes.c_uint64 * 2),
+        ("level_choice", (ctypes.c_uint8 * MAX_LEVELS) * 2),
+        ("level_score", (ctypes.c_uint64 * MAX_LEVELS) * 2),
+    ]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -131,6 +165,27 @@ def lib():
             L.ora_inspect.argtypes = [ctypes.c_void_p, ctypes.c_uint64,
                                       ctypes.POINTER(ctypes.c_int), u64p,
                                       ctypes.POINTER(ctypes.c_double)]
+            L.ora_default_tune_params.restype = None
+            L.ora_default_tune_params.argtypes = [ctypes.POINTER(TuneParams)]
+            L.ora_blockmap_size.restype = ctypes.c_uint64
+            L.ora_blockmap_size.argtypes = [ctypes.c_int, u64p, ctypes.c_int]
+            L.ora_tune.restype = ctypes.c_int
+            L.ora_tune.argtypes = [
+                ctypes.c_void_p, ctypes.c_int, u64p, ctypes.c_int,
+                ctypes.c_double, ctypes.POINTER(TuneParams),
+                ctypes.POINTER(Config), ctypes.c_void_p, ctypes.c_uint64,
+                ctypes.POINTER(TuneReport)]
+            L.ora_tune_candidate.restype = ctypes.c_int
+            L.ora_tune_candidate.argtypes = [
+                ctypes.POINTER(TuneParams), ctypes.c_int, ctypes.c_int,
+                ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                ctypes.POINTER(ctypes.c_int), ctypes.c_void_p,
+                ctypes.POINTER(ctypes.c_int)]
+            L.ora_subfield_test.restype = ctypes.c_int
+            L.ora_subfield_test.argtypes = [
+                ctypes.c_void_p, ctypes.c_int, u64p, ctypes.POINTER(Config),
+                ctypes.c_float, ctypes.c_int, ctypes.c_void_p,
+                ctypes.c_void_p, u64p, u64p]
             _lib = L
     return _lib
 
@@ -283,3 +338,72 @@ def canonical_codes(lens) -> np.ndarray:
 def md_weight(inv_var, mask: int, d: int) -> np.float32:
     iv = np.ascontiguousarray(inv_var, dtype=np.float64)
     return np.float32(lib().ora_md_weight(iv.ctypes.data, mask, d))
+
+
+# ---------------------------------------------------------------- tuning
+def default_tune_params(**kw) -> TuneParams:
+    t = TuneParams()
+    lib().ora_default_tune_params(ctypes.byref(t))
+    for k, v in kw.items():
+        setattr(t, k, v)
+    return t
+
+
+def blockmap_size(shape, block_size: int = 32) -> int:
+    dims = (ctypes.c_uint64 * 3)(*[int(v) for v in shape] + [1] * (3 - len(shape)))
+    return int(lib().ora_blockmap_size(len(shape), dims, block_size))
+
+
+def tune(x: np.ndarray, eb: float, eb_mode: int = EB_REL,
+         params: TuneParams | None = None):
+    """Runs the Sec. 6 tuner; returns (config, report).  The config keeps a
+    reference to its block map when one was produced."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    ndim = x.ndim
+    dims = (ctypes.c_uint64 * 3)(*[int(v) for v in x.shape] + [1] * (3 - ndim))
+    tp = params if params is not None else default_tune_params()
+    nbm = blockmap_size(x.shape, tp.block_size)
+    bm = np.zeros(max(nbm, 1), np.uint8)
+    cfg = Config()
+    rep = TuneReport()
+    rc = lib().ora_tune(x.ctypes.data, ndim, dims, eb_mode, float(eb),
+                        ctypes.byref(tp), ctypes.byref(cfg), bm.ctypes.data,
+                        bm.size, ctypes.byref(rep))
+    if rc != 0:
+        raise OracleError(rc)
+    cfg._blockmap_ref = bm[:nbm] if cfg.blockwise else None
+    if cfg.blockwise:
+        cfg.blockmap = cfg._blockmap_ref.ctypes.data
+    return cfg, rep
+
+
+def tune_candidate(ndim: int, frozen: int, j: int,
+                   params: TuneParams | None = None):
+    """(kind, paradigm, order tuple, same_level) of candidate j, or None."""
+    tp = params if params is not None else default_tune_params()
+    kind, par, same = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    order = (ctypes.c_uint8 * 3)()
+    ok = lib().ora_tune_candidate(ctypes.byref(tp), ndim, frozen, j,
+                                  ctypes.byref(kind), ctypes.byref(par),
+                                  order, ctypes.byref(same))
+    if not ok:
+        return None
+    return kind.value, par.value, tuple(order), same.value
+
+
+def subfield_test(xs: np.ndarray, config: Config, e: float, l_stop: int = 1):
+    """Compression test on a sub-field: (scores[16], hist, n_out, n_anchors)."""
+    xs = np.ascontiguousarray(xs, dtype=np.float32)
+    ndim = xs.ndim
+    dims = (ctypes.c_uint64 * 3)(*[int(v) for v in xs.shape] + [1] * (3 - ndim))
+    score = np.zeros(MAX_LEVELS, np.uint64)
+    hist = np.zeros(65536, np.uint64)
+    nout = ctypes.c_uint64(0)
+    na = ctypes.c_uint64(0)
+    rc = lib().ora_subfield_test(xs.ctypes.data, ndim, dims,
+                                 ctypes.byref(config), float(e), l_stop,
+                                 score.ctypes.data, hist.ctypes.data,
+                                 ctypes.byref(nout), ctypes.byref(na))
+    if rc != 0:
+        raise OracleError(rc)
+    return score, hist, nout.value, na.value
