@@ -162,6 +162,82 @@ HPEZ_API int hpez_inspect(const void* h_header, uint64_t n, int* ndim, uint64_t*
 /* Static text for an error code. */
 HPEZ_API const char* hpez_strerror(int code);
 
+/* ---- auto-tuning (Sec. 6) ----
+ * The tuner picks theta for one field from compression tests on samples:
+ *   Sec. 6.1  statistics on a uniform lattice (stride t, the smallest with
+ *             t^ndim * sample_rate >= 1) of points whose +-3 neighbours
+ *             exist on every dim: per dim, the squared error of linear and
+ *             of not-a-knot cubic interpolation of the original values, as
+ *             fixed-point sums of floor(min(|err|/e, 2^16)^2 * 256).  They
+ *             give the Eq. 14 inverse variances count*256/max(sum, 1) and
+ *             the most non-smooth dim (largest cubic sum, first on ties).
+ *   Sec. 6.2  per level, coarsest first, every candidate (linear, then
+ *             not-a-knot, then natural cubic; for each the 1D-style orders
+ *             of the interpolation dims in lexicographic order and then the
+ *             multi-dimensional paradigm; cubic ones without and with
+ *             same-level interpolation) is tested on the sample blocks
+ *             (A+1 points per side on a lattice of blocks, about block_rate
+ *             of the volume); the smallest sum of floor(min(|err|/e_l, 2^24)
+ *             * 256) over the level's points wins, the first on ties.
+ *   Sec. 6.4  (alpha, beta) from {(1,1)} + {1.25,1.5,1.75,2} x {2,4,8,16}:
+ *             the smallest estimate of Huffman bits of the sample codes
+ *             + 32 per escape + 32 per anchor.
+ *   Sec. 6.3  the same tuning with the most non-smooth dim frozen; kept
+ *             if its estimate is smaller.
+ *   Sec. 6.5  order-1 and order-2 Lorenzo tests on the same blocks (zero
+ *             padding, global bound), bits * lorenzo_coef compared with the
+ *             interpolation estimate; reported only (the compressor runs
+ *             interpolation).
+ *   Sec. 6.6  per block of block_size^ndim, a centred sub-block of side
+ *             max(5, round(block_size * sub_frac^(1/ndim))), anchor stride
+ *             the largest power of two <= max(2, side-1); candidates
+ *             linear, not-a-knot, not-a-knot + same-level, natural,
+ *             natural + same-level, one for all levels; the smallest
+ *             summed level score wins -> block map codes 0,1,5,2,6.
+ * All scores are integers, so the choices do not depend on the order of
+ * the reductions. */
+typedef struct {
+  double sample_rate;   /* Sec. 6.1 lattice density, default 0.002 */
+  double block_rate;    /* Sec. 6.2 sampled volume fraction, default 0.01 */
+  double sub_frac;      /* Sec. 6.6 sub-block volume fraction, default 0.04 */
+  double lorenzo_coef;  /* Sec. 6.5 multiplier of the Lorenzo bits, 1.0 */
+  int32_t block_size;   /* Sec. 6.6 block side, default 32 */
+  int32_t tune_levels, tune_eb, tune_freeze, tune_lorenzo, tune_blockwise;
+  int32_t allow_natural, allow_same_level;  /* candidate sets */
+  int32_t anchor_stride; /* 0: the default for ndim */
+} hpez_tune_params;
+
+typedef struct {
+  uint64_t stats_count, mse_lin[3], mse_cub[3]; /* Sec. 6.1 fixed-point sums */
+  int32_t nonsmooth_dim, froze, lorenzo_better;
+  uint32_t n_sample_blocks;
+  uint64_t bits[2];          /* sample estimate without / with freezing */
+  uint64_t lorenzo_bits[2];  /* order 1, order 2 */
+  uint8_t level_choice[2][HPEZ_MAX_LEVELS]; /* candidate index per level */
+  uint64_t level_score[2][HPEZ_MAX_LEVELS]; /* its score */
+} hpez_tune_report;
+
+HPEZ_API int hpez_default_tune_params(hpez_tune_params* out);
+/* Entries of the block map for these dims: prod ceil(dims[d]/block_size). */
+HPEZ_API uint64_t hpez_blockmap_size(int ndim, const uint64_t* dims, int block_size);
+
+/* Tune theta for the field d_in (device, N float32, row-major).
+ *   tp          host, NULL = hpez_default_tune_params
+ *   h_cfg       host, receives theta (ready for hpez_compress)
+ *   h_blockmap  host, >= hpez_blockmap_size entries when tune_blockwise;
+ *               h_cfg->h_blockmap points at it when the map is produced
+ *   h_report    host, optional, the intermediate results
+ * A constant field (relative mode) yields the default theta.  The sample
+ * blocks must fit in shared memory: (A+1)^k * (other extents) * 4 bytes
+ * <= 200 KiB, else UNSUPPORTED.  Errors: INVALID_ARG, NONFINITE_INPUT
+ * (relative mode), OUT_TOO_SMALL (block map), UNSUPPORTED, NO_MEMORY,
+ * CUDA.  Synchronizes `stream` several times (not graph-capturable). */
+HPEZ_API int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim,
+                       const uint64_t* dims, int eb_mode, double eb,
+                       const hpez_tune_params* tp, hpez_config* h_cfg,
+                       uint8_t* h_blockmap, uint64_t blockmap_cap,
+                       hpez_tune_report* h_report, void* stream);
+
 /* Execution options of a context (the results never depend on them):
  *  HPEZ_OPT_FUSED_LEVELS  1 (default): a level of the 1D-style paradigm
  *                         runs as one tiled kernel; 0: one kernel per pass
@@ -196,7 +272,12 @@ HPEZ_API int hpez_set_option(hpez_ctx* ctx, int option, int64_t value);
 #define HPEZ_PH_SCATTER 10  /* outlier scatter */
 #define HPEZ_PH_LEVEL 11    /* + (l-1): compress level l, l = 1..16 */
 #define HPEZ_PH_DLEVEL 27   /* + (l-1): decompress level l */
-#define HPEZ_PROFILE_PHASES 43
+#define HPEZ_PH_TUNE_STATS 43    /* tuner: Sec. 6.1 statistics */
+#define HPEZ_PH_TUNE_LEVELS 44   /* tuner: Sec. 6.2 candidate tests */
+#define HPEZ_PH_TUNE_EB 45       /* tuner: Sec. 6.4 (alpha, beta) tests */
+#define HPEZ_PH_TUNE_LORENZO 46  /* tuner: Sec. 6.5 Lorenzo tests */
+#define HPEZ_PH_TUNE_BLOCKS 47   /* tuner: Sec. 6.6 block-wise tests */
+#define HPEZ_PROFILE_PHASES 48
 
 /* Enable (1) or disable (0) phase timing; resets the accumulators and the
  * launch counter.  Errors: INVALID_ARG. */

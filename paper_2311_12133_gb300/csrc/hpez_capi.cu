@@ -11,88 +11,14 @@
 
 #include "hpez_internal.cuh"
 #include "hpez_launch.h"
+#include "hpez_ctx.h"
 
 using namespace hpez;
 
-// Opt-in phase timer: CUDA events recorded on the call's stream around
-// each phase, read after the call's final synchronization.
-struct PhaseProfiler {
-  bool on = false;
-  std::vector<cudaEvent_t> pool;
-  size_t used = 0;
-  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
-  double total_ms[HPEZ_PROFILE_PHASES] = {};
-  uint64_t count[HPEZ_PROFILE_PHASES] = {};
-  cudaEvent_t take() {
-    if (used == pool.size()) {
-      cudaEvent_t e;
-      cudaEventCreate(&e);
-      pool.push_back(e);
-    }
-    return pool[used++];
-  }
-  void begin(int ph, cudaStream_t s) {
-    if (!on) return;
-    cudaEvent_t e = take();
-    cudaEventRecord(e, s);
-    marks.push_back({ph, {e, nullptr}});
-  }
-  void end(cudaStream_t s) {
-    if (!on || marks.empty()) return;
-    cudaEvent_t e = take();
-    cudaEventRecord(e, s);
-    marks.back().second.second = e;
-  }
-  // after the stream has been synchronized
-  void collect() {
-    for (auto& m : marks) {
-      float ms = 0.f;
-      if (m.second.second &&
-          cudaEventElapsedTime(&ms, m.second.first, m.second.second) == cudaSuccess) {
-        total_ms[m.first] += ms;
-        count[m.first] += 1;
-      }
-    }
-    marks.clear();
-    used = 0;
-    cudaGetLastError();
-  }
-  void reset() {
-    marks.clear();
-    used = 0;
-    for (int i = 0; i < HPEZ_PROFILE_PHASES; ++i) {
-      total_ms[i] = 0;
-      count[i] = 0;
-    }
-  }
-  ~PhaseProfiler() {
-    for (auto e : pool) cudaEventDestroy(e);
-  }
-};
 
-struct hpez_ctx {
-  PhaseProfiler prof;
-  uint64_t launches = 0;
-  int fused_levels = 1;        // HPEZ_OPT_FUSED_LEVELS
-  int level3d = 1;             // HPEZ_OPT_LEVEL3D
-  bool x_aligned16 = true;     // per call: input pointer 16-byte aligned
-  bool codes_aligned16 = true;
-  bool out_aligned16 = true;   // per call: decompress output 16-byte aligned
-  int tile_e[3] = {0, 0, 0};   // HPEZ_OPT_TILE_E0..2 (0 = heuristic)
-  size_t fused_smem_cap = 96 * 1024;
-  int device = 0;
-  int num_sms = 152;
-  char* scratch = nullptr;
-  size_t scratch_cap = 0;
-  Ctl* h_ctl = nullptr;        // pinned
-  uint8_t* h_hdr = nullptr;    // pinned, 512 bytes
-  void* io_in = nullptr;       // device staging for the *_host calls
-  size_t io_in_cap = 0;
-  void* io_out = nullptr;
-  size_t io_out_cap = 0;
-};
 
-namespace {
+namespace hpez {
+namespace host {
 
 // ---------------------------------------------------------------------
 // header layout (byte offsets)
@@ -141,19 +67,6 @@ bool pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 // ---------------------------------------------------------------------
 // geometry plan
 // ---------------------------------------------------------------------
-struct Plan {
-  int ndim = 0, off = 0;
-  uint32_t n[3] = {1, 1, 1};
-  uint32_t fst[3] = {0, 0, 1};
-  uint32_t N = 1;
-  bool interp[3] = {false, false, false};
-  int k = 0, A = 0, L = 0;
-  LevelGeom grid[kMaxLevels + 1];  // grid[g]: stride 2^g (g = L: anchors)
-  uint32_t gsize[kMaxLevels + 1];
-  uint32_t C = 4096, nch = 0;
-  uint32_t nb[3] = {1, 1, 1};
-  uint32_t nblocks = 0;
-};
 
 int plan_geometry(Plan& p, int ndim, const uint64_t* dims, int A,
                   int frozen) {
@@ -488,15 +401,6 @@ bool plan_level3d(const hpez_ctx* ctx, const Plan& p, const hpez_config& c,
 // ---------------------------------------------------------------------
 // scratch arena
 // ---------------------------------------------------------------------
-struct Arena {
-  size_t off = 0;
-  template <class T>
-  size_t take(size_t count) {
-    const size_t o = (off + 255) & ~(size_t)255;
-    off = o + count * sizeof(T);
-    return o;
-  }
-};
 
 int ensure_scratch(hpez_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->scratch_cap) return HPEZ_OK;
@@ -622,7 +526,10 @@ struct CompressBufs {
   uint8_t* bmap;
 };
 
-}  // namespace
+}  // namespace host
+}  // namespace hpez
+
+using namespace hpez::host;
 
 // =====================================================================
 // C-ABI
@@ -698,6 +605,11 @@ const char* hpez_profile_phase_name(int phase) {
   static char names[HPEZ_PROFILE_PHASES][24];
   if (phase < 0 || phase >= HPEZ_PROFILE_PHASES) return "";
   if (phase < HPEZ_PH_LEVEL) return fixed[phase];
+  if (phase >= HPEZ_PH_TUNE_STATS) {
+    static const char* tune[] = {"tune_stats", "tune_levels", "tune_eb",
+                                 "tune_lorenzo", "tune_blocks"};
+    return tune[phase - HPEZ_PH_TUNE_STATS];
+  }
   if (phase < HPEZ_PH_DLEVEL)
     std::snprintf(names[phase], 24, "level%d", phase - HPEZ_PH_LEVEL + 1);
   else

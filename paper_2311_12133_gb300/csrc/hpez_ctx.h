@@ -1,0 +1,133 @@
+// hpez_ctx.h -- host-side state shared by the C-ABI translation units:
+// the context, its phase profiler, the field geometry plan and the scratch
+// arena, and the plan/config helpers that compress, decompress and the
+// tuner all use.
+#pragma once
+
+#include <cstdint>
+#include <utility>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "hpez.h"
+#include "hpez_internal.cuh"
+
+// Opt-in phase timer: CUDA events recorded on the call's stream around
+// each phase, read after the call's final synchronization.
+struct PhaseProfiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+  double total_ms[HPEZ_PROFILE_PHASES] = {};
+  uint64_t count[HPEZ_PROFILE_PHASES] = {};
+  cudaEvent_t take() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  void begin(int ph, cudaStream_t s) {
+    if (!on) return;
+    cudaEvent_t e = take();
+    cudaEventRecord(e, s);
+    marks.push_back({ph, {e, nullptr}});
+  }
+  void end(cudaStream_t s) {
+    if (!on || marks.empty()) return;
+    cudaEvent_t e = take();
+    cudaEventRecord(e, s);
+    marks.back().second.second = e;
+  }
+  // after the stream has been synchronized
+  void collect() {
+    for (auto& m : marks) {
+      float ms = 0.f;
+      if (m.second.second &&
+          cudaEventElapsedTime(&ms, m.second.first, m.second.second) == cudaSuccess) {
+        total_ms[m.first] += ms;
+        count[m.first] += 1;
+      }
+    }
+    marks.clear();
+    used = 0;
+    cudaGetLastError();
+  }
+  void reset() {
+    marks.clear();
+    used = 0;
+    for (int i = 0; i < HPEZ_PROFILE_PHASES; ++i) {
+      total_ms[i] = 0;
+      count[i] = 0;
+    }
+  }
+  ~PhaseProfiler() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+struct hpez_ctx {
+  PhaseProfiler prof;
+  uint64_t launches = 0;
+  int fused_levels = 1;        // HPEZ_OPT_FUSED_LEVELS
+  int level3d = 1;             // HPEZ_OPT_LEVEL3D
+  bool x_aligned16 = true;     // per call: input pointer 16-byte aligned
+  bool codes_aligned16 = true;
+  bool out_aligned16 = true;   // per call: decompress output 16-byte aligned
+  int tile_e[3] = {0, 0, 0};   // HPEZ_OPT_TILE_E0..2 (0 = heuristic)
+  size_t fused_smem_cap = 96 * 1024;
+  int device = 0;
+  int num_sms = 152;
+  char* scratch = nullptr;
+  size_t scratch_cap = 0;
+  hpez::Ctl* h_ctl = nullptr;        // pinned
+  uint8_t* h_hdr = nullptr;    // pinned, 512 bytes
+  void* io_in = nullptr;       // device staging for the *_host calls
+  size_t io_in_cap = 0;
+  void* io_out = nullptr;
+  size_t io_out_cap = 0;
+};
+
+namespace hpez {
+namespace host {
+
+// geometry plan
+struct Plan {
+  int ndim = 0, off = 0;
+  uint32_t n[3] = {1, 1, 1};
+  uint32_t fst[3] = {0, 0, 1};
+  uint32_t N = 1;
+  bool interp[3] = {false, false, false};
+  int k = 0, A = 0, L = 0;
+  LevelGeom grid[kMaxLevels + 1];  // grid[g]: stride 2^g (g = L: anchors)
+  uint32_t gsize[kMaxLevels + 1];
+  uint32_t C = 4096, nch = 0;
+  uint32_t nb[3] = {1, 1, 1};
+  uint32_t nblocks = 0;
+};
+
+// scratch arena: 256-byte aligned sub-allocations of one device buffer
+struct Arena {
+  size_t off = 0;
+  template <class T>
+  size_t take(size_t count) {
+    const size_t o = (off + 255) & ~(size_t)255;
+    off = o + count * sizeof(T);
+    return o;
+  }
+};
+
+int plan_geometry(Plan& p, int ndim, const uint64_t* dims, int A, int frozen);
+int check_config(const Plan& p, const hpez_config& c);
+// Eq. 14 weight of slot `slot` within the slot mask S
+float md_weight(const Plan& p, const hpez_config& c, unsigned S, int slot);
+int ensure_scratch(hpez_ctx* ctx, size_t bytes);
+int map_status(int st);
+int cuda_check(cudaError_t e);
+void default_config(int ndim, hpez_config* c);
+
+}  // namespace host
+}  // namespace hpez

@@ -314,4 +314,31 @@ struct Level3D {
   int vec_out;       // rows of the output grids start 16-byte aligned
 };
 
+// ---------------------------------------------------------------------
+// Auto-tuner (Sec. 6): one theta of a compression test, and the geometry
+// of the sub-fields the tests run on.
+// ---------------------------------------------------------------------
+struct TuneCfg {
+  uint8_t kind[kMaxLevels];   // interpolator per level (l-1)
+  uint8_t md[kMaxLevels];     // 1: multi-dimensional paradigm
+  uint8_t same[kMaxLevels];   // same-level interpolation
+  uint8_t ord[kMaxLevels][3]; // 1D-style order as slots
+  double alpha, beta;         // Eq. 15 (the device fills el/inv2/twoe)
+  float el[kMaxLevels], inv2[kMaxLevels], twoe[kMaxLevels];
+  double inv_el[kMaxLevels];  // 1 / e_l for the error scores
+  float mdw[8][3];            // Eq. 14 weight per odd-slot mask and slot
+};
+
+struct TuneGeom {
+  uint32_t n[3];     // field extents per slot (padded slots 1)
+  uint32_t fst[3];   // field strides
+  int interp[3];     // interpolation slots
+  int k;             // number of interpolation slots
+  int off;           // padded slots (3 - ndim)
+  int A, L;          // anchor stride, levels
+  uint32_t ext[3];   // sample-block extents
+  uint32_t cnt[3];   // sample blocks per slot
+  uint32_t step[3];  // start offset between sample blocks per slot
+};
+
 }  // namespace hpez

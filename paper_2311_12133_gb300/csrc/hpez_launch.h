@@ -88,4 +88,26 @@ void launch_finalize(const uint8_t* hdr, const uint8_t* hdr_const,
                      const uint8_t* tlens, const Ctl* ctl, int num_sms,
                      cudaStream_t s);
 
+// k_tune.cu
+void launch_tune_stats(const float* x, const uint32_t n[3],
+                       const uint32_t fst[3], const int real[3], int t,
+                       const Ctl* ctl, unsigned long long* acc, int num_sms,
+                       cudaStream_t s);
+void launch_tune_params(TuneCfg* cfgs, int nvar, int L, const Ctl* ctl,
+                        cudaStream_t s);
+size_t tune_test_smem(const TuneGeom& g);
+void launch_tune_test(const float* x, const TuneGeom& g, const TuneCfg* cfgs,
+                      int nvar, int nblk, int l_stop, bool hist,
+                      unsigned long long* score, uint32_t* hists,
+                      unsigned long long* nout, cudaStream_t s);
+void launch_tune_lorenzo(const float* x, const TuneGeom& g, int nblk,
+                         const Ctl* ctl, uint32_t* hists,
+                         unsigned long long* nout, cudaStream_t s);
+void launch_tune_blockwise(const float* x, const TuneGeom& g, int bs, int Q,
+                           int frozen_slot, const uint32_t nb[3],
+                           uint32_t nblocks, const TuneCfg* base,
+                           unsigned allow, uint8_t* bmap, cudaStream_t s);
+void launch_tune_cost(const uint32_t* hist, const uint8_t* lens,
+                      unsigned long long* cost, cudaStream_t s);
+
 }  // namespace hpez

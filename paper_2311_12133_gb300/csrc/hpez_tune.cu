@@ -1,0 +1,579 @@
+// hpez_tune.cu -- hpez_tune (declared in include/hpez.h): the host side of
+// the auto-tuner of Sec. 6.  It lays out the samples, builds the candidate
+// thetas, launches the compression tests of k_tune.cu and takes the
+// argmins over the integer scores the kernels return.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "hpez.h"
+#include "hpez_ctx.h"
+#include "hpez_internal.cuh"
+#include "hpez_launch.h"
+
+using namespace hpez;
+using namespace hpez::host;
+
+namespace {
+
+constexpr size_t kTuneSmemMax = 200 * 1024;
+constexpr int kMaxVariants = 64;
+const double kAlpha[5] = {1.0, 1.25, 1.5, 1.75, 2.0};
+const double kBeta[4] = {2.0, 4.0, 8.0, 16.0};
+
+// One candidate of the per-level tuning (Sec. 6.2); ord lists real dims.
+struct Cand {
+  int kind, md, same;
+  uint8_t ord[3];
+};
+
+// Linear, not-a-knot, natural; for each the 1D-style orders of the
+// interpolation dims (lexicographic) and then the multi-dimensional
+// paradigm; for the cubic ones without and with same-level interpolation.
+std::vector<Cand> candidates(const hpez_tune_params& tp, int ndim,
+                             int frozen) {
+  std::vector<int> dims;
+  for (int d = 0; d < ndim; ++d)
+    if (d != frozen) dims.push_back(d);
+  const int k = (int)dims.size();
+  std::vector<std::vector<int>> perms;
+  std::vector<int> p = dims;
+  do perms.push_back(p);
+  while (std::next_permutation(p.begin(), p.end()));
+  const int nvar = (int)perms.size() + (k >= 2 ? 1 : 0);
+  std::vector<Cand> out;
+  for (int kd = 0; kd < 3; ++kd) {
+    if (kd == HPEZ_CUBIC_NAT && !tp.allow_natural) continue;
+    const int nsl = (kd == HPEZ_LINEAR || !tp.allow_same_level) ? 1 : 2;
+    for (int v = 0; v < nvar; ++v)
+      for (int sl = 0; sl < nsl; ++sl) {
+        Cand c;
+        c.kind = kd;
+        c.same = sl;
+        c.md = v >= (int)perms.size();
+        for (int q = 0; q < 3; ++q)
+          c.ord[q] = (uint8_t)(q < k ? (c.md ? dims[q] : perms[v][q]) : 255);
+        out.push_back(c);
+      }
+  }
+  return out;
+}
+
+void set_level(hpez_config& c, int l, const Cand& k) {
+  c.interp[l - 1] = (uint8_t)k.kind;
+  c.paradigm[l - 1] = (uint8_t)(k.md ? HPEZ_PARADIGM_MD : HPEZ_PARADIGM_1D);
+  c.same_level[l - 1] = (uint8_t)k.same;
+  for (int q = 0; q < 3; ++q) c.order[l - 1][q] = k.ord[q];
+}
+
+// Device form of a theta: orders as slots, Eq. 14 weights per odd-slot
+// mask; the level bounds are filled in on the device.
+TuneCfg to_device(const Plan& p, const hpez_config& c) {
+  TuneCfg t;
+  std::memset(&t, 0, sizeof(t));
+  for (int l = 0; l < kMaxLevels; ++l) {
+    t.kind[l] = c.interp[l];
+    t.md[l] = c.paradigm[l] == HPEZ_PARADIGM_MD;
+    t.same[l] = c.same_level[l];
+    for (int j = 0; j < 3; ++j)
+      t.ord[l][j] = (uint8_t)(j < p.k ? c.order[l][j] + p.off : 0);
+  }
+  t.alpha = c.alpha;
+  t.beta = c.beta;
+  unsigned imask = 0;
+  for (int s = 0; s < 3; ++s)
+    if (p.interp[s]) imask |= 1u << s;
+  for (unsigned S = 1; S < 8; ++S) {
+    if ((S & imask) != S) continue;
+    for (int s = 0; s < 3; ++s)
+      if (S & (1u << s)) t.mdw[S][s] = md_weight(p, c, S, s);
+  }
+  return t;
+}
+
+// device buffers of one hpez_tune call
+struct Bufs {
+  Ctl* ctl;
+  Ctl* ctl2;  // codebook status
+  unsigned long long* acc;
+  TuneCfg* cfgs;
+  unsigned long long* score;
+  unsigned long long* nout;
+  unsigned long long* cost;
+  uint32_t* hists;
+  uint8_t* lens;
+  unsigned long long* enc;
+  uint16_t* tsyms;
+  uint8_t* tlens;
+  unsigned long long* gkeys;
+  unsigned long long* giw;
+  uint32_t* gpar;
+  uint8_t* bmap;
+};
+
+struct Call {
+  hpez_ctx* ctx;
+  cudaStream_t s;
+  const float* x;
+  int ndim;
+  const uint64_t* dims;
+  const hpez_tune_params* tp;
+  Bufs b;
+};
+
+int sync_check(Call& k) {
+  const cudaError_t e = cudaStreamSynchronize(k.s);
+  if (e != cudaSuccess) return cuda_check(e);
+  return cuda_check(cudaGetLastError());
+}
+
+// Sample blocks of A+1 points every tau blocks per dim (Sec. 6.2), tau
+// the smallest stride giving at most round(block_rate * N / A^ndim) (>= 1)
+// blocks.  Returns the block count.
+int sample_geometry(const Plan& p, const hpez_tune_params& tp, TuneGeom& g) {
+  const int A = p.A;
+  uint64_t nb[3], N = 1, vol = 1;
+  for (int s = 0; s < 3; ++s) {
+    g.n[s] = p.n[s];
+    g.fst[s] = p.fst[s];
+    g.interp[s] = p.interp[s];
+    nb[s] = s < p.off ? 0 : (p.n[s] - 1) / (uint64_t)A;
+  }
+  for (int d = 0; d < p.ndim; ++d) {
+    N *= p.n[d + p.off];
+    vol *= (uint64_t)A;
+  }
+  g.k = p.k;
+  g.off = p.off;
+  g.A = A;
+  g.L = p.L;
+  const double tgt = std::floor(tp.block_rate * (double)N / (double)vol + 0.5);
+  const uint64_t target = tgt < 1.0 ? 1 : (uint64_t)tgt;
+  uint64_t tau = 1;
+  for (;;) {
+    uint64_t cnt = 1;
+    for (int s = p.off; s < 3; ++s) {
+      const uint64_t m = nb[s] ? nb[s] : 1;
+      cnt *= (m + tau - 1) / tau;
+    }
+    if (cnt <= target) break;
+    ++tau;
+  }
+  int total = 1;
+  for (int s = 0; s < 3; ++s) {
+    if (s < p.off) {
+      g.ext[s] = 1;
+      g.cnt[s] = 1;
+      g.step[s] = 0;
+    } else if (nb[s]) {
+      g.ext[s] = (uint32_t)A + 1;
+      g.cnt[s] = (uint32_t)((nb[s] + tau - 1) / tau);
+      g.step[s] = (uint32_t)(tau * (uint64_t)A);
+    } else {
+      g.ext[s] = p.n[s];
+      g.cnt[s] = 1;
+      g.step[s] = 0;
+    }
+    total *= (int)g.cnt[s];
+  }
+  return total;
+}
+
+// anchors of one sample block (every interpolation coordinate a multiple
+// of A)
+uint64_t block_anchors(const TuneGeom& g) {
+  uint64_t na = 1;
+  for (int s = 0; s < 3; ++s)
+    na *= g.interp[s] ? (g.ext[s] + (uint64_t)g.A - 1) / (uint64_t)g.A : g.ext[s];
+  return na;
+}
+
+// Huffman bits of histograms [0, nvar) into b.cost[0, nvar)
+void hist_costs(Call& k, int nvar) {
+  uint64_t& nl = k.ctx->launches;
+  launch_init_ctl(k.b.ctl2, k.s);
+  ++nl;
+  for (int v = 0; v < nvar; ++v) {
+    const uint32_t* h = k.b.hists + (size_t)v * 65536;
+    cudaMemsetAsync(k.b.lens, 0, 65536, k.s);
+    launch_codebook(h, k.b.enc, k.b.tsyms, k.b.tlens, k.b.gkeys, k.b.giw,
+                    k.b.gpar, k.b.lens, k.b.ctl2, k.s);
+    launch_tune_cost(h, k.b.lens, k.b.cost + v, k.s);
+    nl += 2;
+  }
+}
+
+// Sec. 6.2 + 6.4 for one choice of frozen dim; returns the sample bits
+// estimate in *bits.
+int tune_global(Call& k, int frozen, const double inv_var[3],
+                hpez_config& cfg, hpez_tune_report* rep, int slot,
+                uint64_t* bits) {
+  const hpez_tune_params& tp = *k.tp;
+  default_config(k.ndim, &cfg);
+  if (tp.anchor_stride) cfg.anchor_stride = tp.anchor_stride;
+  cfg.frozen_dim = frozen;
+  for (int d = 0; d < 3; ++d) cfg.md_inv_var[d] = inv_var[d];
+  for (int l = 0; l < HPEZ_MAX_LEVELS; ++l) {
+    int q = 0;
+    for (int d = 0; d < k.ndim; ++d)
+      if (d != frozen) cfg.order[l][q++] = (uint8_t)d;
+    for (; q < 3; ++q) cfg.order[l][q] = 255;
+  }
+  Plan p;
+  int rc = plan_geometry(p, k.ndim, k.dims, cfg.anchor_stride, frozen);
+  if (rc) return rc;
+  TuneGeom g;
+  const int nblk = sample_geometry(p, tp, g);
+  if (tune_test_smem(g) > kTuneSmemMax) return HPEZ_ERR_UNSUPPORTED;
+  if (rep && slot == 0) rep->n_sample_blocks = (uint32_t)nblk;
+  uint64_t& nl = k.ctx->launches;
+  PhaseProfiler& prof = k.ctx->prof;
+  std::vector<TuneCfg> host(kMaxVariants);
+  std::vector<unsigned long long> sc(kMaxVariants);
+
+  if (tp.tune_levels) {
+    const std::vector<Cand> cands = candidates(tp, k.ndim, frozen);
+    const int nvar = (int)cands.size();
+    if (nvar > kMaxVariants) return HPEZ_ERR_UNSUPPORTED;
+    for (int l = p.L; l >= 1; --l) {
+      for (int j = 0; j < nvar; ++j) {
+        hpez_config c2 = cfg;
+        set_level(c2, l, cands[j]);
+        host[j] = to_device(p, c2);
+      }
+      prof.begin(HPEZ_PH_TUNE_LEVELS, k.s);
+      cudaMemcpyAsync(k.b.cfgs, host.data(), sizeof(TuneCfg) * nvar,
+                      cudaMemcpyHostToDevice, k.s);
+      launch_tune_params(k.b.cfgs, nvar, kMaxLevels, k.b.ctl, k.s);
+      cudaMemsetAsync(k.b.score, 0, sizeof(unsigned long long) * nvar, k.s);
+      launch_tune_test(k.x, g, k.b.cfgs, nvar, nblk, l, false, k.b.score,
+                       nullptr, k.b.nout, k.s);
+      nl += 2;
+      prof.end(k.s);
+      cudaMemcpyAsync(sc.data(), k.b.score, sizeof(unsigned long long) * nvar,
+                      cudaMemcpyDeviceToHost, k.s);
+      if ((rc = sync_check(k))) return rc;
+      int best = 0;
+      for (int j = 1; j < nvar; ++j)
+        if (sc[j] < sc[best]) best = j;
+      set_level(cfg, l, cands[best]);
+      if (rep) {
+        rep->level_choice[slot][l - 1] = (uint8_t)best;
+        rep->level_score[slot][l - 1] = sc[best];
+      }
+    }
+  }
+
+  // (alpha, beta): the grid, or the defaults alone
+  std::vector<std::pair<double, double>> grid;
+  if (tp.tune_eb) {
+    grid.push_back({1.0, 1.0});
+    for (int a = 1; a < 5; ++a)
+      for (int b = 0; b < 4; ++b) grid.push_back({kAlpha[a], kBeta[b]});
+  } else {
+    grid.push_back({cfg.alpha, cfg.beta});
+  }
+  const int nvar = (int)grid.size();
+  for (int v = 0; v < nvar; ++v) {
+    hpez_config c2 = cfg;
+    c2.alpha = grid[v].first;
+    c2.beta = grid[v].second;
+    host[v] = to_device(p, c2);
+  }
+  prof.begin(HPEZ_PH_TUNE_EB, k.s);
+  cudaMemcpyAsync(k.b.cfgs, host.data(), sizeof(TuneCfg) * nvar,
+                  cudaMemcpyHostToDevice, k.s);
+  launch_tune_params(k.b.cfgs, nvar, kMaxLevels, k.b.ctl, k.s);
+  cudaMemsetAsync(k.b.hists, 0, sizeof(uint32_t) * 65536 * nvar, k.s);
+  cudaMemsetAsync(k.b.nout, 0, sizeof(unsigned long long) * nvar, k.s);
+  cudaMemsetAsync(k.b.score, 0, sizeof(unsigned long long) * nvar, k.s);
+  launch_tune_test(k.x, g, k.b.cfgs, nvar, nblk, 1, true, k.b.score,
+                   k.b.hists, k.b.nout, k.s);
+  nl += 2;
+  hist_costs(k, nvar);
+  prof.end(k.s);
+  std::vector<unsigned long long> cost(nvar), nout(nvar);
+  Ctl st;
+  cudaMemcpyAsync(cost.data(), k.b.cost, sizeof(unsigned long long) * nvar,
+                  cudaMemcpyDeviceToHost, k.s);
+  cudaMemcpyAsync(nout.data(), k.b.nout, sizeof(unsigned long long) * nvar,
+                  cudaMemcpyDeviceToHost, k.s);
+  cudaMemcpyAsync(&st, k.b.ctl2, sizeof(Ctl), cudaMemcpyDeviceToHost, k.s);
+  if ((rc = sync_check(k))) return rc;
+  if (st.status) return HPEZ_ERR_UNSUPPORTED;
+  const uint64_t na = block_anchors(g) * (uint64_t)nblk;
+  int best = 0;
+  uint64_t best_bits = 0;
+  for (int v = 0; v < nvar; ++v) {
+    const uint64_t b = cost[v] + 32ull * nout[v] + 32ull * na;
+    if (v == 0 || b < best_bits) {
+      best_bits = b;
+      best = v;
+    }
+  }
+  cfg.alpha = grid[best].first;
+  cfg.beta = grid[best].second;
+  *bits = best_bits;
+  if (rep) rep->bits[slot] = best_bits;
+  return HPEZ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hpez_default_tune_params(hpez_tune_params* t) {
+  if (!t) return HPEZ_ERR_INVALID_ARG;
+  std::memset(t, 0, sizeof(*t));
+  t->sample_rate = 0.002;
+  t->block_rate = 0.01;
+  t->sub_frac = 0.04;
+  t->lorenzo_coef = 1.0;
+  t->block_size = 32;
+  t->tune_levels = 1;
+  t->tune_eb = 1;
+  t->tune_freeze = 1;
+  t->tune_lorenzo = 1;
+  t->tune_blockwise = 1;
+  t->allow_natural = 1;
+  t->allow_same_level = 1;
+  t->anchor_stride = 0;
+  return HPEZ_OK;
+}
+
+uint64_t hpez_blockmap_size(int ndim, const uint64_t* dims, int bs) {
+  if (!dims || bs < 1 || ndim < 1 || ndim > 3) return 0;
+  uint64_t t = 1;
+  for (int d = 0; d < ndim; ++d) t *= (dims[d] + (uint64_t)bs - 1) / (uint64_t)bs;
+  return t;
+}
+
+int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
+              int eb_mode, double eb, const hpez_tune_params* tp_in,
+              hpez_config* h_cfg, uint8_t* h_blockmap, uint64_t blockmap_cap,
+              hpez_tune_report* rep, void* stream) {
+  if (!ctx || !d_in || !dims || !h_cfg || ndim < 1 || ndim > 3)
+    return HPEZ_ERR_INVALID_ARG;
+  hpez_tune_params tpd;
+  if (!tp_in) {
+    hpez_default_tune_params(&tpd);
+    tp_in = &tpd;
+  }
+  const hpez_tune_params& tp = *tp_in;
+  if (eb_mode != HPEZ_EB_ABS && eb_mode != HPEZ_EB_REL) return HPEZ_ERR_INVALID_ARG;
+  if (!(eb > 0.0) || !std::isfinite(eb)) return HPEZ_ERR_INVALID_ARG;
+  if (tp.block_size < 1 || !(tp.sample_rate > 0.0) || !(tp.block_rate > 0.0) ||
+      !(tp.sub_frac > 0.0) || tp.sub_frac > 1.0)
+    return HPEZ_ERR_INVALID_ARG;
+  const uint64_t nbm = hpez_blockmap_size(ndim, dims, tp.block_size);
+  if (tp.tune_blockwise && (!h_blockmap || blockmap_cap < nbm))
+    return HPEZ_ERR_OUT_TOO_SMALL;
+  if (rep) std::memset(rep, 0, sizeof(*rep));
+  default_config(ndim, h_cfg);
+  if (tp.anchor_stride) h_cfg->anchor_stride = tp.anchor_stride;
+  Plan p0;
+  int rc = plan_geometry(p0, ndim, dims, h_cfg->anchor_stride, -1);
+  if (rc) return rc;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  Arena ar;
+  const size_t o_ctl = ar.take<Ctl>(1);
+  const size_t o_ctl2 = ar.take<Ctl>(1);
+  const size_t o_acc = ar.take<unsigned long long>(8);
+  const size_t o_cfgs = ar.take<TuneCfg>(kMaxVariants);
+  const size_t o_score = ar.take<unsigned long long>(kMaxVariants);
+  const size_t o_nout = ar.take<unsigned long long>(kMaxVariants);
+  const size_t o_cost = ar.take<unsigned long long>(kMaxVariants);
+  const size_t o_hists = ar.take<uint32_t>((size_t)65536 * 17);
+  const size_t o_lens = ar.take<uint8_t>(65536);
+  const size_t o_enc = ar.take<unsigned long long>(65536);
+  const size_t o_tsyms = ar.take<uint16_t>(65536);
+  const size_t o_tlens = ar.take<uint8_t>(65536);
+  const size_t o_gkeys = ar.take<unsigned long long>(65536);
+  const size_t o_giw = ar.take<unsigned long long>(65536);
+  const size_t o_gpar = ar.take<uint32_t>(131072);
+  const size_t o_bmap = ar.take<uint8_t>(nbm ? nbm : 1);
+  if ((rc = ensure_scratch(ctx, ar.off))) return rc;
+  char* base = ctx->scratch;
+  Call k;
+  k.ctx = ctx;
+  k.s = s;
+  k.x = d_in;
+  k.ndim = ndim;
+  k.dims = dims;
+  k.tp = &tp;
+  k.b.ctl = reinterpret_cast<Ctl*>(base + o_ctl);
+  k.b.ctl2 = reinterpret_cast<Ctl*>(base + o_ctl2);
+  k.b.acc = reinterpret_cast<unsigned long long*>(base + o_acc);
+  k.b.cfgs = reinterpret_cast<TuneCfg*>(base + o_cfgs);
+  k.b.score = reinterpret_cast<unsigned long long*>(base + o_score);
+  k.b.nout = reinterpret_cast<unsigned long long*>(base + o_nout);
+  k.b.cost = reinterpret_cast<unsigned long long*>(base + o_cost);
+  k.b.hists = reinterpret_cast<uint32_t*>(base + o_hists);
+  k.b.lens = reinterpret_cast<uint8_t*>(base + o_lens);
+  k.b.enc = reinterpret_cast<unsigned long long*>(base + o_enc);
+  k.b.tsyms = reinterpret_cast<uint16_t*>(base + o_tsyms);
+  k.b.tlens = reinterpret_cast<uint8_t*>(base + o_tlens);
+  k.b.gkeys = reinterpret_cast<unsigned long long*>(base + o_gkeys);
+  k.b.giw = reinterpret_cast<unsigned long long*>(base + o_giw);
+  k.b.gpar = reinterpret_cast<uint32_t*>(base + o_gpar);
+  k.b.bmap = reinterpret_cast<uint8_t*>(base + o_bmap);
+  uint64_t& nl = ctx->launches;
+  PhaseProfiler& prof = ctx->prof;
+
+  // the absolute bound, exactly as the compressor derives it
+  launch_init_ctl(k.b.ctl, s);
+  ++nl;
+  if (eb_mode == HPEZ_EB_REL) {
+    prof.begin(HPEZ_PH_RANGE, s);
+    launch_range(d_in, p0.N, k.b.ctl, ctx->num_sms, s);
+    prof.end(s);
+    ++nl;
+  }
+  launch_params(k.b.ctl, eb_mode, eb, 1.0, 1.0, p0.L, d_in, s);
+  ++nl;
+  cudaMemcpyAsync(ctx->h_ctl, k.b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+  if ((rc = sync_check(k))) return rc;
+  if (ctx->h_ctl->status) return map_status(ctx->h_ctl->status);
+  if (ctx->h_ctl->is_const) {
+    prof.collect();
+    return HPEZ_OK;  // constant field: nothing to tune
+  }
+
+  // Sec. 6.1 statistics on the lattice
+  int t = 1;
+  for (;;) {
+    double pp = 1.0;
+    for (int d = 0; d < ndim; ++d) pp *= (double)t;
+    if (pp * tp.sample_rate >= 1.0) break;
+    ++t;
+  }
+  bool ok = true;
+  int real[3];
+  for (int sl = 0; sl < 3; ++sl) {
+    real[sl] = sl >= p0.off;
+    if (real[sl] && p0.n[sl] < 7) ok = false;
+  }
+  unsigned long long acc[8] = {0};
+  if (ok) {
+    prof.begin(HPEZ_PH_TUNE_STATS, s);
+    cudaMemsetAsync(k.b.acc, 0, sizeof(unsigned long long) * 8, s);
+    launch_tune_stats(d_in, p0.n, p0.fst, real, t, k.b.ctl, k.b.acc,
+                      ctx->num_sms, s);
+    ++nl;
+    prof.end(s);
+    cudaMemcpyAsync(acc, k.b.acc, sizeof(acc), cudaMemcpyDeviceToHost, s);
+    if ((rc = sync_check(k))) return rc;
+  }
+  const uint64_t cnt = acc[0];
+  double inv_var[3] = {1.0, 1.0, 1.0};
+  int nonsmooth = -1;
+  if (cnt) {
+    uint64_t mx = 0;
+    for (int d = 0; d < ndim; ++d) {
+      const uint64_t cub = acc[4 + d + p0.off];
+      inv_var[d] = (double)cnt * 256.0 / (double)(cub ? cub : 1);
+      if (nonsmooth < 0 || cub > mx) {
+        mx = cub;
+        nonsmooth = d;
+      }
+    }
+  }
+  if (rep) {
+    rep->stats_count = cnt;
+    for (int d = 0; d < 3; ++d) {
+      rep->mse_lin[d] = d < ndim ? acc[1 + d + p0.off] : 0;
+      rep->mse_cub[d] = d < ndim ? acc[4 + d + p0.off] : 0;
+    }
+    rep->nonsmooth_dim = nonsmooth;
+    rep->froze = 0;
+  }
+
+  // Sec. 6.2 + 6.4 without freezing, and (Sec. 6.3) with the most
+  // non-smooth dim frozen; the smaller estimate wins
+  hpez_config cfg_nf, cfg_f;
+  uint64_t bits_nf = 0, bits_f = 0;
+  if ((rc = tune_global(k, -1, inv_var, cfg_nf, rep, 0, &bits_nf))) return rc;
+  hpez_config out = cfg_nf;
+  uint64_t bits_best = bits_nf;
+  if (tp.tune_freeze && cnt && ndim >= 2) {
+    if ((rc = tune_global(k, nonsmooth, inv_var, cfg_f, rep, 1, &bits_f)))
+      return rc;
+    if (bits_f < bits_nf) {
+      out = cfg_f;
+      bits_best = bits_f;
+      if (rep) rep->froze = 1;
+    }
+  }
+
+  // Sec. 6.5: order-1 and order-2 Lorenzo on the same sample blocks
+  if (tp.tune_lorenzo) {
+    Plan p;
+    if ((rc = plan_geometry(p, ndim, dims, out.anchor_stride, -1))) return rc;
+    TuneGeom g;
+    const int nblk = sample_geometry(p, tp, g);
+    prof.begin(HPEZ_PH_TUNE_LORENZO, s);
+    cudaMemsetAsync(k.b.hists, 0, sizeof(uint32_t) * 65536 * 2, s);
+    cudaMemsetAsync(k.b.nout, 0, sizeof(unsigned long long) * 2, s);
+    launch_tune_lorenzo(d_in, g, nblk, k.b.ctl, k.b.hists, k.b.nout, s);
+    ++nl;
+    hist_costs(k, 2);
+    prof.end(s);
+    unsigned long long cost[2], nout[2];
+    Ctl st;
+    cudaMemcpyAsync(cost, k.b.cost, sizeof(cost), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(nout, k.b.nout, sizeof(nout), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&st, k.b.ctl2, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+    if ((rc = sync_check(k))) return rc;
+    if (st.status) return HPEZ_ERR_UNSUPPORTED;
+    const uint64_t lb0 = cost[0] + 32ull * nout[0];
+    const uint64_t lb1 = cost[1] + 32ull * nout[1];
+    if (rep) {
+      rep->lorenzo_bits[0] = lb0;
+      rep->lorenzo_bits[1] = lb1;
+      const uint64_t m = lb0 < lb1 ? lb0 : lb1;
+      rep->lorenzo_better = (double)m * tp.lorenzo_coef < (double)bits_best;
+    }
+  }
+
+  // Sec. 6.6: block-wise interpolator map
+  if (tp.tune_blockwise) {
+    Plan p;
+    if ((rc = plan_geometry(p, ndim, dims, out.anchor_stride, out.frozen_dim)))
+      return rc;
+    const int bsz = tp.block_size;
+    const double q0 = 32.0 * std::pow(tp.sub_frac, 1.0 / (double)ndim);
+    int Q = (int)std::floor((double)bsz / 32.0 * q0 + 0.5);
+    if (Q < 5) Q = 5;
+    size_t vol = 1;
+    for (int d = 0; d < ndim; ++d) vol *= (size_t)std::min(Q, bsz);
+    if (vol * sizeof(float) > kTuneSmemMax) return HPEZ_ERR_UNSUPPORTED;
+    TuneGeom g;
+    sample_geometry(p, tp, g);
+    uint32_t nb[3];
+    for (int sl = 0; sl < 3; ++sl)
+      nb[sl] = sl < p.off ? 1u : (p.n[sl] + (uint32_t)bsz - 1) / (uint32_t)bsz;
+    TuneCfg host = to_device(p, out);
+    prof.begin(HPEZ_PH_TUNE_BLOCKS, s);
+    cudaMemcpyAsync(k.b.cfgs, &host, sizeof(TuneCfg), cudaMemcpyHostToDevice, s);
+    launch_tune_params(k.b.cfgs, 1, kMaxLevels, k.b.ctl, s);
+    const unsigned allow = (tp.allow_natural ? 1u : 0u) | (tp.allow_same_level ? 2u : 0u);
+    launch_tune_blockwise(d_in, g, bsz, Q,
+                          out.frozen_dim < 0 ? -1 : out.frozen_dim + p.off, nb,
+                          (uint32_t)nbm, k.b.cfgs, allow, k.b.bmap, s);
+    nl += 2;
+    prof.end(s);
+    cudaMemcpyAsync(h_blockmap, k.b.bmap, nbm, cudaMemcpyDeviceToHost, s);
+    if ((rc = sync_check(k))) return rc;
+    out.blockwise = 1;
+    out.block_size = bsz;
+    out.h_blockmap = h_blockmap;
+  }
+  prof.collect();
+  *h_cfg = out;
+  return HPEZ_OK;
+}
+
+}  // extern "C"

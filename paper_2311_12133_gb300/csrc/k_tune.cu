@@ -1,0 +1,595 @@
+// k_tune.cu -- the auto-tuner's data-parallel work (Sec. 6): the sampling
+// statistics (Sec. 6.1), compression tests of candidate thetas on sample
+// blocks (Sec. 6.2 / 6.4), the Lorenzo test (Sec. 6.5), the block-wise
+// tests (Sec. 6.6), and the Huffman bit count of a code histogram.
+//
+// A test runs one sub-field in one CTA: its reconstruction lives in shared
+// memory, its input is read from the field in place.  Every score is an
+// integer (fixed-point errors, code counts), so the sums do not depend on
+// the order in which threads add them; the floating-point steps follow the
+// compressor's operation order with explicit round-to-nearest intrinsics.
+#include <cfloat>
+
+#include "hpez_internal.cuh"
+#include "hpez_launch.h"
+
+namespace hpez {
+namespace {
+
+constexpr int kTuneThreads = 512;
+constexpr int kBlockThreads = 128;
+constexpr size_t kTuneSmemMax = 200 * 1024;
+
+// floor(min(|d| / e_l, 2^24) * 256): the per-point error score
+__device__ __forceinline__ unsigned long long err_fixed(float d,
+                                                        double inv_el) {
+  double v = __dmul_rn(fabs((double)d), inv_el);
+  v = fmin(v, 16777216.0);
+  return (unsigned long long)floor(__dmul_rn(v, 256.0));
+}
+
+// floor(min(|d| / e, 2^16)^2 * 256): the statistics' squared error
+__device__ __forceinline__ unsigned long long sq_fixed(float d,
+                                                       double inv_e) {
+  double v = __dmul_rn(fabs((double)d), inv_e);
+  v = fmin(v, 65536.0);
+  return (unsigned long long)floor(__dmul_rn(__dmul_rn(v, v), 256.0));
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// CTA-wide sum, valid in thread 0.  `red` holds 32 entries.
+__device__ unsigned long long block_sum(unsigned long long v,
+                                        unsigned long long* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  unsigned long long t = 0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0ull;
+    t = warp_sum(t);
+  }
+  return t;
+}
+
+// ---------------------------------------------------------------------
+// Sec. 6.1 statistics: lattice points with +-3 neighbours on every dim
+// ---------------------------------------------------------------------
+struct StatsGeom {
+  uint32_t fst[3];
+  uint32_t lo[3], step[3], cnt[3];
+  int real[3];
+};
+
+__global__ void __launch_bounds__(256)
+    k_tune_stats(const float* __restrict__ x, StatsGeom g,
+                 unsigned long long total, const Ctl* __restrict__ ctl,
+                 unsigned long long* acc) {
+  __shared__ unsigned long long red[32];
+  const double inv_e = __ddiv_rn(1.0, (double)ctl->e);
+  unsigned long long cnt = 0, lin[3] = {0, 0, 0}, cub[3] = {0, 0, 0};
+  const unsigned long long nthr = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x +
+                              threadIdx.x;
+       q < total; q += nthr) {
+    const uint32_t u2 = (uint32_t)(q % g.cnt[2]);
+    const unsigned long long r = q / g.cnt[2];
+    const uint32_t u1 = (uint32_t)(r % g.cnt[1]);
+    const uint32_t u0 = (uint32_t)(r / g.cnt[1]);
+    const size_t i = (size_t)(g.lo[0] + g.step[0] * u0) * g.fst[0] +
+                     (size_t)(g.lo[1] + g.step[1] * u1) * g.fst[1] +
+                     (size_t)(g.lo[2] + g.step[2] * u2);
+    ++cnt;
+    const float xv = x[i];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      if (!g.real[s]) continue;
+      const size_t st = g.fst[s];
+      const float m3 = x[i - 3 * st], m1 = x[i - st], p1 = x[i + st],
+                  p3 = x[i + 3 * st];
+      const float pc = eval_formula(F_NAK4, m3, 0.f, m1, p1, 0.f, p3);
+      const float pl = eval_formula(F_LIN, 0.f, 0.f, m1, p1, 0.f, 0.f);
+      cub[s] += sq_fixed(__fsub_rn(xv, pc), inv_e);
+      lin[s] += sq_fixed(__fsub_rn(xv, pl), inv_e);
+    }
+  }
+  unsigned long long v[7] = {cnt, lin[0], lin[1], lin[2], cub[0], cub[1], cub[2]};
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    const unsigned long long t = block_sum(v[j], red);
+    if (threadIdx.x == 0 && t) atomicAdd(acc + j, t);
+  }
+}
+
+// ---------------------------------------------------------------------
+// level error bounds of every variant (Eq. 15), as the compressor does
+// ---------------------------------------------------------------------
+__global__ void k_tune_params(TuneCfg* cfgs, int nvar, int L,
+                              const Ctl* __restrict__ ctl) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nvar) return;
+  TuneCfg& c = cfgs[v];
+  const float e = ctl->e;
+  for (int l = 1; l <= L; ++l) {
+    double ap = 1.0;
+    for (int i = 1; i < l; ++i) ap = __dmul_rn(ap, c.alpha);
+    const double m = ap < c.beta ? ap : c.beta;
+    const float el = __double2float_rn(__ddiv_rn((double)e, m));
+    c.el[l - 1] = el;
+    c.twoe[l - 1] = __fmul_rn(2.0f, el);
+    c.inv2[l - 1] = __double2float_rn(__ddiv_rn(1.0, __dmul_rn(2.0, (double)el)));
+    c.inv_el[l - 1] = __ddiv_rn(1.0, (double)el);
+  }
+}
+
+// ---------------------------------------------------------------------
+// one sub-field in shared memory
+// ---------------------------------------------------------------------
+struct Sub {
+  int n[3];          // extents per slot
+  int st[3];         // shared-memory strides
+  const float* x;    // input at the sub-field origin
+  size_t xst[3];     // input strides
+};
+
+__device__ __forceinline__ void set_strides(Sub& f) {
+  f.st[2] = 1;
+  f.st[1] = f.n[2];
+  f.st[0] = f.n[1] * f.n[2];
+}
+
+// sample block b of the lattice of blocks
+__device__ Sub sample_block(const float* x, const TuneGeom& g, unsigned b) {
+  Sub f;
+  size_t off = 0;
+  for (int d = 2; d >= 0; --d) {
+    const unsigned j = b % g.cnt[d];
+    b /= g.cnt[d];
+    off += (size_t)j * g.step[d] * g.fst[d];
+    f.n[d] = (int)g.ext[d];
+    f.xst[d] = g.fst[d];
+  }
+  f.x = x + off;
+  set_strides(f);
+  return f;
+}
+
+__device__ __forceinline__ float xval(const Sub& f, const int c[3]) {
+  return f.x[(size_t)c[0] * f.xst[0] + (size_t)c[1] * f.xst[1] +
+             (size_t)c[2] * f.xst[2]];
+}
+
+// anchors (every interpolation coordinate a multiple of A) from the input;
+// the other entries are set by the sweep before they are read
+__device__ void init_anchors(float* R, const Sub& f, const int interp[3],
+                             int A) {
+  const int tot = f.n[0] * f.n[1] * f.n[2];
+  for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+    int c[3];
+    c[2] = q % f.n[2];
+    const int r = q / f.n[2];
+    c[1] = r % f.n[1];
+    c[0] = r / f.n[1];
+    bool anc = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (interp[d] && (c[d] % A) != 0) anc = false;
+    R[q] = anc ? xval(f, c) : 0.0f;
+  }
+  __syncthreads();
+}
+
+// prediction along one slot from shared memory (same stencil choice and
+// operation order as the compressor)
+__device__ __forceinline__ float predict_smem(const float* R, int i, int st,
+                                              int u, int m, int kind,
+                                              bool half_b) {
+  const int f = choose_formula(kind, half_b, u, m);
+  float m3 = 0.f, m2 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+  const float m1 = R[i - st];
+  switch (f) {
+    case F_COPY:
+      break;
+    case F_EXTRAP:
+      m3 = R[i - 3 * st];
+      break;
+    case F_LIN:
+      p1 = R[i + st];
+      break;
+    case F_NAK4:
+    case F_NAT4:
+      m3 = R[i - 3 * st];
+      p1 = R[i + st];
+      p3 = R[i + 3 * st];
+      break;
+    case F_NAK3L:
+    case F_NAT3L:
+      m3 = R[i - 3 * st];
+      p1 = R[i + st];
+      break;
+    case F_NAK3R:
+    case F_NAT3R:
+      p1 = R[i + st];
+      p3 = R[i + 3 * st];
+      break;
+    case F_SL_NAK:
+      m2 = R[i - 2 * st];
+      p1 = R[i + st];
+      p2 = R[i + 2 * st];
+      break;
+    case F_SL_NAT:
+      m3 = R[i - 3 * st];
+      m2 = R[i - 2 * st];
+      p1 = R[i + st];
+      p2 = R[i + 2 * st];
+      p3 = R[i + 3 * st];
+      break;
+  }
+  return eval_formula(f, m3, m2, m1, p1, p2, p3);
+}
+
+// One level (stride s = 2^(l-1)) of the sweep on the sub-field: passes
+// and same-level halves in the compressor's order, a barrier after each.
+// Adds the error scores (when score_on), the code counts (kHist) and the
+// escapes of the level's points to the thread's accumulators.
+template <bool kHist>
+__device__ void sweep_level(float* R, const Sub& f, const int interp[3],
+                            int k, int l, const TuneCfg& c, bool score_on,
+                            unsigned long long& score, uint32_t* hist,
+                            unsigned long long& nout) {
+  const int sh = l - 1, s = 1 << sh;
+  int step[3], m[3], line[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    step[d] = interp[d] ? s : 1;
+    m[d] = (f.n[d] + step[d] - 1) / step[d];
+    line[d] = (f.n[d] - 1) / s + 1;
+  }
+  const int M = m[0] * m[1] * m[2];
+  const int kind = c.kind[l - 1];
+  const bool md = c.md[l - 1] != 0;
+  const bool same = c.same[l - 1] != 0 && kind != LINEAR;
+  const float el = c.el[l - 1], inv2 = c.inv2[l - 1], twoe = c.twoe[l - 1];
+  const double inv_el = c.inv_el[l - 1];
+  for (int pj = 0; pj < k; ++pj) {
+    const int ps = md ? -1 : c.ord[l - 1][pj];
+    unsigned later = 0;  // 1D-style: slots later in the order stay even
+    if (!md)
+      for (int q = pj + 1; q < k; ++q) later |= 1u << c.ord[l - 1][q];
+    for (int half = 0; half < (same ? 2 : 1); ++half) {
+      for (int q = threadIdx.x; q < M; q += blockDim.x) {
+        int cc[3];
+        cc[2] = (q % m[2]) * step[2];
+        const int r = q / m[2];
+        cc[1] = (r % m[1]) * step[1];
+        cc[0] = (r / m[1]) * step[0];
+        unsigned odd = 0;
+        int nodd = 0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+          if (interp[d] && ((cc[d] >> sh) & 1)) {
+            odd |= 1u << d;
+            ++nodd;
+          }
+        if (nodd == 0) continue;
+        unsigned S;
+        if (!md) {
+          if (!(odd & (1u << ps)) || (odd & later)) continue;
+          S = 1u << ps;
+        } else {
+          if (nodd != pj + 1) continue;
+          S = odd;
+        }
+        unsigned par = 0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+          if (S & (1u << d)) par += (unsigned)(((cc[d] >> sh) - 1) >> 1);
+        const bool in_b = same && (par & 1u);
+        if ((int)in_b != half) continue;
+        const int i = cc[0] * f.st[0] + cc[1] * f.st[1] + cc[2];
+        float p;
+        if (!md) {
+          p = predict_smem(R, i, s * f.st[ps], cc[ps] >> sh, line[ps], kind,
+                           in_b);
+        } else {
+          float acc = 0.0f;
+          bool first = true;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            if (!(S & (1u << d))) continue;
+            const float pd = predict_smem(R, i, s * f.st[d], cc[d] >> sh,
+                                          line[d], kind, in_b);
+            const float t = __fmul_rn(c.mdw[S][d], pd);
+            acc = first ? t : __fadd_rn(acc, t);
+            first = false;
+          }
+          p = acc;
+        }
+        const float xv = xval(f, cc);
+        float rv;
+        const unsigned code = quantize(xv, p, el, inv2, twoe, rv);
+        R[i] = rv;
+        if (score_on) score += err_fixed(__fsub_rn(xv, p), inv_el);
+        if (kHist) atomicAdd(hist + code, 1u);
+        if (code == 0u) ++nout;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ __forceinline__ void load_cfg(TuneCfg* dst, const TuneCfg* src) {
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(TuneCfg) / 4); i += blockDim.x)
+    d[i] = s[i];
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------
+// Sec. 6.2 / 6.4: CTA (sample block, variant): anchors, levels L..l_stop
+// ---------------------------------------------------------------------
+template <bool kHist>
+__global__ void __launch_bounds__(kTuneThreads)
+    k_tune_test(const float* __restrict__ x, TuneGeom g,
+                const TuneCfg* __restrict__ cfgs, int l_stop,
+                unsigned long long* score, uint32_t* hists,
+                unsigned long long* nout) {
+  extern __shared__ float R[];
+  __shared__ TuneCfg c;
+  __shared__ unsigned long long red[32];
+  const int v = blockIdx.y;
+  load_cfg(&c, cfgs + v);
+  const Sub f = sample_block(x, g, blockIdx.x);
+  init_anchors(R, f, g.interp, g.A);
+  unsigned long long sc = 0, no = 0;
+  uint32_t* h = kHist ? hists + (size_t)v * 65536 : nullptr;
+  for (int l = g.L; l >= l_stop; --l)
+    sweep_level<kHist>(R, f, g.interp, g.k, l, c, l == l_stop, sc, h, no);
+  sc = block_sum(sc, red);
+  if (threadIdx.x == 0 && sc) atomicAdd(score + v, sc);
+  no = block_sum(no, red);
+  if (threadIdx.x == 0 && no) atomicAdd(nout + v, no);
+}
+
+// ---------------------------------------------------------------------
+// Sec. 6.5: Lorenzo test, CTA (sample block, order).  The recurrence runs
+// as a wavefront over the planes i0 + i1 + i2 = t: every neighbour a point
+// reads lies on an earlier plane.  Neighbours outside the block read 0.
+// ---------------------------------------------------------------------
+__global__ void __launch_bounds__(kTuneThreads)
+    k_tune_lorenzo(const float* __restrict__ x, TuneGeom g,
+                   const Ctl* __restrict__ ctl, uint32_t* hists,
+                   unsigned long long* nout) {
+  extern __shared__ float R[];
+  __shared__ unsigned long long red[32];
+  const int order = blockIdx.y + 1;
+  const Sub f = sample_block(x, g, blockIdx.x);
+  const float e = ctl->e;
+  const float inv2 = __double2float_rn(__ddiv_rn(1.0, __dmul_rn(2.0, (double)e)));
+  const float twoe = __fmul_rn(2.0f, e);
+  const float co[2][3] = {{1.0f, -1.0f, 0.0f}, {1.0f, -2.0f, 1.0f}};
+  int lim[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) lim[d] = d < g.off ? 0 : order;
+  uint32_t* h = hists + (size_t)blockIdx.y * 65536;
+  unsigned long long no = 0;
+  const int n0 = f.n[0], n1 = f.n[1], n2 = f.n[2];
+  const int T = (n0 - 1) + (n1 - 1) + (n2 - 1);
+  for (int t = 0; t <= T; ++t) {
+    for (int q = threadIdx.x; q < n0 * n1; q += blockDim.x) {
+      const int i0 = q / n1, i1 = q % n1, i2 = t - i0 - i1;
+      if (i2 < 0 || i2 >= n2) continue;
+      float acc = 0.0f;
+      for (int a = 0; a <= lim[0]; ++a)
+        for (int b = 0; b <= lim[1]; ++b)
+          for (int cz = 0; cz <= lim[2]; ++cz) {
+            if (a == 0 && b == 0 && cz == 0) continue;
+            const float wgt = -__fmul_rn(__fmul_rn(co[order - 1][a], co[order - 1][b]),
+                                         co[order - 1][cz]);
+            float v = 0.0f;
+            if (a <= i0 && b <= i1 && cz <= i2)
+              v = R[((i0 - a) * n1 + (i1 - b)) * n2 + (i2 - cz)];
+            acc = __fadd_rn(acc, __fmul_rn(wgt, v));
+          }
+      const int cc[3] = {i0, i1, i2};
+      float rv;
+      const unsigned code = quantize(xval(f, cc), acc, e, inv2, twoe, rv);
+      R[(i0 * n1 + i1) * n2 + i2] = rv;
+      atomicAdd(h + code, 1u);
+      if (code == 0u) ++no;
+    }
+    __syncthreads();
+  }
+  no = block_sum(no, red);
+  if (threadIdx.x == 0 && no) atomicAdd(nout + blockIdx.y, no);
+}
+
+// ---------------------------------------------------------------------
+// Sec. 6.6: CTA per field block: the centred sub-block, every candidate
+// interpolator for all levels, the smallest summed score wins
+// ---------------------------------------------------------------------
+struct BlockGeom {
+  uint32_t nb[3];
+  int bs, Q, frozen_slot;
+};
+
+__global__ void __launch_bounds__(kBlockThreads)
+    k_tune_blockwise(const float* __restrict__ x, TuneGeom g, BlockGeom bg,
+                     const TuneCfg* __restrict__ base, unsigned allow,
+                     uint8_t* bmap) {
+  extern __shared__ float R[];
+  __shared__ TuneCfg c;
+  __shared__ unsigned long long red[32];
+  load_cfg(&c, base);
+  unsigned b = blockIdx.x;
+  Sub f;
+  size_t off = 0;
+  int qmin = 0x7fffffff;
+  for (int d = 2; d >= 0; --d) {
+    const unsigned j = b % bg.nb[d];
+    b /= bg.nb[d];
+    f.xst[d] = g.fst[d];
+    if (d < g.off) {
+      f.n[d] = 1;
+      continue;
+    }
+    const int b0 = (int)j * bg.bs;
+    const int bext = min(bg.bs, (int)g.n[d] - b0);
+    const int q = min(bext, bg.Q);
+    off += (size_t)(b0 + (bext - q) / 2) * g.fst[d];
+    f.n[d] = q;
+    if (d != bg.frozen_slot) qmin = min(qmin, q);
+  }
+  f.x = x + off;
+  set_strides(f);
+  int As = 2;
+  const int lim = qmin > 1 ? qmin - 1 : 1;
+  while (As * 2 <= lim) As *= 2;
+  int L = 0;
+  while ((1 << L) < As) ++L;
+  const uint8_t codes[5] = {0, 1, 5, 2, 6};
+  unsigned long long best = ~0ull;
+  uint8_t bestc = 0;
+  for (int j = 0; j < 5; ++j) {
+    const uint8_t v = codes[j];
+    if ((v & 3) == CUBIC_NAT && !(allow & 1u)) continue;
+    if ((v & 4) && !(allow & 2u)) continue;
+    __syncthreads();
+    if (threadIdx.x < kMaxLevels) {
+      c.kind[threadIdx.x] = v & 3;
+      c.same[threadIdx.x] = (v >> 2) & 1;
+    }
+    __syncthreads();
+    init_anchors(R, f, g.interp, As);
+    unsigned long long sc = 0, no = 0;
+    for (int l = L; l >= 1; --l)
+      sweep_level<false>(R, f, g.interp, g.k, l, c, true, sc, nullptr, no);
+    sc = block_sum(sc, red);
+    if (threadIdx.x == 0 && sc < best) {
+      best = sc;
+      bestc = v;
+    }
+  }
+  if (threadIdx.x == 0) bmap[blockIdx.x] = bestc;
+}
+
+// Huffman bits of a histogram: sum of count * code length
+__global__ void __launch_bounds__(1024)
+    k_tune_cost(const uint32_t* __restrict__ hist,
+                const uint8_t* __restrict__ lens, unsigned long long* cost) {
+  __shared__ unsigned long long red[32];
+  unsigned long long acc = 0;
+  for (int i = threadIdx.x; i < 65536; i += blockDim.x)
+    acc += (unsigned long long)hist[i] * lens[i];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) *cost = acc;
+}
+
+void set_smem_attr() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(k_tune_test<true>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kTuneSmemMax);
+  cudaFuncSetAttribute(k_tune_test<false>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kTuneSmemMax);
+  cudaFuncSetAttribute(k_tune_lorenzo,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kTuneSmemMax);
+  cudaFuncSetAttribute(k_tune_blockwise,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kTuneSmemMax);
+  done = true;
+}
+
+}  // namespace
+
+void launch_tune_stats(const float* x, const uint32_t n[3],
+                       const uint32_t fst[3], const int real[3], int t,
+                       const Ctl* ctl, unsigned long long* acc, int num_sms,
+                       cudaStream_t s) {
+  StatsGeom g;
+  unsigned long long total = 1;
+  for (int d = 0; d < 3; ++d) {
+    g.fst[d] = fst[d];
+    g.real[d] = real[d];
+    if (real[d]) {
+      g.lo[d] = 3;
+      g.step[d] = (uint32_t)t;
+      g.cnt[d] = n[d] >= 7 ? (n[d] - 7) / (uint32_t)t + 1 : 0;
+    } else {
+      g.lo[d] = 0;
+      g.step[d] = 1;
+      g.cnt[d] = 1;
+    }
+    total *= g.cnt[d];
+  }
+  if (total == 0) return;
+  unsigned long long blocks = (total + 255) / 256;
+  if (blocks > (unsigned long long)num_sms * 8) blocks = (unsigned long long)num_sms * 8;
+  k_tune_stats<<<(unsigned)blocks, 256, 0, s>>>(x, g, total, ctl, acc);
+}
+
+void launch_tune_params(TuneCfg* cfgs, int nvar, int L, const Ctl* ctl,
+                        cudaStream_t s) {
+  k_tune_params<<<(nvar + 63) / 64, 64, 0, s>>>(cfgs, nvar, L, ctl);
+}
+
+size_t tune_test_smem(const TuneGeom& g) {
+  return (size_t)g.ext[0] * g.ext[1] * g.ext[2] * sizeof(float);
+}
+
+void launch_tune_test(const float* x, const TuneGeom& g, const TuneCfg* cfgs,
+                      int nvar, int nblk, int l_stop, bool hist,
+                      unsigned long long* score, uint32_t* hists,
+                      unsigned long long* nout, cudaStream_t s) {
+  set_smem_attr();
+  const dim3 grid((unsigned)nblk, (unsigned)nvar);
+  const size_t sm = tune_test_smem(g);
+  if (hist)
+    k_tune_test<true><<<grid, kTuneThreads, sm, s>>>(x, g, cfgs, l_stop, score,
+                                                     hists, nout);
+  else
+    k_tune_test<false><<<grid, kTuneThreads, sm, s>>>(x, g, cfgs, l_stop, score,
+                                                      hists, nout);
+}
+
+void launch_tune_lorenzo(const float* x, const TuneGeom& g, int nblk,
+                         const Ctl* ctl, uint32_t* hists,
+                         unsigned long long* nout, cudaStream_t s) {
+  set_smem_attr();
+  k_tune_lorenzo<<<dim3((unsigned)nblk, 2), kTuneThreads, tune_test_smem(g), s>>>(
+      x, g, ctl, hists, nout);
+}
+
+void launch_tune_blockwise(const float* x, const TuneGeom& g, int bs, int Q,
+                           int frozen_slot, const uint32_t nb[3],
+                           uint32_t nblocks, const TuneCfg* base,
+                           unsigned allow, uint8_t* bmap, cudaStream_t s) {
+  set_smem_attr();
+  BlockGeom bg;
+  size_t vol = 1;
+  for (int d = 0; d < 3; ++d) {
+    bg.nb[d] = nb[d];
+    if (d >= g.off) vol *= (size_t)(Q < bs ? Q : bs);
+  }
+  bg.bs = bs;
+  bg.Q = Q;
+  bg.frozen_slot = frozen_slot;
+  k_tune_blockwise<<<nblocks, kBlockThreads, vol * sizeof(float), s>>>(
+      x, g, bg, base, allow, bmap);
+}
+
+void launch_tune_cost(const uint32_t* hist, const uint8_t* lens,
+                      unsigned long long* cost, cudaStream_t s) {
+  k_tune_cost<<<1, 1024, 0, s>>>(hist, lens, cost);
+}
+
+}  // namespace hpez

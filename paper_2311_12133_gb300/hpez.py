@@ -50,6 +50,40 @@ class hpez_config(ctypes.Structure):
     ]
 
 
+class hpez_tune_params(ctypes.Structure):
+    _fields_ = [
+        ("sample_rate", ctypes.c_double),
+        ("block_rate", ctypes.c_double),
+        ("sub_frac", ctypes.c_double),
+        ("lorenzo_coef", ctypes.c_double),
+        ("block_size", ctypes.c_int32),
+        ("tune_levels", ctypes.c_int32),
+        ("tune_eb", ctypes.c_int32),
+        ("tune_freeze", ctypes.c_int32),
+        ("tune_lorenzo", ctypes.c_int32),
+        ("tune_blockwise", ctypes.c_int32),
+        ("allow_natural", ctypes.c_int32),
+        ("allow_same_level", ctypes.c_int32),
+        ("anchor_stride", ctypes.c_int32),
+    ]
+
+
+class hpez_tune_report(ctypes.Structure):
+    _fields_ = [
+        ("stats_count", ctypes.c_uint64),
+        ("mse_lin", ctypes.c_uint64 * 3),
+        ("mse_cub", ctypes.c_uint64 * 3),
+        ("nonsmooth_dim", ctypes.c_int32),
+        ("froze", ctypes.c_int32),
+        ("lorenzo_better", ctypes.c_int32),
+        ("n_sample_blocks", ctypes.c_uint32),
+        ("bits", ctypes.c_uint64 * 2),
+        ("lorenzo_bits", ctypes.c_uint64 * 2),
+        ("level_choice", (ctypes.c_uint8 * HPEZ_MAX_LEVELS) * 2),
+        ("level_score", (ctypes.c_uint64 * HPEZ_MAX_LEVELS) * 2),
+    ]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -94,6 +128,14 @@ def _load():
             "hpez_launch_count": (ctypes.c_int, [vp, u64p]),
             "hpez_set_option": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int64]),
             "hpez_decompress_noalloc": (ctypes.c_int, [vp, u64, vp, u64, vp]),
+            "hpez_default_tune_params": (ctypes.c_int,
+                                         [ctypes.POINTER(hpez_tune_params)]),
+            "hpez_blockmap_size": (u64, [ctypes.c_int, u64p, ctypes.c_int]),
+            "hpez_tune": (ctypes.c_int, [vp, vp, ctypes.c_int, u64p, ctypes.c_int,
+                                         ctypes.c_double,
+                                         ctypes.POINTER(hpez_tune_params), cfgp,
+                                         vp, u64, ctypes.POINTER(hpez_tune_report),
+                                         vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -110,7 +152,8 @@ def exported_symbols() -> list[str]:
             "hpez_compress_host", "hpez_decompress_host", "hpez_inspect",
             "hpez_strerror", "hpez_profile_enable", "hpez_profile_get",
             "hpez_profile_phase_name", "hpez_launch_count", "hpez_set_option",
-            "hpez_decompress_noalloc"]
+            "hpez_decompress_noalloc", "hpez_default_tune_params",
+            "hpez_blockmap_size", "hpez_tune"]
 
 
 def _check(rc: int, what: str):
@@ -215,7 +258,9 @@ def hpez_inspect(header: bytes):
 HPEZ_PH_RANGE, HPEZ_PH_ANCHORS, HPEZ_PH_HIST, HPEZ_PH_CODEBOOK = 0, 1, 2, 3
 HPEZ_PH_ENCODE, HPEZ_PH_PACK, HPEZ_PH_OUTLIERS, HPEZ_PH_FINALIZE = 4, 5, 6, 7
 HPEZ_PH_DEC_PREP, HPEZ_PH_DECODE, HPEZ_PH_SCATTER = 8, 9, 10
-HPEZ_PH_LEVEL, HPEZ_PH_DLEVEL, HPEZ_PROFILE_PHASES = 11, 27, 43
+HPEZ_PH_LEVEL, HPEZ_PH_DLEVEL = 11, 27
+HPEZ_PH_TUNE_STATS, HPEZ_PH_TUNE_LEVELS, HPEZ_PH_TUNE_EB = 43, 44, 45
+HPEZ_PH_TUNE_LORENZO, HPEZ_PH_TUNE_BLOCKS, HPEZ_PROFILE_PHASES = 46, 47, 48
 
 
 def hpez_profile_enable(ctx, enable: bool) -> None:
@@ -246,6 +291,37 @@ def hpez_launch_count(ctx) -> int:
     n = ctypes.c_uint64(0)
     _check(_load().hpez_launch_count(ctx, ctypes.byref(n)), "hpez_launch_count")
     return n.value
+
+
+def hpez_default_tune_params(**kw) -> hpez_tune_params:
+    t = hpez_tune_params()
+    _check(_load().hpez_default_tune_params(ctypes.byref(t)), "hpez_default_tune_params")
+    for k, v in kw.items():
+        setattr(t, k, v)
+    return t
+
+
+def hpez_blockmap_size(shape, block_size: int = 32) -> int:
+    return int(_load().hpez_blockmap_size(len(shape), _dims(shape), block_size))
+
+
+def hpez_tune(ctx, d_in: int, shape, eb_mode: int, eb: float,
+              tp: hpez_tune_params | None = None, stream: int = 0):
+    """Runs the Sec. 6 tuner on a device field; returns (config, report).
+    The config keeps a reference to its host block map."""
+    bs = tp.block_size if tp is not None else 32
+    nbm = hpez_blockmap_size(shape, bs) if bs >= 1 else 0
+    bm = np.zeros(max(nbm, 1), np.uint8)
+    cfg = hpez_config()
+    rep = hpez_tune_report()
+    _check(_load().hpez_tune(ctx, d_in, len(shape), _dims(shape), eb_mode, float(eb),
+                             ctypes.byref(tp) if tp is not None else None,
+                             ctypes.byref(cfg), bm.ctypes.data, bm.size,
+                             ctypes.byref(rep), stream or None), "hpez_tune")
+    cfg._blockmap_ref = bm[:nbm] if cfg.blockwise else None
+    if cfg.blockwise:
+        cfg.h_blockmap = cfg._blockmap_ref.ctypes.data
+    return cfg, rep
 
 
 # --------------------------------------------------------------------------
@@ -334,6 +410,14 @@ class Context:
         size = hpez_compress(self.handle, x.data_ptr(), tuple(x.shape), eb_mode, eb,
                              config, out.data_ptr(), out.numel(), self._stream(stream))
         return out, size
+
+    def tune(self, x, eb: float, eb_mode: int = HPEZ_EB_REL,
+             params: hpez_tune_params | None = None, stream=None):
+        """x: contiguous float32 CUDA tensor.  Returns (config, report)."""
+        import torch
+        assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+        return hpez_tune(self.handle, x.data_ptr(), tuple(x.shape), eb_mode, eb,
+                         params, self._stream(stream))
 
     def decompress(self, stream_buf, size: int, out=None, shape=None, stream=None):
         """stream_buf: uint8 CUDA tensor holding `size` bytes."""
