@@ -162,6 +162,113 @@ HPEZ_API int hpez_inspect(const void* h_header, uint64_t n, int* ndim, uint64_t*
 /* Static text for an error code. */
 HPEZ_API const char* hpez_strerror(int code);
 
+/* ---- batched form (no counterpart in the paper: a GPU execution form of
+ * the same method) ----
+ * Many fields compressed (or streams decompressed) together.  Each field
+ * runs exactly the single-field operations, so its stream is byte-identical
+ * to hpez_compress's; the operations of all fields advance in lockstep
+ * ("ticks"), and each tick launches one kernel per operation kind over the
+ * concatenated work of every field (levels of different fields, 2D and 3D,
+ * share launches).  Creation plans every field, allocates one workspace and
+ * uploads every tick's job tables; a run is kernel launches only. */
+typedef struct {
+  const float* d_in;     /* device, N float32, row-major */
+  int32_t ndim;
+  int32_t eb_mode;       /* HPEZ_EB_ABS / HPEZ_EB_REL */
+  uint64_t dims[3];
+  double eb;
+  const hpez_config* cfg; /* host, NULL = default; read at creation */
+  void* d_out;           /* device, out_cap bytes, 16-byte aligned */
+  uint64_t out_cap;
+} hpez_field_desc;
+
+typedef struct {
+  const void* d_in;      /* device stream, 16-byte aligned */
+  uint64_t in_size;
+  const void* h_header;  /* host copy of the stream's first 512 bytes */
+  float* d_out;          /* device, >= N floats, 4-byte aligned */
+  uint64_t out_cap_elems;
+} hpez_stream_desc;
+
+typedef struct hpez_batch hpez_batch;
+
+/* Plan n fields (streams) into one batch.  The device pointers are bound
+ * to the batch: every run reads and writes the same buffers.  Errors:
+ * INVALID_ARG / CORRUPT_STREAM / OUT_TOO_SMALL for the first bad entry,
+ * NO_MEMORY, CUDA.  Synchronizes the device once (the uploads). */
+HPEZ_API int hpez_batch_create_compress(hpez_ctx* ctx, int n,
+                                        const hpez_field_desc* fields,
+                                        hpez_batch** out);
+HPEZ_API int hpez_batch_create_decompress(hpez_ctx* ctx, int n,
+                                          const hpez_stream_desc* streams,
+                                          hpez_batch** out);
+/* Enqueue one run on `stream` (asynchronous, launches only). */
+HPEZ_API int hpez_batch_run(hpez_batch* b, void* stream);
+/* The same run through a CUDA graph: the first call captures the launch
+ * sequence on `stream` (which must not be the legacy default stream),
+ * later calls replay it. */
+HPEZ_API int hpez_batch_run_graph(hpez_batch* b, void* stream);
+/* After a run: per-field stream sizes (compress; 0 for decompress) and
+ * status (0 or a negative HPEZ_ERR_*), copied to host arrays of n entries
+ * (either may be NULL).  Synchronizes `stream`. */
+HPEZ_API int hpez_batch_results(hpez_batch* b, void* stream, uint64_t* h_sizes,
+                                int32_t* h_status);
+/* Kernel launches and ticks of one run. */
+HPEZ_API int hpez_batch_launch_count(hpez_batch* b, uint64_t* launches,
+                                     uint64_t* ticks);
+HPEZ_API int hpez_batch_destroy(hpez_batch* b);
+
+/* ---- served form (no counterpart in the paper) ----
+ * A request loop with continuous batching.  Requests carry HOST buffers.
+ * Each step: finished requests copy their result to the host and free their
+ * memory; queued requests are admitted (FIFO) while a slot is free and their
+ * device memory (input + output + workspace) fits the budget, their input
+ * is copied to the device; then one tick advances every admitted request by
+ * one operation (as in the batched form), so a request admitted now runs
+ * alongside requests that are levels or stages ahead.  Results equal the
+ * single-call results. */
+#define HPEZ_REQ_COMPRESS 0
+#define HPEZ_REQ_DECOMPRESS 1
+typedef struct {
+  int32_t op;             /* HPEZ_REQ_* */
+  int32_t ndim;           /* compress */
+  uint64_t dims[3];       /* compress */
+  int32_t eb_mode;        /* compress */
+  int32_t reserved;
+  double eb;              /* compress */
+  const hpez_config* cfg; /* compress, NULL = default; copied at submit */
+  const void* h_in;       /* host: the field (compress) or stream (decompress);
+                             must stay valid until the request completes */
+  uint64_t in_bytes;      /* decompress: stream size */
+  void* h_out;            /* host: stream (compress) or field (decompress) */
+  uint64_t out_cap;       /* bytes of h_out */
+} hpez_request;
+
+typedef struct hpez_server hpez_server;
+
+/* budget_bytes of device memory is allocated at creation; max_slots bounds
+ * the requests in flight.  Errors: INVALID_ARG, NO_MEMORY, CUDA. */
+HPEZ_API int hpez_server_create(hpez_ctx* ctx, uint64_t budget_bytes,
+                                int max_slots, void* stream,
+                                hpez_server** out);
+/* Queue a request; *id identifies it in hpez_server_poll.  Errors:
+ * INVALID_ARG / CORRUPT_STREAM (checked now), TOO_LARGE (it can never fit
+ * the budget). */
+HPEZ_API int hpez_server_submit(hpez_server* s, const hpez_request* req,
+                                uint64_t* id);
+/* One step: retire, admit, one tick.  Never waits for the GPU except to
+ * reuse a job-table buffer (at most 4 ticks in flight). */
+HPEZ_API int hpez_server_step(hpez_server* s);
+/* Completed requests since the last poll (up to cap): id, status, result
+ * bytes, latency from submit to completion in seconds. */
+HPEZ_API int hpez_server_poll(hpez_server* s, int cap, uint64_t* ids,
+                              int32_t* status, uint64_t* sizes,
+                              double* latency_s, int* n);
+HPEZ_API int hpez_server_stats(hpez_server* s, int* active, int* queued,
+                               uint64_t* used_bytes, uint64_t* ticks,
+                               uint64_t* launches);
+HPEZ_API int hpez_server_destroy(hpez_server* s);
+
 /* ---- auto-tuning (Sec. 6) ----
  * The tuner picks theta for one field from compression tests on samples:
  *   Sec. 6.1  statistics on a uniform lattice (stride t, the smallest with

@@ -20,22 +20,6 @@ using namespace hpez;
 namespace hpez {
 namespace host {
 
-// ---------------------------------------------------------------------
-// header layout (byte offsets)
-// ---------------------------------------------------------------------
-enum : int {
-  H_MAGIC = 0, H_VERSION = 4, H_FLAGS = 8, H_NDIM = 12, H_DIMS = 16,
-  H_EBMODE = 40, H_ANCHOR = 44, H_EBVALUE = 48, H_E = 56, H_CONST = 60,
-  H_FROZEN = 64, H_CHUNK = 68, H_ALPHA = 72, H_BETA = 80, H_MDIV = 88,
-  H_INTERP = 112, H_PARADIGM = 128, H_SAME = 144, H_ORDER = 160,
-  H_PREDICTOR = 208, H_BLOCKWISE = 212, H_NANCHORS = 216, H_NOUTLIERS = 224,
-  H_NUSED = 232, H_BLOCKSIZE = 236, H_NCHUNKS = 240, H_TOTALWORDS = 248,
-  H_OFF_ANCHORS = 256, H_OFF_CHUNKW = 264, H_OFF_TABLE = 272,
-  H_OFF_OUTLIERS = 280, H_OFF_BITS = 288, H_OFF_BLOCKMAP = 296,
-  H_TOTAL = 304, H_NBLOCKS = 312
-};
-constexpr uint32_t kMagic = 0x5A455048u;  // "HPEZ"
-constexpr uint32_t kVersion = 1u;
 
 void wr32(uint8_t* b, int o, uint32_t v) { std::memcpy(b + o, &v, 4); }
 void wr64(uint8_t* b, int o, uint64_t v) { std::memcpy(b + o, &v, 8); }
@@ -162,10 +146,6 @@ float md_weight(const Plan& p, const hpez_config& c, unsigned S, int slot) {
 // (order pi: odd on pi_j, any parity on earlier dims, even on later ones);
 // for the multi-dimensional paradigm one box per odd-slot set S, grouped by
 // |S|.  Each (pass, half) is a launch; launches run in list order.
-struct Launch {
-  PassBox pb;
-  int group;  // launches of the same group are independent
-};
 
 std::vector<Launch> level_schedule(const Plan& p, const hpez_config& c,
                                    int l) {
@@ -526,6 +506,81 @@ struct CompressBufs {
   uint8_t* bmap;
 };
 
+
+// Reads and validates a stream header (host copy of its first 512 bytes).
+int parse_stream_header(const uint8_t* h, uint64_t in_size, StreamInfo& si) {
+  si = StreamInfo();  // value-initialized: the plan keeps its defaults
+  int nd;
+  uint64_t dims[3];
+  int rc = hpez_inspect(h, kHeaderBytes, &nd, dims, nullptr);
+  if (rc) return rc;
+  if (rd64(h, H_TOTAL) > in_size) return HPEZ_ERR_CORRUPT_STREAM;
+  uint64_t N = 1;
+  for (int d = 0; d < nd; ++d) {
+    if (dims[d] == 0) return HPEZ_ERR_CORRUPT_STREAM;
+    N *= dims[d];
+    if (N > 0xFFFFFFFFull) return HPEZ_ERR_CORRUPT_STREAM;
+  }
+  si.nd = nd;
+  for (int d = 0; d < 3; ++d) si.dims[d] = d < nd ? dims[d] : 1;
+  si.N = N;
+  hpez_config& cfg = si.cfg;
+  cfg.anchor_stride = (int32_t)rd32(h, H_ANCHOR);
+  cfg.frozen_dim = (int32_t)rd32(h, H_FROZEN);
+  cfg.chunk_syms = (int32_t)rd32(h, H_CHUNK);
+  cfg.blockwise = (int32_t)rd32(h, H_BLOCKWISE);
+  cfg.block_size = (int32_t)rd32(h, H_BLOCKSIZE);
+  cfg.alpha = rdf64(h, H_ALPHA);
+  cfg.beta = rdf64(h, H_BETA);
+  for (int d = 0; d < 3; ++d) cfg.md_inv_var[d] = rdf64(h, H_MDIV + 8 * d);
+  for (int l = 0; l < HPEZ_MAX_LEVELS; ++l) {
+    cfg.interp[l] = h[H_INTERP + l];
+    cfg.paradigm[l] = h[H_PARADIGM + l];
+    cfg.same_level[l] = h[H_SAME + l];
+    for (int j = 0; j < 3; ++j) cfg.order[l][j] = h[H_ORDER + 3 * l + j];
+  }
+  if (rd32(h, H_FLAGS) & 1u) {
+    // constant field
+    if (plan_geometry(si.p, nd, dims, 2, -1)) return HPEZ_ERR_CORRUPT_STREAM;
+    si.is_const = true;
+    si.const_value = rdf32(h, H_CONST);
+    return HPEZ_OK;
+  }
+  Plan& p = si.p;
+  if (plan_geometry(p, nd, dims, cfg.anchor_stride, cfg.frozen_dim))
+    return HPEZ_ERR_CORRUPT_STREAM;
+  if (check_config(p, cfg)) return HPEZ_ERR_CORRUPT_STREAM;
+  plan_chunks_blocks(p, cfg);
+  const float e = rdf32(h, H_E);
+  if (!(e > 0.0f) || !std::isfinite(e)) return HPEZ_ERR_CORRUPT_STREAM;
+  si.e = e;
+  const uint64_t na = rd64(h, H_NANCHORS), nout = rd64(h, H_NOUTLIERS),
+                 nch = rd64(h, H_NCHUNKS), twords = rd64(h, H_TOTALWORDS);
+  const uint32_t nused = rd32(h, H_NUSED);
+  const uint64_t oa = rd64(h, H_OFF_ANCHORS), ocw = rd64(h, H_OFF_CHUNKW),
+                 ot = rd64(h, H_OFF_TABLE), oo = rd64(h, H_OFF_OUTLIERS),
+                 ob = rd64(h, H_OFF_BITS), obm = rd64(h, H_OFF_BLOCKMAP);
+  if (na != n_anchors(p) || nch != p.nch || nused == 0 || nused > 65536 ||
+      nout > N || (cfg.blockwise && rd64(h, H_NBLOCKS) != p.nblocks))
+    return HPEZ_ERR_CORRUPT_STREAM;
+  if (oa + 4 * na > in_size || ocw + 64 * nch > in_size ||
+      ot + 3ull * nused > in_size || oo + 4 * nout > in_size ||
+      ob + 4 * twords > in_size || (cfg.blockwise && obm + p.nblocks > in_size) ||
+      (oa & 15) || (ocw & 15) || (oo & 15) || (ob & 15))
+    return HPEZ_ERR_CORRUPT_STREAM;
+  si.na = na;
+  si.nout = nout;
+  si.nch = nch;
+  si.twords = twords;
+  si.nused = nused;
+  si.oa = oa;
+  si.ocw = ocw;
+  si.ot = ot;
+  si.oo = oo;
+  si.ob = ob;
+  si.obm = obm;
+  return HPEZ_OK;
+}
 }  // namespace host
 }  // namespace hpez
 
@@ -878,67 +933,25 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   if (rc) return rc;
   rc = cuda_check(cudaStreamSynchronize(s));
   if (rc) return rc;
-  const uint8_t* h = ctx->h_hdr;
-  int nd;
-  uint64_t dims[3];
-  rc = hpez_inspect(h, kHeaderBytes, &nd, dims, nullptr);
+  StreamInfo si;
+  rc = parse_stream_header(ctx->h_hdr, in_size, si);
   if (rc) return rc;
-  if (rd64(h, H_TOTAL) > in_size) return HPEZ_ERR_CORRUPT_STREAM;
-  uint64_t N = 1;
-  for (int d = 0; d < nd; ++d) {
-    if (dims[d] == 0) return HPEZ_ERR_CORRUPT_STREAM;
-    N *= dims[d];
-    if (N > 0xFFFFFFFFull) return HPEZ_ERR_CORRUPT_STREAM;
-  }
+  const uint64_t N = si.N;
   if (N > out_cap_elems) return HPEZ_ERR_OUT_TOO_SMALL;
   const uint8_t* in = static_cast<const uint8_t*>(d_in);
-
-  hpez_config cfg;
-  std::memset(&cfg, 0, sizeof(cfg));
-  cfg.anchor_stride = (int32_t)rd32(h, H_ANCHOR);
-  cfg.frozen_dim = (int32_t)rd32(h, H_FROZEN);
-  cfg.chunk_syms = (int32_t)rd32(h, H_CHUNK);
-  cfg.blockwise = (int32_t)rd32(h, H_BLOCKWISE);
-  cfg.block_size = (int32_t)rd32(h, H_BLOCKSIZE);
-  cfg.alpha = rdf64(h, H_ALPHA);
-  cfg.beta = rdf64(h, H_BETA);
-  for (int d = 0; d < 3; ++d) cfg.md_inv_var[d] = rdf64(h, H_MDIV + 8 * d);
-  for (int l = 0; l < HPEZ_MAX_LEVELS; ++l) {
-    cfg.interp[l] = h[H_INTERP + l];
-    cfg.paradigm[l] = h[H_PARADIGM + l];
-    cfg.same_level[l] = h[H_SAME + l];
-    for (int j = 0; j < 3; ++j) cfg.order[l][j] = h[H_ORDER + 3 * l + j];
-  }
-  if (rd32(h, H_FLAGS) & 1u) {
-    // constant field
-    Plan p;
-    if (plan_geometry(p, nd, dims, 2, -1)) return HPEZ_ERR_CORRUPT_STREAM;
-    launch_fill(d_out, p.N, rdf32(h, H_CONST), ctx->num_sms, s);
+  if (si.is_const) {
+    launch_fill(d_out, (uint32_t)N, si.const_value, ctx->num_sms, s);
     rc = cuda_check(cudaGetLastError());
     if (rc) return rc;
     return cuda_check(cudaStreamSynchronize(s));
   }
-  Plan p;
-  if (plan_geometry(p, nd, dims, cfg.anchor_stride, cfg.frozen_dim))
-    return HPEZ_ERR_CORRUPT_STREAM;
-  if (check_config(p, cfg)) return HPEZ_ERR_CORRUPT_STREAM;
-  plan_chunks_blocks(p, cfg);
-  const float e = rdf32(h, H_E);
-  if (!(e > 0.0f) || !std::isfinite(e)) return HPEZ_ERR_CORRUPT_STREAM;
-  const uint64_t na = rd64(h, H_NANCHORS), nout = rd64(h, H_NOUTLIERS),
-                 nch = rd64(h, H_NCHUNKS), twords = rd64(h, H_TOTALWORDS);
-  const uint32_t nused = rd32(h, H_NUSED);
-  const uint64_t oa = rd64(h, H_OFF_ANCHORS), ocw = rd64(h, H_OFF_CHUNKW),
-                 ot = rd64(h, H_OFF_TABLE), oo = rd64(h, H_OFF_OUTLIERS),
-                 ob = rd64(h, H_OFF_BITS), obm = rd64(h, H_OFF_BLOCKMAP);
-  if (na != n_anchors(p) || nch != p.nch || nused == 0 || nused > 65536 ||
-      nout > N || (cfg.blockwise && rd64(h, H_NBLOCKS) != p.nblocks))
-    return HPEZ_ERR_CORRUPT_STREAM;
-  if (oa + 4 * na > in_size || ocw + 64 * nch > in_size ||
-      ot + 3ull * nused > in_size || oo + 4 * nout > in_size ||
-      ob + 4 * twords > in_size || (cfg.blockwise && obm + p.nblocks > in_size) ||
-      (oa & 15) || (ocw & 15) || (oo & 15) || (ob & 15))
-    return HPEZ_ERR_CORRUPT_STREAM;
+  const hpez_config& cfg = si.cfg;
+  const Plan& p = si.p;
+  const float e = si.e;
+  const uint64_t nout = si.nout, twords = si.twords;
+  const uint32_t nused = si.nused;
+  const uint64_t oa = si.oa, ocw = si.ocw, ot = si.ot, oo = si.oo, ob = si.ob,
+                 obm = si.obm;
   uint16_t single_sym = 0;
   if (nused == 1) {
     // the lone symbol of a single-symbol code table
@@ -948,7 +961,6 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
     if (rc) return rc;
     single_sym = (uint16_t)(ctx->h_hdr[0] | (ctx->h_hdr[1] << 8));
   }
-
   Arena ar;
   const size_t o_ctl = ar.take<Ctl>(1);
   const size_t o_lut = ar.take<uint32_t>(4096);

@@ -94,6 +94,23 @@ struct hpez_ctx {
 namespace hpez {
 namespace host {
 
+// ---------------------------------------------------------------------
+// header layout (byte offsets)
+// ---------------------------------------------------------------------
+enum : int {
+  H_MAGIC = 0, H_VERSION = 4, H_FLAGS = 8, H_NDIM = 12, H_DIMS = 16,
+  H_EBMODE = 40, H_ANCHOR = 44, H_EBVALUE = 48, H_E = 56, H_CONST = 60,
+  H_FROZEN = 64, H_CHUNK = 68, H_ALPHA = 72, H_BETA = 80, H_MDIV = 88,
+  H_INTERP = 112, H_PARADIGM = 128, H_SAME = 144, H_ORDER = 160,
+  H_PREDICTOR = 208, H_BLOCKWISE = 212, H_NANCHORS = 216, H_NOUTLIERS = 224,
+  H_NUSED = 232, H_BLOCKSIZE = 236, H_NCHUNKS = 240, H_TOTALWORDS = 248,
+  H_OFF_ANCHORS = 256, H_OFF_CHUNKW = 264, H_OFF_TABLE = 272,
+  H_OFF_OUTLIERS = 280, H_OFF_BITS = 288, H_OFF_BLOCKMAP = 296,
+  H_TOTAL = 304, H_NBLOCKS = 312
+};
+constexpr uint32_t kMagic = 0x5A455048u;  // "HPEZ"
+constexpr uint32_t kVersion = 1u;
+
 // geometry plan
 struct Plan {
   int ndim = 0, off = 0;
@@ -120,7 +137,44 @@ struct Arena {
   }
 };
 
+// one launch of the per-pass path
+struct Launch {
+  PassBox pb;
+  int group;  // launches of the same group are independent
+};
+
 int plan_geometry(Plan& p, int ndim, const uint64_t* dims, int A, int frozen);
+void plan_chunks_blocks(Plan& p, const hpez_config& c);
+std::vector<Launch> level_schedule(const Plan& p, const hpez_config& c, int l);
+bool plan_fused(const hpez_ctx* ctx, const Plan& p, const hpez_config& c, int l,
+                bool decomp, FusedLevel& F);
+bool plan_level3d(const hpez_ctx* ctx, const Plan& p, const hpez_config& c,
+                  int l, bool decomp, Level3D& F);
+uint64_t n_anchors(const Plan& p);
+void header_templates(const Plan& p, const hpez_config& c, int eb_mode,
+                      double eb, uint64_t off_anchors, uint64_t off_bmap,
+                      uint64_t off_chw, uint8_t* h, uint8_t* hc);
+uint64_t a16(uint64_t v);
+
+// a validated stream header
+struct StreamInfo {
+  int nd;
+  uint64_t dims[3];
+  uint64_t N;
+  hpez_config cfg;
+  bool is_const;
+  float const_value;
+  Plan p;
+  float e;
+  uint64_t na, nout, nch, twords;
+  uint32_t nused;
+  uint64_t oa, ocw, ot, oo, ob, obm;
+};
+int parse_stream_header(const uint8_t* h, uint64_t in_size, StreamInfo& si);
+uint32_t rd32(const uint8_t* b, int o);
+uint64_t rd64(const uint8_t* b, int o);
+double rdf64(const uint8_t* b, int o);
+float rdf32(const uint8_t* b, int o);
 int check_config(const Plan& p, const hpez_config& c);
 // Eq. 14 weight of slot `slot` within the slot mask S
 float md_weight(const Plan& p, const hpez_config& c, unsigned S, int slot);

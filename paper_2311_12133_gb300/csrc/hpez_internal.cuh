@@ -341,4 +341,102 @@ struct TuneGeom {
   uint32_t step[3];  // start offset between sample blocks per slot
 };
 
+// ---------------------------------------------------------------------
+// Batched work lists.  A batched launch runs one stage for many fields:
+// job j owns the launch's blocks [off[j], off[j+1]), and its block
+// blockIdx.x - off[j] plays the role the block index plays in the
+// single-field launch.  Single-CTA stages run one block per job.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ int batch_job(const uint32_t* __restrict__ off,
+                                         int nj) {
+  int lo = 0, hi = nj - 1;
+  const uint32_t b = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+struct InitJob { Ctl* ctl; };
+struct RangeJob { const float* x; uint32_t N; Ctl* ctl; };
+struct ParamsJob {
+  Ctl* ctl; int eb_mode; int L; double eb, alpha, beta; const float* x;
+};
+struct AnchorJob {
+  const float* x; LevelGeom ga; uint32_t total; float* RA; uint16_t* CA;
+  const Ctl* ctl;
+};
+struct FillJob { float* out; uint32_t N; float v; };
+struct ZeroJob { void* ptr; unsigned long long bytes; };
+struct UpsampleJob {
+  LevelGeom gc; uint32_t total_c; LevelGeom gs; const float* Rc;
+  const uint16_t* Cc; float* Rs; uint16_t* Cs; const Ctl* ctl;
+};
+struct PassJob { LevelGeom g; PassBox pb; SweepBufs B; };
+// a request's outcome: status (0 or a negative error) and stream size
+struct ResultJob {
+  const Ctl* ctl; const unsigned long long* tot;  // decompress: counters
+  unsigned long long twords, nout;                // decompress: expected
+  unsigned long long* size_out; int* status_out; int decomp;
+};
+struct Level3DJob {
+  Level3D P; const float* X; const uint16_t* codes_full; const float* outl_full;
+  const float* Rc; const uint16_t* Cc; float* Rs; uint16_t* Cs; const Ctl* ctl;
+};
+struct LevelJob {
+  FusedLevel P; SweepBufs B; const float* Rc; const uint16_t* Cc; float* Rs;
+  uint16_t* Cs;
+};
+struct HistJob {
+  const uint16_t* codes; uint32_t N, C, nch; uint32_t* hist; uint32_t* zc;
+  const Ctl* ctl;
+};
+struct ScanJob {
+  const uint32_t* in; unsigned long long* out; uint32_t n;
+  unsigned long long* total; const Ctl* ctl;
+};
+struct CodebookJob {
+  const uint32_t* hist; unsigned long long* enc; uint16_t* tsyms; uint8_t* tlens;
+  unsigned long long* gkeys; unsigned long long* giw; uint32_t* gpar;
+  uint8_t* lens_by_sym; Ctl* ctl;
+};
+struct EncLenJob {
+  const uint16_t* codes; uint32_t N, C, nch; const unsigned long long* enc;
+  uint16_t* lanebits; uint32_t* chw; const Ctl* ctl;
+};
+struct LayoutJob { Ctl* ctl; unsigned long long off_table, cap; };
+struct PackJob {
+  const uint16_t* codes; uint32_t N, C, nch; const unsigned long long* enc;
+  const uint16_t* lanebits; const uint32_t* chw; const unsigned long long* woff;
+  uint8_t* out; const Ctl* ctl;
+};
+struct OutlierJob {
+  const uint16_t* codes; uint32_t N, C, nch; const uint32_t* zc;
+  const unsigned long long* zoff; const float* src; float* dst; uint8_t* stream;
+  unsigned long long max_out; Ctl* ctl; int gather;
+};
+struct FinalizeJob {
+  const uint8_t* hdr; const uint8_t* hdr_const; uint8_t* out; const float* RA;
+  uint32_t na; unsigned long long off_anchors; const uint8_t* bmap;
+  uint32_t nblocks; unsigned long long off_bmap; const uint16_t* lanebits;
+  uint32_t nch; unsigned long long off_chw; const uint16_t* tsyms;
+  const uint8_t* tlens; const Ctl* ctl;
+};
+struct ChunkWordsJob { const uint8_t* lanebits_bytes; uint32_t nch; uint32_t* chw; };
+struct DecTablesJob {
+  const uint8_t* stream; uint32_t n_used; unsigned long long off_table;
+  uint32_t* lut; uint32_t* cnt; unsigned long long* first; uint32_t* offs;
+  uint16_t* sorted; unsigned long long* gkeys; Ctl* ctl;
+};
+struct DecodeJob {
+  const uint8_t* stream; unsigned long long off_bits, total_words;
+  const uint8_t* lanebits_bytes; const unsigned long long* woff; uint32_t N, C,
+      nch, n_used;
+  const uint8_t* single_src;  // the lone symbol of a one-symbol table
+  const uint32_t* lut; const uint32_t* cnt; const unsigned long long* first;
+  const uint32_t* offs; const uint16_t* sorted; uint16_t* codes; uint32_t* zc;
+  Ctl* ctl;
+};
+
 }  // namespace hpez

@@ -88,6 +88,56 @@ void launch_finalize(const uint8_t* hdr, const uint8_t* hdr_const,
                      const uint8_t* tlens, const Ctl* ctl, int num_sms,
                      cudaStream_t s);
 
+// batched forms (one launch for many fields; job j owns the launch's blocks
+// [off[j], off[j+1]); single-CTA stages run one block per job)
+void launch_init_ctl_batch(const InitJob* J, int nj, cudaStream_t s);
+void launch_range_batch(const RangeJob* J, const uint32_t* off, int nj,
+                        uint32_t nblk, cudaStream_t s);
+void launch_params_batch(const ParamsJob* J, int nj, cudaStream_t s);
+void launch_anchor_batch(const AnchorJob* J, const uint32_t* off, int nj,
+                         uint32_t nblk, cudaStream_t s);
+void launch_fill_batch(const FillJob* J, const uint32_t* off, int nj,
+                       uint32_t nblk, cudaStream_t s);
+void launch_level3d_batch(bool decomp, int kind, const Level3DJob* J,
+                          const uint32_t* off, int nj, uint32_t nblk,
+                          size_t smem, cudaStream_t s);
+void launch_level_batch(bool decomp, int kind, const LevelJob* J,
+                        const uint32_t* off, int nj, uint32_t nblk, size_t smem,
+                        cudaStream_t s);
+int level_kind(const SweepBufs& B);
+uint32_t hist_blocks(uint32_t nch, int num_sms);
+uint32_t enc_blocks(uint32_t nch, int num_sms);
+uint32_t decode_blocks(uint32_t nch, int num_sms);
+uint32_t chunk_words_blocks(uint32_t nch, int num_sms);
+uint32_t finalize_blocks(uint32_t na, uint32_t nch, int num_sms);
+void launch_hist_batch(const HistJob* J, const uint32_t* off, int nj,
+                       uint32_t nblk, cudaStream_t s);
+void launch_codebook_batch(const CodebookJob* J, int nj, cudaStream_t s);
+void launch_enc_len_batch(const EncLenJob* J, const uint32_t* off, int nj,
+                          uint32_t nblk, cudaStream_t s);
+void launch_pack_batch(const PackJob* J, const uint32_t* off, int nj,
+                       uint32_t nblk, cudaStream_t s);
+void launch_chunk_words_batch(const ChunkWordsJob* J, const uint32_t* off,
+                              int nj, uint32_t nblk, cudaStream_t s);
+void launch_outliers_batch(const OutlierJob* J, const uint32_t* off, int nj,
+                           uint32_t nblk, cudaStream_t s);
+void launch_dec_tables_batch(const DecTablesJob* J, int nj, cudaStream_t s);
+void launch_decode_batch(const DecodeJob* J, const uint32_t* off, int nj,
+                         uint32_t nblk, cudaStream_t s);
+void launch_scan_batch(const ScanJob* J, int nj, cudaStream_t s);
+void launch_layout_batch(const LayoutJob* J, int nj, cudaStream_t s);
+void launch_finalize_batch(const FinalizeJob* J, const uint32_t* off, int nj,
+                           uint32_t nblk, cudaStream_t s);
+void launch_result_batch(const ResultJob* J, int nj, cudaStream_t s);
+void launch_upsample_batch(const UpsampleJob* J, const uint32_t* off, int nj,
+                           uint32_t nblk, cudaStream_t s);
+void launch_pass_batch(bool decomp, const PassJob* J, const uint32_t* off,
+                       int nj, uint32_t nblk, cudaStream_t s);
+void launch_zero_batch(const ZeroJob* J, const uint32_t* off, int nj,
+                       uint32_t nblk, cudaStream_t s);
+uint32_t grid_blocks(uint64_t n, unsigned cap);
+uint32_t pass_blocks(uint32_t total, int num_sms);
+
 // k_tune.cu
 void launch_tune_stats(const float* x, const uint32_t n[3],
                        const uint32_t fst[3], const int real[3], int t,

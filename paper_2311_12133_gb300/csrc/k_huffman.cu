@@ -24,18 +24,20 @@ constexpr int kHistWarps = 8;
 // between lanes of one warp); the three central bins are counted in
 // registers; bins outside the window go straight to global atomics.
 // ---------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-    k_hist(const uint16_t* __restrict__ codes, uint32_t N, uint32_t C,
-           uint32_t nch, uint32_t* __restrict__ hist, uint32_t* __restrict__ zc,
-           const Ctl* __restrict__ ctl) {
+__device__ __forceinline__ void hist_body(const uint16_t* __restrict__ codes,
+                                          uint32_t N, uint32_t C, uint32_t nch,
+                                          uint32_t* __restrict__ hist,
+                                          uint32_t* __restrict__ zc,
+                                          const Ctl* __restrict__ ctl,
+                                          unsigned bid, unsigned nblk) {
   if (ctl->status || ctl->is_const) return;
   extern __shared__ uint32_t shw[];  // [kHistWarps][kHistWin]
   for (int i = threadIdx.x; i < kHistWarps * kHistWin; i += blockDim.x) shw[i] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   uint32_t* sh = shw + (threadIdx.x >> 5) * kHistWin;
-  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t warp = (bid * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (nblk * blockDim.x) >> 5;
   uint32_t cm1 = 0, c0 = 0, cp1 = 0;  // the three central bins in registers
   auto add = [&](unsigned v) {
     cm1 += (v == kRadius - 1);
@@ -100,6 +102,13 @@ __global__ void __launch_bounds__(256)
     for (int w = 0; w < kHistWarps; ++w) t += shw[w * kHistWin + i];
     if (t) atomicAdd(&hist[kHistLo + i], t);
   }
+}
+
+__global__ void __launch_bounds__(256)
+    k_hist(const uint16_t* __restrict__ codes, uint32_t N, uint32_t C,
+           uint32_t nch, uint32_t* __restrict__ hist, uint32_t* __restrict__ zc,
+           const Ctl* __restrict__ ctl) {
+  hist_body(codes, N, C, nch, hist, zc, ctl, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------
@@ -170,11 +179,10 @@ constexpr size_t kCodebookSmem =
 // scratch (global): gkeys u64[65536], giw u64[65536], gpar u32[131072],
 //                   lens_by_sym u8[65536]
 // ---------------------------------------------------------------------
-__global__ void __launch_bounds__(1024)
-    k_codebook(const uint32_t* __restrict__ hist, unsigned long long* enc,
-               uint16_t* tsyms, uint8_t* tlens, unsigned long long* gkeys,
-               unsigned long long* giw, uint32_t* gpar, uint8_t* lens_by_sym,
-               Ctl* ctl) {
+__device__ __forceinline__ void codebook_body(
+    const uint32_t* __restrict__ hist, unsigned long long* enc, uint16_t* tsyms,
+    uint8_t* tlens, unsigned long long* gkeys, unsigned long long* giw,
+    uint32_t* gpar, uint8_t* lens_by_sym, Ctl* ctl) {
   if (ctl->status || ctl->is_const) return;
   extern __shared__ unsigned long long smem[];
   __shared__ uint32_t s_n;
@@ -370,18 +378,26 @@ __global__ void __launch_bounds__(1024)
   for (uint32_t k = tid; k < n; k += blockDim.x) tlens[k] = lens_by_sym[tsyms[k]];
 }
 
+__global__ void __launch_bounds__(1024)
+    k_codebook(const uint32_t* __restrict__ hist, unsigned long long* enc,
+               uint16_t* tsyms, uint8_t* tlens, unsigned long long* gkeys,
+               unsigned long long* giw, uint32_t* gpar, uint8_t* lens_by_sym,
+               Ctl* ctl) {
+  codebook_body(hist, enc, tsyms, tlens, gkeys, giw, gpar, lens_by_sym, ctl);
+}
+
 // ---------------------------------------------------------------------
 // encode: lane bit counts and chunk word counts
 // ---------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-    k_enc_len(const uint16_t* __restrict__ codes, uint32_t N, uint32_t C,
-              uint32_t nch, const unsigned long long* __restrict__ enc,
-              uint16_t* __restrict__ lanebits, uint32_t* __restrict__ chw,
-              const Ctl* __restrict__ ctl) {
+__device__ __forceinline__ void enc_len_body(
+    const uint16_t* __restrict__ codes, uint32_t N, uint32_t C, uint32_t nch,
+    const unsigned long long* __restrict__ enc, uint16_t* __restrict__ lanebits,
+    uint32_t* __restrict__ chw, const Ctl* __restrict__ ctl, unsigned bid,
+    unsigned nblk) {
   if (ctl->status || ctl->is_const) return;
   const int lane = threadIdx.x & 31;
-  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t warp = (bid * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (nblk * blockDim.x) >> 5;
   for (uint32_t c = warp; c < nch; c += nwarps) {
     const uint32_t beg = c * C, nc = min(C, N - beg);
     uint32_t bits = 0;
@@ -403,6 +419,14 @@ __global__ void __launch_bounds__(256)
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
     if (lane == 0) chw[c] = (tot + 31) >> 5;
   }
+}
+
+__global__ void __launch_bounds__(256)
+    k_enc_len(const uint16_t* __restrict__ codes, uint32_t N, uint32_t C,
+              uint32_t nch, const unsigned long long* __restrict__ enc,
+              uint16_t* __restrict__ lanebits, uint32_t* __restrict__ chw,
+              const Ctl* __restrict__ ctl) {
+  enc_len_body(codes, N, C, nch, enc, lanebits, chw, ctl, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------
@@ -448,17 +472,16 @@ struct BitWriter {
   }
 };
 
-__global__ void __launch_bounds__(256)
-    k_pack(const uint16_t* __restrict__ codes, uint32_t N, uint32_t C,
-           uint32_t nch, const unsigned long long* __restrict__ enc,
-           const uint16_t* __restrict__ lanebits,
-           const uint32_t* __restrict__ chw,
-           const unsigned long long* __restrict__ woff, uint8_t* out,
-           const Ctl* __restrict__ ctl) {
+__device__ __forceinline__ void pack_body(
+    const uint16_t* __restrict__ codes, uint32_t N, uint32_t C, uint32_t nch,
+    const unsigned long long* __restrict__ enc,
+    const uint16_t* __restrict__ lanebits, const uint32_t* __restrict__ chw,
+    const unsigned long long* __restrict__ woff, uint8_t* out,
+    const Ctl* __restrict__ ctl, unsigned bid, unsigned nblk) {
   if (ctl->status || ctl->is_const) return;
   const int lane = threadIdx.x & 31;
-  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t warp = (bid * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (nblk * blockDim.x) >> 5;
   uint32_t* bits = reinterpret_cast<uint32_t*>(out + ctl->off_bits);
   for (uint32_t c = warp; c < nch; c += nwarps) {
     const uint32_t beg = c * C, nc = min(C, N - beg);
@@ -496,16 +519,33 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+__global__ void __launch_bounds__(256)
+    k_pack(const uint16_t* __restrict__ codes, uint32_t N, uint32_t C,
+           uint32_t nch, const unsigned long long* __restrict__ enc,
+           const uint16_t* __restrict__ lanebits,
+           const uint32_t* __restrict__ chw,
+           const unsigned long long* __restrict__ woff, uint8_t* out,
+           const Ctl* __restrict__ ctl) {
+  pack_body(codes, N, C, nch, enc, lanebits, chw, woff, out, ctl, blockIdx.x,
+            gridDim.x);
+}
+
 // chunk word counts from the stored lane bit counts (decompress)
-__global__ void k_chunk_words(const uint8_t* __restrict__ lanebits_bytes,
-                              uint32_t nch, uint32_t* __restrict__ chw) {
-  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nch;
-       c += gridDim.x * blockDim.x) {
+__device__ __forceinline__ void chunk_words_body(
+    const uint8_t* __restrict__ lanebits_bytes, uint32_t nch,
+    uint32_t* __restrict__ chw, unsigned bid, unsigned nblk) {
+  for (uint32_t c = bid * blockDim.x + threadIdx.x; c < nch;
+       c += nblk * blockDim.x) {
     const uint8_t* p = lanebits_bytes + (size_t)c * 64;
     uint32_t s = 0;
     for (int l = 0; l < 32; ++l) s += (uint32_t)p[2 * l] | ((uint32_t)p[2 * l + 1] << 8);
     chw[c] = (s + 31) >> 5;
   }
+}
+
+__global__ void k_chunk_words(const uint8_t* __restrict__ lanebits_bytes,
+                              uint32_t nch, uint32_t* __restrict__ chw) {
+  chunk_words_body(lanebits_bytes, nch, chw, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------
@@ -515,14 +555,13 @@ __global__ void k_chunk_words(const uint8_t* __restrict__ lanebits_bytes,
 // chunk, a block scan turns the counts into ranks, and the thread moves
 // its outliers in order.
 // ---------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-    k_outliers(bool gather, const uint16_t* __restrict__ codes, uint32_t N,
-               uint32_t C, uint32_t nch, const uint32_t* __restrict__ zc,
-               const unsigned long long* __restrict__ zoff, const float* src,
-               float* dst, uint8_t* stream, unsigned long long max_out,
-               Ctl* ctl) {
+__device__ __forceinline__ void outliers_body(
+    bool gather, const uint16_t* __restrict__ codes, uint32_t N, uint32_t C,
+    uint32_t nch, const uint32_t* __restrict__ zc,
+    const unsigned long long* __restrict__ zoff, const float* src, float* dst,
+    uint8_t* stream, unsigned long long max_out, Ctl* ctl, unsigned bid) {
   if (ctl->status || ctl->is_const) return;
-  const uint32_t c = blockIdx.x;
+  const uint32_t c = bid;
   if (c >= nch || zc[c] == 0) return;
   float* outl = reinterpret_cast<float*>(stream + ctl->off_outliers);
   const uint32_t beg = c * C, end = min(beg + C, N);
@@ -559,6 +598,16 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+__global__ void __launch_bounds__(256)
+    k_outliers(bool gather, const uint16_t* __restrict__ codes, uint32_t N,
+               uint32_t C, uint32_t nch, const uint32_t* __restrict__ zc,
+               const unsigned long long* __restrict__ zoff, const float* src,
+               float* dst, uint8_t* stream, unsigned long long max_out,
+               Ctl* ctl) {
+  outliers_body(gather, codes, N, C, nch, zc, zoff, src, dst, stream, max_out,
+                ctl, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------
 // decode tables from the stream's (symbol, length) table
 //   dec: [0,4096) LUT (len << 16 | sym, 0 = longer than 12 bits)
@@ -566,11 +615,10 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------
 constexpr int kLutBits = 12;
 
-__global__ void __launch_bounds__(1024)
-    k_dec_tables(const uint8_t* __restrict__ stream, uint32_t n_used,
-                 uint64_t off_table, uint32_t* lut, uint32_t* cnt,
-                 unsigned long long* first, uint32_t* offs, uint16_t* sorted,
-                 unsigned long long* gkeys, Ctl* ctl) {
+__device__ __forceinline__ void dec_tables_body(
+    const uint8_t* __restrict__ stream, uint32_t n_used, uint64_t off_table,
+    uint32_t* lut, uint32_t* cnt, unsigned long long* first, uint32_t* offs,
+    uint16_t* sorted, unsigned long long* gkeys, Ctl* ctl) {
   extern __shared__ unsigned long long smem[];
   __shared__ uint32_t s_bad;
   __shared__ uint32_t s_cnt[64];
@@ -653,20 +701,28 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
+__global__ void __launch_bounds__(1024)
+    k_dec_tables(const uint8_t* __restrict__ stream, uint32_t n_used,
+                 uint64_t off_table, uint32_t* lut, uint32_t* cnt,
+                 unsigned long long* first, uint32_t* offs, uint16_t* sorted,
+                 unsigned long long* gkeys, Ctl* ctl) {
+  dec_tables_body(stream, n_used, off_table, lut, cnt, first, offs, sorted,
+                  gkeys, ctl);
+}
+
 // ---------------------------------------------------------------------
 // decode: one warp per chunk, lane l decodes its own bit range
 // ---------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-    k_decode(const uint8_t* __restrict__ stream, uint64_t off_bits,
-             uint64_t total_words, const uint8_t* __restrict__ lanebits_bytes,
-             const unsigned long long* __restrict__ woff, uint32_t N,
-             uint32_t C, uint32_t nch, uint32_t n_used, uint16_t single_sym,
-             const uint32_t* __restrict__ g_lut,
-             const uint32_t* __restrict__ g_cnt,
-             const unsigned long long* __restrict__ g_first,
-             const uint32_t* __restrict__ g_offs,
-             const uint16_t* __restrict__ sorted, uint16_t* __restrict__ codes,
-             uint32_t* __restrict__ zc, Ctl* ctl) {
+__device__ __forceinline__ void decode_body(
+    const uint8_t* __restrict__ stream, uint64_t off_bits, uint64_t total_words,
+    const uint8_t* __restrict__ lanebits_bytes,
+    const unsigned long long* __restrict__ woff, uint32_t N, uint32_t C,
+    uint32_t nch, uint32_t n_used, uint16_t single_sym,
+    const uint32_t* __restrict__ g_lut, const uint32_t* __restrict__ g_cnt,
+    const unsigned long long* __restrict__ g_first,
+    const uint32_t* __restrict__ g_offs, const uint16_t* __restrict__ sorted,
+    uint16_t* __restrict__ codes, uint32_t* __restrict__ zc, Ctl* ctl,
+    unsigned bid, unsigned nblk) {
   __shared__ uint32_t lut[1 << kLutBits];
   __shared__ uint32_t cnt[64], offs[64];
   __shared__ unsigned long long first[64];
@@ -679,8 +735,8 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   if (ctl->status) return;
   const int lane = threadIdx.x & 31;
-  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t warp = (bid * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (nblk * blockDim.x) >> 5;
   const uint32_t* allw = reinterpret_cast<const uint32_t*>(stream + off_bits);
   for (uint32_t c = warp; c < nch; c += nwarps) {
     const uint32_t beg = c * C, nc = min(C, N - beg);
@@ -753,6 +809,94 @@ __global__ void __launch_bounds__(256)
     for (int o = 16; o > 0; o >>= 1) zeros += __shfl_xor_sync(0xffffffffu, zeros, o);
     if (lane == 0) zc[c] = zeros;
   }
+}
+
+__global__ void __launch_bounds__(256)
+    k_decode(const uint8_t* __restrict__ stream, uint64_t off_bits,
+             uint64_t total_words, const uint8_t* __restrict__ lanebits_bytes,
+             const unsigned long long* __restrict__ woff, uint32_t N,
+             uint32_t C, uint32_t nch, uint32_t n_used, uint16_t single_sym,
+             const uint32_t* __restrict__ g_lut,
+             const uint32_t* __restrict__ g_cnt,
+             const unsigned long long* __restrict__ g_first,
+             const uint32_t* __restrict__ g_offs,
+             const uint16_t* __restrict__ sorted, uint16_t* __restrict__ codes,
+             uint32_t* __restrict__ zc, Ctl* ctl) {
+  decode_body(stream, off_bits, total_words, lanebits_bytes, woff, N, C, nch,
+              n_used, single_sym, g_lut, g_cnt, g_first, g_offs, sorted, codes,
+              zc, ctl, blockIdx.x, gridDim.x);
+}
+
+// ---------------------------------------------------------------------
+// batched forms
+// ---------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+    k_hist_batch(const HistJob* __restrict__ J, const uint32_t* __restrict__ off,
+                 int nj) {
+  const int j = batch_job(off, nj);
+  const HistJob& q = J[j];
+  hist_body(q.codes, q.N, q.C, q.nch, q.hist, q.zc, q.ctl, blockIdx.x - off[j],
+            off[j + 1] - off[j]);
+}
+
+__global__ void __launch_bounds__(1024) k_codebook_batch(const CodebookJob* __restrict__ J) {
+  const CodebookJob& q = J[blockIdx.x];
+  codebook_body(q.hist, q.enc, q.tsyms, q.tlens, q.gkeys, q.giw, q.gpar,
+                q.lens_by_sym, q.ctl);
+}
+
+__global__ void __launch_bounds__(256)
+    k_enc_len_batch(const EncLenJob* __restrict__ J,
+                    const uint32_t* __restrict__ off, int nj) {
+  const int j = batch_job(off, nj);
+  const EncLenJob& q = J[j];
+  enc_len_body(q.codes, q.N, q.C, q.nch, q.enc, q.lanebits, q.chw, q.ctl,
+               blockIdx.x - off[j], off[j + 1] - off[j]);
+}
+
+__global__ void __launch_bounds__(256)
+    k_pack_batch(const PackJob* __restrict__ J, const uint32_t* __restrict__ off,
+                 int nj) {
+  const int j = batch_job(off, nj);
+  const PackJob& q = J[j];
+  pack_body(q.codes, q.N, q.C, q.nch, q.enc, q.lanebits, q.chw, q.woff, q.out,
+            q.ctl, blockIdx.x - off[j], off[j + 1] - off[j]);
+}
+
+__global__ void k_chunk_words_batch(const ChunkWordsJob* __restrict__ J,
+                                    const uint32_t* __restrict__ off, int nj) {
+  const int j = batch_job(off, nj);
+  chunk_words_body(J[j].lanebits_bytes, J[j].nch, J[j].chw, blockIdx.x - off[j],
+                   off[j + 1] - off[j]);
+}
+
+__global__ void __launch_bounds__(256)
+    k_outliers_batch(const OutlierJob* __restrict__ J,
+                     const uint32_t* __restrict__ off, int nj) {
+  const int j = batch_job(off, nj);
+  const OutlierJob& q = J[j];
+  outliers_body(q.gather != 0, q.codes, q.N, q.C, q.nch, q.zc, q.zoff, q.src,
+                q.dst, q.stream, q.max_out, q.ctl, blockIdx.x - off[j]);
+}
+
+__global__ void __launch_bounds__(1024)
+    k_dec_tables_batch(const DecTablesJob* __restrict__ J) {
+  const DecTablesJob& q = J[blockIdx.x];
+  dec_tables_body(q.stream, q.n_used, q.off_table, q.lut, q.cnt, q.first,
+                  q.offs, q.sorted, q.gkeys, q.ctl);
+}
+
+__global__ void __launch_bounds__(256)
+    k_decode_batch(const DecodeJob* __restrict__ J,
+                   const uint32_t* __restrict__ off, int nj) {
+  const int j = batch_job(off, nj);
+  const DecodeJob& q = J[j];
+  const uint16_t single =
+      q.single_src ? (uint16_t)(q.single_src[0] | (q.single_src[1] << 8)) : 0;
+  decode_body(q.stream, q.off_bits, q.total_words, q.lanebits_bytes, q.woff, q.N,
+              q.C, q.nch, q.n_used, single, q.lut, q.cnt, q.first, q.offs,
+              q.sorted, q.codes, q.zc, q.ctl, blockIdx.x - off[j],
+              off[j + 1] - off[j]);
 }
 
 // ---------------------------------------------------------------------
@@ -857,6 +1001,80 @@ void launch_decode(const uint8_t* stream, uint64_t off_bits,
   k_decode<<<warps_grid(nch, num_sms * 2), 256, 0, s>>>(
       stream, off_bits, total_words, lanebits_bytes, woff, N, C, nch, n_used,
       single_sym, lut, cnt, first, offs, sorted, codes, zc, ctl);
+}
+
+// ---------------------------------------------------------------------
+// batched launchers (block counts per job: the *_blocks helpers)
+// ---------------------------------------------------------------------
+uint32_t hist_blocks(uint32_t nch, int num_sms) { return warps_grid(nch, num_sms); }
+uint32_t enc_blocks(uint32_t nch, int num_sms) { return warps_grid(nch, num_sms); }
+uint32_t decode_blocks(uint32_t nch, int num_sms) {
+  return warps_grid(nch, num_sms * 2);
+}
+uint32_t chunk_words_blocks(uint32_t nch, int num_sms) {
+  unsigned g = (nch + 255) / 256;
+  if (g < 1) g = 1;
+  if (g > (unsigned)num_sms * 8) g = num_sms * 8;
+  return g;
+}
+
+void launch_hist_batch(const HistJob* J, const uint32_t* off, int nj,
+                       uint32_t nblk, cudaStream_t s) {
+  static bool attr = false;
+  const int smem = kHistWarps * kHistWin * (int)sizeof(uint32_t);
+  if (!attr) {
+    cudaFuncSetAttribute(k_hist_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
+    attr = true;
+  }
+  if (nblk) k_hist_batch<<<nblk, 256, smem, s>>>(J, off, nj);
+}
+
+void launch_codebook_batch(const CodebookJob* J, int nj, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_codebook_batch,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kCodebookSmem);
+    attr = true;
+  }
+  if (nj > 0) k_codebook_batch<<<nj, 1024, kCodebookSmem, s>>>(J);
+}
+
+void launch_enc_len_batch(const EncLenJob* J, const uint32_t* off, int nj,
+                          uint32_t nblk, cudaStream_t s) {
+  if (nblk) k_enc_len_batch<<<nblk, 256, 0, s>>>(J, off, nj);
+}
+
+void launch_pack_batch(const PackJob* J, const uint32_t* off, int nj,
+                       uint32_t nblk, cudaStream_t s) {
+  if (nblk) k_pack_batch<<<nblk, 256, 0, s>>>(J, off, nj);
+}
+
+void launch_chunk_words_batch(const ChunkWordsJob* J, const uint32_t* off,
+                              int nj, uint32_t nblk, cudaStream_t s) {
+  if (nblk) k_chunk_words_batch<<<nblk, 256, 0, s>>>(J, off, nj);
+}
+
+void launch_outliers_batch(const OutlierJob* J, const uint32_t* off, int nj,
+                           uint32_t nblk, cudaStream_t s) {
+  if (nblk) k_outliers_batch<<<nblk, 256, 0, s>>>(J, off, nj);
+}
+
+void launch_dec_tables_batch(const DecTablesJob* J, int nj, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_dec_tables_batch,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(kSmemLeaves * 8));
+    attr = true;
+  }
+  if (nj > 0) k_dec_tables_batch<<<nj, 1024, kSmemLeaves * 8, s>>>(J);
+}
+
+void launch_decode_batch(const DecodeJob* J, const uint32_t* off, int nj,
+                         uint32_t nblk, cudaStream_t s) {
+  if (nblk) k_decode_batch<<<nblk, 256, 0, s>>>(J, off, nj);
 }
 
 }  // namespace hpez

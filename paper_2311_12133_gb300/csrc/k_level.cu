@@ -309,10 +309,13 @@ __device__ __forceinline__ void run_step(const FusedLevel& P, const SweepBufs& B
 }
 
 template <bool kDecomp, int KIND>
-__global__ void __launch_bounds__(256)
-    k_level(FusedLevel P, SweepBufs B, const float* __restrict__ Rc,
-            const uint16_t* __restrict__ Cc, float* __restrict__ Rs,
-            uint16_t* __restrict__ Cs) {
+__device__ __forceinline__ void level_body(const FusedLevel& P,
+                                           const SweepBufs& B,
+                                           const float* __restrict__ Rc,
+                                           const uint16_t* __restrict__ Cc,
+                                           float* __restrict__ Rs,
+                                           uint16_t* __restrict__ Cs,
+                                           unsigned bid) {
   const Ctl* ctl = B.ctl;
   if (ctl->status || ctl->is_const) return;
   extern __shared__ float sm[];
@@ -322,7 +325,7 @@ __global__ void __launch_bounds__(256)
   const int nwarps = blockDim.x >> 5;
   Region R;
   {
-    uint32_t tb = blockIdx.x;
+    uint32_t tb = bid;
     const uint32_t t2 = tb % P.ntile[2];
     tb /= P.ntile[2];
     const uint32_t t1 = tb % P.ntile[1];
@@ -449,6 +452,24 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+template <bool kDecomp, int KIND>
+__global__ void __launch_bounds__(256)
+    k_level(FusedLevel P, SweepBufs B, const float* __restrict__ Rc,
+            const uint16_t* __restrict__ Cc, float* __restrict__ Rs,
+            uint16_t* __restrict__ Cs) {
+  level_body<kDecomp, KIND>(P, B, Rc, Cc, Rs, Cs, blockIdx.x);
+}
+
+// batched: job j owns tiles [off[j], off[j+1]) of the launch
+template <bool kDecomp, int KIND>
+__global__ void __launch_bounds__(256)
+    k_level_batch(const LevelJob* __restrict__ J, const uint32_t* __restrict__ off,
+                  int nj) {
+  const int j = batch_job(off, nj);
+  const LevelJob& q = J[j];
+  level_body<kDecomp, KIND>(q.P, q.B, q.Rc, q.Cc, q.Rs, q.Cs, blockIdx.x - off[j]);
+}
+
 size_t fused_smem_bytes(const FusedLevel& P, bool decomp) {
   size_t b = (size_t)P.RX[0] * P.RX[1] * P.RX[2] * sizeof(float);
   if (decomp && P.stage_x) b += (size_t)P.RX[0] * P.RX[1] * P.RX[2] * sizeof(uint16_t);
@@ -492,5 +513,42 @@ void launch_level(bool decomp, const FusedLevel& P, const SweepBufs& B,
   else
     launch_dec<false>(P, B, smem, Rc, Cc, Rs, Cs, s);
 }
+
+template <bool kDecomp, int KIND>
+static void launch_kind_b(const LevelJob* J, const uint32_t* off, int nj,
+                          uint32_t nblk, size_t smem, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_level_batch<kDecomp, KIND>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_level_batch<kDecomp, KIND><<<nblk, 256, smem, s>>>(J, off, nj);
+}
+
+// kind: the interpolator of every job, or 3 for the per-point path (block
+// map or same-level), the value level_kind() returns
+void launch_level_batch(bool decomp, int kind, const LevelJob* J,
+                        const uint32_t* off, int nj, uint32_t nblk, size_t smem,
+                        cudaStream_t s) {
+  if (!nblk) return;
+  if (decomp) {
+    switch (kind) {
+      case LINEAR: launch_kind_b<true, LINEAR>(J, off, nj, nblk, smem, s); break;
+      case CUBIC_NAK: launch_kind_b<true, CUBIC_NAK>(J, off, nj, nblk, smem, s); break;
+      case CUBIC_NAT: launch_kind_b<true, CUBIC_NAT>(J, off, nj, nblk, smem, s); break;
+      default: launch_kind_b<true, 3>(J, off, nj, nblk, smem, s); break;
+    }
+  } else {
+    switch (kind) {
+      case LINEAR: launch_kind_b<false, LINEAR>(J, off, nj, nblk, smem, s); break;
+      case CUBIC_NAK: launch_kind_b<false, CUBIC_NAK>(J, off, nj, nblk, smem, s); break;
+      case CUBIC_NAT: launch_kind_b<false, CUBIC_NAT>(J, off, nj, nblk, smem, s); break;
+      default: launch_kind_b<false, 3>(J, off, nj, nblk, smem, s); break;
+    }
+  }
+}
+
+int level_kind(const SweepBufs& B) { return (B.blockmap || B.same) ? 3 : B.kind; }
 
 }  // namespace hpez

@@ -82,12 +82,12 @@ __device__ __forceinline__ int edge_formula(bool hm3, bool hp1, bool hp3) {
 // works on 4 consecutive columns through float4 accesses (conflict-free),
 // and pass 3 writes whole rows of codes / reconstructions to global memory.
 template <bool kDecomp, int KIND>
-__global__ void __launch_bounds__(256)
-    k_level3d(Level3D P, const float* __restrict__ X,
-              const uint16_t* __restrict__ codes_full,
-              const float* __restrict__ outl_full, const float* __restrict__ Rc,
-              const uint16_t* __restrict__ Cc, float* __restrict__ Rs,
-              uint16_t* __restrict__ Cs, const Ctl* __restrict__ ctl) {
+__device__ __forceinline__ void level3d_body(
+    const Level3D& P, const float* __restrict__ X,
+    const uint16_t* __restrict__ codes_full, const float* __restrict__ outl_full,
+    const float* __restrict__ Rc, const uint16_t* __restrict__ Cc,
+    float* __restrict__ Rs, uint16_t* __restrict__ Cs,
+    const Ctl* __restrict__ ctl, unsigned bid) {
   if (ctl->status || ctl->is_const) return;
   extern __shared__ float4 sm4[];
   float* sm = reinterpret_cast<float*>(sm4);
@@ -96,8 +96,8 @@ __global__ void __launch_bounds__(256)
   const int m0 = P.m[0], m1 = P.m[1], m2 = P.m[2];
   const int RR = P.E1 + 6;
   const int W = P.W, W4 = W >> 2;
-  const int t1 = blockIdx.x % P.nt1;
-  const int t0 = blockIdx.x / P.nt1;
+  const int t1 = (int)(bid % (unsigned)P.nt1);
+  const int t0 = (int)(bid / (unsigned)P.nt1);
   const int P0 = 2 * t0;
   const bool odd_plane = P0 + 1 < m0;
   const int R0 = t1 * P.E1;
@@ -327,6 +327,29 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+template <bool kDecomp, int KIND>
+__global__ void __launch_bounds__(256)
+    k_level3d(Level3D P, const float* __restrict__ X,
+              const uint16_t* __restrict__ codes_full,
+              const float* __restrict__ outl_full, const float* __restrict__ Rc,
+              const uint16_t* __restrict__ Cc, float* __restrict__ Rs,
+              uint16_t* __restrict__ Cs, const Ctl* __restrict__ ctl) {
+  level3d_body<kDecomp, KIND>(P, X, codes_full, outl_full, Rc, Cc, Rs, Cs, ctl,
+                              blockIdx.x);
+}
+
+// batched: job j owns tiles [off[j], off[j+1]) of the launch
+template <bool kDecomp, int KIND>
+__global__ void __launch_bounds__(256)
+    k_level3d_batch(const Level3DJob* __restrict__ J,
+                    const uint32_t* __restrict__ off, int nj) {
+  const int j = batch_job(off, nj);
+  const Level3DJob& q = J[j];
+  const Level3D P = q.P;
+  level3d_body<kDecomp, KIND>(P, q.X, q.codes_full, q.outl_full, q.Rc, q.Cc,
+                              q.Rs, q.Cs, q.ctl, blockIdx.x - off[j]);
+}
+
 size_t level3d_smem_bytes(const Level3D& P, bool decomp) {
   size_t b = 2ull * (P.E1 + 6) * P.W * sizeof(float);
   if (decomp && P.stage_codes) b += 2ull * (P.E1 + 6) * P.W * sizeof(uint16_t);
@@ -359,6 +382,33 @@ void launch_level3d(bool decomp, const Level3D& P, const SweepBufs& B,
     if (B.kind == LINEAR) launch3<false, LINEAR>(P, B, Rc, Cc, Rs, Cs, s);
     else if (B.kind == CUBIC_NAK) launch3<false, CUBIC_NAK>(P, B, Rc, Cc, Rs, Cs, s);
     else launch3<false, CUBIC_NAT>(P, B, Rc, Cc, Rs, Cs, s);
+  }
+}
+
+template <bool kDecomp, int KIND>
+static void launch3b(const Level3DJob* J, const uint32_t* off, int nj,
+                     uint32_t nblk, size_t smem, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_level3d_batch<kDecomp, KIND>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_level3d_batch<kDecomp, KIND><<<nblk, 256, smem, s>>>(J, off, nj);
+}
+
+void launch_level3d_batch(bool decomp, int kind, const Level3DJob* J,
+                          const uint32_t* off, int nj, uint32_t nblk,
+                          size_t smem, cudaStream_t s) {
+  if (!nblk) return;
+  if (decomp) {
+    if (kind == LINEAR) launch3b<true, LINEAR>(J, off, nj, nblk, smem, s);
+    else if (kind == CUBIC_NAK) launch3b<true, CUBIC_NAK>(J, off, nj, nblk, smem, s);
+    else launch3b<true, CUBIC_NAT>(J, off, nj, nblk, smem, s);
+  } else {
+    if (kind == LINEAR) launch3b<false, LINEAR>(J, off, nj, nblk, smem, s);
+    else if (kind == CUBIC_NAK) launch3b<false, CUBIC_NAK>(J, off, nj, nblk, smem, s);
+    else launch3b<false, CUBIC_NAT>(J, off, nj, nblk, smem, s);
   }
 }
 

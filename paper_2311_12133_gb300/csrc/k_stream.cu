@@ -13,9 +13,10 @@ namespace hpez {
 
 // exclusive scan of n u32 values into u64, single CTA of 1024 threads;
 // *total receives the sum
-__global__ void __launch_bounds__(1024)
-    k_scan(const uint32_t* __restrict__ in, unsigned long long* __restrict__ out,
-           uint32_t n, unsigned long long* total, const Ctl* __restrict__ ctl) {
+__device__ __forceinline__ void scan_body(const uint32_t* __restrict__ in,
+                                          unsigned long long* __restrict__ out,
+                                          uint32_t n, unsigned long long* total,
+                                          const Ctl* __restrict__ ctl) {
   if (ctl->status || ctl->is_const) return;
   __shared__ unsigned long long warp_sums[32];
   __shared__ unsigned long long carry;
@@ -60,13 +61,20 @@ __global__ void __launch_bounds__(1024)
   if (tid == 0) *total = carry;
 }
 
+__global__ void __launch_bounds__(1024)
+    k_scan(const uint32_t* __restrict__ in, unsigned long long* __restrict__ out,
+           uint32_t n, unsigned long long* total, const Ctl* __restrict__ ctl) {
+  scan_body(in, out, n, total, ctl);
+}
+
 __host__ __device__ inline unsigned long long align16(unsigned long long v) {
   return (v + 15ull) & ~15ull;
 }
 
 // dynamic section offsets + capacity check
-__global__ void k_layout(Ctl* ctl, unsigned long long off_table,
-                         unsigned long long cap) {
+__device__ __forceinline__ void layout_body(Ctl* ctl,
+                                            unsigned long long off_table,
+                                            unsigned long long cap) {
   if (threadIdx.x != 0 || ctl->status) return;
   if (ctl->is_const) {
     ctl->total_size = kHeaderBytes;
@@ -78,6 +86,11 @@ __global__ void k_layout(Ctl* ctl, unsigned long long off_table,
   ctl->off_bits = align16(ctl->off_outliers + 4ull * ctl->n_out);
   ctl->total_size = ctl->off_bits + 4ull * ctl->total_words;
   if (ctl->total_size > cap) ctl->status = ST_OUT_TOO_SMALL;
+}
+
+__global__ void k_layout(Ctl* ctl, unsigned long long off_table,
+                         unsigned long long cap) {
+  layout_body(ctl, off_table, cap);
 }
 
 struct HeaderImage {
@@ -101,23 +114,20 @@ constexpr int kHE = 56, kHConst = 60, kHNOut = 224, kHNUsed = 232,
 
 // Writes the header and the static-size sections; pads every section end
 // with zeros up to the next 16-byte boundary.
-__global__ void k_finalize(HeaderImage hdr, HeaderImage hdr_const,
-                           uint8_t* __restrict__ out,
-                           const float* __restrict__ RA, uint32_t na,
-                           unsigned long long off_anchors,
-                           const uint8_t* __restrict__ bmap, uint32_t nblocks,
-                           unsigned long long off_bmap,
-                           const uint16_t* __restrict__ lanebits,
-                           uint32_t nch, unsigned long long off_chw,
-                           const uint16_t* __restrict__ tsyms,
-                           const uint8_t* __restrict__ tlens,
-                           const Ctl* __restrict__ ctl) {
+__device__ __forceinline__ void finalize_body(
+    const uint8_t* hdr, const uint8_t* hdr_const, uint8_t* __restrict__ out,
+    const float* __restrict__ RA, uint32_t na, unsigned long long off_anchors,
+    const uint8_t* __restrict__ bmap, uint32_t nblocks,
+    unsigned long long off_bmap, const uint16_t* __restrict__ lanebits,
+    uint32_t nch, unsigned long long off_chw, const uint16_t* __restrict__ tsyms,
+    const uint8_t* __restrict__ tlens, const Ctl* __restrict__ ctl,
+    unsigned bid, unsigned nblk) {
   if (ctl->status) return;
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t nthr = gridDim.x * blockDim.x;
+  const uint32_t tid = bid * blockDim.x + threadIdx.x;
+  const uint32_t nthr = nblk * blockDim.x;
   if (ctl->is_const) {
     for (uint32_t i = tid; i < (uint32_t)kHeaderBytes; i += nthr) {
-      uint8_t v = hdr_const.b[i];
+      uint8_t v = hdr_const[i];
       if (i >= kHConst && i < kHConst + 4)
         v = (uint8_t)(__float_as_uint(ctl->const_value) >> (8 * (i - kHConst)));
       out[i] = v;
@@ -126,7 +136,7 @@ __global__ void k_finalize(HeaderImage hdr, HeaderImage hdr_const,
   }
   if (tid == 0) {
     uint8_t h[kHeaderBytes];
-    for (int i = 0; i < kHeaderBytes; ++i) h[i] = hdr.b[i];
+    for (int i = 0; i < kHeaderBytes; ++i) h[i] = hdr[i];
     put_u32(h + kHE, __float_as_uint(ctl->e));
     put_u64(h + kHNOut, ctl->n_out);
     put_u32(h + kHNUsed, ctl->n_used);
@@ -168,6 +178,61 @@ __global__ void k_finalize(HeaderImage hdr, HeaderImage hdr_const,
   }
 }
 
+__global__ void k_finalize(HeaderImage hdr, HeaderImage hdr_const,
+                           uint8_t* __restrict__ out,
+                           const float* __restrict__ RA, uint32_t na,
+                           unsigned long long off_anchors,
+                           const uint8_t* __restrict__ bmap, uint32_t nblocks,
+                           unsigned long long off_bmap,
+                           const uint16_t* __restrict__ lanebits,
+                           uint32_t nch, unsigned long long off_chw,
+                           const uint16_t* __restrict__ tsyms,
+                           const uint8_t* __restrict__ tlens,
+                           const Ctl* __restrict__ ctl) {
+  finalize_body(hdr.b, hdr_const.b, out, RA, na, off_anchors, bmap, nblocks,
+                off_bmap, lanebits, nch, off_chw, tsyms, tlens, ctl, blockIdx.x,
+                gridDim.x);
+}
+
+// ---------------------------------------------------------------------
+// batched forms
+// ---------------------------------------------------------------------
+// Per request: the device status (its values equal the C-ABI error codes)
+// and, for compress, the stream size; decompress also checks that the
+// decoded word and outlier counts match the header.
+__global__ void k_result_batch(const ResultJob* __restrict__ J, int nj) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nj) return;
+  const ResultJob& q = J[j];
+  int st = q.ctl->status;
+  unsigned long long size = 0;
+  if (!q.decomp) {
+    size = st ? 0ull : q.ctl->total_size;
+  } else if (!st && q.tot && (q.tot[0] != q.twords || q.tot[1] != q.nout)) {
+    st = ST_CORRUPT;
+  }
+  if (q.size_out) *q.size_out = size;
+  if (q.status_out) *q.status_out = st;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_batch(const ScanJob* __restrict__ J) {
+  const ScanJob& q = J[blockIdx.x];
+  scan_body(q.in, q.out, q.n, q.total, q.ctl);
+}
+
+__global__ void k_layout_batch(const LayoutJob* __restrict__ J) {
+  layout_body(J[blockIdx.x].ctl, J[blockIdx.x].off_table, J[blockIdx.x].cap);
+}
+
+__global__ void k_finalize_batch(const FinalizeJob* __restrict__ J,
+                                 const uint32_t* __restrict__ off, int nj) {
+  const int j = batch_job(off, nj);
+  const FinalizeJob& q = J[j];
+  finalize_body(q.hdr, q.hdr_const, q.out, q.RA, q.na, q.off_anchors, q.bmap,
+                q.nblocks, q.off_bmap, q.lanebits, q.nch, q.off_chw, q.tsyms,
+                q.tlens, q.ctl, blockIdx.x - off[j], off[j + 1] - off[j]);
+}
+
 // ---------------------------------------------------------------------
 void launch_scan(const uint32_t* in, unsigned long long* out, uint32_t n,
                  unsigned long long* total, const Ctl* ctl, cudaStream_t s) {
@@ -200,6 +265,33 @@ void launch_finalize(const uint8_t* hdr, const uint8_t* hdr_const,
   k_finalize<<<grid, 256, 0, s>>>(h, hc, out, RA, na, off_anchors, bmap,
                                   nblocks, off_bmap, lanebits, nch, off_chw, tsyms,
                                   tlens, ctl);
+}
+
+void launch_result_batch(const ResultJob* J, int nj, cudaStream_t s) {
+  if (nj > 0) k_result_batch<<<(nj + 127) / 128, 128, 0, s>>>(J, nj);
+}
+
+void launch_scan_batch(const ScanJob* J, int nj, cudaStream_t s) {
+  if (nj > 0) k_scan_batch<<<nj, 1024, 0, s>>>(J);
+}
+
+void launch_layout_batch(const LayoutJob* J, int nj, cudaStream_t s) {
+  if (nj > 0) k_layout_batch<<<nj, 32, 0, s>>>(J);
+}
+
+void launch_finalize_batch(const FinalizeJob* J, const uint32_t* off, int nj,
+                           uint32_t nblk, cudaStream_t s) {
+  if (nblk) k_finalize_batch<<<nblk, 256, 0, s>>>(J, off, nj);
+}
+
+// blocks the single-field finalize would use
+uint32_t finalize_blocks(uint32_t na, uint32_t nch, int num_sms) {
+  uint64_t work = na;
+  if (16ull * nch > work) work = 16ull * nch;
+  unsigned grid = (unsigned)((work + 255) / 256);
+  if (grid < 1) grid = 1;
+  if (grid > (unsigned)num_sms * 4) grid = num_sms * 4;
+  return grid;
 }
 
 }  // namespace hpez

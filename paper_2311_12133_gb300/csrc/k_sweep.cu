@@ -16,7 +16,7 @@ namespace hpez {
 // ---------------------------------------------------------------------
 // control block init + value range (Sec. 7.1.3: e = eps * (max - min))
 // ---------------------------------------------------------------------
-__global__ void k_init_ctl(Ctl* ctl) {
+__device__ __forceinline__ void init_ctl_body(Ctl* ctl) {
   unsigned* p = reinterpret_cast<unsigned*>(ctl);
   for (int i = threadIdx.x; i < (int)(sizeof(Ctl) / 4); i += blockDim.x)
     p[i] = 0u;
@@ -27,12 +27,15 @@ __global__ void k_init_ctl(Ctl* ctl) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_range(const float* __restrict__ x,
-                                               uint32_t N, Ctl* ctl) {
+__global__ void k_init_ctl(Ctl* ctl) { init_ctl_body(ctl); }
+
+__device__ __forceinline__ void range_body(const float* __restrict__ x,
+                                           uint32_t N, Ctl* ctl, unsigned bid,
+                                           unsigned nblk) {
   float mn = FLT_MAX, mx = -FLT_MAX;
   int bad = 0;
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t nthr = gridDim.x * blockDim.x;
+  const uint32_t tid = bid * blockDim.x + threadIdx.x;
+  const uint32_t nthr = nblk * blockDim.x;
   const bool vec = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
   uint32_t done = 0;
   if (vec) {
@@ -84,12 +87,18 @@ __global__ void __launch_bounds__(256) k_range(const float* __restrict__ x,
   }
 }
 
+__global__ void __launch_bounds__(256) k_range(const float* __restrict__ x,
+                                               uint32_t N, Ctl* ctl) {
+  range_body(x, N, ctl, blockIdx.x, gridDim.x);
+}
+
 // Level parameters in IEEE double, one rounding to binary32 each (Eq. 15):
 // e_l = e / min(alpha^(l-1), beta), alpha^(l-1) by repeated multiplication;
 // inv2_l = 1 / (2 e_l); twoe_l = 2 e_l.
-__global__ void k_params(Ctl* ctl, int eb_mode, double eb, double alpha,
-                         double beta, int L, const float* __restrict__ x) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ __forceinline__ void params_body(Ctl* ctl, int eb_mode, double eb,
+                                            double alpha, double beta, int L,
+                                            const float* __restrict__ x) {
+  if (threadIdx.x != 0) return;
   float e;
   if (eb_mode == 1) {
     if (ctl->nonfinite) {
@@ -128,16 +137,24 @@ __global__ void k_params(Ctl* ctl, int eb_mode, double eb, double alpha,
   }
 }
 
+__global__ void k_params(Ctl* ctl, int eb_mode, double eb, double alpha,
+                         double beta, int L, const float* __restrict__ x) {
+  if (blockIdx.x != 0) return;
+  params_body(ctl, eb_mode, eb, alpha, beta, L, x);
+}
+
 // ---------------------------------------------------------------------
 // anchors: G_A <- x (compress) ; G_A <- stored anchors (decompress)
 // ---------------------------------------------------------------------
-__global__ void k_anchor_gather(const float* __restrict__ x, LevelGeom ga,
-                                uint32_t total, float* __restrict__ RA,
-                                uint16_t* __restrict__ CA,
-                                const Ctl* __restrict__ ctl) {
+__device__ __forceinline__ void anchor_body(const float* __restrict__ x,
+                                            const LevelGeom& ga, uint32_t total,
+                                            float* __restrict__ RA,
+                                            uint16_t* __restrict__ CA,
+                                            const Ctl* __restrict__ ctl,
+                                            unsigned bid, unsigned nblk) {
   if (ctl->status || ctl->is_const) return;
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += gridDim.x * blockDim.x) {
+  for (uint32_t t = bid * blockDim.x + threadIdx.x; t < total;
+       t += nblk * blockDim.x) {
     const uint32_t u2 = t % ga.m[2];
     const uint32_t r = t / ga.m[2];
     const uint32_t u1 = r % ga.m[1];
@@ -149,15 +166,22 @@ __global__ void k_anchor_gather(const float* __restrict__ x, LevelGeom ga,
   }
 }
 
+__global__ void k_anchor_gather(const float* __restrict__ x, LevelGeom ga,
+                                uint32_t total, float* __restrict__ RA,
+                                uint16_t* __restrict__ CA,
+                                const Ctl* __restrict__ ctl) {
+  anchor_body(x, ga, total, RA, CA, ctl, blockIdx.x, gridDim.x);
+}
+
 // G_2s -> G_s: coarse points keep their reconstruction (and code).
-__global__ void k_upsample(LevelGeom gc, uint32_t total_c, LevelGeom gs,
-                           const float* __restrict__ Rc,
-                           const uint16_t* __restrict__ Cc,
-                           float* __restrict__ Rs, uint16_t* __restrict__ Cs,
-                           const Ctl* __restrict__ ctl) {
+__device__ __forceinline__ void upsample_body(
+    const LevelGeom& gc, uint32_t total_c, const LevelGeom& gs,
+    const float* __restrict__ Rc, const uint16_t* __restrict__ Cc,
+    float* __restrict__ Rs, uint16_t* __restrict__ Cs,
+    const Ctl* __restrict__ ctl, unsigned bid, unsigned nblk) {
   if (ctl->status || ctl->is_const) return;
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total_c;
-       t += gridDim.x * blockDim.x) {
+  for (uint32_t t = bid * blockDim.x + threadIdx.x; t < total_c;
+       t += nblk * blockDim.x) {
     const uint32_t v2 = t % gc.m[2];
     const uint32_t r = t / gc.m[2];
     const uint32_t v1 = r % gc.m[1];
@@ -171,18 +195,27 @@ __global__ void k_upsample(LevelGeom gc, uint32_t total_c, LevelGeom gs,
   }
 }
 
+__global__ void k_upsample(LevelGeom gc, uint32_t total_c, LevelGeom gs,
+                           const float* __restrict__ Rc,
+                           const uint16_t* __restrict__ Cc,
+                           float* __restrict__ Rs, uint16_t* __restrict__ Cs,
+                           const Ctl* __restrict__ ctl) {
+  upsample_body(gc, total_c, gs, Rc, Cc, Rs, Cs, ctl, blockIdx.x, gridDim.x);
+}
+
 // ---------------------------------------------------------------------
 // the predict-and-quantize pass (one launch per (pass, half))
 // ---------------------------------------------------------------------
 template <bool kDecomp>
-__global__ void __launch_bounds__(256)
-    k_pass(LevelGeom g, PassBox pb, SweepBufs B) {
+__device__ __forceinline__ void pass_body(const LevelGeom& g, const PassBox& pb,
+                                          const SweepBufs& B, unsigned bid,
+                                          unsigned nblk) {
   const Ctl* ctl = B.ctl;
   if (ctl->status || ctl->is_const) return;
   const int li = pb.level - 1;
   const float el = ctl->el[li], inv2 = ctl->inv2[li], twoe = ctl->twoe[li];
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < pb.total;
-       t += gridDim.x * blockDim.x) {
+  for (uint32_t t = bid * blockDim.x + threadIdx.x; t < pb.total;
+       t += nblk * blockDim.x) {
     const uint32_t t2 = t % pb.cnt[2];
     const uint32_t r = t / pb.cnt[2];
     const uint32_t t1 = r % pb.cnt[1];
@@ -242,10 +275,82 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-__global__ void k_fill(float* __restrict__ out, uint32_t N, float v) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N;
-       i += gridDim.x * blockDim.x)
+template <bool kDecomp>
+__global__ void __launch_bounds__(256)
+    k_pass(LevelGeom g, PassBox pb, SweepBufs B) {
+  pass_body<kDecomp>(g, pb, B, blockIdx.x, gridDim.x);
+}
+
+__device__ __forceinline__ void fill_body(float* __restrict__ out, uint32_t N,
+                                          float v, unsigned bid, unsigned nblk) {
+  for (uint32_t i = bid * blockDim.x + threadIdx.x; i < N; i += nblk * blockDim.x)
     out[i] = v;
+}
+
+__global__ void k_fill(float* __restrict__ out, uint32_t N, float v) {
+  fill_body(out, N, v, blockIdx.x, gridDim.x);
+}
+
+// ---------------------------------------------------------------------
+// batched forms: one launch over the concatenated work of many fields
+// ---------------------------------------------------------------------
+__global__ void k_init_ctl_batch(const InitJob* __restrict__ J) {
+  init_ctl_body(J[blockIdx.x].ctl);
+}
+
+__global__ void __launch_bounds__(256)
+    k_range_batch(const RangeJob* __restrict__ J, const uint32_t* __restrict__ off,
+                  int nj) {
+  const int j = batch_job(off, nj);
+  range_body(J[j].x, J[j].N, J[j].ctl, blockIdx.x - off[j], off[j + 1] - off[j]);
+}
+
+__global__ void k_params_batch(const ParamsJob* __restrict__ J) {
+  const ParamsJob& q = J[blockIdx.x];
+  params_body(q.ctl, q.eb_mode, q.eb, q.alpha, q.beta, q.L, q.x);
+}
+
+__global__ void k_anchor_batch(const AnchorJob* __restrict__ J,
+                               const uint32_t* __restrict__ off, int nj) {
+  const int j = batch_job(off, nj);
+  const AnchorJob& q = J[j];
+  anchor_body(q.x, q.ga, q.total, q.RA, q.CA, q.ctl, blockIdx.x - off[j],
+              off[j + 1] - off[j]);
+}
+
+__global__ void k_upsample_batch(const UpsampleJob* __restrict__ J,
+                                 const uint32_t* __restrict__ off, int nj) {
+  const int j = batch_job(off, nj);
+  const UpsampleJob& q = J[j];
+  upsample_body(q.gc, q.total_c, q.gs, q.Rc, q.Cc, q.Rs, q.Cs, q.ctl,
+                blockIdx.x - off[j], off[j + 1] - off[j]);
+}
+
+template <bool kDecomp>
+__global__ void __launch_bounds__(256)
+    k_pass_batch(const PassJob* __restrict__ J, const uint32_t* __restrict__ off,
+                 int nj) {
+  const int j = batch_job(off, nj);
+  const PassJob& q = J[j];
+  pass_body<kDecomp>(q.g, q.pb, q.B, blockIdx.x - off[j], off[j + 1] - off[j]);
+}
+
+// zero-fill of byte ranges (16-byte multiples, 16-byte aligned)
+__global__ void k_zero_batch(const ZeroJob* __restrict__ J,
+                             const uint32_t* __restrict__ off, int nj) {
+  const int j = batch_job(off, nj);
+  uint4* p = reinterpret_cast<uint4*>(J[j].ptr);
+  const unsigned long long n = J[j].bytes >> 4;
+  const unsigned b = blockIdx.x - off[j], nb = off[j + 1] - off[j];
+  for (unsigned long long i = (unsigned long long)b * blockDim.x + threadIdx.x;
+       i < n; i += (unsigned long long)nb * blockDim.x)
+    p[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+__global__ void k_fill_batch(const FillJob* __restrict__ J,
+                             const uint32_t* __restrict__ off, int nj) {
+  const int j = batch_job(off, nj);
+  fill_body(J[j].out, J[j].N, J[j].v, blockIdx.x - off[j], off[j + 1] - off[j]);
 }
 
 // ---------------------------------------------------------------------
@@ -299,6 +404,46 @@ void launch_pass(bool decomp, const LevelGeom& g, const PassBox& pb,
     k_pass<true><<<grid, 256, 0, s>>>(g, pb, B);
   else
     k_pass<false><<<grid, 256, 0, s>>>(g, pb, B);
+}
+
+void launch_init_ctl_batch(const InitJob* J, int nj, cudaStream_t s) {
+  if (nj > 0) k_init_ctl_batch<<<nj, 256, 0, s>>>(J);
+}
+void launch_range_batch(const RangeJob* J, const uint32_t* off, int nj,
+                        uint32_t nblk, cudaStream_t s) {
+  if (nblk) k_range_batch<<<nblk, 256, 0, s>>>(J, off, nj);
+}
+void launch_params_batch(const ParamsJob* J, int nj, cudaStream_t s) {
+  if (nj > 0) k_params_batch<<<nj, 32, 0, s>>>(J);
+}
+void launch_anchor_batch(const AnchorJob* J, const uint32_t* off, int nj,
+                         uint32_t nblk, cudaStream_t s) {
+  if (nblk) k_anchor_batch<<<nblk, 256, 0, s>>>(J, off, nj);
+}
+void launch_fill_batch(const FillJob* J, const uint32_t* off, int nj,
+                       uint32_t nblk, cudaStream_t s) {
+  if (nblk) k_fill_batch<<<nblk, 256, 0, s>>>(J, off, nj);
+}
+
+void launch_upsample_batch(const UpsampleJob* J, const uint32_t* off, int nj,
+                           uint32_t nblk, cudaStream_t s) {
+  if (nblk) k_upsample_batch<<<nblk, 256, 0, s>>>(J, off, nj);
+}
+void launch_pass_batch(bool decomp, const PassJob* J, const uint32_t* off,
+                       int nj, uint32_t nblk, cudaStream_t s) {
+  if (!nblk) return;
+  if (decomp)
+    k_pass_batch<true><<<nblk, 256, 0, s>>>(J, off, nj);
+  else
+    k_pass_batch<false><<<nblk, 256, 0, s>>>(J, off, nj);
+}
+void launch_zero_batch(const ZeroJob* J, const uint32_t* off, int nj,
+                       uint32_t nblk, cudaStream_t s) {
+  if (nblk) k_zero_batch<<<nblk, 256, 0, s>>>(J, off, nj);
+}
+uint32_t grid_blocks(uint64_t n, unsigned cap) { return grid_for(n, 256, cap); }
+uint32_t pass_blocks(uint32_t total, int num_sms) {
+  return grid_for(total, 256, (unsigned)num_sms * 16);
 }
 
 }  // namespace hpez

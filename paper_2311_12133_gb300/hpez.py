@@ -84,6 +84,47 @@ class hpez_tune_report(ctypes.Structure):
     ]
 
 
+class hpez_field_desc(ctypes.Structure):
+    _fields_ = [
+        ("d_in", ctypes.c_void_p),
+        ("ndim", ctypes.c_int32),
+        ("eb_mode", ctypes.c_int32),
+        ("dims", ctypes.c_uint64 * 3),
+        ("eb", ctypes.c_double),
+        ("cfg", ctypes.POINTER(hpez_config)),
+        ("d_out", ctypes.c_void_p),
+        ("out_cap", ctypes.c_uint64),
+    ]
+
+
+class hpez_stream_desc(ctypes.Structure):
+    _fields_ = [
+        ("d_in", ctypes.c_void_p),
+        ("in_size", ctypes.c_uint64),
+        ("h_header", ctypes.c_void_p),
+        ("d_out", ctypes.c_void_p),
+        ("out_cap_elems", ctypes.c_uint64),
+    ]
+
+
+class hpez_request(ctypes.Structure):
+    _fields_ = [
+        ("op", ctypes.c_int32),
+        ("ndim", ctypes.c_int32),
+        ("dims", ctypes.c_uint64 * 3),
+        ("eb_mode", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("eb", ctypes.c_double),
+        ("cfg", ctypes.POINTER(hpez_config)),
+        ("h_in", ctypes.c_void_p),
+        ("in_bytes", ctypes.c_uint64),
+        ("h_out", ctypes.c_void_p),
+        ("out_cap", ctypes.c_uint64),
+    ]
+
+
+HPEZ_REQ_COMPRESS, HPEZ_REQ_DECOMPRESS = 0, 1
+
 _lock = threading.Lock()
 _lib = None
 
@@ -136,6 +177,30 @@ def _load():
                                          ctypes.POINTER(hpez_tune_params), cfgp,
                                          vp, u64, ctypes.POINTER(hpez_tune_report),
                                          vp]),
+            "hpez_batch_create_compress": (ctypes.c_int, [vp, ctypes.c_int,
+                                                          ctypes.POINTER(hpez_field_desc),
+                                                          ctypes.POINTER(vp)]),
+            "hpez_batch_create_decompress": (ctypes.c_int, [vp, ctypes.c_int,
+                                                            ctypes.POINTER(hpez_stream_desc),
+                                                            ctypes.POINTER(vp)]),
+            "hpez_batch_run": (ctypes.c_int, [vp, vp]),
+            "hpez_batch_run_graph": (ctypes.c_int, [vp, vp]),
+            "hpez_batch_results": (ctypes.c_int, [vp, vp, u64p,
+                                                  ctypes.POINTER(ctypes.c_int32)]),
+            "hpez_batch_launch_count": (ctypes.c_int, [vp, u64p, u64p]),
+            "hpez_batch_destroy": (ctypes.c_int, [vp]),
+            "hpez_server_create": (ctypes.c_int, [vp, u64, ctypes.c_int, vp,
+                                                  ctypes.POINTER(vp)]),
+            "hpez_server_submit": (ctypes.c_int, [vp, ctypes.POINTER(hpez_request), u64p]),
+            "hpez_server_step": (ctypes.c_int, [vp]),
+            "hpez_server_poll": (ctypes.c_int, [vp, ctypes.c_int, u64p,
+                                                ctypes.POINTER(ctypes.c_int32), u64p,
+                                                ctypes.POINTER(ctypes.c_double),
+                                                ctypes.POINTER(ctypes.c_int)]),
+            "hpez_server_stats": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int),
+                                                 ctypes.POINTER(ctypes.c_int), u64p,
+                                                 u64p, u64p]),
+            "hpez_server_destroy": (ctypes.c_int, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -153,7 +218,11 @@ def exported_symbols() -> list[str]:
             "hpez_strerror", "hpez_profile_enable", "hpez_profile_get",
             "hpez_profile_phase_name", "hpez_launch_count", "hpez_set_option",
             "hpez_decompress_noalloc", "hpez_default_tune_params",
-            "hpez_blockmap_size", "hpez_tune"]
+            "hpez_blockmap_size", "hpez_tune", "hpez_batch_create_compress",
+            "hpez_batch_create_decompress", "hpez_batch_run", "hpez_batch_run_graph",
+            "hpez_batch_results", "hpez_batch_launch_count", "hpez_batch_destroy",
+            "hpez_server_create", "hpez_server_submit", "hpez_server_step",
+            "hpez_server_poll", "hpez_server_stats", "hpez_server_destroy"]
 
 
 def _check(rc: int, what: str):
@@ -431,3 +500,196 @@ class Context:
         hpez_decompress(self.handle, stream_buf.data_ptr(), size, out.data_ptr(), n,
                         self._stream(stream))
         return out
+
+
+# --------------------------------------------------------------------------
+# batched and served forms
+# --------------------------------------------------------------------------
+def _cfg_ptr(cfg):
+    return ctypes.pointer(cfg) if cfg is not None else None
+
+
+class Batch:
+    """A batch of compress (or decompress) requests bound to device buffers.
+
+    compress: ``fields`` = list of (x tensor, eb, eb_mode, config or None);
+    output buffers are allocated here (compress bound each).
+    decompress: ``streams`` = list of (uint8 tensor, size, header bytes)."""
+
+    def __init__(self, ctx: Context, fields=None, streams=None):
+        import torch
+        self.ctx = ctx
+        self._keep = []
+        h = ctypes.c_void_p(0)
+        if fields is not None:
+            n = len(fields)
+            descs = (hpez_field_desc * n)()
+            self.outs = []
+            for i, (x, eb, mode, cfg) in enumerate(fields):
+                assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+                cap = hpez_compress_bound(tuple(x.shape))
+                out = torch.empty(cap, dtype=torch.uint8, device=x.device)
+                self.outs.append(out)
+                d = descs[i]
+                d.d_in = x.data_ptr()
+                d.ndim = x.dim()
+                d.eb_mode = mode
+                for k in range(3):
+                    d.dims[k] = int(x.shape[k]) if k < x.dim() else 1
+                d.eb = float(eb)
+                if cfg is not None:
+                    self._keep.append(cfg)
+                    d.cfg = ctypes.pointer(cfg)
+                d.d_out = out.data_ptr()
+                d.out_cap = cap
+            self._keep.append(descs)
+            _check(_load().hpez_batch_create_compress(ctx.handle, n, descs, ctypes.byref(h)),
+                   "hpez_batch_create_compress")
+            self.decomp = False
+        else:
+            n = len(streams)
+            descs = (hpez_stream_desc * n)()
+            self.outs = []
+            for i, (buf, size, header) in enumerate(streams):
+                _, shape, _ = hpez_inspect(header)
+                out = torch.empty(shape, dtype=torch.float32, device=buf.device)
+                self.outs.append(out)
+                hb = np.frombuffer(header[:HPEZ_HEADER_BYTES], dtype=np.uint8).copy()
+                self._keep.append(hb)
+                d = descs[i]
+                d.d_in = buf.data_ptr()
+                d.in_size = size
+                d.h_header = hb.ctypes.data
+                d.d_out = out.data_ptr()
+                d.out_cap_elems = out.numel()
+            self._keep.append(descs)
+            _check(_load().hpez_batch_create_decompress(ctx.handle, n, descs, ctypes.byref(h)),
+                   "hpez_batch_create_decompress")
+            self.decomp = True
+        self.n = n
+        self.handle = h.value
+
+    def run(self, stream=None, graph=False):
+        s = Context._stream(stream)
+        if graph:
+            _check(_load().hpez_batch_run_graph(self.handle, s), "hpez_batch_run_graph")
+        else:
+            _check(_load().hpez_batch_run(self.handle, s), "hpez_batch_run")
+
+    def results(self, stream=None):
+        sizes = (ctypes.c_uint64 * self.n)()
+        status = (ctypes.c_int32 * self.n)()
+        _check(_load().hpez_batch_results(self.handle, Context._stream(stream), sizes, status),
+               "hpez_batch_results")
+        return list(sizes), list(status)
+
+    def launch_count(self):
+        a, b = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        _check(_load().hpez_batch_launch_count(self.handle, ctypes.byref(a), ctypes.byref(b)),
+               "hpez_batch_launch_count")
+        return a.value, b.value
+
+    def close(self):
+        if self.handle:
+            _load().hpez_batch_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """The served form: submit requests with host buffers, step, poll."""
+
+    def __init__(self, ctx: Context, budget_bytes: int, max_slots: int = 64,
+                 stream=None):
+        import torch
+        self.ctx = ctx
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        h = ctypes.c_void_p(0)
+        _check(_load().hpez_server_create(ctx.handle, int(budget_bytes), max_slots,
+                                          self.stream.cuda_stream, ctypes.byref(h)),
+               "hpez_server_create")
+        self.handle = h.value
+        self._keep = {}
+
+    def submit_compress(self, h_in: np.ndarray, eb: float, eb_mode=HPEZ_EB_REL,
+                        cfg=None, h_out=None):
+        """h_in: C-contiguous float32 (pinned memory for asynchronous copies).
+        Returns (id, output buffer)."""
+        assert h_in.dtype == np.float32 and h_in.flags.c_contiguous
+        if h_out is None:
+            h_out = np.empty(hpez_compress_bound(h_in.shape), dtype=np.uint8)
+        r = hpez_request()
+        r.op = HPEZ_REQ_COMPRESS
+        r.ndim = h_in.ndim
+        for k in range(3):
+            r.dims[k] = int(h_in.shape[k]) if k < h_in.ndim else 1
+        r.eb_mode = eb_mode
+        r.eb = float(eb)
+        if cfg is not None:
+            r.cfg = ctypes.pointer(cfg)
+        r.h_in = h_in.ctypes.data
+        r.h_out = h_out.ctypes.data
+        r.out_cap = h_out.nbytes
+        rid = ctypes.c_uint64(0)
+        _check(_load().hpez_server_submit(self.handle, ctypes.byref(r), ctypes.byref(rid)),
+               "hpez_server_submit")
+        self._keep[rid.value] = (h_in, h_out, cfg)
+        return rid.value, h_out
+
+    def submit_decompress(self, h_stream: np.ndarray, size: int, h_out=None):
+        _, shape, _ = hpez_inspect(h_stream[:HPEZ_HEADER_BYTES].tobytes())
+        if h_out is None:
+            h_out = np.empty(shape, dtype=np.float32)
+        r = hpez_request()
+        r.op = HPEZ_REQ_DECOMPRESS
+        r.h_in = h_stream.ctypes.data
+        r.in_bytes = int(size)
+        r.h_out = h_out.ctypes.data
+        r.out_cap = h_out.nbytes
+        rid = ctypes.c_uint64(0)
+        _check(_load().hpez_server_submit(self.handle, ctypes.byref(r), ctypes.byref(rid)),
+               "hpez_server_submit")
+        self._keep[rid.value] = (h_stream, h_out, None)
+        return rid.value, h_out
+
+    def step(self):
+        _check(_load().hpez_server_step(self.handle), "hpez_server_step")
+
+    def poll(self, cap: int = 256):
+        ids = (ctypes.c_uint64 * cap)()
+        st = (ctypes.c_int32 * cap)()
+        sz = (ctypes.c_uint64 * cap)()
+        lat = (ctypes.c_double * cap)()
+        n = ctypes.c_int(0)
+        _check(_load().hpez_server_poll(self.handle, cap, ids, st, sz, lat, ctypes.byref(n)),
+               "hpez_server_poll")
+        out = []
+        for i in range(n.value):
+            self._keep.pop(ids[i], None)
+            out.append((ids[i], st[i], sz[i], lat[i]))
+        return out
+
+    def stats(self):
+        a, q = ctypes.c_int(0), ctypes.c_int(0)
+        u, t, l = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+        _check(_load().hpez_server_stats(self.handle, ctypes.byref(a), ctypes.byref(q),
+                                         ctypes.byref(u), ctypes.byref(t), ctypes.byref(l)),
+               "hpez_server_stats")
+        return dict(active=a.value, queued=q.value, used_bytes=u.value, ticks=t.value,
+                    launches=l.value)
+
+    def close(self):
+        if self.handle:
+            _load().hpez_server_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

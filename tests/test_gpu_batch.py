@@ -1,0 +1,195 @@
+"""The batched and served forms against the single-field path and the
+oracle.
+
+Both forms run the single-field operations, only grouped into shared
+launches, so every stream must equal the one hpez_compress writes (and the
+oracle's), and every decompressed field the single-field result, byte for
+byte -- alone or in any mix.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_12133_gb300 import build as B
+    B.build()
+    from paper_2311_12133_gb300 import hpez
+    ctx = hpez.Context(0)
+    yield ctx
+    ctx.close()
+
+
+def _mix(seed=0):
+    """Fields of mixed dimension, shape, bound mode and configuration,
+    including the per-pass path (multi-dimensional paradigm), a block map,
+    a frozen dimension, 1D and a constant field."""
+    from paper_2311_12133_gb300 import fields, hpez
+    rng = np.random.default_rng(seed)
+    out = []
+    out.append((fields.make("bumps", (40, 36, 33), 1), 1e-3, 1, None))
+    out.append((fields.make("grf", (64, 64, 64), 2), 1e-2, 1, None))
+    out.append((fields.make("climate2d", (90, 130), 3), 1e-3, 1, None))
+    out.append((fields.make("grf", (17, 300), 4), 1e-4, 1, None))
+    out.append((fields.make("lognormal", (30, 41, 52), 5), 0.05, 0, None))
+    out.append((np.cumsum(rng.normal(0, 1, 3000)).astype(np.float32), 1e-3, 1, None))
+    out.append((fields.make("grf", (33, 40, 47), 6), 1e-3, 1,
+                dict(paradigm=1, interp=2)))
+    nb = hpez.hpez_blockmap_size((48, 50, 37), 16)
+    out.append((fields.make("bumps", (48, 50, 37), 7), 1e-3, 1,
+                dict(block_size=16, blockmap=rng.choice([0, 1, 2, 5, 6], nb))))
+    out.append((fields.make("grf", (36, 40, 44), 8), 1e-3, 1,
+                dict(frozen_dim=1, same_level=1)))
+    out.append((np.full((20, 30), 2.5, np.float32), 1e-3, 1, None))
+    out.append((fields.make("aniso", (10, 96, 96), 9), 1e-3, 1,
+                dict(interp=0, anchor_stride=16)))
+    return out
+
+
+def _cfgs(x, kw):
+    from oracle import oracle as O
+    from paper_2311_12133_gb300 import hpez
+    if kw is None:
+        return None, None
+    return hpez.make_config(x.ndim, **kw), O.make_config(x.ndim, **kw)
+
+
+def test_batch_compress_equals_single_and_oracle(gpu, oracle):
+    import torch
+    from paper_2311_12133_gb300 import hpez
+    mix = _mix()
+    xs, fields_arg, ocfgs = [], [], []
+    for x, eb, mode, kw in mix:
+        g, o = _cfgs(x, kw)
+        xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        xs.append(xd)
+        fields_arg.append((xd, eb, mode, g))
+        ocfgs.append(o)
+    b = hpez.Batch(gpu, fields=fields_arg)
+    b.run()
+    sizes, status = b.results()
+    assert status == [0] * len(mix)
+    launches, ticks = b.launch_count()
+    assert launches < 4 * ticks
+    streams = []
+    for i, (x, eb, mode, kw) in enumerate(mix):
+        got = b.outs[i][:sizes[i]].cpu().numpy().tobytes()
+        buf, size = gpu.compress(xs[i], eb, mode, fields_arg[i][3])
+        assert got == buf[:size].cpu().numpy().tobytes(), i
+        want, _, _, _ = oracle.compress(x, eb, mode, ocfgs[i])
+        assert got == want, i
+        streams.append(got)
+    # a second run and a graph replay give the same bytes
+    b.run(graph=True)
+    b.run(graph=True)
+    sizes2, status2 = b.results()
+    assert sizes2 == sizes and status2 == status
+    for i in range(len(mix)):
+        assert b.outs[i][:sizes[i]].cpu().numpy().tobytes() == streams[i]
+    b.close()
+
+    # batched decompress of the same streams
+    bufs = [torch.from_numpy(np.frombuffer(s_, np.uint8).copy()).cuda() for s_ in streams]
+    d = hpez.Batch(gpu, streams=[(bufs[i], len(streams[i]), streams[i][:512])
+                                 for i in range(len(streams))])
+    d.run(graph=True)
+    _, st = d.results()
+    assert st == [0] * len(streams)
+    for i in range(len(streams)):
+        y = gpu.decompress(bufs[i], len(streams[i])).cpu().numpy()
+        assert d.outs[i].cpu().numpy().tobytes() == y.tobytes(), i
+        assert y.tobytes() == oracle.decompress(streams[i]).tobytes(), i
+    d.close()
+
+
+def test_batch_errors(gpu):
+    import torch
+    from paper_2311_12133_gb300 import hpez
+    x = torch.rand((20, 20), device="cuda")
+    with pytest.raises(hpez.HpezError) as e:
+        hpez.Batch(gpu, fields=[(x, 1e-3, 1, None), (x, -1.0, 1, None)])
+    assert e.value.code == -1
+    # a corrupt stream is reported per request, the others succeed
+    xs = [torch.rand((30, 40), device="cuda") for _ in range(3)]
+    b = hpez.Batch(gpu, fields=[(v, 1e-3, 1, None) for v in xs])
+    b.run()
+    sizes, st = b.results()
+    assert st == [0, 0, 0]
+    bufs = [b.outs[i][:sizes[i]].clone() for i in range(3)]
+    hdrs = [bufs[i][:512].cpu().numpy().tobytes() for i in range(3)]
+    raw = bufs[1].cpu().numpy()
+    # swap the first two code-table symbols: the table is no longer
+    # ascending, which the decoder rejects
+    ot = int(np.frombuffer(raw[272:280].tobytes(), np.uint64)[0])
+    raw[[ot, ot + 1, ot + 2, ot + 3]] = raw[[ot + 2, ot + 3, ot, ot + 1]]
+    bufs[1] = torch.from_numpy(raw).cuda()
+    d = hpez.Batch(gpu, streams=[(bufs[i], sizes[i], hdrs[i]) for i in range(3)])
+    d.run()
+    _, st = d.results()
+    assert st[0] == 0 and st[2] == 0 and st[1] == -4
+
+
+def test_server_results_equal_single_calls(gpu, oracle):
+    """Requests of mixed size and kind, submitted while others run, under a
+    budget that forces queueing: every result equals the single call's."""
+    import torch
+    from paper_2311_12133_gb300 import hpez
+    mix = _mix(1)
+    single = []
+    for x, eb, mode, kw in mix:
+        g, _ = _cfgs(x, kw)
+        xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        buf, size = gpu.compress(xd, eb, mode, g)
+        s_ = buf[:size].cpu().numpy().tobytes()
+        single.append((s_, gpu.decompress(buf, size).cpu().numpy()))
+    budget = 48 << 20
+    srv = hpez.Server(gpu, budget, max_slots=4)
+    pending = {}
+    order = list(range(len(mix))) * 2
+    rng = np.random.default_rng(0)
+    rng.shuffle(order)
+    k = 0
+    while k < len(order) or pending:
+        # submit a few, then step: later requests join running ones
+        for _ in range(int(rng.integers(0, 3))):
+            if k >= len(order):
+                break
+            i = order[k]
+            x, eb, mode, kw = mix[i]
+            if k % 2 == 0:
+                g, _ = _cfgs(x, kw)
+                rid, out = srv.submit_compress(np.ascontiguousarray(x), eb, mode, g)
+                pending[rid] = ("c", i, out)
+            else:
+                s_ = single[i][0]
+                h = np.frombuffer(s_, np.uint8).copy()
+                rid, out = srv.submit_decompress(h, len(s_))
+                pending[rid] = ("d", i, out)
+            k += 1
+        srv.step()
+        for rid, st, size, lat in srv.poll():
+            kind, i, out = pending.pop(rid)
+            assert st == 0, (kind, i, st)
+            if kind == "c":
+                assert out[:size].tobytes() == single[i][0], i
+            else:
+                assert out.tobytes() == single[i][1].tobytes(), i
+            assert lat >= 0
+    stats = srv.stats()
+    assert stats["active"] == 0 and stats["queued"] == 0 and stats["used_bytes"] == 0
+    srv.close()
+
+
+def test_server_rejects_oversized(gpu):
+    from paper_2311_12133_gb300 import hpez
+    srv = hpez.Server(gpu, 1 << 20, max_slots=2)
+    x = np.zeros((128, 128, 64), np.float32)
+    with pytest.raises(hpez.HpezError) as e:
+        srv.submit_compress(x, 1e-3)
+    assert e.value.code == -10
+    srv.close()
