@@ -54,6 +54,10 @@ def parse():
                     help="fused tile extents e0,e1,e2 (0 = heuristic)")
     ap.add_argument("--profile-only", action="store_true",
                     help="run warm-up + timed steps only (for ncu captures)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 64-field batched-vs-plain measurement")
+    ap.add_argument("--no-served", action="store_true",
+                    help="skip the served-form measurement")
     return ap.parse_args()
 
 
@@ -236,6 +240,185 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+def bench_batched(ctx, steps, warmup):
+    """64 fields of uneven shapes (32^3 .. 256x384x384, 2D and 3D, per-field
+    relative eb), compress + decompress: one graph-captured batched run
+    against 64 sequential single-field calls on the same GPU."""
+    import torch
+    from paper_2311_12133_gb300 import fields, hpez
+    mix = fields.batch_mix(64, seed=0)
+    xs = [(fields.make_torch(k, sh, sd), eb) for k, sh, sd, eb in mix]
+    nbytes = sum(a.numel() * 4 for a, _ in xs)
+    s = torch.cuda.Stream()
+
+    def timed(fn):
+        for _ in range(max(3, warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(steps):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    with torch.cuda.stream(s):
+        outs = [torch.empty(hpez.hpez_compress_bound(a.shape), dtype=torch.uint8,
+                            device="cuda") for a, _ in xs]
+        ys = [torch.empty_like(a) for a, _ in xs]
+        sizes = [0] * len(xs)
+
+        def plain():
+            for i, (a, eb) in enumerate(xs):
+                sizes[i] = ctx.compress(a, eb, hpez.HPEZ_EB_REL, None, out=outs[i],
+                                        stream=s)[1]
+            for i in range(len(xs)):
+                ctx.decompress(outs[i], sizes[i], out=ys[i], shape=tuple(xs[i][0].shape),
+                               stream=s)
+
+        plain_ms = timed(plain)
+        bc = hpez.Batch(ctx, fields=[(a, eb, hpez.HPEZ_EB_REL, None) for a, eb in xs])
+        bc.run(stream=s)
+        bsz, bst = bc.results(stream=s)
+        assert bst == [0] * len(xs) and bsz == sizes, "batched compress differs"
+        hdrs = [bc.outs[i][:512].cpu().numpy().tobytes() for i in range(len(xs))]
+        bd = hpez.Batch(ctx, streams=[(bc.outs[i], bsz[i], hdrs[i]) for i in range(len(xs))])
+
+        def batched():
+            bc.run(stream=s, graph=True)
+            bd.run(stream=s, graph=True)
+
+        batch_ms = timed(batched)
+        _, dst = bd.results(stream=s)
+        assert dst == [0] * len(xs)
+        for i in range(len(xs)):
+            assert torch.equal(bd.outs[i].view(-1), ys[i].view(-1)), "batched decompress differs"
+        la, ta = bc.launch_count()
+        lb, tb = bd.launch_count()
+        bc.close()
+        bd.close()
+    return {"workload": "64 fields, log-uniform 32^3 .. 256x384x384 points, ~1/3 2D, "
+                        "bumps/grf/lognormal/aniso/climate2d, rel eb per field in "
+                        "{1e-2,1e-3,1e-4}, compress+decompress",
+            "input_MB": round(nbytes / 1e6, 1),
+            "value": round(nbytes / (batch_ms / 1e3) / 1e9, 3), "unit": "GB/s",
+            "ms_per_step": round(batch_ms, 3),
+            "plain_value": round(nbytes / (plain_ms / 1e3) / 1e9, 3),
+            "plain_ms_per_step": round(plain_ms, 3),
+            "speedup_vs_plain": round(plain_ms / batch_ms, 3),
+            "launches_per_step": la + lb, "ticks_per_step": ta + tb,
+            "graph": True}
+
+
+def bench_served(ctx, seconds=3.0, rate=200.0):
+    """Poisson stream of compress/decompress requests over fields of 1 MB ..
+    512 MB (log-uniform), rel eb from {1e-2,1e-3,1e-4}, host buffers,
+    40 GB device budget; the served loop against one single-field host call
+    per request in arrival order.  Also the saturated case: every request
+    submitted at once."""
+    import numpy as np
+    import torch
+    from paper_2311_12133_gb300 import fields, hpez
+    rng = np.random.default_rng(1)
+    kinds3 = ["bumps", "grf", "lognormal", "aniso"]
+    pool = []
+    for i in range(12):
+        npts = float(np.exp(rng.uniform(np.log(1 << 20), np.log(512 << 20)))) / 4
+        if rng.uniform() < 1 / 3:
+            ny = max(8, int(round(np.sqrt(npts / 2))))
+            shape = (ny, max(8, int(round(npts / ny))))
+            kind = ["climate2d", "grf"][int(rng.integers(0, 2))]
+        else:
+            r = rng.uniform(0.5, 2.0, 3)
+            r = r / np.prod(r) ** (1 / 3)
+            shape = tuple(max(8, int(round(npts ** (1 / 3) * v))) for v in r)
+            kind = kinds3[int(rng.integers(0, 4))]
+        eb = [1e-2, 1e-3, 1e-4][int(rng.integers(0, 3))]
+        xd = fields.make_torch(kind, shape, 100 + i)
+        h = torch.empty(xd.shape, dtype=torch.float32, pin_memory=True)
+        h.copy_(xd)
+        buf, size = ctx.compress(xd, eb, hpez.HPEZ_EB_REL, None)
+        hs = torch.empty(size, dtype=torch.uint8, pin_memory=True)
+        hs.copy_(buf[:size])
+        pool.append(dict(eb=eb, h=h.numpy(), hs=hs.numpy(), size=size,
+                         oc=torch.empty(hpez.hpez_compress_bound(shape), dtype=torch.uint8,
+                                        pin_memory=True).numpy(),
+                         od=torch.empty(xd.shape, dtype=torch.float32,
+                                        pin_memory=True).numpy(),
+                         nbytes=xd.numel() * 4, keep=(h, hs)))
+        del xd, buf
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    arr, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > seconds:
+            break
+        arr.append((t, int(rng.integers(0, len(pool))), int(rng.integers(0, 2))))
+    total = sum(pool[i]["nbytes"] for _, i, _ in arr)
+
+    def ours(burst):
+        srv = hpez.Server(ctx, 40 << 30, max_slots=64)
+        lat, pend, k = {}, {}, 0
+        start = time.perf_counter()
+        while k < len(arr) or pend:
+            now = time.perf_counter() - start
+            while k < len(arr) and (burst or arr[k][0] <= now):
+                _, i, op = arr[k]
+                p = pool[i]
+                if op == 0:
+                    rid, _ = srv.submit_compress(p["h"], p["eb"], hpez.HPEZ_EB_REL, None,
+                                                 h_out=p["oc"])
+                else:
+                    rid, _ = srv.submit_decompress(p["hs"], p["size"], h_out=p["od"])
+                pend[rid] = k
+                k += 1
+            srv.step()
+            for rid, st, _, l in srv.poll():
+                assert st == 0, st
+                lat[pend.pop(rid)] = l
+        wall = time.perf_counter() - start
+        stats = srv.stats()
+        srv.close()
+        L = np.array([lat[j] for j in range(len(arr))])
+        return {"p50_ms": round(float(np.percentile(L, 50)) * 1e3, 3),
+                "p99_ms": round(float(np.percentile(L, 99)) * 1e3, 3),
+                "GBps": round(total / wall / 1e9, 3), "wall_s": round(wall, 3),
+                "ticks": stats["ticks"], "launches": stats["launches"]}
+
+    def plain(burst):
+        lat = []
+        start = time.perf_counter()
+        for ta, i, op in arr:
+            now = time.perf_counter() - start
+            if not burst and ta > now:
+                time.sleep(ta - now)
+            p = pool[i]
+            if op == 0:
+                hpez.hpez_compress_host(ctx.handle, p["h"], hpez.HPEZ_EB_REL, p["eb"], None,
+                                        p["oc"])
+            else:
+                hpez.hpez_decompress_host(ctx.handle, p["hs"], p["size"], p["od"])
+            lat.append(time.perf_counter() - start - (0.0 if burst else ta))
+        wall = time.perf_counter() - start
+        L = np.array(lat)
+        return {"p50_ms": round(float(np.percentile(L, 50)) * 1e3, 3),
+                "p99_ms": round(float(np.percentile(L, 99)) * 1e3, 3),
+                "GBps": round(total / wall / 1e9, 3), "wall_s": round(wall, 3)}
+
+    ours(True)  # warm-up of the served path
+    r = {"workload": f"Poisson {rate:g} req/s for {seconds:g} s, {len(arr)} requests "
+                     f"(compress or decompress, 1 MB..512 MB log-uniform, 12-field pool), "
+                     f"host buffers, 40 GB budget, 64 slots",
+         "input_GB": round(total / 1e9, 3),
+         "poisson": ours(False), "plain_poisson": plain(False),
+         "saturated": ours(True), "plain_saturated": plain(True)}
+    r["speedup_saturated"] = round(r["saturated"]["GBps"] / r["plain_saturated"]["GBps"], 3)
+    return r
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -382,6 +565,12 @@ def main():
                "sample": f"2 compress+decompress round trips of the first 64 planes "
                          f"({'x'.join(map(str, slab.shape))}) of the same field, {secs:.1f} s"}
 
+    batched = served = None
+    if rank == 0 and world == 1 and not args.no_batched:
+        batched = bench_batched(ctx, max(3, args.steps // 2), args.warmup)
+    if rank == 0 and world == 1 and not args.no_served:
+        served = bench_served(ctx)
+
     if rank == 0:
         line = {
             "metric": "compress+decompress input GB/s (rel eb 1e-3)",
@@ -403,6 +592,7 @@ def main():
             "roofline": roofline, "phases": phase_report,
             "gpu_launches": int(launches),
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+            "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

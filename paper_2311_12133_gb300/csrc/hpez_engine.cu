@@ -752,7 +752,9 @@ struct SrvReq {
   Request plan;
   size_t cursor = 0;
   int state = RS_QUEUED;
-  cudaEvent_t ev = nullptr;
+  cudaEvent_t ev = nullptr;     // result ready / output copied
+  cudaEvent_t ev_in = nullptr;  // input on the device
+  bool wait_in = false;
   int status = 0;
   uint64_t size = 0;
   double t_submit = 0;
@@ -812,7 +814,9 @@ constexpr int kRing = 4;
 
 struct hpez_server {
   hpez_ctx* ctx = nullptr;
-  cudaStream_t s = nullptr;
+  cudaStream_t s = nullptr;      // kernels (the caller's stream)
+  cudaStream_t s_in = nullptr;   // host -> device copies
+  cudaStream_t s_out = nullptr;  // device -> host copies
   char* pool_mem = nullptr;
   size_t budget = 0;
   Pool pool;
@@ -907,6 +911,8 @@ int hpez_server_create(hpez_ctx* ctx, uint64_t budget_bytes, int max_slots,
             cudaMallocHost(&S->h_status, sizeof(int) * max_slots) == cudaSuccess;
   for (int k = 0; ok && k < kRing; ++k)
     ok = cudaEventCreateWithFlags(&S->tab_ev[k], cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&S->s_in, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaStreamCreateWithFlags(&S->s_out, cudaStreamNonBlocking) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     hpez_server_destroy(S);
@@ -987,8 +993,9 @@ int hpez_server_step(hpez_server* S) {
       }
       if (!q->status) {
         const size_t o_out = al256(q->plan.in_bytes);
-        cudaMemcpyAsync(q->rq.h_out, base + o_out, q->size, cudaMemcpyDeviceToHost, s);
-        cudaEventRecord(q->ev, s);
+        cudaMemcpyAsync(q->rq.h_out, base + o_out, q->size, cudaMemcpyDeviceToHost,
+                        S->s_out);
+        cudaEventRecord(q->ev, S->s_out);
         q->state = RS_COPYING;
       } else {
         gone = true;
@@ -998,7 +1005,8 @@ int hpez_server_step(hpez_server* S) {
     }
     if (gone) {
       cudaEventDestroy(q->ev);
-      q->ev = nullptr;
+      cudaEventDestroy(q->ev_in);
+      q->ev = q->ev_in = nullptr;
       srv_retire(S, q);
       S->active.erase(S->active.begin() + i);
     } else {
@@ -1019,19 +1027,25 @@ int hpez_server_step(hpez_server* S) {
     int rc = srv_plan(S, q, base);
     if (!rc)
       rc = cuda_check(cudaMemcpyAsync(base, q->rq.h_in, q->plan.in_bytes,
-                                      cudaMemcpyHostToDevice, s));
+                                      cudaMemcpyHostToDevice, S->s_in));
     for (const Upload& u : q->plan.uploads)
       if (!rc)
         rc = cuda_check(cudaMemcpyAsync(u.dst, u.bytes.data(), u.bytes.size(),
-                                        cudaMemcpyHostToDevice, s));
+                                        cudaMemcpyHostToDevice, S->s_in));
     if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming));
+    if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&q->ev_in, cudaEventDisableTiming));
+    if (!rc) rc = cuda_check(cudaEventRecord(q->ev_in, S->s_in));
     if (rc) {
+      if (q->ev) cudaEventDestroy(q->ev);
+      if (q->ev_in) cudaEventDestroy(q->ev_in);
+      q->ev = q->ev_in = nullptr;
       q->status = rc;
       srv_retire(S, q);
       continue;
     }
     q->state = RS_ACTIVE;
     q->cursor = 0;
+    q->wait_in = true;
     S->active.push_back(q);
   }
   // 3. one tick over every active request
@@ -1039,6 +1053,10 @@ int hpez_server_step(hpez_server* S) {
   std::vector<SrvReq*> finishing;
   for (SrvReq* q : S->active) {
     if (q->state != RS_ACTIVE) continue;
+    if (q->wait_in) {  // its first operation waits for its input copy
+      cudaStreamWaitEvent(s, q->ev_in, 0);
+      q->wait_in = false;
+    }
     now.push_back(&q->plan.ops[q->cursor++]);
     if (q->cursor == q->plan.ops.size()) finishing.push_back(q);
   }
@@ -1129,8 +1147,11 @@ int hpez_server_destroy(hpez_server* S) {
   for (SrvReq* q : S->queue) delete q;
   for (SrvReq* q : S->active) {
     if (q->ev) cudaEventDestroy(q->ev);
+    if (q->ev_in) cudaEventDestroy(q->ev_in);
     delete q;
   }
+  if (S->s_in) cudaStreamDestroy(S->s_in);
+  if (S->s_out) cudaStreamDestroy(S->s_out);
   for (SrvReq* q : S->done) delete q;
   for (int k = 0; k < kRing; ++k) {
     if (S->h_tab[k]) cudaFreeHost(S->h_tab[k]);

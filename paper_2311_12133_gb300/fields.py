@@ -189,6 +189,91 @@ def grf_torch(shape=(512, 512, 512), seed=0, slope=-5.0 / 3.0, device="cuda"):
     return f.contiguous()
 
 
+def _grf_axes_torch(shape, seed, slope, axes, device):
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
+    w = torch.randn(shape, generator=g, device=device, dtype=torch.float32)
+    W = torch.fft.rfftn(w, dim=axes)
+    del w
+    filt = torch.from_numpy(_spectral_filter(shape, slope, axes)
+                            .astype(np.float32)).to(device)
+    W *= filt
+    del filt
+    f = torch.fft.irfftn(W, s=[shape[a] for a in axes], dim=axes)
+    del W
+    f -= f.mean(dtype=torch.float64).float()
+    f /= f.std().float()
+    return f.contiguous()
+
+
+def make_torch(kind: str, shape, seed: int, device="cuda"):
+    """The recipes above drawn on the GPU with torch (same parameters and
+    spectra, a different random stream for the white-noise parts), for
+    large or many benchmark inputs.  Returns a float32 CUDA tensor."""
+    import torch
+    shape = tuple(int(s) for s in shape)
+    nd = len(shape)
+    if kind == "grf":
+        return grf_torch(shape, seed, device=device)
+    if kind == "lognormal":
+        f = grf_torch(shape, seed, device=device)
+        f *= float(np.sqrt(2.0))
+        return torch.exp_(f)
+    if kind == "aniso":
+        if nd != 3:
+            return grf_torch(shape, seed, slope=-3.0, device=device)
+        return _grf_axes_torch(shape, seed, -3.0, (1, 2), device)
+    if kind == "bumps":
+        rng = np.random.default_rng(seed)
+        axes = [torch.arange(n, device=device, dtype=torch.float32) for n in shape]
+        out = torch.zeros(shape, device=device, dtype=torch.float32)
+        for _ in range(32):
+            amp = rng.uniform(-1, 1)
+            width = rng.uniform(4, 24)
+            ctr = [rng.uniform(0, n) for n in shape]
+            g = None
+            for d in range(nd):
+                gd = torch.exp(-0.5 * ((axes[d] - ctr[d]) / width) ** 2)
+                sh = [1] * nd
+                sh[d] = shape[d]
+                gd = gd.reshape(sh)
+                g = gd if g is None else g * gd
+            out += amp * g
+        for _ in range(3):
+            k = rng.integers(1, 4, size=nd)
+            ph = rng.uniform(0, 2 * np.pi)
+            arg = None
+            for d in range(nd):
+                sh = [1] * nd
+                sh[d] = shape[d]
+                a_ = (2 * np.pi * float(k[d]) * axes[d] / shape[d]).reshape(sh)
+                arg = a_ if arg is None else arg + a_
+            out += 0.1 * torch.sin(arg + ph)
+        gen = torch.Generator(device=device)
+        gen.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
+        out += 1e-4 * torch.randn(shape, generator=gen, device=device)
+        return out.contiguous()
+    if kind == "climate2d":
+        rng = np.random.default_rng(seed)
+        ny, nx = shape[-2], shape[-1]
+        lat = torch.linspace(-np.pi / 2, np.pi / 2, ny, device=device)
+        mean = 30.0 * torch.cos(lat) + 3.0 * torch.cos(6 * lat)
+        f = mean[:, None] + 2.0 * grf_torch((ny, nx), seed + 1, slope=-3.0,
+                                            device=device)
+        fill = float(f.min())
+        area, target = 0, 0.05 * ny * nx
+        while area < target:
+            h = int(rng.integers(max(ny // 40, 1), max(ny // 8, 2)))
+            w = int(rng.integers(max(nx // 40, 1), max(nx // 8, 2)))
+            y0 = int(rng.integers(0, max(ny - h, 1)))
+            x0 = int(rng.integers(0, max(nx - w, 1)))
+            f[y0:y0 + h, x0:x0 + w] = fill
+            area += h * w
+        return f.contiguous()
+    raise ValueError(kind)
+
+
 GENERATORS = {
     "bumps": bumps,
     "grf": grf,
