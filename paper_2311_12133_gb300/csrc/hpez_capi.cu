@@ -439,6 +439,61 @@ void default_config(int ndim, hpez_config* c) {
   }
 }
 
+// A level of the multi-dimensional paradigm with one interpolator for every
+// point and no same-level halves runs as one launch per sub-pass.
+bool plan_md(const hpez_ctx* ctx, const Plan& p, const hpez_config& c, int l,
+             bool decomp, LevelMD& F) {
+  if (!ctx->fused_levels || c.paradigm[l - 1] != HPEZ_PARADIGM_MD || p.k == 0)
+    return false;
+  if (c.blockwise) return false;
+  if (c.same_level[l - 1] && c.interp[l - 1] != HPEZ_LINEAR) return false;
+  std::memset(&F, 0, sizeof(F));
+  F.g = p.grid[l - 1];
+  F.gc = p.grid[l];
+  unsigned imask = 0;
+  for (int s = 0; s < 3; ++s) {
+    F.interp[s] = p.interp[s] ? 1 : 0;
+    F.nc[s] = F.gc.m[s];
+    F.fst[s] = p.fst[s];
+    if (p.interp[s]) imask |= 1u << s;
+  }
+  F.k = p.k;
+  F.level = l;
+  F.write_recon = (decomp || l > 1) ? 1 : 0;
+  for (unsigned S = 1; S < 8; ++S) {
+    if ((S & imask) != S) continue;
+    const int kk = __builtin_popcount(S);
+    F.masks[kk - 1][F.nmask[kk - 1]++] = (uint8_t)S;
+    for (int s = 0; s < 3; ++s)
+      if (S & (1u << s)) F.w[S][s] = md_weight(p, c, S, s);
+  }
+  return true;
+}
+
+// A block map whose blocks all carry the same interpolator is the same
+// predictor as that interpolator (and same-level flag) at every level.
+bool uniform_blockmap(const uint8_t* bm, uint32_t n, uint8_t* v) {
+  if (!bm || n == 0) return false;
+  for (uint32_t i = 1; i < n; ++i)
+    if (bm[i] != bm[0]) return false;
+  *v = bm[0];
+  return true;
+}
+
+hpez_config sweep_config(const hpez_config& c, const uint8_t* h_bmap,
+                         uint32_t nblocks) {
+  hpez_config r = c;
+  uint8_t v;
+  if (c.blockwise && uniform_blockmap(h_bmap, nblocks, &v)) {
+    r.blockwise = 0;
+    for (int l = 0; l < HPEZ_MAX_LEVELS; ++l) {
+      r.interp[l] = (uint8_t)((v & 3u) > HPEZ_CUBIC_NAT ? HPEZ_CUBIC_NAT : (v & 3u));
+      r.same_level[l] = (uint8_t)((v >> 2) & 1u);
+    }
+  }
+  return r;
+}
+
 uint64_t n_anchors(const Plan& p) { return p.gsize[p.L]; }
 
 void header_templates(const Plan& p, const hpez_config& c, int eb_mode,
@@ -827,10 +882,13 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
                        b.ctl, s);
   pf.end(s);
   ++nl;
+  // the predictor the sweep runs (a uniform block map becomes its
+  // interpolator); the header keeps the configuration as given
+  const hpez_config sc = sweep_config(cfg, cfg.h_blockmap, p.nblocks);
   SweepBufs sb;
   std::memset(&sb, 0, sizeof(sb));
   sb.x = d_in;
-  sb.blockmap = cfg.blockwise ? b.bmap : nullptr;
+  sb.blockmap = sc.blockwise ? b.bmap : nullptr;
   sb.bs = (uint32_t)(cfg.block_size > 0 ? cfg.block_size : 1);
   for (int s3 = 0; s3 < 3; ++s3) sb.nb[s3] = p.nb[s3];
   sb.ctl = b.ctl;
@@ -839,21 +897,26 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
     pf.begin(HPEZ_PH_LEVEL + g, s);
     sb.R = b.R[g];
     sb.C = b.Cg[g];
-    sb.kind = cfg.interp[l - 1];
-    sb.same = cfg.same_level[l - 1];
+    sb.kind = sc.interp[l - 1];
+    sb.same = sc.same_level[l - 1];
     FusedLevel F;
     Level3D F3;
-    if (ctx->fused_levels && plan_level3d(ctx, p, cfg, l, false, F3)) {
+    LevelMD FM;
+    if (ctx->fused_levels && plan_level3d(ctx, p, sc, l, false, F3)) {
       launch_level3d(false, F3, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g], s);
       ++nl;
-    } else if (ctx->fused_levels && plan_fused(ctx, p, cfg, l, false, F)) {
+    } else if (plan_md(ctx, p, sc, l, false, FM)) {
+      launch_level_md(false, sb.kind, FM, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g],
+                      ctx->num_sms, s);
+      nl += FM.k;
+    } else if (ctx->fused_levels && plan_fused(ctx, p, sc, l, false, F)) {
       launch_level(false, F, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g], s);
       ++nl;
     } else {
       launch_upsample(p.grid[l], p.gsize[l], p.grid[g], b.R[l], b.Cg[l], b.R[g],
                       b.Cg[g], b.ctl, s);
       ++nl;
-      for (const Launch& L : level_schedule(p, cfg, l)) {
+      for (const Launch& L : level_schedule(p, sc, l)) {
         launch_pass(false, p.grid[g], L.pb, sb, ctx->num_sms, s);
         nl += L.pb.total ? 1 : 0;
       }
@@ -1019,11 +1082,21 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
                   const_cast<uint8_t*>(in) + oo, nout, ctl, ctx->num_sms, s);
   pf.end(s);
   nl += 8;
+  // a uniform block map runs as its interpolator (the map is read back)
+  std::vector<uint8_t> hmap;
+  if (cfg.blockwise) {
+    hmap.resize(p.nblocks);
+    rc = cuda_check(cudaMemcpyAsync(hmap.data(), in + obm, p.nblocks,
+                                    cudaMemcpyDeviceToHost, s));
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(s));
+    if (rc) return rc;
+  }
+  const hpez_config sc = sweep_config(cfg, hmap.data(), p.nblocks);
   SweepBufs sb;
   std::memset(&sb, 0, sizeof(sb));
   sb.codes_full = codes;
   sb.outl_full = d_out;
-  sb.blockmap = cfg.blockwise ? in + obm : nullptr;
+  sb.blockmap = sc.blockwise ? in + obm : nullptr;
   sb.bs = (uint32_t)(cfg.block_size > 0 ? cfg.block_size : 1);
   for (int s3 = 0; s3 < 3; ++s3) sb.nb[s3] = p.nb[s3];
   sb.ctl = ctl;
@@ -1031,21 +1104,26 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
     const int g = l - 1;
     pf.begin(HPEZ_PH_DLEVEL + g, s);
     sb.R = R[g];
-    sb.kind = cfg.interp[l - 1];
-    sb.same = cfg.same_level[l - 1];
+    sb.kind = sc.interp[l - 1];
+    sb.same = sc.same_level[l - 1];
     FusedLevel F;
     Level3D F3;
-    if (ctx->fused_levels && plan_level3d(ctx, p, cfg, l, true, F3)) {
+    LevelMD FM;
+    if (ctx->fused_levels && plan_level3d(ctx, p, sc, l, true, F3)) {
       launch_level3d(true, F3, sb, R[l], nullptr, R[g], nullptr, s);
       ++nl;
-    } else if (ctx->fused_levels && plan_fused(ctx, p, cfg, l, true, F)) {
+    } else if (plan_md(ctx, p, sc, l, true, FM)) {
+      launch_level_md(true, sb.kind, FM, sb, R[l], nullptr, R[g], nullptr,
+                      ctx->num_sms, s);
+      nl += FM.k;
+    } else if (ctx->fused_levels && plan_fused(ctx, p, sc, l, true, F)) {
       launch_level(true, F, sb, R[l], nullptr, R[g], nullptr, s);
       ++nl;
     } else {
       launch_upsample(p.grid[l], p.gsize[l], p.grid[g], R[l], nullptr, R[g],
                       nullptr, ctl, s);
       ++nl;
-      for (const Launch& L : level_schedule(p, cfg, l)) {
+      for (const Launch& L : level_schedule(p, sc, l)) {
         launch_pass(true, p.grid[g], L.pb, sb, ctx->num_sms, s);
         nl += L.pb.total ? 1 : 0;
       }

@@ -151,6 +151,12 @@ bool plan_fused(const hpez_ctx* ctx, const Plan& p, const hpez_config& c, int l,
 bool plan_level3d(const hpez_ctx* ctx, const Plan& p, const hpez_config& c,
                   int l, bool decomp, Level3D& F);
 uint64_t n_anchors(const Plan& p);
+bool plan_md(const hpez_ctx* ctx, const Plan& p, const hpez_config& c, int l,
+             bool decomp, LevelMD& F);
+// the predictor a sweep runs: a block map with one interpolator for every
+// block becomes that interpolator at every level
+hpez_config sweep_config(const hpez_config& c, const uint8_t* h_bmap,
+                         uint32_t nblocks);
 void header_templates(const Plan& p, const hpez_config& c, int eb_mode,
                       double eb, uint64_t off_anchors, uint64_t off_bmap,
                       uint64_t off_chw, uint8_t* h, uint8_t* hc);

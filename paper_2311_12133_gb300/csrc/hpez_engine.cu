@@ -204,10 +204,11 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
                         AnchorJob{d_in, p.grid[p.L], p.gsize[p.L], R[p.L],
                                   Cg[p.L], ctl},
                         grid_blocks(p.gsize[p.L], 65535)));
+  const hpez_config sc = sweep_config(cfg, cfg.h_blockmap, p.nblocks);
   SweepBufs sb;
   std::memset(&sb, 0, sizeof(sb));
   sb.x = d_in;
-  sb.blockmap = cfg.blockwise ? bmap : nullptr;
+  sb.blockmap = sc.blockwise ? bmap : nullptr;
   sb.bs = (uint32_t)(cfg.block_size > 0 ? cfg.block_size : 1);
   for (int s3 = 0; s3 < 3; ++s3) sb.nb[s3] = p.nb[s3];
   sb.ctl = ctl;
@@ -216,15 +217,15 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
     const int g = l - 1;
     sb.R = R[g];
     sb.C = Cg[g];
-    sb.kind = cfg.interp[l - 1];
-    sb.same = cfg.same_level[l - 1];
+    sb.kind = sc.interp[l - 1];
+    sb.same = sc.same_level[l - 1];
     FusedLevel F;
     Level3D F3;
-    if (ctx->fused_levels && plan_level3d(ctx, p, cfg, l, false, F3)) {
+    if (ctx->fused_levels && plan_level3d(ctx, p, sc, l, false, F3)) {
       Level3DJob j{F3, d_in, nullptr, nullptr, R[l], Cg[l], R[g], Cg[g], ctl};
       ops.push_back(make_op(OP_L3D_C + sb.kind, j, (uint32_t)(F3.nt0 * F3.nt1),
                             (uint32_t)level3d_smem_bytes(F3, false)));
-    } else if (ctx->fused_levels && plan_fused(ctx, p, cfg, l, false, F)) {
+    } else if (ctx->fused_levels && plan_fused(ctx, p, sc, l, false, F)) {
       LevelJob j{F, sb, R[l], Cg[l], R[g], Cg[g]};
       ops.push_back(make_op(OP_LVL_C + level_kind(sb), j, F.ntiles,
                             (uint32_t)fused_smem_bytes(F, false)));
@@ -233,7 +234,7 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
                             UpsampleJob{p.grid[l], p.gsize[l], p.grid[g], R[l],
                                         Cg[l], R[g], Cg[g], ctl},
                             grid_blocks(p.gsize[l], 65535)));
-      for (const Launch& L : level_schedule(p, cfg, l))
+      for (const Launch& L : level_schedule(p, sc, l))
         if (L.pb.total)
           ops.push_back(make_op(OP_PASS_C, PassJob{p.grid[g], L.pb, sb},
                                 pass_blocks(L.pb.total, sms)));

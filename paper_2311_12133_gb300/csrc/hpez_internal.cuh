@@ -314,6 +314,20 @@ struct Level3D {
   int vec_out;       // rows of the output grids start 16-byte aligned
 };
 
+// One level of the multi-dimensional paradigm (one launch per sub-pass).
+struct LevelMD {
+  LevelGeom g, gc;     // level grid, coarse grid
+  uint32_t nc[3];      // cells per slot (coarse extent; the extent on a
+                       // non-interpolation slot)
+  uint32_t fst[3];     // full-field strides
+  int interp[3];
+  int k;               // interpolation slots = sub-passes
+  int level, write_recon;
+  int nmask[3];        // odd sets of sub-pass k' (index k'-1)
+  uint8_t masks[3][3];
+  float w[8][3];       // Eq. 14 weight per odd set and slot
+};
+
 // ---------------------------------------------------------------------
 // Auto-tuner (Sec. 6): one theta of a compression test, and the geometry
 // of the sub-fields the tests run on.

@@ -37,6 +37,11 @@ void launch_level3d(bool decomp, const Level3D& P, const SweepBufs& B,
                     const float* Rc, const uint16_t* Cc, float* Rs, uint16_t* Cs,
                     cudaStream_t s);
 
+// k_level_md.cu
+void launch_level_md(bool decomp, int kind, const LevelMD& P, const SweepBufs& B,
+                     const float* Rc, const uint16_t* Cc, float* Rs, uint16_t* Cs,
+                     int num_sms, cudaStream_t s);
+
 // k_huffman.cu
 void launch_hist(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,
                  uint32_t* hist, uint32_t* zc, const Ctl* ctl, int num_sms,
@@ -157,7 +162,8 @@ void launch_tune_blockwise(const float* x, const TuneGeom& g, int bs, int Q,
                            int frozen_slot, const uint32_t nb[3],
                            uint32_t nblocks, const TuneCfg* base,
                            unsigned allow, uint8_t* bmap, cudaStream_t s);
-void launch_tune_cost(const uint32_t* hist, const uint8_t* lens,
-                      unsigned long long* cost, cudaStream_t s);
+// Huffman bits of nvar histograms (65536 bins each, lengths alike)
+void launch_tune_cost(const uint32_t* hists, const uint8_t* lens,
+                      unsigned long long* cost, int nvar, cudaStream_t s);
 
 }  // namespace hpez

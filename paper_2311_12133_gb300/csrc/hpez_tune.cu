@@ -93,9 +93,12 @@ TuneCfg to_device(const Plan& p, const hpez_config& c) {
 }
 
 // device buffers of one hpez_tune call
+constexpr int kMaxHists = 17;  // (alpha, beta) grid
+
 struct Bufs {
   Ctl* ctl;
-  Ctl* ctl2;  // codebook status
+  Ctl* ctl2;  // codebook status, one per histogram
+  CodebookJob* cbjobs;
   unsigned long long* acc;
   TuneCfg* cfgs;
   unsigned long long* score;
@@ -189,19 +192,36 @@ uint64_t block_anchors(const TuneGeom& g) {
   return na;
 }
 
-// Huffman bits of histograms [0, nvar) into b.cost[0, nvar)
+// Huffman bits of histograms [0, nvar) into b.cost[0, nvar): one batched
+// codebook launch (a CTA per histogram) and one cost launch
 void hist_costs(Call& k, int nvar) {
   uint64_t& nl = k.ctx->launches;
-  launch_init_ctl(k.b.ctl2, k.s);
-  ++nl;
+  CodebookJob jobs[kMaxHists];
   for (int v = 0; v < nvar; ++v) {
-    const uint32_t* h = k.b.hists + (size_t)v * 65536;
-    cudaMemsetAsync(k.b.lens, 0, 65536, k.s);
-    launch_codebook(h, k.b.enc, k.b.tsyms, k.b.tlens, k.b.gkeys, k.b.giw,
-                    k.b.gpar, k.b.lens, k.b.ctl2, k.s);
-    launch_tune_cost(h, k.b.lens, k.b.cost + v, k.s);
-    nl += 2;
+    const size_t o = (size_t)v * 65536;
+    jobs[v] = CodebookJob{k.b.hists + o, k.b.enc + o, k.b.tsyms + o, k.b.tlens + o,
+                          k.b.gkeys + o, k.b.giw + o, k.b.gpar + 2 * o,
+                          k.b.lens + o, k.b.ctl2 + v};
   }
+  cudaMemsetAsync(k.b.ctl2, 0, sizeof(Ctl) * nvar, k.s);
+  cudaMemsetAsync(k.b.lens, 0, (size_t)65536 * nvar, k.s);
+  cudaMemcpyAsync(k.b.cbjobs, jobs, sizeof(CodebookJob) * nvar,
+                  cudaMemcpyHostToDevice, k.s);
+  launch_codebook_batch(k.b.cbjobs, nvar, k.s);
+  launch_tune_cost(k.b.hists, k.b.lens, k.b.cost, nvar, k.s);
+  nl += 2;
+}
+
+// status of the histogram codebooks (0 when every one was built)
+int costs_status(Call& k, int nvar) {
+  std::vector<Ctl> st(nvar);
+  cudaMemcpyAsync(st.data(), k.b.ctl2, sizeof(Ctl) * nvar, cudaMemcpyDeviceToHost,
+                  k.s);
+  int rc = sync_check(k);
+  if (rc) return rc;
+  for (int v = 0; v < nvar; ++v)
+    if (st[v].status) return HPEZ_ERR_UNSUPPORTED;
+  return HPEZ_OK;
 }
 
 // Sec. 6.2 + 6.4 for one choice of frozen dim; returns the sample bits
@@ -294,14 +314,11 @@ int tune_global(Call& k, int frozen, const double inv_var[3],
   hist_costs(k, nvar);
   prof.end(k.s);
   std::vector<unsigned long long> cost(nvar), nout(nvar);
-  Ctl st;
   cudaMemcpyAsync(cost.data(), k.b.cost, sizeof(unsigned long long) * nvar,
                   cudaMemcpyDeviceToHost, k.s);
   cudaMemcpyAsync(nout.data(), k.b.nout, sizeof(unsigned long long) * nvar,
                   cudaMemcpyDeviceToHost, k.s);
-  cudaMemcpyAsync(&st, k.b.ctl2, sizeof(Ctl), cudaMemcpyDeviceToHost, k.s);
-  if ((rc = sync_check(k))) return rc;
-  if (st.status) return HPEZ_ERR_UNSUPPORTED;
+  if ((rc = costs_status(k, nvar))) return rc;
   const uint64_t na = block_anchors(g) * (uint64_t)nblk;
   int best = 0;
   uint64_t best_bits = 0;
@@ -380,20 +397,21 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
 
   Arena ar;
   const size_t o_ctl = ar.take<Ctl>(1);
-  const size_t o_ctl2 = ar.take<Ctl>(1);
+  const size_t o_ctl2 = ar.take<Ctl>(kMaxHists);
+  const size_t o_cbjobs = ar.take<CodebookJob>(kMaxHists);
   const size_t o_acc = ar.take<unsigned long long>(8);
   const size_t o_cfgs = ar.take<TuneCfg>(kMaxVariants);
   const size_t o_score = ar.take<unsigned long long>(kMaxVariants);
   const size_t o_nout = ar.take<unsigned long long>(kMaxVariants);
   const size_t o_cost = ar.take<unsigned long long>(kMaxVariants);
-  const size_t o_hists = ar.take<uint32_t>((size_t)65536 * 17);
-  const size_t o_lens = ar.take<uint8_t>(65536);
-  const size_t o_enc = ar.take<unsigned long long>(65536);
-  const size_t o_tsyms = ar.take<uint16_t>(65536);
-  const size_t o_tlens = ar.take<uint8_t>(65536);
-  const size_t o_gkeys = ar.take<unsigned long long>(65536);
-  const size_t o_giw = ar.take<unsigned long long>(65536);
-  const size_t o_gpar = ar.take<uint32_t>(131072);
+  const size_t o_hists = ar.take<uint32_t>((size_t)65536 * kMaxHists);
+  const size_t o_lens = ar.take<uint8_t>((size_t)65536 * kMaxHists);
+  const size_t o_enc = ar.take<unsigned long long>((size_t)65536 * kMaxHists);
+  const size_t o_tsyms = ar.take<uint16_t>((size_t)65536 * kMaxHists);
+  const size_t o_tlens = ar.take<uint8_t>((size_t)65536 * kMaxHists);
+  const size_t o_gkeys = ar.take<unsigned long long>((size_t)65536 * kMaxHists);
+  const size_t o_giw = ar.take<unsigned long long>((size_t)65536 * kMaxHists);
+  const size_t o_gpar = ar.take<uint32_t>((size_t)131072 * kMaxHists);
   const size_t o_bmap = ar.take<uint8_t>(nbm ? nbm : 1);
   if ((rc = ensure_scratch(ctx, ar.off))) return rc;
   char* base = ctx->scratch;
@@ -406,6 +424,7 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
   k.tp = &tp;
   k.b.ctl = reinterpret_cast<Ctl*>(base + o_ctl);
   k.b.ctl2 = reinterpret_cast<Ctl*>(base + o_ctl2);
+  k.b.cbjobs = reinterpret_cast<CodebookJob*>(base + o_cbjobs);
   k.b.acc = reinterpret_cast<unsigned long long*>(base + o_acc);
   k.b.cfgs = reinterpret_cast<TuneCfg*>(base + o_cfgs);
   k.b.score = reinterpret_cast<unsigned long long*>(base + o_score);
@@ -522,12 +541,9 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
     hist_costs(k, 2);
     prof.end(s);
     unsigned long long cost[2], nout[2];
-    Ctl st;
     cudaMemcpyAsync(cost, k.b.cost, sizeof(cost), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(nout, k.b.nout, sizeof(nout), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(&st, k.b.ctl2, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
-    if ((rc = sync_check(k))) return rc;
-    if (st.status) return HPEZ_ERR_UNSUPPORTED;
+    if ((rc = costs_status(k, 2))) return rc;
     const uint64_t lb0 = cost[0] + 32ull * nout[0];
     const uint64_t lb1 = cost[1] + 32ull * nout[1];
     if (rep) {

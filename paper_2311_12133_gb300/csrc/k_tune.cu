@@ -235,88 +235,143 @@ __device__ __forceinline__ float predict_smem(const float* R, int i, int st,
 
 // One level (stride s = 2^(l-1)) of the sweep on the sub-field: passes
 // and same-level halves in the compressor's order, a barrier after each.
-// Adds the error scores (when score_on), the code counts (kHist) and the
-// escapes of the level's points to the thread's accumulators.
+// A pass's points form boxes of the stride-s lattice (a 1D-style pass one
+// box: odd along its direction, any multiple of s on earlier directions,
+// even on later ones; a multi-dimensional sub-pass one box per set of odd
+// directions of its size), enumerated directly.  Adds the error scores
+// (when score_on), the code counts (kHist) and the escapes of the level's
+// points to the thread's accumulators.
+struct Box {
+  int a[3], b[3], cnt[3];
+  int total;
+  unsigned S;
+};
+
+__device__ __forceinline__ void make_box(Box& bx, const Sub& f,
+                                         const int interp[3], int s,
+                                         unsigned odd, unsigned any) {
+  bx.total = 1;
+  bx.S = odd;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int n = f.n[d];
+    if (!interp[d]) {
+      bx.a[d] = 0;
+      bx.b[d] = 1;
+      bx.cnt[d] = n;
+    } else if (odd & (1u << d)) {
+      bx.a[d] = s;
+      bx.b[d] = 2 * s;
+      bx.cnt[d] = n - 1 >= s ? (n - 1 - s) / (2 * s) + 1 : 0;
+    } else if (any & (1u << d)) {
+      bx.a[d] = 0;
+      bx.b[d] = s;
+      bx.cnt[d] = (n - 1) / s + 1;
+    } else {
+      bx.a[d] = 0;
+      bx.b[d] = 2 * s;
+      bx.cnt[d] = (n - 1) / (2 * s) + 1;
+    }
+    bx.total *= bx.cnt[d];
+  }
+}
+
 template <bool kHist>
 __device__ void sweep_level(float* R, const Sub& f, const int interp[3],
                             int k, int l, const TuneCfg& c, bool score_on,
                             unsigned long long& score, uint32_t* hist,
                             unsigned long long& nout) {
   const int sh = l - 1, s = 1 << sh;
-  int step[3], m[3], line[3];
+  int line[3];
+  unsigned imask = 0;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    step[d] = interp[d] ? s : 1;
-    m[d] = (f.n[d] + step[d] - 1) / step[d];
     line[d] = (f.n[d] - 1) / s + 1;
+    if (interp[d]) imask |= 1u << d;
   }
-  const int M = m[0] * m[1] * m[2];
   const int kind = c.kind[l - 1];
   const bool md = c.md[l - 1] != 0;
   const bool same = c.same[l - 1] != 0 && kind != LINEAR;
   const float el = c.el[l - 1], inv2 = c.inv2[l - 1], twoe = c.twoe[l - 1];
   const double inv_el = c.inv_el[l - 1];
   for (int pj = 0; pj < k; ++pj) {
-    const int ps = md ? -1 : c.ord[l - 1][pj];
-    unsigned later = 0;  // 1D-style: slots later in the order stay even
-    if (!md)
-      for (int q = pj + 1; q < k; ++q) later |= 1u << c.ord[l - 1][q];
+    Box bx[3];
+    int nb = 0;
+    if (!md) {
+      unsigned any = 0;  // directions earlier in the order: any parity
+      for (int q = 0; q < pj; ++q) any |= 1u << c.ord[l - 1][q];
+      make_box(bx[0], f, interp, s, 1u << c.ord[l - 1][pj], any);
+      nb = 1;
+    } else {
+      for (unsigned S = 1; S < 8; ++S)
+        if ((S & imask) == S && __popc(S) == pj + 1)
+          make_box(bx[nb++], f, interp, s, S, 0u);
+    }
+    int tot = 0;
+    for (int q = 0; q < nb; ++q) tot += bx[q].total;
     for (int half = 0; half < (same ? 2 : 1); ++half) {
-      for (int q = threadIdx.x; q < M; q += blockDim.x) {
-        int cc[3];
-        cc[2] = (q % m[2]) * step[2];
-        const int r = q / m[2];
-        cc[1] = (r % m[1]) * step[1];
-        cc[0] = (r / m[1]) * step[0];
-        unsigned odd = 0;
-        int nodd = 0;
+      // four points per thread and round: their input loads are issued
+      // together before any of them is predicted
+      constexpr int U = 4;
+      for (int t0 = threadIdx.x; t0 < tot; t0 += U * blockDim.x) {
+        int cc[U][3], ii[U];
+        unsigned SS[U];
+        bool ok[U], bb[U];
+        float xv[U];
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
-          if (interp[d] && ((cc[d] >> sh) & 1)) {
-            odd |= 1u << d;
-            ++nodd;
-          }
-        if (nodd == 0) continue;
-        unsigned S;
-        if (!md) {
-          if (!(odd & (1u << ps)) || (odd & later)) continue;
-          S = 1u << ps;
-        } else {
-          if (nodd != pj + 1) continue;
-          S = odd;
+        for (int u = 0; u < U; ++u) {
+          const int t = t0 + u * blockDim.x;
+          ok[u] = t < tot;
+          if (!ok[u]) continue;
+          int q = 0, r = t;
+          while (r >= bx[q].total) r -= bx[q++].total;
+          const Box& B = bx[q];
+          cc[u][2] = B.a[2] + B.b[2] * (r % B.cnt[2]);
+          r /= B.cnt[2];
+          cc[u][1] = B.a[1] + B.b[1] * (r % B.cnt[1]);
+          cc[u][0] = B.a[0] + B.b[0] * (r / B.cnt[1]);
+          SS[u] = B.S;
+          unsigned par = 0;
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+            if (SS[u] & (1u << d)) par += (unsigned)(((cc[u][d] >> sh) - 1) >> 1);
+          bb[u] = same && (par & 1u);
+          ok[u] = (int)bb[u] == half;
+          if (!ok[u]) continue;
+          ii[u] = cc[u][0] * f.st[0] + cc[u][1] * f.st[1] + cc[u][2];
+          xv[u] = xval(f, cc[u]);
         }
-        unsigned par = 0;
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
-          if (S & (1u << d)) par += (unsigned)(((cc[d] >> sh) - 1) >> 1);
-        const bool in_b = same && (par & 1u);
-        if ((int)in_b != half) continue;
-        const int i = cc[0] * f.st[0] + cc[1] * f.st[1] + cc[2];
-        float p;
-        if (!md) {
-          p = predict_smem(R, i, s * f.st[ps], cc[ps] >> sh, line[ps], kind,
-                           in_b);
-        } else {
-          float acc = 0.0f;
-          bool first = true;
+        for (int u = 0; u < U; ++u) {
+          if (!ok[u]) continue;
+          const unsigned S = SS[u];
+          const int i = ii[u];
+          float p;
+          if (!md) {
+            const int ps = __ffs(S) - 1;
+            p = predict_smem(R, i, s * f.st[ps], cc[u][ps] >> sh, line[ps], kind,
+                             bb[u]);
+          } else {
+            float acc = 0.0f;
+            bool first = true;
 #pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            if (!(S & (1u << d))) continue;
-            const float pd = predict_smem(R, i, s * f.st[d], cc[d] >> sh,
-                                          line[d], kind, in_b);
-            const float t = __fmul_rn(c.mdw[S][d], pd);
-            acc = first ? t : __fadd_rn(acc, t);
-            first = false;
+            for (int d = 0; d < 3; ++d) {
+              if (!(S & (1u << d))) continue;
+              const float pd = predict_smem(R, i, s * f.st[d], cc[u][d] >> sh,
+                                            line[d], kind, bb[u]);
+              const float tw = __fmul_rn(c.mdw[S][d], pd);
+              acc = first ? tw : __fadd_rn(acc, tw);
+              first = false;
+            }
+            p = acc;
           }
-          p = acc;
+          float rv;
+          const unsigned code = quantize(xv[u], p, el, inv2, twoe, rv);
+          R[i] = rv;
+          if (score_on) score += err_fixed(__fsub_rn(xv[u], p), inv_el);
+          if (kHist) atomicAdd(hist + code, 1u);
+          if (code == 0u) ++nout;
         }
-        const float xv = xval(f, cc);
-        float rv;
-        const unsigned code = quantize(xv, p, el, inv2, twoe, rv);
-        R[i] = rv;
-        if (score_on) score += err_fixed(__fsub_rn(xv, p), inv_el);
-        if (kHist) atomicAdd(hist + code, 1u);
-        if (code == 0u) ++nout;
       }
       __syncthreads();
     }
@@ -479,16 +534,18 @@ __global__ void __launch_bounds__(kBlockThreads)
   if (threadIdx.x == 0) bmap[blockIdx.x] = bestc;
 }
 
-// Huffman bits of a histogram: sum of count * code length
+// Huffman bits of histogram v: sum of count * code length (block v)
 __global__ void __launch_bounds__(1024)
-    k_tune_cost(const uint32_t* __restrict__ hist,
+    k_tune_cost(const uint32_t* __restrict__ hists,
                 const uint8_t* __restrict__ lens, unsigned long long* cost) {
   __shared__ unsigned long long red[32];
+  const uint32_t* hist = hists + (size_t)blockIdx.x * 65536;
+  const uint8_t* ln = lens + (size_t)blockIdx.x * 65536;
   unsigned long long acc = 0;
   for (int i = threadIdx.x; i < 65536; i += blockDim.x)
-    acc += (unsigned long long)hist[i] * lens[i];
+    acc += (unsigned long long)hist[i] * ln[i];
   acc = block_sum(acc, red);
-  if (threadIdx.x == 0) *cost = acc;
+  if (threadIdx.x == 0) cost[blockIdx.x] = acc;
 }
 
 void set_smem_attr() {
@@ -587,9 +644,9 @@ void launch_tune_blockwise(const float* x, const TuneGeom& g, int bs, int Q,
       x, g, bg, base, allow, bmap);
 }
 
-void launch_tune_cost(const uint32_t* hist, const uint8_t* lens,
-                      unsigned long long* cost, cudaStream_t s) {
-  k_tune_cost<<<1, 1024, 0, s>>>(hist, lens, cost);
+void launch_tune_cost(const uint32_t* hists, const uint8_t* lens,
+                      unsigned long long* cost, int nvar, cudaStream_t s) {
+  if (nvar > 0) k_tune_cost<<<nvar, 1024, 0, s>>>(hists, lens, cost);
 }
 
 }  // namespace hpez

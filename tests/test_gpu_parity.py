@@ -251,3 +251,30 @@ def test_per_pass_path_still_exact(opts, oracle):
     x = fields.grf((40, 41, 42), seed=8)
     _check(opts, oracle, x, 1e-3, 1)
     _check(opts, oracle, x, 1e-3, 1, same_level=1, interp=2, order=(2, 0, 1))
+
+
+@pytest.mark.parametrize("shape,frozen", [((37, 50, 67), -1), ((129, 257), -1),
+                                          ((40, 36, 44), 1), ((3000,), -1)])
+@pytest.mark.parametrize("interp,same", [(0, 0), (1, 0), (2, 0), (0, 1)])
+def test_md_levels(gpu, oracle, shape, frozen, interp, same):
+    """Multi-dimensional levels (one launch per sub-pass) in 1D, 2D, 3D and
+    with a frozen dimension."""
+    from paper_2311_12133_gb300 import fields
+    if len(shape) == 1:
+        x = np.cumsum(np.random.default_rng(5).normal(0, 1, shape[0])).astype(np.float32)
+    else:
+        x = fields.grf(shape, seed=len(shape) * 10 + interp)
+    _check(gpu, oracle, x, 1e-3, 1, interp=interp, paradigm=1, same_level=same,
+           frozen_dim=frozen, md_inv_var=(1.0, 2.5, 0.7))
+
+
+@pytest.mark.parametrize("code", [0, 1, 2, 5, 6])
+@pytest.mark.parametrize("paradigm", [0, 1])
+def test_uniform_blockmap(gpu, oracle, code, paradigm):
+    """A block map with one code everywhere runs as that interpolator."""
+    from paper_2311_12133_gb300 import fields, hpez
+    shape = (48, 40, 36)
+    x = fields.bumps(shape, seed=code)
+    nb = hpez.hpez_blockmap_size(shape, 16)
+    _check(gpu, oracle, x, 1e-3, 1, blockmap=np.full(nb, code, np.uint8),
+           block_size=16, paradigm=paradigm)
