@@ -4,8 +4,10 @@
 One step = compress then decompress one 512x512x512 float32 Gaussian random
 field with a k^-5/3 power spectrum (turbulence-like stand-in for the
 paper's JHTDB field, which is not available) at value-range relative error
-bound 1e-3, with the default predictor (cubic not-a-knot, 1D-style order
-0,1,2, anchor stride 32), through the C-ABI (libhpez.so).
+bound 1e-3, with full auto-tuning: hpez_compress_auto runs the Sec. 6 tuner
+(statistics, per-level candidates, alpha/beta, dimension freezing, Lorenzo
+test, block-wise map) and compresses with the tuned predictor; then
+hpez_decompress.  Everything goes through the C-ABI (libhpez.so).
 
 value     input GB/s of the round trip: sum over ranks of 4 N bytes per step
           divided by the max-over-ranks time per step (CUDA events)
@@ -190,14 +192,15 @@ def ncu_traffic(phase: str):
 # CPU oracle baseline (rank 0, N = 1)
 # ---------------------------------------------------------------------------
 def cpu_oracle_sample(x_slab, eb, rounds=1):
-    """Compress + decompress the slab with the CPU oracle; returns
+    """Tune + compress + decompress the slab with the CPU oracle; returns
     (bytes processed, seconds)."""
     from oracle import oracle as O
     O.build()
     t0 = time.perf_counter()
     nbytes = 0
     for _ in range(rounds):
-        s, _, _, _ = O.compress(x_slab, eb, O.EB_REL)
+        cfg, _ = O.tune(x_slab, eb, O.EB_REL)
+        s, _, _, _ = O.compress(x_slab, eb, O.EB_REL, cfg)
         O.decompress(s)
         nbytes += x_slab.nbytes
     return nbytes, time.perf_counter() - t0
@@ -229,7 +232,7 @@ def run_reference(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"grf k^-5/3 float32 slab {'x'.join(map(str, slab))} of the "
                                f"{'x'.join(map(str, shape))} workload, rel eb {args.eb}, "
-                               "compress+decompress by the single-threaded CPU oracle"},
+                               "tune+compress+decompress by the single-threaded CPU oracle"},
         "cpu_baseline": {"value": round(value, 6), "unit": "GB/s", "cores": 1,
                          "kind": "oracle",
                          "sample": f"{'x'.join(map(str, slab))} slab per step"},
@@ -455,8 +458,9 @@ def main():
     sptr = stream.cuda_stream
 
     def step():
-        size = hpez.hpez_compress(ctx.handle, x.data_ptr(), shape, hpez.HPEZ_EB_REL,
-                                  args.eb, None, cbuf.data_ptr(), cap, sptr)
+        size = hpez.hpez_compress_auto(ctx.handle, x.data_ptr(), shape,
+                                       hpez.HPEZ_EB_REL, args.eb, None,
+                                       cbuf.data_ptr(), cap, sptr)
         hpez.hpez_decompress(ctx.handle, cbuf.data_ptr(), size, y.data_ptr(), N, sptr)
         return size
 
@@ -479,8 +483,9 @@ def main():
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
     ev[0].record(stream)
     for k in range(args.steps):
-        size = hpez.hpez_compress(ctx.handle, x.data_ptr(), shape, hpez.HPEZ_EB_REL,
-                                  args.eb, None, cbuf.data_ptr(), cap, sptr)
+        size = hpez.hpez_compress_auto(ctx.handle, x.data_ptr(), shape,
+                                       hpez.HPEZ_EB_REL, args.eb, None,
+                                       cbuf.data_ptr(), cap, sptr)
         ev[2 * k + 1].record(stream)
         hpez.hpez_decompress(ctx.handle, cbuf.data_ptr(), size, y.data_ptr(), N, sptr)
         ev[2 * k + 2].record(stream)
@@ -517,8 +522,13 @@ def main():
     assert err <= e_abs, f"error bound violated: {err} > {e_abs}"
 
     peak, peak_kind = measured_peaks()
-    dom = max(phases.items(), key=lambda kv: kv[1][0])
+    # the roofline is taken on the dominant phase of the HBM-bound data path
+    # (levels, Huffman); the tuner's phases run on L2-resident samples and
+    # are reported with their share of the step
+    data_phases = {k: v for k, v in phases.items() if not k.startswith("tune_")}
+    dom = max(data_phases.items(), key=lambda kv: kv[1][0])
     dom_name, (dom_ms, dom_cnt) = dom
+    tune_ms = sum(v[0] for k, v in phases.items() if k.startswith("tune_")) / args.steps
     dom_bytes = phase_bytes(dom_name, shape, A, size)
     achieved = dom_bytes / (dom_ms / dom_cnt / 1e3) / 1e9 if dom_bytes else None
     roofline = {"bound": "hbm", "phase": dom_name,
@@ -527,7 +537,9 @@ def main():
                 "frac": round(achieved / peak, 4) if achieved else None,
                 "traffic": ncu_traffic(dom_name),
                 "algorithmic_bytes": dom_bytes,
-                "launch_ms": round(dom_ms / dom_cnt, 4)}
+                "launch_ms": round(dom_ms / dom_cnt, 4),
+                "tuner_ms_per_step": round(tune_ms, 3),
+                "tuner_share": round(tune_ms / ms_per_step, 3)}
     phase_report = {k: {"ms": round(v[0] / v[1], 4), "n": v[1],
                         "GBps": round(phase_bytes(k, shape, A, size) / (v[0] / v[1] / 1e3) / 1e9, 1)
                         if phase_bytes(k, shape, A, size) else None}
@@ -540,13 +552,15 @@ def main():
         hout = torch.empty(cap, dtype=torch.uint8).pin_memory().numpy()
         hy = torch.empty(N, dtype=torch.float32).pin_memory().numpy()
         for _ in range(2):
-            sz = hpez.hpez_compress_host(ctx.handle, hx, hpez.HPEZ_EB_REL, args.eb, None, hout, sptr)
+            sz = hpez.hpez_compress_auto_host(ctx.handle, hx, hpez.HPEZ_EB_REL, args.eb, None,
+                                              hout, sptr)
             hpez.hpez_decompress_host(ctx.handle, hout, sz, hy, sptr)
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            sz = hpez.hpez_compress_host(ctx.handle, hx, hpez.HPEZ_EB_REL, args.eb, None, hout, sptr)
+            sz = hpez.hpez_compress_auto_host(ctx.handle, hx, hpez.HPEZ_EB_REL, args.eb, None,
+                                              hout, sptr)
             hpez.hpez_decompress_host(ctx.handle, hout, sz, hy, sptr)
         e2e_s = (time.perf_counter() - t0) / args.steps
         te = torch.tensor([e2e_s], dtype=torch.float64, device=x.device)
@@ -562,8 +576,30 @@ def main():
         nb, secs = cpu_oracle_sample(slab, args.eb, rounds=2)
         cpu = {"value": round(nb / secs / 1e9, 6), "unit": "GB/s", "cores": 1,
                "kind": "oracle",
-               "sample": f"2 compress+decompress round trips of the first 64 planes "
+               "sample": f"2 tune+compress+decompress round trips of the first 64 planes "
                          f"({'x'.join(map(str, slab.shape))}) of the same field, {secs:.1f} s"}
+
+    # the same field with the default predictor (no tuning), for reference
+    def default_step():
+        sz = hpez.hpez_compress(ctx.handle, x.data_ptr(), shape, hpez.HPEZ_EB_REL,
+                                args.eb, None, cbuf.data_ptr(), cap, sptr)
+        hpez.hpez_decompress(ctx.handle, cbuf.data_ptr(), sz, y.data_ptr(), N, sptr)
+        return sz
+    for _ in range(3):
+        dsz = default_step()
+    torch.cuda.synchronize()
+    d0 = torch.cuda.Event(enable_timing=True)
+    d1 = torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    for _ in range(args.steps):
+        dsz = default_step()
+    d1.record(stream)
+    torch.cuda.synchronize()
+    dms = d0.elapsed_time(d1) / args.steps
+    default_pred = {"value": round(world * 4 * N / (dms / 1e3) / 1e9, 3), "unit": "GB/s",
+                    "ms_per_step": round(dms, 4),
+                    "compression_ratio": round(4 * N / dsz, 3),
+                    "predictor": "cubic not-a-knot, 1D-style order 0,1,2, A=32, no tuning"}
 
     batched = served = None
     if rank == 0 and world == 1 and not args.no_batched:
@@ -580,8 +616,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"grf k^-5/3 float32 {'x'.join(map(str, shape))} per GPU, "
-                                   f"rel eb {args.eb}, compress+decompress, default predictor "
-                                   "(cubic not-a-knot, 1D-style order 0,1,2, A=32)",
+                                   f"rel eb {args.eb}, full auto-tuning + compress "
+                                   "(hpez_compress_auto) + decompress",
                        "global_batch": world, "parallelism": f"replicas{world}",
                        "l2": f"input {4 * N / 1e6:.0f} MB > L2 {L2_BYTES / 1e6:.0f} MB, no flush"},
             "compress_gbps": round(world * 4 * N / (comp_ms / args.steps / 1e3) / 1e9, 3),
@@ -592,6 +628,7 @@ def main():
             "roofline": roofline, "phases": phase_report,
             "gpu_launches": int(launches),
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+            "default_predictor": default_pred,
             "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)

@@ -339,6 +339,23 @@ HPEZ_API uint64_t hpez_blockmap_size(int ndim, const uint64_t* dims, int block_s
  * <= 200 KiB, else UNSUPPORTED.  Errors: INVALID_ARG, NONFINITE_INPUT
  * (relative mode), OUT_TOO_SMALL (block map), UNSUPPORTED, NO_MEMORY,
  * CUDA.  Synchronizes `stream` several times (not graph-capturable). */
+/* Compress with full auto-tuning (the paper's compression: Sec. 6 tuning,
+ * then Sec. 4-5 with the tuned theta): hpez_tune (tp NULL = defaults) then
+ * hpez_compress.  Arguments and errors as in those two calls; h_report is
+ * optional. */
+HPEZ_API int hpez_compress_auto(hpez_ctx* ctx, const float* d_in, int ndim,
+                                const uint64_t* dims, int eb_mode, double eb,
+                                const hpez_tune_params* tp, void* d_out,
+                                uint64_t out_cap, uint64_t* h_out_size,
+                                hpez_tune_report* h_report, void* stream);
+/* The same from host memory: the field is copied to the device, tuned and
+ * compressed, and the stream copied back.  Synchronizes `stream`. */
+HPEZ_API int hpez_compress_auto_host(hpez_ctx* ctx, const float* h_in, int ndim,
+                                     const uint64_t* dims, int eb_mode, double eb,
+                                     const hpez_tune_params* tp, void* h_out,
+                                     uint64_t out_cap, uint64_t* h_out_size,
+                                     void* stream);
+
 HPEZ_API int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim,
                        const uint64_t* dims, int eb_mode, double eb,
                        const hpez_tune_params* tp, hpez_config* h_cfg,

@@ -410,13 +410,14 @@ typedef struct {
   uint64_t nout;       /* escapes among predicted points */
 } sweep;
 
-/* Fixed-point error measure of the tuner: |d| / e_l as an IEEE double,
- * capped at 2^24, in units of 1/256, floored.  Integer sums of it do not
- * depend on the summation order. */
-static uint64_t err_fixed(float d, double inv_el) {
-  double v = fabs((double)d) * inv_el;
-  v = fmin(v, 16777216.0);
-  return (uint64_t)floor(v * 256.0);
+/* Fixed-point error measure of the tuner: |d| * (1/e_l) in binary32 (the
+ * reciprocal rounded once from double), capped at 2^24 - 1, in units of
+ * 1/256 (exact scaling), floored: a 32-bit value per point.  Integer sums
+ * of it do not depend on the summation order. */
+static uint64_t err_fixed(float d, float inv_el) {
+  float v = fabsf(d) * inv_el;
+  v = fminf(v, 16777215.0f);
+  return (uint64_t)(uint32_t)floorf(v * 256.0f);
 }
 
 static float load_known(sweep* w, uint64_t idx) {
@@ -501,7 +502,8 @@ static void process_point(sweep* w, int l, uint64_t i, const uint64_t c[3],
                                w->twoe[l - 1], &r);
     w->recon[i] = r;
     if (w->score)
-      w->score[l - 1] += err_fixed(w->x[i] - p, 1.0 / (double)w->el[l - 1]);
+      w->score[l - 1] +=
+          err_fixed(w->x[i] - p, (float)(1.0 / (double)w->el[l - 1]));
     if (w->chist) w->chist[w->codes[i]]++;
     if (w->codes[i] == 0) w->nout++;
   } else {

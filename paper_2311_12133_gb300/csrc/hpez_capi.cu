@@ -636,6 +636,23 @@ int parse_stream_header(const uint8_t* h, uint64_t in_size, StreamInfo& si) {
   si.obm = obm;
   return HPEZ_OK;
 }
+int ensure_io(void** buf, size_t* cap, size_t bytes) {
+  if (bytes <= *cap) return HPEZ_OK;
+  if (*buf) {
+    cudaDeviceSynchronize();
+    cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+  }
+  if (cudaMalloc(buf, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *buf = nullptr;
+    return HPEZ_ERR_NO_MEMORY;
+  }
+  *cap = bytes;
+  return HPEZ_OK;
+}
+
 }  // namespace host
 }  // namespace hpez
 
@@ -1147,22 +1164,6 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   return HPEZ_OK;
 }
 
-static int ensure_io(void** buf, size_t* cap, size_t bytes) {
-  if (bytes <= *cap) return HPEZ_OK;
-  if (*buf) {
-    cudaDeviceSynchronize();
-    cudaFree(*buf);
-    *buf = nullptr;
-    *cap = 0;
-  }
-  if (cudaMalloc(buf, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    *buf = nullptr;
-    return HPEZ_ERR_NO_MEMORY;
-  }
-  *cap = bytes;
-  return HPEZ_OK;
-}
 
 int hpez_compress_host(hpez_ctx* ctx, const float* h_in, int ndim,
                        const uint64_t* dims, int eb_mode, double eb,

@@ -89,6 +89,7 @@ struct hpez_ctx {
   size_t io_in_cap = 0;
   void* io_out = nullptr;
   size_t io_out_cap = 0;
+  std::vector<uint8_t> h_bmap;  // block map of the last auto-tuned compress
 };
 
 namespace hpez {
@@ -185,6 +186,8 @@ int check_config(const Plan& p, const hpez_config& c);
 // Eq. 14 weight of slot `slot` within the slot mask S
 float md_weight(const Plan& p, const hpez_config& c, unsigned S, int slot);
 int ensure_scratch(hpez_ctx* ctx, size_t bytes);
+// device staging buffer of the host-memory entry points, grown on demand
+int ensure_io(void** buf, size_t* cap, size_t bytes);
 int map_status(int st);
 int cuda_check(cudaError_t e);
 void default_config(int ndim, hpez_config* c);

@@ -339,7 +339,7 @@ struct TuneCfg {
   uint8_t ord[kMaxLevels][3]; // 1D-style order as slots
   double alpha, beta;         // Eq. 15 (the device fills el/inv2/twoe)
   float el[kMaxLevels], inv2[kMaxLevels], twoe[kMaxLevels];
-  double inv_el[kMaxLevels];  // 1 / e_l for the error scores
+  float inv_el[kMaxLevels];   // (float)(1 / e_l) for the error scores
   float mdw[8][3];            // Eq. 14 weight per odd-slot mask and slot
 };
 

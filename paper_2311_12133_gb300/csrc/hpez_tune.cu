@@ -246,6 +246,8 @@ int tune_global(Call& k, int frozen, const double inv_var[3],
   TuneGeom g;
   const int nblk = sample_geometry(p, tp, g);
   if (tune_test_smem(g) > kTuneSmemMax) return HPEZ_ERR_UNSUPPORTED;
+  // the Lorenzo wavefront keeps at most 4 (i0, i1) pairs per thread
+  if ((uint64_t)g.ext[0] * g.ext[1] > 4096) return HPEZ_ERR_UNSUPPORTED;
   if (rep && slot == 0) rep->n_sample_blocks = (uint32_t)nblk;
   uint64_t& nl = k.ctx->launches;
   PhaseProfiler& prof = k.ctx->prof;
@@ -590,6 +592,50 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
   prof.collect();
   *h_cfg = out;
   return HPEZ_OK;
+}
+
+int hpez_compress_auto(hpez_ctx* ctx, const float* d_in, int ndim,
+                       const uint64_t* dims, int eb_mode, double eb,
+                       const hpez_tune_params* tp, void* d_out, uint64_t out_cap,
+                       uint64_t* h_out_size, hpez_tune_report* h_report,
+                       void* stream) {
+  if (!ctx || !dims || ndim < 1 || ndim > 3) return HPEZ_ERR_INVALID_ARG;
+  const int bs = tp ? tp->block_size : 32;
+  const uint64_t nbm = hpez_blockmap_size(ndim, dims, bs);
+  std::vector<uint8_t>& bm = ctx->h_bmap;
+  if (bm.size() < nbm) bm.resize(nbm);
+  hpez_config cfg;
+  int rc = hpez_tune(ctx, d_in, ndim, dims, eb_mode, eb, tp, &cfg,
+                     bm.empty() ? nullptr : bm.data(), bm.size(), h_report, stream);
+  if (rc) return rc;
+  return hpez_compress(ctx, d_in, ndim, dims, eb_mode, eb, &cfg, d_out, out_cap,
+                       h_out_size, stream);
+}
+
+int hpez_compress_auto_host(hpez_ctx* ctx, const float* h_in, int ndim,
+                            const uint64_t* dims, int eb_mode, double eb,
+                            const hpez_tune_params* tp, void* h_out,
+                            uint64_t out_cap, uint64_t* h_out_size, void* stream) {
+  if (!ctx || !h_in || !h_out || !h_out_size || !dims || ndim < 1 || ndim > 3)
+    return HPEZ_ERR_INVALID_ARG;
+  uint64_t N = 1;
+  for (int d = 0; d < ndim; ++d) N *= dims[d];
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = ensure_io(&ctx->io_in, &ctx->io_in_cap, N * sizeof(float));
+  if (!rc) rc = ensure_io(&ctx->io_out, &ctx->io_out_cap, out_cap);
+  if (!rc)
+    rc = cuda_check(cudaMemcpyAsync(ctx->io_in, h_in, N * sizeof(float),
+                                    cudaMemcpyHostToDevice, s));
+  if (!rc)
+    rc = hpez_compress_auto(ctx, static_cast<const float*>(ctx->io_in), ndim, dims,
+                            eb_mode, eb, tp, ctx->io_out, out_cap, h_out_size,
+                            nullptr, stream);
+  if (!rc)
+    rc = cuda_check(cudaMemcpyAsync(h_out, ctx->io_out, *h_out_size,
+                                    cudaMemcpyDeviceToHost, s));
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(s));
+  return rc;
 }
 
 }  // extern "C"

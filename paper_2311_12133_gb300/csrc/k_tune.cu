@@ -16,16 +16,24 @@
 namespace hpez {
 namespace {
 
-constexpr int kTuneThreads = 512;
+constexpr int kTuneThreads = 1024;
 constexpr int kBlockThreads = 128;
 constexpr size_t kTuneSmemMax = 200 * 1024;
 
-// floor(min(|d| / e_l, 2^24) * 256): the per-point error score
-__device__ __forceinline__ unsigned long long err_fixed(float d,
-                                                        double inv_el) {
-  double v = __dmul_rn(fabs((double)d), inv_el);
-  v = fmin(v, 16777216.0);
-  return (unsigned long long)floor(__dmul_rn(v, 256.0));
+// floor(min(|d| * (1/e_l), 2^24 - 1) * 256) in binary32: the per-point
+// error score (the scaling by 256 is exact, the result fits 32 bits)
+__device__ __forceinline__ unsigned err_fixed(float d, float inv_el) {
+  float v = __fmul_rn(fabsf(d), inv_el);
+  v = fminf(v, 16777215.0f);
+  return (unsigned)floorf(__fmul_rn(v, 256.0f));
+}
+
+// r / n for r * n < 2^32 with a precomputed m = ceil(2^32 / n) (m = 0: n = 1)
+__device__ __forceinline__ unsigned fdiv(unsigned r, unsigned m) {
+  return m ? __umulhi(r, m) : r;
+}
+__host__ __device__ __forceinline__ unsigned fdiv_magic(unsigned n) {
+  return n <= 1 ? 0u : (unsigned)((0x100000000ull + n - 1) / n);
 }
 
 // floor(min(|d| / e, 2^16)^2 * 256): the statistics' squared error
@@ -123,7 +131,7 @@ __global__ void k_tune_params(TuneCfg* cfgs, int nvar, int L,
     c.el[l - 1] = el;
     c.twoe[l - 1] = __fmul_rn(2.0f, el);
     c.inv2[l - 1] = __double2float_rn(__ddiv_rn(1.0, __dmul_rn(2.0, (double)el)));
-    c.inv_el[l - 1] = __ddiv_rn(1.0, (double)el);
+    c.inv_el[l - 1] = __double2float_rn(__ddiv_rn(1.0, (double)el));
   }
 }
 
@@ -243,6 +251,7 @@ __device__ __forceinline__ float predict_smem(const float* R, int i, int st,
 // points to the thread's accumulators.
 struct Box {
   int a[3], b[3], cnt[3];
+  unsigned mg[3];  // division magic of cnt
   int total;
   unsigned S;
 };
@@ -273,6 +282,87 @@ __device__ __forceinline__ void make_box(Box& bx, const Sub& f,
       bx.cnt[d] = (n - 1) / (2 * s) + 1;
     }
     bx.total *= bx.cnt[d];
+    bx.mg[d] = fdiv_magic((unsigned)bx.cnt[d]);
+  }
+}
+
+// exact bound check with a fast accept: rn(r - x) strictly inside the
+// bound implies the exact difference is inside (rounding is monotonic)
+__device__ __forceinline__ unsigned quantize_t(float x, float p, float el,
+                                               float inv2, float twoe,
+                                               float& recon) {
+  const float diff = __fsub_rn(x, p);
+  const float m = __fadd_rn(__fmul_rn(fabsf(diff), inv2), 0.5f);
+  if (m < 32768.0f) {
+    const int k = __float2int_rz(m);
+    const int q = diff < 0.0f ? -k : k;
+    const float r = __fadd_rn(p, __fmul_rn(__int2float_rn(q), twoe));
+    if (fabsf(__fsub_rn(r, x)) < el || within_bound(r, x, el)) {
+      recon = r;
+      return (unsigned)(q + kRadius);
+    }
+  }
+  recon = x;
+  return 0u;
+}
+
+// The points of one pass (or same-level half) of a level, specialized on
+// the interpolator and the paradigm, which are uniform within a level.
+template <int KIND, bool MD, bool kHist>
+__device__ void sweep_pass(float* R, const Sub& f, const Box* bx, int nb,
+                           int tot, int half, bool same, int sh,
+                           const int line[3], const TuneCfg& c, int l,
+                           bool score_on, unsigned long long& score,
+                           uint32_t* hist, unsigned long long& nout) {
+  const int s = 1 << sh;
+  const float el = c.el[l - 1], inv2 = c.inv2[l - 1], twoe = c.twoe[l - 1];
+  const float inv_el = c.inv_el[l - 1];
+  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+    int q = 0, r = t;
+    while (q + 1 < nb && r >= bx[q].total) r -= bx[q++].total;
+    const Box& B = bx[q];
+    const unsigned r1 = fdiv((unsigned)r, B.mg[2]);
+    int cc[3];
+    cc[2] = B.a[2] + B.b[2] * (r - (int)r1 * B.cnt[2]);
+    const unsigned r0 = fdiv(r1, B.mg[1]);
+    cc[1] = B.a[1] + B.b[1] * ((int)r1 - (int)r0 * B.cnt[1]);
+    cc[0] = B.a[0] + B.b[0] * (int)r0;
+    const unsigned S = B.S;
+    bool in_b = false;
+    if (KIND != LINEAR && same) {
+      unsigned par = 0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        if (S & (1u << d)) par += (unsigned)(((cc[d] >> sh) - 1) >> 1);
+      in_b = (par & 1u) != 0;
+      if ((int)in_b != half) continue;
+    }
+    const int i = cc[0] * f.st[0] + cc[1] * f.st[1] + cc[2];
+    const float xv = xval(f, cc);
+    float p;
+    if (!MD) {
+      const int ps = S == 1u ? 0 : (S == 2u ? 1 : 2);
+      p = predict_smem(R, i, s * f.st[ps], cc[ps] >> sh, line[ps], KIND, in_b);
+    } else {
+      float acc = 0.0f;
+      bool first = true;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (!(S & (1u << d))) continue;
+        const float pd = predict_smem(R, i, s * f.st[d], cc[d] >> sh, line[d],
+                                      KIND, in_b);
+        const float tw = __fmul_rn(c.mdw[S][d], pd);
+        acc = first ? tw : __fadd_rn(acc, tw);
+        first = false;
+      }
+      p = acc;
+    }
+    float rv;
+    const unsigned code = quantize_t(xv, p, el, inv2, twoe, rv);
+    R[i] = rv;
+    if (score_on) score += err_fixed(__fsub_rn(xv, p), inv_el);
+    if (kHist) atomicAdd(hist + code, 1u);
+    if (code == 0u) ++nout;
   }
 }
 
@@ -292,8 +382,6 @@ __device__ void sweep_level(float* R, const Sub& f, const int interp[3],
   const int kind = c.kind[l - 1];
   const bool md = c.md[l - 1] != 0;
   const bool same = c.same[l - 1] != 0 && kind != LINEAR;
-  const float el = c.el[l - 1], inv2 = c.inv2[l - 1], twoe = c.twoe[l - 1];
-  const double inv_el = c.inv_el[l - 1];
   for (int pj = 0; pj < k; ++pj) {
     Box bx[3];
     int nb = 0;
@@ -310,69 +398,19 @@ __device__ void sweep_level(float* R, const Sub& f, const int interp[3],
     int tot = 0;
     for (int q = 0; q < nb; ++q) tot += bx[q].total;
     for (int half = 0; half < (same ? 2 : 1); ++half) {
-      // four points per thread and round: their input loads are issued
-      // together before any of them is predicted
-      constexpr int U = 4;
-      for (int t0 = threadIdx.x; t0 < tot; t0 += U * blockDim.x) {
-        int cc[U][3], ii[U];
-        unsigned SS[U];
-        bool ok[U], bb[U];
-        float xv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int t = t0 + u * blockDim.x;
-          ok[u] = t < tot;
-          if (!ok[u]) continue;
-          int q = 0, r = t;
-          while (r >= bx[q].total) r -= bx[q++].total;
-          const Box& B = bx[q];
-          cc[u][2] = B.a[2] + B.b[2] * (r % B.cnt[2]);
-          r /= B.cnt[2];
-          cc[u][1] = B.a[1] + B.b[1] * (r % B.cnt[1]);
-          cc[u][0] = B.a[0] + B.b[0] * (r / B.cnt[1]);
-          SS[u] = B.S;
-          unsigned par = 0;
-#pragma unroll
-          for (int d = 0; d < 3; ++d)
-            if (SS[u] & (1u << d)) par += (unsigned)(((cc[u][d] >> sh) - 1) >> 1);
-          bb[u] = same && (par & 1u);
-          ok[u] = (int)bb[u] == half;
-          if (!ok[u]) continue;
-          ii[u] = cc[u][0] * f.st[0] + cc[u][1] * f.st[1] + cc[u][2];
-          xv[u] = xval(f, cc[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (!ok[u]) continue;
-          const unsigned S = SS[u];
-          const int i = ii[u];
-          float p;
-          if (!md) {
-            const int ps = __ffs(S) - 1;
-            p = predict_smem(R, i, s * f.st[ps], cc[u][ps] >> sh, line[ps], kind,
-                             bb[u]);
-          } else {
-            float acc = 0.0f;
-            bool first = true;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-              if (!(S & (1u << d))) continue;
-              const float pd = predict_smem(R, i, s * f.st[d], cc[u][d] >> sh,
-                                            line[d], kind, bb[u]);
-              const float tw = __fmul_rn(c.mdw[S][d], pd);
-              acc = first ? tw : __fadd_rn(acc, tw);
-              first = false;
-            }
-            p = acc;
-          }
-          float rv;
-          const unsigned code = quantize(xv[u], p, el, inv2, twoe, rv);
-          R[i] = rv;
-          if (score_on) score += err_fixed(__fsub_rn(xv[u], p), inv_el);
-          if (kHist) atomicAdd(hist + code, 1u);
-          if (code == 0u) ++nout;
-        }
+#define HPEZ_SWEEP(K, M)                                                      \
+  sweep_pass<K, M, kHist>(R, f, bx, nb, tot, half, same, sh, line, c, l,      \
+                          score_on, score, hist, nout)
+      if (md) {
+        if (kind == LINEAR) HPEZ_SWEEP(LINEAR, true);
+        else if (kind == CUBIC_NAK) HPEZ_SWEEP(CUBIC_NAK, true);
+        else HPEZ_SWEEP(CUBIC_NAT, true);
+      } else {
+        if (kind == LINEAR) HPEZ_SWEEP(LINEAR, false);
+        else if (kind == CUBIC_NAK) HPEZ_SWEEP(CUBIC_NAK, false);
+        else HPEZ_SWEEP(CUBIC_NAT, false);
       }
+#undef HPEZ_SWEEP
       __syncthreads();
     }
   }
@@ -436,9 +474,32 @@ __global__ void __launch_bounds__(kTuneThreads)
   unsigned long long no = 0;
   const int n0 = f.n[0], n1 = f.n[1], n2 = f.n[2];
   const int T = (n0 - 1) + (n1 - 1) + (n2 - 1);
+  const int npair = n0 * n1;
+  const unsigned mg1 = fdiv_magic((unsigned)n1);
+  // a thread's pairs (i0, i1) are q = tid + k * blockDim (at most kP); the
+  // input values of plane t + 1 are loaded while plane t is computed
+  constexpr int kP = 4;
+  float xcur[kP], xnext[kP];
+  auto load_plane = [&](int t, float* xv) {
+#pragma unroll
+    for (int k = 0; k < kP; ++k) {
+      const int q = threadIdx.x + k * blockDim.x;
+      xv[k] = 0.0f;
+      if (q >= npair) continue;
+      const int i0 = (int)fdiv((unsigned)q, mg1), i1 = q - i0 * n1, i2 = t - i0 - i1;
+      if (i2 < 0 || i2 >= n2) continue;
+      const int cc[3] = {i0, i1, i2};
+      xv[k] = xval(f, cc);
+    }
+  };
+  load_plane(0, xcur);
   for (int t = 0; t <= T; ++t) {
-    for (int q = threadIdx.x; q < n0 * n1; q += blockDim.x) {
-      const int i0 = q / n1, i1 = q % n1, i2 = t - i0 - i1;
+    if (t < T) load_plane(t + 1, xnext);
+#pragma unroll
+    for (int k = 0; k < kP; ++k) {
+      const int q = threadIdx.x + k * blockDim.x;
+      if (q >= npair) continue;
+      const int i0 = (int)fdiv((unsigned)q, mg1), i1 = q - i0 * n1, i2 = t - i0 - i1;
       if (i2 < 0 || i2 >= n2) continue;
       float acc = 0.0f;
       for (int a = 0; a <= lim[0]; ++a)
@@ -452,14 +513,15 @@ __global__ void __launch_bounds__(kTuneThreads)
               v = R[((i0 - a) * n1 + (i1 - b)) * n2 + (i2 - cz)];
             acc = __fadd_rn(acc, __fmul_rn(wgt, v));
           }
-      const int cc[3] = {i0, i1, i2};
       float rv;
-      const unsigned code = quantize(xval(f, cc), acc, e, inv2, twoe, rv);
+      const unsigned code = quantize(xcur[k], acc, e, inv2, twoe, rv);
       R[(i0 * n1 + i1) * n2 + i2] = rv;
       atomicAdd(h + code, 1u);
       if (code == 0u) ++no;
     }
     __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kP; ++k) xcur[k] = xnext[k];
   }
   no = block_sum(no, red);
   if (threadIdx.x == 0 && no) atomicAdd(nout + blockIdx.y, no);

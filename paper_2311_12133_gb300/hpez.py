@@ -172,6 +172,15 @@ def _load():
             "hpez_default_tune_params": (ctypes.c_int,
                                          [ctypes.POINTER(hpez_tune_params)]),
             "hpez_blockmap_size": (u64, [ctypes.c_int, u64p, ctypes.c_int]),
+            "hpez_compress_auto": (ctypes.c_int, [vp, vp, ctypes.c_int, u64p,
+                                                  ctypes.c_int, ctypes.c_double,
+                                                  ctypes.POINTER(hpez_tune_params),
+                                                  vp, u64, u64p,
+                                                  ctypes.POINTER(hpez_tune_report), vp]),
+            "hpez_compress_auto_host": (ctypes.c_int, [vp, vp, ctypes.c_int, u64p,
+                                                       ctypes.c_int, ctypes.c_double,
+                                                       ctypes.POINTER(hpez_tune_params),
+                                                       vp, u64, u64p, vp]),
             "hpez_tune": (ctypes.c_int, [vp, vp, ctypes.c_int, u64p, ctypes.c_int,
                                          ctypes.c_double,
                                          ctypes.POINTER(hpez_tune_params), cfgp,
@@ -218,7 +227,8 @@ def exported_symbols() -> list[str]:
             "hpez_strerror", "hpez_profile_enable", "hpez_profile_get",
             "hpez_profile_phase_name", "hpez_launch_count", "hpez_set_option",
             "hpez_decompress_noalloc", "hpez_default_tune_params",
-            "hpez_blockmap_size", "hpez_tune", "hpez_batch_create_compress",
+            "hpez_blockmap_size", "hpez_tune", "hpez_compress_auto",
+            "hpez_compress_auto_host", "hpez_batch_create_compress",
             "hpez_batch_create_decompress", "hpez_batch_run", "hpez_batch_run_graph",
             "hpez_batch_results", "hpez_batch_launch_count", "hpez_batch_destroy",
             "hpez_server_create", "hpez_server_submit", "hpez_server_step",
@@ -368,6 +378,33 @@ def hpez_default_tune_params(**kw) -> hpez_tune_params:
     for k, v in kw.items():
         setattr(t, k, v)
     return t
+
+
+def hpez_compress_auto(ctx, d_in: int, shape, eb_mode: int, eb: float,
+                       tp: hpez_tune_params | None, d_out: int, out_cap: int,
+                       stream: int = 0, report: bool = False):
+    """Tune (Sec. 6) then compress; returns the stream size (and the tuning
+    report when asked)."""
+    size = ctypes.c_uint64(0)
+    rep = hpez_tune_report() if report else None
+    _check(_load().hpez_compress_auto(ctx, d_in, len(shape), _dims(shape), eb_mode,
+                                      float(eb), ctypes.byref(tp) if tp is not None else None,
+                                      d_out, out_cap, ctypes.byref(size),
+                                      ctypes.byref(rep) if rep is not None else None,
+                                      stream or None), "hpez_compress_auto")
+    return (size.value, rep) if report else size.value
+
+
+def hpez_compress_auto_host(ctx, h_in: np.ndarray, eb_mode: int, eb: float,
+                            tp: hpez_tune_params | None, h_out: np.ndarray,
+                            stream: int = 0) -> int:
+    assert h_in.dtype == np.float32 and h_in.flags.c_contiguous
+    size = ctypes.c_uint64(0)
+    _check(_load().hpez_compress_auto_host(
+        ctx, h_in.ctypes.data, h_in.ndim, _dims(h_in.shape), eb_mode, float(eb),
+        ctypes.byref(tp) if tp is not None else None, h_out.ctypes.data, h_out.nbytes,
+        ctypes.byref(size), stream or None), "hpez_compress_auto_host")
+    return size.value
 
 
 def hpez_blockmap_size(shape, block_size: int = 32) -> int:
