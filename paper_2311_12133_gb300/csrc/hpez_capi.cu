@@ -781,6 +781,9 @@ int hpez_destroy(hpez_ctx* ctx) {
   if (ctx->io_out) cudaFree(ctx->io_out);
   if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
   if (ctx->h_hdr) cudaFreeHost(ctx->h_hdr);
+  if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+  for (int i = 0; i < 2; ++i)
+    if (ctx->aux_ev[i]) cudaEventDestroy(ctx->aux_ev[i]);
   delete ctx;
   return HPEZ_OK;
 }

@@ -90,6 +90,8 @@ struct hpez_ctx {
   void* io_out = nullptr;
   size_t io_out_cap = 0;
   std::vector<uint8_t> h_bmap;  // block map of the last auto-tuned compress
+  cudaStream_t aux_stream = nullptr;  // the tuner's side stream
+  cudaEvent_t aux_ev[2] = {nullptr, nullptr};
 };
 
 namespace hpez {

@@ -151,19 +151,22 @@ void launch_tune_stats(const float* x, const uint32_t n[3],
 void launch_tune_params(TuneCfg* cfgs, int nvar, int L, const Ctl* ctl,
                         cudaStream_t s);
 size_t tune_test_smem(const TuneGeom& g);
-void launch_tune_test(const float* x, const TuneGeom& g, const TuneCfg* cfgs,
-                      int nvar, int nblk, int l_stop, bool hist,
-                      unsigned long long* score, uint32_t* hists,
-                      unsigned long long* nout, cudaStream_t s);
+// (sample block, variant) CTAs; variants < ny0 use geometry g0, the rest g1
+void launch_tune_test(const float* x, const TuneGeom& g0, const TuneGeom& g1,
+                      int ny0, const TuneCfg* cfgs, int nvar, int nblk,
+                      int l_stop, bool hist, unsigned long long* score,
+                      uint32_t* hists, unsigned long long* nout, cudaStream_t s);
 void launch_tune_lorenzo(const float* x, const TuneGeom& g, int nblk,
                          const Ctl* ctl, uint32_t* hists,
                          unsigned long long* nout, cudaStream_t s);
 void launch_tune_blockwise(const float* x, const TuneGeom& g, int bs, int Q,
                            int frozen_slot, const uint32_t nb[3],
                            uint32_t nblocks, const TuneCfg* base,
-                           unsigned allow, uint8_t* bmap, cudaStream_t s);
-// Huffman bits of nvar histograms (65536 bins each, lengths alike)
-void launch_tune_cost(const uint32_t* hists, const uint8_t* lens,
-                      unsigned long long* cost, int nvar, cudaStream_t s);
+                           unsigned allow, unsigned long long* scores,
+                           uint8_t* bmap, cudaStream_t s);
+// Huffman bits of the histograms of nvar codebook jobs (lengths: 65536
+// per job, in job order)
+void launch_tune_cost(const CodebookJob* jobs, int nvar, const uint8_t* lens,
+                      unsigned long long* cost, cudaStream_t s);
 
 }  // namespace hpez

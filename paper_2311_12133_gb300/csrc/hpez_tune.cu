@@ -18,7 +18,7 @@ using namespace hpez::host;
 namespace {
 
 constexpr size_t kTuneSmemMax = 200 * 1024;
-constexpr int kMaxVariants = 64;
+constexpr int kMaxVariants = 72;
 const double kAlpha[5] = {1.0, 1.25, 1.5, 1.75, 2.0};
 const double kBeta[4] = {2.0, 4.0, 8.0, 16.0};
 
@@ -93,7 +93,10 @@ TuneCfg to_device(const Plan& p, const hpez_config& c) {
 }
 
 // device buffers of one hpez_tune call
-constexpr int kMaxHists = 17;  // (alpha, beta) grid
+// histograms: the (alpha, beta) grid with and without freezing, then the
+// two Lorenzo tests
+constexpr int kMaxHists = 36;
+constexpr int kLorenzoSlot = 34;
 
 struct Bufs {
   Ctl* ctl;
@@ -113,6 +116,7 @@ struct Bufs {
   unsigned long long* giw;
   uint32_t* gpar;
   uint8_t* bmap;
+  unsigned long long* bscore;  // block-wise candidate scores
 };
 
 struct Call {
@@ -192,23 +196,24 @@ uint64_t block_anchors(const TuneGeom& g) {
   return na;
 }
 
-// Huffman bits of histograms [0, nvar) into b.cost[0, nvar): one batched
+// Huffman bits of the histograms in `slots` into b.cost[0, n): one batched
 // codebook launch (a CTA per histogram) and one cost launch
-void hist_costs(Call& k, int nvar) {
+void hist_costs(Call& k, const std::vector<int>& slots) {
   uint64_t& nl = k.ctx->launches;
+  const int n = (int)slots.size();
   CodebookJob jobs[kMaxHists];
-  for (int v = 0; v < nvar; ++v) {
-    const size_t o = (size_t)v * 65536;
-    jobs[v] = CodebookJob{k.b.hists + o, k.b.enc + o, k.b.tsyms + o, k.b.tlens + o,
+  for (int v = 0; v < n; ++v) {
+    const size_t h = (size_t)slots[v] * 65536, o = (size_t)v * 65536;
+    jobs[v] = CodebookJob{k.b.hists + h, k.b.enc + o, k.b.tsyms + o, k.b.tlens + o,
                           k.b.gkeys + o, k.b.giw + o, k.b.gpar + 2 * o,
                           k.b.lens + o, k.b.ctl2 + v};
   }
-  cudaMemsetAsync(k.b.ctl2, 0, sizeof(Ctl) * nvar, k.s);
-  cudaMemsetAsync(k.b.lens, 0, (size_t)65536 * nvar, k.s);
-  cudaMemcpyAsync(k.b.cbjobs, jobs, sizeof(CodebookJob) * nvar,
+  cudaMemsetAsync(k.b.ctl2, 0, sizeof(Ctl) * n, k.s);
+  cudaMemsetAsync(k.b.lens, 0, (size_t)65536 * n, k.s);
+  cudaMemcpyAsync(k.b.cbjobs, jobs, sizeof(CodebookJob) * n,
                   cudaMemcpyHostToDevice, k.s);
-  launch_codebook_batch(k.b.cbjobs, nvar, k.s);
-  launch_tune_cost(k.b.hists, k.b.lens, k.b.cost, nvar, k.s);
+  launch_codebook_batch(k.b.cbjobs, n, k.s);
+  launch_tune_cost(k.b.cbjobs, n, k.b.lens, k.b.cost, k.s);
   nl += 2;
 }
 
@@ -224,65 +229,93 @@ int costs_status(Call& k, int nvar) {
   return HPEZ_OK;
 }
 
-// Sec. 6.2 + 6.4 for one choice of frozen dim; returns the sample bits
-// estimate in *bits.
-int tune_global(Call& k, int frozen, const double inv_var[3],
-                hpez_config& cfg, hpez_tune_report* rep, int slot,
-                uint64_t* bits) {
+// One global tuning (Sec. 6.2 + 6.4) for one choice of frozen dimension.
+struct Variant {
+  int frozen = -1;
+  int slot = 0;        // report slot: 0 without, 1 with freezing
+  hpez_config cfg;
+  Plan p;
+  TuneGeom g;
+  int nblk = 0;
+  std::vector<Cand> cands;
+  uint64_t bits = 0;
+};
+
+int init_variant(Call& k, Variant& v, const double inv_var[3]) {
   const hpez_tune_params& tp = *k.tp;
+  hpez_config& cfg = v.cfg;
   default_config(k.ndim, &cfg);
   if (tp.anchor_stride) cfg.anchor_stride = tp.anchor_stride;
-  cfg.frozen_dim = frozen;
+  cfg.frozen_dim = v.frozen;
   for (int d = 0; d < 3; ++d) cfg.md_inv_var[d] = inv_var[d];
   for (int l = 0; l < HPEZ_MAX_LEVELS; ++l) {
     int q = 0;
     for (int d = 0; d < k.ndim; ++d)
-      if (d != frozen) cfg.order[l][q++] = (uint8_t)d;
+      if (d != v.frozen) cfg.order[l][q++] = (uint8_t)d;
     for (; q < 3; ++q) cfg.order[l][q] = 255;
   }
-  Plan p;
-  int rc = plan_geometry(p, k.ndim, k.dims, cfg.anchor_stride, frozen);
+  int rc = plan_geometry(v.p, k.ndim, k.dims, cfg.anchor_stride, v.frozen);
   if (rc) return rc;
-  TuneGeom g;
-  const int nblk = sample_geometry(p, tp, g);
-  if (tune_test_smem(g) > kTuneSmemMax) return HPEZ_ERR_UNSUPPORTED;
+  v.nblk = sample_geometry(v.p, tp, v.g);
+  if (tune_test_smem(v.g) > kTuneSmemMax) return HPEZ_ERR_UNSUPPORTED;
   // the Lorenzo wavefront keeps at most 4 (i0, i1) pairs per thread
-  if ((uint64_t)g.ext[0] * g.ext[1] > 4096) return HPEZ_ERR_UNSUPPORTED;
-  if (rep && slot == 0) rep->n_sample_blocks = (uint32_t)nblk;
+  if ((uint64_t)v.g.ext[0] * v.g.ext[1] > 4096) return HPEZ_ERR_UNSUPPORTED;
+  v.cands = candidates(tp, k.ndim, v.frozen);
+  if ((int)v.cands.size() * 2 > kMaxVariants) return HPEZ_ERR_UNSUPPORTED;
+  return HPEZ_OK;
+}
+
+// Sec. 6.2 + 6.4 for every variant at once: each level's candidate tests
+// (and then the (alpha, beta) tests) of all variants go out together, with
+// one synchronization per round.
+int tune_globals(Call& k, std::vector<Variant>& vs, hpez_tune_report* rep,
+                 const std::vector<int>& extra, cudaEvent_t extra_ready,
+                 std::vector<unsigned long long>& extra_cost) {
+  const hpez_tune_params& tp = *k.tp;
   uint64_t& nl = k.ctx->launches;
   PhaseProfiler& prof = k.ctx->prof;
+  const int nv = (int)vs.size();
   std::vector<TuneCfg> host(kMaxVariants);
   std::vector<unsigned long long> sc(kMaxVariants);
-
+  int rc;
+  if (rep) rep->n_sample_blocks = (uint32_t)vs[0].nblk;
+  const int L = vs[0].p.L;
   if (tp.tune_levels) {
-    const std::vector<Cand> cands = candidates(tp, k.ndim, frozen);
-    const int nvar = (int)cands.size();
-    if (nvar > kMaxVariants) return HPEZ_ERR_UNSUPPORTED;
-    for (int l = p.L; l >= 1; --l) {
-      for (int j = 0; j < nvar; ++j) {
-        hpez_config c2 = cfg;
-        set_level(c2, l, cands[j]);
-        host[j] = to_device(p, c2);
+    for (int l = L; l >= 1; --l) {
+      int at = 0;
+      std::vector<int> base(nv);
+      for (int i = 0; i < nv; ++i) {
+        base[i] = at;
+        for (size_t j = 0; j < vs[i].cands.size(); ++j) {
+          hpez_config c2 = vs[i].cfg;
+          set_level(c2, l, vs[i].cands[j]);
+          host[at++] = to_device(vs[i].p, c2);
+        }
       }
       prof.begin(HPEZ_PH_TUNE_LEVELS, k.s);
-      cudaMemcpyAsync(k.b.cfgs, host.data(), sizeof(TuneCfg) * nvar,
+      cudaMemcpyAsync(k.b.cfgs, host.data(), sizeof(TuneCfg) * at,
                       cudaMemcpyHostToDevice, k.s);
-      launch_tune_params(k.b.cfgs, nvar, kMaxLevels, k.b.ctl, k.s);
-      cudaMemsetAsync(k.b.score, 0, sizeof(unsigned long long) * nvar, k.s);
-      launch_tune_test(k.x, g, k.b.cfgs, nvar, nblk, l, false, k.b.score,
-                       nullptr, k.b.nout, k.s);
+      launch_tune_params(k.b.cfgs, at, kMaxLevels, k.b.ctl, k.s);
+      cudaMemsetAsync(k.b.score, 0, sizeof(unsigned long long) * at, k.s);
+      // every variant's candidates in one launch (escapes unused here)
+      launch_tune_test(k.x, vs[0].g, vs[nv - 1].g, (int)vs[0].cands.size(),
+                       k.b.cfgs, at, vs[0].nblk, l, false, k.b.score, nullptr,
+                       k.b.nout + kMaxHists, k.s);
       nl += 2;
       prof.end(k.s);
-      cudaMemcpyAsync(sc.data(), k.b.score, sizeof(unsigned long long) * nvar,
+      cudaMemcpyAsync(sc.data(), k.b.score, sizeof(unsigned long long) * at,
                       cudaMemcpyDeviceToHost, k.s);
       if ((rc = sync_check(k))) return rc;
-      int best = 0;
-      for (int j = 1; j < nvar; ++j)
-        if (sc[j] < sc[best]) best = j;
-      set_level(cfg, l, cands[best]);
-      if (rep) {
-        rep->level_choice[slot][l - 1] = (uint8_t)best;
-        rep->level_score[slot][l - 1] = sc[best];
+      for (int i = 0; i < nv; ++i) {
+        const int n = (int)vs[i].cands.size();
+        int best = 0;
+        for (int j = 1; j < n; ++j)
+          if (sc[base[i] + j] < sc[base[i] + best]) best = j;
+        set_level(vs[i].cfg, l, vs[i].cands[best]);
+        if (rep) {
+          rep->level_choice[vs[i].slot][l - 1] = (uint8_t)best;
+          rep->level_score[vs[i].slot][l - 1] = sc[base[i] + best];
+        }
       }
     }
   }
@@ -294,47 +327,61 @@ int tune_global(Call& k, int frozen, const double inv_var[3],
     for (int a = 1; a < 5; ++a)
       for (int b = 0; b < 4; ++b) grid.push_back({kAlpha[a], kBeta[b]});
   } else {
-    grid.push_back({cfg.alpha, cfg.beta});
+    grid.push_back({vs[0].cfg.alpha, vs[0].cfg.beta});
   }
-  const int nvar = (int)grid.size();
-  for (int v = 0; v < nvar; ++v) {
-    hpez_config c2 = cfg;
-    c2.alpha = grid[v].first;
-    c2.beta = grid[v].second;
-    host[v] = to_device(p, c2);
-  }
-  prof.begin(HPEZ_PH_TUNE_EB, k.s);
-  cudaMemcpyAsync(k.b.cfgs, host.data(), sizeof(TuneCfg) * nvar,
-                  cudaMemcpyHostToDevice, k.s);
-  launch_tune_params(k.b.cfgs, nvar, kMaxLevels, k.b.ctl, k.s);
-  cudaMemsetAsync(k.b.hists, 0, sizeof(uint32_t) * 65536 * nvar, k.s);
-  cudaMemsetAsync(k.b.nout, 0, sizeof(unsigned long long) * nvar, k.s);
-  cudaMemsetAsync(k.b.score, 0, sizeof(unsigned long long) * nvar, k.s);
-  launch_tune_test(k.x, g, k.b.cfgs, nvar, nblk, 1, true, k.b.score,
-                   k.b.hists, k.b.nout, k.s);
-  nl += 2;
-  hist_costs(k, nvar);
-  prof.end(k.s);
-  std::vector<unsigned long long> cost(nvar), nout(nvar);
-  cudaMemcpyAsync(cost.data(), k.b.cost, sizeof(unsigned long long) * nvar,
-                  cudaMemcpyDeviceToHost, k.s);
-  cudaMemcpyAsync(nout.data(), k.b.nout, sizeof(unsigned long long) * nvar,
-                  cudaMemcpyDeviceToHost, k.s);
-  if ((rc = costs_status(k, nvar))) return rc;
-  const uint64_t na = block_anchors(g) * (uint64_t)nblk;
-  int best = 0;
-  uint64_t best_bits = 0;
-  for (int v = 0; v < nvar; ++v) {
-    const uint64_t b = cost[v] + 32ull * nout[v] + 32ull * na;
-    if (v == 0 || b < best_bits) {
-      best_bits = b;
-      best = v;
+  const int ng = (int)grid.size();
+  const int nh = ng * nv;
+  for (int i = 0; i < nv; ++i)
+    for (int v = 0; v < ng; ++v) {
+      hpez_config c2 = vs[i].cfg;
+      c2.alpha = grid[v].first;
+      c2.beta = grid[v].second;
+      host[i * ng + v] = to_device(vs[i].p, c2);
     }
+  prof.begin(HPEZ_PH_TUNE_EB, k.s);
+  cudaMemcpyAsync(k.b.cfgs, host.data(), sizeof(TuneCfg) * nh,
+                  cudaMemcpyHostToDevice, k.s);
+  launch_tune_params(k.b.cfgs, nh, kMaxLevels, k.b.ctl, k.s);
+  cudaMemsetAsync(k.b.hists, 0, sizeof(uint32_t) * 65536 * nh, k.s);
+  cudaMemsetAsync(k.b.nout, 0, sizeof(unsigned long long) * nh, k.s);
+  cudaMemsetAsync(k.b.score, 0, sizeof(unsigned long long) * nh, k.s);
+  launch_tune_test(k.x, vs[0].g, vs[nv - 1].g, ng, k.b.cfgs, nh, vs[0].nblk, 1,
+                   true, k.b.score, k.b.hists, k.b.nout, k.s);
+  nl += 2;
+  // the codebooks of these histograms and of the extra ones (the Lorenzo
+  // tests, run on the side stream) in one launch
+  std::vector<int> slots;
+  for (int v = 0; v < nh; ++v) slots.push_back(v);
+  if (!extra.empty()) {
+    cudaStreamWaitEvent(k.s, extra_ready, 0);
+    for (int v : extra) slots.push_back(v);
   }
-  cfg.alpha = grid[best].first;
-  cfg.beta = grid[best].second;
-  *bits = best_bits;
-  if (rep) rep->bits[slot] = best_bits;
+  const int nc = (int)slots.size();
+  hist_costs(k, slots);
+  prof.end(k.s);
+  std::vector<unsigned long long> cost(nc), nout(nh);
+  cudaMemcpyAsync(cost.data(), k.b.cost, sizeof(unsigned long long) * nc,
+                  cudaMemcpyDeviceToHost, k.s);
+  cudaMemcpyAsync(nout.data(), k.b.nout, sizeof(unsigned long long) * nh,
+                  cudaMemcpyDeviceToHost, k.s);
+  if ((rc = costs_status(k, nc))) return rc;
+  extra_cost.assign(cost.begin() + nh, cost.end());
+  for (int i = 0; i < nv; ++i) {
+    const uint64_t na = block_anchors(vs[i].g) * (uint64_t)vs[i].nblk;
+    int best = 0;
+    uint64_t best_bits = 0;
+    for (int v = 0; v < ng; ++v) {
+      const uint64_t b = cost[i * ng + v] + 32ull * nout[i * ng + v] + 32ull * na;
+      if (v == 0 || b < best_bits) {
+        best_bits = b;
+        best = v;
+      }
+    }
+    vs[i].cfg.alpha = grid[best].first;
+    vs[i].cfg.beta = grid[best].second;
+    vs[i].bits = best_bits;
+    if (rep) rep->bits[vs[i].slot] = best_bits;
+  }
   return HPEZ_OK;
 }
 
@@ -415,6 +462,7 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
   const size_t o_giw = ar.take<unsigned long long>((size_t)65536 * kMaxHists);
   const size_t o_gpar = ar.take<uint32_t>((size_t)131072 * kMaxHists);
   const size_t o_bmap = ar.take<uint8_t>(nbm ? nbm : 1);
+  const size_t o_bscore = ar.take<unsigned long long>(5 * (nbm ? nbm : 1));
   if ((rc = ensure_scratch(ctx, ar.off))) return rc;
   char* base = ctx->scratch;
   Call k;
@@ -441,6 +489,7 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
   k.b.giw = reinterpret_cast<unsigned long long*>(base + o_giw);
   k.b.gpar = reinterpret_cast<uint32_t*>(base + o_gpar);
   k.b.bmap = reinterpret_cast<uint8_t*>(base + o_bmap);
+  k.b.bscore = reinterpret_cast<unsigned long long*>(base + o_bscore);
   uint64_t& nl = ctx->launches;
   PhaseProfiler& prof = ctx->prof;
 
@@ -513,41 +562,62 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
   }
 
   // Sec. 6.2 + 6.4 without freezing, and (Sec. 6.3) with the most
-  // non-smooth dim frozen; the smaller estimate wins
-  hpez_config cfg_nf, cfg_f;
-  uint64_t bits_nf = 0, bits_f = 0;
-  if ((rc = tune_global(k, -1, inv_var, cfg_nf, rep, 0, &bits_nf))) return rc;
-  hpez_config out = cfg_nf;
-  uint64_t bits_best = bits_nf;
+  // non-smooth dim frozen, side by side; the smaller estimate wins
+  std::vector<Variant> vs(1);
+  vs[0].frozen = -1;
+  vs[0].slot = 0;
   if (tp.tune_freeze && cnt && ndim >= 2) {
-    if ((rc = tune_global(k, nonsmooth, inv_var, cfg_f, rep, 1, &bits_f)))
+    vs.emplace_back();
+    vs[1].frozen = nonsmooth;
+    vs[1].slot = 1;
+  }
+  for (Variant& v : vs)
+    if ((rc = init_variant(k, v, inv_var))) return rc;
+  // Sec. 6.5: order-1 and order-2 Lorenzo tests on the same sample blocks,
+  // on a side stream, overlapping the candidate tests
+  std::vector<int> lor_slots;
+  if (tp.tune_lorenzo) {
+    if (!ctx->aux_stream &&
+        (rc = cuda_check(cudaStreamCreateWithFlags(&ctx->aux_stream,
+                                                   cudaStreamNonBlocking))))
       return rc;
-    if (bits_f < bits_nf) {
-      out = cfg_f;
-      bits_best = bits_f;
-      if (rep) rep->froze = 1;
-    }
+    if (!ctx->aux_ev[0] &&
+        ((rc = cuda_check(cudaEventCreateWithFlags(&ctx->aux_ev[0], cudaEventDisableTiming))) ||
+         (rc = cuda_check(cudaEventCreateWithFlags(&ctx->aux_ev[1], cudaEventDisableTiming)))))
+      return rc;
+    cudaStream_t s2 = ctx->aux_stream;
+    cudaEventRecord(ctx->aux_ev[0], s);
+    cudaStreamWaitEvent(s2, ctx->aux_ev[0], 0);
+    prof.begin(HPEZ_PH_TUNE_LORENZO, s2);
+    cudaMemsetAsync(k.b.hists + (size_t)kLorenzoSlot * 65536, 0,
+                    sizeof(uint32_t) * 65536 * 2, s2);
+    cudaMemsetAsync(k.b.nout + kLorenzoSlot, 0, sizeof(unsigned long long) * 2, s2);
+    launch_tune_lorenzo(d_in, vs[0].g, vs[0].nblk, k.b.ctl,
+                        k.b.hists + (size_t)kLorenzoSlot * 65536,
+                        k.b.nout + kLorenzoSlot, s2);
+    prof.end(s2);
+    cudaEventRecord(ctx->aux_ev[1], s2);
+    ++nl;
+    lor_slots = {kLorenzoSlot, kLorenzoSlot + 1};
+  }
+  std::vector<unsigned long long> lor_cost;
+  if ((rc = tune_globals(k, vs, rep, lor_slots, ctx->aux_ev[1], lor_cost))) return rc;
+  hpez_config out = vs[0].cfg;
+  uint64_t bits_best = vs[0].bits;
+  if (vs.size() > 1 && vs[1].bits < vs[0].bits) {
+    out = vs[1].cfg;
+    bits_best = vs[1].bits;
+    if (rep) rep->froze = 1;
   }
 
-  // Sec. 6.5: order-1 and order-2 Lorenzo on the same sample blocks
+  // Lorenzo bits from the costs and escapes computed above
   if (tp.tune_lorenzo) {
-    Plan p;
-    if ((rc = plan_geometry(p, ndim, dims, out.anchor_stride, -1))) return rc;
-    TuneGeom g;
-    const int nblk = sample_geometry(p, tp, g);
-    prof.begin(HPEZ_PH_TUNE_LORENZO, s);
-    cudaMemsetAsync(k.b.hists, 0, sizeof(uint32_t) * 65536 * 2, s);
-    cudaMemsetAsync(k.b.nout, 0, sizeof(unsigned long long) * 2, s);
-    launch_tune_lorenzo(d_in, g, nblk, k.b.ctl, k.b.hists, k.b.nout, s);
-    ++nl;
-    hist_costs(k, 2);
-    prof.end(s);
-    unsigned long long cost[2], nout[2];
-    cudaMemcpyAsync(cost, k.b.cost, sizeof(cost), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(nout, k.b.nout, sizeof(nout), cudaMemcpyDeviceToHost, s);
-    if ((rc = costs_status(k, 2))) return rc;
-    const uint64_t lb0 = cost[0] + 32ull * nout[0];
-    const uint64_t lb1 = cost[1] + 32ull * nout[1];
+    unsigned long long nout[2];
+    cudaMemcpyAsync(nout, k.b.nout + kLorenzoSlot, sizeof(nout),
+                    cudaMemcpyDeviceToHost, s);
+    if ((rc = sync_check(k))) return rc;
+    const uint64_t lb0 = lor_cost[0] + 32ull * nout[0];
+    const uint64_t lb1 = lor_cost[1] + 32ull * nout[1];
     if (rep) {
       rep->lorenzo_bits[0] = lb0;
       rep->lorenzo_bits[1] = lb1;
@@ -580,8 +650,8 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
     const unsigned allow = (tp.allow_natural ? 1u : 0u) | (tp.allow_same_level ? 2u : 0u);
     launch_tune_blockwise(d_in, g, bsz, Q,
                           out.frozen_dim < 0 ? -1 : out.frozen_dim + p.off, nb,
-                          (uint32_t)nbm, k.b.cfgs, allow, k.b.bmap, s);
-    nl += 2;
+                          (uint32_t)nbm, k.b.cfgs, allow, k.b.bscore, k.b.bmap, s);
+    nl += 3;
     prof.end(s);
     cudaMemcpyAsync(h_blockmap, k.b.bmap, nbm, cudaMemcpyDeviceToHost, s);
     if ((rc = sync_check(k))) return rc;

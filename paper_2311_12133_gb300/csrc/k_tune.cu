@@ -8,6 +8,7 @@
 // integer (fixed-point errors, code counts), so the sums do not depend on
 // the order in which threads add them; the floating-point steps follow the
 // compressor's operation order with explicit round-to-nearest intrinsics.
+#include <algorithm>
 #include <cfloat>
 
 #include "hpez_internal.cuh"
@@ -17,7 +18,10 @@ namespace hpez {
 namespace {
 
 constexpr int kTuneThreads = 1024;
-constexpr int kBlockThreads = 128;
+// block-map codes of the block-wise candidates, in test order: linear,
+// not-a-knot, not-a-knot + same-level, natural, natural + same-level
+__constant__ uint8_t kBlockCodes[5] = {0, 1, 5, 2, 6};
+constexpr int kBlockThreads = 32;  // one warp per (block, candidate)
 constexpr size_t kTuneSmemMax = 200 * 1024;
 
 // floor(min(|d| * (1/e_l), 2^24 - 1) * 256) in binary32: the per-point
@@ -142,7 +146,7 @@ struct Sub {
   int n[3];          // extents per slot
   int st[3];         // shared-memory strides
   const float* x;    // input at the sub-field origin
-  size_t xst[3];     // input strides
+  uint32_t xst[3];   // input strides (a field has fewer than 2^32 points)
 };
 
 __device__ __forceinline__ void set_strides(Sub& f) {
@@ -154,11 +158,11 @@ __device__ __forceinline__ void set_strides(Sub& f) {
 // sample block b of the lattice of blocks
 __device__ Sub sample_block(const float* x, const TuneGeom& g, unsigned b) {
   Sub f;
-  size_t off = 0;
+  uint32_t off = 0;
   for (int d = 2; d >= 0; --d) {
     const unsigned j = b % g.cnt[d];
     b /= g.cnt[d];
-    off += (size_t)j * g.step[d] * g.fst[d];
+    off += j * g.step[d] * g.fst[d];
     f.n[d] = (int)g.ext[d];
     f.xst[d] = g.fst[d];
   }
@@ -168,26 +172,29 @@ __device__ Sub sample_block(const float* x, const TuneGeom& g, unsigned b) {
 }
 
 __device__ __forceinline__ float xval(const Sub& f, const int c[3]) {
-  return f.x[(size_t)c[0] * f.xst[0] + (size_t)c[1] * f.xst[1] +
-             (size_t)c[2] * f.xst[2]];
+  return f.x[(uint32_t)c[0] * f.xst[0] + (uint32_t)c[1] * f.xst[1] +
+             (uint32_t)c[2] * f.xst[2]];
 }
 
-// anchors (every interpolation coordinate a multiple of A) from the input;
-// the other entries are set by the sweep before they are read
+// anchors (every interpolation coordinate a multiple of A) from the input,
+// enumerated on their own lattice; every other entry is written by the
+// sweep before it is read
 __device__ void init_anchors(float* R, const Sub& f, const int interp[3],
                              int A) {
-  const int tot = f.n[0] * f.n[1] * f.n[2];
+  int m[3], st[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    st[d] = interp[d] ? A : 1;
+    m[d] = (f.n[d] + st[d] - 1) / st[d];
+  }
+  const int tot = m[0] * m[1] * m[2];
   for (int q = threadIdx.x; q < tot; q += blockDim.x) {
     int c[3];
-    c[2] = q % f.n[2];
-    const int r = q / f.n[2];
-    c[1] = r % f.n[1];
-    c[0] = r / f.n[1];
-    bool anc = true;
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-      if (interp[d] && (c[d] % A) != 0) anc = false;
-    R[q] = anc ? xval(f, c) : 0.0f;
+    c[2] = (q % m[2]) * st[2];
+    const int r = q / m[2];
+    c[1] = (r % m[1]) * st[1];
+    c[0] = (r / m[1]) * st[0];
+    R[c[0] * f.st[0] + c[1] * f.st[1] + c[2]] = xval(f, c);
   }
   __syncthreads();
 }
@@ -286,6 +293,23 @@ __device__ __forceinline__ void make_box(Box& bx, const Sub& f,
   }
 }
 
+// codes within kWin/2 of the zero-error code are counted in shared memory
+constexpr int kWin = 2048;
+
+// the histogram a point's code goes to: the shared window, or global
+// memory beyond it
+struct HistSink {
+  uint32_t* win;   // shared, kWin bins centred on the zero-error code
+  uint32_t* glob;  // global, 65536 bins
+  __device__ __forceinline__ void add(unsigned code) const {
+    const unsigned o = code - (unsigned)(kRadius - kWin / 2);
+    if (o < (unsigned)kWin)
+      atomicAdd(win + o, 1u);
+    else
+      atomicAdd(glob + code, 1u);
+  }
+};
+
 // exact bound check with a fast accept: rn(r - x) strictly inside the
 // bound implies the exact difference is inside (rounding is monotonic)
 __device__ __forceinline__ unsigned quantize_t(float x, float p, float el,
@@ -308,12 +332,12 @@ __device__ __forceinline__ unsigned quantize_t(float x, float p, float el,
 
 // The points of one pass (or same-level half) of a level, specialized on
 // the interpolator and the paradigm, which are uniform within a level.
-template <int KIND, bool MD, bool kHist>
+template <int KIND, bool MD, int PS, bool kHist>
 __device__ void sweep_pass(float* R, const Sub& f, const Box* bx, int nb,
                            int tot, int half, bool same, int sh,
                            const int line[3], const TuneCfg& c, int l,
                            bool score_on, unsigned long long& score,
-                           uint32_t* hist, unsigned long long& nout) {
+                           const HistSink& hist, unsigned long long& nout) {
   const int s = 1 << sh;
   const float el = c.el[l - 1], inv2 = c.inv2[l - 1], twoe = c.twoe[l - 1];
   const float inv_el = c.inv_el[l - 1];
@@ -341,8 +365,7 @@ __device__ void sweep_pass(float* R, const Sub& f, const Box* bx, int nb,
     const float xv = xval(f, cc);
     float p;
     if (!MD) {
-      const int ps = S == 1u ? 0 : (S == 2u ? 1 : 2);
-      p = predict_smem(R, i, s * f.st[ps], cc[ps] >> sh, line[ps], KIND, in_b);
+      p = predict_smem(R, i, s * f.st[PS], cc[PS] >> sh, line[PS], KIND, in_b);
     } else {
       float acc = 0.0f;
       bool first = true;
@@ -361,7 +384,7 @@ __device__ void sweep_pass(float* R, const Sub& f, const Box* bx, int nb,
     const unsigned code = quantize_t(xv, p, el, inv2, twoe, rv);
     R[i] = rv;
     if (score_on) score += err_fixed(__fsub_rn(xv, p), inv_el);
-    if (kHist) atomicAdd(hist + code, 1u);
+    if (kHist) hist.add(code);
     if (code == 0u) ++nout;
   }
 }
@@ -369,7 +392,7 @@ __device__ void sweep_pass(float* R, const Sub& f, const Box* bx, int nb,
 template <bool kHist>
 __device__ void sweep_level(float* R, const Sub& f, const int interp[3],
                             int k, int l, const TuneCfg& c, bool score_on,
-                            unsigned long long& score, uint32_t* hist,
+                            unsigned long long& score, const HistSink& hist,
                             unsigned long long& nout) {
   const int sh = l - 1, s = 1 << sh;
   int line[3];
@@ -398,18 +421,26 @@ __device__ void sweep_level(float* R, const Sub& f, const int interp[3],
     int tot = 0;
     for (int q = 0; q < nb; ++q) tot += bx[q].total;
     for (int half = 0; half < (same ? 2 : 1); ++half) {
-#define HPEZ_SWEEP(K, M)                                                      \
-  sweep_pass<K, M, kHist>(R, f, bx, nb, tot, half, same, sh, line, c, l,      \
-                          score_on, score, hist, nout)
+#define HPEZ_SWEEP(K, M, P)                                                   \
+  sweep_pass<K, M, P, kHist>(R, f, bx, nb, tot, half, same, sh, line, c, l,   \
+                             score_on, score, hist, nout)
+#define HPEZ_SWEEP_1D(K)                                                      \
+  do {                                                                        \
+    const int ps = c.ord[l - 1][pj];                                          \
+    if (ps == 0) HPEZ_SWEEP(K, false, 0);                                     \
+    else if (ps == 1) HPEZ_SWEEP(K, false, 1);                                \
+    else HPEZ_SWEEP(K, false, 2);                                             \
+  } while (0)
       if (md) {
-        if (kind == LINEAR) HPEZ_SWEEP(LINEAR, true);
-        else if (kind == CUBIC_NAK) HPEZ_SWEEP(CUBIC_NAK, true);
-        else HPEZ_SWEEP(CUBIC_NAT, true);
+        if (kind == LINEAR) HPEZ_SWEEP(LINEAR, true, 0);
+        else if (kind == CUBIC_NAK) HPEZ_SWEEP(CUBIC_NAK, true, 0);
+        else HPEZ_SWEEP(CUBIC_NAT, true, 0);
       } else {
-        if (kind == LINEAR) HPEZ_SWEEP(LINEAR, false);
-        else if (kind == CUBIC_NAK) HPEZ_SWEEP(CUBIC_NAK, false);
-        else HPEZ_SWEEP(CUBIC_NAT, false);
+        if (kind == LINEAR) HPEZ_SWEEP_1D(LINEAR);
+        else if (kind == CUBIC_NAK) HPEZ_SWEEP_1D(CUBIC_NAK);
+        else HPEZ_SWEEP_1D(CUBIC_NAT);
       }
+#undef HPEZ_SWEEP_1D
 #undef HPEZ_SWEEP
       __syncthreads();
     }
@@ -427,23 +458,32 @@ __device__ __forceinline__ void load_cfg(TuneCfg* dst, const TuneCfg* src) {
 // ---------------------------------------------------------------------
 // Sec. 6.2 / 6.4: CTA (sample block, variant): anchors, levels L..l_stop
 // ---------------------------------------------------------------------
+// Variants y < ny0 use geometry g0, the others g1 (two frozen-dimension
+// choices in one launch).
 template <bool kHist>
 __global__ void __launch_bounds__(kTuneThreads)
-    k_tune_test(const float* __restrict__ x, TuneGeom g,
+    k_tune_test(const float* __restrict__ x, TuneGeom g0, TuneGeom g1, int ny0,
                 const TuneCfg* __restrict__ cfgs, int l_stop,
                 unsigned long long* score, uint32_t* hists,
                 unsigned long long* nout) {
+  const TuneGeom& g = (int)blockIdx.y < ny0 ? g0 : g1;
   extern __shared__ float R[];
   __shared__ TuneCfg c;
   __shared__ unsigned long long red[32];
+  __shared__ uint32_t win[kHist ? kWin : 1];
   const int v = blockIdx.y;
+  if (kHist)
+    for (int i = threadIdx.x; i < kWin; i += blockDim.x) win[i] = 0;
   load_cfg(&c, cfgs + v);
   const Sub f = sample_block(x, g, blockIdx.x);
   init_anchors(R, f, g.interp, g.A);
   unsigned long long sc = 0, no = 0;
-  uint32_t* h = kHist ? hists + (size_t)v * 65536 : nullptr;
+  HistSink h{win, kHist ? hists + (size_t)v * 65536 : nullptr};
   for (int l = g.L; l >= l_stop; --l)
     sweep_level<kHist>(R, f, g.interp, g.k, l, c, l == l_stop, sc, h, no);
+  if (kHist)
+    for (int i = threadIdx.x; i < kWin; i += blockDim.x)
+      if (win[i]) atomicAdd(h.glob + (kRadius - kWin / 2) + i, win[i]);
   sc = block_sum(sc, red);
   if (threadIdx.x == 0 && sc) atomicAdd(score + v, sc);
   no = block_sum(no, red);
@@ -536,17 +576,25 @@ struct BlockGeom {
   int bs, Q, frozen_slot;
 };
 
+// CTA (field block, candidate j): the summed level score of the centred
+// sub-block with candidate j at every level; ~0 for a candidate not allowed
 __global__ void __launch_bounds__(kBlockThreads)
     k_tune_blockwise(const float* __restrict__ x, TuneGeom g, BlockGeom bg,
                      const TuneCfg* __restrict__ base, unsigned allow,
-                     uint8_t* bmap) {
+                     unsigned long long* scores) {
   extern __shared__ float R[];
   __shared__ TuneCfg c;
   __shared__ unsigned long long red[32];
+  const uint8_t v = kBlockCodes[blockIdx.y];
+  unsigned long long* out = scores + (size_t)blockIdx.x * 5 + blockIdx.y;
+  if (((v & 3) == CUBIC_NAT && !(allow & 1u)) || ((v & 4) && !(allow & 2u))) {
+    if (threadIdx.x == 0) *out = ~0ull;
+    return;
+  }
   load_cfg(&c, base);
   unsigned b = blockIdx.x;
   Sub f;
-  size_t off = 0;
+  uint32_t off = 0;
   int qmin = 0x7fffffff;
   for (int d = 2; d >= 0; --d) {
     const unsigned j = b % bg.nb[d];
@@ -559,7 +607,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     const int b0 = (int)j * bg.bs;
     const int bext = min(bg.bs, (int)g.n[d] - b0);
     const int q = min(bext, bg.Q);
-    off += (size_t)(b0 + (bext - q) / 2) * g.fst[d];
+    off += (uint32_t)(b0 + (bext - q) / 2) * g.fst[d];
     f.n[d] = q;
     if (d != bg.frozen_slot) qmin = min(qmin, q);
   }
@@ -570,38 +618,44 @@ __global__ void __launch_bounds__(kBlockThreads)
   while (As * 2 <= lim) As *= 2;
   int L = 0;
   while ((1 << L) < As) ++L;
-  const uint8_t codes[5] = {0, 1, 5, 2, 6};
-  unsigned long long best = ~0ull;
-  uint8_t bestc = 0;
-  for (int j = 0; j < 5; ++j) {
-    const uint8_t v = codes[j];
-    if ((v & 3) == CUBIC_NAT && !(allow & 1u)) continue;
-    if ((v & 4) && !(allow & 2u)) continue;
-    __syncthreads();
-    if (threadIdx.x < kMaxLevels) {
-      c.kind[threadIdx.x] = v & 3;
-      c.same[threadIdx.x] = (v >> 2) & 1;
-    }
-    __syncthreads();
-    init_anchors(R, f, g.interp, As);
-    unsigned long long sc = 0, no = 0;
-    for (int l = L; l >= 1; --l)
-      sweep_level<false>(R, f, g.interp, g.k, l, c, true, sc, nullptr, no);
-    sc = block_sum(sc, red);
-    if (threadIdx.x == 0 && sc < best) {
-      best = sc;
-      bestc = v;
-    }
+  if (threadIdx.x < kMaxLevels) {
+    c.kind[threadIdx.x] = v & 3;
+    c.same[threadIdx.x] = (v >> 2) & 1;
   }
-  if (threadIdx.x == 0) bmap[blockIdx.x] = bestc;
+  __syncthreads();
+  init_anchors(R, f, g.interp, As);
+  unsigned long long sc = 0, no = 0;
+  const HistSink none{nullptr, nullptr};
+  for (int l = L; l >= 1; --l)
+    sweep_level<false>(R, f, g.interp, g.k, l, c, true, sc, none, no);
+  sc = block_sum(sc, red);
+  if (threadIdx.x == 0) *out = sc;
 }
 
-// Huffman bits of histogram v: sum of count * code length (block v)
+// the block map: per block the first candidate with the smallest score
+__global__ void k_tune_block_argmin(const unsigned long long* __restrict__ scores,
+                                    uint32_t nblocks, uint8_t* bmap) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nblocks) return;
+  unsigned long long best = scores[(size_t)b * 5];
+  int bj = 0;
+  for (int j = 1; j < 5; ++j) {
+    const unsigned long long v = scores[(size_t)b * 5 + j];
+    if (v < best) {
+      best = v;
+      bj = j;
+    }
+  }
+  bmap[b] = kBlockCodes[bj];
+}
+
+// Huffman bits of histogram v (the histogram of codebook job v): sum of
+// count * code length (block v)
 __global__ void __launch_bounds__(1024)
-    k_tune_cost(const uint32_t* __restrict__ hists,
+    k_tune_cost(const CodebookJob* __restrict__ jobs,
                 const uint8_t* __restrict__ lens, unsigned long long* cost) {
   __shared__ unsigned long long red[32];
-  const uint32_t* hist = hists + (size_t)blockIdx.x * 65536;
+  const uint32_t* hist = jobs[blockIdx.x].hist;
   const uint8_t* ln = lens + (size_t)blockIdx.x * 65536;
   unsigned long long acc = 0;
   for (int i = threadIdx.x; i < 65536; i += blockDim.x)
@@ -665,19 +719,19 @@ size_t tune_test_smem(const TuneGeom& g) {
   return (size_t)g.ext[0] * g.ext[1] * g.ext[2] * sizeof(float);
 }
 
-void launch_tune_test(const float* x, const TuneGeom& g, const TuneCfg* cfgs,
-                      int nvar, int nblk, int l_stop, bool hist,
-                      unsigned long long* score, uint32_t* hists,
-                      unsigned long long* nout, cudaStream_t s) {
+void launch_tune_test(const float* x, const TuneGeom& g0, const TuneGeom& g1,
+                      int ny0, const TuneCfg* cfgs, int nvar, int nblk,
+                      int l_stop, bool hist, unsigned long long* score,
+                      uint32_t* hists, unsigned long long* nout, cudaStream_t s) {
   set_smem_attr();
   const dim3 grid((unsigned)nblk, (unsigned)nvar);
-  const size_t sm = tune_test_smem(g);
+  const size_t sm = std::max(tune_test_smem(g0), tune_test_smem(g1));
   if (hist)
-    k_tune_test<true><<<grid, kTuneThreads, sm, s>>>(x, g, cfgs, l_stop, score,
-                                                     hists, nout);
+    k_tune_test<true><<<grid, kTuneThreads, sm, s>>>(x, g0, g1, ny0, cfgs, l_stop,
+                                                     score, hists, nout);
   else
-    k_tune_test<false><<<grid, kTuneThreads, sm, s>>>(x, g, cfgs, l_stop, score,
-                                                      hists, nout);
+    k_tune_test<false><<<grid, kTuneThreads, sm, s>>>(x, g0, g1, ny0, cfgs, l_stop,
+                                                      score, hists, nout);
 }
 
 void launch_tune_lorenzo(const float* x, const TuneGeom& g, int nblk,
@@ -691,7 +745,8 @@ void launch_tune_lorenzo(const float* x, const TuneGeom& g, int nblk,
 void launch_tune_blockwise(const float* x, const TuneGeom& g, int bs, int Q,
                            int frozen_slot, const uint32_t nb[3],
                            uint32_t nblocks, const TuneCfg* base,
-                           unsigned allow, uint8_t* bmap, cudaStream_t s) {
+                           unsigned allow, unsigned long long* scores,
+                           uint8_t* bmap, cudaStream_t s) {
   set_smem_attr();
   BlockGeom bg;
   size_t vol = 1;
@@ -702,13 +757,14 @@ void launch_tune_blockwise(const float* x, const TuneGeom& g, int bs, int Q,
   bg.bs = bs;
   bg.Q = Q;
   bg.frozen_slot = frozen_slot;
-  k_tune_blockwise<<<nblocks, kBlockThreads, vol * sizeof(float), s>>>(
-      x, g, bg, base, allow, bmap);
+  k_tune_blockwise<<<dim3(nblocks, 5), kBlockThreads, vol * sizeof(float), s>>>(
+      x, g, bg, base, allow, scores);
+  k_tune_block_argmin<<<(nblocks + 255) / 256, 256, 0, s>>>(scores, nblocks, bmap);
 }
 
-void launch_tune_cost(const uint32_t* hists, const uint8_t* lens,
-                      unsigned long long* cost, int nvar, cudaStream_t s) {
-  if (nvar > 0) k_tune_cost<<<nvar, 1024, 0, s>>>(hists, lens, cost);
+void launch_tune_cost(const CodebookJob* jobs, int nvar, const uint8_t* lens,
+                      unsigned long long* cost, cudaStream_t s) {
+  if (nvar > 0) k_tune_cost<<<nvar, 1024, 0, s>>>(jobs, lens, cost);
 }
 
 }  // namespace hpez
