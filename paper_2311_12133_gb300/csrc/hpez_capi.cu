@@ -470,6 +470,18 @@ bool plan_md(const hpez_ctx* ctx, const Plan& p, const hpez_config& c, int l,
   return true;
 }
 
+// A 3D multi-dimensional level with every dimension interpolated runs as
+// two launches (even planes, odd planes) of row tiles E1 rows high.
+bool plan_md3(const hpez_ctx* ctx, const Plan& p, const hpez_config& c, int l,
+              bool decomp, LevelMD& F, int& E1) {
+  if (p.ndim != 3 || p.k != 3) return false;
+  if (!plan_md(ctx, p, c, l, decomp, F)) return false;
+  if (F.g.m[0] < 2 || F.g.m[1] < 2 || F.g.m[2] < 2) return false;
+  E1 = 16;
+  while (E1 > 2 && md3_smem_bytes(F, E1) > 96 * 1024) E1 /= 2;
+  return md3_smem_bytes(F, E1) <= 160 * 1024;
+}
+
 // A block map whose blocks all carry the same interpolator is the same
 // predictor as that interpolator (and same-level flag) at every level.
 bool uniform_blockmap(const uint8_t* bm, uint32_t n, uint8_t* v) {
@@ -922,9 +934,14 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
     FusedLevel F;
     Level3D F3;
     LevelMD FM;
+    int E1 = 0;
     if (ctx->fused_levels && plan_level3d(ctx, p, sc, l, false, F3)) {
       launch_level3d(false, F3, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g], s);
       ++nl;
+    } else if (plan_md3(ctx, p, sc, l, false, FM, E1)) {
+      launch_level_md3(false, sb.kind, FM, E1, sb, b.R[l], b.Cg[l], b.R[g],
+                       b.Cg[g], s);
+      nl += 2;
     } else if (plan_md(ctx, p, sc, l, false, FM)) {
       launch_level_md(false, sb.kind, FM, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g],
                       ctx->num_sms, s);
@@ -1129,9 +1146,13 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
     FusedLevel F;
     Level3D F3;
     LevelMD FM;
+    int E1 = 0;
     if (ctx->fused_levels && plan_level3d(ctx, p, sc, l, true, F3)) {
       launch_level3d(true, F3, sb, R[l], nullptr, R[g], nullptr, s);
       ++nl;
+    } else if (plan_md3(ctx, p, sc, l, true, FM, E1)) {
+      launch_level_md3(true, sb.kind, FM, E1, sb, R[l], nullptr, R[g], nullptr, s);
+      nl += 2;
     } else if (plan_md(ctx, p, sc, l, true, FM)) {
       launch_level_md(true, sb.kind, FM, sb, R[l], nullptr, R[g], nullptr,
                       ctx->num_sms, s);

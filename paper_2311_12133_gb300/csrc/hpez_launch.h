@@ -42,6 +42,12 @@ void launch_level_md(bool decomp, int kind, const LevelMD& P, const SweepBufs& B
                      const float* Rc, const uint16_t* Cc, float* Rs, uint16_t* Cs,
                      int num_sms, cudaStream_t s);
 
+// k_level_md3.cu
+size_t md3_smem_bytes(const LevelMD& P, int E1);
+void launch_level_md3(bool decomp, int kind, const LevelMD& P, int E1,
+                      const SweepBufs& B, const float* Rc, const uint16_t* Cc,
+                      float* Rs, uint16_t* Cs, cudaStream_t s);
+
 // k_huffman.cu
 void launch_hist(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,
                  uint32_t* hist, uint32_t* zc, const Ctl* ctl, int num_sms,
