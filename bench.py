@@ -60,6 +60,9 @@ def parse():
                     help="skip the 64-field batched-vs-plain measurement")
     ap.add_argument("--no-served", action="store_true",
                     help="skip the served-form measurement")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="time the default predictor instead of auto-tuning "
+                         "(for profiles of that path)")
     return ap.parse_args()
 
 
@@ -457,10 +460,16 @@ def main():
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
 
-    def step():
-        size = hpez.hpez_compress_auto(ctx.handle, x.data_ptr(), shape,
+    def compress():
+        if args.no_tune:
+            return hpez.hpez_compress(ctx.handle, x.data_ptr(), shape, hpez.HPEZ_EB_REL,
+                                      args.eb, None, cbuf.data_ptr(), cap, sptr)
+        return hpez.hpez_compress_auto(ctx.handle, x.data_ptr(), shape,
                                        hpez.HPEZ_EB_REL, args.eb, None,
                                        cbuf.data_ptr(), cap, sptr)
+
+    def step():
+        size = compress()
         hpez.hpez_decompress(ctx.handle, cbuf.data_ptr(), size, y.data_ptr(), N, sptr)
         return size
 
@@ -483,9 +492,7 @@ def main():
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
     ev[0].record(stream)
     for k in range(args.steps):
-        size = hpez.hpez_compress_auto(ctx.handle, x.data_ptr(), shape,
-                                       hpez.HPEZ_EB_REL, args.eb, None,
-                                       cbuf.data_ptr(), cap, sptr)
+        size = compress()
         ev[2 * k + 1].record(stream)
         hpez.hpez_decompress(ctx.handle, cbuf.data_ptr(), size, y.data_ptr(), N, sptr)
         ev[2 * k + 2].record(stream)
@@ -616,8 +623,10 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"grf k^-5/3 float32 {'x'.join(map(str, shape))} per GPU, "
-                                   f"rel eb {args.eb}, full auto-tuning + compress "
-                                   "(hpez_compress_auto) + decompress",
+                                   f"rel eb {args.eb}, " + (
+                                       "default predictor (no tuning)" if args.no_tune else
+                                       "full auto-tuning + compress (hpez_compress_auto)")
+                                   + " + decompress",
                        "global_batch": world, "parallelism": f"replicas{world}",
                        "l2": f"input {4 * N / 1e6:.0f} MB > L2 {L2_BYTES / 1e6:.0f} MB, no flush"},
             "compress_gbps": round(world * 4 * N / (comp_ms / args.steps / 1e3) / 1e9, 3),
