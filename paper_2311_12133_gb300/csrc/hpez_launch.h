@@ -157,11 +157,19 @@ void launch_tune_stats(const float* x, const uint32_t n[3],
 void launch_tune_params(TuneCfg* cfgs, int nvar, int L, const Ctl* ctl,
                         cudaStream_t s);
 size_t tune_test_smem(const TuneGeom& g);
-// (sample block, variant) CTAs; variants < ny0 use geometry g0, the rest g1
+// (sample block, variant) CTAs; variants < ny0 use geometry g0, the rest g1.
+// state: each block's reconstruction after the levels above l_stop (run
+// level l_stop only), or null (run levels L..l_stop from the anchors)
 void launch_tune_test(const float* x, const TuneGeom& g0, const TuneGeom& g1,
                       int ny0, const TuneCfg* cfgs, int nvar, int nblk,
                       int l_stop, bool hist, unsigned long long* score,
-                      uint32_t* hists, unsigned long long* nout, cudaStream_t s);
+                      uint32_t* hists, unsigned long long* nout, float* state,
+                      cudaStream_t s);
+// runs level l with the chosen config of each of nv variants and keeps the
+// result in state
+void launch_tune_advance(const float* x, const TuneGeom& g0, const TuneGeom& g1,
+                         int nv, int nblk, const TuneCfg* cfgs, int l, float* state,
+                         cudaStream_t s);
 void launch_tune_lorenzo(const float* x, const TuneGeom& g, int nblk,
                          const Ctl* ctl, uint32_t* hists,
                          unsigned long long* nout, cudaStream_t s);

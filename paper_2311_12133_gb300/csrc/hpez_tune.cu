@@ -117,6 +117,7 @@ struct Bufs {
   uint32_t* gpar;
   uint8_t* bmap;
   unsigned long long* bscore;  // block-wise candidate scores
+  float* state;                // sample blocks' reconstruction, per variant
 };
 
 struct Call {
@@ -297,10 +298,11 @@ int tune_globals(Call& k, std::vector<Variant>& vs, hpez_tune_report* rep,
                       cudaMemcpyHostToDevice, k.s);
       launch_tune_params(k.b.cfgs, at, kMaxLevels, k.b.ctl, k.s);
       cudaMemsetAsync(k.b.score, 0, sizeof(unsigned long long) * at, k.s);
-      // every variant's candidates in one launch (escapes unused here)
+      // every variant's candidates in one launch (escapes unused here),
+      // from the blocks' state after the levels above l
       launch_tune_test(k.x, vs[0].g, vs[nv - 1].g, (int)vs[0].cands.size(),
                        k.b.cfgs, at, vs[0].nblk, l, false, k.b.score, nullptr,
-                       k.b.nout + kMaxHists, k.s);
+                       k.b.nout + kMaxHists, k.b.state, k.s);
       nl += 2;
       prof.end(k.s);
       cudaMemcpyAsync(sc.data(), k.b.score, sizeof(unsigned long long) * at,
@@ -316,6 +318,18 @@ int tune_globals(Call& k, std::vector<Variant>& vs, hpez_tune_report* rep,
           rep->level_choice[vs[i].slot][l - 1] = (uint8_t)best;
           rep->level_score[vs[i].slot][l - 1] = sc[base[i] + best];
         }
+      }
+      if (l > 1) {
+        // the chosen level l of each variant, kept for the finer levels
+        for (int i = 0; i < nv; ++i) host[i] = to_device(vs[i].p, vs[i].cfg);
+        prof.begin(HPEZ_PH_TUNE_LEVELS, k.s);
+        cudaMemcpyAsync(k.b.cfgs, host.data(), sizeof(TuneCfg) * nv,
+                        cudaMemcpyHostToDevice, k.s);
+        launch_tune_params(k.b.cfgs, nv, kMaxLevels, k.b.ctl, k.s);
+        launch_tune_advance(k.x, vs[0].g, vs[nv - 1].g, nv, vs[0].nblk, k.b.cfgs, l,
+                            k.b.state, k.s);
+        nl += 2;
+        prof.end(k.s);
       }
     }
   }
@@ -346,7 +360,7 @@ int tune_globals(Call& k, std::vector<Variant>& vs, hpez_tune_report* rep,
   cudaMemsetAsync(k.b.nout, 0, sizeof(unsigned long long) * nh, k.s);
   cudaMemsetAsync(k.b.score, 0, sizeof(unsigned long long) * nh, k.s);
   launch_tune_test(k.x, vs[0].g, vs[nv - 1].g, ng, k.b.cfgs, nh, vs[0].nblk, 1,
-                   true, k.b.score, k.b.hists, k.b.nout, k.s);
+                   true, k.b.score, k.b.hists, k.b.nout, nullptr, k.s);
   nl += 2;
   // the codebooks of these histograms and of the extra ones (the Lorenzo
   // tests, run on the side stream) in one launch
@@ -463,6 +477,11 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
   const size_t o_gpar = ar.take<uint32_t>((size_t)131072 * kMaxHists);
   const size_t o_bmap = ar.take<uint8_t>(nbm ? nbm : 1);
   const size_t o_bscore = ar.take<unsigned long long>(5 * (nbm ? nbm : 1));
+  // the sample blocks' state, per frozen-dimension variant
+  TuneGeom gs;
+  const int nblk0 = sample_geometry(p0, tp, gs);
+  const size_t o_state =
+      ar.take<float>(2 * (size_t)nblk0 * (tune_test_smem(gs) / sizeof(float)));
   if ((rc = ensure_scratch(ctx, ar.off))) return rc;
   char* base = ctx->scratch;
   Call k;
@@ -490,6 +509,7 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
   k.b.gpar = reinterpret_cast<uint32_t*>(base + o_gpar);
   k.b.bmap = reinterpret_cast<uint8_t*>(base + o_bmap);
   k.b.bscore = reinterpret_cast<unsigned long long*>(base + o_bscore);
+  k.b.state = reinterpret_cast<float*>(base + o_state);
   uint64_t& nl = ctx->launches;
   PhaseProfiler& prof = ctx->prof;
 
@@ -651,7 +671,7 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
     launch_tune_blockwise(d_in, g, bsz, Q,
                           out.frozen_dim < 0 ? -1 : out.frozen_dim + p.off, nb,
                           (uint32_t)nbm, k.b.cfgs, allow, k.b.bscore, k.b.bmap, s);
-    nl += 3;
+    nl += 5;
     prof.end(s);
     cudaMemcpyAsync(h_blockmap, k.b.bmap, nbm, cudaMemcpyDeviceToHost, s);
     if ((rc = sync_check(k))) return rc;

@@ -121,22 +121,22 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------
 // level error bounds of every variant (Eq. 15), as the compressor does
 // ---------------------------------------------------------------------
+// one thread per (variant, level)
 __global__ void k_tune_params(TuneCfg* cfgs, int nvar, int L,
                               const Ctl* __restrict__ ctl) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = t / L, l = t % L + 1;
   if (v >= nvar) return;
   TuneCfg& c = cfgs[v];
   const float e = ctl->e;
-  for (int l = 1; l <= L; ++l) {
-    double ap = 1.0;
-    for (int i = 1; i < l; ++i) ap = __dmul_rn(ap, c.alpha);
-    const double m = ap < c.beta ? ap : c.beta;
-    const float el = __double2float_rn(__ddiv_rn((double)e, m));
-    c.el[l - 1] = el;
-    c.twoe[l - 1] = __fmul_rn(2.0f, el);
-    c.inv2[l - 1] = __double2float_rn(__ddiv_rn(1.0, __dmul_rn(2.0, (double)el)));
-    c.inv_el[l - 1] = __double2float_rn(__ddiv_rn(1.0, (double)el));
-  }
+  double ap = 1.0;
+  for (int i = 1; i < l; ++i) ap = __dmul_rn(ap, c.alpha);
+  const double m = ap < c.beta ? ap : c.beta;
+  const float el = __double2float_rn(__ddiv_rn((double)e, m));
+  c.el[l - 1] = el;
+  c.twoe[l - 1] = __fmul_rn(2.0f, el);
+  c.inv2[l - 1] = __double2float_rn(__ddiv_rn(1.0, __dmul_rn(2.0, (double)el)));
+  c.inv_el[l - 1] = __double2float_rn(__ddiv_rn(1.0, (double)el));
 }
 
 // ---------------------------------------------------------------------
@@ -389,11 +389,13 @@ __device__ void sweep_pass(float* R, const Sub& f, const Box* bx, int nb,
   }
 }
 
-template <bool kHist>
-__device__ void sweep_level(float* R, const Sub& f, const int interp[3],
-                            int k, int l, const TuneCfg& c, bool score_on,
-                            unsigned long long& score, const HistSink& hist,
-                            unsigned long long& nout) {
+// KIND < 0: the level's interpolator read from the config; KIND >= 0:
+// fixed (the config's value is that kind)
+template <int KIND, bool kHist>
+__device__ void sweep_level_k(float* R, const Sub& f, const int interp[3],
+                              int k, int l, const TuneCfg& c, bool score_on,
+                              unsigned long long& score, const HistSink& hist,
+                              unsigned long long& nout) {
   const int sh = l - 1, s = 1 << sh;
   int line[3];
   unsigned imask = 0;
@@ -431,7 +433,10 @@ __device__ void sweep_level(float* R, const Sub& f, const int interp[3],
     else if (ps == 1) HPEZ_SWEEP(K, false, 1);                                \
     else HPEZ_SWEEP(K, false, 2);                                             \
   } while (0)
-      if (md) {
+      if (KIND >= 0) {
+        if (md) HPEZ_SWEEP(KIND < 0 ? 0 : KIND, true, 0);
+        else HPEZ_SWEEP_1D(KIND < 0 ? 0 : KIND);
+      } else if (md) {
         if (kind == LINEAR) HPEZ_SWEEP(LINEAR, true, 0);
         else if (kind == CUBIC_NAK) HPEZ_SWEEP(CUBIC_NAK, true, 0);
         else HPEZ_SWEEP(CUBIC_NAT, true, 0);
@@ -447,6 +452,16 @@ __device__ void sweep_level(float* R, const Sub& f, const int interp[3],
   }
 }
 
+template <bool kHist>
+__device__ __forceinline__ void sweep_level(float* R, const Sub& f,
+                                            const int interp[3], int k, int l,
+                                            const TuneCfg& c, bool score_on,
+                                            unsigned long long& score,
+                                            const HistSink& hist,
+                                            unsigned long long& nout) {
+  sweep_level_k<-1, kHist>(R, f, interp, k, l, c, score_on, score, hist, nout);
+}
+
 __device__ __forceinline__ void load_cfg(TuneCfg* dst, const TuneCfg* src) {
   const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
   uint32_t* d = reinterpret_cast<uint32_t*>(dst);
@@ -458,15 +473,48 @@ __device__ __forceinline__ void load_cfg(TuneCfg* dst, const TuneCfg* src) {
 // ---------------------------------------------------------------------
 // Sec. 6.2 / 6.4: CTA (sample block, variant): anchors, levels L..l_stop
 // ---------------------------------------------------------------------
+// the points of the sub-field whose interpolation coordinates are multiples
+// of st, copied between shared memory and a state buffer of the same layout
+template <bool kLoad>
+__device__ void copy_lattice(float* R, float* __restrict__ state, const Sub& f,
+                             const int interp[3], int st) {
+  int m[3], sp[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    sp[d] = interp[d] ? st : 1;
+    m[d] = (f.n[d] + sp[d] - 1) / sp[d];
+  }
+  const unsigned mg2 = fdiv_magic((unsigned)m[2]), mg1 = fdiv_magic((unsigned)m[1]);
+  const int tot = m[0] * m[1] * m[2];
+  for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+    const unsigned r1 = fdiv((unsigned)q, mg2);
+    const unsigned r0 = fdiv(r1, mg1);
+    const int c2 = (q - (int)r1 * m[2]) * sp[2];
+    const int c1 = ((int)r1 - (int)r0 * m[1]) * sp[1];
+    const int c0 = (int)r0 * sp[0];
+    const int i = c0 * f.st[0] + c1 * f.st[1] + c2;
+    if (kLoad)
+      R[i] = state[i];
+    else
+      state[i] = R[i];
+  }
+  __syncthreads();
+}
+
 // Variants y < ny0 use geometry g0, the others g1 (two frozen-dimension
-// choices in one launch).
+// choices in one launch).  With a state buffer (candidate tests of level
+// l_stop), a CTA starts from its block's reconstruction after the coarser
+// levels, kept there by k_tune_advance, and runs level l_stop only;
+// without one it starts from the anchors and runs levels L..l_stop.
 template <bool kHist>
 __global__ void __launch_bounds__(kTuneThreads)
     k_tune_test(const float* __restrict__ x, TuneGeom g0, TuneGeom g1, int ny0,
                 const TuneCfg* __restrict__ cfgs, int l_stop,
                 unsigned long long* score, uint32_t* hists,
-                unsigned long long* nout) {
-  const TuneGeom& g = (int)blockIdx.y < ny0 ? g0 : g1;
+                unsigned long long* nout, float* __restrict__ state,
+                unsigned vol) {
+  const bool second = (int)blockIdx.y >= ny0;
+  const TuneGeom& g = second ? g1 : g0;
   extern __shared__ float R[];
   __shared__ TuneCfg c;
   __shared__ unsigned long long red[32];
@@ -476,10 +524,17 @@ __global__ void __launch_bounds__(kTuneThreads)
     for (int i = threadIdx.x; i < kWin; i += blockDim.x) win[i] = 0;
   load_cfg(&c, cfgs + v);
   const Sub f = sample_block(x, g, blockIdx.x);
-  init_anchors(R, f, g.interp, g.A);
+  int l_top = g.L;
+  if (state && l_stop < g.L) {
+    float* st = state + ((size_t)(second ? 1 : 0) * gridDim.x + blockIdx.x) * vol;
+    copy_lattice<true>(R, st, f, g.interp, 2 << (l_stop - 1));
+    l_top = l_stop;
+  } else {
+    init_anchors(R, f, g.interp, g.A);
+  }
   unsigned long long sc = 0, no = 0;
   HistSink h{win, kHist ? hists + (size_t)v * 65536 : nullptr};
-  for (int l = g.L; l >= l_stop; --l)
+  for (int l = l_top; l >= l_stop; --l)
     sweep_level<kHist>(R, f, g.interp, g.k, l, c, l == l_stop, sc, h, no);
   if (kHist)
     for (int i = threadIdx.x; i < kWin; i += blockDim.x)
@@ -488,6 +543,30 @@ __global__ void __launch_bounds__(kTuneThreads)
   if (threadIdx.x == 0 && sc) atomicAdd(score + v, sc);
   no = block_sum(no, red);
   if (threadIdx.x == 0 && no) atomicAdd(nout + v, no);
+}
+
+// After level l's choice: CTA (sample block, variant w) runs level l with
+// the chosen config cfgs[w] from the block's state (the anchors at the
+// coarsest level) and stores the stride-2^(l-1) lattice back.
+__global__ void __launch_bounds__(kTuneThreads)
+    k_tune_advance(const float* __restrict__ x, TuneGeom g0, TuneGeom g1,
+                   const TuneCfg* __restrict__ cfgs, int l,
+                   float* __restrict__ state, unsigned vol) {
+  const int w = blockIdx.y;
+  const TuneGeom& g = w ? g1 : g0;
+  extern __shared__ float R[];
+  __shared__ TuneCfg c;
+  load_cfg(&c, cfgs + w);
+  const Sub f = sample_block(x, g, blockIdx.x);
+  float* st = state + ((size_t)w * gridDim.x + blockIdx.x) * vol;
+  if (l == g.L)
+    init_anchors(R, f, g.interp, g.A);
+  else
+    copy_lattice<true>(R, st, f, g.interp, 2 << (l - 1));
+  unsigned long long sc = 0, no = 0;
+  const HistSink none{nullptr, nullptr};
+  sweep_level<false>(R, f, g.interp, g.k, l, c, false, sc, none, no);
+  copy_lattice<false>(R, st, f, g.interp, 1 << (l - 1));
 }
 
 // ---------------------------------------------------------------------
@@ -578,15 +657,19 @@ struct BlockGeom {
 
 // CTA (field block, candidate j): the summed level score of the centred
 // sub-block with candidate j at every level; ~0 for a candidate not allowed
+// one launch per interpolator kind: candidate j of the launch is
+// kBlockCodes[j0 + j]
+template <int KIND>
 __global__ void __launch_bounds__(kBlockThreads)
     k_tune_blockwise(const float* __restrict__ x, TuneGeom g, BlockGeom bg,
-                     const TuneCfg* __restrict__ base, unsigned allow,
+                     const TuneCfg* __restrict__ base, unsigned allow, int j0,
                      unsigned long long* scores) {
   extern __shared__ float R[];
   __shared__ TuneCfg c;
   __shared__ unsigned long long red[32];
-  const uint8_t v = kBlockCodes[blockIdx.y];
-  unsigned long long* out = scores + (size_t)blockIdx.x * 5 + blockIdx.y;
+  const int jj = j0 + (int)blockIdx.y;
+  const uint8_t v = kBlockCodes[jj];
+  unsigned long long* out = scores + (size_t)blockIdx.x * 5 + jj;
   if (((v & 3) == CUBIC_NAT && !(allow & 1u)) || ((v & 4) && !(allow & 2u))) {
     if (threadIdx.x == 0) *out = ~0ull;
     return;
@@ -627,7 +710,7 @@ __global__ void __launch_bounds__(kBlockThreads)
   unsigned long long sc = 0, no = 0;
   const HistSink none{nullptr, nullptr};
   for (int l = L; l >= 1; --l)
-    sweep_level<false>(R, f, g.interp, g.k, l, c, true, sc, none, no);
+    sweep_level_k<KIND, false>(R, f, g.interp, g.k, l, c, true, sc, none, no);
   sc = block_sum(sc, red);
   if (threadIdx.x == 0) *out = sc;
 }
@@ -676,7 +759,16 @@ void set_smem_attr() {
   cudaFuncSetAttribute(k_tune_lorenzo,
                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)kTuneSmemMax);
-  cudaFuncSetAttribute(k_tune_blockwise,
+  cudaFuncSetAttribute(k_tune_advance,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kTuneSmemMax);
+  cudaFuncSetAttribute(k_tune_blockwise<LINEAR>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kTuneSmemMax);
+  cudaFuncSetAttribute(k_tune_blockwise<CUBIC_NAK>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kTuneSmemMax);
+  cudaFuncSetAttribute(k_tune_blockwise<CUBIC_NAT>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)kTuneSmemMax);
   done = true;
@@ -712,7 +804,8 @@ void launch_tune_stats(const float* x, const uint32_t n[3],
 
 void launch_tune_params(TuneCfg* cfgs, int nvar, int L, const Ctl* ctl,
                         cudaStream_t s) {
-  k_tune_params<<<(nvar + 63) / 64, 64, 0, s>>>(cfgs, nvar, L, ctl);
+  const int n = nvar * L;
+  k_tune_params<<<(n + 127) / 128, 128, 0, s>>>(cfgs, nvar, L, ctl);
 }
 
 size_t tune_test_smem(const TuneGeom& g) {
@@ -722,16 +815,28 @@ size_t tune_test_smem(const TuneGeom& g) {
 void launch_tune_test(const float* x, const TuneGeom& g0, const TuneGeom& g1,
                       int ny0, const TuneCfg* cfgs, int nvar, int nblk,
                       int l_stop, bool hist, unsigned long long* score,
-                      uint32_t* hists, unsigned long long* nout, cudaStream_t s) {
+                      uint32_t* hists, unsigned long long* nout, float* state,
+                      cudaStream_t s) {
   set_smem_attr();
   const dim3 grid((unsigned)nblk, (unsigned)nvar);
   const size_t sm = std::max(tune_test_smem(g0), tune_test_smem(g1));
+  const unsigned vol = (unsigned)(tune_test_smem(g0) / sizeof(float));
   if (hist)
     k_tune_test<true><<<grid, kTuneThreads, sm, s>>>(x, g0, g1, ny0, cfgs, l_stop,
-                                                     score, hists, nout);
+                                                     score, hists, nout, state, vol);
   else
     k_tune_test<false><<<grid, kTuneThreads, sm, s>>>(x, g0, g1, ny0, cfgs, l_stop,
-                                                      score, hists, nout);
+                                                      score, hists, nout, state, vol);
+}
+
+void launch_tune_advance(const float* x, const TuneGeom& g0, const TuneGeom& g1,
+                         int nv, int nblk, const TuneCfg* cfgs, int l, float* state,
+                         cudaStream_t s) {
+  set_smem_attr();
+  const size_t sm = std::max(tune_test_smem(g0), tune_test_smem(g1));
+  const unsigned vol = (unsigned)(tune_test_smem(g0) / sizeof(float));
+  k_tune_advance<<<dim3((unsigned)nblk, (unsigned)nv), kTuneThreads, sm, s>>>(
+      x, g0, g1, cfgs, l, state, vol);
 }
 
 void launch_tune_lorenzo(const float* x, const TuneGeom& g, int nblk,
@@ -757,8 +862,13 @@ void launch_tune_blockwise(const float* x, const TuneGeom& g, int bs, int Q,
   bg.bs = bs;
   bg.Q = Q;
   bg.frozen_slot = frozen_slot;
-  k_tune_blockwise<<<dim3(nblocks, 5), kBlockThreads, vol * sizeof(float), s>>>(
-      x, g, bg, base, allow, scores);
+  // codes 0 | 1, 5 | 2, 6: linear, not-a-knot, natural
+  k_tune_blockwise<LINEAR><<<dim3(nblocks, 1), kBlockThreads, vol * sizeof(float), s>>>(
+      x, g, bg, base, allow, 0, scores);
+  k_tune_blockwise<CUBIC_NAK><<<dim3(nblocks, 2), kBlockThreads, vol * sizeof(float), s>>>(
+      x, g, bg, base, allow, 1, scores);
+  k_tune_blockwise<CUBIC_NAT><<<dim3(nblocks, 2), kBlockThreads, vol * sizeof(float), s>>>(
+      x, g, bg, base, allow, 3, scores);
   k_tune_block_argmin<<<(nblocks + 255) / 256, 256, 0, s>>>(scores, nblocks, bmap);
 }
 
