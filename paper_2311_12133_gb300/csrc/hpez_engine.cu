@@ -112,6 +112,20 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   plan_chunks_blocks(p, cfg);
   r.decomp = 0;
   r.N = p.N;
+  // the predictor the sweep runs (a uniform block map becomes its
+  // interpolator); the header keeps the configuration as given
+  const hpez_config sc = sweep_config(cfg, cfg.h_blockmap, p.nblocks);
+  ctx->x_aligned16 = (reinterpret_cast<uintptr_t>(d_in) & 15u) == 0;
+  // the finest level's fused kernels write no reconstruction in compress:
+  // its grid is then not allocated
+  bool need_r0 = true;
+  {
+    FusedLevel F;
+    Level3D F3;
+    if (ctx->fused_levels && (plan_level3d(ctx, p, sc, 1, false, F3) ||
+                              plan_fused(ctx, p, sc, 1, false, F)))
+      need_r0 = false;
+  }
 
   Arena ar;
   const size_t o_ctl = ar.take<Ctl>(1);
@@ -125,7 +139,7 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   const size_t o_gpar = ar.take<uint32_t>(131072);
   size_t o_R[kMaxLevels + 1], o_C[kMaxLevels + 1];
   for (int g = 0; g <= p.L; ++g) {
-    o_R[g] = ar.take<float>(p.gsize[g]);
+    o_R[g] = (g > 0 || need_r0) ? ar.take<float>(p.gsize[g]) : 0;
     o_C[g] = ar.take<uint16_t>(p.gsize[g]);
   }
   const size_t o_zc = ar.take<uint32_t>(p.nch);
@@ -151,7 +165,7 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   float* R[kMaxLevels + 1];
   uint16_t* Cg[kMaxLevels + 1];
   for (int g = 0; g <= p.L; ++g) {
-    R[g] = reinterpret_cast<float*>(base + o_R[g]);
+    R[g] = (g > 0 || need_r0) ? reinterpret_cast<float*>(base + o_R[g]) : nullptr;
     Cg[g] = reinterpret_cast<uint16_t*>(base + o_C[g]);
   }
   uint32_t* zc = reinterpret_cast<uint32_t*>(base + o_zc);
@@ -204,7 +218,6 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
                         AnchorJob{d_in, p.grid[p.L], p.gsize[p.L], R[p.L],
                                   Cg[p.L], ctl},
                         grid_blocks(p.gsize[p.L], 65535)));
-  const hpez_config sc = sweep_config(cfg, cfg.h_blockmap, p.nblocks);
   SweepBufs sb;
   std::memset(&sb, 0, sizeof(sb));
   sb.x = d_in;
@@ -212,7 +225,6 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   sb.bs = (uint32_t)(cfg.block_size > 0 ? cfg.block_size : 1);
   for (int s3 = 0; s3 < 3; ++s3) sb.nb[s3] = p.nb[s3];
   sb.ctl = ctl;
-  ctx->x_aligned16 = (reinterpret_cast<uintptr_t>(d_in) & 15u) == 0;
   for (int l = p.L; l >= 1; --l) {
     const int g = l - 1;
     sb.R = R[g];
@@ -534,6 +546,55 @@ void launch_entry(const Entry& e, const unsigned char* d_tab, cudaStream_t s) {
   }
 }
 
+// A tick's launches of different operation kinds are independent (they
+// belong to different requests): they fan out over a main stream and up to
+// kSide side streams, joined again at the end of the tick.
+constexpr int kSide = 3;
+
+struct TickStreams {
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kSide] = {};
+  int create() {
+    int rc = cuda_check(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    for (int i = 0; !rc && i < kSide; ++i) {
+      rc = cuda_check(cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking));
+      if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming));
+    }
+    return rc;
+  }
+  void destroy() {
+    for (int i = 0; i < kSide; ++i) {
+      if (side[i]) cudaStreamDestroy(side[i]);
+      if (join[i]) cudaEventDestroy(join[i]);
+      side[i] = nullptr;
+      join[i] = nullptr;
+    }
+    if (fork) cudaEventDestroy(fork);
+    fork = nullptr;
+  }
+};
+
+void enqueue_tick(const std::vector<Entry>& es, const unsigned char* d_tab,
+                  cudaStream_t s, TickStreams& ts) {
+  const int n = (int)es.size();
+  const int nside = std::min(kSide, n - 1);
+  if (nside <= 0 || !ts.fork) {
+    for (const Entry& e : es) launch_entry(e, d_tab, s);
+    return;
+  }
+  cudaEventRecord(ts.fork, s);
+  for (int i = 0; i < nside; ++i) cudaStreamWaitEvent(ts.side[i], ts.fork, 0);
+  for (int i = 0; i < n; ++i) {
+    const int k = i % (nside + 1);
+    launch_entry(es[i], d_tab, k == 0 ? s : ts.side[k - 1]);
+  }
+  for (int i = 0; i < nside; ++i) {
+    cudaEventRecord(ts.join[i], ts.side[i]);
+    cudaStreamWaitEvent(s, ts.join[i], 0);
+  }
+}
+
 int upload(const Request& r) {
   for (const Upload& u : r.uploads)
     if (cudaMemcpy(u.dst, u.bytes.data(), u.bytes.size(), cudaMemcpyHostToDevice) !=
@@ -559,6 +620,7 @@ struct hpez_batch {
   uint64_t launches = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  TickStreams ts;
 };
 
 namespace {
@@ -627,6 +689,11 @@ int batch_create(hpez_ctx* ctx, int n, int decomp, const void* descs,
     b->launches += es.size();
     b->ticks.push_back(std::move(es));
   }
+  if (b->ts.create()) {
+    cudaGetLastError();
+    hpez_batch_destroy(b);
+    return HPEZ_ERR_CUDA;
+  }
   if (cudaMalloc(&b->d_tab, tab.size() ? tab.size() : 256) != cudaSuccess) {
     cudaGetLastError();
     hpez_batch_destroy(b);
@@ -643,8 +710,7 @@ int batch_create(hpez_ctx* ctx, int n, int decomp, const void* descs,
 }
 
 void batch_enqueue(hpez_batch* b, cudaStream_t s) {
-  for (const auto& es : b->ticks)
-    for (const Entry& e : es) launch_entry(e, b->d_tab, s);
+  for (const auto& es : b->ticks) enqueue_tick(es, b->d_tab, s, b->ts);
 }
 
 }  // namespace
@@ -727,6 +793,7 @@ int hpez_batch_destroy(hpez_batch* b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->ws) cudaFree(b->ws);
   if (b->d_tab) cudaFree(b->d_tab);
+  b->ts.destroy();
   delete b;
   return HPEZ_OK;
 }
@@ -742,6 +809,7 @@ enum ReqState { RS_QUEUED, RS_ACTIVE, RS_RESULT, RS_COPYING, RS_DONE };
 
 struct SrvReq {
   uint64_t id = 0;
+  bool full_bound = false;  // compress output sized by hpez_compress_bound
   hpez_request rq;
   hpez_config cfg;
   bool has_cfg = false;
@@ -840,6 +908,7 @@ struct hpez_server {
   unsigned char* d_tab = nullptr;
   size_t d_tab_cap = 0;
   uint64_t ticks = 0, launches = 0;
+  TickStreams ts;
 };
 
 namespace {
@@ -854,6 +923,9 @@ int srv_plan(hpez_server* S, SrvReq* q, char* base) {
     uint64_t bound = 0;
     int rc = hpez_compress_bound(r.ndim, r.dims, &bound);
     if (rc) return rc;
+    // the stream rarely needs the bound (every point an outlier); start
+    // with 4.5 bytes per point and retry with the bound if that overflows
+    if (!q->full_bound) bound = std::min<uint64_t>(bound, N * 9 / 2 + (1u << 20));
     const size_t o_in = 0, o_out = al256(N * 4), o_ws = o_out + al256(bound);
     float* d_in = base ? reinterpret_cast<float*>(base + o_in) : reinterpret_cast<float*>(256);
     void* d_out = base ? base + o_out : reinterpret_cast<void*>(512);
@@ -913,7 +985,8 @@ int hpez_server_create(hpez_ctx* ctx, uint64_t budget_bytes, int max_slots,
   for (int k = 0; ok && k < kRing; ++k)
     ok = cudaEventCreateWithFlags(&S->tab_ev[k], cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&S->s_in, cudaStreamNonBlocking) == cudaSuccess &&
-       cudaStreamCreateWithFlags(&S->s_out, cudaStreamNonBlocking) == cudaSuccess;
+       cudaStreamCreateWithFlags(&S->s_out, cudaStreamNonBlocking) == cudaSuccess &&
+       S->ts.create() == HPEZ_OK;
   if (!ok) {
     cudaGetLastError();
     hpez_server_destroy(S);
@@ -992,6 +1065,22 @@ int hpez_server_step(hpez_server* S) {
           q->size = q->plan.out_cap;
         }
       }
+      if (q->status == HPEZ_ERR_OUT_TOO_SMALL && !q->plan.decomp && !q->full_bound &&
+          q->size == 0) {
+        // the short output overflowed: run again with the full bound
+        cudaEventDestroy(q->ev);
+        cudaEventDestroy(q->ev_in);
+        q->ev = q->ev_in = nullptr;
+        S->pool.release(q->pool_off, q->need);
+        S->free_slots.push_back(q->slot);
+        q->full_bound = true;
+        q->status = 0;
+        q->state = RS_QUEUED;
+        srv_plan(S, q, nullptr);
+        S->queue.push_front(q);
+        S->active.erase(S->active.begin() + i);
+        continue;
+      }
       if (!q->status) {
         const size_t o_out = al256(q->plan.in_bytes);
         cudaMemcpyAsync(q->rq.h_out, base + o_out, q->size, cudaMemcpyDeviceToHost,
@@ -1018,6 +1107,13 @@ int hpez_server_step(hpez_server* S) {
   // 2. admit, first come first served
   while (!S->queue.empty() && !S->free_slots.empty()) {
     SrvReq* q = S->queue.front();
+    if (q->need > S->budget) {  // a retry that can never fit
+      S->queue.pop_front();
+      q->status = HPEZ_ERR_TOO_LARGE;
+      q->state = RS_DONE;
+      S->done.push_back(q);
+      continue;
+    }
     size_t off;
     if (!S->pool.alloc(q->need, &off)) break;
     S->queue.pop_front();
@@ -1094,7 +1190,7 @@ int hpez_server_step(hpez_server* S) {
   cudaMemcpyAsync(S->d_tab, S->h_tab[k], tab.size(), cudaMemcpyHostToDevice, s);
   cudaEventRecord(S->tab_ev[k], s);
   S->tab_used[k] = true;
-  for (const Entry& e : es) launch_entry(e, S->d_tab, s);
+  enqueue_tick(es, S->d_tab, s, S->ts);
   S->launches += es.size();
   S->ctx->launches += es.size();
   ++S->ticks;
@@ -1153,6 +1249,7 @@ int hpez_server_destroy(hpez_server* S) {
   }
   if (S->s_in) cudaStreamDestroy(S->s_in);
   if (S->s_out) cudaStreamDestroy(S->s_out);
+  S->ts.destroy();
   for (SrvReq* q : S->done) delete q;
   for (int k = 0; k < kRing; ++k) {
     if (S->h_tab[k]) cudaFreeHost(S->h_tab[k]);
