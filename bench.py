@@ -318,7 +318,7 @@ def bench_batched(ctx, steps, warmup):
             "graph": True}
 
 
-def bench_served(ctx, seconds=3.0, rate=200.0):
+def bench_served(ctx, seconds=3.0, rate=200.0, slots=256):
     """Poisson stream of compress/decompress requests over fields of 1 MB ..
     512 MB (log-uniform), rel eb from {1e-2,1e-3,1e-4}, host buffers,
     40 GB device budget; the served loop against one single-field host call
@@ -366,7 +366,7 @@ def bench_served(ctx, seconds=3.0, rate=200.0):
     total = sum(pool[i]["nbytes"] for _, i, _ in arr)
 
     def ours(burst):
-        srv = hpez.Server(ctx, 40 << 30, max_slots=64)
+        srv = hpez.Server(ctx, 40 << 30, max_slots=slots)
         lat, pend, k = {}, {}, 0
         start = time.perf_counter()
         while k < len(arr) or pend:
@@ -417,7 +417,7 @@ def bench_served(ctx, seconds=3.0, rate=200.0):
     ours(True)  # warm-up of the served path
     r = {"workload": f"Poisson {rate:g} req/s for {seconds:g} s, {len(arr)} requests "
                      f"(compress or decompress, 1 MB..512 MB log-uniform, 12-field pool), "
-                     f"host buffers, 40 GB budget, 64 slots",
+                     f"host buffers, 40 GB budget, {slots} slots",
          "input_GB": round(total / 1e9, 3),
          "poisson": ours(False), "plain_poisson": plain(False),
          "saturated": ours(True), "plain_saturated": plain(True)}

@@ -257,7 +257,7 @@ HPEZ_API int hpez_server_create(hpez_ctx* ctx, uint64_t budget_bytes,
 HPEZ_API int hpez_server_submit(hpez_server* s, const hpez_request* req,
                                 uint64_t* id);
 /* One step: retire, admit, one tick.  Never waits for the GPU except to
- * reuse a job-table buffer (at most 4 ticks in flight). */
+ * reuse a job-table buffer (at most 8 ticks in flight). */
 HPEZ_API int hpez_server_step(hpez_server* s);
 /* Completed requests since the last poll (up to cap): id, status, result
  * bytes, latency from submit to completion in seconds. */

@@ -877,7 +877,7 @@ struct Pool {
   }
 };
 
-constexpr int kRing = 4;
+constexpr int kRing = 8;
 
 }  // namespace
 
@@ -1150,8 +1150,10 @@ int hpez_server_step(hpez_server* S) {
   std::vector<SrvReq*> finishing;
   for (SrvReq* q : S->active) {
     if (q->state != RS_ACTIVE) continue;
-    if (q->wait_in) {  // its first operation waits for its input copy
-      cudaStreamWaitEvent(s, q->ev_in, 0);
+    if (q->wait_in) {
+      // a request joins the ticks once its input is on the device, so
+      // the copies of later requests overlap the work of earlier ones
+      if (cudaEventQuery(q->ev_in) != cudaSuccess) continue;
       q->wait_in = false;
     }
     now.push_back(&q->plan.ops[q->cursor++]);
