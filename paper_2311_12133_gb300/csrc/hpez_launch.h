@@ -124,6 +124,8 @@ uint32_t finalize_blocks(uint32_t na, uint32_t nch, int num_sms);
 void launch_hist_batch(const HistJob* J, const uint32_t* off, int nj,
                        uint32_t nblk, cudaStream_t s);
 void launch_codebook_batch(const CodebookJob* J, int nj, cudaStream_t s);
+void launch_hcost_batch(const CodebookJob* J, int nj, unsigned long long* cost,
+                        cudaStream_t s);
 void launch_enc_len_batch(const EncLenJob* J, const uint32_t* off, int nj,
                           uint32_t nblk, cudaStream_t s);
 void launch_pack_batch(const PackJob* J, const uint32_t* off, int nj,
@@ -178,9 +180,5 @@ void launch_tune_blockwise(const float* x, const TuneGeom& g, int bs, int Q,
                            uint32_t nblocks, const TuneCfg* base,
                            unsigned allow, unsigned long long* scores,
                            uint8_t* bmap, cudaStream_t s);
-// Huffman bits of the histograms of nvar codebook jobs (lengths: 65536
-// per job, in job order)
-void launch_tune_cost(const CodebookJob* jobs, int nvar, const uint8_t* lens,
-                      unsigned long long* cost, cudaStream_t s);
 
 }  // namespace hpez

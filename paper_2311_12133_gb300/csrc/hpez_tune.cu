@@ -108,13 +108,8 @@ struct Bufs {
   unsigned long long* nout;
   unsigned long long* cost;
   uint32_t* hists;
-  uint8_t* lens;
-  unsigned long long* enc;
-  uint16_t* tsyms;
-  uint8_t* tlens;
-  unsigned long long* gkeys;
+  unsigned long long* gkeys;  // codebook scratch of alphabets beyond shared memory
   unsigned long long* giw;
-  uint32_t* gpar;
   uint8_t* bmap;
   unsigned long long* bscore;  // block-wise candidate scores
   float* state;                // sample blocks' reconstruction, per variant
@@ -197,25 +192,23 @@ uint64_t block_anchors(const TuneGeom& g) {
   return na;
 }
 
-// Huffman bits of the histograms in `slots` into b.cost[0, n): one batched
-// codebook launch (a CTA per histogram) and one cost launch
+// Huffman bits of the histograms in `slots` into b.cost[0, n): one launch,
+// a CTA per histogram
 void hist_costs(Call& k, const std::vector<int>& slots) {
   uint64_t& nl = k.ctx->launches;
   const int n = (int)slots.size();
   CodebookJob jobs[kMaxHists];
   for (int v = 0; v < n; ++v) {
     const size_t h = (size_t)slots[v] * 65536, o = (size_t)v * 65536;
-    jobs[v] = CodebookJob{k.b.hists + h, k.b.enc + o, k.b.tsyms + o, k.b.tlens + o,
-                          k.b.gkeys + o, k.b.giw + o, k.b.gpar + 2 * o,
-                          k.b.lens + o, k.b.ctl2 + v};
+    // only the cost: no codes, tables, lengths or parents are written
+    jobs[v] = CodebookJob{k.b.hists + h, nullptr, nullptr, nullptr, k.b.gkeys + o,
+                          k.b.giw + o, nullptr, nullptr, k.b.ctl2 + v};
   }
   cudaMemsetAsync(k.b.ctl2, 0, sizeof(Ctl) * n, k.s);
-  cudaMemsetAsync(k.b.lens, 0, (size_t)65536 * n, k.s);
   cudaMemcpyAsync(k.b.cbjobs, jobs, sizeof(CodebookJob) * n,
                   cudaMemcpyHostToDevice, k.s);
-  launch_codebook_batch(k.b.cbjobs, n, k.s);
-  launch_tune_cost(k.b.cbjobs, n, k.b.lens, k.b.cost, k.s);
-  nl += 2;
+  launch_hcost_batch(k.b.cbjobs, n, k.b.cost, k.s);
+  nl += 1;
 }
 
 // status of the histogram codebooks (0 when every one was built)
@@ -468,13 +461,8 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
   const size_t o_nout = ar.take<unsigned long long>(kMaxVariants);
   const size_t o_cost = ar.take<unsigned long long>(kMaxVariants);
   const size_t o_hists = ar.take<uint32_t>((size_t)65536 * kMaxHists);
-  const size_t o_lens = ar.take<uint8_t>((size_t)65536 * kMaxHists);
-  const size_t o_enc = ar.take<unsigned long long>((size_t)65536 * kMaxHists);
-  const size_t o_tsyms = ar.take<uint16_t>((size_t)65536 * kMaxHists);
-  const size_t o_tlens = ar.take<uint8_t>((size_t)65536 * kMaxHists);
   const size_t o_gkeys = ar.take<unsigned long long>((size_t)65536 * kMaxHists);
   const size_t o_giw = ar.take<unsigned long long>((size_t)65536 * kMaxHists);
-  const size_t o_gpar = ar.take<uint32_t>((size_t)131072 * kMaxHists);
   const size_t o_bmap = ar.take<uint8_t>(nbm ? nbm : 1);
   const size_t o_bscore = ar.take<unsigned long long>(5 * (nbm ? nbm : 1));
   // the sample blocks' state, per frozen-dimension variant
@@ -500,13 +488,8 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
   k.b.nout = reinterpret_cast<unsigned long long*>(base + o_nout);
   k.b.cost = reinterpret_cast<unsigned long long*>(base + o_cost);
   k.b.hists = reinterpret_cast<uint32_t*>(base + o_hists);
-  k.b.lens = reinterpret_cast<uint8_t*>(base + o_lens);
-  k.b.enc = reinterpret_cast<unsigned long long*>(base + o_enc);
-  k.b.tsyms = reinterpret_cast<uint16_t*>(base + o_tsyms);
-  k.b.tlens = reinterpret_cast<uint8_t*>(base + o_tlens);
   k.b.gkeys = reinterpret_cast<unsigned long long*>(base + o_gkeys);
   k.b.giw = reinterpret_cast<unsigned long long*>(base + o_giw);
-  k.b.gpar = reinterpret_cast<uint32_t*>(base + o_gpar);
   k.b.bmap = reinterpret_cast<uint8_t*>(base + o_bmap);
   k.b.bscore = reinterpret_cast<unsigned long long*>(base + o_bscore);
   k.b.state = reinterpret_cast<float*>(base + o_state);

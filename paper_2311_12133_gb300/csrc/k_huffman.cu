@@ -173,16 +173,109 @@ constexpr size_t kCodebookSmem =
     (size_t)kSmemLeaves * 8 + (size_t)kSmemLeaves * 8 + (size_t)kSmemLeaves * 8;
 
 // ---------------------------------------------------------------------
+// The two-queue Huffman merge, run by one warp.  keys[0..n) are the leaves
+// sorted by (frequency, symbol) as (frequency << 16) | symbol; iw receives
+// the internal weights in creation order, par (if not null) every node's
+// parent (leaves 0..n-1 in sorted order, internal nodes n, n+1, ...).
+// Returns the sum of the internal weights, the code's total bits.
+//
+// The sequential merge picks the two lightest waiting nodes n - 1 times, a
+// leaf before an internal node of the same weight and internal nodes in
+// creation order; the internal weights never decrease.  A round here reads
+// the first 32 waiting leaves and the first 32 waiting internal nodes and
+// ranks them in that pick order (a leaf's rank counts the lighter internal
+// nodes, an internal node's the leaves no heavier than it).  Every new node
+// of the round weighs at least w0, the sum of its first two picks, and
+// comes after every waiting node of weight <= w0; so the ranked picks up to
+// the last one of weight <= w0 are exactly the sequential ones, and the
+// round commits them in pairs.  A run of equal small frequencies goes 16
+// pairs per round.
+// ---------------------------------------------------------------------
+__device__ unsigned long long warp_huffman_merge(const unsigned long long* keys,
+                                                 uint32_t n, unsigned long long* iw,
+                                                 uint32_t* par) {
+  __shared__ unsigned long long pv[32];
+  __shared__ uint32_t pid[32];
+  constexpr unsigned kFull = 0xffffffffu;
+  constexpr unsigned long long kInf = ~0ull;
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t a = 0, b = 0, m = 0;  // leaf head, internal head, internal count
+  unsigned long long cost = 0;
+  while ((n - a) + (m - b) >= 2) {
+    const unsigned long long lv = a + lane < n ? (keys[a + lane] >> 16) : kInf;
+    const unsigned long long iv = b + lane < m ? iw[b + lane] : kInf;
+    // cl = internal nodes lighter than lv, ci = leaves not heavier than iv
+    // (both lists ascend across the lanes)
+    uint32_t cl = 0, ci = 0;
+#pragma unroll
+    for (uint32_t st = 16; st >= 1; st >>= 1) {
+      const unsigned long long pi = __shfl_sync(kFull, iv, (int)(cl + st - 1));
+      const unsigned long long pl = __shfl_sync(kFull, lv, (int)(ci + st - 1));
+      if (pi < lv) cl += st;
+      if (pl <= iv) ci += st;
+    }
+    if (__shfl_sync(kFull, iv, (int)cl) < lv) ++cl;
+    if (__shfl_sync(kFull, lv, (int)ci) <= iv) ++ci;
+    const uint32_t rl = lane + cl, ri = lane + ci;
+    const unsigned long long l0 = __shfl_sync(kFull, lv, 0), l1 = __shfl_sync(kFull, lv, 1);
+    const unsigned long long i0 = __shfl_sync(kFull, iv, 0), i1 = __shfl_sync(kFull, iv, 1);
+    unsigned long long s0, s1;
+    if (l0 <= i0) {
+      s0 = l0;
+      s1 = l1 <= i0 ? l1 : i0;
+    } else {
+      s0 = i0;
+      s1 = l0 <= i1 ? l0 : i1;
+    }
+    const unsigned long long w0 = s0 + s1;
+    const uint32_t q = min(32u, (uint32_t)(__popc(__ballot_sync(kFull, lv <= w0)) +
+                                           __popc(__ballot_sync(kFull, iv <= w0))));
+    const uint32_t take = q & ~1u;
+    const bool ul = lv <= w0 && rl < take, ui = iv <= w0 && ri < take;
+    if (ul) {
+      pv[rl] = lv;
+      pid[rl] = a + lane;
+    }
+    if (ui) {
+      pv[ri] = iv;
+      pid[ri] = n + b + lane;
+    }
+    __syncwarp();
+    const uint32_t c = take >> 1;
+    if (lane < c) {
+      const unsigned long long w = pv[2 * lane] + pv[2 * lane + 1];
+      iw[m + lane] = w;
+      cost += w;
+      if (par) {
+        par[pid[2 * lane]] = n + m + lane;
+        par[pid[2 * lane + 1]] = n + m + lane;
+      }
+    }
+    a += __popc(__ballot_sync(kFull, ul));
+    b += __popc(__ballot_sync(kFull, ui));
+    m += c;
+    __syncwarp();
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) cost += __shfl_xor_sync(kFull, cost, o);
+  return cost;
+}
+
+// ---------------------------------------------------------------------
 // codebook: one CTA of 1024 threads
 //   hist[65536] -> enc[sym] = (len << 56) | code, table (syms asc, lens),
 //   ctl->n_used, ctl->max_len
 // scratch (global): gkeys u64[65536], giw u64[65536], gpar u32[131072],
 //                   lens_by_sym u8[65536]
+// kCostOnly: only the code's total bits (sum of frequency x length, the
+// same for every optimal code) to *cost; enc, tables and lengths untouched.
 // ---------------------------------------------------------------------
+template <bool kCostOnly>
 __device__ __forceinline__ void codebook_body(
     const uint32_t* __restrict__ hist, unsigned long long* enc, uint16_t* tsyms,
     uint8_t* tlens, unsigned long long* gkeys, unsigned long long* giw,
-    uint32_t* gpar, uint8_t* lens_by_sym, Ctl* ctl) {
+    uint32_t* gpar, uint8_t* lens_by_sym, Ctl* ctl,
+    unsigned long long* cost = nullptr) {
   if (ctl->status || ctl->is_const) return;
   extern __shared__ unsigned long long smem[];
   __shared__ uint32_t s_n;
@@ -198,13 +291,21 @@ __device__ __forceinline__ void codebook_body(
   //    give every used bin its position
   __shared__ uint32_t masks[32][64];
   __shared__ uint32_t wtot[32];
+  const uint32_t* hw = hist + wid * 2048 + lane;
   {
+    // 16 loads in flight per thread, then their ballots
     uint32_t c = 0;
-    for (int it = 0; it < 64; ++it) {
-      const uint32_t f = hist[wid * 2048 + it * 32 + lane];
-      const uint32_t m = __ballot_sync(0xffffffffu, f != 0);
-      if (lane == 0) masks[wid][it] = m;
-      c += __popc(m);
+#pragma unroll
+    for (int g = 0; g < 64; g += 16) {
+      uint32_t f[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) f[u] = hw[(g + u) * 32];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const uint32_t m = __ballot_sync(0xffffffffu, f[u] != 0);
+        if (lane == 0) masks[wid][g + u] = m;
+        c += __popc(m);
+      }
     }
     if (lane == 0) wtot[wid] = c;
   }
@@ -230,19 +331,30 @@ __device__ __forceinline__ void codebook_body(
                           : gpar;
   {
     uint32_t pos = wtot[wid];
-    for (int it = 0; it < 64; ++it) {
-      const uint32_t m = masks[wid][it];
-      const uint32_t b = wid * 2048 + it * 32 + lane;
-      if (m & (1u << lane)) {
-        const uint32_t k = pos + __popc(m & ((1u << lane) - 1u));
-        keys[k] = ((unsigned long long)hist[b] << 16) | b;
-        tsyms[k] = (uint16_t)b;
+#pragma unroll
+    for (int g = 0; g < 64; g += 16) {
+      uint32_t f[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) f[u] = hw[(g + u) * 32];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const uint32_t m = masks[wid][g + u];
+        const uint32_t b = wid * 2048 + (g + u) * 32 + lane;
+        if (m & (1u << lane)) {
+          const uint32_t k = pos + __popc(m & ((1u << lane) - 1u));
+          keys[k] = ((unsigned long long)f[u] << 16) | b;
+          if (!kCostOnly) tsyms[k] = (uint16_t)b;
+        }
+        pos += __popc(m);
       }
-      pos += __popc(m);
     }
   }
   for (uint32_t i = n + tid; i < P; i += blockDim.x) keys[i] = ~0ull;
   __syncthreads();
+  if (kCostOnly && n <= 1) {  // a lone symbol gets the empty code
+    if (tid == 0) *cost = 0;
+    return;
+  }
   if (n == 1) {
     if (tid == 0) {
       const uint32_t sym = (uint32_t)(keys[0] & 0xFFFFu);
@@ -270,35 +382,12 @@ __device__ __forceinline__ void codebook_body(
   } else {
     bitonic_sort(keys, P);
   }
-  // 3. two-queue merge (sequential by nature)
-  if (tid == 0) {
-    uint32_t a = 0, b = 0, m = 0;
-    unsigned long long la = keys[0] >> 16;
-    unsigned long long ib = ~0ull;
-    for (uint32_t t = 0; t + 1 < n; ++t) {
-      uint32_t node[2];
-      unsigned long long wsum = 0;
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        if (a < n && (b >= m || la <= ib)) {
-          node[r] = a;
-          wsum += la;
-          ++a;
-          la = a < n ? (keys[a] >> 16) : ~0ull;
-        } else {
-          node[r] = n + b;
-          wsum += ib;
-          ++b;
-          ib = b < m ? iw[b] : ~0ull;
-        }
-      }
-      iw[m] = wsum;
-      par[node[0]] = n + m;
-      par[node[1]] = n + m;
-      if (b == m) ib = wsum;
-      ++m;
-    }
+  // 3. two-queue merge
+  if (wid == 0) {
+    const unsigned long long c = warp_huffman_merge(keys, n, iw, kCostOnly ? nullptr : par);
+    if (kCostOnly && lane == 0) *cost = c;
   }
+  if (kCostOnly) return;
   __syncthreads();
   // 4. leaf depths by walking to the root (one walk per leaf)
   const uint32_t root = 2 * n - 2;
@@ -383,7 +472,7 @@ __global__ void __launch_bounds__(1024)
                uint16_t* tsyms, uint8_t* tlens, unsigned long long* gkeys,
                unsigned long long* giw, uint32_t* gpar, uint8_t* lens_by_sym,
                Ctl* ctl) {
-  codebook_body(hist, enc, tsyms, tlens, gkeys, giw, gpar, lens_by_sym, ctl);
+  codebook_body<false>(hist, enc, tsyms, tlens, gkeys, giw, gpar, lens_by_sym, ctl);
 }
 
 // ---------------------------------------------------------------------
@@ -841,8 +930,17 @@ __global__ void __launch_bounds__(256)
 
 __global__ void __launch_bounds__(1024) k_codebook_batch(const CodebookJob* __restrict__ J) {
   const CodebookJob& q = J[blockIdx.x];
-  codebook_body(q.hist, q.enc, q.tsyms, q.tlens, q.gkeys, q.giw, q.gpar,
-                q.lens_by_sym, q.ctl);
+  codebook_body<false>(q.hist, q.enc, q.tsyms, q.tlens, q.gkeys, q.giw, q.gpar,
+                       q.lens_by_sym, q.ctl);
+}
+
+// total bits of an optimal code of each job's histogram (the tuner's
+// estimate), one CTA per job
+__global__ void __launch_bounds__(1024)
+    k_hcost_batch(const CodebookJob* __restrict__ J, unsigned long long* cost) {
+  const CodebookJob& q = J[blockIdx.x];
+  codebook_body<true>(q.hist, q.enc, q.tsyms, q.tlens, q.gkeys, q.giw, q.gpar,
+                      q.lens_by_sym, q.ctl, cost + blockIdx.x);
 }
 
 __global__ void __launch_bounds__(256)
@@ -1039,6 +1137,17 @@ void launch_codebook_batch(const CodebookJob* J, int nj, cudaStream_t s) {
     attr = true;
   }
   if (nj > 0) k_codebook_batch<<<nj, 1024, kCodebookSmem, s>>>(J);
+}
+
+void launch_hcost_batch(const CodebookJob* J, int nj, unsigned long long* cost,
+                        cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_hcost_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kCodebookSmem);
+    attr = true;
+  }
+  if (nj > 0) k_hcost_batch<<<nj, 1024, kCodebookSmem, s>>>(J, cost);
 }
 
 void launch_enc_len_batch(const EncLenJob* J, const uint32_t* off, int nj,

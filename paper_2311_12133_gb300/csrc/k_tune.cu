@@ -732,21 +732,6 @@ __global__ void k_tune_block_argmin(const unsigned long long* __restrict__ score
   bmap[b] = kBlockCodes[bj];
 }
 
-// Huffman bits of histogram v (the histogram of codebook job v): sum of
-// count * code length (block v)
-__global__ void __launch_bounds__(1024)
-    k_tune_cost(const CodebookJob* __restrict__ jobs,
-                const uint8_t* __restrict__ lens, unsigned long long* cost) {
-  __shared__ unsigned long long red[32];
-  const uint32_t* hist = jobs[blockIdx.x].hist;
-  const uint8_t* ln = lens + (size_t)blockIdx.x * 65536;
-  unsigned long long acc = 0;
-  for (int i = threadIdx.x; i < 65536; i += blockDim.x)
-    acc += (unsigned long long)hist[i] * ln[i];
-  acc = block_sum(acc, red);
-  if (threadIdx.x == 0) cost[blockIdx.x] = acc;
-}
-
 void set_smem_attr() {
   static bool done = false;
   if (done) return;
@@ -872,9 +857,5 @@ void launch_tune_blockwise(const float* x, const TuneGeom& g, int bs, int Q,
   k_tune_block_argmin<<<(nblocks + 255) / 256, 256, 0, s>>>(scores, nblocks, bmap);
 }
 
-void launch_tune_cost(const CodebookJob* jobs, int nvar, const uint8_t* lens,
-                      unsigned long long* cost, cudaStream_t s) {
-  if (nvar > 0) k_tune_cost<<<nvar, 1024, 0, s>>>(jobs, lens, cost);
-}
 
 }  // namespace hpez
