@@ -370,6 +370,10 @@ HPEZ_API int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim,
  *  HPEZ_OPT_FUSED_SMEM    shared-memory cap in bytes for a fused tile
  *  HPEZ_OPT_LEVEL3D       1 (default): 3D levels in direction order 0,1,2
  *                         with one interpolator use the dedicated kernel
+ *  HPEZ_OPT_STREAM_LEVELS 1 (default): the finest 3D level of the
+ *                         multi-dimensional paradigm streams its planes
+ *                         through shared memory in one launch (rows of a
+ *                         multiple of 8 points); 0: two launches
  * Errors: INVALID_ARG for an unknown option or an out-of-range value. */
 #define HPEZ_OPT_FUSED_LEVELS 1
 #define HPEZ_OPT_TILE_E0 2
@@ -377,6 +381,7 @@ HPEZ_API int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim,
 #define HPEZ_OPT_TILE_E2 4
 #define HPEZ_OPT_FUSED_SMEM 5
 #define HPEZ_OPT_LEVEL3D 6
+#define HPEZ_OPT_STREAM_LEVELS 7
 HPEZ_API int hpez_set_option(hpez_ctx* ctx, int option, int64_t value);
 
 /* ---- measurement hooks (not part of the paper's method) ----

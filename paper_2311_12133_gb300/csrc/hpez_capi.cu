@@ -411,6 +411,7 @@ int map_status(int st) {
     case ST_NONFINITE: return HPEZ_ERR_NONFINITE_INPUT;
     case ST_OUT_TOO_SMALL: return HPEZ_ERR_OUT_TOO_SMALL;
     case ST_CORRUPT: return HPEZ_ERR_CORRUPT_STREAM;
+    case ST_TIMEOUT: return HPEZ_ERR_TIMEOUT;
   }
   return HPEZ_ERR_CUDA;
 }
@@ -723,6 +724,9 @@ int hpez_set_option(hpez_ctx* ctx, int option, int64_t value) {
     case HPEZ_OPT_LEVEL3D:
       ctx->level3d = value != 0;
       return HPEZ_OK;
+    case HPEZ_OPT_STREAM_LEVELS:
+      ctx->stream_levels = value != 0;
+      return HPEZ_OK;
     case HPEZ_OPT_FUSED_SMEM:
       if (value < 4096 || value > 200 * 1024) return HPEZ_ERR_INVALID_ARG;
       ctx->fused_smem_cap = (size_t)value;
@@ -939,9 +943,15 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
       launch_level3d(false, F3, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g], s);
       ++nl;
     } else if (plan_md3(ctx, p, sc, l, false, FM, E1)) {
-      launch_level_md3(false, sb.kind, FM, E1, sb, b.R[l], b.Cg[l], b.R[g],
-                       b.Cg[g], s);
-      nl += 2;
+      if (ctx->stream_levels && md3s_supported(FM, false, d_in, b.R[l], b.Cg[l]) &&
+          launch_level_md3s(false, sb.kind, FM, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g],
+                            b.ctl, ctx->num_sms, s)) {
+        ++nl;
+      } else {
+        launch_level_md3(false, sb.kind, FM, E1, sb, b.R[l], b.Cg[l], b.R[g],
+                         b.Cg[g], s);
+        nl += 2;
+      }
     } else if (plan_md(ctx, p, sc, l, false, FM)) {
       launch_level_md(false, sb.kind, FM, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g],
                       ctx->num_sms, s);
@@ -1151,8 +1161,14 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
       launch_level3d(true, F3, sb, R[l], nullptr, R[g], nullptr, s);
       ++nl;
     } else if (plan_md3(ctx, p, sc, l, true, FM, E1)) {
-      launch_level_md3(true, sb.kind, FM, E1, sb, R[l], nullptr, R[g], nullptr, s);
-      nl += 2;
+      if (ctx->stream_levels && md3s_supported(FM, true, codes, R[l], nullptr) &&
+          launch_level_md3s(true, sb.kind, FM, sb, R[l], nullptr, R[g], nullptr, ctl,
+                            ctx->num_sms, s)) {
+        ++nl;
+      } else {
+        launch_level_md3(true, sb.kind, FM, E1, sb, R[l], nullptr, R[g], nullptr, s);
+        nl += 2;
+      }
     } else if (plan_md(ctx, p, sc, l, true, FM)) {
       launch_level_md(true, sb.kind, FM, sb, R[l], nullptr, R[g], nullptr,
                       ctx->num_sms, s);

@@ -74,6 +74,7 @@ struct hpez_ctx {
   uint64_t launches = 0;
   int fused_levels = 1;        // HPEZ_OPT_FUSED_LEVELS
   int level3d = 1;             // HPEZ_OPT_LEVEL3D
+  int stream_levels = 1;       // HPEZ_OPT_STREAM_LEVELS
   bool x_aligned16 = true;     // per call: input pointer 16-byte aligned
   bool codes_aligned16 = true;
   bool out_aligned16 = true;   // per call: decompress output 16-byte aligned

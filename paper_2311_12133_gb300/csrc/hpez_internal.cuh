@@ -25,6 +25,7 @@ enum DevStatus {
   ST_NONFINITE = -2,
   ST_OUT_TOO_SMALL = -3,
   ST_CORRUPT = -4,
+  ST_TIMEOUT = -9,
 };
 
 // Per-call control block in device memory.

@@ -212,6 +212,7 @@ def opts(gpu):
     from paper_2311_12133_gb300 import hpez
     yield gpu
     hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_FUSED_LEVELS, 1)
+    hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_STREAM_LEVELS, 1)
     for o in (hpez.HPEZ_OPT_TILE_E0, hpez.HPEZ_OPT_TILE_E1, hpez.HPEZ_OPT_TILE_E2):
         hpez.hpez_set_option(gpu.handle, o, 0)
 
@@ -266,6 +267,39 @@ def test_md_levels(gpu, oracle, shape, frozen, interp, same):
         x = fields.grf(shape, seed=len(shape) * 10 + interp)
     _check(gpu, oracle, x, 1e-3, 1, interp=interp, paradigm=1, same_level=same,
            frozen_dim=frozen, md_inv_var=(1.0, 2.5, 0.7))
+
+
+@pytest.mark.parametrize("shape,eb", [((40, 48, 64), 1e-3), ((33, 17, 128), 1e-3),
+                                      ((9, 70, 136), 1e-4), ((64, 40, 256), 1e-3),
+                                      ((2, 3, 8), 1e-3), ((5, 16, 24), 1e-6),
+                                      ((66, 20, 16), 1e-3)])
+@pytest.mark.parametrize("interp", [0, 1, 2])
+def test_md_stream_level(opts, oracle, shape, eb, interp):
+    """The finest 3D multi-dimensional level streamed in one launch (rows a
+    multiple of 8 points; compress also needs the coarse rows in whole
+    16-byte units, i.e. rows a multiple of 16): partial row and column
+    tiles, odd and even plane counts, chunk boundaries, outliers (eb 1e-6);
+    equal to the oracle, and to the two-launch path, which needs one launch
+    more."""
+    import torch
+    from paper_2311_12133_gb300 import fields, hpez
+    x = fields.grf(shape, seed=sum(shape) + interp)
+    kw = dict(interp=interp, paradigm=1, md_inv_var=(1.0, 2.5, 0.7))
+    _check(opts, oracle, x, eb, 1, **kw)
+    _, gcfg = _pair_configs(3, **kw)
+    xd = torch.from_numpy(x).cuda()
+    count = lambda: hpez.hpez_launch_count(opts.handle)
+    runs = {}
+    for on in (1, 0):
+        hpez.hpez_set_option(opts.handle, hpez.HPEZ_OPT_STREAM_LEVELS, on)
+        n0 = count()
+        buf, size = opts.compress(xd, eb, 1, gcfg)
+        n1 = count()
+        y = opts.decompress(buf, size).cpu().numpy()
+        runs[on] = (buf[:size].cpu().numpy().tobytes(), y.tobytes(), n1 - n0, count() - n1)
+    assert runs[1][0] == runs[0][0] and runs[1][1] == runs[0][1]
+    assert runs[0][2] - runs[1][2] == (1 if shape[2] % 16 == 0 else 0)
+    assert runs[0][3] - runs[1][3] == 1
 
 
 @pytest.mark.parametrize("code", [0, 1, 2, 5, 6])
