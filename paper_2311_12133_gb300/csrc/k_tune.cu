@@ -17,7 +17,9 @@
 namespace hpez {
 namespace {
 
-constexpr int kTuneThreads = 1024;
+constexpr int kTuneThreads = 1024;  // Lorenzo wavefront
+// candidate tests and level advances: 512 threads leave each 128 registers
+constexpr int kTestThreads = 512;
 // block-map codes of the block-wise candidates, in test order: linear,
 // not-a-knot, not-a-knot + same-level, natural, natural + same-level
 __constant__ uint8_t kBlockCodes[5] = {0, 1, 5, 2, 6};
@@ -250,12 +252,15 @@ __device__ __forceinline__ float predict_smem(const float* R, int i, int st,
 
 // One level (stride s = 2^(l-1)) of the sweep on the sub-field: passes
 // and same-level halves in the compressor's order, a barrier after each.
-// A pass's points form boxes of the stride-s lattice (a 1D-style pass one
-// box: odd along its direction, any multiple of s on earlier directions,
-// even on later ones; a multi-dimensional sub-pass one box per set of odd
-// directions of its size), enumerated directly.  Adds the error scores
-// (when score_on), the code counts (kHist) and the escapes of the level's
-// points to the thread's accumulators.
+// The points of a pass (or of one same-level half of it) are a few boxes
+// of the stride-s lattice, enumerated directly: a 1D-style pass is one box
+// (odd along its direction, any multiple of s on earlier directions, even
+// on later ones), a multi-dimensional sub-pass one box per set of odd
+// directions of its size.  A same-level half keeps the points whose odd
+// indices t_d (coordinate s (2 t_d + 1)) have a sum of that parity: per
+// parity pattern of the t_d, a box of step 4s along the odd directions.
+// Adds the error scores (when score_on), the code counts (kHist) and the
+// escapes of the level's points to the thread's accumulators.
 struct Box {
   int a[3], b[3], cnt[3];
   unsigned mg[3];  // division magic of cnt
@@ -263,9 +268,12 @@ struct Box {
   unsigned S;
 };
 
+// odd: directions odd at stride s; any: directions at any multiple of s;
+// split: restrict the odd directions to index parities par (same-level)
 __device__ __forceinline__ void make_box(Box& bx, const Sub& f,
                                          const int interp[3], int s,
-                                         unsigned odd, unsigned any) {
+                                         unsigned odd, unsigned any,
+                                         bool split, unsigned par) {
   bx.total = 1;
   bx.S = odd;
 #pragma unroll
@@ -276,9 +284,11 @@ __device__ __forceinline__ void make_box(Box& bx, const Sub& f,
       bx.b[d] = 1;
       bx.cnt[d] = n;
     } else if (odd & (1u << d)) {
-      bx.a[d] = s;
-      bx.b[d] = 2 * s;
-      bx.cnt[d] = n - 1 >= s ? (n - 1 - s) / (2 * s) + 1 : 0;
+      const int a = split ? s * (2 * (int)((par >> d) & 1u) + 1) : s;
+      const int b = split ? 4 * s : 2 * s;
+      bx.a[d] = a;
+      bx.b[d] = b;
+      bx.cnt[d] = n - 1 >= a ? (n - 1 - a) / b + 1 : 0;
     } else if (any & (1u << d)) {
       bx.a[d] = 0;
       bx.b[d] = s;
@@ -291,6 +301,20 @@ __device__ __forceinline__ void make_box(Box& bx, const Sub& f,
     bx.total *= bx.cnt[d];
     bx.mg[d] = fdiv_magic((unsigned)bx.cnt[d]);
   }
+}
+
+// the boxes of odd set S (and any) for half `half` of a same-level pass
+// (split), or of the whole pass
+__device__ __forceinline__ void add_boxes(Box* bx, int& nb, const Sub& f,
+                                          const int interp[3], int s, unsigned S,
+                                          unsigned any, bool split, int half) {
+  if (!split) {
+    make_box(bx[nb++], f, interp, s, S, any, false, 0u);
+    return;
+  }
+  for (unsigned par = 0; par < 8; ++par)
+    if ((par & ~S) == 0 && (int)(__popc(par) & 1) == half)
+      make_box(bx[nb++], f, interp, s, S, any, true, par);
 }
 
 // codes within kWin/2 of the zero-error code are counted in shared memory
@@ -330,10 +354,157 @@ __device__ __forceinline__ unsigned quantize_t(float x, float p, float el,
   return 0u;
 }
 
-// The points of one pass (or same-level half) of a level, specialized on
-// the interpolator and the paradigm, which are uniform within a level.
+// prediction along one slot from shared memory: the stencil of an
+// interior point directly (the one choose_formula selects there), else the
+// general choice
+template <int KIND>
+__device__ __forceinline__ float predict_t(const float* R, int i, int st, int u, int m,
+                                           bool hb) {
+  if (!hb) {
+    if (KIND == LINEAR) {
+      if (u + 1 <= m - 1) return eval_formula(F_LIN, 0.f, 0.f, R[i - st], R[i + st], 0.f, 0.f);
+    } else if (u >= 3 && u + 3 <= m - 1) {
+      return eval_formula(KIND == CUBIC_NAK ? F_NAK4 : F_NAT4, R[i - 3 * st], 0.f,
+                          R[i - st], R[i + st], 0.f, R[i + 3 * st]);
+    }
+  } else if (KIND == CUBIC_NAK) {
+    if (u >= 2 && u + 2 <= m - 1)
+      return eval_formula(F_SL_NAK, 0.f, R[i - 2 * st], R[i - st], R[i + st],
+                          R[i + 2 * st], 0.f);
+  } else if (KIND == CUBIC_NAT) {
+    if (u >= 3 && u + 3 <= m - 1)
+      return eval_formula(F_SL_NAT, R[i - 3 * st], R[i - 2 * st], R[i - st], R[i + st],
+                          R[i + 2 * st], R[i + 3 * st]);
+  }
+  return predict_smem(R, i, st, u, m, KIND, hb);
+}
+
+// The points of one box of a pass (or same-level half), specialized on the
+// interpolator and the paradigm, which are uniform within a level; hb: the
+// box is in half B of a same-level pass.
 template <int KIND, bool MD, int PS, bool kHist>
-__device__ void sweep_pass(float* R, const Sub& f, const Box* bx, int nb,
+__device__ __forceinline__ void sweep_box(float* R, const Sub& f, const Box B, bool hb,
+                                          int sh, const int line[3], const TuneCfg& c,
+                                          int l, bool score_on, unsigned long long& score,
+                                          const HistSink& hist, unsigned long long& nout) {
+  const int s = 1 << sh;
+  const float el = c.el[l - 1], inv2 = c.inv2[l - 1], twoe = c.twoe[l - 1];
+  const float inv_el = c.inv_el[l - 1];
+  const unsigned S = B.S;
+  float w[3] = {0.f, 0.f, 0.f};
+  int sst[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    sst[d] = s * f.st[d];
+    if (MD) w[d] = c.mdw[S][d];
+  }
+  for (int t = threadIdx.x; t < B.total; t += blockDim.x) {
+    const unsigned r1 = fdiv((unsigned)t, B.mg[2]);
+    int cc[3];
+    cc[2] = B.a[2] + B.b[2] * (t - (int)r1 * B.cnt[2]);
+    const unsigned r0 = fdiv(r1, B.mg[1]);
+    cc[1] = B.a[1] + B.b[1] * ((int)r1 - (int)r0 * B.cnt[1]);
+    cc[0] = B.a[0] + B.b[0] * (int)r0;
+    const int i = cc[0] * f.st[0] + cc[1] * f.st[1] + cc[2];
+    const float xv = xval(f, cc);
+    float p;
+    if (!MD) {
+      p = predict_t<KIND>(R, i, sst[PS], cc[PS] >> sh, line[PS], hb);
+    } else {
+      float acc = 0.0f;
+      bool first = true;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (!(S & (1u << d))) continue;
+        const float pd = predict_t<KIND>(R, i, sst[d], cc[d] >> sh, line[d], hb);
+        const float tw = __fmul_rn(w[d], pd);
+        acc = first ? tw : __fadd_rn(acc, tw);
+        first = false;
+      }
+      p = acc;
+    }
+    float rv;
+    const unsigned code = quantize_t(xv, p, el, inv2, twoe, rv);
+    R[i] = rv;
+    if (score_on) score += err_fixed(__fsub_rn(xv, p), inv_el);
+    if (kHist) hist.add(code);
+    if (code == 0u) ++nout;
+  }
+}
+
+// KIND < 0: the level's interpolator read from the config; KIND >= 0:
+// fixed (the config's value is that kind)
+template <int KIND, bool kHist>
+__device__ void sweep_level_k(float* R, const Sub& f, const int interp[3],
+                              int k, int l, const TuneCfg& c, bool score_on,
+                              unsigned long long& score, const HistSink& hist,
+                              unsigned long long& nout) {
+  const int sh = l - 1, s = 1 << sh;
+  int line[3];
+  unsigned imask = 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    line[d] = (f.n[d] - 1) / s + 1;
+    if (interp[d]) imask |= 1u << d;
+  }
+  const int kind = c.kind[l - 1];
+  const bool md = c.md[l - 1] != 0;
+  const bool same = c.same[l - 1] != 0 && kind != LINEAR;
+  for (int pj = 0; pj < k; ++pj) {
+    for (int half = 0; half < (same ? 2 : 1); ++half) {
+      Box bx[6];
+      int nb = 0;
+      if (!md) {
+        unsigned any = 0;  // directions earlier in the order: any parity
+        for (int q = 0; q < pj; ++q) any |= 1u << c.ord[l - 1][q];
+        add_boxes(bx, nb, f, interp, s, 1u << c.ord[l - 1][pj], any, same, half);
+      } else {
+        for (unsigned S = 1; S < 8; ++S)
+          if ((S & imask) == S && __popc(S) == pj + 1)
+            add_boxes(bx, nb, f, interp, s, S, 0u, same, half);
+      }
+      const bool hb = half == 1;
+      for (int q = 0; q < nb; ++q) {
+        const Box B = bx[q];
+        if (B.total == 0) continue;
+#define HPEZ_SWEEP(K, M, P)                                                   \
+  sweep_box<K, M, P, kHist>(R, f, B, hb, sh, line, c, l, score_on, score,     \
+                            hist, nout)
+#define HPEZ_SWEEP_1D(K)                                                      \
+  do {                                                                        \
+    const int ps = c.ord[l - 1][pj];                                          \
+    if (ps == 0) HPEZ_SWEEP(K, false, 0);                                     \
+    else if (ps == 1) HPEZ_SWEEP(K, false, 1);                                \
+    else HPEZ_SWEEP(K, false, 2);                                             \
+  } while (0)
+        if (KIND >= 0) {
+          if (md) HPEZ_SWEEP(KIND < 0 ? 0 : KIND, true, 0);
+          else HPEZ_SWEEP_1D(KIND < 0 ? 0 : KIND);
+        } else if (md) {
+          if (kind == LINEAR) HPEZ_SWEEP(LINEAR, true, 0);
+          else if (kind == CUBIC_NAK) HPEZ_SWEEP(CUBIC_NAK, true, 0);
+          else HPEZ_SWEEP(CUBIC_NAT, true, 0);
+        } else {
+          if (kind == LINEAR) HPEZ_SWEEP_1D(LINEAR);
+          else if (kind == CUBIC_NAK) HPEZ_SWEEP_1D(CUBIC_NAK);
+          else HPEZ_SWEEP_1D(CUBIC_NAT);
+        }
+#undef HPEZ_SWEEP_1D
+#undef HPEZ_SWEEP
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// The same sweep for small sub-fields (the block-wise tests, one warp
+// each): the boxes of a pass in one enumeration, each same-level half
+// skipping the other half's points -- fewer partial iterations than a loop
+// per box when the boxes hold a few points each.  The points of one pass
+// (or same-level half) of a level, specialized on the interpolator and the
+// paradigm, which are uniform within a level.
+template <int KIND, bool MD, int PS, bool kHist>
+__device__ void sweep_pass_skip(float* R, const Sub& f, const Box* bx, int nb,
                            int tot, int half, bool same, int sh,
                            const int line[3], const TuneCfg& c, int l,
                            bool score_on, unsigned long long& score,
@@ -392,7 +563,7 @@ __device__ void sweep_pass(float* R, const Sub& f, const Box* bx, int nb,
 // KIND < 0: the level's interpolator read from the config; KIND >= 0:
 // fixed (the config's value is that kind)
 template <int KIND, bool kHist>
-__device__ void sweep_level_k(float* R, const Sub& f, const int interp[3],
+__device__ void sweep_level_skip(float* R, const Sub& f, const int interp[3],
                               int k, int l, const TuneCfg& c, bool score_on,
                               unsigned long long& score, const HistSink& hist,
                               unsigned long long& nout) {
@@ -413,18 +584,18 @@ __device__ void sweep_level_k(float* R, const Sub& f, const int interp[3],
     if (!md) {
       unsigned any = 0;  // directions earlier in the order: any parity
       for (int q = 0; q < pj; ++q) any |= 1u << c.ord[l - 1][q];
-      make_box(bx[0], f, interp, s, 1u << c.ord[l - 1][pj], any);
+      make_box(bx[0], f, interp, s, 1u << c.ord[l - 1][pj], any, false, 0u);
       nb = 1;
     } else {
       for (unsigned S = 1; S < 8; ++S)
         if ((S & imask) == S && __popc(S) == pj + 1)
-          make_box(bx[nb++], f, interp, s, S, 0u);
+          make_box(bx[nb++], f, interp, s, S, 0u, false, 0u);
     }
     int tot = 0;
     for (int q = 0; q < nb; ++q) tot += bx[q].total;
     for (int half = 0; half < (same ? 2 : 1); ++half) {
 #define HPEZ_SWEEP(K, M, P)                                                   \
-  sweep_pass<K, M, P, kHist>(R, f, bx, nb, tot, half, same, sh, line, c, l,   \
+  sweep_pass_skip<K, M, P, kHist>(R, f, bx, nb, tot, half, same, sh, line, c, l,   \
                              score_on, score, hist, nout)
 #define HPEZ_SWEEP_1D(K)                                                      \
   do {                                                                        \
@@ -507,7 +678,7 @@ __device__ void copy_lattice(float* R, float* __restrict__ state, const Sub& f,
 // levels, kept there by k_tune_advance, and runs level l_stop only;
 // without one it starts from the anchors and runs levels L..l_stop.
 template <bool kHist>
-__global__ void __launch_bounds__(kTuneThreads)
+__global__ void __launch_bounds__(kTestThreads, 1)
     k_tune_test(const float* __restrict__ x, TuneGeom g0, TuneGeom g1, int ny0,
                 const TuneCfg* __restrict__ cfgs, int l_stop,
                 unsigned long long* score, uint32_t* hists,
@@ -548,7 +719,7 @@ __global__ void __launch_bounds__(kTuneThreads)
 // After level l's choice: CTA (sample block, variant w) runs level l with
 // the chosen config cfgs[w] from the block's state (the anchors at the
 // coarsest level) and stores the stride-2^(l-1) lattice back.
-__global__ void __launch_bounds__(kTuneThreads)
+__global__ void __launch_bounds__(kTestThreads, 1)
     k_tune_advance(const float* __restrict__ x, TuneGeom g0, TuneGeom g1,
                    const TuneCfg* __restrict__ cfgs, int l,
                    float* __restrict__ state, unsigned vol) {
@@ -710,7 +881,7 @@ __global__ void __launch_bounds__(kBlockThreads)
   unsigned long long sc = 0, no = 0;
   const HistSink none{nullptr, nullptr};
   for (int l = L; l >= 1; --l)
-    sweep_level_k<KIND, false>(R, f, g.interp, g.k, l, c, true, sc, none, no);
+    sweep_level_skip<KIND, false>(R, f, g.interp, g.k, l, c, true, sc, none, no);
   sc = block_sum(sc, red);
   if (threadIdx.x == 0) *out = sc;
 }
@@ -807,10 +978,10 @@ void launch_tune_test(const float* x, const TuneGeom& g0, const TuneGeom& g1,
   const size_t sm = std::max(tune_test_smem(g0), tune_test_smem(g1));
   const unsigned vol = (unsigned)(tune_test_smem(g0) / sizeof(float));
   if (hist)
-    k_tune_test<true><<<grid, kTuneThreads, sm, s>>>(x, g0, g1, ny0, cfgs, l_stop,
+    k_tune_test<true><<<grid, kTestThreads, sm, s>>>(x, g0, g1, ny0, cfgs, l_stop,
                                                      score, hists, nout, state, vol);
   else
-    k_tune_test<false><<<grid, kTuneThreads, sm, s>>>(x, g0, g1, ny0, cfgs, l_stop,
+    k_tune_test<false><<<grid, kTestThreads, sm, s>>>(x, g0, g1, ny0, cfgs, l_stop,
                                                       score, hists, nout, state, vol);
 }
 
@@ -820,7 +991,7 @@ void launch_tune_advance(const float* x, const TuneGeom& g0, const TuneGeom& g1,
   set_smem_attr();
   const size_t sm = std::max(tune_test_smem(g0), tune_test_smem(g1));
   const unsigned vol = (unsigned)(tune_test_smem(g0) / sizeof(float));
-  k_tune_advance<<<dim3((unsigned)nblk, (unsigned)nv), kTuneThreads, sm, s>>>(
+  k_tune_advance<<<dim3((unsigned)nblk, (unsigned)nv), kTestThreads, sm, s>>>(
       x, g0, g1, cfgs, l, state, vol);
 }
 
