@@ -904,9 +904,13 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   launch_init_ctl(b.ctl, s);
   ++nl;
   if (eb_mode == HPEZ_EB_REL) {
-    pf.begin(HPEZ_PH_RANGE, s);
-    launch_range(d_in, p.N, b.ctl, ctx->num_sms, s);
-    pf.end(s);
+    if (ctx->range_hint_on && ctx->range_x == d_in && ctx->range_n == p.N) {
+      launch_set_range(b.ctl, ctx->range_kmin, ctx->range_kmax, s);
+    } else {
+      pf.begin(HPEZ_PH_RANGE, s);
+      launch_range(d_in, p.N, b.ctl, ctx->num_sms, s);
+      pf.end(s);
+    }
     ++nl;
   }
   launch_params(b.ctl, eb_mode, eb, cfg.alpha, cfg.beta, p.L, d_in, s);

@@ -75,6 +75,12 @@ struct hpez_ctx {
   int fused_levels = 1;        // HPEZ_OPT_FUSED_LEVELS
   int level3d = 1;             // HPEZ_OPT_LEVEL3D
   int stream_levels = 1;       // HPEZ_OPT_STREAM_LEVELS
+  // the value range of the last tuned input (order-preserving keys), which
+  // the compress call of hpez_compress_auto reuses instead of a second pass
+  bool range_hint_on = false;
+  const void* range_x = nullptr;
+  uint64_t range_n = 0;
+  unsigned range_kmin = 0, range_kmax = 0;
   bool x_aligned16 = true;     // per call: input pointer 16-byte aligned
   bool codes_aligned16 = true;
   bool out_aligned16 = true;   // per call: decompress output 16-byte aligned

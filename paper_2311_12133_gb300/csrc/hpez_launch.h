@@ -14,6 +14,7 @@ void launch_fill(float* out, uint32_t N, float v, int num_sms,
                  cudaStream_t s);
 void launch_range(const float* x, uint32_t N, Ctl* ctl, int num_sms,
                   cudaStream_t s);
+void launch_set_range(Ctl* ctl, unsigned kmin, unsigned kmax, cudaStream_t s);
 void launch_params(Ctl* ctl, int eb_mode, double eb, double alpha,
                    double beta, int L, const float* x, cudaStream_t s);
 void launch_anchor_gather(const float* x, const LevelGeom& ga, uint32_t total,

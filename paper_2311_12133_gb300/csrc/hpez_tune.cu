@@ -510,6 +510,13 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
   cudaMemcpyAsync(ctx->h_ctl, k.b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
   if ((rc = sync_check(k))) return rc;
   if (ctx->h_ctl->status) return map_status(ctx->h_ctl->status);
+  ctx->range_x = nullptr;
+  if (eb_mode == HPEZ_EB_REL && !ctx->h_ctl->nonfinite) {
+    ctx->range_x = d_in;
+    ctx->range_n = p0.N;
+    ctx->range_kmin = ctx->h_ctl->vmin_key;
+    ctx->range_kmax = ctx->h_ctl->vmax_key;
+  }
   if (ctx->h_ctl->is_const) {
     prof.collect();
     return HPEZ_OK;  // constant field: nothing to tune
@@ -681,8 +688,11 @@ int hpez_compress_auto(hpez_ctx* ctx, const float* d_in, int ndim,
   int rc = hpez_tune(ctx, d_in, ndim, dims, eb_mode, eb, tp, &cfg,
                      bm.empty() ? nullptr : bm.data(), bm.size(), h_report, stream);
   if (rc) return rc;
-  return hpez_compress(ctx, d_in, ndim, dims, eb_mode, eb, &cfg, d_out, out_cap,
-                       h_out_size, stream);
+  ctx->range_hint_on = true;  // the tuner's pass over d_in found the range
+  rc = hpez_compress(ctx, d_in, ndim, dims, eb_mode, eb, &cfg, d_out, out_cap,
+                     h_out_size, stream);
+  ctx->range_hint_on = false;
+  return rc;
 }
 
 int hpez_compress_auto_host(hpez_ctx* ctx, const float* h_in, int ndim,

@@ -29,6 +29,12 @@ __device__ __forceinline__ void init_ctl_body(Ctl* ctl) {
 
 __global__ void k_init_ctl(Ctl* ctl) { init_ctl_body(ctl); }
 
+// the value range found by an earlier pass over the same input
+__global__ void k_set_range(Ctl* ctl, unsigned kmin, unsigned kmax) {
+  ctl->vmin_key = kmin;
+  ctl->vmax_key = kmax;
+}
+
 __device__ __forceinline__ void range_body(const float* __restrict__ x,
                                            uint32_t N, Ctl* ctl, unsigned bid,
                                            unsigned nblk) {
@@ -375,6 +381,10 @@ void launch_fill(float* out, uint32_t N, float v, int num_sms,
 void launch_range(const float* x, uint32_t N, Ctl* ctl, int num_sms,
                   cudaStream_t s) {
   k_range<<<grid_for(N / 4 + 1, 256, num_sms * 8), 256, 0, s>>>(x, N, ctl);
+}
+
+void launch_set_range(Ctl* ctl, unsigned kmin, unsigned kmax, cudaStream_t s) {
+  k_set_range<<<1, 1, 0, s>>>(ctl, kmin, kmax);
 }
 
 void launch_params(Ctl* ctl, int eb_mode, double eb, double alpha,
