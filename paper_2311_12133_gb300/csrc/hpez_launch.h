@@ -165,6 +165,7 @@ void launch_tune_stats(const float* x, const uint32_t n[3],
 void launch_tune_params(TuneCfg* cfgs, int nvar, int L, const Ctl* ctl,
                         cudaStream_t s);
 size_t tune_test_smem(const TuneGeom& g);
+size_t tune_lorenzo_smem(const TuneGeom& g);
 // (sample block, variant) CTAs; variants < ny0 use geometry g0, the rest g1.
 // state: each block's reconstruction after the levels above l_stop (run
 // level l_stop only), or null (run levels L..l_stop from the anchors)

@@ -251,7 +251,8 @@ int init_variant(Call& k, Variant& v, const double inv_var[3]) {
   int rc = plan_geometry(v.p, k.ndim, k.dims, cfg.anchor_stride, v.frozen);
   if (rc) return rc;
   v.nblk = sample_geometry(v.p, tp, v.g);
-  if (tune_test_smem(v.g) > kTuneSmemMax) return HPEZ_ERR_UNSUPPORTED;
+  if (tune_test_smem(v.g) > kTuneSmemMax || tune_lorenzo_smem(v.g) > kTuneSmemMax)
+    return HPEZ_ERR_UNSUPPORTED;
   // the Lorenzo wavefront keeps at most 4 (i0, i1) pairs per thread
   if ((uint64_t)v.g.ext[0] * v.g.ext[1] > 4096) return HPEZ_ERR_UNSUPPORTED;
   v.cands = candidates(tp, k.ndim, v.frozen);

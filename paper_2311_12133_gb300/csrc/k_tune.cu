@@ -39,7 +39,8 @@ __device__ __forceinline__ unsigned fdiv(unsigned r, unsigned m) {
   return m ? __umulhi(r, m) : r;
 }
 __host__ __device__ __forceinline__ unsigned fdiv_magic(unsigned n) {
-  return n <= 1 ? 0u : (unsigned)((0x100000000ull + n - 1) / n);
+  // ceil(2^32 / n) = floor((2^32 - 1) / n) + 1 for n >= 2 (32-bit division)
+  return n <= 1 ? 0u : 0xFFFFFFFFu / n + 1u;
 }
 
 // floor(min(|d| / e, 2^16)^2 * 256): the statistics' squared error
@@ -303,18 +304,21 @@ __device__ __forceinline__ void make_box(Box& bx, const Sub& f,
   }
 }
 
+// what make_box needs for one box of a pass
+struct BoxDesc {
+  unsigned S, any, par;
+};
+
 // the boxes of odd set S (and any) for half `half` of a same-level pass
 // (split), or of the whole pass
-__device__ __forceinline__ void add_boxes(Box* bx, int& nb, const Sub& f,
-                                          const int interp[3], int s, unsigned S,
-                                          unsigned any, bool split, int half) {
+__device__ __forceinline__ void add_boxes(BoxDesc* bd, int& nb, unsigned S, unsigned any,
+                                          bool split, int half) {
   if (!split) {
-    make_box(bx[nb++], f, interp, s, S, any, false, 0u);
+    bd[nb++] = BoxDesc{S, any, 0u};
     return;
   }
   for (unsigned par = 0; par < 8; ++par)
-    if ((par & ~S) == 0 && (int)(__popc(par) & 1) == half)
-      make_box(bx[nb++], f, interp, s, S, any, true, par);
+    if ((par & ~S) == 0 && (int)(__popc(par) & 1) == half) bd[nb++] = BoxDesc{S, any, par};
 }
 
 // codes within kWin/2 of the zero-error code are counted in shared memory
@@ -434,11 +438,13 @@ __device__ __forceinline__ void sweep_box(float* R, const Sub& f, const Box B, b
 
 // KIND < 0: the level's interpolator read from the config; KIND >= 0:
 // fixed (the config's value is that kind)
+// sbox: shared memory for the boxes of a pass (at most 6), each built by
+// one thread
 template <int KIND, bool kHist>
 __device__ void sweep_level_k(float* R, const Sub& f, const int interp[3],
                               int k, int l, const TuneCfg& c, bool score_on,
                               unsigned long long& score, const HistSink& hist,
-                              unsigned long long& nout) {
+                              unsigned long long& nout, Box* sbox) {
   const int sh = l - 1, s = 1 << sh;
   int line[3];
   unsigned imask = 0;
@@ -452,20 +458,24 @@ __device__ void sweep_level_k(float* R, const Sub& f, const int interp[3],
   const bool same = c.same[l - 1] != 0 && kind != LINEAR;
   for (int pj = 0; pj < k; ++pj) {
     for (int half = 0; half < (same ? 2 : 1); ++half) {
-      Box bx[6];
+      BoxDesc bd[6];
       int nb = 0;
       if (!md) {
         unsigned any = 0;  // directions earlier in the order: any parity
         for (int q = 0; q < pj; ++q) any |= 1u << c.ord[l - 1][q];
-        add_boxes(bx, nb, f, interp, s, 1u << c.ord[l - 1][pj], any, same, half);
+        add_boxes(bd, nb, 1u << c.ord[l - 1][pj], any, same, half);
       } else {
         for (unsigned S = 1; S < 8; ++S)
-          if ((S & imask) == S && __popc(S) == pj + 1)
-            add_boxes(bx, nb, f, interp, s, S, 0u, same, half);
+          if ((S & imask) == S && __popc(S) == pj + 1) add_boxes(bd, nb, S, 0u, same, half);
       }
+      if ((int)threadIdx.x < nb) {
+        const BoxDesc d = bd[threadIdx.x];
+        make_box(sbox[threadIdx.x], f, interp, s, d.S, d.any, same, d.par);
+      }
+      __syncthreads();
       const bool hb = half == 1;
       for (int q = 0; q < nb; ++q) {
-        const Box B = bx[q];
+        const Box B = sbox[q];
         if (B.total == 0) continue;
 #define HPEZ_SWEEP(K, M, P)                                                   \
   sweep_box<K, M, P, kHist>(R, f, B, hb, sh, line, c, l, score_on, score,     \
@@ -629,8 +639,8 @@ __device__ __forceinline__ void sweep_level(float* R, const Sub& f,
                                             const TuneCfg& c, bool score_on,
                                             unsigned long long& score,
                                             const HistSink& hist,
-                                            unsigned long long& nout) {
-  sweep_level_k<-1, kHist>(R, f, interp, k, l, c, score_on, score, hist, nout);
+                                            unsigned long long& nout, Box* sbox) {
+  sweep_level_k<-1, kHist>(R, f, interp, k, l, c, score_on, score, hist, nout, sbox);
 }
 
 __device__ __forceinline__ void load_cfg(TuneCfg* dst, const TuneCfg* src) {
@@ -690,6 +700,7 @@ __global__ void __launch_bounds__(kTestThreads, 1)
   __shared__ TuneCfg c;
   __shared__ unsigned long long red[32];
   __shared__ uint32_t win[kHist ? kWin : 1];
+  __shared__ Box sbox[6];
   const int v = blockIdx.y;
   if (kHist)
     for (int i = threadIdx.x; i < kWin; i += blockDim.x) win[i] = 0;
@@ -706,7 +717,7 @@ __global__ void __launch_bounds__(kTestThreads, 1)
   unsigned long long sc = 0, no = 0;
   HistSink h{win, kHist ? hists + (size_t)v * 65536 : nullptr};
   for (int l = l_top; l >= l_stop; --l)
-    sweep_level<kHist>(R, f, g.interp, g.k, l, c, l == l_stop, sc, h, no);
+    sweep_level<kHist>(R, f, g.interp, g.k, l, c, l == l_stop, sc, h, no, sbox);
   if (kHist)
     for (int i = threadIdx.x; i < kWin; i += blockDim.x)
       if (win[i]) atomicAdd(h.glob + (kRadius - kWin / 2) + i, win[i]);
@@ -727,6 +738,7 @@ __global__ void __launch_bounds__(kTestThreads, 1)
   const TuneGeom& g = w ? g1 : g0;
   extern __shared__ float R[];
   __shared__ TuneCfg c;
+  __shared__ Box sbox[6];
   load_cfg(&c, cfgs + w);
   const Sub f = sample_block(x, g, blockIdx.x);
   float* st = state + ((size_t)w * gridDim.x + blockIdx.x) * vol;
@@ -736,7 +748,7 @@ __global__ void __launch_bounds__(kTestThreads, 1)
     copy_lattice<true>(R, st, f, g.interp, 2 << (l - 1));
   unsigned long long sc = 0, no = 0;
   const HistSink none{nullptr, nullptr};
-  sweep_level<false>(R, f, g.interp, g.k, l, c, false, sc, none, no);
+  sweep_level<false>(R, f, g.interp, g.k, l, c, false, sc, none, no, sbox);
   copy_lattice<false>(R, st, f, g.interp, 1 << (l - 1));
 }
 
@@ -745,24 +757,24 @@ __global__ void __launch_bounds__(kTestThreads, 1)
 // as a wavefront over the planes i0 + i1 + i2 = t: every neighbour a point
 // reads lies on an earlier plane.  Neighbours outside the block read 0.
 // ---------------------------------------------------------------------
-__global__ void __launch_bounds__(kTuneThreads)
-    k_tune_lorenzo(const float* __restrict__ x, TuneGeom g,
-                   const Ctl* __restrict__ ctl, uint32_t* hists,
-                   unsigned long long* nout) {
-  extern __shared__ float R[];
-  __shared__ unsigned long long red[32];
-  const int order = blockIdx.y + 1;
-  const Sub f = sample_block(x, g, blockIdx.x);
-  const float e = ctl->e;
-  const float inv2 = __double2float_rn(__ddiv_rn(1.0, __dmul_rn(2.0, (double)e)));
-  const float twoe = __fmul_rn(2.0f, e);
-  const float co[2][3] = {{1.0f, -1.0f, 0.0f}, {1.0f, -2.0f, 1.0f}};
-  int lim[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) lim[d] = d < g.off ? 0 : order;
-  uint32_t* h = hists + (size_t)blockIdx.y * 65536;
-  unsigned long long no = 0;
-  const int n0 = f.n[0], n1 = f.n[1], n2 = f.n[2];
+// Lorenzo coefficient of offset a (0..ORDER) along one direction: order 1
+// (1, -1), order 2 (1, -2, 1); a point's weight is minus the product over
+// the three directions (small integers, so every product is exact)
+template <int ORDER>
+__device__ __forceinline__ float lorenzo_coef(int a) {
+  return ORDER == 1 ? (a == 0 ? 1.0f : -1.0f) : (a == 1 ? -2.0f : 1.0f);
+}
+
+// row length of the Lorenzo block in shared memory: even, so that the
+// points of a wavefront plane taken by consecutive lanes (i1 + 1, i2 - 1:
+// a step of n2p - 1 words) fall in distinct banks
+__host__ __device__ __forceinline__ int lorenzo_row(int n2) { return n2 + (n2 & 1); }
+
+template <int ORDER>
+__device__ __forceinline__ void lorenzo_body(const Sub& f, const int lim[3], float e,
+                                             float inv2, float twoe, float* R,
+                                             uint32_t* h, unsigned long long& no) {
+  const int n0 = f.n[0], n1 = f.n[1], n2 = f.n[2], n2p = lorenzo_row(n2);
   const int T = (n0 - 1) + (n1 - 1) + (n2 - 1);
   const int npair = n0 * n1;
   const unsigned mg1 = fdiv_magic((unsigned)n1);
@@ -791,21 +803,27 @@ __global__ void __launch_bounds__(kTuneThreads)
       if (q >= npair) continue;
       const int i0 = (int)fdiv((unsigned)q, mg1), i1 = q - i0 * n1, i2 = t - i0 - i1;
       if (i2 < 0 || i2 >= n2) continue;
+      const int base = (i0 * n1 + i1) * n2p + i2;
+      // terms in the order a (dim 0), b (dim 1), cz (dim 2); neighbours
+      // outside the block read 0
       float acc = 0.0f;
-      for (int a = 0; a <= lim[0]; ++a)
-        for (int b = 0; b <= lim[1]; ++b)
-          for (int cz = 0; cz <= lim[2]; ++cz) {
+#pragma unroll
+      for (int a = 0; a <= ORDER; ++a)
+#pragma unroll
+        for (int b = 0; b <= ORDER; ++b)
+#pragma unroll
+          for (int cz = 0; cz <= ORDER; ++cz) {
             if (a == 0 && b == 0 && cz == 0) continue;
-            const float wgt = -__fmul_rn(__fmul_rn(co[order - 1][a], co[order - 1][b]),
-                                         co[order - 1][cz]);
+            if (a > lim[0] || b > lim[1] || cz > lim[2]) continue;
+            const float wgt = -__fmul_rn(__fmul_rn(lorenzo_coef<ORDER>(a), lorenzo_coef<ORDER>(b)),
+                                         lorenzo_coef<ORDER>(cz));
             float v = 0.0f;
-            if (a <= i0 && b <= i1 && cz <= i2)
-              v = R[((i0 - a) * n1 + (i1 - b)) * n2 + (i2 - cz)];
+            if (a <= i0 && b <= i1 && cz <= i2) v = R[base - (a * n1 + b) * n2p - cz];
             acc = __fadd_rn(acc, __fmul_rn(wgt, v));
           }
       float rv;
       const unsigned code = quantize(xcur[k], acc, e, inv2, twoe, rv);
-      R[(i0 * n1 + i1) * n2 + i2] = rv;
+      R[base] = rv;
       atomicAdd(h + code, 1u);
       if (code == 0u) ++no;
     }
@@ -813,6 +831,28 @@ __global__ void __launch_bounds__(kTuneThreads)
 #pragma unroll
     for (int k = 0; k < kP; ++k) xcur[k] = xnext[k];
   }
+}
+
+__global__ void __launch_bounds__(kTuneThreads)
+    k_tune_lorenzo(const float* __restrict__ x, TuneGeom g,
+                   const Ctl* __restrict__ ctl, uint32_t* hists,
+                   unsigned long long* nout) {
+  extern __shared__ float R[];
+  __shared__ unsigned long long red[32];
+  const int order = blockIdx.y + 1;
+  const Sub f = sample_block(x, g, blockIdx.x);
+  const float e = ctl->e;
+  const float inv2 = __double2float_rn(__ddiv_rn(1.0, __dmul_rn(2.0, (double)e)));
+  const float twoe = __fmul_rn(2.0f, e);
+  int lim[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) lim[d] = d < g.off ? 0 : order;
+  uint32_t* h = hists + (size_t)blockIdx.y * 65536;
+  unsigned long long no = 0;
+  if (order == 1)
+    lorenzo_body<1>(f, lim, e, inv2, twoe, R, h, no);
+  else
+    lorenzo_body<2>(f, lim, e, inv2, twoe, R, h, no);
   no = block_sum(no, red);
   if (threadIdx.x == 0 && no) atomicAdd(nout + blockIdx.y, no);
 }
@@ -968,6 +1008,10 @@ size_t tune_test_smem(const TuneGeom& g) {
   return (size_t)g.ext[0] * g.ext[1] * g.ext[2] * sizeof(float);
 }
 
+size_t tune_lorenzo_smem(const TuneGeom& g) {
+  return (size_t)g.ext[0] * g.ext[1] * lorenzo_row((int)g.ext[2]) * sizeof(float);
+}
+
 void launch_tune_test(const float* x, const TuneGeom& g0, const TuneGeom& g1,
                       int ny0, const TuneCfg* cfgs, int nvar, int nblk,
                       int l_stop, bool hist, unsigned long long* score,
@@ -999,7 +1043,7 @@ void launch_tune_lorenzo(const float* x, const TuneGeom& g, int nblk,
                          const Ctl* ctl, uint32_t* hists,
                          unsigned long long* nout, cudaStream_t s) {
   set_smem_attr();
-  k_tune_lorenzo<<<dim3((unsigned)nblk, 2), kTuneThreads, tune_test_smem(g), s>>>(
+  k_tune_lorenzo<<<dim3((unsigned)nblk, 2), kTuneThreads, tune_lorenzo_smem(g), s>>>(
       x, g, ctl, hists, nout);
 }
 
