@@ -576,7 +576,7 @@ template <int KIND, bool kHist>
 __device__ void sweep_level_skip(float* R, const Sub& f, const int interp[3],
                               int k, int l, const TuneCfg& c, bool score_on,
                               unsigned long long& score, const HistSink& hist,
-                              unsigned long long& nout) {
+                              unsigned long long& nout, Box* bx) {
   const int sh = l - 1, s = 1 << sh;
   int line[3];
   unsigned imask = 0;
@@ -589,18 +589,22 @@ __device__ void sweep_level_skip(float* R, const Sub& f, const int interp[3],
   const bool md = c.md[l - 1] != 0;
   const bool same = c.same[l - 1] != 0 && kind != LINEAR;
   for (int pj = 0; pj < k; ++pj) {
-    Box bx[3];
+    // the pass's boxes (at most 3) in shared memory, one thread each
+    BoxDesc bd[3];
     int nb = 0;
     if (!md) {
       unsigned any = 0;  // directions earlier in the order: any parity
       for (int q = 0; q < pj; ++q) any |= 1u << c.ord[l - 1][q];
-      make_box(bx[0], f, interp, s, 1u << c.ord[l - 1][pj], any, false, 0u);
-      nb = 1;
+      bd[nb++] = BoxDesc{1u << c.ord[l - 1][pj], any, 0u};
     } else {
       for (unsigned S = 1; S < 8; ++S)
-        if ((S & imask) == S && __popc(S) == pj + 1)
-          make_box(bx[nb++], f, interp, s, S, 0u, false, 0u);
+        if ((S & imask) == S && __popc(S) == pj + 1) bd[nb++] = BoxDesc{S, 0u, 0u};
     }
+    __syncthreads();  // the previous pass is done with bx
+    if ((int)threadIdx.x < nb)
+      make_box(bx[threadIdx.x], f, interp, s, bd[threadIdx.x].S, bd[threadIdx.x].any, false,
+               0u);
+    __syncthreads();
     int tot = 0;
     for (int q = 0; q < nb; ++q) tot += bx[q].total;
     for (int half = 0; half < (same ? 2 : 1); ++half) {
@@ -878,6 +882,7 @@ __global__ void __launch_bounds__(kBlockThreads)
   extern __shared__ float R[];
   __shared__ TuneCfg c;
   __shared__ unsigned long long red[32];
+  __shared__ Box sbx[3];
   const int jj = j0 + (int)blockIdx.y;
   const uint8_t v = kBlockCodes[jj];
   unsigned long long* out = scores + (size_t)blockIdx.x * 5 + jj;
@@ -921,7 +926,7 @@ __global__ void __launch_bounds__(kBlockThreads)
   unsigned long long sc = 0, no = 0;
   const HistSink none{nullptr, nullptr};
   for (int l = L; l >= 1; --l)
-    sweep_level_skip<KIND, false>(R, f, g.interp, g.k, l, c, true, sc, none, no);
+    sweep_level_skip<KIND, false>(R, f, g.interp, g.k, l, c, true, sc, none, no, sbx);
   sc = block_sum(sc, red);
   if (threadIdx.x == 0) *out = sc;
 }
