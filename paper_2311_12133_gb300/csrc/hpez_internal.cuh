@@ -333,6 +333,12 @@ struct LevelMD {
 // Auto-tuner (Sec. 6): one theta of a compression test, and the geometry
 // of the sub-fields the tests run on.
 // ---------------------------------------------------------------------
+// one candidate of a level's tests: the level's fields of a theta (the
+// 1D-style order as slots)
+struct TuneCand {
+  uint8_t kind, md, same, ord[3];
+};
+
 struct TuneCfg {
   uint8_t kind[kMaxLevels];   // interpolator per level (l-1)
   uint8_t md[kMaxLevels];     // 1: multi-dimensional paradigm

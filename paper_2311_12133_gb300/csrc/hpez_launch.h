@@ -164,6 +164,16 @@ void launch_tune_stats(const float* x, const uint32_t n[3],
                        cudaStream_t s);
 void launch_tune_params(TuneCfg* cfgs, int nvar, int L, const Ctl* ctl,
                         cudaStream_t s);
+// cfgs[t] (t < n0 + n1) = base[variant of t] with level l's fields from
+// cands[t] (variant 0: t < n0)
+void launch_tune_expand(const TuneCfg* base, const TuneCand* cands, int n0, int n1, int l,
+                        TuneCfg* cfgs, cudaStream_t s);
+// per variant (nv <= 2): the first candidate with the smallest score; its
+// fields go into base[v] at level l, its index and score to
+// choice/best[v * 16 + l - 1]
+void launch_tune_select(const unsigned long long* score, const TuneCand* cands, int n0,
+                        int n1, int nv, int l, TuneCfg* base, uint8_t* choice,
+                        unsigned long long* best, cudaStream_t s);
 size_t tune_test_smem(const TuneGeom& g);
 size_t tune_lorenzo_smem(const TuneGeom& g);
 // (sample block, variant) CTAs; variants < ny0 use geometry g0, the rest g1.

@@ -104,6 +104,10 @@ struct Bufs {
   CodebookJob* cbjobs;
   unsigned long long* acc;
   TuneCfg* cfgs;
+  TuneCfg* base;     // each variant's theta during the level rounds
+  TuneCand* cands;   // the candidates of both variants
+  uint8_t* choice;   // per variant and level: the chosen candidate
+  unsigned long long* best;  // and its score
   unsigned long long* score;
   unsigned long long* nout;
   unsigned long long* cost;
@@ -271,61 +275,69 @@ int tune_globals(Call& k, std::vector<Variant>& vs, hpez_tune_report* rep,
   PhaseProfiler& prof = k.ctx->prof;
   const int nv = (int)vs.size();
   std::vector<TuneCfg> host(kMaxVariants);
-  std::vector<unsigned long long> sc(kMaxVariants);
   int rc;
   if (rep) rep->n_sample_blocks = (uint32_t)vs[0].nblk;
   const int L = vs[0].p.L;
   if (tp.tune_levels) {
-    for (int l = L; l >= 1; --l) {
-      int at = 0;
-      std::vector<int> base(nv);
-      for (int i = 0; i < nv; ++i) {
-        base[i] = at;
-        for (size_t j = 0; j < vs[i].cands.size(); ++j) {
-          hpez_config c2 = vs[i].cfg;
-          set_level(c2, l, vs[i].cands[j]);
-          host[at++] = to_device(vs[i].p, c2);
-        }
-      }
-      prof.begin(HPEZ_PH_TUNE_LEVELS, k.s);
-      cudaMemcpyAsync(k.b.cfgs, host.data(), sizeof(TuneCfg) * at,
-                      cudaMemcpyHostToDevice, k.s);
-      launch_tune_params(k.b.cfgs, at, kMaxLevels, k.b.ctl, k.s);
-      cudaMemsetAsync(k.b.score, 0, sizeof(unsigned long long) * at, k.s);
-      // every variant's candidates in one launch (escapes unused here),
-      // from the blocks' state after the levels above l
-      launch_tune_test(k.x, vs[0].g, vs[nv - 1].g, (int)vs[0].cands.size(),
-                       k.b.cfgs, at, vs[0].nblk, l, false, k.b.score, nullptr,
-                       k.b.nout + kMaxHists, k.b.state, k.s);
-      nl += 2;
-      prof.end(k.s);
-      cudaMemcpyAsync(sc.data(), k.b.score, sizeof(unsigned long long) * at,
-                      cudaMemcpyDeviceToHost, k.s);
-      if ((rc = sync_check(k))) return rc;
-      for (int i = 0; i < nv; ++i) {
-        const int n = (int)vs[i].cands.size();
-        int best = 0;
-        for (int j = 1; j < n; ++j)
-          if (sc[base[i] + j] < sc[base[i] + best]) best = j;
-        set_level(vs[i].cfg, l, vs[i].cands[best]);
-        if (rep) {
-          rep->level_choice[vs[i].slot][l - 1] = (uint8_t)best;
-          rep->level_score[vs[i].slot][l - 1] = sc[base[i] + best];
-        }
-      }
-      if (l > 1) {
-        // the chosen level l of each variant, kept for the finer levels
-        for (int i = 0; i < nv; ++i) host[i] = to_device(vs[i].p, vs[i].cfg);
-        prof.begin(HPEZ_PH_TUNE_LEVELS, k.s);
-        cudaMemcpyAsync(k.b.cfgs, host.data(), sizeof(TuneCfg) * nv,
-                        cudaMemcpyHostToDevice, k.s);
-        launch_tune_params(k.b.cfgs, nv, kMaxLevels, k.b.ctl, k.s);
-        launch_tune_advance(k.x, vs[0].g, vs[nv - 1].g, nv, vs[0].nblk, k.b.cfgs, l,
-                            k.b.state, k.s);
-        nl += 2;
-        prof.end(k.s);
+    // The levels' rounds run on the device end to end: each variant's
+    // theta lives in b.base; a round expands it into the candidates of
+    // level l, tests them, and selects the first best candidate into it
+    // (the same choice as a host-side argmin); the choices come back once.
+    const int n0 = (int)vs[0].cands.size(), n1 = nv > 1 ? (int)vs[1].cands.size() : 0;
+    std::vector<TuneCand> tc;
+    for (int i = 0; i < nv; ++i) {
+      host[i] = to_device(vs[i].p, vs[i].cfg);
+      for (const Cand& c : vs[i].cands) {
+        TuneCand t;
+        t.kind = (uint8_t)c.kind;
+        t.md = (uint8_t)(c.md ? 1 : 0);
+        t.same = (uint8_t)c.same;
+        for (int j = 0; j < 3; ++j)
+          t.ord[j] = (uint8_t)(j < vs[i].p.k ? c.ord[j] + vs[i].p.off : 0);
+        tc.push_back(t);
       }
     }
+    prof.begin(HPEZ_PH_TUNE_LEVELS, k.s);
+    cudaMemcpyAsync(k.b.base, host.data(), sizeof(TuneCfg) * nv, cudaMemcpyHostToDevice,
+                    k.s);
+    cudaMemcpyAsync(k.b.cands, tc.data(), sizeof(TuneCand) * tc.size(),
+                    cudaMemcpyHostToDevice, k.s);
+    launch_tune_params(k.b.base, nv, kMaxLevels, k.b.ctl, k.s);
+    nl += 1;
+    prof.end(k.s);
+    for (int l = L; l >= 1; --l) {
+      prof.begin(HPEZ_PH_TUNE_LEVELS, k.s);
+      launch_tune_expand(k.b.base, k.b.cands, n0, n1, l, k.b.cfgs, k.s);
+      cudaMemsetAsync(k.b.score, 0, sizeof(unsigned long long) * (n0 + n1), k.s);
+      // every variant's candidates in one launch (escapes unused here),
+      // from the blocks' state after the levels above l
+      launch_tune_test(k.x, vs[0].g, vs[nv - 1].g, n0, k.b.cfgs, n0 + n1, vs[0].nblk, l,
+                       false, k.b.score, nullptr, k.b.nout + kMaxHists, k.b.state, k.s);
+      launch_tune_select(k.b.score, k.b.cands, n0, n1, nv, l, k.b.base, k.b.choice,
+                         k.b.best, k.s);
+      nl += 3;
+      // the chosen level l of each variant, kept for the finer levels
+      if (l > 1) {
+        launch_tune_advance(k.x, vs[0].g, vs[nv - 1].g, nv, vs[0].nblk, k.b.base, l,
+                            k.b.state, k.s);
+        ++nl;
+      }
+      prof.end(k.s);
+    }
+    uint8_t choice[2 * kMaxLevels];
+    unsigned long long best[2 * kMaxLevels];
+    cudaMemcpyAsync(choice, k.b.choice, sizeof(choice), cudaMemcpyDeviceToHost, k.s);
+    cudaMemcpyAsync(best, k.b.best, sizeof(best), cudaMemcpyDeviceToHost, k.s);
+    if ((rc = sync_check(k))) return rc;
+    for (int i = 0; i < nv; ++i)
+      for (int l = L; l >= 1; --l) {
+        const int c = choice[i * kMaxLevels + l - 1];
+        set_level(vs[i].cfg, l, vs[i].cands[c]);
+        if (rep) {
+          rep->level_choice[vs[i].slot][l - 1] = (uint8_t)c;
+          rep->level_score[vs[i].slot][l - 1] = best[i * kMaxLevels + l - 1];
+        }
+      }
   }
 
   // (alpha, beta): the grid, or the defaults alone
@@ -458,6 +470,10 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
   const size_t o_cbjobs = ar.take<CodebookJob>(kMaxHists);
   const size_t o_acc = ar.take<unsigned long long>(8);
   const size_t o_cfgs = ar.take<TuneCfg>(kMaxVariants);
+  const size_t o_base = ar.take<TuneCfg>(2);
+  const size_t o_cands = ar.take<TuneCand>(kMaxVariants);
+  const size_t o_choice = ar.take<uint8_t>(2 * kMaxLevels);
+  const size_t o_best = ar.take<unsigned long long>(2 * kMaxLevels);
   const size_t o_score = ar.take<unsigned long long>(kMaxVariants);
   const size_t o_nout = ar.take<unsigned long long>(kMaxVariants);
   const size_t o_cost = ar.take<unsigned long long>(kMaxVariants);
@@ -485,6 +501,10 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
   k.b.cbjobs = reinterpret_cast<CodebookJob*>(base + o_cbjobs);
   k.b.acc = reinterpret_cast<unsigned long long*>(base + o_acc);
   k.b.cfgs = reinterpret_cast<TuneCfg*>(base + o_cfgs);
+  k.b.base = reinterpret_cast<TuneCfg*>(base + o_base);
+  k.b.cands = reinterpret_cast<TuneCand*>(base + o_cands);
+  k.b.choice = reinterpret_cast<uint8_t*>(base + o_choice);
+  k.b.best = reinterpret_cast<unsigned long long*>(base + o_best);
   k.b.score = reinterpret_cast<unsigned long long*>(base + o_score);
   k.b.nout = reinterpret_cast<unsigned long long*>(base + o_nout);
   k.b.cost = reinterpret_cast<unsigned long long*>(base + o_cost);

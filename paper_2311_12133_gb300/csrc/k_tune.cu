@@ -142,6 +142,44 @@ __global__ void k_tune_params(TuneCfg* cfgs, int nvar, int L,
   c.inv_el[l - 1] = __double2float_rn(__ddiv_rn(1.0, (double)el));
 }
 
+__global__ void k_tune_expand(const TuneCfg* __restrict__ base,
+                              const TuneCand* __restrict__ cands, int n0, int l,
+                              TuneCfg* __restrict__ cfgs) {
+  const int t = blockIdx.x;
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(base + (t < n0 ? 0 : 1));
+  uint32_t* d = reinterpret_cast<uint32_t*>(cfgs + t);
+  for (int i = threadIdx.x; i < (int)(sizeof(TuneCfg) / 4); i += blockDim.x) d[i] = s[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const TuneCand c = cands[t];
+    TuneCfg& o = cfgs[t];
+    o.kind[l - 1] = c.kind;
+    o.md[l - 1] = c.md;
+    o.same[l - 1] = c.same;
+    for (int j = 0; j < 3; ++j) o.ord[l - 1][j] = c.ord[j];
+  }
+}
+
+__global__ void k_tune_select(const unsigned long long* __restrict__ score,
+                              const TuneCand* __restrict__ cands, int n0, int n1, int nv,
+                              int l, TuneCfg* base, uint8_t* choice,
+                              unsigned long long* best_score) {
+  const int v = threadIdx.x;
+  if (v >= nv) return;
+  const int b0 = v == 0 ? 0 : n0, n = v == 0 ? n0 : n1;
+  int best = 0;
+  for (int j = 1; j < n; ++j)
+    if (score[b0 + j] < score[b0 + best]) best = j;
+  const TuneCand c = cands[b0 + best];
+  TuneCfg& o = base[v];
+  o.kind[l - 1] = c.kind;
+  o.md[l - 1] = c.md;
+  o.same[l - 1] = c.same;
+  for (int j = 0; j < 3; ++j) o.ord[l - 1][j] = c.ord[j];
+  choice[v * kMaxLevels + l - 1] = (uint8_t)best;
+  best_score[v * kMaxLevels + l - 1] = score[b0 + best];
+}
+
 // ---------------------------------------------------------------------
 // one sub-field in shared memory
 // ---------------------------------------------------------------------
@@ -1007,6 +1045,17 @@ void launch_tune_params(TuneCfg* cfgs, int nvar, int L, const Ctl* ctl,
                         cudaStream_t s) {
   const int n = nvar * L;
   k_tune_params<<<(n + 127) / 128, 128, 0, s>>>(cfgs, nvar, L, ctl);
+}
+
+void launch_tune_expand(const TuneCfg* base, const TuneCand* cands, int n0, int n1, int l,
+                        TuneCfg* cfgs, cudaStream_t s) {
+  if (n0 + n1 > 0) k_tune_expand<<<n0 + n1, 64, 0, s>>>(base, cands, n0, l, cfgs);
+}
+
+void launch_tune_select(const unsigned long long* score, const TuneCand* cands, int n0,
+                        int n1, int nv, int l, TuneCfg* base, uint8_t* choice,
+                        unsigned long long* best, cudaStream_t s) {
+  k_tune_select<<<1, 32, 0, s>>>(score, cands, n0, n1, nv, l, base, choice, best);
 }
 
 size_t tune_test_smem(const TuneGeom& g) {
