@@ -478,12 +478,14 @@ __device__ __forceinline__ void sweep_box(float* R, const Sub& f, const Box B, b
 // fixed (the config's value is that kind)
 // sbox: shared memory for the boxes of a pass (at most 6), each built by
 // one thread
+// sh: the level's stride as a shift in the coordinates of f (l - 1 on the
+// sample block, 0 on its compact level-l grid)
 template <int KIND, bool kHist>
 __device__ void sweep_level_k(float* R, const Sub& f, const int interp[3],
-                              int k, int l, const TuneCfg& c, bool score_on,
+                              int k, int l, int sh, const TuneCfg& c, bool score_on,
                               unsigned long long& score, const HistSink& hist,
                               unsigned long long& nout, Box* sbox) {
-  const int sh = l - 1, s = 1 << sh;
+  const int s = 1 << sh;
   int line[3];
   unsigned imask = 0;
 #pragma unroll
@@ -681,8 +683,9 @@ __device__ __forceinline__ void sweep_level(float* R, const Sub& f,
                                             const TuneCfg& c, bool score_on,
                                             unsigned long long& score,
                                             const HistSink& hist,
-                                            unsigned long long& nout, Box* sbox) {
-  sweep_level_k<-1, kHist>(R, f, interp, k, l, c, score_on, score, hist, nout, sbox);
+                                            unsigned long long& nout, Box* sbox,
+                                            int sh) {
+  sweep_level_k<-1, kHist>(R, f, interp, k, l, sh, c, score_on, score, hist, nout, sbox);
 }
 
 __device__ __forceinline__ void load_cfg(TuneCfg* dst, const TuneCfg* src) {
@@ -724,6 +727,51 @@ __device__ void copy_lattice(float* R, float* __restrict__ state, const Sub& f,
   __syncthreads();
 }
 
+// The level-s grid of a sample block (the points whose interpolation
+// coordinates are multiples of s) as a sub-field of its own: compact in
+// shared memory, its input strides scaled by s.  A level's passes read and
+// write only points of its grid, with neighbours at s, 2s, 3s (1, 2, 3 on
+// the compact grid), so the level runs on the compact grid unchanged.
+__device__ __forceinline__ Sub compact_sub(const Sub& f, const int interp[3], int s) {
+  Sub c = f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    if (interp[d]) {
+      c.n[d] = (f.n[d] - 1) / s + 1;
+      c.xst[d] = f.xst[d] * (uint32_t)s;
+    }
+  set_strides(c);
+  return c;
+}
+
+// the state's stride-2s lattice (sample-block layout) into the compact
+// level-s grid (its points at even compact coordinates)
+__device__ void load_state_compact(float* R, const float* __restrict__ state, const Sub& f,
+                                   const Sub& fc, const int interp[3], int s) {
+  int m[3], sp[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    sp[d] = interp[d] ? 2 : 1;
+    m[d] = (fc.n[d] + sp[d] - 1) / sp[d];
+  }
+  const unsigned mg2 = fdiv_magic((unsigned)m[2]), mg1 = fdiv_magic((unsigned)m[1]);
+  const int tot = m[0] * m[1] * m[2];
+  for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+    const unsigned r1 = fdiv((unsigned)q, mg2);
+    const unsigned r0 = fdiv(r1, mg1);
+    const int c[3] = {(int)r0 * sp[0], ((int)r1 - (int)r0 * m[1]) * sp[1],
+                      (q - (int)r1 * m[2]) * sp[2]};
+    int full = 0, comp = 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      full += c[d] * (interp[d] ? s : 1) * f.st[d];
+      comp += c[d] * fc.st[d];
+    }
+    R[comp] = state[full];
+  }
+  __syncthreads();
+}
+
 // Variants y < ny0 use geometry g0, the others g1 (two frozen-dimension
 // choices in one launch).  With a state buffer (candidate tests of level
 // l_stop), a CTA starts from its block's reconstruction after the coarser
@@ -748,18 +796,24 @@ __global__ void __launch_bounds__(kTestThreads, 1)
     for (int i = threadIdx.x; i < kWin; i += blockDim.x) win[i] = 0;
   load_cfg(&c, cfgs + v);
   const Sub f = sample_block(x, g, blockIdx.x);
-  int l_top = g.L;
-  if (state && l_stop < g.L) {
-    float* st = state + ((size_t)(second ? 1 : 0) * gridDim.x + blockIdx.x) * vol;
-    copy_lattice<true>(R, st, f, g.interp, 2 << (l_stop - 1));
-    l_top = l_stop;
-  } else {
-    init_anchors(R, f, g.interp, g.A);
-  }
   unsigned long long sc = 0, no = 0;
   HistSink h{win, kHist ? hists + (size_t)v * 65536 : nullptr};
-  for (int l = l_top; l >= l_stop; --l)
-    sweep_level<kHist>(R, f, g.interp, g.k, l, c, l == l_stop, sc, h, no, sbox);
+  if (state) {
+    // level l_stop alone, on the compact level grid, from the state after
+    // the levels above it (the anchors at the coarsest level)
+    const int s = 1 << (l_stop - 1);
+    const Sub fc = compact_sub(f, g.interp, s);
+    if (l_stop < g.L)
+      load_state_compact(R, state + ((size_t)(second ? 1 : 0) * gridDim.x + blockIdx.x) * vol,
+                         f, fc, g.interp, s);
+    else
+      init_anchors(R, fc, g.interp, 2);
+    sweep_level<kHist>(R, fc, g.interp, g.k, l_stop, c, true, sc, h, no, sbox, 0);
+  } else {
+    init_anchors(R, f, g.interp, g.A);
+    for (int l = g.L; l >= l_stop; --l)
+      sweep_level<kHist>(R, f, g.interp, g.k, l, c, l == l_stop, sc, h, no, sbox, l - 1);
+  }
   if (kHist)
     for (int i = threadIdx.x; i < kWin; i += blockDim.x)
       if (win[i]) atomicAdd(h.glob + (kRadius - kWin / 2) + i, win[i]);
@@ -790,7 +844,7 @@ __global__ void __launch_bounds__(kTestThreads, 1)
     copy_lattice<true>(R, st, f, g.interp, 2 << (l - 1));
   unsigned long long sc = 0, no = 0;
   const HistSink none{nullptr, nullptr};
-  sweep_level<false>(R, f, g.interp, g.k, l, c, false, sc, none, no, sbox);
+  sweep_level<false>(R, f, g.interp, g.k, l, c, false, sc, none, no, sbox, l - 1);
   copy_lattice<false>(R, st, f, g.interp, 1 << (l - 1));
 }
 
@@ -1062,6 +1116,14 @@ size_t tune_test_smem(const TuneGeom& g) {
   return (size_t)g.ext[0] * g.ext[1] * g.ext[2] * sizeof(float);
 }
 
+// the compact level-l grid of a sample block
+size_t tune_level_smem(const TuneGeom& g, int l) {
+  const uint32_t st = 1u << (l - 1);
+  size_t n = sizeof(float);
+  for (int d = 0; d < 3; ++d) n *= g.interp[d] ? (g.ext[d] - 1) / st + 1 : g.ext[d];
+  return n;
+}
+
 size_t tune_lorenzo_smem(const TuneGeom& g) {
   return (size_t)g.ext[0] * g.ext[1] * lorenzo_row((int)g.ext[2]) * sizeof(float);
 }
@@ -1073,14 +1135,23 @@ void launch_tune_test(const float* x, const TuneGeom& g0, const TuneGeom& g1,
                       cudaStream_t s) {
   set_smem_attr();
   const dim3 grid((unsigned)nblk, (unsigned)nvar);
-  const size_t sm = std::max(tune_test_smem(g0), tune_test_smem(g1));
+  const size_t sm = state ? std::max(tune_level_smem(g0, l_stop), tune_level_smem(g1, l_stop))
+                          : std::max(tune_test_smem(g0), tune_test_smem(g1));
   const unsigned vol = (unsigned)(tune_test_smem(g0) / sizeof(float));
+  // a coarse level's compact grid holds a few hundred or thousand points: a
+  // smaller CTA per (block, candidate) lets every CTA of the launch be
+  // resident at once (their fixed costs then overlap)
+  int tpb = kTestThreads;
+  if (state) {
+    const size_t pts = sm / sizeof(float);
+    tpb = pts <= 1024 ? 128 : pts <= 8192 ? 256 : kTestThreads;
+  }
   if (hist)
-    k_tune_test<true><<<grid, kTestThreads, sm, s>>>(x, g0, g1, ny0, cfgs, l_stop,
-                                                     score, hists, nout, state, vol);
+    k_tune_test<true><<<grid, tpb, sm, s>>>(x, g0, g1, ny0, cfgs, l_stop, score, hists, nout,
+                                            state, vol);
   else
-    k_tune_test<false><<<grid, kTestThreads, sm, s>>>(x, g0, g1, ny0, cfgs, l_stop,
-                                                      score, hists, nout, state, vol);
+    k_tune_test<false><<<grid, tpb, sm, s>>>(x, g0, g1, ny0, cfgs, l_stop, score, hists,
+                                             nout, state, vol);
 }
 
 void launch_tune_advance(const float* x, const TuneGeom& g0, const TuneGeom& g1,
