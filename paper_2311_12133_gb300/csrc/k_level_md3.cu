@@ -329,8 +329,6 @@ static_assert((kXC * 2) % 16 == 0 && (kCC * 2) % 16 == 0,
 static_assert(kXOff >= 3 && kCOff >= 2, "boxes cover the halo");
 constexpr int kNB = 3;                             // input boxes in flight
 constexpr int kStreamThreads = 512;
-constexpr int kRegRows = kS1 / 2 + 3;              // even rows of the region
-constexpr int kRegCols = kS2 / 2 + 3;              // even columns of the region
 constexpr int kWaitLimit = 1 << 20;
 
 __host__ __device__ constexpr int round128(int v) { return (v + 127) & ~127; }
@@ -482,26 +480,29 @@ __device__ __forceinline__ void stream_finish(const StreamCtx& S, const LevelMD&
 }
 
 // even plane k: coarse points, (0,0,1) and (0,1,0), then (0,1,1)
-template <bool kDecomp, int KIND, class In>
+// HR: the region's extra even rows / columns beyond the tile's (2 for
+// the cubic stencils' +-3 reads, 0 when only +-1 is read)
+template <bool kDecomp, int KIND, int HR, class In>
 __device__ __forceinline__ void stream_even(const StreamCtx& S, const LevelMD& P, int k,
                                             bool own_e, float* B, const In* xb,
                                             const float* cb, const uint16_t* ccb,
                                             const float* __restrict__ outl,
                                             float* __restrict__ Rs,
                                             uint16_t* __restrict__ Cs) {
+  constexpr int RR = kS1 / 2 + 1 + HR, RC = kS2 / 2 + 1 + HR;
   const int tid = threadIdx.x;
   const int u0 = 2 * k;
   const int r_hi = min(S.R0 + kS1, S.m1), c_hi = min(S.C0 + kS2, S.m2);
-  for (int i = tid; i < kRegRows * kRegCols; i += kStreamThreads) {
-    const int ii = i / kRegCols, jj = i - ii * kRegCols;
-    const int r = S.R0 - 2 + 2 * ii, c = S.C0 - 2 + 2 * jj;
+  for (int i = tid; i < RR * RC; i += kStreamThreads) {
+    const int ii = i / RC, jj = i - ii * RC;
+    const int r = S.R0 - HR + 2 * ii, c = S.C0 - HR + 2 * jj;
     if (r < 0 || r >= S.m1 || c < 0 || c >= S.m2) continue;
-    const float v = cb[ii * kCC + jj + kCOff - 1];
-    B[(1 + 2 * ii) * kBC + 1 + 2 * jj] = v;
+    const float v = cb[(ii + 1 - HR / 2) * kCC + jj + kCOff - HR / 2];
+    B[(3 - HR + 2 * ii) * kBC + 3 - HR + 2 * jj] = v;
     if (own_e && r >= S.R0 && r < r_hi && c >= S.C0 && c < c_hi) {
       const uint32_t fi = (uint32_t)u0 * S.gst0 + (uint32_t)r * S.gst1 + (uint32_t)c;
       if (!kDecomp) {
-        Cs[fi] = ccb[ii * kCC + jj + kCOff - 1];
+        Cs[fi] = ccb[(ii + 1 - HR / 2) * kCC + jj + kCOff - HR / 2];
       } else {
         Rs[fi] = v;
       }
@@ -510,26 +511,26 @@ __device__ __forceinline__ void stream_even(const StreamCtx& S, const LevelMD& P
   __syncthreads();
   // (0,0,1): even rows of the region, odd columns of the tile, along dim 2;
   // (0,1,0): odd rows of the tile, even columns of the region, along dim 1
-  constexpr int n1 = kRegRows * (kS2 / 2), n2 = (kS1 / 2) * kRegCols;
+  constexpr int n1 = RR * (kS2 / 2), n2 = (kS1 / 2) * RC;
   for (int i = tid; i < n1 + n2; i += kStreamThreads) {
     if (i < n1) {
       const int ii = i / (kS2 / 2), jj = i - ii * (kS2 / 2);
-      const int r = S.R0 - 2 + 2 * ii, c = S.C0 + 1 + 2 * jj;
+      const int r = S.R0 - HR + 2 * ii, c = S.C0 + 1 + 2 * jj;
       if (r < 0 || r >= S.m1 || c >= S.m2) continue;
-      const int br = 1 + 2 * ii, bc = 4 + 2 * jj;
+      const int br = 3 - HR + 2 * ii, bc = 4 + 2 * jj;
       const float* row = B + br * kBC + bc;
       const float pd = predict_fast<KIND>([&](int j) { return row[j]; }, c, S.m2);
       stream_finish<kDecomp>(S, P, u0, r, c, br, bc, kXOff + 1 + 2 * jj, __fmul_rn(P.w[4][2], pd),
                              own_e && r >= S.R0 && r < r_hi, B, xb, outl, Rs, Cs);
     } else {
       const int i2 = i - n1;
-      const int ii = i2 / kRegCols, jj = i2 - ii * kRegCols;
-      const int r = S.R0 + 1 + 2 * ii, c = S.C0 - 2 + 2 * jj;
+      const int ii = i2 / RC, jj = i2 - ii * RC;
+      const int r = S.R0 + 1 + 2 * ii, c = S.C0 - HR + 2 * jj;
       if (r >= S.m1 || c < 0 || c >= S.m2) continue;
-      const int br = 4 + 2 * ii, bc = 1 + 2 * jj;
+      const int br = 4 + 2 * ii, bc = 3 - HR + 2 * jj;
       const float* col = B + br * kBC + bc;
       const float pd = predict_fast<KIND>([&](int j) { return col[j * kBC]; }, r, S.m1);
-      stream_finish<kDecomp>(S, P, u0, r, c, br, bc, kXOff - 2 + 2 * jj, __fmul_rn(P.w[2][1], pd),
+      stream_finish<kDecomp>(S, P, u0, r, c, br, bc, kXOff - HR + 2 * jj, __fmul_rn(P.w[2][1], pd),
                              own_e && c >= S.C0 && c < c_hi, B, xb, outl, Rs, Cs);
     }
   }
@@ -590,7 +591,7 @@ __device__ __forceinline__ float pred_dim0(int f0, const float* const E[4], int 
 
 // odd plane k: (1,0,0), then (1,0,1) and (1,1,0), then (1,1,1); FZ as
 // for pred_dim0
-template <bool kDecomp, int KIND, int FZ, class In>
+template <bool kDecomp, int KIND, int FZ, int HR, class In>
 __device__ __forceinline__ void stream_odd(const StreamCtx& S, const LevelMD& P, int k,
                                            int f0, float* O, const float* ring, const In* xb,
                                            const float* __restrict__ outl,
@@ -598,30 +599,31 @@ __device__ __forceinline__ void stream_odd(const StreamCtx& S, const LevelMD& P,
                                            uint16_t* __restrict__ Cs) {
   constexpr int RN = Ring<KIND>::n;
   constexpr int PB = round128(kBR * kBC * 4) / 4;
+  constexpr int RR = kS1 / 2 + 1 + HR, RC = kS2 / 2 + 1 + HR;
   const int tid = threadIdx.x;
   const int u0 = 2 * k + 1;
   const float* E[4] = {ring + ((k + RN - 1) % RN) * PB, ring + (k % RN) * PB,
                        ring + ((k + 1) % RN) * PB, ring + ((k + 2) % RN) * PB};
   const int r_hi = min(S.R0 + kS1, S.m1), c_hi = min(S.C0 + kS2, S.m2);
-  for (int i = tid; i < kRegRows * kRegCols; i += kStreamThreads) {
-    const int ii = i / kRegCols, jj = i - ii * kRegCols;
-    const int r = S.R0 - 2 + 2 * ii, c = S.C0 - 2 + 2 * jj;
+  for (int i = tid; i < RR * RC; i += kStreamThreads) {
+    const int ii = i / RC, jj = i - ii * RC;
+    const int r = S.R0 - HR + 2 * ii, c = S.C0 - HR + 2 * jj;
     if (r < 0 || r >= S.m1 || c < 0 || c >= S.m2) continue;
-    const int br = 1 + 2 * ii, bc = 1 + 2 * jj;
+    const int br = 3 - HR + 2 * ii, bc = 3 - HR + 2 * jj;
     const float pd = pred_dim0<FZ>(f0, E, br * kBC + bc);
-    stream_finish<kDecomp>(S, P, u0, r, c, br, bc, kXOff - 2 + 2 * jj, __fmul_rn(P.w[1][0], pd),
+    stream_finish<kDecomp>(S, P, u0, r, c, br, bc, kXOff - HR + 2 * jj, __fmul_rn(P.w[1][0], pd),
                            r >= S.R0 && r < r_hi && c >= S.C0 && c < c_hi, O, xb, outl, Rs,
                            Cs);
   }
   __syncthreads();
-  constexpr int n1 = kRegRows * (kS2 / 2), n2 = (kS1 / 2) * kRegCols;
+  constexpr int n1 = RR * (kS2 / 2), n2 = (kS1 / 2) * RC;
   for (int i = tid; i < n1 + n2; i += kStreamThreads) {
     if (i < n1) {
       // (1,0,1): even rows of the region, odd columns of the tile
       const int ii = i / (kS2 / 2), jj = i - ii * (kS2 / 2);
-      const int r = S.R0 - 2 + 2 * ii, c = S.C0 + 1 + 2 * jj;
+      const int r = S.R0 - HR + 2 * ii, c = S.C0 + 1 + 2 * jj;
       if (r < 0 || r >= S.m1 || c >= S.m2) continue;
-      const int br = 1 + 2 * ii, bc = 4 + 2 * jj;
+      const int br = 3 - HR + 2 * ii, bc = 4 + 2 * jj;
       const float* pt = O + br * kBC + bc;
       const float p0 = pred_dim0<FZ>(f0, E, br * kBC + bc);
       const float p2 = predict_fast<KIND>([&](int j) { return pt[j]; }, c, S.m2);
@@ -631,15 +633,15 @@ __device__ __forceinline__ void stream_odd(const StreamCtx& S, const LevelMD& P,
     } else {
       // (1,1,0): odd rows of the tile, even columns of the region
       const int i2 = i - n1;
-      const int ii = i2 / kRegCols, jj = i2 - ii * kRegCols;
-      const int r = S.R0 + 1 + 2 * ii, c = S.C0 - 2 + 2 * jj;
+      const int ii = i2 / RC, jj = i2 - ii * RC;
+      const int r = S.R0 + 1 + 2 * ii, c = S.C0 - HR + 2 * jj;
       if (r >= S.m1 || c < 0 || c >= S.m2) continue;
-      const int br = 4 + 2 * ii, bc = 1 + 2 * jj;
+      const int br = 4 + 2 * ii, bc = 3 - HR + 2 * jj;
       const float* pt = O + br * kBC + bc;
       const float p0 = pred_dim0<FZ>(f0, E, br * kBC + bc);
       const float p1 = predict_fast<KIND>([&](int j) { return pt[j * kBC]; }, r, S.m1);
       const float p = __fadd_rn(__fmul_rn(P.w[3][0], p0), __fmul_rn(P.w[3][1], p1));
-      stream_finish<kDecomp>(S, P, u0, r, c, br, bc, kXOff - 2 + 2 * jj, p,
+      stream_finish<kDecomp>(S, P, u0, r, c, br, bc, kXOff - HR + 2 * jj, p,
                              c >= S.C0 && c < c_hi, O, xb, outl, Rs, Cs);
     }
   }
@@ -691,6 +693,12 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
   const int chunk = (int)(blockIdx.x / (unsigned)ntiles);
   S.R0 = (tile / nt2) * kS1;
   S.C0 = (tile % nt2) * kS2;
+  // the region beyond the tile: +-3 reads need two more even rows and
+  // columns on each side; linear reads +-1 (within the tile and one row /
+  // column past it), except extrapolation at the field's end, which reads
+  // 3 back and leaves the tile only when the last tile has under 4 rows or
+  // columns
+  const bool wide = KIND != LINEAR || S.m1 - S.R0 < 4 || S.m2 - S.C0 < 4;
   const int ke = (S.m0 + 1) / 2, ko = S.m0 / 2;
   const int K0 = chunk * K;
   const int K1o = min(K0 + K, ko), K1e = min(K0 + K, ke);
@@ -758,14 +766,25 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
       const uint16_t* ccb =
           reinterpret_cast<const uint16_t*>(smem + L::kOffCC + slot * round128(L::kCCBytes));
       float* B = ring + (k % RN) * (round128(L::kBufBytes) / 4);
-      stream_even<kDecomp, KIND>(S, P, k, k >= K0 && k < K1e, B, xb, cb, ccb, outl, Rs, Cs);
+      if (wide)
+        stream_even<kDecomp, KIND, 2>(S, P, k, k >= K0 && k < K1e, B, xb, cb, ccb, outl, Rs,
+                                      Cs);
+      else
+        stream_even<kDecomp, KIND, 0>(S, P, k, k >= K0 && k < K1e, B, xb, cb, ccb, outl, Rs,
+                                      Cs);
     } else {
       constexpr int FZ = KIND == LINEAR ? F_LIN : (KIND == CUBIC_NAK ? F_NAK4 : F_NAT4);
       const int f0 = choose_formula(KIND, false, 2 * k + 1, S.m0);
-      if (f0 == FZ)
-        stream_odd<kDecomp, KIND, FZ>(S, P, k, f0, O, ring, xb, outl, Rs, Cs);
-      else
-        stream_odd<kDecomp, KIND, -1>(S, P, k, f0, O, ring, xb, outl, Rs, Cs);
+      if (f0 == FZ) {
+        if (wide)
+          stream_odd<kDecomp, KIND, FZ, 2>(S, P, k, f0, O, ring, xb, outl, Rs, Cs);
+        else
+          stream_odd<kDecomp, KIND, FZ, 0>(S, P, k, f0, O, ring, xb, outl, Rs, Cs);
+      } else if (wide) {
+        stream_odd<kDecomp, KIND, -1, 2>(S, P, k, f0, O, ring, xb, outl, Rs, Cs);
+      } else {
+        stream_odd<kDecomp, KIND, -1, 0>(S, P, k, f0, O, ring, xb, outl, Rs, Cs);
+      }
     }
     ++done;
     __syncthreads();  // the slot and the plane buffers are free again
