@@ -40,6 +40,28 @@ HBM_FALLBACK_GBS = 6800.0
 L2_BYTES = 129 * 1024 * 1024
 
 
+def max_over_ranks(vals, dist, device="cpu"):
+    """Each value's maximum over the ranks: the slowest rank sets the job's
+    time (no data-path collective; this is the only exchange)."""
+    import torch
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_gbps(world: int, n_points: int, seconds: float) -> float:
+    """Whole-job input throughput: every rank processes its own field of
+    n_points float32 values (replicas, weak scaling)."""
+    return world * 4 * n_points / seconds / 1e9
+
+
+def replica_seed(rank: int) -> int:
+    """Seed of the field rank `rank` generates (each replica its own field)."""
+    from paper_2311_12133_gb300 import fields
+    return fields.seed_of("bench", rank)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -447,7 +469,7 @@ def main():
     shape = tuple(int(v) for v in args.shape.split(","))
     N = int(np.prod(shape))
     A = 32 if len(shape) == 3 else (64 if len(shape) == 2 else 128)
-    x = fields.grf_torch(shape, seed=fields.seed_of("bench", rank), device=f"cuda:{local}")
+    x = fields.grf_torch(shape, seed=replica_seed(rank), device=f"cuda:{local}")
     ctx = hpez.Context(local)
     hpez.hpez_set_option(ctx.handle, hpez.HPEZ_OPT_FUSED_LEVELS, args.fused)
     if args.tile:
@@ -513,12 +535,9 @@ def main():
     if args.profile_only:
         return
 
-    t = torch.tensor([total_ms, comp_ms, dec_ms], dtype=torch.float64, device=x.device)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms, comp_ms, dec_ms = [float(v) for v in t.tolist()]
+    total_ms, comp_ms, dec_ms = max_over_ranks([total_ms, comp_ms, dec_ms], dist, x.device)
     ms_per_step = total_ms / args.steps
-    value = world * 4 * N / (ms_per_step / 1e3) / 1e9
+    value = job_gbps(world, N, ms_per_step / 1e3)
 
     # correctness of what was timed: bound held at every point
     hdr = cbuf[:512].cpu().numpy().tobytes()
@@ -570,11 +589,8 @@ def main():
                                               hout, sptr)
             hpez.hpez_decompress_host(ctx.handle, hout, sz, hy, sptr)
         e2e_s = (time.perf_counter() - t0) / args.steps
-        te = torch.tensor([e2e_s], dtype=torch.float64, device=x.device)
-        if dist:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e_s = float(te.item())
-        e2e = {"value": round(world * 4 * N / e2e_s / 1e9, 3), "unit": "GB/s",
+        e2e_s = max_over_ranks([e2e_s], dist, x.device)[0]
+        e2e = {"value": round(job_gbps(world, N, e2e_s), 3), "unit": "GB/s",
                "h2d_bytes_per_step": 4 * N + sz, "d2h_bytes_per_step": sz + 4 * N}
 
     cpu = None
