@@ -374,6 +374,11 @@ HPEZ_API int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim,
  *                         multi-dimensional paradigm streams its planes
  *                         through shared memory in one launch (rows of a
  *                         multiple of 8 points); 0: two launches
+ *  HPEZ_OPT_DROP_COPY     0 (default); n > 0: a test of the bounded device
+ *                         waits -- the first CTA of the streamed level kernel
+ *                         leaves out the copies of its n-th plane, its wait for
+ *                         them expires and the call returns HPEZ_ERR_TIMEOUT
+ *                         (no copy stays in flight; the context stays usable)
  * Errors: INVALID_ARG for an unknown option or an out-of-range value. */
 #define HPEZ_OPT_FUSED_LEVELS 1
 #define HPEZ_OPT_TILE_E0 2
@@ -382,6 +387,7 @@ HPEZ_API int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim,
 #define HPEZ_OPT_FUSED_SMEM 5
 #define HPEZ_OPT_LEVEL3D 6
 #define HPEZ_OPT_STREAM_LEVELS 7
+#define HPEZ_OPT_DROP_COPY 8
 HPEZ_API int hpez_set_option(hpez_ctx* ctx, int option, int64_t value);
 
 /* ---- measurement hooks (not part of the paper's method) ----

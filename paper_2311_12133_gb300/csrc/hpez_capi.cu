@@ -727,6 +727,10 @@ int hpez_set_option(hpez_ctx* ctx, int option, int64_t value) {
     case HPEZ_OPT_STREAM_LEVELS:
       ctx->stream_levels = value != 0;
       return HPEZ_OK;
+    case HPEZ_OPT_DROP_COPY:
+      if (value < 0 || value > 1000000) return HPEZ_ERR_INVALID_ARG;
+      ctx->drop_copy = (int)value;
+      return HPEZ_OK;
     case HPEZ_OPT_FUSED_SMEM:
       if (value < 4096 || value > 200 * 1024) return HPEZ_ERR_INVALID_ARG;
       ctx->fused_smem_cap = (size_t)value;
@@ -949,7 +953,7 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
     } else if (plan_md3(ctx, p, sc, l, false, FM, E1)) {
       if (ctx->stream_levels && md3s_supported(FM, false, d_in, b.R[l], b.Cg[l]) &&
           launch_level_md3s(false, sb.kind, FM, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g],
-                            b.ctl, ctx->num_sms, s)) {
+                            b.ctl, ctx->num_sms, ctx->drop_copy, s)) {
         ++nl;
       } else {
         launch_level_md3(false, sb.kind, FM, E1, sb, b.R[l], b.Cg[l], b.R[g],
@@ -1167,7 +1171,7 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
     } else if (plan_md3(ctx, p, sc, l, true, FM, E1)) {
       if (ctx->stream_levels && md3s_supported(FM, true, codes, R[l], nullptr) &&
           launch_level_md3s(true, sb.kind, FM, sb, R[l], nullptr, R[g], nullptr, ctl,
-                            ctx->num_sms, s)) {
+                            ctx->num_sms, ctx->drop_copy, s)) {
         ++nl;
       } else {
         launch_level_md3(true, sb.kind, FM, E1, sb, R[l], nullptr, R[g], nullptr, s);

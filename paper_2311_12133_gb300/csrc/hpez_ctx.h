@@ -75,6 +75,7 @@ struct hpez_ctx {
   int fused_levels = 1;        // HPEZ_OPT_FUSED_LEVELS
   int level3d = 1;             // HPEZ_OPT_LEVEL3D
   int stream_levels = 1;       // HPEZ_OPT_STREAM_LEVELS
+  int drop_copy = 0;           // HPEZ_OPT_DROP_COPY
   // the value range of the last tuned input (order-preserving keys), which
   // the compress call of hpez_compress_auto reuses instead of a second pass
   bool range_hint_on = false;

@@ -52,7 +52,7 @@ bool md3s_supported(const LevelMD& P, bool decomp, const void* in, const float* 
                     const uint16_t* Cc);
 int launch_level_md3s(bool decomp, int kind, const LevelMD& P, const SweepBufs& B,
                       const float* Rc, const uint16_t* Cc, float* Rs, uint16_t* Cs,
-                      Ctl* ctl, int num_sms, cudaStream_t s);
+                      Ctl* ctl, int num_sms, int drop_copy, cudaStream_t s);
 
 // k_huffman.cu
 void launch_hist(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,

@@ -329,7 +329,8 @@ static_assert((kXC * 2) % 16 == 0 && (kCC * 2) % 16 == 0,
 static_assert(kXOff >= 3 && kCOff >= 2, "boxes cover the halo");
 constexpr int kNB = 3;                             // input boxes in flight
 constexpr int kStreamThreads = 512;
-constexpr int kWaitLimit = 1 << 20;
+constexpr int kWaitLimit = 1 << 24;
+constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s
 
 __host__ __device__ constexpr int round128(int v) { return (v + 127) & ~127; }
 
@@ -378,9 +379,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+
+// A wait ends after kWaitNs of wall time (the nanosecond global timer) or
+// kWaitLimit polls, whichever comes first; false: the copy did not land.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int it = 0; it < kWaitLimit; ++it)
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (int it = 0; it < kWaitLimit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
   return false;
 }
 
@@ -669,7 +682,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
                  const __grid_constant__ CUtensorMap tm_c,
                  const __grid_constant__ CUtensorMap tm_cc, LevelMD P, int nt2,
                  int ntiles, int K, const float* __restrict__ outl, float* __restrict__ Rs,
-                 uint16_t* __restrict__ Cs, Ctl* ctl) {
+                 uint16_t* __restrict__ Cs, Ctl* ctl, int drop_copy) {
   using L = StreamLayout<kDecomp>;
   using In = typename L::In;
   constexpr int RN = Ring<KIND>::n;
@@ -715,7 +728,10 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
   sp.e_end = max(K1e - 1, min(ke - 1, K1o - 1 + sp.ahead));
   Sched si = sp;  // issue cursor, kNB planes ahead
 
-  auto issue = [&](int slot, bool odd, int k) {
+  // drop_copy > 0 (a test of the bounded waits): CTA 0 does not issue the
+  // copies of its plane drop_copy - 1, so the wait for them expires
+  auto issue = [&](int slot, bool odd, int k, int item) {
+    if (blockIdx.x == 0 && item + 1 == drop_copy) return;
     uint64_t* b = bar + slot;
     mbar_expect_tx(b, (uint32_t)(L::kInBytes + (odd ? 0 : L::kCBytes + L::kCCBytes)));
     tma_load_3d(smem + L::kOffIn + slot * round128(L::kInBytes), &tm_in, b, S.C0 - kXOff,
@@ -738,7 +754,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
     bool odd;
     int k;
     for (int b = 0; b < kNB && si.next(odd, k); ++b) {
-      if (tid == 0) issue(b, odd, k);
+      if (tid == 0) issue(b, odd, k, issued);
       ++issued;
     }
   }
@@ -793,7 +809,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
     if (si.next(odd2, k2)) {
       if (tid == 0) {
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        issue(slot, odd2, k2);
+        issue(slot, odd2, k2, issued);
       }
       ++issued;
     }
@@ -803,7 +819,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
 template <bool kDecomp, int KIND>
 int launch_md3s_k(const CUtensorMap& tin, const CUtensorMap& tc, const CUtensorMap& tcc,
                   const LevelMD& P, const float* outl, float* Rs, uint16_t* Cs, Ctl* ctl,
-                  int num_sms, cudaStream_t s) {
+                  int num_sms, int drop_copy, cudaStream_t s) {
   const int smem = StreamLayout<kDecomp>::bytes(Ring<KIND>::n);
   static bool attr = false;
   if (!attr) {
@@ -824,7 +840,7 @@ int launch_md3s_k(const CUtensorMap& tin, const CUtensorMap& tc, const CUtensorM
   const int K = (ke + nch - 1) / nch;
   nch = (ke + K - 1) / K;
   k_md3_stream<kDecomp, KIND><<<(unsigned)(ntiles * nch), kStreamThreads, smem, s>>>(
-      tin, tc, tcc, P, nt2, ntiles, K, outl, Rs, Cs, ctl);
+      tin, tc, tcc, P, nt2, ntiles, K, outl, Rs, Cs, ctl, drop_copy);
   return nch;
 }
 
@@ -915,7 +931,7 @@ bool md3s_supported(const LevelMD& P, bool decomp, const void* in, const float* 
 // made; nothing was launched then).
 int launch_level_md3s(bool decomp, int kind, const LevelMD& P, const SweepBufs& B,
                       const float* Rc, const uint16_t* Cc, float* Rs, uint16_t* Cs,
-                      Ctl* ctl, int num_sms, cudaStream_t s) {
+                      Ctl* ctl, int num_sms, int drop_copy, cudaStream_t s) {
   CUtensorMap tin, tc, tcc;
   const void* in = decomp ? (const void*)B.codes_full : (const void*)B.x;
   if (!make_map(&tin, in, decomp, P.g.m, kXC, kXR)) return 0;
@@ -928,16 +944,16 @@ int launch_level_md3s(bool decomp, int kind, const LevelMD& P, const SweepBufs& 
   const float* outl = B.outl_full;
   if (decomp) {
     if (kind == LINEAR)
-      return launch_md3s_k<true, LINEAR>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, s);
+      return launch_md3s_k<true, LINEAR>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, drop_copy, s);
     if (kind == CUBIC_NAK)
-      return launch_md3s_k<true, CUBIC_NAK>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, s);
-    return launch_md3s_k<true, CUBIC_NAT>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, s);
+      return launch_md3s_k<true, CUBIC_NAK>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, drop_copy, s);
+    return launch_md3s_k<true, CUBIC_NAT>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, drop_copy, s);
   }
   if (kind == LINEAR)
-    return launch_md3s_k<false, LINEAR>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, s);
+    return launch_md3s_k<false, LINEAR>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, drop_copy, s);
   if (kind == CUBIC_NAK)
-    return launch_md3s_k<false, CUBIC_NAK>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, s);
-  return launch_md3s_k<false, CUBIC_NAT>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, s);
+    return launch_md3s_k<false, CUBIC_NAK>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, drop_copy, s);
+  return launch_md3s_k<false, CUBIC_NAT>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, drop_copy, s);
 }
 
 }  // namespace hpez

@@ -213,6 +213,7 @@ def opts(gpu):
     yield gpu
     hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_FUSED_LEVELS, 1)
     hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_STREAM_LEVELS, 1)
+    hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_DROP_COPY, 0)
     for o in (hpez.HPEZ_OPT_TILE_E0, hpez.HPEZ_OPT_TILE_E1, hpez.HPEZ_OPT_TILE_E2):
         hpez.hpez_set_option(gpu.handle, o, 0)
 
@@ -300,6 +301,33 @@ def test_md_stream_level(opts, oracle, shape, eb, interp):
     assert runs[1][0] == runs[0][0] and runs[1][1] == runs[0][1]
     assert runs[0][2] - runs[1][2] == (1 if shape[2] % 16 == 0 else 0)
     assert runs[0][3] - runs[1][3] == 1
+
+
+def test_bounded_wait_expires(opts, oracle):
+    """A copy that never lands makes its bounded wait expire: the first CTA of
+    the streamed level kernel leaves out one plane's copies on request, the
+    call returns HPEZ_ERR_TIMEOUT within seconds, and the next call on the
+    same context is exact again (compress and decompress)."""
+    import time
+    import torch
+    from paper_2311_12133_gb300 import fields, hpez
+    x = fields.grf((40, 48, 64), seed=3)
+    kw = dict(interp=0, paradigm=1)
+    _, gcfg = _pair_configs(3, **kw)
+    xd = torch.from_numpy(x).cuda()
+    buf, size = opts.compress(xd, 1e-3, 1, gcfg)
+    for item in (1, 3):
+        hpez.hpez_set_option(opts.handle, hpez.HPEZ_OPT_DROP_COPY, item)
+        t0 = time.time()
+        with pytest.raises(hpez.HpezError) as e:
+            opts.compress(xd, 1e-3, 1, gcfg)
+        assert e.value.code == -9
+        with pytest.raises(hpez.HpezError) as e:
+            opts.decompress(buf, size)
+        assert e.value.code == -9
+        assert time.time() - t0 < 60
+    hpez.hpez_set_option(opts.handle, hpez.HPEZ_OPT_DROP_COPY, 0)
+    _check(opts, oracle, x, 1e-3, 1, **kw)
 
 
 @pytest.mark.parametrize("code", [0, 1, 2, 5, 6])
