@@ -209,6 +209,8 @@ static int check_config(const geom* g, const ora_config* c) {
   if (c->blockwise) {
     if (!c->blockmap || c->block_size < 1) return ORA_ERR_INVALID_ARG;
   }
+  if (c->predictor < 0 || c->predictor > 2 || (c->predictor && c->blockwise))
+    return ORA_ERR_INVALID_ARG;
   for (int l = 0; l < g->L; ++l) {
     if (c->interp[l] > ORA_CUBIC_NAT || c->paradigm[l] > ORA_MD ||
         c->same_level[l] > 1)
@@ -710,6 +712,62 @@ uint64_t ora_compress_bound(int ndim, const uint64_t* dims) {
          (17 * N) / 8 + 4 * nch + 64;
 }
 
+/* The Lorenzo predictor over the whole field (Sec. 6.5, the dynamic-order
+ * predictor of sz-auto, read here as block-local): the field is cut into
+ * blocks of side A along every dimension (the last ones ragged); inside a
+ * block, in row-major order, a point is predicted from the reconstructed
+ * points of its block by the order-1 or order-2 Lorenzo stencil, a
+ * neighbour outside the block reading 0 -- the recurrence the tuner's
+ * Lorenzo test runs on its sample blocks.  Terms in the order of the
+ * offsets (a, b, c) along dims 0, 1, 2, a outermost; each weight is minus
+ * the product of the per-dimension coefficients (1, -1) or (1, -2, 1).
+ * The error bound is the global e.  compress: codes and recon from x;
+ * decompress: recon from the codes, recon already holding the outliers. */
+static void lorenzo_field(const geom* g, int order, float e, const float* x,
+                          uint16_t* codes, float* recon, int decompress) {
+  const float inv2 = (float)(1.0 / (2.0 * (double)e));
+  const float twoe = 2.0f * e;
+  const float co[2][3] = {{1.0f, -1.0f, 0.0f}, {1.0f, -2.0f, 1.0f}};
+  int lim[3];
+  for (int d = 0; d < 3; ++d) lim[d] = d < g->off ? 0 : order;
+  const uint64_t B = (uint64_t)g->A;
+  uint64_t o[3];
+  for (o[0] = 0; o[0] < g->n[0]; o[0] += (g->off > 0 ? 1 : B))
+    for (o[1] = 0; o[1] < g->n[1]; o[1] += (g->off > 1 ? 1 : B))
+      for (o[2] = 0; o[2] < g->n[2]; o[2] += B) {
+        uint64_t m[3];
+        for (int d = 0; d < 3; ++d) {
+          const uint64_t side = d < g->off ? 1 : B;
+          m[d] = g->n[d] - o[d] < side ? g->n[d] - o[d] : side;
+        }
+        for (uint64_t i0 = 0; i0 < m[0]; ++i0)
+          for (uint64_t i1 = 0; i1 < m[1]; ++i1)
+            for (uint64_t i2 = 0; i2 < m[2]; ++i2) {
+              float acc = 0.0f;
+              for (int a = 0; a <= lim[0]; ++a)
+                for (int b = 0; b <= lim[1]; ++b)
+                  for (int c = 0; c <= lim[2]; ++c) {
+                    if (a == 0 && b == 0 && c == 0) continue;
+                    const float wgt = -(co[order - 1][a] * co[order - 1][b] * co[order - 1][c]);
+                    float v = 0.0f;
+                    if ((uint64_t)a <= i0 && (uint64_t)b <= i1 && (uint64_t)c <= i2)
+                      v = recon[(o[0] + i0 - a) * g->st[0] + (o[1] + i1 - b) * g->st[1] +
+                                (o[2] + i2 - c)];
+                    acc = acc + wgt * v;
+                  }
+              const uint64_t i = (o[0] + i0) * g->st[0] + (o[1] + i1) * g->st[1] + (o[2] + i2);
+              if (!decompress) {
+                float rec;
+                codes[i] = ora_quantize(x[i], acc, e, inv2, twoe, &rec);
+                recon[i] = rec;
+              } else if (codes[i] != 0) {
+                const int q = (int)codes[i] - ORA_RADIUS;
+                recon[i] = acc + (float)q * twoe;
+              } /* else: the outlier value is already in recon[i] */
+            }
+      }
+}
+
 static int write_const(uint8_t* out, uint64_t cap, uint64_t* out_size,
                        int ndim, const uint64_t* dims, int eb_mode, double eb,
                        float v, const ora_config* c) {
@@ -793,11 +851,16 @@ int ora_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode,
     return ORA_ERR_NO_MEMORY;
   }
 
-  /* anchors (Sec. 5.1): stored losslessly, code = radius (zero error) */
-  uint64_t na = count_anchors(&g);
+  /* anchors (Sec. 5.1): stored losslessly, code = radius (zero error);
+   * the Lorenzo predictor has none */
+  uint64_t na = c->predictor ? 0 : count_anchors(&g);
   float* anchors = (float*)malloc(sizeof(float) * (na ? na : 1));
   uint64_t ai = 0;
-  {
+  uint64_t missing = 0;
+  if (c->predictor) {
+    lorenzo_field(&g, c->predictor, e, x, w.codes, w.recon, 0);
+    w.predicted = N;
+  } else {
     uint64_t cc[3];
     for (cc[0] = 0; cc[0] < g.n[0]; ++cc[0])
       for (cc[1] = 0; cc[1] < g.n[1]; ++cc[1])
@@ -810,16 +873,15 @@ int ora_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode,
             w.stamp[i] = 1;
           }
         }
+    w.cur = 1;
+
+    /* the level sweep, coarse to fine */
+    for (int l = g.L; l >= 1; --l) run_level(&w, l);
+
+    /* every point is either an anchor or predicted exactly once */
+    for (uint64_t i = 0; i < N; ++i)
+      if (w.stamp[i] == 0) missing++;
   }
-  w.cur = 1;
-
-  /* the level sweep, coarse to fine */
-  for (int l = g.L; l >= 1; --l) run_level(&w, l);
-
-  /* every point is either an anchor or predicted exactly once */
-  uint64_t missing = 0;
-  for (uint64_t i = 0; i < N; ++i)
-    if (w.stamp[i] == 0) missing++;
 
   /* outliers in row-major order */
   uint64_t nout = 0;
@@ -917,7 +979,7 @@ int ora_compress(const float* x, int ndim, const uint64_t* dims, int eb_mode,
         put_u8(out, H_ORDER + 3 * l + j,
                (used && j < g.k) ? c->order[l][j] : 255);
     }
-    put_u32(out, H_PREDICTOR, 0);
+    put_u32(out, H_PREDICTOR, (uint32_t)c->predictor);
     put_u32(out, H_BLOCKWISE, (uint32_t)c->blockwise);
     put_u64(out, H_NANCHORS, na);
     put_u64(out, H_NOUTLIERS, nout);
@@ -1024,6 +1086,7 @@ int ora_decompress(const uint8_t* in, uint64_t size, float* out,
   }
   c.blockwise = (int32_t)get_u32(in, H_BLOCKWISE);
   c.block_size = (int32_t)get_u32(in, H_BLOCKSIZE);
+  c.predictor = (int32_t)get_u32(in, H_PREDICTOR);
   geom g;
   rc = geom_init(&g, ndim, dims, c.anchor_stride, c.frozen_dim);
   if (rc) return ORA_ERR_CORRUPT;
@@ -1056,7 +1119,7 @@ int ora_decompress(const uint8_t* in, uint64_t size, float* out,
   uint64_t nch = get_u64(in, H_NCHUNKS);
   uint64_t twords = get_u64(in, H_TOTALWORDS);
   const uint64_t C = (uint64_t)c.chunk_syms;
-  if (na != count_anchors(&g) || nch != (N + C - 1) / C || nused == 0 ||
+  if (na != (c.predictor ? 0 : count_anchors(&g)) || nch != (N + C - 1) / C || nused == 0 ||
       nused > 65536 || nout > N)
     return ORA_ERR_CORRUPT;
   uint64_t oa = get_u64(in, H_OFF_ANCHORS), ocw = get_u64(in, H_OFF_CHUNKW),
@@ -1159,7 +1222,7 @@ int ora_decompress(const uint8_t* in, uint64_t size, float* out,
       for (cc[1] = 0; cc[1] < g.n[1]; ++cc[1])
         for (cc[2] = 0; cc[2] < g.n[2]; ++cc[2]) {
           uint64_t i = cc[0] * g.st[0] + cc[1] * g.st[1] + cc[2];
-          if (is_anchor(&g, cc)) {
+          if (!c.predictor && is_anchor(&g, cc)) {
             out[i] = get_f32(in, oa + 4 * ai);
             ai++;
             w.stamp[i] = 1;
@@ -1170,7 +1233,9 @@ int ora_decompress(const uint8_t* in, uint64_t size, float* out,
         }
     if (oi != nout) rc = ORA_ERR_CORRUPT;
   }
-  if (!rc) {
+  if (!rc && c.predictor) {
+    lorenzo_field(&g, c.predictor, e, NULL, codes, out, 1);
+  } else if (!rc) {
     w.cur = 1;
     for (int l = g.L; l >= 1; --l) run_level(&w, l);
     if (w.bad_reads || w.double_visits) rc = ORA_ERR_SELFCHECK;
@@ -1680,11 +1745,19 @@ int ora_tune(const float* x, int ndim, const uint64_t* dims, int eb_mode,
       free(hist);
     }
     free_blocks(&bs);
+    const uint64_t m = lb[0] <= lb[1] ? lb[0] : lb[1];
+    const int better = (double)m * tp->lorenzo_coef < (double)bits_best;
     if (rep) {
       rep->lorenzo_bits[0] = lb[0];
       rep->lorenzo_bits[1] = lb[1];
-      const uint64_t m = lb[0] < lb[1] ? lb[0] : lb[1];
-      rep->lorenzo_better = (double)m * tp->lorenzo_coef < (double)bits_best;
+      rep->lorenzo_better = better;
+    }
+    /* the selection (Sec. 6.5): the Lorenzo predictor of the order with
+     * the smaller estimate (order 1 on a tie) when it beats interpolation;
+     * the block-wise interpolation tuning then does not apply */
+    if (better) {
+      out->predictor = lb[0] <= lb[1] ? 1 : 2;
+      return ORA_OK;
     }
   }
 

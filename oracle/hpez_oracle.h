@@ -46,7 +46,8 @@ typedef struct {
   int32_t chunk_syms;    /* Huffman chunk length, power of two in [256, 32768] */
   int32_t blockwise;     /* 1: per-block interpolator from blockmap (Sec. 6.6) */
   int32_t block_size;    /* block side for the block map (Sec. 6.6: 32) */
-  int32_t pad_;
+  int32_t predictor;     /* 0 interpolation; 1, 2: Lorenzo of that order
+                            on blocks of side anchor_stride (Sec. 6.5) */
   double alpha, beta;    /* Eq. 15 */
   double md_inv_var[3];  /* 1/sigma_i^2 per dimension for Eq. 14 weights */
   uint8_t interp[ORA_MAX_LEVELS];     /* per level l (index l-1) */

@@ -51,7 +51,7 @@ class Config(ctypes.Structure):
         ("chunk_syms", ctypes.c_int32),
         ("blockwise", ctypes.c_int32),
         ("block_size", ctypes.c_int32),
-        ("pad_", ctypes.c_int32),
+        ("predictor", ctypes.c_int32),
         ("alpha", ctypes.c_double),
         ("beta", ctypes.c_double),
         ("md_inv_var", ctypes.c_double * 3),
@@ -199,7 +199,7 @@ def default_config(ndim: int) -> Config:
 def make_config(ndim: int, *, anchor_stride=None, frozen_dim=-1,
                 chunk_syms=16384, alpha=1.0, beta=1.0, md_inv_var=(1, 1, 1),
                 interp=CUBIC_NAK, paradigm=P1D, same_level=0, order=None,
-                blockmap=None, block_size=32) -> Config:
+                blockmap=None, block_size=32, predictor=0) -> Config:
     """Config with one setting for every level unless per-level lists are
     given (index l-1)."""
     c = default_config(ndim)
@@ -232,6 +232,7 @@ def make_config(ndim: int, *, anchor_stride=None, frozen_dim=-1,
             c.order[l][j] = o[j] if j < len(o) else 255
     c.blockwise = 0
     c.block_size = block_size
+    c.predictor = predictor
     c._blockmap_ref = None
     if blockmap is not None:
         bm = np.ascontiguousarray(blockmap, dtype=np.uint8)
