@@ -72,7 +72,10 @@ typedef struct {
   int32_t chunk_syms;    /* Huffman chunk of 32 lanes, 2^k in [256, 32768] */
   int32_t blockwise;     /* 1: per-block interpolator map (Sec. 6.6) */
   int32_t block_size;    /* block side of the map (Sec. 6.6 default 32) */
-  int32_t reserved;
+  int32_t predictor;     /* 0 interpolation; 1, 2: the Lorenzo predictor of
+                            that order (Sec. 6.5) on blocks of side
+                            anchor_stride (blocks whose image fits a CTA:
+                            A <= 32 in 3D, 128 in 2D) */
   double alpha, beta;    /* Eq. 15 level bounds, both >= 1 */
   double md_inv_var[3];  /* 1/sigma_d^2 for the Eq. 14 weights, > 0 */
   uint8_t interp[HPEZ_MAX_LEVELS];     /* HPEZ_LINEAR / _CUBIC_NAK / _NAT */

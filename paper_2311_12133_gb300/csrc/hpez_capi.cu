@@ -103,6 +103,8 @@ int check_config(const Plan& p, const hpez_config& c) {
     if (!(c.md_inv_var[d] > 0.0) || !std::isfinite(c.md_inv_var[d]))
       return HPEZ_ERR_INVALID_ARG;
   if (c.blockwise && c.block_size < 1) return HPEZ_ERR_INVALID_ARG;
+  if (c.predictor < 0 || c.predictor > 2 || (c.predictor && c.blockwise))
+    return HPEZ_ERR_INVALID_ARG;
   for (int l = 0; l < p.L; ++l) {
     if (c.interp[l] > HPEZ_CUBIC_NAT || c.paradigm[l] > HPEZ_PARADIGM_MD ||
         c.same_level[l] > 1)
@@ -543,9 +545,9 @@ void header_templates(const Plan& p, const hpez_config& c, int eb_mode,
     for (int j = 0; j < 3; ++j)
       h[H_ORDER + 3 * l + j] = (used && j < p.k) ? c.order[l][j] : 255;
   }
-  wr32(h, H_PREDICTOR, 0);
+  wr32(h, H_PREDICTOR, (uint32_t)c.predictor);
   wr32(h, H_BLOCKWISE, (uint32_t)c.blockwise);
-  wr64(h, H_NANCHORS, n_anchors(p));
+  wr64(h, H_NANCHORS, c.predictor ? 0 : n_anchors(p));
   wr32(h, H_BLOCKSIZE, (uint32_t)c.block_size);
   wr64(h, H_NCHUNKS, p.nch);
   wr64(h, H_OFF_ANCHORS, off_anchors);
@@ -598,6 +600,7 @@ int parse_stream_header(const uint8_t* h, uint64_t in_size, StreamInfo& si) {
   cfg.chunk_syms = (int32_t)rd32(h, H_CHUNK);
   cfg.blockwise = (int32_t)rd32(h, H_BLOCKWISE);
   cfg.block_size = (int32_t)rd32(h, H_BLOCKSIZE);
+  cfg.predictor = (int32_t)rd32(h, H_PREDICTOR);
   cfg.alpha = rdf64(h, H_ALPHA);
   cfg.beta = rdf64(h, H_BETA);
   for (int d = 0; d < 3; ++d) cfg.md_inv_var[d] = rdf64(h, H_MDIV + 8 * d);
@@ -628,8 +631,8 @@ int parse_stream_header(const uint8_t* h, uint64_t in_size, StreamInfo& si) {
   const uint64_t oa = rd64(h, H_OFF_ANCHORS), ocw = rd64(h, H_OFF_CHUNKW),
                  ot = rd64(h, H_OFF_TABLE), oo = rd64(h, H_OFF_OUTLIERS),
                  ob = rd64(h, H_OFF_BITS), obm = rd64(h, H_OFF_BLOCKMAP);
-  if (na != n_anchors(p) || nch != p.nch || nused == 0 || nused > 65536 ||
-      nout > N || (cfg.blockwise && rd64(h, H_NBLOCKS) != p.nblocks))
+  if (na != (cfg.predictor ? 0 : n_anchors(p)) || nch != p.nch || nused == 0 ||
+      nused > 65536 || nout > N || (cfg.blockwise && rd64(h, H_NBLOCKS) != p.nblocks))
     return HPEZ_ERR_CORRUPT_STREAM;
   if (oa + 4 * na > in_size || ocw + 64 * nch > in_size ||
       ot + 3ull * nused > in_size || oo + 4 * nout > in_size ||
@@ -842,6 +845,8 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   rc = check_config(p, cfg);
   if (rc) return rc;
   if (cfg.blockwise && !cfg.h_blockmap) return HPEZ_ERR_INVALID_ARG;
+  if (cfg.predictor && !lorenzo_supported(p.n, p.fst, p.off, p.A))
+    return HPEZ_ERR_UNSUPPORTED;
   plan_chunks_blocks(p, cfg);
   cudaSetDevice(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -894,7 +899,7 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   b.bmap = reinterpret_cast<uint8_t*>(S + o_bmap);
 
   // stream layout (static part)
-  const uint64_t na = n_anchors(p);
+  const uint64_t na = cfg.predictor ? 0 : n_anchors(p);
   const uint64_t off_anchors = kHeaderBytes;
   const uint64_t off_bmap = a16(off_anchors + 4 * na);
   const uint64_t off_chw = a16(off_bmap + p.nblocks);
@@ -921,6 +926,16 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   ++nl;
   if (cfg.blockwise)
     cudaMemcpyAsync(b.bmap, cfg.h_blockmap, p.nblocks, cudaMemcpyHostToDevice, s);
+  if (cfg.predictor) {
+    // Sec. 6.5: the Lorenzo predictor over the field, codes into the
+    // finest grid's code array
+    pf.begin(HPEZ_PH_LEVEL, s);
+    rc = launch_lorenzo(false, cfg.predictor, p.n, p.fst, p.off, p.A, d_in, b.Cg[0],
+                        nullptr, b.ctl, s);
+    pf.end(s);
+    if (rc) return rc;
+    ++nl;
+  } else {
   pf.begin(HPEZ_PH_ANCHORS, s);
   launch_anchor_gather(d_in, p.grid[p.L], p.gsize[p.L], b.R[p.L], b.Cg[p.L],
                        b.ctl, s);
@@ -978,6 +993,7 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
     }
     pf.end(s);
   }
+  }  // interpolation
   uint16_t* codes = b.Cg[0];
   pf.begin(HPEZ_PH_HIST, s);
   cudaMemsetAsync(b.hist, 0, 65536 * sizeof(uint32_t), s);
@@ -1137,6 +1153,17 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
                   const_cast<uint8_t*>(in) + oo, nout, ctl, ctx->num_sms, s);
   pf.end(s);
   nl += 8;
+  if (cfg.predictor) {
+    // Sec. 6.5: the Lorenzo recurrence over the decoded codes; outliers
+    // are already in place
+    if (!lorenzo_supported(p.n, p.fst, p.off, p.A)) return HPEZ_ERR_UNSUPPORTED;
+    pf.begin(HPEZ_PH_DLEVEL, s);
+    rc = launch_lorenzo(true, cfg.predictor, p.n, p.fst, p.off, p.A, nullptr, codes,
+                        d_out, ctl, s);
+    pf.end(s);
+    if (rc) return rc;
+    ++nl;
+  }
   // a uniform block map runs as its interpolator (the map is read back)
   std::vector<uint8_t> hmap;
   if (cfg.blockwise) {
@@ -1155,7 +1182,7 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   sb.bs = (uint32_t)(cfg.block_size > 0 ? cfg.block_size : 1);
   for (int s3 = 0; s3 < 3; ++s3) sb.nb[s3] = p.nb[s3];
   sb.ctl = ctl;
-  for (int l = p.L; l >= 1; --l) {
+  for (int l = cfg.predictor ? 0 : p.L; l >= 1; --l) {
     const int g = l - 1;
     pf.begin(HPEZ_PH_DLEVEL + g, s);
     sb.R = R[g];
@@ -1348,6 +1375,7 @@ extern "C" int hpez_decompress_noalloc(const void* d_in, uint64_t in_size,
   cfg.chunk_syms = (int32_t)rd32(h, H_CHUNK);
   cfg.blockwise = (int32_t)rd32(h, H_BLOCKWISE);
   cfg.block_size = (int32_t)rd32(h, H_BLOCKSIZE);
+  cfg.predictor = (int32_t)rd32(h, H_PREDICTOR);
   cfg.alpha = rdf64(h, H_ALPHA);
   cfg.beta = rdf64(h, H_BETA);
   for (int d = 0; d < 3; ++d) cfg.md_inv_var[d] = rdf64(h, H_MDIV + 8 * d);
@@ -1369,6 +1397,7 @@ extern "C" int hpez_decompress_noalloc(const void* d_in, uint64_t in_size,
   if (plan_geometry(p, nd, dims, cfg.anchor_stride, cfg.frozen_dim))
     return HPEZ_ERR_CORRUPT_STREAM;
   if (check_config(p, cfg)) return HPEZ_ERR_CORRUPT_STREAM;
+  if (cfg.predictor) return HPEZ_ERR_UNSUPPORTED;  // Lorenzo streams: hpez_decompress
   plan_chunks_blocks(p, cfg);
   const float e = rdf32(h, H_E);
   if (!(e > 0.0f) || !std::isfinite(e)) return HPEZ_ERR_CORRUPT_STREAM;
@@ -1378,8 +1407,8 @@ extern "C" int hpez_decompress_noalloc(const void* d_in, uint64_t in_size,
   const uint64_t oa = rd64(h, H_OFF_ANCHORS), ocw = rd64(h, H_OFF_CHUNKW),
                  ot = rd64(h, H_OFF_TABLE), oo = rd64(h, H_OFF_OUTLIERS),
                  ob = rd64(h, H_OFF_BITS), obm = rd64(h, H_OFF_BLOCKMAP);
-  if (na != n_anchors(p) || nch != p.nch || nused == 0 || nused > 65536 ||
-      nout > N || (cfg.blockwise && rd64(h, H_NBLOCKS) != p.nblocks))
+  if (na != (cfg.predictor ? 0 : n_anchors(p)) || nch != p.nch || nused == 0 ||
+      nused > 65536 || nout > N || (cfg.blockwise && rd64(h, H_NBLOCKS) != p.nblocks))
     return HPEZ_ERR_CORRUPT_STREAM;
   if (oa + 4 * na > in_size || ocw + 64 * nch > in_size ||
       ot + 3ull * nused > in_size || oo + 4 * nout > in_size ||

@@ -109,6 +109,7 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   if (rc) return rc;
   if ((rc = check_config(p, cfg))) return rc;
   if (cfg.blockwise && !cfg.h_blockmap) return HPEZ_ERR_INVALID_ARG;
+  if (cfg.predictor) return HPEZ_ERR_UNSUPPORTED;  // Lorenzo: hpez_compress
   plan_chunks_blocks(p, cfg);
   r.decomp = 0;
   r.N = p.N;
@@ -300,6 +301,7 @@ int plan_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   int rc = parse_stream_header(static_cast<const uint8_t*>(h_header), in_size, si);
   if (rc) return rc;
   if (si.N > out_cap_elems) return HPEZ_ERR_OUT_TOO_SMALL;
+  if (!si.is_const && si.cfg.predictor) return HPEZ_ERR_UNSUPPORTED;
   r.decomp = 1;
   r.N = si.N;
   const Plan& p = si.p;

@@ -649,11 +649,21 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
     if ((rc = sync_check(k))) return rc;
     const uint64_t lb0 = lor_cost[0] + 32ull * nout[0];
     const uint64_t lb1 = lor_cost[1] + 32ull * nout[1];
+    const uint64_t m = lb0 <= lb1 ? lb0 : lb1;
+    const bool better = (double)m * tp.lorenzo_coef < (double)bits_best;
     if (rep) {
       rep->lorenzo_bits[0] = lb0;
       rep->lorenzo_bits[1] = lb1;
-      const uint64_t m = lb0 < lb1 ? lb0 : lb1;
-      rep->lorenzo_better = (double)m * tp.lorenzo_coef < (double)bits_best;
+      rep->lorenzo_better = better;
+    }
+    // Sec. 6.5: the Lorenzo predictor of the order with the smaller
+    // estimate (order 1 on a tie) replaces interpolation when it wins;
+    // block-wise interpolator tuning then has nothing to choose
+    if (better) {
+      out.predictor = lb0 <= lb1 ? 1 : 2;
+      prof.collect();
+      *h_cfg = out;
+      return HPEZ_OK;
     }
   }
 

@@ -38,7 +38,7 @@ class hpez_config(ctypes.Structure):
         ("chunk_syms", ctypes.c_int32),
         ("blockwise", ctypes.c_int32),
         ("block_size", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("predictor", ctypes.c_int32),
         ("alpha", ctypes.c_double),
         ("beta", ctypes.c_double),
         ("md_inv_var", ctypes.c_double * 3),
@@ -438,9 +438,10 @@ def hpez_tune(ctx, d_in: int, shape, eb_mode: int, eb: float,
 def make_config(ndim: int, *, anchor_stride=None, frozen_dim=-1, chunk_syms=16384,
                 alpha=1.0, beta=1.0, md_inv_var=(1, 1, 1), interp=HPEZ_CUBIC_NAK,
                 paradigm=HPEZ_PARADIGM_1D, same_level=0, order=None,
-                blockmap=None, block_size=32) -> hpez_config:
+                blockmap=None, block_size=32, predictor=0) -> hpez_config:
     """Config with one setting for all levels unless per-level lists are
-    given (index l-1); ``order`` may be one order or a per-level list."""
+    given (index l-1); ``order`` may be one order or a per-level list;
+    ``predictor`` 1 or 2 selects the Lorenzo predictor of that order."""
     c = hpez_default_config(ndim)
     if anchor_stride is not None:
         c.anchor_stride = anchor_stride
@@ -470,6 +471,7 @@ def make_config(ndim: int, *, anchor_stride=None, frozen_dim=-1, chunk_syms=1638
             c.order[l][j] = o[j] if j < len(o) else 255
     c.block_size = block_size
     c.blockwise = 0
+    c.predictor = predictor
     c._blockmap_ref = None
     if blockmap is not None:
         bm = np.ascontiguousarray(blockmap, dtype=np.uint8)

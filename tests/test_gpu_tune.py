@@ -39,7 +39,7 @@ def _val(v):
 
 def _compare(g_cfg, g_rep, o_cfg, o_rep):
     for f in ("anchor_stride", "frozen_dim", "chunk_syms", "blockwise",
-              "block_size", "alpha", "beta"):
+              "block_size", "predictor", "alpha", "beta"):
         assert getattr(g_cfg, f) == getattr(o_cfg, f), f
     for f in ("md_inv_var", "interp", "paradigm", "same_level", "order"):
         assert _val(getattr(g_cfg, f)) == _val(getattr(o_cfg, f)), f
