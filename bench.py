@@ -82,6 +82,8 @@ def parse():
                     help="skip the 64-field batched-vs-plain measurement")
     ap.add_argument("--no-served", action="store_true",
                     help="skip the served-form measurement")
+    ap.add_argument("--no-lorenzo", action="store_true",
+                    help="skip the Lorenzo-predictor round trips on the same field")
     ap.add_argument("--no-tune", action="store_true",
                     help="time the default predictor instead of auto-tuning "
                          "(for profiles of that path)")
@@ -338,6 +340,56 @@ def bench_batched(ctx, steps, warmup):
             "speedup_vs_plain": round(plain_ms / batch_ms, 3),
             "launches_per_step": la + lb, "ticks_per_step": ta + tb,
             "graph": True}
+
+
+def bench_lorenzo(ctx, x, shape, eb, cbuf, cap, y, stream, steps, peak):
+    """The same field through the Lorenzo predictor (Sec. 6.5) of order 1
+    and 2, configured directly: round-trip GB/s, compression ratio, and the
+    roofline of the Lorenzo kernels (compress: 4 N bytes of x read, 2 N of
+    codes written; decompress: 2 N of codes read, 4 N written)."""
+    import torch
+    from paper_2311_12133_gb300 import hpez
+    N = x.numel()
+    sptr = stream.cuda_stream
+    res = {}
+    for order in (1, 2):
+        cfg = hpez.make_config(len(shape), predictor=order)
+
+        def st():
+            sz = hpez.hpez_compress(ctx.handle, x.data_ptr(), shape, hpez.HPEZ_EB_REL, eb,
+                                    cfg, cbuf.data_ptr(), cap, sptr)
+            hpez.hpez_decompress(ctx.handle, cbuf.data_ptr(), sz, y.data_ptr(), N, sptr)
+            return sz
+        for _ in range(3):
+            sz = st()
+        torch.cuda.synchronize()
+        hpez.hpez_profile_enable(ctx.handle, True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            sz = st()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        kc, nc = hpez.hpez_profile_get(ctx.handle, hpez.HPEZ_PH_LEVEL)
+        kd, nd = hpez.hpez_profile_get(ctx.handle, hpez.HPEZ_PH_DLEVEL)
+        hpez.hpez_profile_enable(ctx.handle, False)
+        hdr = cbuf[:512].cpu().numpy().tobytes()
+        e_abs = hpez.hpez_inspect(hdr)[2]
+        err = (y.double() - x.double()).abs().max().item()
+        assert err <= e_abs, f"Lorenzo order {order}: bound violated: {err} > {e_abs}"
+        kern = {}
+        for name, (t, n) in (("compress", (kc, nc)), ("decompress", (kd, nd))):
+            if n:
+                gbs = 6 * N / (t / n / 1e3) / 1e9
+                kern[name] = {"launch_ms": round(t / n, 4), "achieved": round(gbs, 1),
+                              "frac": round(gbs / peak, 4), "algorithmic_bytes": 6 * N}
+        res[f"order{order}"] = {"value": round(4 * N / (ms / 1e3) / 1e9, 3), "unit": "GB/s",
+                                "ms_per_step": round(ms, 4),
+                                "compression_ratio": round(4 * N / sz, 3),
+                                "max_abs_err": err, "kernel_roofline": kern}
+    return res
 
 
 def bench_served(ctx, seconds=3.0, rate=200.0, slots=256):
@@ -624,6 +676,11 @@ def main():
                     "compression_ratio": round(4 * N / dsz, 3),
                     "predictor": "cubic not-a-knot, 1D-style order 0,1,2, A=32, no tuning"}
 
+    lorenzo = None
+    if not args.no_lorenzo:
+        lorenzo = bench_lorenzo(ctx, x, shape, args.eb, cbuf, cap, y, stream,
+                                max(3, args.steps // 2), peak)
+
     batched = served = None
     if rank == 0 and world == 1 and not args.no_batched:
         batched = bench_batched(ctx, max(3, args.steps // 2), args.warmup)
@@ -653,7 +710,7 @@ def main():
             "roofline": roofline, "phases": phase_report,
             "gpu_launches": int(launches),
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
-            "default_predictor": default_pred,
+            "default_predictor": default_pred, "lorenzo": lorenzo,
             "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)

@@ -930,8 +930,8 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
     // Sec. 6.5: the Lorenzo predictor over the field, codes into the
     // finest grid's code array
     pf.begin(HPEZ_PH_LEVEL, s);
-    rc = launch_lorenzo(false, cfg.predictor, p.n, p.fst, p.off, p.A, d_in, b.Cg[0],
-                        nullptr, b.ctl, s);
+    rc = launch_lorenzo(false, cfg.predictor, p.n, p.fst, p.off, p.A, ctx->x_aligned16,
+                        d_in, b.Cg[0], nullptr, b.ctl, ctx->num_sms, s);
     pf.end(s);
     if (rc) return rc;
     ++nl;
@@ -1158,8 +1158,8 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
     // are already in place
     if (!lorenzo_supported(p.n, p.fst, p.off, p.A)) return HPEZ_ERR_UNSUPPORTED;
     pf.begin(HPEZ_PH_DLEVEL, s);
-    rc = launch_lorenzo(true, cfg.predictor, p.n, p.fst, p.off, p.A, nullptr, codes,
-                        d_out, ctl, s);
+    rc = launch_lorenzo(true, cfg.predictor, p.n, p.fst, p.off, p.A, ctx->out_aligned16,
+                        nullptr, codes, d_out, ctl, ctx->num_sms, s);
     pf.end(s);
     if (rc) return rc;
     ++nl;

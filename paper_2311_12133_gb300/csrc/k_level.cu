@@ -17,27 +17,6 @@
 
 namespace hpez {
 
-// Exact bound test with a fast accept: rn(r - x) strictly inside the bound
-// implies the exact difference is inside too (rounding is monotonic), so
-// the TwoSum residual is only needed near the bound.
-__device__ __forceinline__ unsigned quantize_fast(float x, float p, float el,
-                                                  float inv2, float twoe,
-                                                  float& recon) {
-  const float diff = __fsub_rn(x, p);
-  const float m = __fadd_rn(__fmul_rn(fabsf(diff), inv2), 0.5f);
-  if (m < 32768.0f) {
-    const int k = __float2int_rz(m);
-    const int q = diff < 0.0f ? -k : k;
-    const float r = __fadd_rn(p, __fmul_rn(__int2float_rn(q), twoe));
-    if (fabsf(__fsub_rn(r, x)) < el || within_bound(r, x, el)) {
-      recon = r;
-      return (unsigned)(q + kRadius);
-    }
-  }
-  recon = x;
-  return 0u;
-}
-
 // ---------------------------------------------------------------------
 // Shared-memory layout of the CTA's region: rows (slot 0, slot 1) of RX2
 // columns in grid order.  Before the passes the region holds the input

@@ -451,25 +451,6 @@ struct StreamCtx {
   float el, inv2, twoe;
 };
 
-// quantize() with the common case decided first: rn(r - x) below the bound
-// in magnitude means |r - x| <= e exactly (the first test of within_bound)
-__device__ __forceinline__ unsigned quantize_fast(float x, float p, float el, float inv2,
-                                                  float twoe, float& recon) {
-  const float diff = __fsub_rn(x, p);
-  const float m = __fadd_rn(__fmul_rn(fabsf(diff), inv2), 0.5f);
-  if (m < 32768.0f) {
-    const int k = __float2int_rz(m);
-    const int q = diff < 0.0f ? -k : k;
-    const float r = __fadd_rn(p, __fmul_rn(__int2float_rn(q), twoe));
-    if (fabsf(__fsub_rn(r, x)) < el || within_bound(r, x, el)) {
-      recon = r;
-      return (unsigned)(q + kRadius);
-    }
-  }
-  recon = x;
-  return 0u;
-}
-
 // quantize (compress) or reconstruct (decompress) one point, keep it in
 // the plane buffer, write the code / reconstruction of an owned point
 template <bool kDecomp, class In>

@@ -6,11 +6,32 @@
 // outside the block reads 0) -- the recurrence the tuner's Lorenzo test
 // runs on its sample blocks.
 //
-// A CTA owns one block with the block's reconstruction in shared memory
-// and runs the recurrence as a wavefront over the planes i0 + i1 + i2 = t:
-// every neighbour a point reads lies on an earlier plane.  A thread owns
-// one (i0, i1) column of the block; the input of its next point (the field
-// value, or the code) is loaded while the current plane is computed.
+// The recurrence is sequential inside a block: point (i0, i1, i2) needs
+// every neighbour (i0 - a, i1 - b, i2 - c), so the points of one wavefront
+// plane i0 + i1 + i2 = t are independent.  A thread owns one (i0, i1)
+// column of a block and walks it along i2 one step per barrier; a column
+// with s = i0 + i1 starts s steps after column (0, 0).  A CTA does not
+// wait for a block to drain: it streams its blocks back to back, column
+// (i0, i1) working on its j-th block at steps P j + s .. P j + s + P - 1
+// (P = the block side along i2), so past the first s steps every column
+// thread has a point at every step.
+//
+// The value a neighbour column wrote for the same i2 is on the ring slot
+// of the step it was written in: column (i0 - a, i1 - b) reaches i2 at
+// step tau - a - b, one slot per step, a ring of more slots than the
+// stencil's reach (4 for order 1, 8 for order 2).  Values for i2 - c, c >
+// 0, were loaded at the thread's previous steps and stay in registers, so
+// a step reads one value per neighbour column from shared memory.  Rows
+// and columns -1, -2 of the ring are zero, the neighbours outside the
+// block; the i2 history is zeroed when a column starts a block.  The
+// input of the next eight steps (the field values, or the codes and the
+// escaped values) is loaded eight steps ahead, one 32-byte sector of a
+// field row per thread.
+//
+// For 32 x 32 columns (3D, A = 32) lane l of warp w owns column (l,
+// (w - l) mod 32): its s is w or w + 32, so every lane of a warp is at the
+// same i2 at every step and the segment work does not diverge; the ring
+// row width 34 keeps the lanes' shared-memory words in distinct banks.
 #include "hpez.h"
 #include "hpez_internal.cuh"
 #include "hpez_launch.h"
@@ -18,117 +39,458 @@
 namespace hpez {
 namespace {
 
+constexpr int kSeg = 8;  // input / output segment along i2
+
 struct LorGeom {
-  uint32_t n[3];    // field extents per slot (padded slots 1)
-  uint32_t st[3];   // field strides
-  uint32_t B[3];    // block side per slot (1 on padded slots)
-  uint32_t nb[3];   // blocks per slot
-  int lim[3];       // stencil reach per slot: the order, 0 on padded slots
+  uint32_t n[3];     // field extents per slot (padded slots 1)
+  uint32_t st[3];    // field strides
+  uint32_t B[3];     // block side per slot (1 on padded slots)
+  uint32_t nb[3];    // blocks per slot
+  uint32_t nblocks;  // nb[0] nb[1] nb[2]
+  uint32_t g[3];     // the grid size in the radix of nb
+  uint32_t W;        // ring row width in floats (B[1] + 2 padded for banks)
+  uint32_t slot;     // floats per ring slot: (B[0] + 2) W
+  int logP;          // log2 B[2]
 };
 
-// per-dimension coefficient of offset a: order 1 (1, -1), order 2
-// (1, -2, 1); a term's weight is minus the product over the three slots
 template <int ORDER>
-__device__ __forceinline__ float lor_coef(int a) {
+__host__ __device__ constexpr int lor_ring() { return ORDER == 1 ? 4 : 8; }
+
+// per-dimension coefficient of offset a: order 1 (1, -1), order 2
+// (1, -2, 1); the weight of term (a, b, c) is minus their product
+template <int ORDER>
+__host__ __device__ constexpr float lor_coef(int a) {
   return ORDER == 1 ? (a == 0 ? 1.0f : -1.0f) : (a == 1 ? -2.0f : 1.0f);
 }
 
-__host__ __device__ __forceinline__ uint32_t lor_row(uint32_t m2) { return m2 + (m2 & 1u); }
+// acc + w v in binary32 for the constant weight w: +-1 as an add or a
+// subtract (w v is exact), otherwise the product rounded, then the sum
+template <int ORDER>
+__device__ __forceinline__ float lor_term(float acc, int a, int b, int c, float v) {
+  const float w = -(lor_coef<ORDER>(a) * lor_coef<ORDER>(b) * lor_coef<ORDER>(c));
+  if (w == 1.0f) return __fadd_rn(acc, v);
+  if (w == -1.0f) return __fsub_rn(acc, v);
+  return __fadd_rn(acc, __fmul_rn(w, v));
+}
 
-template <bool kDecomp, int ORDER>
-__global__ void __launch_bounds__(1024)
-    k_lorenzo(LorGeom G, const float* __restrict__ x, uint16_t* __restrict__ codes,
-              float* __restrict__ out, const Ctl* __restrict__ ctl) {
-  if (ctl->status || ctl->is_const) return;
-  extern __shared__ float R[];
-  unsigned b = blockIdx.x;
-  uint32_t o[3], m[3];
-  for (int d = 2; d >= 0; --d) {
-    const uint32_t j = b % G.nb[d];
-    b /= G.nb[d];
-    o[d] = j * G.B[d];
-    m[d] = min(G.B[d], G.n[d] - o[d]);
-  }
-  const uint32_t m2p = lor_row(m[2]);
-  const float e = ctl->e;
-  const float inv2 = __double2float_rn(__ddiv_rn(1.0, __dmul_rn(2.0, (double)e)));
-  const float twoe = __fmul_rn(2.0f, e);
-  const int q = (int)threadIdx.x;
-  const bool mine = (uint32_t)q < m[0] * m[1];
-  const int i0 = mine ? q / (int)m[1] : 0, i1 = mine ? q - i0 * (int)m[1] : 0;
-  const uint32_t col = (o[0] + (uint32_t)i0) * G.st[0] + (o[1] + (uint32_t)i1) * G.st[1] + o[2];
-  const int T = (int)(m[0] - 1) + (int)(m[1] - 1) + (int)(m[2] - 1);
-  auto load = [&](int t) -> float {
-    const int i2 = t - i0 - i1;
-    if (!mine || i2 < 0 || i2 >= (int)m[2]) return 0.0f;
-    if (kDecomp) return __uint_as_float((uint32_t)codes[col + (uint32_t)i2]);
-    return __ldg(x + col + (uint32_t)i2);
-  };
-  float cur = load(0);
-  for (int t = 0; t <= T; ++t) {
-    const float nxt = t < T ? load(t + 1) : 0.0f;
-    const int i2 = t - i0 - i1;
-    if (mine && i2 >= 0 && i2 < (int)m[2]) {
-      const int base = (i0 * (int)m[1] + i1) * (int)m2p + i2;
-      float acc = 0.0f;
+// A thread's view of one block: the field index of its column's first
+// point and the column's points inside the block (0 when the column lies
+// outside it)
+struct ColGeo {
+  uint32_t col;
+  int m2;
+};
+
+// The blocks a CTA streams, blockIdx.x + j gridDim.x, walked as a mixed-
+// radix counter over (nb[0], nb[1], nb[2]) whose step is the grid size's
+// digits g: no division per block.
+struct Walk {
+  uint32_t b0, b1, b2;
+};
+
+__device__ __forceinline__ Walk walk_start(const LorGeom& G) {
+  uint32_t b = blockIdx.x;
+  Walk w;
+  w.b2 = b % G.nb[2];
+  b /= G.nb[2];
+  w.b1 = b % G.nb[1];
+  w.b0 = b / G.nb[1];
+  return w;
+}
+
+__device__ __forceinline__ void walk_next(const LorGeom& G, Walk& w) {
+  w.b2 += G.g[2];
+  uint32_t c = w.b2 >= G.nb[2] ? 1u : 0u;
+  w.b2 -= c ? G.nb[2] : 0u;
+  w.b1 += G.g[1] + c;
+  c = w.b1 >= G.nb[1] ? 1u : 0u;
+  w.b1 -= c ? G.nb[1] : 0u;
+  w.b0 += G.g[0] + c;
+}
+
+__device__ __forceinline__ ColGeo col_geo(const LorGeom& G, const Walk& w, int i0, int i1) {
+  const uint32_t o0 = w.b0 * G.B[0] + (uint32_t)i0, o1 = w.b1 * G.B[1] + (uint32_t)i1,
+                 o2 = w.b2 * G.B[2];
+  const bool in = o0 < G.n[0] && o1 < G.n[1] && o2 < G.n[2];
+  ColGeo g;
+  g.m2 = in ? (int)min(G.B[2], G.n[2] - o2) : 0;
+  g.col = in ? o0 * G.st[0] + o1 * G.st[1] + o2 : 0u;
+  return g;
+}
+
+// The loads of a segment go straight into the registers that hold it
+// until it is used a segment later: the index is clamped to 0 (an
+// in-bounds read whose values are not used) instead of branching, so no
+// instruction waits on a load at the time it is issued.  They are volatile
+// asm so that the compiler keeps them where they are issued, a segment
+// ahead, rather than moving them next to their first use.
+//   vec: one 32-byte sector (8 floats or 8 codes) per row; the rows start
+//   on 16-byte boundaries.  Otherwise sl <= 8 scalar loads.
+__device__ __forceinline__ float4 ld_f4(const float* p) {
+  float4 v;
+  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_f1(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint4 ld_u4(const uint16_t* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_u16(const uint16_t* p) {
+  unsigned short v;
+  asm volatile("ld.global.nc.u16 %0, [%1];" : "=h"(v) : "l"(p));
+  return (uint32_t)v;
+}
+
+template <bool kVec>
+__device__ __forceinline__ void load_x(float4& a, float4& b, const float* x, const ColGeo& g,
+                                       int i2, int sl) {
+  if (kVec) {
+    const float* p = x + (i2 < g.m2 ? g.col + (uint32_t)i2 : 0u);
+    a = ld_f4(p);
+    b = ld_f4(p + 4);
+  } else {
+    float t[kSeg];
 #pragma unroll
-      for (int a = 0; a <= ORDER; ++a)
-#pragma unroll
-        for (int bb = 0; bb <= ORDER; ++bb)
-#pragma unroll
-          for (int c = 0; c <= ORDER; ++c) {
-            if (a == 0 && bb == 0 && c == 0) continue;
-            if (a > G.lim[0] || bb > G.lim[1] || c > G.lim[2]) continue;
-            const float w = -__fmul_rn(__fmul_rn(lor_coef<ORDER>(a), lor_coef<ORDER>(bb)),
-                                       lor_coef<ORDER>(c));
-            float v = 0.0f;
-            if (a <= i0 && bb <= i1 && c <= i2) v = R[base - (a * (int)m[1] + bb) * (int)m2p - c];
-            acc = __fadd_rn(acc, __fmul_rn(w, v));
-          }
-      const uint32_t fi = col + (uint32_t)i2;
-      float rec;
-      if (!kDecomp) {
-        const unsigned code = quantize(cur, acc, e, inv2, twoe, rec);
-        codes[fi] = (uint16_t)code;
-      } else {
-        const unsigned code = __float_as_uint(cur);
-        rec = code ? dequantize(code, acc, twoe) : out[fi];
-        out[fi] = rec;
-      }
-      R[base] = rec;
-    }
-    __syncthreads();
-    cur = nxt;
+    for (int k = 0; k < kSeg; ++k)
+      t[k] = ld_f1(x + (k < sl && i2 + k < g.m2 ? g.col + (uint32_t)(i2 + k) : 0u));
+    a = make_float4(t[0], t[1], t[2], t[3]);
+    b = make_float4(t[4], t[5], t[6], t[7]);
   }
 }
 
-bool lor_geom(const uint32_t n[3], const uint32_t fst[3], int off, int A, LorGeom& G,
-              size_t& smem, unsigned& threads) {
+// codes of a segment: vec, one 16-byte load (8 codes, two per word);
+// otherwise 8 scalar loads kept unpacked until the segment is promoted
+struct RawCodes {
+  uint32_t w[kSeg];
+};
+
+template <bool kVec>
+__device__ __forceinline__ void load_codes(uint4& v, RawCodes& r, const uint16_t* codes,
+                                           const ColGeo& g, int i2, int sl) {
+  if (kVec) {
+    v = ld_u4(codes + (i2 < g.m2 ? g.col + (uint32_t)i2 : 0u));
+  } else {
+#pragma unroll
+    for (int k = 0; k < kSeg; ++k) {
+      const bool ok = k < sl && i2 + k < g.m2;
+      r.w[k] = ld_u16(codes + (ok ? g.col + (uint32_t)(i2 + k) : 0u));
+      r.w[k] = ok ? r.w[k] : 1u;
+    }
+  }
+}
+
+template <bool kVec>
+__device__ __forceinline__ uint4 pack_codes(const uint4& v, const RawCodes& r) {
+  if (kVec) return v;
+  return make_uint4(r.w[0] | (r.w[1] << 16), r.w[2] | (r.w[3] << 16), r.w[4] | (r.w[5] << 16),
+                    r.w[6] | (r.w[7] << 16));
+}
+
+__device__ __forceinline__ void prefetch_l1(const float* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+template <bool kDecomp, int ORDER, int NDR, bool kVec, bool kSkew>
+__global__ void __launch_bounds__(1024, 1)
+    k_lorenzo(LorGeom G, const float* __restrict__ x, uint16_t* __restrict__ codes,
+              float* __restrict__ out, const Ctl* __restrict__ ctl) {
+  if (ctl->status || ctl->is_const) return;
+  constexpr int RING = lor_ring<ORDER>();
+  constexpr int L0 = NDR >= 3 ? ORDER : 0;  // stencil reach along slot 0
+  constexpr int L1 = NDR >= 2 ? ORDER : 0;  // along slot 1
+  extern __shared__ float ring[];
+  for (uint32_t i = threadIdx.x; i < RING * G.slot; i += blockDim.x) ring[i] = 0.0f;
+
+  const int B1 = (int)G.B[1];
+  const int q = (int)threadIdx.x;
+  const bool real = q < (int)(G.B[0] * G.B[1]);
+  int i0, i1;
+  if (kSkew) {
+    i0 = q & 31;
+    i1 = ((q >> 5) - i0) & 31;
+  } else {
+    i0 = real ? q / B1 : 0;
+    i1 = real ? q - i0 * B1 : 0;
+  }
+  const int P = (int)G.B[2];
+  const int sl = kVec ? kSeg : min(kSeg, P);
+  const uint32_t J = (G.nblocks - 1u - blockIdx.x) / gridDim.x + 1u;
+  const int span = P * (int)J;  // steps a column is busy
+  const int T = span + (int)G.B[0] + B1 - 2;
+  const int W = (int)G.W;
+  float* const mine = ring + (i0 + 2) * W + i1 + 2;
+  const float e = ctl->e;
+  // 1 / (2 e) in double, rounded once: one thread divides (fp64 is slow)
+  __shared__ float s_inv2;
+  if (threadIdx.x == 0) s_inv2 = __double2float_rn(__ddiv_rn(1.0, __dmul_rn(2.0, (double)e)));
+  const float twoe = __fmul_rn(2.0f, e);
+
+  // h[a][b][c - 1]: column (i0 - a, i1 - b) at i2 - c, for c <= HD on the
+  // neighbour columns (the rest is read from the ring: in 3D order 2 the
+  // registers hold one step of history), all c on the own column
+  constexpr int HD = (ORDER == 2 && NDR == 3) ? 1 : ORDER;
+  float h[L0 + 1][L1 + 1][ORDER];
+
+  // input pipeline.  compress: the field values of the next segment (n0,
+  // n1) and of the current one (cv).  decompress: the codes two segments
+  // ahead (cA), of the next segment (cB, whose escaped values are being
+  // prefetched into L1) and of the current one (cc); ov collects the
+  // reconstructions of the segment for one vector store.
+  Walk wk = walk_start(G);
+  ColGeo cg = col_geo(G, wk, i0, i1);
+  ColGeo gB = cg, gA = cg;
+  float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
+  float cv[kSeg];
+  uint4 cA = make_uint4(0u, 0u, 0u, 0u), cB = cA, cc = cA;
+  RawCodes rA;
+  float ov[kSeg];
+  uint32_t pk[kSeg / 2];  // compress: codes of the segment
+#pragma unroll
+  for (int k = 0; k < kSeg; ++k) {
+    cv[k] = ov[k] = 0.0f;
+    rA.w[k] = 1u;
+  }
+#pragma unroll
+  for (int k = 0; k < kSeg / 2; ++k) pk[k] = 0u;
+  if (real) {
+    if (!kDecomp) {
+      load_x<kVec>(n0, n1, x, cg, 0, sl);
+    } else {
+      load_codes<kVec>(cA, rA, codes, gB, 0, sl);
+      cB = pack_codes<kVec>(cA, rA);
+#pragma unroll
+      for (int k = 0; k < kSeg; ++k)
+        if (k < gB.m2 && ((((k & 1) ? (&cB.x)[k / 2] >> 16 : (&cB.x)[k / 2]) & 0xFFFFu) == 0u))
+          prefetch_l1(out + gB.col + (uint32_t)k);
+      if (sl < span) {
+        const int i2a = sl & (P - 1);
+        if (i2a == 0) {
+          walk_next(G, wk);
+          gA = col_geo(G, wk, i0, i1);
+        }
+        load_codes<kVec>(cA, rA, codes, gA, i2a, sl);
+      }
+    }
+  }
+  __syncthreads();
+  const float inv2 = s_inv2;
+
+  int u = -(i0 + i1);  // this column's step within its block stream
+  for (int tau = 0; tau < T; ++tau, ++u) {
+    if (real && u >= 0 && u < span) {
+      const int i2 = u & (P - 1);
+      const int ks = i2 & (sl - 1);
+      if (ks == 0) {
+        if (i2 == 0) {
+#pragma unroll
+          for (int a = 0; a <= L0; ++a)
+#pragma unroll
+            for (int b = 0; b <= L1; ++b)
+#pragma unroll
+              for (int c = 0; c < ORDER; ++c) h[a][b][c] = 0.0f;
+        }
+        if (!kDecomp) {
+          if (i2 == 0) cg = gB;
+          cv[0] = n0.x;
+          cv[1] = n0.y;
+          cv[2] = n0.z;
+          cv[3] = n0.w;
+          cv[4] = n1.x;
+          cv[5] = n1.y;
+          cv[6] = n1.z;
+          cv[7] = n1.w;
+          if (u + sl < span) {
+            const int i2f = (u + sl) & (P - 1);
+            if (i2f == 0) {
+              walk_next(G, wk);
+              gB = col_geo(G, wk, i0, i1);
+            }
+            load_x<kVec>(n0, n1, x, gB, i2f, sl);
+          }
+        } else {
+          if (i2 == 0) cg = gB;
+          cc = cB;
+          if (u + sl < span) {
+            const int i2b = (u + sl) & (P - 1);
+            gB = gA;
+            cB = pack_codes<kVec>(cA, rA);
+#pragma unroll
+            for (int k = 0; k < kSeg; ++k)
+              if (i2b + k < gB.m2 &&
+                  ((((k & 1) ? (&cB.x)[k / 2] >> 16 : (&cB.x)[k / 2]) & 0xFFFFu) == 0u))
+                prefetch_l1(out + gB.col + (uint32_t)(i2b + k));
+            if (u + 2 * sl < span) {
+              const int i2a = (u + 2 * sl) & (P - 1);
+              if (i2a == 0) {
+                walk_next(G, wk);
+                gA = col_geo(G, wk, i0, i1);
+              }
+              load_codes<kVec>(cA, rA, codes, gA, i2a, sl);
+            }
+          }
+        }
+      }
+      const bool act = i2 < cg.m2;
+      float rec = 0.0f;
+      if (act) {
+        // c = 0 values of the neighbour columns, written d = a + b steps ago
+        float v0[L0 + 1][L1 + 1];
+#pragma unroll
+        for (int a = 0; a <= L0; ++a)
+#pragma unroll
+          for (int b = 0; b <= L1; ++b)
+            if (a + b > 0)
+              v0[a][b] = mine[((tau - a - b) & (RING - 1)) * (int)G.slot - a * W - b];
+        float acc = 0.0f;
+#pragma unroll
+        for (int a = 0; a <= L0; ++a)
+#pragma unroll
+          for (int b = 0; b <= L1; ++b)
+#pragma unroll
+            for (int c = 0; c <= ORDER; ++c) {
+              if (a + b + c == 0) continue;
+              float v;
+              if (c == 0)
+                v = v0[a][b];
+              else if (c <= HD || a + b == 0)
+                v = h[a][b][c - 1];
+              else
+                v = i2 >= c ? mine[((tau - a - b - c) & (RING - 1)) * (int)G.slot - a * W - b]
+                            : 0.0f;
+              acc = lor_term<ORDER>(acc, a, b, c, v);
+            }
+        const uint32_t fi = cg.col + (uint32_t)i2;
+        if (!kDecomp) {
+          const unsigned code = quantize_fast(cv[0], acc, e, inv2, twoe, rec);
+          if (kVec) {
+#pragma unroll
+            for (int k = 0; k < kSeg / 2 - 1; ++k) pk[k] = __funnelshift_r(pk[k], pk[k + 1], 16);
+            pk[kSeg / 2 - 1] = (pk[kSeg / 2 - 1] >> 16) | (code << 16);
+            if (ks == kSeg - 1)
+              *reinterpret_cast<uint4*>(codes + fi - (kSeg - 1)) =
+                  make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          } else {
+            codes[fi] = (uint16_t)code;
+          }
+        } else {
+          const unsigned code = cc.x & 0xFFFFu;
+          rec = code ? dequantize(code, acc, twoe) : out[fi];
+          if (!kVec) out[fi] = rec;
+        }
+        mine[(tau & (RING - 1)) * (int)G.slot] = rec;
+        // shift the i2 histories
+#pragma unroll
+        for (int a = 0; a <= L0; ++a)
+#pragma unroll
+          for (int b = 0; b <= L1; ++b) {
+#pragma unroll
+            for (int c = ORDER - 1; c > 0; --c)
+              if (a + b == 0 || c < HD) h[a][b][c] = h[a][b][c - 1];
+            h[a][b][0] = a + b > 0 ? v0[a][b] : rec;
+          }
+      }
+      // advance the segment cursor
+      if (!kDecomp) {
+#pragma unroll
+        for (int k = 0; k < kSeg - 1; ++k) cv[k] = cv[k + 1];
+      } else {
+        cc.x = __funnelshift_r(cc.x, cc.y, 16);
+        cc.y = __funnelshift_r(cc.y, cc.z, 16);
+        cc.z = __funnelshift_r(cc.z, cc.w, 16);
+        cc.w >>= 16;
+        if (kVec) {
+#pragma unroll
+          for (int k = 0; k < kSeg - 1; ++k) ov[k] = ov[k + 1];
+          ov[kSeg - 1] = rec;
+          if (act && ks == kSeg - 1) {
+            float4* o4 = reinterpret_cast<float4*>(out + cg.col + (uint32_t)(i2 - (kSeg - 1)));
+            o4[0] = make_float4(ov[0], ov[1], ov[2], ov[3]);
+            o4[1] = make_float4(ov[4], ov[5], ov[6], ov[7]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+bool lor_geom(const uint32_t n[3], const uint32_t fst[3], int off, int A, int order,
+              LorGeom& G, size_t& smem, unsigned& threads) {
+  uint64_t nbl = 1;
   for (int d = 0; d < 3; ++d) {
     G.n[d] = n[d];
     G.st[d] = fst[d];
     G.B[d] = d < off ? 1u : (uint32_t)A;
     G.nb[d] = (G.n[d] + G.B[d] - 1) / G.B[d];
-    G.lim[d] = 0;
+    nbl *= G.nb[d];
   }
-  const uint64_t pairs = (uint64_t)G.B[0] * G.B[1];
-  smem = (size_t)G.B[0] * G.B[1] * lor_row(G.B[2]) * sizeof(float);
-  if (pairs > 1024 || smem > 200 * 1024) return false;
-  threads = (unsigned)((pairs + 31) / 32 * 32);
+  if (A < 2 || (A & (A - 1)) != 0 || nbl == 0 || nbl > 0x7FFFFFFFull) return false;
+  G.nblocks = (uint32_t)nbl;
+  G.logP = 0;
+  while ((1 << G.logP) < A) ++G.logP;
+  const uint64_t cols = (uint64_t)G.B[0] * G.B[1];
+  G.W = G.B[1] >= 32 ? G.B[1] + 2 : G.B[1] + 32;
+  G.slot = (G.B[0] + 2) * G.W;
+  const int ring = order == 1 ? lor_ring<1>() : lor_ring<2>();
+  smem = (size_t)ring * G.slot * sizeof(float);
+  if (cols > 1024 || smem > 200 * 1024) return false;
+  // the step count P J + B0 + B1 stays far inside int
+  if ((uint64_t)A * nbl + cols > 0x3FFFFFFFull) return false;
+  threads = (unsigned)((cols + 31) / 32 * 32);
   return true;
 }
 
+template <bool kDecomp, int ORDER, int NDR, bool kVec, bool kSkew = false>
+int launch_lor_k(const LorGeom& G, size_t smem, unsigned threads, int num_sms,
+                 const float* x, uint16_t* codes, float* out, const Ctl* ctl,
+                 cudaStream_t s) {
+  auto kern = k_lorenzo<kDecomp, ORDER, NDR, kVec, kSkew>;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)threads, smem) !=
+          cudaSuccess ||
+      per_sm < 1)
+    return HPEZ_ERR_CUDA;
+  // persistent CTAs, the blocks dealt round robin; the grid shrunk to the
+  // fewest CTAs that keep the most loaded one's block count
+  const uint64_t cap = (uint64_t)per_sm * (uint64_t)(num_sms > 0 ? num_sms : 1);
+  uint64_t grid = G.nblocks < cap ? G.nblocks : cap;
+  const uint64_t J = (G.nblocks + grid - 1) / grid;
+  grid = (G.nblocks + J - 1) / J;
+  LorGeom Gk = G;
+  Gk.g[2] = (uint32_t)(grid % G.nb[2]);
+  Gk.g[1] = (uint32_t)(grid / G.nb[2] % G.nb[1]);
+  Gk.g[0] = (uint32_t)(grid / G.nb[2] / G.nb[1]);
+  kern<<<(unsigned)grid, threads, smem, s>>>(Gk, x, codes, out, ctl);
+  return HPEZ_OK;
+}
+
 template <bool kDecomp, int ORDER>
-void launch_lor_k(const LorGeom& G, size_t smem, unsigned threads, const float* x,
-                  uint16_t* codes, float* out, const Ctl* ctl, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_lorenzo<kDecomp, ORDER>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
-  const unsigned nblk = G.nb[0] * G.nb[1] * G.nb[2];
-  k_lorenzo<kDecomp, ORDER><<<nblk, threads, smem, s>>>(G, x, codes, out, ctl);
+int launch_lor_nd(int ndr, bool vec, const LorGeom& G, size_t smem, unsigned threads,
+                  int num_sms, const float* x, uint16_t* codes, float* out, const Ctl* ctl,
+                  cudaStream_t s) {
+  if (ndr == 3 && G.B[0] == 32 && G.B[1] == 32)
+    return vec ? launch_lor_k<kDecomp, ORDER, 3, true, true>(G, smem, threads, num_sms, x, codes, out, ctl, s)
+               : launch_lor_k<kDecomp, ORDER, 3, false, true>(G, smem, threads, num_sms, x, codes, out, ctl, s);
+  if (ndr == 3)
+    return vec ? launch_lor_k<kDecomp, ORDER, 3, true>(G, smem, threads, num_sms, x, codes, out, ctl, s)
+               : launch_lor_k<kDecomp, ORDER, 3, false>(G, smem, threads, num_sms, x, codes, out, ctl, s);
+  if (ndr == 2)
+    return vec ? launch_lor_k<kDecomp, ORDER, 2, true>(G, smem, threads, num_sms, x, codes, out, ctl, s)
+               : launch_lor_k<kDecomp, ORDER, 2, false>(G, smem, threads, num_sms, x, codes, out, ctl, s);
+  return vec ? launch_lor_k<kDecomp, ORDER, 1, true>(G, smem, threads, num_sms, x, codes, out, ctl, s)
+             : launch_lor_k<kDecomp, ORDER, 1, false>(G, smem, threads, num_sms, x, codes, out, ctl, s);
 }
 
 }  // namespace
@@ -137,30 +499,30 @@ bool lorenzo_supported(const uint32_t n[3], const uint32_t fst[3], int off, int 
   LorGeom G;
   size_t smem;
   unsigned threads;
-  return lor_geom(n, fst, off, A, G, smem, threads);
+  return lor_geom(n, fst, off, A, 2, G, smem, threads);
 }
 
 // The Lorenzo pass over the field (slots n, strides fst, off padded slots,
-// block side A): compress (x -> codes) or decompress (codes, the outliers
-// already scattered into out -> out).  Returns HPEZ_ERR_UNSUPPORTED when a
-// block's shared-memory image or its columns do not fit a CTA.
+// block side A): compress (x -> codes) or decompress (codes, the escaped
+// values already scattered into out -> out).  vec: rows start on 16-byte
+// boundaries (n[2] a multiple of 8 and the float buffer 16-byte aligned;
+// taken when A >= 8).
+// Returns HPEZ_ERR_UNSUPPORTED for geometries the kernel does not take.
 int launch_lorenzo(bool decomp, int order, const uint32_t n[3], const uint32_t fst[3],
-                   int off, int A, const float* x, uint16_t* codes, float* out,
-                   const Ctl* ctl, cudaStream_t s) {
+                   int off, int A, bool vec, const float* x, uint16_t* codes, float* out,
+                   const Ctl* ctl, int num_sms, cudaStream_t s) {
   LorGeom G;
   size_t smem;
   unsigned threads;
-  if (!lor_geom(n, fst, off, A, G, smem, threads) || order < 1 || order > 2)
+  if (order < 1 || order > 2 || !lor_geom(n, fst, off, A, order, G, smem, threads))
     return HPEZ_ERR_UNSUPPORTED;
-  for (int d = 0; d < 3; ++d) G.lim[d] = d < off ? 0 : order;
-  if (decomp) {
-    if (order == 1) launch_lor_k<true, 1>(G, smem, threads, x, codes, out, ctl, s);
-    else launch_lor_k<true, 2>(G, smem, threads, x, codes, out, ctl, s);
-  } else {
-    if (order == 1) launch_lor_k<false, 1>(G, smem, threads, x, codes, out, ctl, s);
-    else launch_lor_k<false, 2>(G, smem, threads, x, codes, out, ctl, s);
-  }
-  return HPEZ_OK;
+  vec = vec && (n[2] % kSeg) == 0 && A >= kSeg;
+  const int ndr = 3 - off;
+  if (decomp)
+    return order == 1 ? launch_lor_nd<true, 1>(ndr, vec, G, smem, threads, num_sms, x, codes, out, ctl, s)
+                      : launch_lor_nd<true, 2>(ndr, vec, G, smem, threads, num_sms, x, codes, out, ctl, s);
+  return order == 1 ? launch_lor_nd<false, 1>(ndr, vec, G, smem, threads, num_sms, x, codes, out, ctl, s)
+                    : launch_lor_nd<false, 2>(ndr, vec, G, smem, threads, num_sms, x, codes, out, ctl, s);
 }
 
 }  // namespace hpez

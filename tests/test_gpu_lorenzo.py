@@ -53,7 +53,11 @@ def _check(ctx, oracle, x, eb, mode, **kw):
     ((37, 50, 67), None),      # ragged blocks of side 32 on every axis
     ((64, 64, 64), 16),        # whole blocks, 64 of them
     ((33, 9, 70), 8),          # side-1 tails
+    ((20, 21, 22), 4),         # blocks shorter than an input segment
+    ((9, 10, 11), 2),
+    ((70, 45, 96), None),      # rows of 16-byte segments, ragged in i0 and i1
     ((129, 257), None),        # 2D, ragged blocks of side 64
+    ((96, 200), 64),           # 2D, rows of 16-byte segments
     ((300, 41), 128),          # 2D, one CTA column per block row
     ((5000,), None),           # 1D
     ((5,), 8),                 # 1D, one partial block
