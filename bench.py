@@ -194,23 +194,35 @@ def phase_bytes(name: str, shape, A, comp_size: int) -> int:
     return 0
 
 
-def src_hash():
+# the sources each phase's kernels are built from: a recorded DRAM traffic
+# figure holds while these files are unchanged
+PHASE_SOURCES = {
+    "level1": ("k_level_md3.cu", "hpez_internal.cuh"),
+    "dlevel1": ("k_level_md3.cu", "hpez_internal.cuh"),
+    "decode": ("k_huffman.cu", "hpez_internal.cuh"),
+    "pack": ("k_huffman.cu", "hpez_internal.cuh"),
+    "hist": ("k_huffman.cu", "hpez_internal.cuh"),
+}
+
+
+def src_hash(files):
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2311_12133_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in sorted(files):
+        h.update(f.encode())
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(phase: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken
-    on the current kernel sources; else None."""
+    on the current sources of the phase's kernel; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        d = json.load(open(p))
-        if d.get("src_hash") != src_hash():
+        e = json.load(open(p))["phases"][phase]
+        if e.get("src_hash") != src_hash(PHASE_SOURCES[phase]):
             return None
-        return d.get("phases", {}).get(phase)
+        return e.get("bytes")
     except Exception:
         return None
 
