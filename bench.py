@@ -84,6 +84,8 @@ def parse():
                     help="skip the served-form measurement")
     ap.add_argument("--no-lorenzo", action="store_true",
                     help="skip the Lorenzo-predictor round trips on the same field")
+    ap.add_argument("--predictor", type=int, default=0, choices=[0, 1, 2],
+                    help="time the Lorenzo predictor of this order (no tuning) as the step")
     ap.add_argument("--no-tune", action="store_true",
                     help="time the default predictor instead of auto-tuning "
                          "(for profiles of that path)")
@@ -165,9 +167,11 @@ def grid_sizes(shape, A):
     return out  # out[g]: points of the stride-2^g grid
 
 
-def phase_bytes(name: str, shape, A, comp_size: int) -> int:
+def phase_bytes(name: str, shape, A, comp_size: int, lorenzo: bool = False) -> int:
     import math
     N = math.prod(shape)
+    if lorenzo and name in ("level1", "dlevel1"):
+        return 6 * N  # the Lorenzo pass: x (or codes) in, codes (or values) out
     gs = grid_sizes(shape, A)
     if name == "range":
         return 4 * N
@@ -546,10 +550,12 @@ def main():
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
 
+    step_cfg = hpez.make_config(len(shape), predictor=args.predictor) if args.predictor else None
+
     def compress():
-        if args.no_tune:
+        if args.no_tune or args.predictor:
             return hpez.hpez_compress(ctx.handle, x.data_ptr(), shape, hpez.HPEZ_EB_REL,
-                                      args.eb, None, cbuf.data_ptr(), cap, sptr)
+                                      args.eb, step_cfg, cbuf.data_ptr(), cap, sptr)
         return hpez.hpez_compress_auto(ctx.handle, x.data_ptr(), shape,
                                        hpez.HPEZ_EB_REL, args.eb, None,
                                        cbuf.data_ptr(), cap, sptr)
@@ -619,20 +625,21 @@ def main():
     dom = max(data_phases.items(), key=lambda kv: kv[1][0])
     dom_name, (dom_ms, dom_cnt) = dom
     tune_ms = sum(v[0] for k, v in phases.items() if k.startswith("tune_")) / args.steps
-    dom_bytes = phase_bytes(dom_name, shape, A, size)
+    lor = args.predictor > 0
+    dom_bytes = phase_bytes(dom_name, shape, A, size, lor)
     achieved = dom_bytes / (dom_ms / dom_cnt / 1e3) / 1e9 if dom_bytes else None
     roofline = {"bound": "hbm", "phase": dom_name,
                 "achieved": round(achieved, 1) if achieved else None,
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": round(achieved / peak, 4) if achieved else None,
-                "traffic": ncu_traffic(dom_name),
+                "traffic": None if lor else ncu_traffic(dom_name),
                 "algorithmic_bytes": dom_bytes,
                 "launch_ms": round(dom_ms / dom_cnt, 4),
                 "tuner_ms_per_step": round(tune_ms, 3),
                 "tuner_share": round(tune_ms / ms_per_step, 3)}
     phase_report = {k: {"ms": round(v[0] / v[1], 4), "n": v[1],
-                        "GBps": round(phase_bytes(k, shape, A, size) / (v[0] / v[1] / 1e3) / 1e9, 1)
-                        if phase_bytes(k, shape, A, size) else None}
+                        "GBps": round(phase_bytes(k, shape, A, size, lor) / (v[0] / v[1] / 1e3) / 1e9, 1)
+                        if phase_bytes(k, shape, A, size, lor) else None}
                     for k, v in sorted(phases.items(), key=lambda kv: -kv[1][0])}
 
     # end to end through the host-buffer entry points
@@ -709,6 +716,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": f"grf k^-5/3 float32 {'x'.join(map(str, shape))} per GPU, "
                                    f"rel eb {args.eb}, " + (
+                                       f"Lorenzo predictor order {args.predictor} (no tuning)"
+                                       if args.predictor else
                                        "default predictor (no tuning)" if args.no_tune else
                                        "full auto-tuning + compress (hpez_compress_auto)")
                                    + " + decompress",

@@ -74,8 +74,12 @@ typedef struct {
   int32_t block_size;    /* block side of the map (Sec. 6.6 default 32) */
   int32_t predictor;     /* 0 interpolation; 1, 2: the Lorenzo predictor of
                             that order (Sec. 6.5) on blocks of side
-                            anchor_stride (blocks whose image fits a CTA:
-                            A <= 32 in 3D, 128 in 2D) */
+                            anchor_stride, not with blockwise.  A block's
+                            columns must fit one CTA: A <= 32 in 3D, <= 1024
+                            in 2D, else hpez_compress returns UNSUPPORTED;
+                            the batched and served forms and
+                            hpez_decompress_noalloc take interpolation
+                            streams only (UNSUPPORTED) */
   double alpha, beta;    /* Eq. 15 level bounds, both >= 1 */
   double md_inv_var[3];  /* 1/sigma_d^2 for the Eq. 14 weights, > 0 */
   uint8_t interp[HPEZ_MAX_LEVELS];     /* HPEZ_LINEAR / _CUBIC_NAK / _NAT */
@@ -141,7 +145,8 @@ HPEZ_API int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
  * before any stream capture.  All calls share the one array: calls that
  * overlap on the GPU (other streams, other host threads) race and must be
  * serialized by the caller.  Synchronizes `stream`.
- * Errors: as hpez_decompress, plus HPEZ_ERR_TOO_LARGE. */
+ * Errors: as hpez_decompress, plus HPEZ_ERR_TOO_LARGE, and
+ * HPEZ_ERR_UNSUPPORTED for a Lorenzo-predictor stream. */
 #define HPEZ_NOALLOC_MAX_POINTS 2097152u
 #define HPEZ_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 HPEZ_API int hpez_decompress_noalloc(const void* d_in, uint64_t in_size,
@@ -198,7 +203,8 @@ typedef struct hpez_batch hpez_batch;
 /* Plan n fields (streams) into one batch.  The device pointers are bound
  * to the batch: every run reads and writes the same buffers.  Errors:
  * INVALID_ARG / CORRUPT_STREAM / OUT_TOO_SMALL for the first bad entry,
- * NO_MEMORY, CUDA.  Synchronizes the device once (the uploads). */
+ * UNSUPPORTED (a Lorenzo-predictor config or stream), NO_MEMORY, CUDA.
+ * Synchronizes the device once (the uploads). */
 HPEZ_API int hpez_batch_create_compress(hpez_ctx* ctx, int n,
                                         const hpez_field_desc* fields,
                                         hpez_batch** out);
@@ -256,7 +262,7 @@ HPEZ_API int hpez_server_create(hpez_ctx* ctx, uint64_t budget_bytes,
                                 hpez_server** out);
 /* Queue a request; *id identifies it in hpez_server_poll.  Errors:
  * INVALID_ARG / CORRUPT_STREAM (checked now), TOO_LARGE (it can never fit
- * the budget). */
+ * the budget), UNSUPPORTED (a Lorenzo-predictor config or stream). */
 HPEZ_API int hpez_server_submit(hpez_server* s, const hpez_request* req,
                                 uint64_t* id);
 /* One step: retire, admit, one tick.  Never waits for the GPU except to

@@ -100,7 +100,7 @@ def test_lorenzo_frozen_and_constant(gpu, oracle):
 
 
 def test_lorenzo_unsupported_forms(gpu):
-    """Blocks whose image does not fit a CTA, a block-wise map with the
+    """Blocks whose columns do not fit a CTA, a block-wise map with the
     Lorenzo predictor, and the engine's request paths are refused."""
     import torch
     from paper_2311_12133_gb300 import hpez
@@ -120,6 +120,20 @@ def test_lorenzo_unsupported_forms(gpu):
     with pytest.raises(hpez.HpezError) as e:
         hpez.Batch(gpu, fields=[(x, 1e-3, 1, hpez.make_config(3, predictor=1))])
     assert e.value.code == -8
+    # a Lorenzo stream: the served form refuses it (so does the
+    # no-allocation decompressor, tested with it), hpez_decompress takes it
+    small = torch.rand((40, 40, 40), device="cuda")
+    buf, size = gpu.compress(small, 1e-3, 1, hpez.make_config(3, predictor=1))
+    srv = hpez.Server(gpu, 1 << 28, 4)
+    with pytest.raises(hpez.HpezError) as e:
+        srv.submit_compress(small.cpu().numpy(), 1e-3, 1, hpez.make_config(3, predictor=2))
+    assert e.value.code == -8
+    with pytest.raises(hpez.HpezError) as e:
+        srv.submit_decompress(buf[:size].cpu().numpy(), size)
+    assert e.value.code == -8
+    srv.close()
+    y = gpu.decompress(buf, size)
+    assert (y - small).abs().max().item() <= 1e-3 * (small.max() - small.min()).item()
 
 
 def _lorenzo_field():

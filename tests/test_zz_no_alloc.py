@@ -62,3 +62,16 @@ def test_noalloc_refuses_fields_beyond_its_scratch(ctx):
     ref = ctx.decompress(buf, size)
     got = _noalloc(buf, size, tuple(y.shape))
     assert torch.equal(got, ref)
+
+
+def test_noalloc_refuses_lorenzo_streams(ctx):
+    """A Lorenzo-predictor stream (Sec. 6.5) is hpez_decompress's only."""
+    import torch
+    from paper_2311_12133_gb300 import hpez
+    x = torch.rand((40, 40, 40), device="cuda")
+    buf, size = ctx.compress(x, 1e-3, 1, hpez.make_config(3, predictor=1))
+    out = torch.empty_like(x)
+    with pytest.raises(hpez.HpezError) as e:
+        hpez.hpez_decompress_noalloc(buf.data_ptr(), size, out.data_ptr(), out.numel(),
+                                     torch.cuda.current_stream().cuda_stream)
+    assert e.value.code == -8
