@@ -200,6 +200,64 @@ __device__ __forceinline__ void prefetch_l1(const float* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
+// The prediction of the point at i2 of this column at step tau: the
+// stencil's terms in the order of the offsets (a, b, c); c = 0 from the
+// ring slot written a + b steps ago, c > 0 from the history h (c <= HD on
+// the neighbour columns) or the ring.  v0 receives the c = 0 values.
+template <int ORDER, int L0, int L1, int HD, int RING>
+__device__ __forceinline__ float lor_predict(const float* mine, int tau, int slot, int W, int i2,
+                                             const float (&h)[L0 + 1][L1 + 1][ORDER],
+                                             float (&v0)[L0 + 1][L1 + 1]) {
+#pragma unroll
+  for (int a = 0; a <= L0; ++a)
+#pragma unroll
+    for (int b = 0; b <= L1; ++b)
+      if (a + b > 0) v0[a][b] = mine[((tau - a - b) & (RING - 1)) * slot - a * W - b];
+  float acc = 0.0f;
+#pragma unroll
+  for (int a = 0; a <= L0; ++a)
+#pragma unroll
+    for (int b = 0; b <= L1; ++b)
+#pragma unroll
+      for (int c = 0; c <= ORDER; ++c) {
+        if (a + b + c == 0) continue;
+        float v;
+        if (c == 0)
+          v = v0[a][b];
+        else if (c <= HD || a + b == 0)
+          v = h[a][b][c - 1];
+        else
+          v = i2 >= c ? mine[((tau - a - b - c) & (RING - 1)) * slot - a * W - b] : 0.0f;
+        acc = lor_term<ORDER>(acc, a, b, c, v);
+      }
+  return acc;
+}
+
+// the histories after the point: c = 1 becomes this step's c = 0 value
+template <int ORDER, int L0, int L1, int HD>
+__device__ __forceinline__ void lor_shift(float (&h)[L0 + 1][L1 + 1][ORDER],
+                                          const float (&v0)[L0 + 1][L1 + 1], float rec) {
+#pragma unroll
+  for (int a = 0; a <= L0; ++a)
+#pragma unroll
+    for (int b = 0; b <= L1; ++b) {
+#pragma unroll
+      for (int c = ORDER - 1; c > 0; --c)
+        if (a + b == 0 || c < HD) h[a][b][c] = h[a][b][c - 1];
+      h[a][b][0] = a + b > 0 ? v0[a][b] : rec;
+    }
+}
+
+template <int ORDER, int L0, int L1>
+__device__ __forceinline__ void lor_zero(float (&h)[L0 + 1][L1 + 1][ORDER]) {
+#pragma unroll
+  for (int a = 0; a <= L0; ++a)
+#pragma unroll
+    for (int b = 0; b <= L1; ++b)
+#pragma unroll
+      for (int c = 0; c < ORDER; ++c) h[a][b][c] = 0.0f;
+}
+
 template <bool kDecomp, int ORDER, int NDR, bool kVec, bool kSkew>
 __global__ void __launch_bounds__(1024, 1)
     k_lorenzo(LorGeom G, const float* __restrict__ x, uint16_t* __restrict__ codes,
@@ -291,14 +349,7 @@ __global__ void __launch_bounds__(1024, 1)
       const int i2 = u & (P - 1);
       const int ks = i2 & (sl - 1);
       if (ks == 0) {
-        if (i2 == 0) {
-#pragma unroll
-          for (int a = 0; a <= L0; ++a)
-#pragma unroll
-            for (int b = 0; b <= L1; ++b)
-#pragma unroll
-              for (int c = 0; c < ORDER; ++c) h[a][b][c] = 0.0f;
-        }
+        if (i2 == 0) lor_zero<ORDER, L0, L1>(h);
         if (!kDecomp) {
           if (i2 == 0) cg = gB;
           cv[0] = n0.x;
@@ -343,32 +394,9 @@ __global__ void __launch_bounds__(1024, 1)
       const bool act = i2 < cg.m2;
       float rec = 0.0f;
       if (act) {
-        // c = 0 values of the neighbour columns, written d = a + b steps ago
         float v0[L0 + 1][L1 + 1];
-#pragma unroll
-        for (int a = 0; a <= L0; ++a)
-#pragma unroll
-          for (int b = 0; b <= L1; ++b)
-            if (a + b > 0)
-              v0[a][b] = mine[((tau - a - b) & (RING - 1)) * (int)G.slot - a * W - b];
-        float acc = 0.0f;
-#pragma unroll
-        for (int a = 0; a <= L0; ++a)
-#pragma unroll
-          for (int b = 0; b <= L1; ++b)
-#pragma unroll
-            for (int c = 0; c <= ORDER; ++c) {
-              if (a + b + c == 0) continue;
-              float v;
-              if (c == 0)
-                v = v0[a][b];
-              else if (c <= HD || a + b == 0)
-                v = h[a][b][c - 1];
-              else
-                v = i2 >= c ? mine[((tau - a - b - c) & (RING - 1)) * (int)G.slot - a * W - b]
-                            : 0.0f;
-              acc = lor_term<ORDER>(acc, a, b, c, v);
-            }
+        const float acc =
+            lor_predict<ORDER, L0, L1, HD, RING>(mine, tau, (int)G.slot, W, i2, h, v0);
         const uint32_t fi = cg.col + (uint32_t)i2;
         if (!kDecomp) {
           const unsigned code = quantize_fast(cv[0], acc, e, inv2, twoe, rec);
@@ -388,16 +416,7 @@ __global__ void __launch_bounds__(1024, 1)
           if (!kVec) out[fi] = rec;
         }
         mine[(tau & (RING - 1)) * (int)G.slot] = rec;
-        // shift the i2 histories
-#pragma unroll
-        for (int a = 0; a <= L0; ++a)
-#pragma unroll
-          for (int b = 0; b <= L1; ++b) {
-#pragma unroll
-            for (int c = ORDER - 1; c > 0; --c)
-              if (a + b == 0 || c < HD) h[a][b][c] = h[a][b][c - 1];
-            h[a][b][0] = a + b > 0 ? v0[a][b] : rec;
-          }
+        lor_shift<ORDER, L0, L1, HD>(h, v0, rec);
       }
       // advance the segment cursor
       if (!kDecomp) {
@@ -423,6 +442,8 @@ __global__ void __launch_bounds__(1024, 1)
     __syncthreads();
   }
 }
+
+
 
 bool lor_geom(const uint32_t n[3], const uint32_t fst[3], int off, int A, int order,
               LorGeom& G, size_t& smem, unsigned& threads) {
