@@ -206,6 +206,10 @@ PHASE_SOURCES = {
     "decode": ("k_huffman.cu", "hpez_internal.cuh"),
     "pack": ("k_huffman.cu", "hpez_internal.cuh"),
     "hist": ("k_huffman.cu", "hpez_internal.cuh"),
+    "lorenzo1_c": ("k_lorenzo.cu", "hpez_internal.cuh"),
+    "lorenzo1_d": ("k_lorenzo.cu", "hpez_internal.cuh"),
+    "lorenzo2_c": ("k_lorenzo.cu", "hpez_internal.cuh"),
+    "lorenzo2_d": ("k_lorenzo.cu", "hpez_internal.cuh"),
 }
 
 
@@ -399,8 +403,10 @@ def bench_lorenzo(ctx, x, shape, eb, cbuf, cap, y, stream, steps, peak):
         for name, (t, n) in (("compress", (kc, nc)), ("decompress", (kd, nd))):
             if n:
                 gbs = 6 * N / (t / n / 1e3) / 1e9
+                tr = ncu_traffic(f"lorenzo{order}_{name[0]}") if N == 512 ** 3 else None
                 kern[name] = {"launch_ms": round(t / n, 4), "achieved": round(gbs, 1),
-                              "frac": round(gbs / peak, 4), "algorithmic_bytes": 6 * N}
+                              "frac": round(gbs / peak, 4), "algorithmic_bytes": 6 * N,
+                              "traffic": tr}
         res[f"order{order}"] = {"value": round(4 * N / (ms / 1e3) / 1e9, 3), "unit": "GB/s",
                                 "ms_per_step": round(ms, 4),
                                 "compression_ratio": round(4 * N / sz, 3),
