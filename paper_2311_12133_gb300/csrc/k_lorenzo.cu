@@ -32,6 +32,9 @@
 // (w - l) mod 32): its s is w or w + 32, so every lane of a warp is at the
 // same i2 at every step and the segment work does not diverge; the ring
 // row width 34 keeps the lanes' shared-memory words in distinct banks.
+// Order 1 on rows of 16-byte multiples takes k_lorenzo_tma instead: the
+// input of a warp's 32 columns arrives as one TMA tensor box per segment.
+#include <cuda.h>
 #include "hpez.h"
 #include "hpez_internal.cuh"
 #include "hpez_launch.h"
@@ -198,6 +201,57 @@ __device__ __forceinline__ uint4 pack_codes(const uint4& v, const RawCodes& r) {
 
 __device__ __forceinline__ void prefetch_l1(const float* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// --- TMA tensor boxes and their mbarriers (the box-fed kernel) ---
+constexpr int kWaitLimit = 1 << 24;
+constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+// ends after kWaitNs of wall time or kWaitLimit polls; false: not landed
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (int it = 0; it < kWaitLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+  return false;
+}
+// 3D tiled tensor copy global -> shared, completing on bar
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
 }
 
 // The prediction of the point at i2 of this column at step tau: the
@@ -445,6 +499,227 @@ __global__ void __launch_bounds__(1024, 1)
 
 
 
+// The 3D, A = 32 form fed by TMA.  Warp w owns the columns (w, 0..31) of
+// its CTA's blocks (lane l: i1 = l, so s = w + l) and reads its input from
+// tensor boxes of 8 columns x 32 rows of plane w (segment m of its stream:
+// block m / 4, columns 8 (m mod 4)..+8): one copy per warp and segment
+// instead of a load per row.  Lane l uses segment m at steps w + 8m + l ..
+// +7, so a box lives for 39 steps: the warp keeps kNB boxes in a ring and
+// fetches kLead segments ahead (compress: 6 boxes, the next segment;
+// decompress: 7 boxes of codes, two segments ahead, so that the escaped
+// values of a segment are prefetched into L1 from its landed codes).  At
+// step w + 8m the warp waits for the box it fetched at the previous
+// event and fetches the next into the buffer of segment m + kLead - kNB,
+// which its last lane left two steps before.
+template <bool kDecomp>
+struct LorBox {
+  static constexpr int kNB = kDecomp ? 7 : 6;
+  static constexpr int kLead = kDecomp ? 2 : 1;
+  static constexpr uint32_t kBytes = 32u * kSeg * (kDecomp ? 2u : 4u);
+  static constexpr uint32_t kStride = kBytes;  // 128-byte aligned (tensor copy destinations)
+  static constexpr uint32_t kWarp = kNB * kStride;
+  static_assert(kStride % 128u == 0u, "box buffers must stay 128-byte aligned");
+};
+
+template <bool kDecomp, int ORDER>
+__global__ void __launch_bounds__(1024, 1)
+    k_lorenzo_tma(const __grid_constant__ CUtensorMap tm, LorGeom G, uint16_t* __restrict__ codes,
+                  float* __restrict__ out, Ctl* __restrict__ ctl, uint32_t ring_bytes) {
+  using BX = LorBox<kDecomp>;
+  __shared__ int s_skip;
+  __shared__ float s_inv2;
+  if (threadIdx.x == 0) s_skip = ctl->status || ctl->is_const;
+  __syncthreads();
+  if (s_skip) return;  // read once: another CTA may set the status meanwhile
+  constexpr int RING = lor_ring<ORDER>();
+  constexpr int L0 = ORDER, L1 = ORDER;
+  constexpr int HD = ORDER == 2 ? 1 : ORDER;
+  extern __shared__ __align__(128) unsigned char lsm[];
+  float* const ring = reinterpret_cast<float*>(lsm);
+  for (uint32_t i = threadIdx.x; i < RING * G.slot; i += blockDim.x) ring[i] = 0.0f;
+  const int q = (int)threadIdx.x, lane = q & 31, w = q >> 5;
+  const int i0 = w, i1 = lane, s = i0 + i1;
+  unsigned char* const boxes = lsm + ring_bytes + (uint32_t)w * BX::kWarp;
+  uint64_t* const bar = reinterpret_cast<uint64_t*>(lsm + ring_bytes + 32u * BX::kWarp) + w;
+  if (lane == 0) mbar_init(bar);
+  const uint32_t J = (G.nblocks - 1u - blockIdx.x) / gridDim.x + 1u;
+  const int span = 32 * (int)J, nseg = 4 * (int)J;
+  const int T = span + 62;
+  const int W = (int)G.W;
+  float* const mine = ring + (i0 + 2) * W + i1 + 2;
+  const float e = ctl->e;
+  if (threadIdx.x == 0) s_inv2 = __double2float_rn(__ddiv_rn(1.0, __dmul_rn(2.0, (double)e)));
+  const float twoe = __fmul_rn(2.0f, e);
+  __syncthreads();
+  const float inv2 = s_inv2;
+
+  // the warp's box walk (block of the next segment to fetch) and the
+  // lane's own walk (block of its current point)
+  Walk wb = walk_start(G), wl = wb;
+  ColGeo cg = col_geo(G, wl, i0, i1);
+  int nf = 0;        // segments fetched by this warp
+  uint32_t nw = 0;   // fetches waited for
+  bool fail = false;
+  auto fetch = [&]() {  // warp-uniform: the next segment nf into its buffer
+    if (nf >= nseg) return false;
+    if (nf > 0 && (nf & 3) == 0) walk_next(G, wb);
+    if (lane == 0) {
+      unsigned char* dst = boxes + (uint32_t)(nf % BX::kNB) * BX::kStride;
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      mbar_expect_tx(bar, BX::kBytes);
+      tma_load_3d(dst, &tm, bar, (int)(wb.b2 * 32u) + 8 * (nf & 3), (int)(wb.b1 * 32u),
+                  (int)(wb.b0 * 32u) + w);
+    }
+    ++nf;
+    return true;
+  };
+  // decompress: L1 prefetch of the escaped values of segment m (called
+  // for m = 0, 1, 2, ... in order; we / ge: the block of segment m)
+  Walk we = wb;
+  ColGeo ge = cg;
+  auto escapes = [&](int m) {
+    if (m >= nseg) return;
+    if (m > 0 && (m & 3) == 0) {
+      walk_next(G, we);
+      ge = col_geo(G, we, i0, i1);
+    }
+    const uint4 v = *reinterpret_cast<const uint4*>(
+        boxes + (uint32_t)(m % BX::kNB) * BX::kStride + (uint32_t)lane * 16u);
+    const uint32_t wd[4] = {v.x, v.y, v.z, v.w};
+    const ColGeo& g = ge;
+    const int c0 = 8 * (m & 3);
+#pragma unroll
+    for (int k = 0; k < kSeg; ++k)
+      if (((wd[k >> 1] >> (16 * (k & 1))) & 0xFFFFu) == 0u && c0 + k < g.m2)
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(out + g.col + (uint32_t)(c0 + k)));
+  };
+  if (fetch()) {
+    if (kDecomp) {
+      fail = !mbar_wait(bar, nw & 1u);
+      ++nw;
+      if (!fail) {
+        escapes(0);
+        fetch();
+      }
+    }
+  }
+  float h[L0 + 1][L1 + 1][ORDER];
+  float ov[kSeg];
+  uint32_t pk[kSeg / 2];
+#pragma unroll
+  for (int k = 0; k < kSeg; ++k) ov[k] = 0.0f;
+#pragma unroll
+  for (int k = 0; k < kSeg / 2; ++k) pk[k] = 0u;
+
+  int u = -s;
+  for (int tau = 0; tau < T; ++tau, ++u) {
+    const int ev = tau - w;  // lane 0's stream position
+    if (!fail && ev >= 0 && (ev & (kSeg - 1)) == 0) {
+      const int m = ev >> 3;  // lane 0 starts segment m now
+      // the fetch of the previous event (or the prologue) must have landed
+      if (m + BX::kLead - 1 < nseg) {
+        fail = !mbar_wait(bar, nw & 1u);
+        ++nw;
+      }
+      if (!fail) {
+        if (kDecomp) escapes(m + 1);
+        fetch();
+      }
+    }
+    if (!fail && u >= 0 && u < span) {
+      const int i2 = u & 31, ks = i2 & (kSeg - 1);
+      if (i2 == 0) {
+        if (u > 0) walk_next(G, wl);
+        cg = col_geo(G, wl, i0, i1);
+        lor_zero<ORDER, L0, L1>(h);
+      }
+      const int m = u >> 3;
+      const unsigned char* bp =
+          boxes + (uint32_t)(m % BX::kNB) * BX::kStride + (uint32_t)lane * (BX::kBytes / 32u);
+      const bool act = i2 < cg.m2;
+      float rec = 0.0f;
+      if (act) {
+        float v0[L0 + 1][L1 + 1];
+        const float acc =
+            lor_predict<ORDER, L0, L1, HD, RING>(mine, tau, (int)G.slot, W, i2, h, v0);
+        const uint32_t fi = cg.col + (uint32_t)i2;
+        if (!kDecomp) {
+          const float xv = reinterpret_cast<const float*>(bp)[ks];
+          const unsigned code = quantize_fast(xv, acc, e, inv2, twoe, rec);
+#pragma unroll
+          for (int k = 0; k < kSeg / 2 - 1; ++k) pk[k] = __funnelshift_r(pk[k], pk[k + 1], 16);
+          pk[kSeg / 2 - 1] = (pk[kSeg / 2 - 1] >> 16) | (code << 16);
+          if (ks == kSeg - 1)
+            *reinterpret_cast<uint4*>(codes + fi - (kSeg - 1)) =
+                make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        } else {
+          const unsigned code = reinterpret_cast<const uint16_t*>(bp)[ks];
+          rec = code ? dequantize(code, acc, twoe) : out[fi];
+        }
+        mine[(tau & (RING - 1)) * (int)G.slot] = rec;
+        lor_shift<ORDER, L0, L1, HD>(h, v0, rec);
+      }
+      if (kDecomp) {
+#pragma unroll
+        for (int k = 0; k < kSeg - 1; ++k) ov[k] = ov[k + 1];
+        ov[kSeg - 1] = rec;
+        if (act && ks == kSeg - 1) {
+          float4* o4 = reinterpret_cast<float4*>(out + cg.col + (uint32_t)(i2 - (kSeg - 1)));
+          o4[0] = make_float4(ov[0], ov[1], ov[2], ov[3]);
+          o4[1] = make_float4(ov[4], ov[5], ov[6], ov[7]);
+        }
+      }
+    }
+    if (__syncthreads_or(fail)) break;
+  }
+  if (__syncthreads_or(fail)) {
+    // a box did not land: record it, then wait (bounded) for this warp's
+    // fetch still in flight before leaving
+    if (threadIdx.x == 0) atomicCAS(&ctl->status, 0, ST_TIMEOUT);
+    if (fail)
+      mbar_wait(bar, (nw - 1u) & 1u);
+    else if ((uint32_t)nf > nw)
+      mbar_wait(bar, nw & 1u);
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// the field (or its codes) as a 3D tensor, slot 2 fastest, boxes of 8
+// columns x 32 rows x 1 plane; out-of-range box elements read 0
+bool lor_map(CUtensorMap* map, const void* base, bool u16, const uint32_t n[3]) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t es = u16 ? 2 : 4;
+  const cuuint64_t dim[3] = {n[2], n[1], n[0]};
+  const cuuint64_t stride[2] = {n[2] * es, (cuuint64_t)n[1] * n[2] * es};
+  const cuuint32_t box[3] = {(cuuint32_t)kSeg, 32, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, u16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+            const_cast<void*>(base), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool lor_geom(const uint32_t n[3], const uint32_t fst[3], int off, int A, int order,
               LorGeom& G, size_t& smem, unsigned& threads) {
   uint64_t nbl = 1;
@@ -497,10 +772,50 @@ int launch_lor_k(const LorGeom& G, size_t smem, unsigned threads, int num_sms,
   return HPEZ_OK;
 }
 
+// The box-fed kernel when its shared memory fits and the tensor map can be
+// made; 1: launched, 0: not taken (use the register-fed kernel), < 0: error.
+template <bool kDecomp, int ORDER>
+int launch_lor_tma(const LorGeom& G, int num_sms, const float* x, uint16_t* codes, float* out,
+                   Ctl* ctl, cudaStream_t s) {
+  using BX = LorBox<kDecomp>;
+  auto kern = k_lorenzo_tma<kDecomp, ORDER>;
+  const uint32_t ring_bytes =
+      (uint32_t)(((size_t)lor_ring<ORDER>() * G.slot * sizeof(float) + 127) / 128 * 128);
+  const size_t smem = ring_bytes + 32u * BX::kWarp + 32u * sizeof(uint64_t);
+  if (smem > 220u * 1024u) return 0;
+  CUtensorMap tm;
+  if (!lor_map(&tm, kDecomp ? static_cast<const void*>(codes) : static_cast<const void*>(x),
+               kDecomp, G.n))
+    return 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return HPEZ_ERR_CUDA;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 1024, smem) != cudaSuccess ||
+      per_sm < 1)
+    return HPEZ_ERR_CUDA;
+  const uint64_t cap = (uint64_t)per_sm * (uint64_t)(num_sms > 0 ? num_sms : 1);
+  uint64_t grid = G.nblocks < cap ? G.nblocks : cap;
+  const uint64_t J = (G.nblocks + grid - 1) / grid;
+  grid = (G.nblocks + J - 1) / J;
+  LorGeom Gk = G;
+  Gk.g[2] = (uint32_t)(grid % G.nb[2]);
+  Gk.g[1] = (uint32_t)(grid / G.nb[2] % G.nb[1]);
+  Gk.g[0] = (uint32_t)(grid / G.nb[2] / G.nb[1]);
+  kern<<<(unsigned)grid, 1024, smem, s>>>(tm, Gk, codes, out, ctl, ring_bytes);
+  return 1;
+}
+
 template <bool kDecomp, int ORDER>
 int launch_lor_nd(int ndr, bool vec, const LorGeom& G, size_t smem, unsigned threads,
                   int num_sms, const float* x, uint16_t* codes, float* out, const Ctl* ctl,
                   cudaStream_t s) {
+  // order 1 takes the box-fed kernel (order 2: no faster measured, and the
+  // compressor's shared memory would not fit)
+  if (ORDER == 1 && ndr == 3 && G.B[0] == 32 && G.B[1] == 32 && vec) {
+    const int r = launch_lor_tma<kDecomp, ORDER>(G, num_sms, x, codes, out, const_cast<Ctl*>(ctl), s);
+    if (r != 0) return r < 0 ? r : HPEZ_OK;
+  }
   if (ndr == 3 && G.B[0] == 32 && G.B[1] == 32)
     return vec ? launch_lor_k<kDecomp, ORDER, 3, true, true>(G, smem, threads, num_sms, x, codes, out, ctl, s)
                : launch_lor_k<kDecomp, ORDER, 3, false, true>(G, smem, threads, num_sms, x, codes, out, ctl, s);
