@@ -541,6 +541,11 @@ __global__ void __launch_bounds__(1024, 1)
   const int i0 = w, i1 = lane, s = i0 + i1;
   unsigned char* const boxes = lsm + ring_bytes + (uint32_t)w * BX::kWarp;
   uint64_t* const bar = reinterpret_cast<uint64_t*>(lsm + ring_bytes + 32u * BX::kWarp) + w;
+  // the warp's last two blocks: field index of (o0, o1, o2) and the
+  // extents m0, m1, m2, written when the warp fetches a block's first box
+  // (a lane reaches that block at least 8 steps later, and the entry is
+  // rewritten only after every lane has left the block)
+  __shared__ uint4 s_blk[32][2];
   if (lane == 0) mbar_init(bar);
   const uint32_t J = (G.nblocks - 1u - blockIdx.x) / gridDim.x + 1u;
   const int span = 32 * (int)J, nseg = 4 * (int)J;
@@ -553,16 +558,24 @@ __global__ void __launch_bounds__(1024, 1)
   __syncthreads();
   const float inv2 = s_inv2;
 
-  // the warp's box walk (block of the next segment to fetch) and the
-  // lane's own walk (block of its current point)
-  Walk wb = walk_start(G), wl = wb;
-  ColGeo cg = col_geo(G, wl, i0, i1);
+  // the warp's box walk (block of the next segment to fetch)
+  Walk wb = walk_start(G);
+  const uint32_t lane_off = (uint32_t)i0 * G.st[0] + (uint32_t)i1 * G.st[1];
+  ColGeo cg;
+  cg.col = 0u;
+  cg.m2 = 0;
   int nf = 0;        // segments fetched by this warp
   uint32_t nw = 0;   // fetches waited for
   bool fail = false;
   auto fetch = [&]() {  // warp-uniform: the next segment nf into its buffer
     if (nf >= nseg) return false;
     if (nf > 0 && (nf & 3) == 0) walk_next(G, wb);
+    if (lane == 0 && (nf & 3) == 0) {
+      const uint32_t o0 = wb.b0 * 32u, o1 = wb.b1 * 32u, o2 = wb.b2 * 32u;
+      s_blk[w][(nf >> 2) & 1] =
+          make_uint4(o0 * G.st[0] + o1 * G.st[1] + o2, min(32u, G.n[0] - o0),
+                     min(32u, G.n[1] - o1), min(32u, G.n[2] - o2));
+    }
     if (lane == 0) {
       unsigned char* dst = boxes + (uint32_t)(nf % BX::kNB) * BX::kStride;
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -573,20 +586,23 @@ __global__ void __launch_bounds__(1024, 1)
     ++nf;
     return true;
   };
-  // decompress: L1 prefetch of the escaped values of segment m (called
-  // for m = 0, 1, 2, ... in order; we / ge: the block of segment m)
-  Walk we = wb;
-  ColGeo ge = cg;
+  // this lane's column in the block of table entry t
+  auto geo_of = [&](int t) {
+    __syncwarp();
+    const uint4 b = s_blk[w][t];
+    ColGeo g;
+    const bool in = (uint32_t)i0 < b.y && (uint32_t)i1 < b.z;
+    g.m2 = in ? (int)b.w : 0;
+    g.col = b.x + lane_off;
+    return g;
+  };
+  // decompress: L1 prefetch of the escaped values of segment m (landed)
   auto escapes = [&](int m) {
     if (m >= nseg) return;
-    if (m > 0 && (m & 3) == 0) {
-      walk_next(G, we);
-      ge = col_geo(G, we, i0, i1);
-    }
     const uint4 v = *reinterpret_cast<const uint4*>(
         boxes + (uint32_t)(m % BX::kNB) * BX::kStride + (uint32_t)lane * 16u);
     const uint32_t wd[4] = {v.x, v.y, v.z, v.w};
-    const ColGeo& g = ge;
+    const ColGeo g = geo_of((m >> 2) & 1);
     const int c0 = 8 * (m & 3);
 #pragma unroll
     for (int k = 0; k < kSeg; ++k)
@@ -612,6 +628,7 @@ __global__ void __launch_bounds__(1024, 1)
   for (int k = 0; k < kSeg / 2; ++k) pk[k] = 0u;
 
   int u = -s;
+  int bi = 0;  // this lane's box buffer (its segment mod kNB)
   for (int tau = 0; tau < T; ++tau, ++u) {
     const int ev = tau - w;  // lane 0's stream position
     if (!fail && ev >= 0 && (ev & (kSeg - 1)) == 0) {
@@ -628,14 +645,16 @@ __global__ void __launch_bounds__(1024, 1)
     }
     if (!fail && u >= 0 && u < span) {
       const int i2 = u & 31, ks = i2 & (kSeg - 1);
+      if (ks == 0 && u > 0) bi = bi + 1 == BX::kNB ? 0 : bi + 1;
       if (i2 == 0) {
-        if (u > 0) walk_next(G, wl);
-        cg = col_geo(G, wl, i0, i1);
+        const uint4 b = s_blk[w][(u >> 5) & 1];
+        const bool in = (uint32_t)i0 < b.y && (uint32_t)i1 < b.z;
+        cg.m2 = in ? (int)b.w : 0;
+        cg.col = b.x + lane_off;
         lor_zero<ORDER, L0, L1>(h);
       }
-      const int m = u >> 3;
       const unsigned char* bp =
-          boxes + (uint32_t)(m % BX::kNB) * BX::kStride + (uint32_t)lane * (BX::kBytes / 32u);
+          boxes + (uint32_t)bi * BX::kStride + (uint32_t)lane * (BX::kBytes / 32u);
       const bool act = i2 < cg.m2;
       float rec = 0.0f;
       if (act) {
