@@ -385,9 +385,11 @@ HPEZ_API int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim,
  *                         multiple of 8 points); 0: two launches
  *  HPEZ_OPT_DROP_COPY     0 (default); n > 0: a test of the bounded device
  *                         waits -- the first CTA of the streamed level kernel
- *                         leaves out the copies of its n-th plane, its wait for
- *                         them expires and the call returns HPEZ_ERR_TIMEOUT
- *                         (no copy stays in flight; the context stays usable)
+ *                         leaves out the copies of its n-th plane (of the
+ *                         Lorenzo box-fed kernel: its first warp's n-th box),
+ *                         its wait for them expires and the call returns
+ *                         HPEZ_ERR_TIMEOUT (no copy stays in flight; the
+ *                         context stays usable)
  * Errors: INVALID_ARG for an unknown option or an out-of-range value. */
 #define HPEZ_OPT_FUSED_LEVELS 1
 #define HPEZ_OPT_TILE_E0 2

@@ -931,7 +931,7 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
     // finest grid's code array
     pf.begin(HPEZ_PH_LEVEL, s);
     rc = launch_lorenzo(false, cfg.predictor, p.n, p.fst, p.off, p.A, ctx->x_aligned16,
-                        d_in, b.Cg[0], nullptr, b.ctl, ctx->num_sms, s);
+                        d_in, b.Cg[0], nullptr, b.ctl, ctx->num_sms, ctx->drop_copy, s);
     pf.end(s);
     if (rc) return rc;
     ++nl;
@@ -1159,7 +1159,7 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
     if (!lorenzo_supported(p.n, p.fst, p.off, p.A)) return HPEZ_ERR_UNSUPPORTED;
     pf.begin(HPEZ_PH_DLEVEL, s);
     rc = launch_lorenzo(true, cfg.predictor, p.n, p.fst, p.off, p.A, ctx->out_aligned16,
-                        nullptr, codes, d_out, ctl, ctx->num_sms, s);
+                        nullptr, codes, d_out, ctl, ctx->num_sms, ctx->drop_copy, s);
     pf.end(s);
     if (rc) return rc;
     ++nl;

@@ -58,7 +58,7 @@ int launch_level_md3s(bool decomp, int kind, const LevelMD& P, const SweepBufs& 
 bool lorenzo_supported(const uint32_t n[3], const uint32_t fst[3], int off, int A);
 int launch_lorenzo(bool decomp, int order, const uint32_t n[3], const uint32_t fst[3],
                    int off, int A, bool vec, const float* x, uint16_t* codes, float* out,
-                   const Ctl* ctl, int num_sms, cudaStream_t s);
+                   const Ctl* ctl, int num_sms, int drop_copy, cudaStream_t s);
 
 // k_huffman.cu
 void launch_hist(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,

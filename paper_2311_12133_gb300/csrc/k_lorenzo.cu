@@ -524,7 +524,8 @@ struct LorBox {
 template <bool kDecomp, int ORDER>
 __global__ void __launch_bounds__(1024, 1)
     k_lorenzo_tma(const __grid_constant__ CUtensorMap tm, LorGeom G, uint16_t* __restrict__ codes,
-                  float* __restrict__ out, Ctl* __restrict__ ctl, uint32_t ring_bytes) {
+                  float* __restrict__ out, Ctl* __restrict__ ctl, uint32_t ring_bytes,
+                  int drop) {
   using BX = LorBox<kDecomp>;
   __shared__ int s_skip;
   __shared__ float s_inv2;
@@ -576,7 +577,9 @@ __global__ void __launch_bounds__(1024, 1)
           make_uint4(o0 * G.st[0] + o1 * G.st[1] + o2, min(32u, G.n[0] - o0),
                      min(32u, G.n[1] - o1), min(32u, G.n[2] - o2));
     }
-    if (lane == 0) {
+    // drop > 0 (a test of the bounded waits): warp 0 of CTA 0 leaves out its
+    // fetch drop - 1, whose wait then expires
+    if (lane == 0 && !(drop > 0 && blockIdx.x == 0 && w == 0 && nf + 1 == drop)) {
       unsigned char* dst = boxes + (uint32_t)(nf % BX::kNB) * BX::kStride;
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       mbar_expect_tx(bar, BX::kBytes);
@@ -795,7 +798,7 @@ int launch_lor_k(const LorGeom& G, size_t smem, unsigned threads, int num_sms,
 // made; 1: launched, 0: not taken (use the register-fed kernel), < 0: error.
 template <bool kDecomp, int ORDER>
 int launch_lor_tma(const LorGeom& G, int num_sms, const float* x, uint16_t* codes, float* out,
-                   Ctl* ctl, cudaStream_t s) {
+                   Ctl* ctl, int drop, cudaStream_t s) {
   using BX = LorBox<kDecomp>;
   auto kern = k_lorenzo_tma<kDecomp, ORDER>;
   const uint32_t ring_bytes =
@@ -821,18 +824,19 @@ int launch_lor_tma(const LorGeom& G, int num_sms, const float* x, uint16_t* code
   Gk.g[2] = (uint32_t)(grid % G.nb[2]);
   Gk.g[1] = (uint32_t)(grid / G.nb[2] % G.nb[1]);
   Gk.g[0] = (uint32_t)(grid / G.nb[2] / G.nb[1]);
-  kern<<<(unsigned)grid, 1024, smem, s>>>(tm, Gk, codes, out, ctl, ring_bytes);
+  kern<<<(unsigned)grid, 1024, smem, s>>>(tm, Gk, codes, out, ctl, ring_bytes, drop);
   return 1;
 }
 
 template <bool kDecomp, int ORDER>
 int launch_lor_nd(int ndr, bool vec, const LorGeom& G, size_t smem, unsigned threads,
                   int num_sms, const float* x, uint16_t* codes, float* out, const Ctl* ctl,
-                  cudaStream_t s) {
+                  int drop, cudaStream_t s) {
   // order 1 takes the box-fed kernel (order 2: no faster measured, and the
   // compressor's shared memory would not fit)
   if (ORDER == 1 && ndr == 3 && G.B[0] == 32 && G.B[1] == 32 && vec) {
-    const int r = launch_lor_tma<kDecomp, ORDER>(G, num_sms, x, codes, out, const_cast<Ctl*>(ctl), s);
+    const int r =
+        launch_lor_tma<kDecomp, ORDER>(G, num_sms, x, codes, out, const_cast<Ctl*>(ctl), drop, s);
     if (r != 0) return r < 0 ? r : HPEZ_OK;
   }
   if (ndr == 3 && G.B[0] == 32 && G.B[1] == 32)
@@ -862,10 +866,11 @@ bool lorenzo_supported(const uint32_t n[3], const uint32_t fst[3], int off, int 
 // values already scattered into out -> out).  vec: rows start on 16-byte
 // boundaries (n[2] a multiple of 8 and the float buffer 16-byte aligned;
 // taken when A >= 8).
-// Returns HPEZ_ERR_UNSUPPORTED for geometries the kernel does not take.
+// drop_copy: see HPEZ_OPT_DROP_COPY (0 in normal use).  Returns
+// HPEZ_ERR_UNSUPPORTED for geometries the kernel does not take.
 int launch_lorenzo(bool decomp, int order, const uint32_t n[3], const uint32_t fst[3],
                    int off, int A, bool vec, const float* x, uint16_t* codes, float* out,
-                   const Ctl* ctl, int num_sms, cudaStream_t s) {
+                   const Ctl* ctl, int num_sms, int drop_copy, cudaStream_t s) {
   LorGeom G;
   size_t smem;
   unsigned threads;
@@ -874,10 +879,10 @@ int launch_lorenzo(bool decomp, int order, const uint32_t n[3], const uint32_t f
   vec = vec && (n[2] % kSeg) == 0 && A >= kSeg;
   const int ndr = 3 - off;
   if (decomp)
-    return order == 1 ? launch_lor_nd<true, 1>(ndr, vec, G, smem, threads, num_sms, x, codes, out, ctl, s)
-                      : launch_lor_nd<true, 2>(ndr, vec, G, smem, threads, num_sms, x, codes, out, ctl, s);
-  return order == 1 ? launch_lor_nd<false, 1>(ndr, vec, G, smem, threads, num_sms, x, codes, out, ctl, s)
-                    : launch_lor_nd<false, 2>(ndr, vec, G, smem, threads, num_sms, x, codes, out, ctl, s);
+    return order == 1 ? launch_lor_nd<true, 1>(ndr, vec, G, smem, threads, num_sms, x, codes, out, ctl, drop_copy, s)
+                      : launch_lor_nd<true, 2>(ndr, vec, G, smem, threads, num_sms, x, codes, out, ctl, drop_copy, s);
+  return order == 1 ? launch_lor_nd<false, 1>(ndr, vec, G, smem, threads, num_sms, x, codes, out, ctl, drop_copy, s)
+                    : launch_lor_nd<false, 2>(ndr, vec, G, smem, threads, num_sms, x, codes, out, ctl, drop_copy, s);
 }
 
 }  // namespace hpez

@@ -170,3 +170,32 @@ def test_tune_selects_lorenzo(gpu, oracle):
     g2, r2 = gpu.tune(xd, 1e-3, 1, hpez.hpez_default_tune_params(lorenzo_coef=1e6))
     o2, q2 = oracle.tune(x, 1e-3, oracle.EB_REL, oracle.default_tune_params(lorenzo_coef=1e6))
     assert g2.predictor == o2.predictor == 0 and r2.lorenzo_better == q2.lorenzo_better == 0
+
+
+def test_lorenzo_bounded_wait_expires(gpu, oracle):
+    """The box-fed Lorenzo kernel's waits are bounded: on request the first
+    warp of the first CTA leaves out one box (the prologue's, or a later
+    one), its wait expires, compress and decompress return HPEZ_ERR_TIMEOUT
+    within seconds, and the next calls on the context are exact."""
+    import time
+    import torch
+    from paper_2311_12133_gb300 import fields, hpez
+    x = fields.grf((64, 64, 64), seed=8)
+    xd = torch.from_numpy(x).cuda()
+    cfg = hpez.make_config(3, predictor=1)
+    buf, size = gpu.compress(xd, 1e-3, 1, cfg)
+    try:
+        for item in (1, 3):
+            hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_DROP_COPY, item)
+            t0 = time.time()
+            with pytest.raises(hpez.HpezError) as e:
+                gpu.compress(xd, 1e-3, 1, cfg)
+            assert e.value.code == -9
+            with pytest.raises(hpez.HpezError) as e:
+                gpu.decompress(buf, size)
+            assert e.value.code == -9
+            assert time.time() - t0 < 60
+    finally:
+        hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_DROP_COPY, 0)
+    _check(gpu, oracle, x, 1e-3, 1, predictor=1)
+
