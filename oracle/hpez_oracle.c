@@ -212,8 +212,12 @@ static int check_config(const geom* g, const ora_config* c) {
   if (c->predictor < 0 || c->predictor > 2 || (c->predictor && c->blockwise))
     return ORA_ERR_INVALID_ARG;
   for (int l = 0; l < g->L; ++l) {
-    if (c->interp[l] > ORA_CUBIC_NAT || c->paradigm[l] > ORA_MD ||
+    if (c->interp[l] > ORA_SPLINE_GLOBAL || c->paradigm[l] > ORA_MD ||
         c->same_level[l] > 1)
+      return ORA_ERR_INVALID_ARG;
+    /* the global spline runs along whole lines: one direction per pass */
+    if (c->interp[l] == ORA_SPLINE_GLOBAL &&
+        (c->paradigm[l] != ORA_1D || c->same_level[l] || c->blockwise))
       return ORA_ERR_INVALID_ARG;
     /* the 1D-style order lists each interpolation dimension exactly once */
     int seen[3] = {0, 0, 0};
@@ -441,11 +445,11 @@ static void point_cfg(const sweep* w, int l, const uint64_t c[3], int* kind,
     uint8_t v = w->c->blockmap[b];
     *kind = v & 3;
     *same = (v >> 2) & 1;
+    if (*kind > ORA_CUBIC_NAT) *kind = ORA_CUBIC_NAT;
   } else {
     *kind = w->c->interp[l - 1];
     *same = w->c->same_level[l - 1];
   }
-  if (*kind > ORA_CUBIC_NAT) *kind = ORA_CUBIC_NAT;
   if (*kind == ORA_LINEAR) *same = 0;
 }
 
@@ -466,6 +470,53 @@ static float predict_dim(sweep* w, uint64_t i, const uint64_t c[3], int d,
   return eval_formula(f, v);
 }
 
+/* The natural cubic spline through every known point of the line along
+ * slot d (the knots at the multiples of h = 2s), evaluated halfway between
+ * the two knots around the point.  With N_k = h^2 M_k / 6 (M: the spline's
+ * second derivative at knot k) its conditions read
+ *   N_{k-1} + 4 N_k + N_{k+1} = y_{k-1} - 2 y_k + y_{k+1},  k = 1..K-1,
+ *   N_0 = N_K = 0 (natural ends),
+ * and halfway between knots j and j+1 the cubic piece is
+ *   (y_j + y_{j+1}) / 2 - 3/8 (N_j + N_{j+1}).
+ * The system is solved by the Thomas algorithm: c'_1 = 1/4, c'_k =
+ * 1 / (4 - c'_{k-1}); D_1 = r_1 c'_1, D_k = (r_k - D_{k-1}) c'_k;
+ * N_{K-1} = D_{K-1}, N_k = D_k - c'_k N_{k+1}.  Everything in binary32 in
+ * the order written.  A point with no knot to its right takes the
+ * boundary rule of the other interpolators. */
+static float spline_global(sweep* w, uint64_t i, const uint64_t c[3], int d, uint64_t s) {
+  const geom* g = w->g;
+  const uint64_t h = 2 * s;
+  const uint64_t K = (g->n[d] - 1) / h; /* knots 0..K at k h */
+  const uint64_t j = (c[d] - s) / h;    /* between knots j and j + 1 */
+  if (j + 1 > K) return predict_dim(w, i, c, d, s, ORA_LINEAR, 0);
+  float* y = (float*)malloc(sizeof(float) * (K + 1));
+  float* cp = (float*)calloc(K + 1, sizeof(float));
+  float* D = (float*)calloc(K + 1, sizeof(float));
+  float* N = (float*)calloc(K + 1, sizeof(float));
+  const uint64_t line0 = i - c[d] * g->st[d];
+  for (uint64_t k = 0; k <= K; ++k) y[k] = load_known(w, line0 + k * h * g->st[d]);
+  if (K >= 2) {
+    for (uint64_t k = 1; k <= K - 1; ++k) {
+      const float r = (y[k - 1] + y[k + 1]) - 2.0f * y[k];
+      if (k == 1) {
+        cp[k] = 0.25f;
+        D[k] = r * cp[k];
+      } else {
+        cp[k] = 1.0f / (4.0f - cp[k - 1]);
+        D[k] = (r - D[k - 1]) * cp[k];
+      }
+    }
+    N[K - 1] = D[K - 1];
+    for (uint64_t k = K - 2; k >= 1; --k) N[k] = D[k] - cp[k] * N[k + 1];
+  }
+  const float p = (y[j] + y[j + 1]) * 0.5f - 0.375f * (N[j] + N[j + 1]);
+  free(y);
+  free(cp);
+  free(D);
+  free(N);
+  return p;
+}
+
 static void process_point(sweep* w, int l, uint64_t i, const uint64_t c[3],
                           int md, int pass_slot, unsigned odd_mask,
                           int half_b, int kind) {
@@ -473,7 +524,8 @@ static void process_point(sweep* w, int l, uint64_t i, const uint64_t c[3],
   uint64_t s = (uint64_t)1 << (l - 1);
   float p;
   if (!md) {
-    p = predict_dim(w, i, c, pass_slot, s, kind, half_b);
+    p = kind == ORA_SPLINE_GLOBAL ? spline_global(w, i, c, pass_slot, s)
+                                  : predict_dim(w, i, c, pass_slot, s, kind, half_b);
   } else {
     /* Eq. 8: weighted sum over all odd dimensions, ascending, with the
      * Eq. 14 weights of this odd-dimension set */

@@ -23,8 +23,10 @@ extern "C" {
 #define ORA_HEADER_BYTES 512
 
 /* interpolator kinds (Sec. 5.2): Eq. 2 linear, Eq. 4 not-a-knot cubic,
- * Eq. 6 natural cubic */
-enum { ORA_LINEAR = 0, ORA_CUBIC_NAK = 1, ORA_CUBIC_NAT = 2 };
+ * Eq. 6 natural cubic; and, opt in, the natural cubic spline through every
+ * known point of the line (a global spline, solved per line; 1D-style
+ * paradigm only, without same-level halves or a block map) */
+enum { ORA_LINEAR = 0, ORA_CUBIC_NAK = 1, ORA_CUBIC_NAT = 2, ORA_SPLINE_GLOBAL = 3 };
 /* paradigms (Sec. 5.3): 1D-style (one direction per pass) or
  * multi-dimensional (Eq. 8) */
 enum { ORA_1D = 0, ORA_MD = 1 };

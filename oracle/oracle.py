@@ -29,7 +29,7 @@ _CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
 
 MAX_LEVELS = 16
 RADIUS = 32768
-LINEAR, CUBIC_NAK, CUBIC_NAT = 0, 1, 2
+LINEAR, CUBIC_NAK, CUBIC_NAT, SPLINE_GLOBAL = 0, 1, 2, 3
 P1D, PMD = 0, 1
 EB_ABS, EB_REL = 0, 1
 
