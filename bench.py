@@ -82,6 +82,8 @@ def parse():
                     help="skip the 64-field batched-vs-plain measurement")
     ap.add_argument("--no-served", action="store_true",
                     help="skip the served-form measurement")
+    ap.add_argument("--no-spline", action="store_true",
+                    help="skip the global natural-spline round trips on the same field")
     ap.add_argument("--no-lorenzo", action="store_true",
                     help="skip the Lorenzo-predictor round trips on the same field")
     ap.add_argument("--predictor", type=int, default=0, choices=[0, 1, 2],
@@ -414,6 +416,52 @@ def bench_lorenzo(ctx, x, shape, eb, cbuf, cap, y, stream, steps, peak):
     return res
 
 
+def bench_spline(ctx, x, shape, eb, cbuf, cap, y, stream, steps, peak, A):
+    """The same field with the global natural spline (interp 3, the natural
+    cubic spline through every known point of a pass line) at every level,
+    1D-style order 0, 1, 2: round-trip GB/s, compression ratio, and the
+    finest level's passes against the level's algorithmic bytes."""
+    import torch
+    from paper_2311_12133_gb300 import hpez
+    N = x.numel()
+    sptr = stream.cuda_stream
+    cfg = hpez.make_config(len(shape), interp=hpez.HPEZ_SPLINE_GLOBAL)
+
+    def st():
+        sz = hpez.hpez_compress(ctx.handle, x.data_ptr(), shape, hpez.HPEZ_EB_REL, eb, cfg,
+                                cbuf.data_ptr(), cap, sptr)
+        hpez.hpez_decompress(ctx.handle, cbuf.data_ptr(), sz, y.data_ptr(), N, sptr)
+        return sz
+    for _ in range(3):
+        sz = st()
+    torch.cuda.synchronize()
+    hpez.hpez_profile_enable(ctx.handle, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        sz = st()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    kc, nc = hpez.hpez_profile_get(ctx.handle, hpez.HPEZ_PH_LEVEL)
+    kd, nd = hpez.hpez_profile_get(ctx.handle, hpez.HPEZ_PH_DLEVEL)
+    hpez.hpez_profile_enable(ctx.handle, False)
+    e_abs = hpez.hpez_inspect(cbuf[:512].cpu().numpy().tobytes())[2]
+    err = (y.double() - x.double()).abs().max().item()
+    assert err <= e_abs, f"global spline: bound violated: {err} > {e_abs}"
+    lv = {}
+    for name, ph, (t, n) in (("compress", "level1", (kc, nc)), ("decompress", "dlevel1", (kd, nd))):
+        if n:
+            b = phase_bytes(ph, shape, A, sz)
+            gbs = b / (t / n / 1e3) / 1e9
+            lv[name] = {"launch_ms": round(t / n, 4), "achieved": round(gbs, 1),
+                        "frac": round(gbs / peak, 4), "algorithmic_bytes": b}
+    return {"value": round(4 * N / (ms / 1e3) / 1e9, 3), "unit": "GB/s",
+            "ms_per_step": round(ms, 4), "compression_ratio": round(4 * N / sz, 3),
+            "max_abs_err": err, "finest_level": lv}
+
+
 def bench_served(ctx, seconds=3.0, rate=200.0, slots=256):
     """Poisson stream of compress/decompress requests over fields of 1 MB ..
     512 MB (log-uniform), rel eb from {1e-2,1e-3,1e-4}, host buffers,
@@ -701,6 +749,10 @@ def main():
                     "compression_ratio": round(4 * N / dsz, 3),
                     "predictor": "cubic not-a-knot, 1D-style order 0,1,2, A=32, no tuning"}
 
+    spline = None
+    if not args.no_spline:
+        spline = bench_spline(ctx, x, shape, args.eb, cbuf, cap, y, stream,
+                              max(3, args.steps // 2), peak, A)
     lorenzo = None
     if not args.no_lorenzo:
         lorenzo = bench_lorenzo(ctx, x, shape, args.eb, cbuf, cap, y, stream,
@@ -737,7 +789,7 @@ def main():
             "roofline": roofline, "phases": phase_report,
             "gpu_launches": int(launches),
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
-            "default_predictor": default_pred, "lorenzo": lorenzo,
+            "default_predictor": default_pred, "lorenzo": lorenzo, "spline": spline,
             "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)

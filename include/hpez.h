@@ -60,6 +60,10 @@ extern "C" {
 #define HPEZ_LINEAR 0
 #define HPEZ_CUBIC_NAK 1
 #define HPEZ_CUBIC_NAT 2
+/* the natural cubic spline through every known point of a pass line, solved
+ * per line (a whole-line form beside the paper's local Eq. 6; opt in, for
+ * the 1D-style paradigm without same-level halves or a block map) */
+#define HPEZ_SPLINE_GLOBAL 3
 /* paradigms, Sec. 5.3: 1D-style passes or multi-dimensional (Eq. 8) */
 #define HPEZ_PARADIGM_1D 0
 #define HPEZ_PARADIGM_MD 1
@@ -82,7 +86,8 @@ typedef struct {
                             streams only (UNSUPPORTED) */
   double alpha, beta;    /* Eq. 15 level bounds, both >= 1 */
   double md_inv_var[3];  /* 1/sigma_d^2 for the Eq. 14 weights, > 0 */
-  uint8_t interp[HPEZ_MAX_LEVELS];     /* HPEZ_LINEAR / _CUBIC_NAK / _NAT */
+  uint8_t interp[HPEZ_MAX_LEVELS];     /* HPEZ_LINEAR / _CUBIC_NAK / _NAT /
+                                          _SPLINE_GLOBAL */
   uint8_t paradigm[HPEZ_MAX_LEVELS];   /* HPEZ_PARADIGM_* */
   uint8_t same_level[HPEZ_MAX_LEVELS]; /* Sec. 5.4.2, cubic only */
   uint8_t order[HPEZ_MAX_LEVELS][3];   /* 1D-style dim order (interp dims) */

@@ -106,8 +106,12 @@ int check_config(const Plan& p, const hpez_config& c) {
   if (c.predictor < 0 || c.predictor > 2 || (c.predictor && c.blockwise))
     return HPEZ_ERR_INVALID_ARG;
   for (int l = 0; l < p.L; ++l) {
-    if (c.interp[l] > HPEZ_CUBIC_NAT || c.paradigm[l] > HPEZ_PARADIGM_MD ||
+    if (c.interp[l] > HPEZ_SPLINE_GLOBAL || c.paradigm[l] > HPEZ_PARADIGM_MD ||
         c.same_level[l] > 1)
+      return HPEZ_ERR_INVALID_ARG;
+    // the global spline runs along whole lines: one direction per pass
+    if (c.interp[l] == HPEZ_SPLINE_GLOBAL &&
+        (c.paradigm[l] != HPEZ_PARADIGM_1D || c.same_level[l] || c.blockwise))
       return HPEZ_ERR_INVALID_ARG;
     bool seen[3] = {false, false, false};
     for (int j = 0; j < p.k; ++j) {
@@ -962,10 +966,11 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
     Level3D F3;
     LevelMD FM;
     int E1 = 0;
-    if (ctx->fused_levels && plan_level3d(ctx, p, sc, l, false, F3)) {
+    const bool spline = sc.interp[l - 1] == HPEZ_SPLINE_GLOBAL;
+    if (!spline && ctx->fused_levels && plan_level3d(ctx, p, sc, l, false, F3)) {
       launch_level3d(false, F3, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g], s);
       ++nl;
-    } else if (plan_md3(ctx, p, sc, l, false, FM, E1)) {
+    } else if (!spline && plan_md3(ctx, p, sc, l, false, FM, E1)) {
       if (ctx->stream_levels && md3s_supported(FM, false, d_in, b.R[l], b.Cg[l]) &&
           launch_level_md3s(false, sb.kind, FM, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g],
                             b.ctl, ctx->num_sms, ctx->drop_copy, s)) {
@@ -975,11 +980,11 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
                          b.Cg[g], s);
         nl += 2;
       }
-    } else if (plan_md(ctx, p, sc, l, false, FM)) {
+    } else if (!spline && plan_md(ctx, p, sc, l, false, FM)) {
       launch_level_md(false, sb.kind, FM, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g],
                       ctx->num_sms, s);
       nl += FM.k;
-    } else if (ctx->fused_levels && plan_fused(ctx, p, sc, l, false, F)) {
+    } else if (!spline && ctx->fused_levels && plan_fused(ctx, p, sc, l, false, F)) {
       launch_level(false, F, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g], s);
       ++nl;
     } else {
@@ -987,7 +992,10 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
                       b.Cg[g], b.ctl, s);
       ++nl;
       for (const Launch& L : level_schedule(p, sc, l)) {
-        launch_pass(false, p.grid[g], L.pb, sb, ctx->num_sms, s);
+        if (spline)
+          launch_spline_pass(false, p.grid[g], L.pb, sb, nullptr, ctx->num_sms, s);
+        else
+          launch_pass(false, p.grid[g], L.pb, sb, ctx->num_sms, s);
         nl += L.pb.total ? 1 : 0;
       }
     }
@@ -1111,6 +1119,10 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   const size_t o_woff = ar.take<unsigned long long>(p.nch);
   const size_t o_dchw = ar.take<uint32_t>(p.nch);
   const size_t o_tot = ar.take<unsigned long long>(2);
+  // level 1 of the global spline: its forward sweep must not overwrite the
+  // escaped values already in the output
+  const bool spline1 = !cfg.predictor && !cfg.blockwise && cfg.interp[0] == HPEZ_SPLINE_GLOBAL;
+  const size_t o_dscr = spline1 ? ar.take<float>(p.gsize[0]) : 0;
   rc = ensure_scratch(ctx, ar.off);
   if (rc) return rc;
   char* S = ctx->scratch;
@@ -1131,6 +1143,7 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   for (int g = 1; g < p.L; ++g) R[g] = reinterpret_cast<float*>(S + o_R[g]);
   R[0] = d_out;
   R[p.L] = const_cast<float*>(reinterpret_cast<const float*>(in + oa));
+  float* const dscr = spline1 ? reinterpret_cast<float*>(S + o_dscr) : nullptr;
 
   PhaseProfiler& pf = ctx->prof;
   uint64_t& nl = ctx->launches;
@@ -1192,10 +1205,11 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
     Level3D F3;
     LevelMD FM;
     int E1 = 0;
-    if (ctx->fused_levels && plan_level3d(ctx, p, sc, l, true, F3)) {
+    const bool spline = sc.interp[l - 1] == HPEZ_SPLINE_GLOBAL;
+    if (!spline && ctx->fused_levels && plan_level3d(ctx, p, sc, l, true, F3)) {
       launch_level3d(true, F3, sb, R[l], nullptr, R[g], nullptr, s);
       ++nl;
-    } else if (plan_md3(ctx, p, sc, l, true, FM, E1)) {
+    } else if (!spline && plan_md3(ctx, p, sc, l, true, FM, E1)) {
       if (ctx->stream_levels && md3s_supported(FM, true, codes, R[l], nullptr) &&
           launch_level_md3s(true, sb.kind, FM, sb, R[l], nullptr, R[g], nullptr, ctl,
                             ctx->num_sms, ctx->drop_copy, s)) {
@@ -1204,11 +1218,11 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
         launch_level_md3(true, sb.kind, FM, E1, sb, R[l], nullptr, R[g], nullptr, s);
         nl += 2;
       }
-    } else if (plan_md(ctx, p, sc, l, true, FM)) {
+    } else if (!spline && plan_md(ctx, p, sc, l, true, FM)) {
       launch_level_md(true, sb.kind, FM, sb, R[l], nullptr, R[g], nullptr,
                       ctx->num_sms, s);
       nl += FM.k;
-    } else if (ctx->fused_levels && plan_fused(ctx, p, sc, l, true, F)) {
+    } else if (!spline && ctx->fused_levels && plan_fused(ctx, p, sc, l, true, F)) {
       launch_level(true, F, sb, R[l], nullptr, R[g], nullptr, s);
       ++nl;
     } else {
@@ -1216,7 +1230,11 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
                       nullptr, ctl, s);
       ++nl;
       for (const Launch& L : level_schedule(p, sc, l)) {
-        launch_pass(true, p.grid[g], L.pb, sb, ctx->num_sms, s);
+        if (spline)
+          launch_spline_pass(true, p.grid[g], L.pb, sb, g == 0 ? dscr : nullptr,
+                             ctx->num_sms, s);
+        else
+          launch_pass(true, p.grid[g], L.pb, sb, ctx->num_sms, s);
         nl += L.pb.total ? 1 : 0;
       }
     }
@@ -1398,6 +1416,8 @@ extern "C" int hpez_decompress_noalloc(const void* d_in, uint64_t in_size,
     return HPEZ_ERR_CORRUPT_STREAM;
   if (check_config(p, cfg)) return HPEZ_ERR_CORRUPT_STREAM;
   if (cfg.predictor) return HPEZ_ERR_UNSUPPORTED;  // Lorenzo streams: hpez_decompress
+  for (int l = 0; l < p.L; ++l)  // global-spline streams: hpez_decompress
+    if (cfg.interp[l] == HPEZ_SPLINE_GLOBAL) return HPEZ_ERR_UNSUPPORTED;
   plan_chunks_blocks(p, cfg);
   const float e = rdf32(h, H_E);
   if (!(e > 0.0f) || !std::isfinite(e)) return HPEZ_ERR_CORRUPT_STREAM;

@@ -110,6 +110,8 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   if ((rc = check_config(p, cfg))) return rc;
   if (cfg.blockwise && !cfg.h_blockmap) return HPEZ_ERR_INVALID_ARG;
   if (cfg.predictor) return HPEZ_ERR_UNSUPPORTED;  // Lorenzo: hpez_compress
+  for (int l = 0; l < p.L; ++l)  // global spline: hpez_compress
+    if (cfg.interp[l] == HPEZ_SPLINE_GLOBAL) return HPEZ_ERR_UNSUPPORTED;
   plan_chunks_blocks(p, cfg);
   r.decomp = 0;
   r.N = p.N;
@@ -302,6 +304,9 @@ int plan_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   if (rc) return rc;
   if (si.N > out_cap_elems) return HPEZ_ERR_OUT_TOO_SMALL;
   if (!si.is_const && si.cfg.predictor) return HPEZ_ERR_UNSUPPORTED;
+  if (!si.is_const)
+    for (int l = 0; l < si.p.L; ++l)
+      if (si.cfg.interp[l] == HPEZ_SPLINE_GLOBAL) return HPEZ_ERR_UNSUPPORTED;
   r.decomp = 1;
   r.N = si.N;
   const Plan& p = si.p;

@@ -54,6 +54,10 @@ int launch_level_md3s(bool decomp, int kind, const LevelMD& P, const SweepBufs& 
                       const float* Rc, const uint16_t* Cc, float* Rs, uint16_t* Cs,
                       Ctl* ctl, int num_sms, int drop_copy, cudaStream_t s);
 
+// k_spline.cu
+void launch_spline_pass(bool decomp, const LevelGeom& g, const PassBox& pb, const SweepBufs& B,
+                        float* dscr, int num_sms, cudaStream_t s);
+
 // k_lorenzo.cu
 bool lorenzo_supported(const uint32_t n[3], const uint32_t fst[3], int off, int A);
 int launch_lorenzo(bool decomp, int order, const uint32_t n[3], const uint32_t fst[3],

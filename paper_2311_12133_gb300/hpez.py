@@ -20,7 +20,7 @@ HPEZ_MAX_LEVELS = 16
 HPEZ_HEADER_BYTES = 512
 HPEZ_OK = 0
 HPEZ_EB_ABS, HPEZ_EB_REL = 0, 1
-HPEZ_LINEAR, HPEZ_CUBIC_NAK, HPEZ_CUBIC_NAT = 0, 1, 2
+HPEZ_LINEAR, HPEZ_CUBIC_NAK, HPEZ_CUBIC_NAT, HPEZ_SPLINE_GLOBAL = 0, 1, 2, 3
 HPEZ_PARADIGM_1D, HPEZ_PARADIGM_MD = 0, 1
 
 

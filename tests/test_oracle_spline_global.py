@@ -141,3 +141,14 @@ def test_refused_forms(kw):
     c = O.make_config(2, interp=O.SPLINE_GLOBAL, **kw)
     with pytest.raises(Exception):
         O.compress(x, 1e-3, O.EB_REL, c)
+
+
+def test_thomas_coefficients_reach_their_fixed_point():
+    """c'_1 = 1/4, c'_k = 1/(4 - c'_{k-1}) in binary32 (IEEE division) is
+    stationary from k = 7 on: a table of the first 16 coefficients, reused
+    for every larger k, gives each c'_k exactly (the kernel relies on it)."""
+    c = [np.float32(0.25)]
+    for _ in range(2, 64):
+        c.append(np.float32(1.0) / (np.float32(4.0) - c[-1]))
+    assert all(v == c[14] for v in c[14:])
+    assert c[6] == c[7] and c[5] != c[6]
