@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(256)
     };
     if (K >= 2) {
       float ym = R[0], y0 = R[2u * st], Dp = 0.0f;
+#pragma unroll 4
       for (int k = 1; k <= K - 1; ++k) {
         const float yp = R[(uint32_t)(2 * k + 2) * st];
         const float r = __fsub_rn(__fadd_rn(ym, yp), __fmul_rn(2.0f, y0));
@@ -95,6 +96,7 @@ __global__ void __launch_bounds__(256)
     }
     float Nn = 0.0f;                          // N_{k+1}
     float yr = R[(uint32_t)(2 * K) * st];     // y_{k+1}
+#pragma unroll 4
     for (int k = K - 1; k >= 0; --k) {
       const float yl = R[(uint32_t)(2 * k) * st];
       float Nk = 0.0f;
