@@ -307,8 +307,10 @@ HPEZ_API int hpez_server_destroy(hpez_server* s);
  *             if its estimate is smaller.
  *   Sec. 6.5  order-1 and order-2 Lorenzo tests on the same blocks (zero
  *             padding, global bound), bits * lorenzo_coef compared with the
- *             interpolation estimate; reported only (the compressor runs
- *             interpolation).
+ *             interpolation estimate; when the smaller is strictly below,
+ *             theta selects the Lorenzo predictor of that order
+ *             (predictor 1 or 2, order 1 on a tie) and no block map is
+ *             tuned.
  *   Sec. 6.6  per block of block_size^ndim, a centred sub-block of side
  *             max(5, round(block_size * sub_frac^(1/ndim))), anchor stride
  *             the largest power of two <= max(2, side-1); candidates
