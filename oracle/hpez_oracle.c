@@ -15,10 +15,16 @@
  *   Sec. 5.3 Eq. 8, 14     multi-dimensional interpolation, weights
  *                          alpha_i proportional to 1/sigma_i^2
  *   Sec. 5.4.2 Eq. 10, 11  same-level cubic interpolation (two halves)
+ *   Sec. 6.1-6.6           the auto-tuner (statistics, per-level tests,
+ *                          (alpha, beta), freezing, Lorenzo test, block map)
  *   Sec. 6.3               dimension freezing (anchor stride 1 on one dim)
  *   Sec. 6.4 Eq. 15        level error bounds e_l = e / min(alpha^(l-1), beta)
+ *   Sec. 6.5               the full-field dynamic-order Lorenzo predictor,
+ *                          read as block-local (blocks of side A)
  *   Sec. 6.6               block-wise interpolator choice (block map)
  *   Sec. 7.1.3             value-range relative bound e = eps * (max - min)
+ * and, opt in beside Eq. 6, the natural cubic spline through every known
+ * point of a pass line (a global spline, Thomas algorithm per line).
  *
  * Readings where the paper is silent (each listed in the design notes):
  * boundary fallbacks of the stencils, the quantizer's exact rounding steps,
