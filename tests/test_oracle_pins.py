@@ -412,14 +412,25 @@ def test_corrupt_streams_rejected(oracle):
     bad[0] ^= 0xFF
     with pytest.raises(oracle.OracleError):
         oracle.decompress(bytes(bad))
+    # flip the first bit of lane 1 of chunk 0: the code of point 1 (never an
+    # anchor) changes, so the decoder must either reject the stream (the
+    # lane no longer ends on its stored bit count, or the escape count no
+    # longer matches) or return a different field
+    hdr = np.frombuffer(s[:512], np.uint8)
+    ocw = int(hdr[264:272].view(np.uint64)[0])
+    obits = int(hdr[288:296].view(np.uint64)[0])
+    lane0_bits = int(np.frombuffer(s[ocw:ocw + 2], np.uint16)[0])
+    assert int(np.frombuffer(s[ocw + 2:ocw + 4], np.uint16)[0]) > 0
+    word = obits + 4 * (lane0_bits // 32)
+    bit = 31 - lane0_bits % 32
     bad = bytearray(s)
-    bad[-1] ^= 0xFF  # flip bits in the last bitstream word
-    bad[-2] ^= 0xFF
+    w = int.from_bytes(bad[word:word + 4], "little") ^ (1 << bit)
+    bad[word:word + 4] = w.to_bytes(4, "little")
     try:
         y = oracle.decompress(bytes(bad))
-        assert not np.array_equal(y, oracle.decompress(s)) or True
     except oracle.OracleError:
-        pass
+        return
+    assert not np.array_equal(y, oracle.decompress(s))
 
 
 def test_error_bound_on_workload_fields(oracle):
