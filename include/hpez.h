@@ -151,7 +151,8 @@ HPEZ_API int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
  * overlap on the GPU (other streams, other host threads) race and must be
  * serialized by the caller.  Synchronizes `stream`.
  * Errors: as hpez_decompress, plus HPEZ_ERR_TOO_LARGE, and
- * HPEZ_ERR_UNSUPPORTED for a Lorenzo-predictor stream. */
+ * HPEZ_ERR_UNSUPPORTED for a Lorenzo-predictor stream or a stream with a
+ * global natural-spline level (interp HPEZ_SPLINE_GLOBAL). */
 #define HPEZ_NOALLOC_MAX_POINTS 2097152u
 #define HPEZ_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 HPEZ_API int hpez_decompress_noalloc(const void* d_in, uint64_t in_size,
@@ -397,6 +398,13 @@ HPEZ_API int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim,
  *                         its wait for them expires and the call returns
  *                         HPEZ_ERR_TIMEOUT (no copy stays in flight; the
  *                         context stays usable)
+ *  HPEZ_OPT_STREAM_CHUNKS 0 (default: as many chunks of planes as fill the
+ *                         resident CTAs); n > 0: the streamed finest level
+ *                         cuts dim 0 into n chunks, so a CTA walks more planes
+ *                         through its ring (what a large field does)
+ *  HPEZ_OPT_LORENZO_CTAS  0 (default: the resident CTAs); n > 0: at most n
+ *                         persistent CTAs for the Lorenzo kernels, so each
+ *                         streams more blocks back to back
  * Errors: INVALID_ARG for an unknown option or an out-of-range value. */
 #define HPEZ_OPT_FUSED_LEVELS 1
 #define HPEZ_OPT_TILE_E0 2
@@ -406,6 +414,8 @@ HPEZ_API int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim,
 #define HPEZ_OPT_LEVEL3D 6
 #define HPEZ_OPT_STREAM_LEVELS 7
 #define HPEZ_OPT_DROP_COPY 8
+#define HPEZ_OPT_STREAM_CHUNKS 9
+#define HPEZ_OPT_LORENZO_CTAS 10
 HPEZ_API int hpez_set_option(hpez_ctx* ctx, int option, int64_t value);
 
 /* ---- measurement hooks (not part of the paper's method) ----

@@ -738,6 +738,14 @@ int hpez_set_option(hpez_ctx* ctx, int option, int64_t value) {
       if (value < 0 || value > 1000000) return HPEZ_ERR_INVALID_ARG;
       ctx->drop_copy = (int)value;
       return HPEZ_OK;
+    case HPEZ_OPT_STREAM_CHUNKS:
+      if (value < 0 || value > 1000000) return HPEZ_ERR_INVALID_ARG;
+      ctx->stream_chunks = (int)value;
+      return HPEZ_OK;
+    case HPEZ_OPT_LORENZO_CTAS:
+      if (value < 0 || value > 1000000) return HPEZ_ERR_INVALID_ARG;
+      ctx->lorenzo_ctas = (int)value;
+      return HPEZ_OK;
     case HPEZ_OPT_FUSED_SMEM:
       if (value < 4096 || value > 200 * 1024) return HPEZ_ERR_INVALID_ARG;
       ctx->fused_smem_cap = (size_t)value;
@@ -935,7 +943,8 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
     // finest grid's code array
     pf.begin(HPEZ_PH_LEVEL, s);
     rc = launch_lorenzo(false, cfg.predictor, p.n, p.fst, p.off, p.A, ctx->x_aligned16,
-                        d_in, b.Cg[0], nullptr, b.ctl, ctx->num_sms, ctx->drop_copy, s);
+                        d_in, b.Cg[0], nullptr, b.ctl, ctx->num_sms, ctx->drop_copy,
+                        ctx->lorenzo_ctas, s);
     pf.end(s);
     if (rc) return rc;
     ++nl;
@@ -973,7 +982,7 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
     } else if (!spline && plan_md3(ctx, p, sc, l, false, FM, E1)) {
       if (ctx->stream_levels && md3s_supported(FM, false, d_in, b.R[l], b.Cg[l]) &&
           launch_level_md3s(false, sb.kind, FM, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g],
-                            b.ctl, ctx->num_sms, ctx->drop_copy, s)) {
+                            b.ctl, ctx->num_sms, ctx->drop_copy, ctx->stream_chunks, s)) {
         ++nl;
       } else {
         launch_level_md3(false, sb.kind, FM, E1, sb, b.R[l], b.Cg[l], b.R[g],
@@ -1172,7 +1181,8 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
     if (!lorenzo_supported(p.n, p.fst, p.off, p.A)) return HPEZ_ERR_UNSUPPORTED;
     pf.begin(HPEZ_PH_DLEVEL, s);
     rc = launch_lorenzo(true, cfg.predictor, p.n, p.fst, p.off, p.A, ctx->out_aligned16,
-                        nullptr, codes, d_out, ctl, ctx->num_sms, ctx->drop_copy, s);
+                        nullptr, codes, d_out, ctl, ctx->num_sms, ctx->drop_copy,
+                        ctx->lorenzo_ctas, s);
     pf.end(s);
     if (rc) return rc;
     ++nl;
@@ -1212,7 +1222,7 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
     } else if (!spline && plan_md3(ctx, p, sc, l, true, FM, E1)) {
       if (ctx->stream_levels && md3s_supported(FM, true, codes, R[l], nullptr) &&
           launch_level_md3s(true, sb.kind, FM, sb, R[l], nullptr, R[g], nullptr, ctl,
-                            ctx->num_sms, ctx->drop_copy, s)) {
+                            ctx->num_sms, ctx->drop_copy, ctx->stream_chunks, s)) {
         ++nl;
       } else {
         launch_level_md3(true, sb.kind, FM, E1, sb, R[l], nullptr, R[g], nullptr, s);
@@ -1372,69 +1382,31 @@ extern "C" int hpez_decompress_noalloc(const void* d_in, uint64_t in_size,
   rc = cuda_check(cudaMemcpyAsync(h, d_in, kHeaderBytes, cudaMemcpyDeviceToHost, s));
   if (!rc) rc = cuda_check(cudaStreamSynchronize(s));
   if (rc) return rc;
-  int nd;
-  uint64_t dims[3];
-  rc = hpez_inspect(h, kHeaderBytes, &nd, dims, nullptr);
+  // the same header validation as hpez_decompress (dims, offsets, counts,
+  // alignment of the sections)
+  StreamInfo si;
+  rc = parse_stream_header(h, in_size, si);
   if (rc) return rc;
-  if (rd64(h, H_TOTAL) > in_size) return HPEZ_ERR_CORRUPT_STREAM;
-  uint64_t N = 1;
-  for (int d = 0; d < nd; ++d) {
-    if (dims[d] == 0) return HPEZ_ERR_CORRUPT_STREAM;
-    N *= dims[d];
-    if (N > 0xFFFFFFFFull) return HPEZ_ERR_CORRUPT_STREAM;
-  }
+  const uint64_t N = si.N;
   if (N > HPEZ_NOALLOC_MAX_POINTS) return HPEZ_ERR_TOO_LARGE;
   if (N > out_cap_elems) return HPEZ_ERR_OUT_TOO_SMALL;
   const uint8_t* in = static_cast<const uint8_t*>(d_in);
-  hpez_config cfg;
-  std::memset(&cfg, 0, sizeof(cfg));
-  cfg.anchor_stride = (int32_t)rd32(h, H_ANCHOR);
-  cfg.frozen_dim = (int32_t)rd32(h, H_FROZEN);
-  cfg.chunk_syms = (int32_t)rd32(h, H_CHUNK);
-  cfg.blockwise = (int32_t)rd32(h, H_BLOCKWISE);
-  cfg.block_size = (int32_t)rd32(h, H_BLOCKSIZE);
-  cfg.predictor = (int32_t)rd32(h, H_PREDICTOR);
-  cfg.alpha = rdf64(h, H_ALPHA);
-  cfg.beta = rdf64(h, H_BETA);
-  for (int d = 0; d < 3; ++d) cfg.md_inv_var[d] = rdf64(h, H_MDIV + 8 * d);
-  for (int l = 0; l < HPEZ_MAX_LEVELS; ++l) {
-    cfg.interp[l] = h[H_INTERP + l];
-    cfg.paradigm[l] = h[H_PARADIGM + l];
-    cfg.same_level[l] = h[H_SAME + l];
-    for (int j = 0; j < 3; ++j) cfg.order[l][j] = h[H_ORDER + 3 * l + j];
-  }
-  if (rd32(h, H_FLAGS) & 1u) {
-    Plan p;
-    if (plan_geometry(p, nd, dims, 2, -1)) return HPEZ_ERR_CORRUPT_STREAM;
-    launch_fill(d_out, p.N, rdf32(h, H_CONST), opt.num_sms, s);
+  if (si.is_const) {
+    launch_fill(d_out, (uint32_t)N, si.const_value, opt.num_sms, s);
     rc = cuda_check(cudaGetLastError());
     if (rc) return rc;
     return cuda_check(cudaStreamSynchronize(s));
   }
-  Plan p;
-  if (plan_geometry(p, nd, dims, cfg.anchor_stride, cfg.frozen_dim))
-    return HPEZ_ERR_CORRUPT_STREAM;
-  if (check_config(p, cfg)) return HPEZ_ERR_CORRUPT_STREAM;
+  const hpez_config& cfg = si.cfg;
+  const Plan& p = si.p;
   if (cfg.predictor) return HPEZ_ERR_UNSUPPORTED;  // Lorenzo streams: hpez_decompress
   for (int l = 0; l < p.L; ++l)  // global-spline streams: hpez_decompress
     if (cfg.interp[l] == HPEZ_SPLINE_GLOBAL) return HPEZ_ERR_UNSUPPORTED;
-  plan_chunks_blocks(p, cfg);
-  const float e = rdf32(h, H_E);
-  if (!(e > 0.0f) || !std::isfinite(e)) return HPEZ_ERR_CORRUPT_STREAM;
-  const uint64_t na = rd64(h, H_NANCHORS), nout = rd64(h, H_NOUTLIERS),
-                 nch = rd64(h, H_NCHUNKS), twords = rd64(h, H_TOTALWORDS);
-  const uint32_t nused = rd32(h, H_NUSED);
-  const uint64_t oa = rd64(h, H_OFF_ANCHORS), ocw = rd64(h, H_OFF_CHUNKW),
-                 ot = rd64(h, H_OFF_TABLE), oo = rd64(h, H_OFF_OUTLIERS),
-                 ob = rd64(h, H_OFF_BITS), obm = rd64(h, H_OFF_BLOCKMAP);
-  if (na != (cfg.predictor ? 0 : n_anchors(p)) || nch != p.nch || nused == 0 ||
-      nused > 65536 || nout > N || (cfg.blockwise && rd64(h, H_NBLOCKS) != p.nblocks))
-    return HPEZ_ERR_CORRUPT_STREAM;
-  if (oa + 4 * na > in_size || ocw + 64 * nch > in_size ||
-      ot + 3ull * nused > in_size || oo + 4 * nout > in_size ||
-      ob + 4 * twords > in_size || (cfg.blockwise && obm + p.nblocks > in_size) ||
-      (oa & 15) || (ocw & 15) || (oo & 15) || (ob & 15))
-    return HPEZ_ERR_CORRUPT_STREAM;
+  const float e = si.e;
+  const uint64_t nout = si.nout, twords = si.twords;
+  const uint32_t nused = si.nused;
+  const uint64_t oa = si.oa, ocw = si.ocw, ot = si.ot, oo = si.oo, ob = si.ob,
+                 obm = si.obm;
   uint16_t single_sym = 0;
   if (nused == 1) {
     uint8_t tb[2];

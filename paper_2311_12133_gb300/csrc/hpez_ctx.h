@@ -76,6 +76,8 @@ struct hpez_ctx {
   int level3d = 1;             // HPEZ_OPT_LEVEL3D
   int stream_levels = 1;       // HPEZ_OPT_STREAM_LEVELS
   int drop_copy = 0;           // HPEZ_OPT_DROP_COPY
+  int stream_chunks = 0;       // HPEZ_OPT_STREAM_CHUNKS (0 = heuristic)
+  int lorenzo_ctas = 0;        // HPEZ_OPT_LORENZO_CTAS (0 = resident CTAs)
   // the value range of the last tuned input (order-preserving keys), which
   // the compress call of hpez_compress_auto reuses instead of a second pass
   bool range_hint_on = false;

@@ -52,7 +52,7 @@ bool md3s_supported(const LevelMD& P, bool decomp, const void* in, const float* 
                     const uint16_t* Cc);
 int launch_level_md3s(bool decomp, int kind, const LevelMD& P, const SweepBufs& B,
                       const float* Rc, const uint16_t* Cc, float* Rs, uint16_t* Cs,
-                      Ctl* ctl, int num_sms, int drop_copy, cudaStream_t s);
+                      Ctl* ctl, int num_sms, int drop_copy, int chunks, cudaStream_t s);
 
 // k_spline.cu
 void launch_spline_pass(bool decomp, const LevelGeom& g, const PassBox& pb, const SweepBufs& B,
@@ -62,7 +62,8 @@ void launch_spline_pass(bool decomp, const LevelGeom& g, const PassBox& pb, cons
 bool lorenzo_supported(const uint32_t n[3], const uint32_t fst[3], int off, int A);
 int launch_lorenzo(bool decomp, int order, const uint32_t n[3], const uint32_t fst[3],
                    int off, int A, bool vec, const float* x, uint16_t* codes, float* out,
-                   const Ctl* ctl, int num_sms, int drop_copy, cudaStream_t s);
+                   const Ctl* ctl, int num_sms, int drop_copy, int max_ctas,
+                   cudaStream_t s);
 
 // k_huffman.cu
 void launch_hist(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,

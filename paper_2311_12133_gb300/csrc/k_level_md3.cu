@@ -800,7 +800,7 @@ __global__ void __launch_bounds__(kStreamThreads, 2)
 template <bool kDecomp, int KIND>
 int launch_md3s_k(const CUtensorMap& tin, const CUtensorMap& tc, const CUtensorMap& tcc,
                   const LevelMD& P, const float* outl, float* Rs, uint16_t* Cs, Ctl* ctl,
-                  int num_sms, int drop_copy, cudaStream_t s) {
+                  int num_sms, int drop_copy, int chunks, cudaStream_t s) {
   const int smem = StreamLayout<kDecomp>::bytes(Ring<KIND>::n);
   static bool attr = false;
   if (!attr) {
@@ -816,7 +816,9 @@ int launch_md3s_k(const CUtensorMap& tin, const CUtensorMap& tc, const CUtensorM
   const int nt1 = (m1 + kS1 - 1) / kS1, nt2 = (m2 + kS2 - 1) / kS2;
   const int ntiles = nt1 * nt2;
   const int ke = (m0 + 1) / 2;
-  int nch = (num_sms * per_sm) / ntiles;
+  // chunks > 0 (an execution option) sets the chunk count; the default
+  // fills the resident CTAs
+  int nch = chunks > 0 ? chunks : (num_sms * per_sm) / ntiles;
   nch = std::max(1, std::min(nch, ke));
   const int K = (ke + nch - 1) / nch;
   nch = (ke + K - 1) / K;
@@ -912,7 +914,7 @@ bool md3s_supported(const LevelMD& P, bool decomp, const void* in, const float* 
 // made; nothing was launched then).
 int launch_level_md3s(bool decomp, int kind, const LevelMD& P, const SweepBufs& B,
                       const float* Rc, const uint16_t* Cc, float* Rs, uint16_t* Cs,
-                      Ctl* ctl, int num_sms, int drop_copy, cudaStream_t s) {
+                      Ctl* ctl, int num_sms, int drop_copy, int chunks, cudaStream_t s) {
   CUtensorMap tin, tc, tcc;
   const void* in = decomp ? (const void*)B.codes_full : (const void*)B.x;
   if (!make_map(&tin, in, decomp, P.g.m, kXC, kXR)) return 0;
@@ -925,16 +927,16 @@ int launch_level_md3s(bool decomp, int kind, const LevelMD& P, const SweepBufs& 
   const float* outl = B.outl_full;
   if (decomp) {
     if (kind == LINEAR)
-      return launch_md3s_k<true, LINEAR>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, drop_copy, s);
+      return launch_md3s_k<true, LINEAR>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, drop_copy, chunks, s);
     if (kind == CUBIC_NAK)
-      return launch_md3s_k<true, CUBIC_NAK>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, drop_copy, s);
-    return launch_md3s_k<true, CUBIC_NAT>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, drop_copy, s);
+      return launch_md3s_k<true, CUBIC_NAK>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, drop_copy, chunks, s);
+    return launch_md3s_k<true, CUBIC_NAT>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, drop_copy, chunks, s);
   }
   if (kind == LINEAR)
-    return launch_md3s_k<false, LINEAR>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, drop_copy, s);
+    return launch_md3s_k<false, LINEAR>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, drop_copy, chunks, s);
   if (kind == CUBIC_NAK)
-    return launch_md3s_k<false, CUBIC_NAK>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, drop_copy, s);
-  return launch_md3s_k<false, CUBIC_NAT>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, drop_copy, s);
+    return launch_md3s_k<false, CUBIC_NAK>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, drop_copy, chunks, s);
+  return launch_md3s_k<false, CUBIC_NAT>(tin, tc, tcc, P, outl, Rs, Cs, ctl, num_sms, drop_copy, chunks, s);
 }
 
 }  // namespace hpez

@@ -770,7 +770,7 @@ bool lor_geom(const uint32_t n[3], const uint32_t fst[3], int off, int A, int or
 
 template <bool kDecomp, int ORDER, int NDR, bool kVec, bool kSkew = false>
 int launch_lor_k(const LorGeom& G, size_t smem, unsigned threads, int num_sms,
-                 const float* x, uint16_t* codes, float* out, const Ctl* ctl,
+                 int max_ctas, const float* x, uint16_t* codes, float* out, const Ctl* ctl,
                  cudaStream_t s) {
   auto kern = k_lorenzo<kDecomp, ORDER, NDR, kVec, kSkew>;
   if (smem > 48 * 1024)
@@ -782,7 +782,8 @@ int launch_lor_k(const LorGeom& G, size_t smem, unsigned threads, int num_sms,
     return HPEZ_ERR_CUDA;
   // persistent CTAs, the blocks dealt round robin; the grid shrunk to the
   // fewest CTAs that keep the most loaded one's block count
-  const uint64_t cap = (uint64_t)per_sm * (uint64_t)(num_sms > 0 ? num_sms : 1);
+  uint64_t cap = (uint64_t)per_sm * (uint64_t)(num_sms > 0 ? num_sms : 1);
+  if (max_ctas > 0 && cap > (uint64_t)max_ctas) cap = (uint64_t)max_ctas;
   uint64_t grid = G.nblocks < cap ? G.nblocks : cap;
   const uint64_t J = (G.nblocks + grid - 1) / grid;
   grid = (G.nblocks + J - 1) / J;
@@ -797,8 +798,8 @@ int launch_lor_k(const LorGeom& G, size_t smem, unsigned threads, int num_sms,
 // The box-fed kernel when its shared memory fits and the tensor map can be
 // made; 1: launched, 0: not taken (use the register-fed kernel), < 0: error.
 template <bool kDecomp, int ORDER>
-int launch_lor_tma(const LorGeom& G, int num_sms, const float* x, uint16_t* codes, float* out,
-                   Ctl* ctl, int drop, cudaStream_t s) {
+int launch_lor_tma(const LorGeom& G, int num_sms, int max_ctas, const float* x, uint16_t* codes,
+                   float* out, Ctl* ctl, int drop, cudaStream_t s) {
   using BX = LorBox<kDecomp>;
   auto kern = k_lorenzo_tma<kDecomp, ORDER>;
   const uint32_t ring_bytes =
@@ -816,7 +817,8 @@ int launch_lor_tma(const LorGeom& G, int num_sms, const float* x, uint16_t* code
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 1024, smem) != cudaSuccess ||
       per_sm < 1)
     return HPEZ_ERR_CUDA;
-  const uint64_t cap = (uint64_t)per_sm * (uint64_t)(num_sms > 0 ? num_sms : 1);
+  uint64_t cap = (uint64_t)per_sm * (uint64_t)(num_sms > 0 ? num_sms : 1);
+  if (max_ctas > 0 && cap > (uint64_t)max_ctas) cap = (uint64_t)max_ctas;
   uint64_t grid = G.nblocks < cap ? G.nblocks : cap;
   const uint64_t J = (G.nblocks + grid - 1) / grid;
   grid = (G.nblocks + J - 1) / J;
@@ -830,26 +832,26 @@ int launch_lor_tma(const LorGeom& G, int num_sms, const float* x, uint16_t* code
 
 template <bool kDecomp, int ORDER>
 int launch_lor_nd(int ndr, bool vec, const LorGeom& G, size_t smem, unsigned threads,
-                  int num_sms, const float* x, uint16_t* codes, float* out, const Ctl* ctl,
-                  int drop, cudaStream_t s) {
+                  int num_sms, int max_ctas, const float* x, uint16_t* codes, float* out,
+                  const Ctl* ctl, int drop, cudaStream_t s) {
   // order 1 takes the box-fed kernel (order 2: no faster measured, and the
   // compressor's shared memory would not fit)
   if (ORDER == 1 && ndr == 3 && G.B[0] == 32 && G.B[1] == 32 && vec) {
     const int r =
-        launch_lor_tma<kDecomp, ORDER>(G, num_sms, x, codes, out, const_cast<Ctl*>(ctl), drop, s);
+        launch_lor_tma<kDecomp, ORDER>(G, num_sms, max_ctas, x, codes, out, const_cast<Ctl*>(ctl), drop, s);
     if (r != 0) return r < 0 ? r : HPEZ_OK;
   }
   if (ndr == 3 && G.B[0] == 32 && G.B[1] == 32)
-    return vec ? launch_lor_k<kDecomp, ORDER, 3, true, true>(G, smem, threads, num_sms, x, codes, out, ctl, s)
-               : launch_lor_k<kDecomp, ORDER, 3, false, true>(G, smem, threads, num_sms, x, codes, out, ctl, s);
+    return vec ? launch_lor_k<kDecomp, ORDER, 3, true, true>(G, smem, threads, num_sms, max_ctas, x, codes, out, ctl, s)
+               : launch_lor_k<kDecomp, ORDER, 3, false, true>(G, smem, threads, num_sms, max_ctas, x, codes, out, ctl, s);
   if (ndr == 3)
-    return vec ? launch_lor_k<kDecomp, ORDER, 3, true>(G, smem, threads, num_sms, x, codes, out, ctl, s)
-               : launch_lor_k<kDecomp, ORDER, 3, false>(G, smem, threads, num_sms, x, codes, out, ctl, s);
+    return vec ? launch_lor_k<kDecomp, ORDER, 3, true>(G, smem, threads, num_sms, max_ctas, x, codes, out, ctl, s)
+               : launch_lor_k<kDecomp, ORDER, 3, false>(G, smem, threads, num_sms, max_ctas, x, codes, out, ctl, s);
   if (ndr == 2)
-    return vec ? launch_lor_k<kDecomp, ORDER, 2, true>(G, smem, threads, num_sms, x, codes, out, ctl, s)
-               : launch_lor_k<kDecomp, ORDER, 2, false>(G, smem, threads, num_sms, x, codes, out, ctl, s);
-  return vec ? launch_lor_k<kDecomp, ORDER, 1, true>(G, smem, threads, num_sms, x, codes, out, ctl, s)
-             : launch_lor_k<kDecomp, ORDER, 1, false>(G, smem, threads, num_sms, x, codes, out, ctl, s);
+    return vec ? launch_lor_k<kDecomp, ORDER, 2, true>(G, smem, threads, num_sms, max_ctas, x, codes, out, ctl, s)
+               : launch_lor_k<kDecomp, ORDER, 2, false>(G, smem, threads, num_sms, max_ctas, x, codes, out, ctl, s);
+  return vec ? launch_lor_k<kDecomp, ORDER, 1, true>(G, smem, threads, num_sms, max_ctas, x, codes, out, ctl, s)
+             : launch_lor_k<kDecomp, ORDER, 1, false>(G, smem, threads, num_sms, max_ctas, x, codes, out, ctl, s);
 }
 
 }  // namespace
@@ -866,11 +868,14 @@ bool lorenzo_supported(const uint32_t n[3], const uint32_t fst[3], int off, int 
 // values already scattered into out -> out).  vec: rows start on 16-byte
 // boundaries (n[2] a multiple of 8 and the float buffer 16-byte aligned;
 // taken when A >= 8).
-// drop_copy: see HPEZ_OPT_DROP_COPY (0 in normal use).  Returns
+// drop_copy: see HPEZ_OPT_DROP_COPY (0 in normal use); max_ctas > 0 caps
+// the persistent grid (HPEZ_OPT_LORENZO_CTAS), so each CTA streams more
+// blocks.  Returns
 // HPEZ_ERR_UNSUPPORTED for geometries the kernel does not take.
 int launch_lorenzo(bool decomp, int order, const uint32_t n[3], const uint32_t fst[3],
                    int off, int A, bool vec, const float* x, uint16_t* codes, float* out,
-                   const Ctl* ctl, int num_sms, int drop_copy, cudaStream_t s) {
+                   const Ctl* ctl, int num_sms, int drop_copy, int max_ctas,
+                   cudaStream_t s) {
   LorGeom G;
   size_t smem;
   unsigned threads;
@@ -879,10 +884,10 @@ int launch_lorenzo(bool decomp, int order, const uint32_t n[3], const uint32_t f
   vec = vec && (n[2] % kSeg) == 0 && A >= kSeg;
   const int ndr = 3 - off;
   if (decomp)
-    return order == 1 ? launch_lor_nd<true, 1>(ndr, vec, G, smem, threads, num_sms, x, codes, out, ctl, drop_copy, s)
-                      : launch_lor_nd<true, 2>(ndr, vec, G, smem, threads, num_sms, x, codes, out, ctl, drop_copy, s);
-  return order == 1 ? launch_lor_nd<false, 1>(ndr, vec, G, smem, threads, num_sms, x, codes, out, ctl, drop_copy, s)
-                    : launch_lor_nd<false, 2>(ndr, vec, G, smem, threads, num_sms, x, codes, out, ctl, drop_copy, s);
+    return order == 1 ? launch_lor_nd<true, 1>(ndr, vec, G, smem, threads, num_sms, max_ctas, x, codes, out, ctl, drop_copy, s)
+                      : launch_lor_nd<true, 2>(ndr, vec, G, smem, threads, num_sms, max_ctas, x, codes, out, ctl, drop_copy, s);
+  return order == 1 ? launch_lor_nd<false, 1>(ndr, vec, G, smem, threads, num_sms, max_ctas, x, codes, out, ctl, drop_copy, s)
+                    : launch_lor_nd<false, 2>(ndr, vec, G, smem, threads, num_sms, max_ctas, x, codes, out, ctl, drop_copy, s);
 }
 
 }  // namespace hpez

@@ -47,6 +47,58 @@ def test_noalloc_matches_decompress_twice(ctx):
             assert got.tobytes() == ref.tobytes()
 
 
+def test_noalloc_matches_tuned_md_and_frozen_streams(ctx):
+    """Streams of every sweep the decompressor can meet: auto-tuned ones
+    (a block map, uniform or mixed), the multi-dimensional paradigm, a
+    frozen dimension, and an explicit mixed block map."""
+    import torch
+    from paper_2311_12133_gb300 import fields, hpez
+    cases = []
+    for kind, shape, seed in (("grf", (64, 64, 64), 1), ("bumps", (70, 64, 40), 9),
+                              ("aniso", (24, 96, 80), 2), ("climate2d", (400, 640), 3)):
+        x = fields.make(kind, shape, seed)
+        xd = torch.from_numpy(x).cuda()
+        cap = hpez.hpez_compress_bound(x.shape)
+        buf = torch.empty(cap, dtype=torch.uint8, device="cuda")
+        size = hpez.hpez_compress_auto(ctx.handle, xd.data_ptr(), x.shape, hpez.HPEZ_EB_REL,
+                                       1e-3, None, buf.data_ptr(), cap,
+                                       torch.cuda.current_stream().cuda_stream)
+        cases.append((x, buf, size))
+    bm = np.random.default_rng(4).choice(np.array([0, 1, 2, 5, 6], np.uint8),
+                                         size=hpez.hpez_blockmap_size((70, 64, 45), 32))
+    for x, kw in ((fields.grf((50, 40, 64), seed=6), {"paradigm": 1, "interp": 2}),
+                  (fields.grf((50, 40, 64), seed=7), {"paradigm": 1, "same_level": 1}),
+                  (fields.aniso((12, 80, 96), seed=1), {"frozen_dim": 0}),
+                  (fields.aniso((12, 80, 96), seed=2), {"frozen_dim": 0, "paradigm": 1}),
+                  (fields.grf((70, 64, 45), seed=5), {"blockmap": bm})):
+        xd = torch.from_numpy(x).cuda()
+        buf, size = ctx.compress(xd, 1e-3, hpez.HPEZ_EB_REL, hpez.make_config(x.ndim, **kw))
+        cases.append((x, buf, size))
+    blockwise = 0
+    for x, buf, size in cases:
+        hdr = buf[:512].cpu().numpy().tobytes()
+        blockwise += int.from_bytes(hdr[212:216], "little")
+        ref = ctx.decompress(buf, size).cpu().numpy()
+        for _ in range(2):
+            got = _noalloc(buf, size, x.shape).cpu().numpy()
+            assert got.tobytes() == ref.tobytes()
+    assert blockwise >= 2  # block maps were among the streams
+
+
+def test_noalloc_refuses_global_spline_streams(ctx):
+    """A stream with a global natural-spline level is hpez_decompress's
+    only."""
+    import torch
+    from paper_2311_12133_gb300 import fields, hpez
+    x = torch.from_numpy(fields.grf((40, 40, 40), seed=8)).cuda()
+    buf, size = ctx.compress(x, 1e-3, 1, hpez.make_config(3, interp=hpez.HPEZ_SPLINE_GLOBAL))
+    out = torch.empty_like(x)
+    with pytest.raises(hpez.HpezError) as e:
+        hpez.hpez_decompress_noalloc(buf.data_ptr(), size, out.data_ptr(), out.numel(),
+                                     torch.cuda.current_stream().cuda_stream)
+    assert e.value.code == -8
+
+
 def test_noalloc_refuses_fields_beyond_its_scratch(ctx):
     import torch
     from paper_2311_12133_gb300 import fields, hpez
