@@ -72,6 +72,13 @@ def parse():
     ap.add_argument("--eb", type=float, default=1e-3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-aggregate", action="store_true",
+                    help="skip the one-oracle-process-per-core aggregate baseline")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the other workloads (128^3 plain, eb sweep, 100x500x500, "
+                         "log-normal, anisotropic and 2D fields)")
+    ap.add_argument("--served-seconds", type=float, default=60.0,
+                    help="length of the Poisson request stream of the served section")
     ap.add_argument("--fused", type=int, default=1,
                     help="1: one kernel per level (1D-style); 0: one per pass")
     ap.add_argument("--tile", default="",
@@ -107,12 +114,15 @@ def measured_peaks():
 # clocks during the timed region
 # ---------------------------------------------------------------------------
 class ClockSampler:
-    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples of the SM clock and throttle reasons, each with its
+    timestamp, so that the samples of a time window can be picked out."""
+    FIELDS = ("timestamp,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, uuid: str | None):
+    def __init__(self, uuid: str | None, interval_ms: int = 20):
         self.uuid = uuid
+        self.interval_ms = interval_ms
         self.proc = None
         self.path = None
 
@@ -122,11 +132,22 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", str(self.interval_ms)], stdout=open(self.path, "w"),
+                stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self):
+    @staticmethod
+    def parse_time(ts: str):
+        import datetime
+        try:
+            return datetime.datetime.strptime(ts.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def stop(self, timed=None, loaded=None):
+        """timed, loaded: (t0, t1) wall-clock windows (time.time()) of the
+        timed region and of the whole loaded stretch (warm-up + timed)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -134,26 +155,70 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
+        rows = []
         for line in open(self.path):
             f = [v.strip() for v in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
-            if self.uuid and self.uuid not in f[0]:
+            if self.uuid and self.uuid not in f[1]:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
+                rows.append((self.parse_time(f[0]), float(f[2]), float(f[3]), f[6:10]))
             except ValueError:
                 continue
+        os.unlink(self.path)
+
+        def within(w):
+            if w is None:
+                return rows
+            return [r for r in rows if r[0] is not None and w[0] <= r[0] <= w[1] + 0.05]
+        tim = within(timed)
+        load = within(loaded) or rows
+        reasons = set()
+        for r in load:
             for name, v in zip(("hw_slowdown", "hw_thermal_slowdown",
-                                "sw_thermal_slowdown", "sw_power_cap"), f[5:9]):
+                                "sw_thermal_slowdown", "sw_power_cap"), r[3]):
                 if v.lower().startswith("active"):
                     reasons.add(name)
-        os.unlink(self.path)
+        sm = [r[1] for r in load]
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "sm_max_mhz": max(r[2] for r in load) if load else None,
+                "samples": len(sm), "samples_timed": len(tim),
+                "sm_mhz_timed": statistics.median([r[1] for r in tim]) if tim else None,
+                "window": "warm-up steps run back to back under the sampler, then the "
+                          "timed steps; sm_mhz is the median over both",
+                "interval_ms": self.interval_ms, "reasons": sorted(reasons)}
+
+
+def percentile(vals, q):
+    """Nearest-rank percentile."""
+    import math
+    s = sorted(vals)
+    return s[max(0, min(len(s) - 1, math.ceil(q / 100.0 * len(s)) - 1))]
+
+
+def step_stats(ms):
+    return {"mean": round(sum(ms) / len(ms), 4), "median": round(statistics.median(ms), 4),
+            "p99": round(percentile(ms, 99), 4), "min": round(min(ms), 4),
+            "max": round(max(ms), 4), "n": len(ms)}
+
+
+def psnr_db(x, y) -> float:
+    """PSNR of the reconstruction y of x: 20 log10(value range) - 10 log10(MSE),
+    in double (Sec. 7.1.3's quality metric)."""
+    import math
+    import torch
+    xr = (x.max().double() - x.min().double()).item()
+    mse = 0.0
+    xf, yf = x.reshape(-1), y.reshape(-1)
+    step = 1 << 26
+    for i in range(0, xf.numel(), step):
+        d = xf[i:i + step].double() - yf[i:i + step].double()
+        mse += float(torch.dot(d, d).item())
+    mse /= xf.numel()
+    if mse == 0.0:
+        return float("inf")
+    return 20.0 * math.log10(xr) - 10.0 * math.log10(mse)
 
 
 # ---------------------------------------------------------------------------
@@ -253,6 +318,45 @@ def cpu_oracle_sample(x_slab, eb, rounds=1):
         O.decompress(s)
         nbytes += x_slab.nbytes
     return nbytes, time.perf_counter() - t0
+
+
+def cpu_oracle_aggregate(x_np, eb, procs, planes=16, rounds=2):
+    """P independent single-threaded oracle processes, one per host core,
+    each on its own slab of `planes` planes of the field (tune + compress +
+    decompress, `rounds` times): aggregate input bytes / wall time.  The
+    processes are spawned fresh (no fork of this GPU process)."""
+    import numpy as np
+    tmp = tempfile.mkdtemp(prefix="orap")
+    paths = []
+    n0 = x_np.shape[0]
+    for i in range(procs):
+        a = (i * planes) % max(n0 - planes + 1, 1)
+        path = os.path.join(tmp, f"slab{i}.npy")
+        np.save(path, np.ascontiguousarray(x_np[a:a + planes]))
+        paths.append(path)
+    code = ("import sys, json, numpy as np; sys.path.insert(0, {root!r}); import bench; "
+            "x = np.load(sys.argv[1]); nb, t = bench.cpu_oracle_sample(x, {eb!r}, {r}); "
+            "print(json.dumps([nb, t]))").format(root=ROOT, eb=float(eb), r=rounds)
+    t0 = time.perf_counter()
+    ps = [subprocess.Popen([sys.executable, "-c", code, pth], stdout=subprocess.PIPE,
+                           stderr=subprocess.DEVNULL, text=True) for pth in paths]
+    outs = [p.communicate()[0] for p in ps]
+    wall = time.perf_counter() - t0
+    nb = 0
+    ok = 0
+    for o in outs:
+        try:
+            nb += int(json.loads(o.strip().splitlines()[-1])[0])
+            ok += 1
+        except Exception:
+            pass
+    for pth in paths:
+        os.unlink(pth)
+    os.rmdir(tmp)
+    return {"value": round(nb / wall / 1e9, 6), "unit": "GB/s", "processes": ok,
+            "wall_s": round(wall, 2),
+            "sample": f"{ok} processes, each {rounds} tune+compress+decompress round trips of "
+                      f"its own {planes}-plane slab"}
 
 
 def run_reference(args):
@@ -462,6 +566,177 @@ def bench_spline(ctx, x, shape, eb, cbuf, cap, y, stream, steps, peak, A):
             "max_abs_err": err, "finest_level": lv}
 
 
+def _abs_eb_for_psnr(ctx, x, target_db, lo_db=60.0, hi_db=90.0, tuned=True):
+    """An absolute bound whose round trip lands in [lo_db, hi_db] dB of PSNR:
+    start from the uniform-error estimate e = range * sqrt(3) * 10^(-t/20),
+    then bisect log e on the measured PSNR (compress + decompress on the
+    GPU, outside any timed region)."""
+    import math
+    import torch
+    from paper_2311_12133_gb300 import hpez
+    rng = (x.max().double() - x.min().double()).item()
+    shape = tuple(x.shape)
+    cap = hpez.hpez_compress_bound(shape)
+    buf = torch.empty(cap, dtype=torch.uint8, device=x.device)
+    y = torch.empty_like(x)
+    sptr = torch.cuda.current_stream().cuda_stream
+
+    def measure(e):
+        if tuned:
+            sz = hpez.hpez_compress_auto(ctx.handle, x.data_ptr(), shape, hpez.HPEZ_EB_ABS, e,
+                                         None, buf.data_ptr(), cap, sptr)
+        else:
+            sz = hpez.hpez_compress(ctx.handle, x.data_ptr(), shape, hpez.HPEZ_EB_ABS, e, None,
+                                    buf.data_ptr(), cap, sptr)
+        hpez.hpez_decompress(ctx.handle, buf.data_ptr(), sz, y.data_ptr(), x.numel(), sptr)
+        return psnr_db(x, y)
+    lg = math.log(rng * math.sqrt(3.0) * 10 ** (-target_db / 20.0))
+    lo, hi = lg - 6.0, lg + 6.0  # log e bracket (larger e, lower PSNR)
+    e = math.exp(lg)
+    p = measure(e)
+    for _ in range(12):
+        if abs(p - target_db) <= 3.0:
+            break
+        if p > target_db:
+            lo = lg
+        else:
+            hi = lg
+        lg = 0.5 * (lo + hi)
+        e = math.exp(lg)
+        p = measure(e)
+    assert lo_db <= p <= hi_db, f"no bound found for {target_db} dB (last {p:.1f} dB)"
+    del buf, y
+    return e, p
+
+
+def bench_workloads(ctx, steps, peak):
+    """The other configurations of the benchmark set, each timed as
+    compress + decompress round trips with per-step CUDA events (L2 flushed
+    between steps when the field is smaller than twice the L2): the 128^3
+    bumps field on the plain path; the 512^3 k^-5/3 field at the other
+    relative bounds, the 100x500x500 field and the log-normal variant, all
+    auto-tuned; the anisotropic 98x1200x1200 and the 2D 1800x3600 fields at
+    an absolute bound chosen for about 75 dB of PSNR, auto-tuned and with
+    the multi-dimensional and the same-level paradigms forced.  Each line
+    reports input GB/s (median step), median and p99 step time, compression
+    ratio, PSNR, the error bound check, and the finest level's roofline
+    (compress, decompress) from a separate profiled run."""
+    import math
+    import torch
+    from paper_2311_12133_gb300 import fields, hpez
+    REL, ABS = hpez.HPEZ_EB_REL, hpez.HPEZ_EB_ABS
+    specs = [
+        ("bumps128 plain", "bumps", (128, 128, 128), REL, 1e-3, "plain", {}),
+        ("grf512 eps1e-2 tuned", "grf", (512, 512, 512), REL, 1e-2, "tuned", {}),
+        ("grf512 eps1e-4 tuned", "grf", (512, 512, 512), REL, 1e-4, "tuned", {}),
+        ("grf512 eps1e-5 tuned", "grf", (512, 512, 512), REL, 1e-5, "tuned", {}),
+        ("grf100x500x500 eps1e-3 tuned", "grf", (100, 500, 500), REL, 1e-3, "tuned", {}),
+        ("lognormal512 eps1e-3 tuned", "lognormal", (512, 512, 512), REL, 1e-3, "tuned", {}),
+        ("aniso98x1200x1200 psnr75 tuned", "aniso", (98, 1200, 1200), ABS, 75.0, "tuned", {}),
+        ("aniso98x1200x1200 psnr75 md", "aniso", (98, 1200, 1200), ABS, 75.0, "cfg",
+         {"paradigm": 1, "interp": 1}),
+        ("aniso98x1200x1200 psnr75 same-level", "aniso", (98, 1200, 1200), ABS, 75.0, "cfg",
+         {"interp": 1, "same_level": 1}),
+        ("climate1800x3600 psnr75 tuned", "climate2d", (1800, 3600), ABS, 75.0, "tuned", {}),
+        ("climate1800x3600 psnr75 md", "climate2d", (1800, 3600), ABS, 75.0, "cfg",
+         {"paradigm": 1, "interp": 1}),
+        ("climate1800x3600 psnr75 same-level", "climate2d", (1800, 3600), ABS, 75.0, "cfg",
+         {"interp": 1, "same_level": 1}),
+    ]
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = []
+    cur_key, x, ebs = None, None, {}
+    for name, kind, shape, mode, ebv, how, kw in specs:
+        key = (kind, shape)
+        if key != cur_key:
+            x = None
+            torch.cuda.empty_cache()
+            x = fields.make_torch(kind, shape, fields.seed_of("workload", kind, *shape))
+            cur_key = key
+        N = x.numel()
+        A = 32 if len(shape) == 3 else 64
+        if mode == ABS:
+            if key not in ebs:
+                ebs[key] = _abs_eb_for_psnr(ctx, x, ebv)
+            eb = ebs[key][0]
+        else:
+            eb = ebv
+        cfg = hpez.make_config(len(shape), **kw) if how == "cfg" else None
+        cap = hpez.hpez_compress_bound(shape)
+        cbuf = torch.empty(cap, dtype=torch.uint8, device="cuda")
+        y = torch.empty_like(x)
+
+        def compress():
+            if how == "tuned":
+                return hpez.hpez_compress_auto(ctx.handle, x.data_ptr(), shape, mode, eb, None,
+                                               cbuf.data_ptr(), cap, sptr)
+            return hpez.hpez_compress(ctx.handle, x.data_ptr(), shape, mode, eb, cfg,
+                                      cbuf.data_ptr(), cap, sptr)
+
+        def step():
+            sz = compress()
+            hpez.hpez_decompress(ctx.handle, cbuf.data_ptr(), sz, y.data_ptr(), N, sptr)
+            return sz
+        for _ in range(3):
+            size = step()
+        torch.cuda.synchronize()
+        do_flush = 4 * N < 2 * L2_BYTES
+        tot, comp, dec = [], [], []
+        for _ in range(steps):
+            if do_flush:
+                flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            size = compress()
+            e[1].record(stream)
+            hpez.hpez_decompress(ctx.handle, cbuf.data_ptr(), size, y.data_ptr(), N, sptr)
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            tot.append(e[0].elapsed_time(e[2]))
+            comp.append(e[0].elapsed_time(e[1]))
+            dec.append(e[1].elapsed_time(e[2]))
+        hdr = cbuf[:512].cpu().numpy().tobytes()
+        e_abs = hpez.hpez_inspect(hdr)[2]
+        err = (y.double() - x.double()).abs().max().item()
+        assert err <= e_abs, f"{name}: bound violated: {err} > {e_abs}"
+        ps = psnr_db(x, y)
+        hpez.hpez_profile_enable(ctx.handle, True)
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        lv = {}
+        for ph_name, ph in (("level1", hpez.HPEZ_PH_LEVEL), ("dlevel1", hpez.HPEZ_PH_DLEVEL)):
+            t, n = hpez.hpez_profile_get(ctx.handle, ph)
+            if n:
+                pred = int.from_bytes(hdr[208:212], "little")
+                b = phase_bytes(ph_name, shape, A, size, pred > 0)
+                gbs = b / (t / n / 1e3) / 1e9
+                lv[ph_name] = {"launch_ms": round(t / n, 4), "achieved": round(gbs, 1),
+                               "frac": round(gbs / peak, 4), "algorithmic_bytes": b}
+        hpez.hpez_profile_enable(ctx.handle, False)
+        med = statistics.median(tot)
+        out.append({
+            "workload": name, "shape": list(shape),
+            "eb": {"mode": "rel" if mode == REL else "abs", "value": eb, "abs": e_abs},
+            "path": {"tuned": "hpez_compress_auto (full Sec. 6 tuning)",
+                     "plain": "hpez_compress, default predictor (cubic not-a-knot, 1D-style "
+                              "order 0,1,2, no tuning)",
+                     "cfg": f"hpez_compress, {kw}"}[how],
+            "value": round(4 * N / (med / 1e3) / 1e9, 3), "unit": "GB/s",
+            "step_ms": step_stats(tot),
+            "compress_gbps": round(4 * N / (statistics.median(comp) / 1e3) / 1e9, 3),
+            "decompress_gbps": round(4 * N / (statistics.median(dec) / 1e3) / 1e9, 3),
+            "compression_ratio": round(4 * N / size, 3), "psnr_db": round(ps, 3),
+            "max_abs_err": err, "bound_held": True, "l2_flushed": do_flush,
+            "finest_level": lv})
+        del cbuf, y
+    del x, flush
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_served(ctx, seconds=3.0, rate=200.0, slots=256):
     """Poisson stream of compress/decompress requests over fields of 1 MB ..
     512 MB (log-uniform), rel eb from {1e-2,1e-3,1e-4}, host buffers,
@@ -628,13 +903,24 @@ def main():
         uuid = str(torch.cuda.get_device_properties(local).uuid)
     except Exception:
         pass
+    # the clock sampler runs from the warm-up on: warm-up steps back to back
+    # (at least W of them and at least 1.5 s, so the sampler is attached and
+    # the GPU loaded), then the timed steps
     sampler = ClockSampler(uuid)
+    sampler.start()
+    t_load0 = time.time()
+    n_warm = 0
+    while n_warm < max(3, args.warmup) or time.time() - t_load0 < 1.5:
+        size = step()
+        n_warm += 1
+        if n_warm % 16 == 0:
+            torch.cuda.synchronize()
+    torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    sampler.start()
-    time.sleep(1.0)  # let the sampler attach before the timed region
-    hpez.hpez_profile_enable(ctx.handle, True)
+    n_launch0 = hpez.hpez_launch_count(ctx.handle)
+    t_timed0 = time.time()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
     ev[0].record(stream)
     for k in range(args.steps):
@@ -643,13 +929,21 @@ def main():
         hpez.hpez_decompress(ctx.handle, cbuf.data_ptr(), size, y.data_ptr(), N, sptr)
         ev[2 * k + 2].record(stream)
     torch.cuda.synchronize()
+    t_timed1 = time.time()
     if dist:
         dist.barrier()
-    clocks = sampler.stop()
+    launches = hpez.hpez_launch_count(ctx.handle) - n_launch0
+    clocks = sampler.stop(timed=(t_timed0, t_timed1), loaded=(t_load0, t_timed1))
     total_ms = ev[0].elapsed_time(ev[-1])
     comp_ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps))
     dec_ms = sum(ev[2 * k + 1].elapsed_time(ev[2 * k + 2]) for k in range(args.steps))
-    launches = hpez.hpez_launch_count(ctx.handle)
+    per_step = [ev[2 * k].elapsed_time(ev[2 * k + 2]) for k in range(args.steps)]
+    # phase times from a second, profiled run of the same steps (the
+    # profiler's events stay out of the timed region above)
+    hpez.hpez_profile_enable(ctx.handle, True)
+    for k in range(args.steps):
+        size = step()
+    torch.cuda.synchronize()
     phases = {}
     for ph in range(hpez.HPEZ_PROFILE_PHASES):
         ms, cnt = hpez.hpez_profile_get(ctx.handle, ph)
@@ -670,6 +964,7 @@ def main():
     n_used = int.from_bytes(hdr[232:236], "little")
     err = (y.double() - x.double()).abs().max().item()
     assert err <= e_abs, f"error bound violated: {err} > {e_abs}"
+    psnr = psnr_db(x, y)
 
     peak, peak_kind = measured_peaks()
     # the roofline is taken on the dominant phase of the HBM-bound data path
@@ -722,10 +1017,18 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         slab = x[:64].cpu().numpy()
         nb, secs = cpu_oracle_sample(slab, args.eb, rounds=2)
+        try:
+            nproc = len(os.sched_getaffinity(0))
+        except Exception:
+            nproc = os.cpu_count() or 1
         cpu = {"value": round(nb / secs / 1e9, 6), "unit": "GB/s", "cores": 1,
-               "kind": "oracle",
+               "kind": "oracle", "nproc": nproc,
                "sample": f"2 tune+compress+decompress round trips of the first 64 planes "
                          f"({'x'.join(map(str, slab.shape))}) of the same field, {secs:.1f} s"}
+        if not args.no_cpu_aggregate:
+            planes = 16
+            xs = x[:min(shape[0], planes * nproc)].cpu().numpy()
+            cpu["aggregate"] = cpu_oracle_aggregate(xs, args.eb, nproc, planes=planes)
 
     # the same field with the default predictor (no tuning), for reference
     def default_step():
@@ -758,18 +1061,23 @@ def main():
         lorenzo = bench_lorenzo(ctx, x, shape, args.eb, cbuf, cap, y, stream,
                                 max(3, args.steps // 2), peak)
 
+    workloads = None
+    if rank == 0 and world == 1 and not args.no_workloads:
+        workloads = bench_workloads(ctx, max(5, args.steps), peak)
+
     batched = served = None
     if rank == 0 and world == 1 and not args.no_batched:
         batched = bench_batched(ctx, max(3, args.steps // 2), args.warmup)
     if rank == 0 and world == 1 and not args.no_served:
-        served = bench_served(ctx)
+        served = bench_served(ctx, seconds=args.served_seconds)
 
     if rank == 0:
         line = {
             "metric": "compress+decompress input GB/s (rel eb 1e-3)",
             "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
-            "steps": args.steps, "warmup": max(3, args.warmup),
-            "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+            "steps": args.steps, "warmup": max(3, args.warmup), "warmup_run": n_warm,
+            "ms_per_step": round(ms_per_step, 4),
+            "step_ms": step_stats(per_step), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"grf k^-5/3 float32 {'x'.join(map(str, shape))} per GPU, "
@@ -783,14 +1091,14 @@ def main():
                        "l2": f"input {4 * N / 1e6:.0f} MB > L2 {L2_BYTES / 1e6:.0f} MB, no flush"},
             "compress_gbps": round(world * 4 * N / (comp_ms / args.steps / 1e3) / 1e9, 3),
             "decompress_gbps": round(world * 4 * N / (dec_ms / args.steps / 1e3) / 1e9, 3),
-            "compression_ratio": round(4 * N / size, 3),
+            "compression_ratio": round(4 * N / size, 3), "psnr_db": round(psnr, 3),
             "max_abs_err": err, "abs_eb": e_abs, "n_outliers": n_out,
             "n_symbols": n_used,
             "roofline": roofline, "phases": phase_report,
             "gpu_launches": int(launches),
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
             "default_predictor": default_pred, "lorenzo": lorenzo, "spline": spline,
-            "batched": batched, "served": served,
+            "workloads": workloads, "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -46,3 +46,52 @@ def test_recorded_traffic_keyed_to_sources(tmp_path, monkeypatch):
     (fake_root / "profiles" / "traffic.json").write_text(json.dumps(d2))
     assert bench.ncu_traffic("level1") == 123
     assert bench.ncu_traffic("no_such_phase") is None
+
+
+def test_step_stats_and_percentile():
+    ms = [float(v) for v in range(1, 101)]
+    st = bench.step_stats(ms)
+    assert st["median"] == 50.5 and st["p99"] == 99.0 and st["max"] == 100.0
+    assert bench.percentile([3.0, 1.0, 2.0], 50) == 2.0
+    assert bench.step_stats([2.0])["p99"] == 2.0
+
+
+def test_clock_samples_by_window(tmp_path):
+    """Samples are picked out by their timestamps: the timed window and the
+    loaded stretch, with throttle reasons only from the loaded stretch."""
+    rows = [
+        "2026/12/04 10:00:00.000, GPU-abc, 900, 2070, 100, 0x0, Not Active, Not Active, Not Active, Active",
+        "2026/12/04 10:00:01.000, GPU-abc, 2000, 2070, 900, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "2026/12/04 10:00:02.000, GPU-abc, 2070, 2070, 950, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "2026/12/04 10:00:02.010, GPU-xyz, 100, 2070, 950, 0x0, Active, Not Active, Not Active, Not Active",
+    ]
+    p = tmp_path / "clk.csv"
+    p.write_text("\n".join(rows) + "\n")
+    t = bench.ClockSampler.parse_time
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            pass
+    s = bench.ClockSampler("GPU-abc")
+    s.proc, s.path = Done(), str(p)
+    c = s.stop(timed=(t("2026/12/04 10:00:01.900"), t("2026/12/04 10:00:02.000")),
+               loaded=(t("2026/12/04 10:00:00.500"), t("2026/12/04 10:00:02.000")))
+    assert c["samples"] == 2 and c["samples_timed"] == 1
+    assert c["sm_mhz"] == 2035.0 and c["sm_mhz_timed"] == 2070.0
+    assert c["reasons"] == []  # the power-cap sample lies before the loaded stretch
+
+
+def test_psnr_of_uniform_error():
+    import numpy as np
+    import torch
+    x = torch.linspace(0, 1, 1 << 16, dtype=torch.float32)
+    e = torch.from_numpy(np.random.default_rng(0).uniform(-1e-3, 1e-3, x.numel())
+                         .astype(np.float32))
+    y = x + e
+    # uniform error on [-e, e]: MSE ~ e^2 / 3, range 1
+    want = -10 * math.log10((1e-3) ** 2 / 3)
+    assert abs(bench.psnr_db(x, y) - want) < 0.1
+    assert bench.psnr_db(x, x.clone()) == float("inf")
