@@ -268,8 +268,8 @@ def phase_bytes(name: str, shape, A, comp_size: int, lorenzo: bool = False) -> i
 # the sources each phase's kernels are built from: a recorded DRAM traffic
 # figure holds while these files are unchanged
 PHASE_SOURCES = {
-    "level1": ("k_level_md3.cu", "hpez_internal.cuh"),
-    "dlevel1": ("k_level_md3.cu", "hpez_internal.cuh"),
+    "level1": ("k_level_md3.cu", "k_level_md3w.cu", "hpez_internal.cuh"),
+    "dlevel1": ("k_level_md3.cu", "k_level_md3w.cu", "hpez_internal.cuh"),
     "decode": ("k_huffman.cu", "hpez_internal.cuh"),
     "pack": ("k_huffman.cu", "hpez_internal.cuh"),
     "hist": ("k_huffman.cu", "hpez_internal.cuh"),

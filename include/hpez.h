@@ -398,10 +398,15 @@ HPEZ_API int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim,
  *                         its wait for them expires and the call returns
  *                         HPEZ_ERR_TIMEOUT (no copy stays in flight; the
  *                         context stays usable)
+ *  HPEZ_OPT_WARP_LEVELS   1 (default): the finest 3D level of the
+ *                         multi-dimensional paradigm runs one warp per strip
+ *                         of rows and columns (rows of an even number of
+ *                         points); 0: the streamed or two-launch kernels
  *  HPEZ_OPT_STREAM_CHUNKS 0 (default: as many chunks of planes as fill the
- *                         resident CTAs); n > 0: the streamed finest level
- *                         cuts dim 0 into n chunks, so a CTA walks more planes
- *                         through its ring (what a large field does)
+ *                         resident warps); n > 0: the finest-level kernels
+ *                         cut dim 0 into n chunks, so a warp or CTA walks
+ *                         more planes through its ring (what a large field
+ *                         does)
  *  HPEZ_OPT_LORENZO_CTAS  0 (default: the resident CTAs); n > 0: at most n
  *                         persistent CTAs for the Lorenzo kernels, so each
  *                         streams more blocks back to back
@@ -416,6 +421,7 @@ HPEZ_API int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim,
 #define HPEZ_OPT_DROP_COPY 8
 #define HPEZ_OPT_STREAM_CHUNKS 9
 #define HPEZ_OPT_LORENZO_CTAS 10
+#define HPEZ_OPT_WARP_LEVELS 11
 HPEZ_API int hpez_set_option(hpez_ctx* ctx, int option, int64_t value);
 
 /* ---- measurement hooks (not part of the paper's method) ----

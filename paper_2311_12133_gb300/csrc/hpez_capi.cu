@@ -738,6 +738,9 @@ int hpez_set_option(hpez_ctx* ctx, int option, int64_t value) {
       if (value < 0 || value > 1000000) return HPEZ_ERR_INVALID_ARG;
       ctx->drop_copy = (int)value;
       return HPEZ_OK;
+    case HPEZ_OPT_WARP_LEVELS:
+      ctx->warp_levels = value != 0;
+      return HPEZ_OK;
     case HPEZ_OPT_STREAM_CHUNKS:
       if (value < 0 || value > 1000000) return HPEZ_ERR_INVALID_ARG;
       ctx->stream_chunks = (int)value;
@@ -878,7 +881,9 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   size_t o_R[kMaxLevels + 1], o_C[kMaxLevels + 1];
   for (int g = 0; g <= p.L; ++g) {
     o_R[g] = ar.take<float>(p.gsize[g]);
-    o_C[g] = ar.take<uint16_t>(p.gsize[g]);
+    // two spare codes: kernels may read a code as the aligned 4-byte word
+    // that holds it
+    o_C[g] = ar.take<uint16_t>(p.gsize[g] + 2);
   }
   const size_t o_zc = ar.take<uint32_t>(p.nch);
   const size_t o_zoff = ar.take<unsigned long long>(p.nch);
@@ -980,7 +985,12 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
       launch_level3d(false, F3, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g], s);
       ++nl;
     } else if (!spline && plan_md3(ctx, p, sc, l, false, FM, E1)) {
-      if (ctx->stream_levels && md3s_supported(FM, false, d_in, b.R[l], b.Cg[l]) &&
+      if (ctx->warp_levels &&
+          md3w_supported(FM, false, d_in, b.R[l], b.Cg[l], b.R[g], b.Cg[g])) {
+        launch_level_md3w(false, sb.kind, FM, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g], b.ctl,
+                          ctx->num_sms, ctx->stream_chunks, s);
+        ++nl;
+      } else if (ctx->stream_levels && md3s_supported(FM, false, d_in, b.R[l], b.Cg[l]) &&
           launch_level_md3s(false, sb.kind, FM, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g],
                             b.ctl, ctx->num_sms, ctx->drop_copy, ctx->stream_chunks, s)) {
         ++nl;
@@ -1220,7 +1230,11 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
       launch_level3d(true, F3, sb, R[l], nullptr, R[g], nullptr, s);
       ++nl;
     } else if (!spline && plan_md3(ctx, p, sc, l, true, FM, E1)) {
-      if (ctx->stream_levels && md3s_supported(FM, true, codes, R[l], nullptr) &&
+      if (ctx->warp_levels && md3w_supported(FM, true, codes, R[l], nullptr, R[g], nullptr)) {
+        launch_level_md3w(true, sb.kind, FM, sb, R[l], nullptr, R[g], nullptr, ctl,
+                          ctx->num_sms, ctx->stream_chunks, s);
+        ++nl;
+      } else if (ctx->stream_levels && md3s_supported(FM, true, codes, R[l], nullptr) &&
           launch_level_md3s(true, sb.kind, FM, sb, R[l], nullptr, R[g], nullptr, ctl,
                             ctx->num_sms, ctx->drop_copy, ctx->stream_chunks, s)) {
         ++nl;

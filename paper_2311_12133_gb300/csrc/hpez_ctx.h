@@ -75,6 +75,7 @@ struct hpez_ctx {
   int fused_levels = 1;        // HPEZ_OPT_FUSED_LEVELS
   int level3d = 1;             // HPEZ_OPT_LEVEL3D
   int stream_levels = 1;       // HPEZ_OPT_STREAM_LEVELS
+  int warp_levels = 1;         // HPEZ_OPT_WARP_LEVELS
   int drop_copy = 0;           // HPEZ_OPT_DROP_COPY
   int stream_chunks = 0;       // HPEZ_OPT_STREAM_CHUNKS (0 = heuristic)
   int lorenzo_ctas = 0;        // HPEZ_OPT_LORENZO_CTAS (0 = resident CTAs)

@@ -54,6 +54,13 @@ int launch_level_md3s(bool decomp, int kind, const LevelMD& P, const SweepBufs& 
                       const float* Rc, const uint16_t* Cc, float* Rs, uint16_t* Cs,
                       Ctl* ctl, int num_sms, int drop_copy, int chunks, cudaStream_t s);
 
+// k_level_md3w.cu
+bool md3w_supported(const LevelMD& P, bool decomp, const void* in, const float* Rc,
+                    const uint16_t* Cc, const float* Rs, const uint16_t* Cs);
+int launch_level_md3w(bool decomp, int kind, const LevelMD& P, const SweepBufs& B,
+                      const float* Rc, const uint16_t* Cc, float* Rs, uint16_t* Cs,
+                      const Ctl* ctl, int num_sms, int chunks, cudaStream_t s);
+
 // k_spline.cu
 void launch_spline_pass(bool decomp, const LevelGeom& g, const PassBox& pb, const SweepBufs& B,
                         float* dscr, int num_sms, cudaStream_t s);

@@ -362,7 +362,7 @@ HPEZ_OPT_FUSED_LEVELS, HPEZ_OPT_TILE_E0, HPEZ_OPT_TILE_E1 = 1, 2, 3
 HPEZ_OPT_TILE_E2, HPEZ_OPT_FUSED_SMEM, HPEZ_OPT_LEVEL3D = 4, 5, 6
 HPEZ_OPT_STREAM_LEVELS = 7
 HPEZ_OPT_DROP_COPY = 8
-HPEZ_OPT_STREAM_CHUNKS, HPEZ_OPT_LORENZO_CTAS = 9, 10
+HPEZ_OPT_STREAM_CHUNKS, HPEZ_OPT_LORENZO_CTAS, HPEZ_OPT_WARP_LEVELS = 9, 10, 11
 
 
 def hpez_set_option(ctx, option: int, value: int) -> None:

@@ -36,6 +36,7 @@ def opts(gpu):
     for o in (hpez.HPEZ_OPT_STREAM_CHUNKS, hpez.HPEZ_OPT_LORENZO_CTAS):
         hpez.hpez_set_option(gpu.handle, o, 0)
     hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_STREAM_LEVELS, 1)
+    hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_WARP_LEVELS, 1)
 
 
 def _first_diff(a: bytes, b: bytes) -> str:
@@ -71,6 +72,7 @@ def test_md_stream_ring_walk(opts, oracle, chunks, shape, interp):
     every mbarrier many times (odd and even plane counts, ragged row and
     column tiles, chunk boundaries inside the field)."""
     from paper_2311_12133_gb300 import fields, hpez
+    hpez.hpez_set_option(opts.handle, hpez.HPEZ_OPT_WARP_LEVELS, 0)
     hpez.hpez_set_option(opts.handle, hpez.HPEZ_OPT_STREAM_CHUNKS, chunks)
     x = fields.grf(shape, seed=sum(shape) + 7 * interp + chunks)
     kw = dict(interp=interp, paradigm=1, md_inv_var=(1.0, 2.5, 0.7))
@@ -92,10 +94,11 @@ def test_md_stream_ring_walk_tuned_config(opts, oracle):
     from paper_2311_12133_gb300 import fields, hpez
     hpez.hpez_set_option(opts.handle, hpez.HPEZ_OPT_STREAM_CHUNKS, 1)
     x = fields.grf((64, 48, 256), seed=5)
-    st = _check(opts, oracle, x, 1e-3, interp=0, paradigm=1)
-    assert st.n_outliers >= 0
-    st = _check(opts, oracle, x, 2e-6, interp=0, paradigm=1)
-    assert st.n_outliers > 0
+    for warp in (1, 0):  # the warp-strip kernel, then the streamed one
+        hpez.hpez_set_option(opts.handle, hpez.HPEZ_OPT_WARP_LEVELS, warp)
+        _check(opts, oracle, x, 1e-3, interp=0, paradigm=1)
+        st = _check(opts, oracle, x, 2e-6, interp=0, paradigm=1)
+        assert st.n_outliers > 0
 
 
 @pytest.mark.parametrize("order", [1, 2])

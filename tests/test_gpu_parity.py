@@ -214,6 +214,8 @@ def opts(gpu):
     hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_FUSED_LEVELS, 1)
     hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_STREAM_LEVELS, 1)
     hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_DROP_COPY, 0)
+    hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_WARP_LEVELS, 1)
+    hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_STREAM_CHUNKS, 0)
     for o in (hpez.HPEZ_OPT_TILE_E0, hpez.HPEZ_OPT_TILE_E1, hpez.HPEZ_OPT_TILE_E2):
         hpez.hpez_set_option(gpu.handle, o, 0)
 
@@ -284,6 +286,7 @@ def test_md_stream_level(opts, oracle, shape, eb, interp):
     more."""
     import torch
     from paper_2311_12133_gb300 import fields, hpez
+    hpez.hpez_set_option(opts.handle, hpez.HPEZ_OPT_WARP_LEVELS, 0)
     x = fields.grf(shape, seed=sum(shape) + interp)
     kw = dict(interp=interp, paradigm=1, md_inv_var=(1.0, 2.5, 0.7))
     _check(opts, oracle, x, eb, 1, **kw)
@@ -311,6 +314,7 @@ def test_bounded_wait_expires(opts, oracle):
     import time
     import torch
     from paper_2311_12133_gb300 import fields, hpez
+    hpez.hpez_set_option(opts.handle, hpez.HPEZ_OPT_WARP_LEVELS, 0)
     x = fields.grf((40, 48, 64), seed=3)
     kw = dict(interp=0, paradigm=1)
     _, gcfg = _pair_configs(3, **kw)
@@ -340,3 +344,34 @@ def test_uniform_blockmap(gpu, oracle, code, paradigm):
     nb = hpez.hpez_blockmap_size(shape, 16)
     _check(gpu, oracle, x, 1e-3, 1, blockmap=np.full(nb, code, np.uint8),
            block_size=16, paradigm=paradigm)
+
+
+@pytest.mark.parametrize("shape", [(48, 64, 256), (49, 40, 128), (50, 17, 144), (9, 70, 136),
+                                   (5, 16, 24), (66, 20, 16), (2, 3, 8), (37, 50, 68),
+                                   (3, 5, 6), (7, 33, 130), (16, 18, 4), (20, 19, 62),
+                                   (11, 2, 120), (30, 50, 500)])
+@pytest.mark.parametrize("interp", [0, 1, 2])
+@pytest.mark.parametrize("chunks", [0, 1, 3])
+def test_md_warp_level(opts, oracle, shape, interp, chunks):
+    """The finest 3D multi-dimensional level with one warp per strip
+    (rows of an even number of points): partial row and column strips, the
+    column strips' halo lanes, short last strips that extrapolate, odd and
+    even plane counts, chunks of planes (one chunk walks every plane);
+    equal to the oracle, and the kernel taken (one launch for the level, two
+    without it)."""
+    import torch
+    from paper_2311_12133_gb300 import fields, hpez
+    hpez.hpez_set_option(opts.handle, hpez.HPEZ_OPT_STREAM_CHUNKS, chunks)
+    x = fields.grf(shape, seed=sum(shape) + 3 * interp + chunks)
+    kw = dict(interp=interp, paradigm=1, md_inv_var=(1.0, 2.5, 0.7))
+    n0 = hpez.hpez_launch_count(opts.handle)
+    _check(opts, oracle, x, 1e-3, 1, **kw)
+    n_warp = hpez.hpez_launch_count(opts.handle) - n0
+    for o in (hpez.HPEZ_OPT_WARP_LEVELS, hpez.HPEZ_OPT_STREAM_LEVELS):
+        hpez.hpez_set_option(opts.handle, o, 0)
+    n0 = hpez.hpez_launch_count(opts.handle)
+    _check(opts, oracle, x, 1e-3, 1, **kw)
+    assert hpez.hpez_launch_count(opts.handle) - n0 >= n_warp + 2
+    hpez.hpez_set_option(opts.handle, hpez.HPEZ_OPT_WARP_LEVELS, 1)
+    # escapes inside the strips
+    _check(opts, oracle, fields.make("lognormal", shape, 2), 1e-6, 1, **kw)
