@@ -737,7 +737,7 @@ def bench_workloads(ctx, steps, peak):
     return out
 
 
-def bench_served(ctx, seconds=3.0, rate=200.0, slots=256):
+def bench_served(ctx, seconds=3.0, rate=200.0, slots=256, pool_size=32):
     """Poisson stream of compress/decompress requests over fields of 1 MB ..
     512 MB (log-uniform), rel eb from {1e-2,1e-3,1e-4}, host buffers,
     40 GB device budget; the served loop against one single-field host call
@@ -749,7 +749,7 @@ def bench_served(ctx, seconds=3.0, rate=200.0, slots=256):
     rng = np.random.default_rng(1)
     kinds3 = ["bumps", "grf", "lognormal", "aniso"]
     pool = []
-    for i in range(12):
+    for i in range(pool_size):
         npts = float(np.exp(rng.uniform(np.log(1 << 20), np.log(512 << 20)))) / 4
         if rng.uniform() < 1 / 3:
             ny = max(8, int(round(np.sqrt(npts / 2))))
@@ -835,7 +835,7 @@ def bench_served(ctx, seconds=3.0, rate=200.0, slots=256):
 
     ours(True)  # warm-up of the served path
     r = {"workload": f"Poisson {rate:g} req/s for {seconds:g} s, {len(arr)} requests "
-                     f"(compress or decompress, 1 MB..512 MB log-uniform, 12-field pool), "
+                     f"(compress or decompress, 1 MB..512 MB log-uniform, {pool_size}-field pool), "
                      f"host buffers, 40 GB budget, {slots} slots",
          "input_GB": round(total / 1e9, 3),
          "poisson": ours(False), "plain_poisson": plain(False),

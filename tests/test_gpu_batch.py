@@ -134,29 +134,35 @@ def test_batch_errors(gpu):
     assert st[0] == 0 and st[2] == 0 and st[1] == -4
 
 
-def test_server_results_equal_single_calls(gpu, oracle):
-    """Requests of mixed size and kind, submitted while others run, under a
-    budget that forces queueing: every result equals the single call's."""
+def _served_mix(gpu, oracle, mix, budget, slots, seed):
+    """Serve every field of `mix` twice (once compressed, once its stream
+    decompressed), submitting a few requests between steps so that later
+    requests join running ones: every result equals the oracle's stream or
+    reconstruction and the single call's."""
     import torch
     from paper_2311_12133_gb300 import hpez
-    mix = _mix(1)
     single = []
     for x, eb, mode, kw in mix:
-        g, _ = _cfgs(x, kw)
+        g, o = _cfgs(x, kw)
+        want, _, _, recon = oracle.compress(x, eb, mode, o, want_recon=True)
         xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
         buf, size = gpu.compress(xd, eb, mode, g)
         s_ = buf[:size].cpu().numpy().tobytes()
-        single.append((s_, gpu.decompress(buf, size).cpu().numpy()))
-    budget = 48 << 20
-    srv = hpez.Server(gpu, budget, max_slots=4)
+        y = gpu.decompress(buf, size).cpu().numpy()
+        assert s_ == want
+        want_y = oracle.decompress(want)
+        assert y.tobytes() == want_y.tobytes()
+        single.append((s_, want_y))
+    srv = hpez.Server(gpu, budget, max_slots=slots)
     pending = {}
     order = list(range(len(mix))) * 2
-    rng = np.random.default_rng(0)
+    rng = np.random.default_rng(seed)
     rng.shuffle(order)
     k = 0
+    served = 0
+    max_active = 0
     while k < len(order) or pending:
-        # submit a few, then step: later requests join running ones
-        for _ in range(int(rng.integers(0, 3))):
+        for _ in range(int(rng.integers(0, 4))):
             if k >= len(order):
                 break
             i = order[k]
@@ -172,6 +178,7 @@ def test_server_results_equal_single_calls(gpu, oracle):
                 pending[rid] = ("d", i, out)
             k += 1
         srv.step()
+        max_active = max(max_active, srv.stats()["active"])
         for rid, st, size, lat in srv.poll():
             kind, i, out = pending.pop(rid)
             assert st == 0, (kind, i, st)
@@ -180,9 +187,43 @@ def test_server_results_equal_single_calls(gpu, oracle):
             else:
                 assert out.tobytes() == single[i][1].tobytes(), i
             assert lat >= 0
+            served += 1
     stats = srv.stats()
     assert stats["active"] == 0 and stats["queued"] == 0 and stats["used_bytes"] == 0
     srv.close()
+    assert served == len(order)
+    return max_active
+
+
+def test_server_results_equal_oracle_under_load(gpu, oracle):
+    """Thirty fields of 0.5-8 MB from the workload generators, rel eb from
+    {1e-2, 1e-3, 1e-4}, served through eight slots under a budget that
+    queues requests: several requests are in flight at once and every
+    served stream and field equals the oracle's."""
+    from paper_2311_12133_gb300 import fields
+    rng = np.random.default_rng(11)
+    mix = []
+    kinds = ["bumps", "grf", "lognormal", "aniso", "climate2d"]
+    for j in range(30):
+        kind = kinds[j % 5]
+        npts = int(np.exp(rng.uniform(np.log(1.3e5), np.log(2.1e6))))
+        if kind == "climate2d":
+            ny = max(16, int(np.sqrt(npts / 2)))
+            shape = (ny, max(16, npts // ny))
+        else:
+            side = max(12, int(round(npts ** (1 / 3))))
+            shape = (side, side + int(rng.integers(-4, 5)), side + int(rng.integers(0, 9)))
+        eb = [1e-2, 1e-3, 1e-4][int(rng.integers(0, 3))]
+        mix.append((fields.make(kind, shape, 40 + j), eb, 1, None))
+    max_active = _served_mix(gpu, oracle, mix, 96 << 20, 8, 3)
+    assert max_active >= 2
+
+
+def test_server_results_equal_single_calls(gpu, oracle):
+    """Requests of mixed size and kind, submitted while others run, under a
+    budget that forces queueing: every result equals the single call's and
+    the oracle's."""
+    _served_mix(gpu, oracle, _mix(1), 48 << 20, 4, 0)
 
 
 def test_server_rejects_oversized(gpu):
