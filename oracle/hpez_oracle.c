@@ -1876,3 +1876,246 @@ int ora_tune(const float* x, int ndim, const uint64_t* dims, int eb_mode,
   }
   return ORA_OK;
 }
+
+/* ================================================================== */
+/* Quality-metric target (Sec. 3.1, Eq. 1 with M = PSNR) and integer    */
+/* inputs.  Both wrap the method above; the arithmetic they add is the  */
+/* metric and the bound search (in double), and the integer widening    */
+/* and rounding.                                                        */
+/* ================================================================== */
+
+int ora_psnr(const float* x, const float* y, uint64_t n, double unit,
+             double* psnr, uint64_t* sse) {
+  if (!x || !y || n == 0 || !(unit > 0.0) || !isfinite(unit)) return ORA_ERR_INVALID_ARG;
+  double vmin = (double)x[0], vmax = (double)x[0];
+  uint64_t acc = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    const double xv = (double)x[i];
+    if (!isfinite(xv)) return ORA_ERR_NONFINITE;
+    if (xv < vmin) vmin = xv;
+    if (xv > vmax) vmax = xv;
+    const double q = rint((xv - (double)y[i]) / unit);
+    if (!(fabs(q) <= 65536.0)) return ORA_ERR_INVALID_ARG;
+    const int64_t iq = (int64_t)q;
+    acc += (uint64_t)(iq * iq);
+  }
+  if (sse) *sse = acc;
+  if (psnr) {
+    if (acc == 0) {
+      *psnr = INFINITY;
+    } else {
+      const double mse = (double)acc * unit * unit / (double)n;
+      *psnr = 20.0 * log10(vmax - vmin) - 10.0 * log10(mse);
+    }
+  }
+  return ORA_OK;
+}
+
+typedef struct {
+  const float* x;
+  int ndim;
+  const uint64_t* dims;
+  const ora_tune_params* tp;
+  uint64_t n, cap;
+  uint8_t* buf;
+  float* y;
+} psnr_probe;
+
+/* one probe of the search: tune + compress at absolute bound e, decompress,
+ * PSNR; the stream stays in p->buf */
+static int probe_psnr(psnr_probe* p, double e, uint64_t* size, double* psnr) {
+  ora_config cfg;
+  uint8_t* bm = (uint8_t*)malloc(ora_blockmap_size(p->ndim, p->dims,
+                                                   p->tp ? p->tp->block_size : 32) + 1);
+  int rc = ora_tune(p->x, p->ndim, p->dims, ORA_EB_ABS, e, p->tp, &cfg, bm,
+                    ora_blockmap_size(p->ndim, p->dims, p->tp ? p->tp->block_size : 32) + 1,
+                    NULL);
+  ora_stats st;
+  if (!rc)
+    rc = ora_compress(p->x, p->ndim, p->dims, ORA_EB_ABS, e, &cfg, p->buf, p->cap, size,
+                      NULL, NULL, &st);
+  free(bm);
+  if (!rc) rc = ora_decompress(p->buf, *size, p->y, p->n);
+  if (!rc) rc = ora_psnr(p->x, p->y, p->n, (double)st.e / 65536.0, psnr, NULL);
+  return rc;
+}
+
+int ora_compress_psnr(const float* x, int ndim, const uint64_t* dims,
+                      double target_db, const ora_tune_params* tp, uint8_t* out,
+                      uint64_t cap, uint64_t* out_size, double* eb_out,
+                      double* psnr_out) {
+  if (!x || !dims || !out || !out_size || ndim < 1 || ndim > 3 || !isfinite(target_db))
+    return ORA_ERR_INVALID_ARG;
+  uint64_t n = 1;
+  for (int d = 0; d < ndim; ++d) n *= dims[d];
+  if (n == 0) return ORA_ERR_INVALID_ARG;
+  double vmin = (double)x[0], vmax = (double)x[0];
+  for (uint64_t i = 0; i < n; ++i) {
+    if (!isfinite(x[i])) return ORA_ERR_NONFINITE;
+    if ((double)x[i] < vmin) vmin = (double)x[i];
+    if ((double)x[i] > vmax) vmax = (double)x[i];
+  }
+  psnr_probe p = {x, ndim, dims, tp, n, ora_compress_bound(ndim, dims), NULL, NULL};
+  p.buf = (uint8_t*)malloc(p.cap);
+  p.y = (float*)malloc(sizeof(float) * n);
+  int rc = ORA_OK;
+  uint64_t size = 0;
+  double ps = 0.0;
+  double lo, hi;
+  const double range = vmax - vmin;
+  /* a constant field: any bound keeps it exact */
+  double e = range > 0.0 ? range * sqrt(3.0) * pow(10.0, -target_db / 20.0) : 1.0;
+  if (!(e > 0.0) || !isfinite(e)) rc = ORA_ERR_INVALID_ARG;
+  int found = 0;
+  if (!rc) rc = probe_psnr(&p, e, &size, &ps);
+  if (!rc && ps >= target_db) {
+    lo = e;
+    hi = 2.0 * e;
+    found = 1;
+    int g;
+    for (g = 0; g < 6 && !rc; ++g) {
+      rc = probe_psnr(&p, hi, &size, &ps);
+      if (rc || ps < target_db) break;
+      lo = hi;
+      hi = 2.0 * hi;
+    }
+    if (!rc && g == 6) hi = 0.0; /* the target holds at every bound tried */
+  } else if (!rc) {
+    hi = e;
+    lo = 0.5 * e;
+    int g;
+    for (g = 0; g < 6 && !rc; ++g) {
+      rc = probe_psnr(&p, lo, &size, &ps);
+      if (rc || ps >= target_db) break;
+      hi = lo;
+      lo = 0.5 * lo;
+    }
+    found = !rc && g < 6;
+    if (!found) hi = 0.0;
+  }
+  if (!rc && hi > 0.0) {
+    for (int it = 0; it < 8 && !rc; ++it) {
+      const double mid = sqrt(lo * hi);
+      rc = probe_psnr(&p, mid, &size, &ps);
+      if (rc) break;
+      if (ps >= target_db)
+        lo = mid;
+      else
+        hi = mid;
+    }
+  }
+  if (!rc) {
+    if (!found) lo = lo * 2.0; /* the smallest bound tried */
+    rc = probe_psnr(&p, lo, &size, &ps);
+  }
+  if (!rc) {
+    if (size > cap) {
+      rc = ORA_ERR_OUT_TOO_SMALL;
+    } else {
+      memcpy(out, p.buf, size);
+      *out_size = size;
+      if (eb_out) *eb_out = lo;
+      if (psnr_out) *psnr_out = ps;
+    }
+  }
+  free(p.buf);
+  free(p.y);
+  return rc;
+}
+
+static int dtype_ok(int dtype) {
+  return dtype == ORA_DTYPE_F32 || dtype == ORA_DTYPE_I16 || dtype == ORA_DTYPE_U16 ||
+         dtype == ORA_DTYPE_I32;
+}
+
+int ora_compress_typed(const void* x, int dtype, int ndim, const uint64_t* dims,
+                       int eb_mode, double eb, const ora_config* cfg, int tune,
+                       const ora_tune_params* tp, uint8_t* out, uint64_t cap,
+                       uint64_t* out_size) {
+  if (!x || !dims || !out || !out_size || ndim < 1 || ndim > 3 || !dtype_ok(dtype))
+    return ORA_ERR_INVALID_ARG;
+  if (eb_mode != ORA_EB_ABS && eb_mode != ORA_EB_REL) return ORA_ERR_INVALID_ARG;
+  uint64_t n = 1;
+  for (int d = 0; d < ndim; ++d) n *= dims[d];
+  if (n == 0) return ORA_ERR_INVALID_ARG;
+  float* xf = (float*)malloc(sizeof(float) * n);
+  double vmin = 0.0, vmax = 0.0;
+  int rc = ORA_OK;
+  for (uint64_t i = 0; i < n && !rc; ++i) {
+    double v;
+    switch (dtype) {
+      case ORA_DTYPE_I16: v = (double)((const int16_t*)x)[i]; break;
+      case ORA_DTYPE_U16: v = (double)((const uint16_t*)x)[i]; break;
+      case ORA_DTYPE_I32:
+        v = (double)((const int32_t*)x)[i];
+        if (fabs(v) > 16777216.0) rc = ORA_ERR_INVALID_ARG;
+        break;
+      default: v = (double)((const float*)x)[i]; break;
+    }
+    xf[i] = (float)v;
+    if (i == 0 || v < vmin) vmin = v;
+    if (i == 0 || v > vmax) vmax = v;
+  }
+  int mode = eb_mode;
+  double e = eb;
+  if (!rc && dtype != ORA_DTYPE_F32) {
+    /* the integer bound and the float bound that keeps the rounded
+     * reconstruction within it */
+    const double ei = eb_mode == ORA_EB_REL ? eb * (vmax - vmin) : eb;
+    if (!(ei >= 0.0) || !isfinite(ei) || ei > 4194304.0) {
+      rc = ORA_ERR_INVALID_ARG;
+    } else {
+      e = (double)nextafterf((float)(floor(ei) + 0.5), 0.0f);
+      mode = ORA_EB_ABS;
+    }
+  }
+  ora_config tc;
+  uint8_t* bm = NULL;
+  if (!rc && tune) {
+    const uint64_t nbm = ora_blockmap_size(ndim, dims, tp ? tp->block_size : 32) + 1;
+    bm = (uint8_t*)malloc(nbm);
+    rc = ora_tune(xf, ndim, dims, mode, e, tp, &tc, bm, nbm, NULL);
+    cfg = &tc;
+  }
+  if (!rc) rc = ora_compress(xf, ndim, dims, mode, e, cfg, out, cap, out_size, NULL, NULL, NULL);
+  if (!rc) put_u32(out, ORA_H_DTYPE, (uint32_t)dtype);
+  free(bm);
+  free(xf);
+  return rc;
+}
+
+int ora_decompress_typed(const uint8_t* in, uint64_t size, void* out, int dtype,
+                         uint64_t cap_elems) {
+  if (!in || !out || !dtype_ok(dtype) || size < ORA_HEADER_BYTES) return ORA_ERR_INVALID_ARG;
+  if ((int)get_u32(in, ORA_H_DTYPE) != dtype) return ORA_ERR_INVALID_ARG;
+  int ndim;
+  uint64_t dims[3];
+  int rc = ora_inspect(in, size, &ndim, dims, NULL);
+  if (rc) return rc;
+  uint64_t n = 1;
+  for (int d = 0; d < ndim; ++d) n *= dims[d];
+  if (n > cap_elems) return ORA_ERR_OUT_TOO_SMALL;
+  float* y = (float*)malloc(sizeof(float) * (n ? n : 1));
+  rc = ora_decompress(in, size, y, n);
+  for (uint64_t i = 0; i < n && !rc; ++i) {
+    float r = rintf(y[i]);
+    switch (dtype) {
+      case ORA_DTYPE_I16:
+        r = fminf(fmaxf(r, -32768.0f), 32767.0f);
+        ((int16_t*)out)[i] = (int16_t)r;
+        break;
+      case ORA_DTYPE_U16:
+        r = fminf(fmaxf(r, 0.0f), 65535.0f);
+        ((uint16_t*)out)[i] = (uint16_t)r;
+        break;
+      case ORA_DTYPE_I32:
+        ((int32_t*)out)[i] = (int32_t)r;
+        break;
+      default:
+        ((float*)out)[i] = y[i];
+        break;
+    }
+  }
+  free(y);
+  return rc;
+}

@@ -155,6 +155,49 @@ int ora_tune(const float* x, int ndim, const uint64_t* dims, int eb_mode,
 /* MD weight of dimension d within the odd-dimension set `mask` (Eq. 14). */
 float ora_md_weight(const double* inv_var, unsigned mask, int d);
 
+/* ---- the quality-metric target (Sec. 3.1, Eq. 1) and integer inputs ---- */
+
+/* PSNR of y against x (Sec. 7.1.3): 20 log10(max x - min x) - 10 log10(MSE).
+ * The squared errors are summed exactly in the fixed-point unit `unit`:
+ * q_i = rint((x_i - y_i) / unit) in double, sse = sum q_i^2 (64-bit
+ * integer), MSE = sse unit^2 / n; +inf when sse = 0.  The caller keeps
+ * |x_i - y_i| / unit <= 2^16 (unit = e / 2^16 for a bound e) and x finite. */
+int ora_psnr(const float* x, const float* y, uint64_t n, double unit,
+             double* psnr, uint64_t* sse);
+
+/* Eq. 1 with M = PSNR and target m0 = target_db: the largest absolute bound
+ * the search below finds whose auto-tuned round trip keeps PSNR >= m0
+ * (the compression ratio grows with the bound).  The search, in double:
+ * e_u = range sqrt(3) 10^(-m0/20) (uniform errors on [-e, e] give exactly
+ * m0); from e_u, double (or halve) up to 6 times to bracket the target;
+ * then 8 geometric bisection steps e = sqrt(lo hi), keeping PSNR(lo) >= m0.
+ * Each probe is ora_tune + ora_compress (absolute bound e) + ora_decompress
+ * + ora_psnr with unit = (float)e / 2^16.  Writes the stream of the final
+ * bound, the bound (eb_out) and its PSNR.  x must be finite. */
+int ora_compress_psnr(const float* x, int ndim, const uint64_t* dims,
+                      double target_db, const ora_tune_params* tp, uint8_t* out,
+                      uint64_t cap, uint64_t* out_size, double* eb_out,
+                      double* psnr_out);
+
+/* Integer inputs (the integer datasets of Sec. 7): int16, uint16 or int32
+ * values (|v| <= 2^24) are widened to binary32 exactly and compressed with
+ * the absolute bound just below floor(e) + 1/2, e the requested bound (REL:
+ * eb (max - min)); decompression rounds to the nearest integer (ties to
+ * even) and clamps to the type's range, so every integer stays within
+ * floor(e) of its input (lossless when e < 1).  The stream records the type
+ * at header byte ORA_H_DTYPE.  tune = 1: auto-tuned (ora_tune), else cfg
+ * (NULL: default). */
+enum { ORA_DTYPE_F32 = 0, ORA_DTYPE_I16 = 1, ORA_DTYPE_U16 = 2, ORA_DTYPE_I32 = 3 };
+#define ORA_H_DTYPE 320
+int ora_compress_typed(const void* x, int dtype, int ndim, const uint64_t* dims,
+                       int eb_mode, double eb, const ora_config* cfg, int tune,
+                       const ora_tune_params* tp, uint8_t* out, uint64_t cap,
+                       uint64_t* out_size);
+/* Decompress an integer (or float) stream into out (cap_elems values of
+ * dtype, which must match the stream's). */
+int ora_decompress_typed(const uint8_t* in, uint64_t size, void* out, int dtype,
+                         uint64_t cap_elems);
+
 #ifdef __cplusplus
 }
 #endif

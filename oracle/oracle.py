@@ -186,6 +186,23 @@ def lib():
                 ctypes.c_void_p, ctypes.c_int, u64p, ctypes.POINTER(Config),
                 ctypes.c_float, ctypes.c_int, ctypes.c_void_p,
                 ctypes.c_void_p, u64p, u64p]
+            L.ora_psnr.restype = ctypes.c_int
+            L.ora_psnr.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                   ctypes.c_double, ctypes.POINTER(ctypes.c_double), u64p]
+            L.ora_compress_psnr.restype = ctypes.c_int
+            L.ora_compress_psnr.argtypes = [
+                ctypes.c_void_p, ctypes.c_int, u64p, ctypes.c_double,
+                ctypes.POINTER(TuneParams), ctypes.c_void_p, ctypes.c_uint64, u64p,
+                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+            L.ora_compress_typed.restype = ctypes.c_int
+            L.ora_compress_typed.argtypes = [
+                ctypes.c_void_p, ctypes.c_int, ctypes.c_int, u64p, ctypes.c_int,
+                ctypes.c_double, ctypes.POINTER(Config), ctypes.c_int,
+                ctypes.POINTER(TuneParams), ctypes.c_void_p, ctypes.c_uint64, u64p]
+            L.ora_decompress_typed.restype = ctypes.c_int
+            L.ora_decompress_typed.argtypes = [ctypes.c_void_p, ctypes.c_uint64,
+                                               ctypes.c_void_p, ctypes.c_int,
+                                               ctypes.c_uint64]
             _lib = L
     return _lib
 
@@ -408,3 +425,73 @@ def subfield_test(xs: np.ndarray, config: Config, e: float, l_stop: int = 1):
     if rc != 0:
         raise OracleError(rc)
     return score, hist, nout.value, na.value
+
+
+# -------------------------------------------- quality target, integer inputs
+DTYPE_F32, DTYPE_I16, DTYPE_U16, DTYPE_I32 = 0, 1, 2, 3
+H_DTYPE = 320
+_DT = {DTYPE_F32: np.float32, DTYPE_I16: np.int16, DTYPE_U16: np.uint16,
+       DTYPE_I32: np.int32}
+
+
+def psnr(x: np.ndarray, y: np.ndarray, unit: float):
+    """(PSNR in dB, fixed-point squared-error sum) of y against x."""
+    x = np.ascontiguousarray(x, dtype=np.float32).ravel()
+    y = np.ascontiguousarray(y, dtype=np.float32).ravel()
+    out = ctypes.c_double(0)
+    sse = ctypes.c_uint64(0)
+    rc = lib().ora_psnr(x.ctypes.data, y.ctypes.data, x.size, float(unit),
+                        ctypes.byref(out), ctypes.byref(sse))
+    if rc != 0:
+        raise OracleError(rc)
+    return out.value, sse.value
+
+
+def compress_psnr(x: np.ndarray, target_db: float, params: TuneParams | None = None):
+    """Eq. 1 with M = PSNR: (stream, absolute bound, PSNR) of the search."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    dims = (ctypes.c_uint64 * 3)(*[int(v) for v in x.shape] + [1] * (3 - x.ndim))
+    cap = int(lib().ora_compress_bound(x.ndim, dims))
+    out = np.zeros(cap, np.uint8)
+    size = ctypes.c_uint64(0)
+    eb = ctypes.c_double(0)
+    ps = ctypes.c_double(0)
+    rc = lib().ora_compress_psnr(x.ctypes.data, x.ndim, dims, float(target_db),
+                                 ctypes.byref(params) if params is not None else None,
+                                 out.ctypes.data, cap, ctypes.byref(size), ctypes.byref(eb),
+                                 ctypes.byref(ps))
+    if rc != 0:
+        raise OracleError(rc)
+    return out[:size.value].tobytes(), eb.value, ps.value
+
+
+def compress_typed(x: np.ndarray, eb: float, eb_mode: int = EB_ABS,
+                   config: Config | None = None, tune: bool = False,
+                   params: TuneParams | None = None) -> bytes:
+    """Integer (int16, uint16, int32) or float input; the stream."""
+    dt = {np.dtype(v): k for k, v in _DT.items()}[np.dtype(x.dtype)]
+    x = np.ascontiguousarray(x)
+    dims = (ctypes.c_uint64 * 3)(*[int(v) for v in x.shape] + [1] * (3 - x.ndim))
+    cap = int(lib().ora_compress_bound(x.ndim, dims))
+    out = np.zeros(cap, np.uint8)
+    size = ctypes.c_uint64(0)
+    rc = lib().ora_compress_typed(x.ctypes.data, dt, x.ndim, dims, eb_mode, float(eb),
+                                  ctypes.byref(config) if config is not None else None,
+                                  int(tune),
+                                  ctypes.byref(params) if params is not None else None,
+                                  out.ctypes.data, cap, ctypes.byref(size))
+    if rc != 0:
+        raise OracleError(rc)
+    return out[:size.value].tobytes()
+
+
+def decompress_typed(stream: bytes, dtype) -> np.ndarray:
+    dt = {np.dtype(v): k for k, v in _DT.items()}[np.dtype(dtype)]
+    nd, shape, _ = inspect(stream)
+    buf = np.frombuffer(stream, dtype=np.uint8)
+    out = np.zeros(int(np.prod(shape)), dtype=_DT[dt])
+    rc = lib().ora_decompress_typed(buf.ctypes.data, len(stream), out.ctypes.data, dt,
+                                    out.size)
+    if rc != 0:
+        raise OracleError(rc)
+    return out.reshape(shape)
