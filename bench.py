@@ -737,6 +737,91 @@ def bench_workloads(ctx, steps, peak):
     return out
 
 
+def bench_quality(ctx, steps):
+    """The quality-metric target (Eq. 1 with M = PSNR) on the 512^3 k^-5/3
+    field at 80 dB (the PSNR of the paper's transfer test): the whole bound
+    search with its auto-tuned round trips, timed end to end; and integer
+    inputs (a uint16 2048x2048 image and an int16 64x512x512 movie,
+    synthetic), lossless (e < 1) and lossy (rel 1e-3, auto-tuned): round-trip
+    GB/s of input, compression ratio, the bound held."""
+    import torch
+    from paper_2311_12133_gb300 import fields, hpez
+    sptr = torch.cuda.current_stream().cuda_stream
+    out = {}
+    shape = (512, 512, 512)
+    x = fields.grf_torch(shape, seed=fields.seed_of("quality", 0))
+    cap = hpez.hpez_compress_bound(shape)
+    buf = torch.empty(cap, dtype=torch.uint8, device="cuda")
+    n0 = hpez.hpez_launch_count(ctx.handle)
+    t0 = time.perf_counter()
+    size, e, ps = hpez.hpez_compress_psnr(ctx.handle, x.data_ptr(), shape, 80.0, None,
+                                          buf.data_ptr(), cap, sptr)
+    wall = time.perf_counter() - t0
+    y = ctx.decompress(buf, size)
+    out["psnr_target"] = {
+        "workload": "grf k^-5/3 512^3, target PSNR 80 dB, auto-tuned probes",
+        "abs_eb": e, "psnr_db": round(ps, 4), "psnr_check_db": round(psnr_db(x, y), 4),
+        "compression_ratio": round(4 * x.numel() / size, 3), "search_s": round(wall, 4),
+        "launches": hpez.hpez_launch_count(ctx.handle) - n0}
+    del x, y, buf
+    torch.cuda.empty_cache()
+    res = []
+    for name, kind, shp, tdt, code, scale, off in (
+            ("uint16 image 2048x2048", "climate2d", (2048, 2048), torch.int16,
+             hpez.HPEZ_DTYPE_U16, 12000.0, 32768.0),
+            ("int16 movie 64x512x512", "grf", (64, 512, 512), torch.int16,
+             hpez.HPEZ_DTYPE_I16, 6000.0, 0.0)):
+        f = fields.make_torch(kind, shp, fields.seed_of("quality", name))
+        f = torch.round((f - f.mean()) / (f.std() + 1e-9) * scale / 4 + off)
+        lo_v, hi_v = (0, 65535) if code == hpez.HPEZ_DTYPE_U16 else (-32768, 32767)
+        v = f.clamp(lo_v, hi_v).to(torch.int32)
+        if code == hpez.HPEZ_DTYPE_U16:
+            v = torch.where(v >= 32768, v - 65536, v)  # the same 16 bits as int16 storage
+        xi = v.to(tdt).contiguous()
+        n = xi.numel()
+        cap = hpez.hpez_compress_bound(shp)
+        buf = torch.empty(cap, dtype=torch.uint8, device="cuda")
+        yi = torch.empty_like(xi)
+        for eb, mode, tune in ((0.4, hpez.HPEZ_EB_ABS, False), (1e-3, hpez.HPEZ_EB_REL, True)):
+            def step():
+                sz = hpez.hpez_compress_typed(ctx.handle, xi.data_ptr(), code, shp, mode, eb,
+                                              None, tune, None, buf.data_ptr(), cap, sptr)
+                hpez.hpez_decompress_typed(ctx.handle, buf.data_ptr(), sz, yi.data_ptr(), code,
+                                           n, sptr)
+                return sz
+            for _ in range(3):
+                sz = step()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                sz = step()
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            a = xi.to(torch.int32)
+            b = yi.to(torch.int32)
+            if code == hpez.HPEZ_DTYPE_U16:
+                a, b = a & 0xFFFF, b & 0xFFFF
+            err = int((a - b).abs().max().item())
+            bound = int(eb) if mode == hpez.HPEZ_EB_ABS else int(
+                eb * (int(a.max().item()) - int(a.min().item())))
+            assert err <= bound, f"{name}: {err} > {bound}"
+            med = statistics.median(ms)
+            res.append({"workload": name, "eb": {"mode": "abs" if mode == 0 else "rel",
+                                                  "value": eb, "integer_bound": bound},
+                        "tuned": tune, "value": round(2 * n / (med / 1e3) / 1e9, 3),
+                        "unit": "GB/s of input (2-byte values)", "step_ms": step_stats(ms),
+                        "compression_ratio": round(2 * n / sz, 3), "max_abs_err": err,
+                        "lossless": err == 0})
+        del xi, yi, buf, f, v
+        torch.cuda.empty_cache()
+    out["integer"] = res
+    return out
+
+
 def bench_served(ctx, seconds=3.0, rate=200.0, slots=256, pool_size=32):
     """Poisson stream of compress/decompress requests over fields of 1 MB ..
     512 MB (log-uniform), rel eb from {1e-2,1e-3,1e-4}, host buffers,
@@ -1065,6 +1150,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_workloads:
         workloads = bench_workloads(ctx, max(5, args.steps), peak)
 
+    quality = None
+    if rank == 0 and world == 1 and not args.no_workloads:
+        quality = bench_quality(ctx, max(5, args.steps))
+
     batched = served = None
     if rank == 0 and world == 1 and not args.no_batched:
         batched = bench_batched(ctx, max(3, args.steps // 2), args.warmup)
@@ -1098,7 +1187,7 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
             "default_predictor": default_pred, "lorenzo": lorenzo, "spline": spline,
-            "workloads": workloads, "batched": batched, "served": served,
+            "workloads": workloads, "quality": quality, "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -379,6 +379,61 @@ HPEZ_API int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim,
                        uint8_t* h_blockmap, uint64_t blockmap_cap,
                        hpez_tune_report* h_report, void* stream);
 
+/* ---- the quality-metric target and integer inputs ----
+ * PSNR of y against x (Sec. 7.1.3): 20 log10(max x - min x) - 10 log10(MSE),
+ * the squared errors summed exactly in the fixed-point unit `unit`:
+ * q_i = rint((x_i - y_i) / unit) in double, sse = sum q_i^2 (64-bit
+ * integer; its value does not depend on the order of the sum), MSE =
+ * sse unit^2 / n; +inf when sse = 0.
+ *   d_x, d_y  device, n floats each; h_psnr, h_sse host, optional
+ * Errors: INVALID_ARG (n = 0, unit <= 0, |x_i - y_i| / unit > 2^16),
+ * NONFINITE_INPUT (x not finite).  Synchronizes `stream`. */
+HPEZ_API int hpez_psnr(hpez_ctx* ctx, const float* d_x, const float* d_y, uint64_t n,
+                       double unit, double* h_psnr, uint64_t* h_sse, void* stream);
+
+/* Eq. 1 (Sec. 3.1) with M = PSNR and target m0 = target_db: the largest
+ * absolute bound the search finds whose auto-tuned round trip keeps
+ * PSNR >= m0, and the stream compressed with it.  The search, in double:
+ * from e_u = range sqrt(3) 10^(-m0/20) (uniform errors on [-e, e] give m0)
+ * double or halve up to 6 times to bracket the target, then 8 geometric
+ * bisection steps e = sqrt(lo hi) keeping PSNR(lo) >= m0; each probe is
+ * hpez_compress_auto at the absolute bound e, hpez_decompress and
+ * hpez_psnr in the unit (stored bound) / 2^16.  d_in finite, device.
+ *   d_out, out_cap as hpez_compress; h_out_size, h_eb (the bound found) and
+ *   h_psnr (its PSNR) on the host.  tp: tuning parameters (NULL: defaults).
+ * Errors: as hpez_compress_auto, NONFINITE_INPUT.  Synchronizes. */
+HPEZ_API int hpez_compress_psnr(hpez_ctx* ctx, const float* d_in, int ndim,
+                                const uint64_t* dims, double target_db,
+                                const hpez_tune_params* tp, void* d_out, uint64_t out_cap,
+                                uint64_t* h_out_size, double* h_eb, double* h_psnr,
+                                void* stream);
+
+/* Integer inputs (the integer datasets of Sec. 7): int16, uint16 or int32
+ * (|v| <= 2^24) fields are widened to binary32 on the device (exactly) and
+ * compressed at the absolute float bound just below floor(e) + 1/2, e the
+ * requested bound (REL: eb (max - min) of the integers); decompression
+ * rounds to the nearest integer (ties to even) and clamps to the type's
+ * range, so every value stays within floor(e) of its input (lossless when
+ * e < 1).  The stream records the type in header byte 320 (0 = float32);
+ * hpez_decompress of an integer stream returns the unrounded floats.
+ *   d_in   device, N values of dtype; tune = 1: hpez_compress_auto with tp,
+ *          else hpez_compress with cfg (NULL: default)
+ * Errors: INVALID_ARG (an int32 beyond 2^24, a bound beyond 2^22, a
+ * dtype that is not the stream's), and those of the calls it makes.
+ * Uses a binary32 staging buffer of the context.  Synchronizes. */
+#define HPEZ_DTYPE_F32 0
+#define HPEZ_DTYPE_I16 1
+#define HPEZ_DTYPE_U16 2
+#define HPEZ_DTYPE_I32 3
+HPEZ_API int hpez_compress_typed(hpez_ctx* ctx, const void* d_in, int dtype, int ndim,
+                                 const uint64_t* dims, int eb_mode, double eb,
+                                 const hpez_config* cfg, int tune,
+                                 const hpez_tune_params* tp, void* d_out, uint64_t out_cap,
+                                 uint64_t* h_out_size, void* stream);
+HPEZ_API int hpez_decompress_typed(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
+                                   void* d_out, int dtype, uint64_t out_cap_elems,
+                                   void* stream);
+
 /* Execution options of a context (the results never depend on them):
  *  HPEZ_OPT_FUSED_LEVELS  1 (default): a level of the 1D-style paradigm
  *                         runs as one tiled kernel; 0: one kernel per pass

@@ -817,6 +817,8 @@ int hpez_destroy(hpez_ctx* ctx) {
   if (ctx->scratch) cudaFree(ctx->scratch);
   if (ctx->io_in) cudaFree(ctx->io_in);
   if (ctx->io_out) cudaFree(ctx->io_out);
+  if (ctx->typed_buf) cudaFree(ctx->typed_buf);
+  if (ctx->typed_red) cudaFree(ctx->typed_red);
   if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
   if (ctx->h_hdr) cudaFreeHost(ctx->h_hdr);
   if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);

@@ -100,6 +100,9 @@ struct hpez_ctx {
   size_t io_in_cap = 0;
   void* io_out = nullptr;
   size_t io_out_cap = 0;
+  void* typed_buf = nullptr;   // binary32 staging of the typed and PSNR-target calls
+  size_t typed_cap = 0;
+  void* typed_red = nullptr;   // their reduction words (256 bytes)
   std::vector<uint8_t> h_bmap;  // block map of the last auto-tuned compress
   cudaStream_t aux_stream = nullptr;  // the tuner's side stream
   cudaEvent_t aux_ev[2] = {nullptr, nullptr};

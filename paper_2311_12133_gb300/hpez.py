@@ -181,6 +181,18 @@ def _load():
                                                        ctypes.c_int, ctypes.c_double,
                                                        ctypes.POINTER(hpez_tune_params),
                                                        vp, u64, u64p, vp]),
+            "hpez_psnr": (ctypes.c_int, [vp, vp, vp, u64, ctypes.c_double,
+                                         ctypes.POINTER(ctypes.c_double), u64p, vp]),
+            "hpez_compress_psnr": (ctypes.c_int, [vp, vp, ctypes.c_int, u64p, ctypes.c_double,
+                                                  ctypes.POINTER(hpez_tune_params), vp, u64,
+                                                  u64p, ctypes.POINTER(ctypes.c_double),
+                                                  ctypes.POINTER(ctypes.c_double), vp]),
+            "hpez_compress_typed": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, u64p,
+                                                   ctypes.c_int, ctypes.c_double, cfgp,
+                                                   ctypes.c_int,
+                                                   ctypes.POINTER(hpez_tune_params), vp, u64,
+                                                   u64p, vp]),
+            "hpez_decompress_typed": (ctypes.c_int, [vp, vp, u64, vp, ctypes.c_int, u64, vp]),
             "hpez_tune": (ctypes.c_int, [vp, vp, ctypes.c_int, u64p, ctypes.c_int,
                                          ctypes.c_double,
                                          ctypes.POINTER(hpez_tune_params), cfgp,
@@ -396,6 +408,50 @@ def hpez_compress_auto(ctx, d_in: int, shape, eb_mode: int, eb: float,
                                       ctypes.byref(rep) if rep is not None else None,
                                       stream or None), "hpez_compress_auto")
     return (size.value, rep) if report else size.value
+
+
+HPEZ_DTYPE_F32, HPEZ_DTYPE_I16, HPEZ_DTYPE_U16, HPEZ_DTYPE_I32 = 0, 1, 2, 3
+
+
+def hpez_psnr(ctx, d_x: int, d_y: int, n: int, unit: float, stream: int = 0):
+    """(PSNR in dB, fixed-point squared-error sum) of y against x."""
+    ps = ctypes.c_double(0)
+    sse = ctypes.c_uint64(0)
+    _check(_load().hpez_psnr(ctx, d_x, d_y, n, float(unit), ctypes.byref(ps),
+                             ctypes.byref(sse), stream or None), "hpez_psnr")
+    return ps.value, sse.value
+
+
+def hpez_compress_psnr(ctx, d_in: int, shape, target_db: float,
+                       tp: hpez_tune_params | None, d_out: int, out_cap: int,
+                       stream: int = 0):
+    """Eq. 1 with M = PSNR: (stream size, absolute bound found, its PSNR)."""
+    size = ctypes.c_uint64(0)
+    eb = ctypes.c_double(0)
+    ps = ctypes.c_double(0)
+    _check(_load().hpez_compress_psnr(ctx, d_in, len(shape), _dims(shape), float(target_db),
+                                      ctypes.byref(tp) if tp is not None else None, d_out,
+                                      out_cap, ctypes.byref(size), ctypes.byref(eb),
+                                      ctypes.byref(ps), stream or None), "hpez_compress_psnr")
+    return size.value, eb.value, ps.value
+
+
+def hpez_compress_typed(ctx, d_in: int, dtype: int, shape, eb_mode: int, eb: float,
+                        cfg: hpez_config | None, tune: bool, tp: hpez_tune_params | None,
+                        d_out: int, out_cap: int, stream: int = 0) -> int:
+    size = ctypes.c_uint64(0)
+    _check(_load().hpez_compress_typed(ctx, d_in, dtype, len(shape), _dims(shape), eb_mode,
+                                       float(eb), ctypes.byref(cfg) if cfg is not None else None,
+                                       int(tune), ctypes.byref(tp) if tp is not None else None,
+                                       d_out, out_cap, ctypes.byref(size), stream or None),
+           "hpez_compress_typed")
+    return size.value
+
+
+def hpez_decompress_typed(ctx, d_in: int, in_size: int, d_out: int, dtype: int,
+                          out_cap_elems: int, stream: int = 0) -> None:
+    _check(_load().hpez_decompress_typed(ctx, d_in, in_size, d_out, dtype, out_cap_elems,
+                                         stream or None), "hpez_decompress_typed")
 
 
 def hpez_compress_auto_host(ctx, h_in: np.ndarray, eb_mode: int, eb: float,
