@@ -132,6 +132,7 @@ static uint64_t align16(uint64_t v) { return (v + 15) & ~(uint64_t)15; }
 #define MAGIC 0x5A455048u /* "HPEZ" */
 #define VERSION 1u
 #define FLAG_CONST 1u
+#define FLAG_LOSSLESS 2u
 
 /* ------------------------------------------------------------------ */
 /* field geometry: every field is held as 3 slots, the real dimensions  */
@@ -1114,6 +1115,18 @@ int ora_decompress(const uint8_t* in, uint64_t size, float* out,
   uint64_t dims[3];
   int rc = ora_inspect(in, size, &ndim, dims, NULL);
   if (rc) return rc;
+  if (get_u32(in, H_FLAGS) & FLAG_LOSSLESS) {
+    /* undo the lossless stage first */
+    const uint64_t raw = get_u64(in, ORA_H_RAWSIZE);
+    if (raw < ORA_HEADER_BYTES || raw > ((uint64_t)1 << 40)) return ORA_ERR_CORRUPT;
+    uint8_t* tmp = (uint8_t*)malloc(raw);
+    uint64_t got = 0;
+    rc = ora_lossless_decode(in, size, tmp, raw, &got);
+    if (!rc && got != raw) rc = ORA_ERR_CORRUPT;
+    if (!rc) rc = ora_decompress(tmp, raw, out, cap_elems);
+    free(tmp);
+    return rc;
+  }
   if (!out) return ORA_ERR_INVALID_ARG;
   uint64_t N = 1;
   for (int d = 0; d < ndim; ++d) {
@@ -2118,4 +2131,138 @@ int ora_decompress_typed(const uint8_t* in, uint64_t size, void* out, int dtype,
   }
   free(y);
   return rc;
+}
+
+/* ================================================================== */
+/* The lossless stage (Sec. 4, Step 5): run suppression of repeated     */
+/* 32-bit words of the stream body, two levels of masks.                */
+/* ================================================================== */
+
+static uint32_t body_word(const uint8_t* b, uint64_t nbytes, uint64_t i) {
+  uint32_t v = 0;
+  for (int k = 0; k < 4; ++k) {
+    const uint64_t o = 4 * i + (uint64_t)k;
+    if (o < nbytes) v |= (uint32_t)b[o] << (8 * k);
+  }
+  return v;
+}
+
+int ora_lossless_encode(const uint8_t* in, uint64_t size, uint8_t* out, uint64_t cap,
+                        uint64_t* out_size) {
+  if (!in || !out || !out_size || size < ORA_HEADER_BYTES) return ORA_ERR_INVALID_ARG;
+  if (get_u32(in, H_FLAGS) & FLAG_LOSSLESS) return ORA_ERR_INVALID_ARG;
+  const uint8_t* body = in + ORA_HEADER_BYTES;
+  const uint64_t nbytes = size - ORA_HEADER_BYTES;
+  const uint64_t nw = (nbytes + 3) / 4, nb = (nw + 31) / 32, ng = (nb + 31) / 32;
+  uint32_t* m1 = (uint32_t*)calloc(nb ? nb : 1, 4);
+  uint32_t* m2 = (uint32_t*)calloc(ng ? ng : 1, 4);
+  uint64_t nlit = 0, nmask = 0;
+  uint32_t prev = 0;
+  for (uint64_t i = 0; i < nw; ++i) {
+    const uint32_t w = body_word(body, nbytes, i);
+    if (w != prev) {
+      m1[i / 32] |= 1u << (i % 32);
+      ++nlit;
+    }
+    prev = w;
+  }
+  for (uint64_t b = 0; b < nb; ++b)
+    if (m1[b]) {
+      m2[b / 32] |= 1u << (b % 32);
+      ++nmask;
+    }
+  const uint64_t zsize = ORA_HEADER_BYTES + 32 + 4 * (ng + nmask + nlit);
+  int rc = ORA_OK;
+  if (zsize >= size) {
+    /* no gain: the stream stays as it is */
+    if (size > cap) {
+      rc = ORA_ERR_OUT_TOO_SMALL;
+    } else {
+      memmove(out, in, size);
+      *out_size = size;
+    }
+  } else if (zsize > cap) {
+    rc = ORA_ERR_OUT_TOO_SMALL;
+  } else {
+    uint8_t* hdr = (uint8_t*)malloc(ORA_HEADER_BYTES);
+    memcpy(hdr, in, ORA_HEADER_BYTES);
+    put_u32(hdr, H_FLAGS, get_u32(hdr, H_FLAGS) | FLAG_LOSSLESS);
+    put_u64(hdr, ORA_H_RAWSIZE, size);
+    uint64_t o = ORA_HEADER_BYTES;
+    uint8_t* z = out;
+    /* literals first into a scratch (the output may alias nothing) */
+    uint32_t* lits = (uint32_t*)malloc(4 * (nlit ? nlit : 1));
+    uint64_t k = 0;
+    prev = 0;
+    for (uint64_t i = 0; i < nw; ++i) {
+      const uint32_t w = body_word(body, nbytes, i);
+      if (w != prev) lits[k++] = w;
+      prev = w;
+    }
+    memcpy(z, hdr, ORA_HEADER_BYTES);
+    put_u64(z, o, nw);
+    put_u64(z, o + 8, nlit);
+    put_u64(z, o + 16, nmask);
+    put_u64(z, o + 24, 0);
+    o += 32;
+    for (uint64_t g = 0; g < ng; ++g, o += 4) put_u32(z, o, m2[g]);
+    for (uint64_t b = 0; b < nb; ++b)
+      if (m1[b]) {
+        put_u32(z, o, m1[b]);
+        o += 4;
+      }
+    for (uint64_t i = 0; i < nlit; ++i, o += 4) put_u32(z, o, lits[i]);
+    *out_size = o;
+    free(lits);
+    free(hdr);
+  }
+  free(m1);
+  free(m2);
+  return rc;
+}
+
+int ora_lossless_decode(const uint8_t* in, uint64_t size, uint8_t* out, uint64_t cap,
+                        uint64_t* out_size) {
+  if (!in || !out || !out_size || size < ORA_HEADER_BYTES + 32) return ORA_ERR_INVALID_ARG;
+  if (!(get_u32(in, H_FLAGS) & FLAG_LOSSLESS)) return ORA_ERR_INVALID_ARG;
+  const uint64_t raw = get_u64(in, ORA_H_RAWSIZE);
+  if (raw < ORA_HEADER_BYTES) return ORA_ERR_CORRUPT;
+  if (raw > cap) return ORA_ERR_OUT_TOO_SMALL;
+  uint64_t o = ORA_HEADER_BYTES;
+  const uint64_t nw = get_u64(in, o), nlit = get_u64(in, o + 8), nmask = get_u64(in, o + 16);
+  const uint64_t nbytes = raw - ORA_HEADER_BYTES;
+  if (nw != (nbytes + 3) / 4 || get_u64(in, o + 24) != 0) return ORA_ERR_CORRUPT;
+  const uint64_t nb = (nw + 31) / 32, ng = (nb + 31) / 32;
+  if (nmask > nb || nlit > nw || size != ORA_HEADER_BYTES + 32 + 4 * (ng + nmask + nlit))
+    return ORA_ERR_CORRUPT;
+  o += 32;
+  const uint64_t om = o + 4 * ng, ol = om + 4 * nmask;
+  uint64_t km = 0, kl = 0;
+  uint32_t prev = 0;
+  memcpy(out, in, ORA_HEADER_BYTES);
+  put_u32(out, H_FLAGS, get_u32(in, H_FLAGS) & ~FLAG_LOSSLESS);
+  put_u64(out, ORA_H_RAWSIZE, 0);
+  for (uint64_t b = 0; b < nb; ++b) {
+    const uint32_t g = get_u32(in, o + 4 * (b / 32));
+    uint32_t m = 0;
+    if ((g >> (b % 32)) & 1u) {
+      if (km >= nmask) return ORA_ERR_CORRUPT;
+      m = get_u32(in, om + 4 * km++);
+      if (!m) return ORA_ERR_CORRUPT;
+    }
+    for (uint64_t j = 0; j < 32 && 32 * b + j < nw; ++j) {
+      if ((m >> j) & 1u) {
+        if (kl >= nlit) return ORA_ERR_CORRUPT;
+        prev = get_u32(in, ol + 4 * kl++);
+      }
+      const uint64_t i = 32 * b + j;
+      for (int q = 0; q < 4; ++q) {
+        const uint64_t ob = 4 * i + (uint64_t)q;
+        if (ob < nbytes) out[ORA_HEADER_BYTES + ob] = (uint8_t)(prev >> (8 * q));
+      }
+    }
+  }
+  if (km != nmask || kl != nlit) return ORA_ERR_CORRUPT;
+  *out_size = raw;
+  return ORA_OK;
 }

@@ -198,6 +198,23 @@ int ora_compress_typed(const void* x, int dtype, int ndim, const uint64_t* dims,
 int ora_decompress_typed(const uint8_t* in, uint64_t size, void* out, int dtype,
                          uint64_t cap_elems);
 
+/* ---- the lossless stage after Huffman (Sec. 4, Step 5) ----
+ * Read as run suppression of repeated 32-bit words over the stream body
+ * (the bytes after the 512-byte header, zero-padded to whole words): in
+ * every block of 32 words a mask marks the words that differ from the word
+ * before them (the word before the first is 0), and only those words are
+ * kept; a second mask per group of 32 blocks marks the blocks whose mask is
+ * not 0, and only those masks are kept.  The result: the header with flag
+ * bit 2 and the raw size at byte ORA_H_RAWSIZE, then the counts (words,
+ * literals, masks, 0 as four u64), the group masks, the kept block masks and
+ * the kept words.  When that is not smaller than the input, the input is
+ * returned unchanged.  ora_decompress accepts either form. */
+#define ORA_H_RAWSIZE 328
+int ora_lossless_encode(const uint8_t* in, uint64_t size, uint8_t* out, uint64_t cap,
+                        uint64_t* out_size);
+int ora_lossless_decode(const uint8_t* in, uint64_t size, uint8_t* out, uint64_t cap,
+                        uint64_t* out_size);
+
 #ifdef __cplusplus
 }
 #endif

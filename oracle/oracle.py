@@ -203,6 +203,10 @@ def lib():
             L.ora_decompress_typed.argtypes = [ctypes.c_void_p, ctypes.c_uint64,
                                                ctypes.c_void_p, ctypes.c_int,
                                                ctypes.c_uint64]
+            for f in (L.ora_lossless_encode, L.ora_lossless_decode):
+                f.restype = ctypes.c_int
+                f.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                              ctypes.c_uint64, u64p]
             _lib = L
     return _lib
 
@@ -495,3 +499,30 @@ def decompress_typed(stream: bytes, dtype) -> np.ndarray:
     if rc != 0:
         raise OracleError(rc)
     return out.reshape(shape)
+
+
+# ------------------------------------------------------- the lossless stage
+H_RAWSIZE = 328
+
+
+def lossless_encode(stream: bytes) -> bytes:
+    src = np.frombuffer(stream, np.uint8).copy()
+    out = np.zeros(len(stream) + 64, np.uint8)
+    size = ctypes.c_uint64(0)
+    rc = lib().ora_lossless_encode(src.ctypes.data, len(stream), out.ctypes.data, out.size,
+                                   ctypes.byref(size))
+    if rc != 0:
+        raise OracleError(rc)
+    return out[:size.value].tobytes()
+
+
+def lossless_decode(z: bytes) -> bytes:
+    src = np.frombuffer(z, np.uint8)
+    raw = int.from_bytes(z[H_RAWSIZE:H_RAWSIZE + 8], "little")
+    out = np.zeros(max(raw, 1), np.uint8)
+    size = ctypes.c_uint64(0)
+    rc = lib().ora_lossless_decode(src.ctypes.data, len(z), out.ctypes.data, out.size,
+                                   ctypes.byref(size))
+    if rc != 0:
+        raise OracleError(rc)
+    return out[:size.value].tobytes()
