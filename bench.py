@@ -702,6 +702,10 @@ def bench_workloads(ctx, steps, peak):
         err = (y.double() - x.double()).abs().max().item()
         assert err <= e_abs, f"{name}: bound violated: {err} > {e_abs}"
         ps = psnr_db(x, y)
+        zb = torch.empty(cap + 64, dtype=torch.uint8, device="cuda")
+        zsize = hpez.hpez_lossless_encode(ctx.handle, cbuf.data_ptr(), size, zb.data_ptr(),
+                                          zb.numel(), sptr)
+        del zb
         hpez.hpez_profile_enable(ctx.handle, True)
         for _ in range(2):
             step()
@@ -729,6 +733,7 @@ def bench_workloads(ctx, steps, peak):
             "compress_gbps": round(4 * N / (statistics.median(comp) / 1e3) / 1e9, 3),
             "decompress_gbps": round(4 * N / (statistics.median(dec) / 1e3) / 1e9, 3),
             "compression_ratio": round(4 * N / size, 3), "psnr_db": round(ps, 3),
+            "compression_ratio_after_lossless_stage": round(4 * N / zsize, 3),
             "max_abs_err": err, "bound_held": True, "l2_flushed": do_flush,
             "finest_level": lv})
         del cbuf, y
@@ -1038,6 +1043,34 @@ def main():
     if args.profile_only:
         return
 
+    # the lossless stage (Sec. 4 Step 5) on the step's stream, timed apart
+    zbuf = torch.empty(cap + 64, dtype=torch.uint8, device=x.device)
+    rbuf = torch.empty(cap + 64, dtype=torch.uint8, device=x.device)
+    zsize = hpez.hpez_lossless_encode(ctx.handle, cbuf.data_ptr(), size, zbuf.data_ptr(),
+                                      zbuf.numel(), sptr)
+    lz_ms = []
+    for _ in range(max(3, args.steps // 2)):
+        l0 = torch.cuda.Event(enable_timing=True)
+        l1 = torch.cuda.Event(enable_timing=True)
+        l2 = torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        zsize = hpez.hpez_lossless_encode(ctx.handle, cbuf.data_ptr(), size, zbuf.data_ptr(),
+                                          zbuf.numel(), sptr)
+        l1.record(stream)
+        if zsize < size:
+            hpez.hpez_lossless_decode(ctx.handle, zbuf.data_ptr(), zsize, rbuf.data_ptr(),
+                                      rbuf.numel(), sptr)
+        l2.record(stream)
+        torch.cuda.synchronize()
+        lz_ms.append((l0.elapsed_time(l1), l1.elapsed_time(l2)))
+    lossless = {"stream_bytes": size, "after_stage_bytes": zsize,
+                "compression_ratio_after_stage": round(4 * N / zsize, 3),
+                "encode_ms": round(statistics.median(a for a, _ in lz_ms), 4),
+                "decode_ms": round(statistics.median(b for _, b in lz_ms), 4),
+                "note": "run suppression of repeated 32-bit words (stays raw when it "
+                        "would not shrink the stream)"}
+    del zbuf, rbuf
+
     total_ms, comp_ms, dec_ms = max_over_ranks([total_ms, comp_ms, dec_ms], dist, x.device)
     ms_per_step = total_ms / args.steps
     value = job_gbps(world, N, ms_per_step / 1e3)
@@ -1181,6 +1214,7 @@ def main():
             "compress_gbps": round(world * 4 * N / (comp_ms / args.steps / 1e3) / 1e9, 3),
             "decompress_gbps": round(world * 4 * N / (dec_ms / args.steps / 1e3) / 1e9, 3),
             "compression_ratio": round(4 * N / size, 3), "psnr_db": round(psnr, 3),
+            "lossless_stage": lossless,
             "max_abs_err": err, "abs_eb": e_abs, "n_outliers": n_out,
             "n_symbols": n_used,
             "roofline": roofline, "phases": phase_report,

@@ -151,8 +151,9 @@ HPEZ_API int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
  * overlap on the GPU (other streams, other host threads) race and must be
  * serialized by the caller.  Synchronizes `stream`.
  * Errors: as hpez_decompress, plus HPEZ_ERR_TOO_LARGE, and
- * HPEZ_ERR_UNSUPPORTED for a Lorenzo-predictor stream or a stream with a
- * global natural-spline level (interp HPEZ_SPLINE_GLOBAL). */
+ * HPEZ_ERR_UNSUPPORTED for a Lorenzo-predictor stream, a stream with a
+ * global natural-spline level (interp HPEZ_SPLINE_GLOBAL) or a stream that
+ * went through the lossless stage (hpez_lossless_encode). */
 #define HPEZ_NOALLOC_MAX_POINTS 2097152u
 #define HPEZ_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 HPEZ_API int hpez_decompress_noalloc(const void* d_in, uint64_t in_size,
@@ -433,6 +434,29 @@ HPEZ_API int hpez_compress_typed(hpez_ctx* ctx, const void* d_in, int dtype, int
 HPEZ_API int hpez_decompress_typed(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
                                    void* d_out, int dtype, uint64_t out_cap_elems,
                                    void* stream);
+
+/* ---- the lossless stage after Huffman (Sec. 4, Step 5) ----
+ * Read as run suppression of repeated 32-bit words of the stream body (the
+ * bytes after the 512-byte header, zero-padded to whole words): per block of
+ * 32 words a mask of the words that differ from the word before them (the
+ * word before the first is 0), per group of 32 blocks a mask of the blocks
+ * whose mask is not 0; only those masks and words are kept.  Output: the
+ * header with flag bit 2 and the raw size at byte 328, four u64 counts
+ * (words, kept words, kept block masks, 0), the group masks, the kept block
+ * masks, the kept words.  When that would not be smaller, the stream is
+ * copied unchanged.  hpez_decompress accepts either form (it undoes the
+ * stage into a buffer of the context); hpez_decompress_noalloc refuses a
+ * stream that went through it (HPEZ_ERR_UNSUPPORTED).
+ *   d_in, d_out  device, 16-byte aligned, not overlapping; sizes in bytes
+ * Errors: INVALID_ARG (an already encoded stream to encode, or a plain one
+ * to decode), OUT_TOO_SMALL, CORRUPT_STREAM (counts or masks that do not
+ * match the sizes).  Synchronize `stream`. */
+HPEZ_API int hpez_lossless_encode(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
+                                  void* d_out, uint64_t out_cap, uint64_t* h_out_size,
+                                  void* stream);
+HPEZ_API int hpez_lossless_decode(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
+                                  void* d_out, uint64_t out_cap, uint64_t* h_out_size,
+                                  void* stream);
 
 /* Execution options of a context (the results never depend on them):
  *  HPEZ_OPT_FUSED_LEVELS  1 (default): a level of the 1D-style paradigm

@@ -819,6 +819,8 @@ int hpez_destroy(hpez_ctx* ctx) {
   if (ctx->io_out) cudaFree(ctx->io_out);
   if (ctx->typed_buf) cudaFree(ctx->typed_buf);
   if (ctx->typed_red) cudaFree(ctx->typed_red);
+  if (ctx->lz_buf) cudaFree(ctx->lz_buf);
+  if (ctx->lz_stream) cudaFree(ctx->lz_stream);
   if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
   if (ctx->h_hdr) cudaFreeHost(ctx->h_hdr);
   if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
@@ -1096,6 +1098,16 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   if (rc) return rc;
   rc = cuda_check(cudaStreamSynchronize(s));
   if (rc) return rc;
+  uint64_t raw = 0;
+  if (lossless_flagged(ctx->h_hdr, &raw)) {
+    // the lossless stage (Sec. 4, Step 5) first, into the context's buffer
+    if (raw < (uint64_t)kHeaderBytes || raw > (1ull << 40)) return HPEZ_ERR_CORRUPT_STREAM;
+    if ((rc = ensure_io(&ctx->lz_stream, &ctx->lz_stream_cap, raw))) return rc;
+    uint64_t got = 0;
+    rc = hpez_lossless_decode(ctx, d_in, in_size, ctx->lz_stream, raw, &got, stream);
+    if (rc) return rc;
+    return hpez_decompress(ctx, ctx->lz_stream, got, d_out, out_cap_elems, stream);
+  }
   StreamInfo si;
   rc = parse_stream_header(ctx->h_hdr, in_size, si);
   if (rc) return rc;
@@ -1398,6 +1410,8 @@ extern "C" int hpez_decompress_noalloc(const void* d_in, uint64_t in_size,
   rc = cuda_check(cudaMemcpyAsync(h, d_in, kHeaderBytes, cudaMemcpyDeviceToHost, s));
   if (!rc) rc = cuda_check(cudaStreamSynchronize(s));
   if (rc) return rc;
+  uint64_t raw = 0;
+  if (lossless_flagged(h, &raw)) return HPEZ_ERR_UNSUPPORTED;  // hpez_decompress undoes it
   // the same header validation as hpez_decompress (dims, offsets, counts,
   // alignment of the sections)
   StreamInfo si;

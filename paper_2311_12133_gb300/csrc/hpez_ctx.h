@@ -103,6 +103,10 @@ struct hpez_ctx {
   void* typed_buf = nullptr;   // binary32 staging of the typed and PSNR-target calls
   size_t typed_cap = 0;
   void* typed_red = nullptr;   // their reduction words (256 bytes)
+  void* lz_buf = nullptr;      // scratch of the lossless stage
+  size_t lz_cap = 0;
+  void* lz_stream = nullptr;   // a stream with the lossless stage undone
+  size_t lz_stream_cap = 0;
   std::vector<uint8_t> h_bmap;  // block map of the last auto-tuned compress
   cudaStream_t aux_stream = nullptr;  // the tuner's side stream
   cudaEvent_t aux_ev[2] = {nullptr, nullptr};
@@ -205,6 +209,9 @@ int ensure_scratch(hpez_ctx* ctx, size_t bytes);
 // device staging buffer of the host-memory entry points, grown on demand
 int ensure_io(void** buf, size_t* cap, size_t bytes);
 int map_status(int st);
+// the header of a stream that went through the lossless stage (and its raw
+// size); hpez_decompress undoes the stage first
+bool lossless_flagged(const uint8_t* hdr, uint64_t* raw);
 int cuda_check(cudaError_t e);
 void default_config(int ndim, hpez_config* c);
 

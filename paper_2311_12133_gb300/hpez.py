@@ -193,6 +193,8 @@ def _load():
                                                    ctypes.POINTER(hpez_tune_params), vp, u64,
                                                    u64p, vp]),
             "hpez_decompress_typed": (ctypes.c_int, [vp, vp, u64, vp, ctypes.c_int, u64, vp]),
+            "hpez_lossless_encode": (ctypes.c_int, [vp, vp, u64, vp, u64, u64p, vp]),
+            "hpez_lossless_decode": (ctypes.c_int, [vp, vp, u64, vp, u64, u64p, vp]),
             "hpez_tune": (ctypes.c_int, [vp, vp, ctypes.c_int, u64p, ctypes.c_int,
                                          ctypes.c_double,
                                          ctypes.POINTER(hpez_tune_params), cfgp,
@@ -452,6 +454,23 @@ def hpez_decompress_typed(ctx, d_in: int, in_size: int, d_out: int, dtype: int,
                           out_cap_elems: int, stream: int = 0) -> None:
     _check(_load().hpez_decompress_typed(ctx, d_in, in_size, d_out, dtype, out_cap_elems,
                                          stream or None), "hpez_decompress_typed")
+
+
+def hpez_lossless_encode(ctx, d_in: int, in_size: int, d_out: int, out_cap: int,
+                         stream: int = 0) -> int:
+    """The lossless stage (Sec. 4 Step 5) over a stream; the output size."""
+    size = ctypes.c_uint64(0)
+    _check(_load().hpez_lossless_encode(ctx, d_in, in_size, d_out, out_cap, ctypes.byref(size),
+                                        stream or None), "hpez_lossless_encode")
+    return size.value
+
+
+def hpez_lossless_decode(ctx, d_in: int, in_size: int, d_out: int, out_cap: int,
+                         stream: int = 0) -> int:
+    size = ctypes.c_uint64(0)
+    _check(_load().hpez_lossless_decode(ctx, d_in, in_size, d_out, out_cap, ctypes.byref(size),
+                                        stream or None), "hpez_lossless_decode")
+    return size.value
 
 
 def hpez_compress_auto_host(ctx, h_in: np.ndarray, eb_mode: int, eb: float,

@@ -127,3 +127,22 @@ def test_noalloc_refuses_lorenzo_streams(ctx):
         hpez.hpez_decompress_noalloc(buf.data_ptr(), size, out.data_ptr(), out.numel(),
                                      torch.cuda.current_stream().cuda_stream)
     assert e.value.code == -8
+
+
+def test_noalloc_refuses_lossless_streams(ctx):
+    """A stream that went through the lossless stage is hpez_decompress's
+    only (undoing the stage needs a buffer)."""
+    import torch
+    from paper_2311_12133_gb300 import fields, hpez
+    x = torch.from_numpy(fields.bumps((40, 40, 40), seed=3)).cuda()
+    buf, size = ctx.compress(x, 1e-1)
+    z = torch.empty(size + 64, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    zs = hpez.hpez_lossless_encode(ctx.handle, buf.data_ptr(), size, z.data_ptr(), z.numel(),
+                                   stream)
+    assert zs < size
+    out = torch.empty_like(x)
+    with pytest.raises(hpez.HpezError) as e:
+        hpez.hpez_decompress_noalloc(z.data_ptr(), zs, out.data_ptr(), out.numel(), stream)
+    assert e.value.code == -8
+    assert torch.equal(ctx.decompress(z, zs), ctx.decompress(buf, size))
