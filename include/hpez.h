@@ -181,11 +181,17 @@ HPEZ_API const char* hpez_strerror(int code);
  * the same method) ----
  * Many fields compressed (or streams decompressed) together.  Each field
  * runs exactly the single-field operations, so its stream is byte-identical
- * to hpez_compress's; the operations of all fields advance in lockstep
- * ("ticks"), and each tick launches one kernel per operation kind over the
- * concatenated work of every field (levels of different fields, 2D and 3D,
- * share launches).  Creation plans every field, allocates one workspace and
- * uploads every tick's job tables; a run is kernel launches only. */
+ * to hpez_compress's.  The operations are grouped into ticks: the ops
+ * before the sweep by position, then level by level from the coarsest
+ * (level l of every field in the same tick, fields with fewer levels
+ * joining at theirs), then the ops after the sweep by position.  A tick
+ * launches one kernel per operation kind over the concatenated work of its
+ * fields; a level's launch is persistent (at most the CTAs resident on the
+ * GPU, each walking tiles of several fields).  The kernel family and tile
+ * shape of each level come from the context's schedule table (below) when
+ * it holds the level's key, else from fixed rules.  Creation plans every
+ * field, allocates one workspace and uploads every tick's job tables; a run
+ * is kernel launches only. */
 typedef struct {
   const float* d_in;     /* device, N float32, row-major */
   int32_t ndim;
@@ -233,6 +239,82 @@ HPEZ_API int hpez_batch_results(hpez_batch* b, void* stream, uint64_t* h_sizes,
 HPEZ_API int hpez_batch_launch_count(hpez_batch* b, uint64_t* launches,
                                      uint64_t* ticks);
 HPEZ_API int hpez_batch_destroy(hpez_batch* b);
+
+/* ---- level schedules of the batched and served forms (no counterpart in
+ * the paper: how the GPU runs a level, never what it computes) ----
+ * A schedule table maps a level key -- the field's shape class, the level's
+ * stride s = 2^(l-1), its interpolator, paradigm and direction -- to a
+ * kernel family and tile shape.  hpez_tuning_search finds the entries by
+ * timing every candidate schedule on the GPU (an offline search); the table
+ * is saved to and loaded from a text file.  A schedule changes speed only:
+ * streams and fields are byte-identical under any table.  A table entry
+ * that a field's level cannot run (shape, alignment, shared memory) falls
+ * back to the fixed rules. */
+typedef struct {
+  int32_t ndim;      /* 1..3 */
+  int32_t cls[3];    /* ceil(log2(n)) of each slot of the field seen as 3D,
+                        slowest first (leading slots 0 for 1D and 2D) */
+  int32_t stride;    /* s = 2^(l-1) */
+  int32_t interp;    /* HPEZ_LINEAR..HPEZ_CUBIC_NAT, or 3: a block map or
+                        same-level halves (the per-point interpolator) */
+  int32_t paradigm;  /* HPEZ_PARADIGM_1D / HPEZ_PARADIGM_MD */
+  int32_t decomp;    /* 0 compress, 1 decompress */
+} hpez_level_key;
+
+#define HPEZ_FAM_LEVEL3D 1  /* 3D level, rows along dim 1 per tile: tile[1] */
+#define HPEZ_FAM_MD3W 2     /* finest 3D multi-dimensional level as warp
+                               strips, `chunks` chunks of planes per field
+                               (0: as many as fill the GPU alone) */
+#define HPEZ_FAM_MD3 3      /* 3D multi-dimensional level, even then odd
+                               planes, tile[1] rows per tile */
+#define HPEZ_FAM_FUSED 4    /* fused tile of extents tile[0..2] */
+#define HPEZ_FAM_PASS 5     /* upsample + one launch per pass */
+
+typedef struct {
+  int32_t family;    /* HPEZ_FAM_* */
+  int32_t tile[3];   /* as the family says; 0 = the fixed rule's value */
+  int32_t chunks;
+  float time_us;     /* the search's time for this level (informational) */
+} hpez_level_sched;
+
+typedef struct hpez_tuning hpez_tuning;
+
+/* A table of level schedules (host memory; no GPU needed). */
+HPEZ_API int hpez_tuning_create(hpez_tuning** out);
+HPEZ_API int hpez_tuning_destroy(hpez_tuning* t);
+/* Insert or replace one entry.  INVALID_ARG for an out-of-range key or
+ * family. */
+HPEZ_API int hpez_tuning_set(hpez_tuning* t, const hpez_level_key* key,
+                             const hpez_level_sched* sched);
+/* *found = 1 and *sched filled when the key is in the table, else 0. */
+HPEZ_API int hpez_tuning_get(const hpez_tuning* t, const hpez_level_key* key,
+                             hpez_level_sched* sched, int* found);
+HPEZ_API int hpez_tuning_count(const hpez_tuning* t, uint64_t* n);
+/* Text file, one entry per line: ndim cls0 cls1 cls2 stride interp
+ * paradigm decomp family tile0 tile1 tile2 chunks time_us ('#' starts a
+ * comment line).  Load merges into the table.  Errors: INVALID_ARG (no
+ * file, or a malformed line, with the table unchanged). */
+HPEZ_API int hpez_tuning_save(const hpez_tuning* t, const char* path);
+HPEZ_API int hpez_tuning_load(hpez_tuning* t, const char* path);
+/* The key of level l (1 = finest) of a field of these dims and config
+ * (NULL = default) in direction decomp.  INVALID_ARG for bad dims, config
+ * or level. */
+HPEZ_API int hpez_level_key_of(int ndim, const uint64_t* dims, const hpez_config* cfg,
+                               int level, int decomp, hpez_level_key* out);
+/* The context copies the table (NULL: back to the fixed rules); batches
+ * and server requests planned afterwards use it. */
+HPEZ_API int hpez_use_tuning(hpez_ctx* ctx, const hpez_tuning* t);
+/* The offline search for one field class: `copies` copies of the device
+ * field (0: enough to hold about 2^25 points) are compressed, and their
+ * streams decompressed, as one batch under each candidate schedule (every
+ * family the field's levels can run, with tile shapes or chunk counts from
+ * a fixed list); each level's ticks are timed with CUDA events over `reps`
+ * runs (median) after a warm-up run, and the fastest candidate of each
+ * level and direction goes into t.  Synchronizes; allocates the batches'
+ * buffers.  Errors as hpez_batch_create_compress. */
+HPEZ_API int hpez_tuning_search(hpez_ctx* ctx, hpez_tuning* t, const float* d_x, int ndim,
+                                const uint64_t* dims, int eb_mode, double eb,
+                                const hpez_config* cfg, int copies, int reps, void* stream);
 
 /* ---- served form (no counterpart in the paper) ----
  * A request loop with continuous batching.  Requests carry HOST buffers.
@@ -489,6 +571,10 @@ HPEZ_API int hpez_lossless_decode(hpez_ctx* ctx, const void* d_in, uint64_t in_s
  *  HPEZ_OPT_LORENZO_CTAS  0 (default: the resident CTAs); n > 0: at most n
  *                         persistent CTAs for the Lorenzo kernels, so each
  *                         streams more blocks back to back
+ *  HPEZ_OPT_BATCH_CTAS    0 (default: the resident CTAs); n > 0: at most n
+ *                         CTAs for each persistent level launch of the
+ *                         batched and served forms, so each CTA walks more
+ *                         tiles of the concatenated work list
  * Errors: INVALID_ARG for an unknown option or an out-of-range value. */
 #define HPEZ_OPT_FUSED_LEVELS 1
 #define HPEZ_OPT_TILE_E0 2
@@ -501,6 +587,7 @@ HPEZ_API int hpez_lossless_decode(hpez_ctx* ctx, const void* d_in, uint64_t in_s
 #define HPEZ_OPT_STREAM_CHUNKS 9
 #define HPEZ_OPT_LORENZO_CTAS 10
 #define HPEZ_OPT_WARP_LEVELS 11
+#define HPEZ_OPT_BATCH_CTAS 12
 HPEZ_API int hpez_set_option(hpez_ctx* ctx, int option, int64_t value);
 
 /* ---- measurement hooks (not part of the paper's method) ----

@@ -21,7 +21,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libhpez.so")
-SOURCES = ["hpez_capi.cu", "hpez_tune.cu", "hpez_engine.cu", "hpez_typed.cu", "k_sweep.cu",
+SOURCES = ["hpez_capi.cu", "hpez_tune.cu", "hpez_engine.cu", "hpez_sched.cu", "hpez_typed.cu",
+           "k_sweep.cu",
            "k_level.cu", "k_level3d.cu", "k_level_md.cu", "k_level_md3.cu", "k_level_md3w.cu",
            "k_huffman.cu", "k_lossless.cu", "k_lorenzo.cu", "k_spline.cu",
            "k_stream.cu",

@@ -484,7 +484,7 @@ bool plan_md3(const hpez_ctx* ctx, const Plan& p, const hpez_config& c, int l,
   if (p.ndim != 3 || p.k != 3) return false;
   if (!plan_md(ctx, p, c, l, decomp, F)) return false;
   if (F.g.m[0] < 2 || F.g.m[1] < 2 || F.g.m[2] < 2) return false;
-  E1 = 16;
+  E1 = ctx->tile_e[1] > 0 ? ((ctx->tile_e[1] + 1) & ~1) : 16;
   while (E1 > 2 && md3_smem_bytes(F, E1) > 96 * 1024) E1 /= 2;
   return md3_smem_bytes(F, E1) <= 160 * 1024;
 }
@@ -748,6 +748,10 @@ int hpez_set_option(hpez_ctx* ctx, int option, int64_t value) {
     case HPEZ_OPT_LORENZO_CTAS:
       if (value < 0 || value > 1000000) return HPEZ_ERR_INVALID_ARG;
       ctx->lorenzo_ctas = (int)value;
+      return HPEZ_OK;
+    case HPEZ_OPT_BATCH_CTAS:
+      if (value < 0 || value > 1000000) return HPEZ_ERR_INVALID_ARG;
+      ctx->batch_ctas = (int)value;
       return HPEZ_OK;
     case HPEZ_OPT_FUSED_SMEM:
       if (value < 4096 || value > 200 * 1024) return HPEZ_ERR_INVALID_ARG;

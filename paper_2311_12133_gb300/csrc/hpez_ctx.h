@@ -4,7 +4,9 @@
 // tuner all use.
 #pragma once
 
+#include <array>
 #include <cstdint>
+#include <map>
 #include <utility>
 #include <vector>
 
@@ -69,8 +71,15 @@ struct PhaseProfiler {
   }
 };
 
+// A table of level schedules of the batched and served forms, keyed by
+// (ndim, cls0, cls1, cls2, stride, interp, paradigm, decomp).
+struct hpez_tuning {
+  std::map<std::array<int32_t, 8>, hpez_level_sched> m;
+};
+
 struct hpez_ctx {
   PhaseProfiler prof;
+  hpez_tuning sched;           // hpez_use_tuning's copy (empty: fixed rules)
   uint64_t launches = 0;
   int fused_levels = 1;        // HPEZ_OPT_FUSED_LEVELS
   int level3d = 1;             // HPEZ_OPT_LEVEL3D
@@ -79,6 +88,7 @@ struct hpez_ctx {
   int drop_copy = 0;           // HPEZ_OPT_DROP_COPY
   int stream_chunks = 0;       // HPEZ_OPT_STREAM_CHUNKS (0 = heuristic)
   int lorenzo_ctas = 0;        // HPEZ_OPT_LORENZO_CTAS (0 = resident CTAs)
+  int batch_ctas = 0;          // HPEZ_OPT_BATCH_CTAS (0 = resident CTAs)
   // the value range of the last tuned input (order-preserving keys), which
   // the compress call of hpez_compress_auto reuses instead of a second pass
   bool range_hint_on = false;
@@ -174,6 +184,13 @@ bool plan_level3d(const hpez_ctx* ctx, const Plan& p, const hpez_config& c,
 uint64_t n_anchors(const Plan& p);
 bool plan_md(const hpez_ctx* ctx, const Plan& p, const hpez_config& c, int l,
              bool decomp, LevelMD& F);
+// the schedule-table key of level l of a planned field (sc: the config
+// the sweep runs)
+std::array<int32_t, 8> sched_key(const Plan& p, const hpez_config& sc, int l, bool decomp);
+// a 3D multi-dimensional level as even-plane and odd-plane launches of
+// E1-row tiles (HPEZ_OPT_TILE_E1 > 0 sets the rows)
+bool plan_md3(const hpez_ctx* ctx, const Plan& p, const hpez_config& c, int l,
+              bool decomp, LevelMD& F, int& E1);
 // the predictor a sweep runs: a block map with one interpolator for every
 // block becomes that interpolator at every level
 hpez_config sweep_config(const hpez_config& c, const uint8_t* h_bmap,

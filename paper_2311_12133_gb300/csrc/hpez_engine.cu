@@ -44,8 +44,23 @@ enum OpType : int {
   OP_UPS = OP_LVL_D + 4, OP_PASS_C, OP_PASS_D,
   OP_ZERO, OP_HIST, OP_SCAN, OP_CODEBOOK, OP_ENCLEN, OP_LAYOUT, OP_PACK,
   OP_OUTL, OP_FINAL, OP_CWORDS, OP_DECTAB, OP_DECODE, OP_FILL, OP_RESULT,
-  OP_COUNT
+  OP_MD3E_C,              // + interpolator (0..2): 3D multi-dimensional level,
+  OP_MD3E_D = OP_MD3E_C + 3,  // even planes
+  OP_MD3O_C = OP_MD3E_D + 3,  // odd planes
+  OP_MD3O_D = OP_MD3O_C + 3,
+  OP_MD3W_C = OP_MD3O_D + 3,  // finest level as warp strips
+  OP_MD3W_D = OP_MD3W_C + 3,
+  OP_COUNT = OP_MD3W_D + 3
 };
+
+// The batched form runs ops of equal key in one tick: the ops before the
+// sweep by position, a level's ops by (level, position within the level),
+// so that every field's level l runs in the same launches, and the ops
+// after the sweep by position.
+constexpr uint32_t kKeyLevel = 1u << 16, kKeyPost = 2u << 16;
+uint32_t level_key(int l, int sub) {
+  return kKeyLevel + ((uint32_t)(kMaxLevels + 1 - l) << 8) + (uint32_t)sub;
+}
 
 bool one_cta_per_job(int t) {
   return t == OP_INIT || t == OP_PARAMS || t == OP_SCAN || t == OP_CODEBOOK ||
@@ -56,6 +71,7 @@ struct Op {
   int type;
   uint32_t nblk;  // blocks of this job
   uint32_t smem;  // dynamic shared memory
+  uint32_t key;   // tick of the batched form
   std::vector<unsigned char> job;
 };
 
@@ -65,6 +81,7 @@ Op make_op(int type, const J& j, uint32_t nblk = 1, uint32_t smem = 0) {
   o.type = type;
   o.nblk = nblk < 1 ? 1 : nblk;
   o.smem = smem;
+  o.key = 0;
   o.job.resize(sizeof(J));
   std::memcpy(o.job.data(), &j, sizeof(J));
   return o;
@@ -85,6 +102,159 @@ struct Request {
 };
 
 size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// ---------------------------------------------------------------------
+// the kernel family of one level (the same order of preference as the
+// single-field call, without the TMA-streamed level)
+// ---------------------------------------------------------------------
+enum LevelFamily { FAM_LEVEL3D, FAM_MD3W, FAM_MD3, FAM_FUSED, FAM_PASS };
+
+struct LevelPick {
+  int fam = FAM_PASS;
+  Level3D F3;
+  FusedLevel F;
+  LevelMD FM;
+  int E1 = 0;
+  int n1 = 0, n2 = 0, K = 0;
+  uint32_t ctas = 0;
+};
+
+// The schedule `want` (HPEZ_FAM_*) for level l when the level can run it.
+bool pick_family(hpez_ctx* ctx, const Plan& p, const hpez_config& sc, int l, bool decomp,
+                 const void* in, const void* rs, int want, const int tile[3], int chunks,
+                 LevelPick& k) {
+  const void* al = reinterpret_cast<const void*>((uintptr_t)256);
+  int saved[3];
+  for (int s = 0; s < 3; ++s) {
+    saved[s] = ctx->tile_e[s];
+    if (tile[s] > 0) ctx->tile_e[s] = tile[s];
+  }
+  bool ok = false;
+  switch (want) {
+    case HPEZ_FAM_LEVEL3D:
+      ok = ctx->fused_levels && plan_level3d(ctx, p, sc, l, decomp, k.F3);
+      if (ok) k.fam = FAM_LEVEL3D;
+      break;
+    case HPEZ_FAM_MD3W:
+    case HPEZ_FAM_MD3:
+      ok = plan_md3(ctx, p, sc, l, decomp, k.FM, k.E1);
+      if (ok && want == HPEZ_FAM_MD3W) {
+        const float* Rs = l == 1 && decomp ? static_cast<const float*>(rs)
+                                           : static_cast<const float*>(al);
+        ok = md3w_supported(k.FM, decomp, in, static_cast<const float*>(al),
+                            static_cast<const uint16_t*>(al), const_cast<float*>(Rs),
+                            static_cast<const uint16_t*>(al));
+        if (ok) {
+          k.fam = FAM_MD3W;
+          md3w_geometry(decomp, sc.interp[l - 1], k.FM, ctx->num_sms, chunks, &k.n1, &k.n2,
+                        &k.K, &k.ctas);
+        }
+      } else if (ok) {
+        k.fam = FAM_MD3;
+      }
+      break;
+    case HPEZ_FAM_FUSED:
+      ok = ctx->fused_levels && plan_fused(ctx, p, sc, l, decomp, k.F);
+      if (ok) k.fam = FAM_FUSED;
+      break;
+    case HPEZ_FAM_PASS:
+      ok = true;
+      k.fam = FAM_PASS;
+      break;
+  }
+  for (int s = 0; s < 3; ++s) ctx->tile_e[s] = saved[s];
+  return ok;
+}
+
+// in: the field (compress) or the code array (decompress); rs: the level's
+// reconstruction (decompress level 1: the caller's output).  Arena buffers
+// are 256-byte aligned.  The context's schedule table first, then the
+// fixed rules.
+LevelPick pick_level(hpez_ctx* ctx, const Plan& p, const hpez_config& sc, int l, bool decomp,
+                     const void* in, const void* rs) {
+  LevelPick k;
+  if (sc.interp[l - 1] == HPEZ_SPLINE_GLOBAL) return k;
+  const int none[3] = {0, 0, 0};
+  if (!ctx->sched.m.empty()) {
+    const auto it = ctx->sched.m.find(sched_key(p, sc, l, decomp));
+    if (it != ctx->sched.m.end()) {
+      const hpez_level_sched& v = it->second;
+      LevelPick t;
+      if (pick_family(ctx, p, sc, l, decomp, in, rs, v.family, v.tile, v.chunks, t)) return t;
+    }
+  }
+  if (pick_family(ctx, p, sc, l, decomp, in, rs, HPEZ_FAM_LEVEL3D, none, 0, k)) return k;
+  if (ctx->warp_levels &&
+      pick_family(ctx, p, sc, l, decomp, in, rs, HPEZ_FAM_MD3W, none, ctx->stream_chunks, k))
+    return k;
+  if (pick_family(ctx, p, sc, l, decomp, in, rs, HPEZ_FAM_MD3, none, 0, k)) return k;
+  if (pick_family(ctx, p, sc, l, decomp, in, rs, HPEZ_FAM_FUSED, none, 0, k)) return k;
+  k = LevelPick();
+  return k;
+}
+
+// The ops of level l, keyed (l, position).  Compress: in = the field;
+// decompress: in = the code array and Rs of level 1 = the caller's output.
+void add_level_ops(hpez_ctx* ctx, const Plan& p, const hpez_config& sc, int l,
+                   bool decomp, const SweepBufs& sb, const float* Rc, const uint16_t* Cc,
+                   float* Rs, uint16_t* Cs, const void* in, Ctl* ctl, std::vector<Op>& ops) {
+  const int g = l - 1;
+  const int kind = sc.interp[l - 1];
+  const int sms = ctx->num_sms;
+  int sub = 0;
+  auto add = [&](Op o) {
+    o.key = level_key(l, sub++);
+    ops.push_back(std::move(o));
+  };
+  const LevelPick k = pick_level(ctx, p, sc, l, decomp, in, Rs);
+  const float* X = decomp ? nullptr : static_cast<const float*>(in);
+  const uint16_t* codes = decomp ? static_cast<const uint16_t*>(in) : nullptr;
+  const float* outl = decomp ? sb.outl_full : nullptr;
+  switch (k.fam) {
+    case FAM_LEVEL3D: {
+      Level3DJob j{k.F3, X, codes, outl, Rc, decomp ? nullptr : Cc, Rs,
+                   decomp ? nullptr : Cs, ctl};
+      add(make_op((decomp ? OP_L3D_D : OP_L3D_C) + kind, j, (uint32_t)(k.F3.nt0 * k.F3.nt1),
+                  (uint32_t)level3d_smem_bytes(k.F3, decomp)));
+      return;
+    }
+    case FAM_MD3W: {
+      MD3WJob j{k.FM, k.n1, k.n2, k.K, in, outl, Rc, decomp ? nullptr : Cc, Rs,
+                decomp ? nullptr : Cs, ctl};
+      add(make_op((decomp ? OP_MD3W_D : OP_MD3W_C) + kind, j, k.ctas));
+      return;
+    }
+    case FAM_MD3: {
+      const int m0 = (int)k.FM.g.m[0], m1 = (int)k.FM.g.m[1];
+      const int nt1 = (m1 + k.E1 - 1) / k.E1;
+      MD3Job j{k.FM, k.E1, nt1, X, codes, outl, Rc, decomp ? nullptr : Cc, Rs,
+               decomp ? nullptr : Cs, ctl};
+      const uint32_t smem = (uint32_t)md3_smem_bytes(k.FM, k.E1);
+      add(make_op((decomp ? OP_MD3E_D : OP_MD3E_C) + kind, j,
+                  (uint32_t)(((m0 + 1) / 2) * nt1), smem));
+      if (m0 / 2 > 0)
+        add(make_op((decomp ? OP_MD3O_D : OP_MD3O_C) + kind, j, (uint32_t)((m0 / 2) * nt1),
+                    smem));
+      return;
+    }
+    case FAM_FUSED: {
+      LevelJob j{k.F, sb, Rc, decomp ? nullptr : Cc, Rs, decomp ? nullptr : Cs};
+      add(make_op((decomp ? OP_LVL_D : OP_LVL_C) + level_kind(sb), j, k.F.ntiles,
+                  (uint32_t)fused_smem_bytes(k.F, decomp)));
+      return;
+    }
+    default:
+      break;
+  }
+  add(make_op(OP_UPS,
+              UpsampleJob{p.grid[l], p.gsize[l], p.grid[g], Rc, decomp ? nullptr : Cc, Rs,
+                          decomp ? nullptr : Cs, ctl},
+              grid_blocks(p.gsize[l], 65535)));
+  for (const Launch& L : level_schedule(p, sc, l))
+    if (L.pb.total)
+      add(make_op(decomp ? OP_PASS_D : OP_PASS_C, PassJob{p.grid[g], L.pb, sb},
+                  pass_blocks(L.pb.total, sms)));
+}
 
 // ---------------------------------------------------------------------
 // planning: with base == nullptr only the workspace size is computed
@@ -121,14 +291,8 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   ctx->x_aligned16 = (reinterpret_cast<uintptr_t>(d_in) & 15u) == 0;
   // the finest level's fused kernels write no reconstruction in compress:
   // its grid is then not allocated
-  bool need_r0 = true;
-  {
-    FusedLevel F;
-    Level3D F3;
-    if (ctx->fused_levels && (plan_level3d(ctx, p, sc, 1, false, F3) ||
-                              plan_fused(ctx, p, sc, 1, false, F)))
-      need_r0 = false;
-  }
+  const LevelPick pick1 = pick_level(ctx, p, sc, 1, false, d_in, nullptr);
+  const bool need_r0 = pick1.fam == FAM_MD3 || pick1.fam == FAM_PASS;
 
   Arena ar;
   const size_t o_ctl = ar.take<Ctl>(1);
@@ -143,7 +307,9 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   size_t o_R[kMaxLevels + 1], o_C[kMaxLevels + 1];
   for (int g = 0; g <= p.L; ++g) {
     o_R[g] = (g > 0 || need_r0) ? ar.take<float>(p.gsize[g]) : 0;
-    o_C[g] = ar.take<uint16_t>(p.gsize[g]);
+    // two spare codes: kernels may read a code as the aligned 4-byte word
+    // that holds it
+    o_C[g] = ar.take<uint16_t>(p.gsize[g] + 2);
   }
   const size_t o_zc = ar.take<uint32_t>(p.nch);
   const size_t o_zoff = ar.take<unsigned long long>(p.nch);
@@ -204,10 +370,15 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   const int sms = ctx->num_sms;
   uint8_t* out = static_cast<uint8_t*>(d_out);
   auto& ops = r.ops;
-  ops.push_back(make_op(OP_INIT, InitJob{ctl}));
+  uint32_t kpre = 0, kpost = kKeyPost;
+  auto pre = [&](Op o) { o.key = kpre++; ops.push_back(std::move(o)); };
+  auto post = [&](Op o) { o.key = kpost++; ops.push_back(std::move(o)); };
+  pre(make_op(OP_INIT, InitJob{ctl}));
   if (eb_mode == HPEZ_EB_REL)
-    ops.push_back(make_op(OP_RANGE, RangeJob{d_in, p.N, ctl},
-                          grid_blocks(p.N / 4 + 1, (unsigned)sms * 8)));
+    pre(make_op(OP_RANGE, RangeJob{d_in, p.N, ctl},
+                grid_blocks(p.N / 4 + 1, (unsigned)sms * 8)));
+  else
+    ++kpre;
   ParamsJob pj;
   pj.ctl = ctl;
   pj.eb_mode = eb_mode;
@@ -216,11 +387,9 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   pj.alpha = cfg.alpha;
   pj.beta = cfg.beta;
   pj.x = d_in;
-  ops.push_back(make_op(OP_PARAMS, pj));
-  ops.push_back(make_op(OP_ANCHOR,
-                        AnchorJob{d_in, p.grid[p.L], p.gsize[p.L], R[p.L],
-                                  Cg[p.L], ctl},
-                        grid_blocks(p.gsize[p.L], 65535)));
+  pre(make_op(OP_PARAMS, pj));
+  pre(make_op(OP_ANCHOR, AnchorJob{d_in, p.grid[p.L], p.gsize[p.L], R[p.L], Cg[p.L], ctl},
+              grid_blocks(p.gsize[p.L], 65535)));
   SweepBufs sb;
   std::memset(&sb, 0, sizeof(sb));
   sb.x = d_in;
@@ -234,43 +403,20 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
     sb.C = Cg[g];
     sb.kind = sc.interp[l - 1];
     sb.same = sc.same_level[l - 1];
-    FusedLevel F;
-    Level3D F3;
-    if (ctx->fused_levels && plan_level3d(ctx, p, sc, l, false, F3)) {
-      Level3DJob j{F3, d_in, nullptr, nullptr, R[l], Cg[l], R[g], Cg[g], ctl};
-      ops.push_back(make_op(OP_L3D_C + sb.kind, j, (uint32_t)(F3.nt0 * F3.nt1),
-                            (uint32_t)level3d_smem_bytes(F3, false)));
-    } else if (ctx->fused_levels && plan_fused(ctx, p, sc, l, false, F)) {
-      LevelJob j{F, sb, R[l], Cg[l], R[g], Cg[g]};
-      ops.push_back(make_op(OP_LVL_C + level_kind(sb), j, F.ntiles,
-                            (uint32_t)fused_smem_bytes(F, false)));
-    } else {
-      ops.push_back(make_op(OP_UPS,
-                            UpsampleJob{p.grid[l], p.gsize[l], p.grid[g], R[l],
-                                        Cg[l], R[g], Cg[g], ctl},
-                            grid_blocks(p.gsize[l], 65535)));
-      for (const Launch& L : level_schedule(p, sc, l))
-        if (L.pb.total)
-          ops.push_back(make_op(OP_PASS_C, PassJob{p.grid[g], L.pb, sb},
-                                pass_blocks(L.pb.total, sms)));
-    }
+    add_level_ops(ctx, p, sc, l, false, sb, R[l], Cg[l], R[g], Cg[g], d_in, ctl, ops);
   }
   uint16_t* codes = Cg[0];
-  ops.push_back(make_op(OP_ZERO, ZeroJob{hist, 65536ull * 4}, 16));
-  ops.push_back(make_op(OP_HIST, HistJob{codes, p.N, p.C, p.nch, hist, zc, ctl},
-                        hist_blocks(p.nch, sms)));
-  ops.push_back(make_op(OP_SCAN, ScanJob{zc, zoff, p.nch, &ctl->n_out, ctl}));
-  ops.push_back(make_op(OP_CODEBOOK, CodebookJob{hist, enc, tsyms, tlens, gkeys,
-                                                 giw, gpar, lbs, ctl}));
-  ops.push_back(make_op(OP_ENCLEN,
-                        EncLenJob{codes, p.N, p.C, p.nch, enc, lbits, chw, ctl},
-                        enc_blocks(p.nch, sms)));
-  ops.push_back(make_op(OP_SCAN, ScanJob{chw, woff, p.nch, &ctl->total_words, ctl}));
-  ops.push_back(make_op(OP_LAYOUT, LayoutJob{ctl, off_table, out_cap}));
-  ops.push_back(make_op(OP_PACK,
-                        PackJob{codes, p.N, p.C, p.nch, enc, lbits, chw, woff,
-                                out, ctl},
-                        enc_blocks(p.nch, sms)));
+  post(make_op(OP_ZERO, ZeroJob{hist, 65536ull * 4}, 16));
+  post(make_op(OP_HIST, HistJob{codes, p.N, p.C, p.nch, hist, zc, ctl},
+               hist_blocks(p.nch, sms)));
+  post(make_op(OP_SCAN, ScanJob{zc, zoff, p.nch, &ctl->n_out, ctl}));
+  post(make_op(OP_CODEBOOK, CodebookJob{hist, enc, tsyms, tlens, gkeys, giw, gpar, lbs, ctl}));
+  post(make_op(OP_ENCLEN, EncLenJob{codes, p.N, p.C, p.nch, enc, lbits, chw, ctl},
+               enc_blocks(p.nch, sms)));
+  post(make_op(OP_SCAN, ScanJob{chw, woff, p.nch, &ctl->total_words, ctl}));
+  post(make_op(OP_LAYOUT, LayoutJob{ctl, off_table, out_cap}));
+  post(make_op(OP_PACK, PackJob{codes, p.N, p.C, p.nch, enc, lbits, chw, woff, out, ctl},
+               enc_blocks(p.nch, sms)));
   OutlierJob oj;
   oj.codes = codes;
   oj.N = p.N;
@@ -284,11 +430,11 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   oj.max_out = ~0ull;
   oj.ctl = ctl;
   oj.gather = 1;
-  ops.push_back(make_op(OP_OUTL, oj, p.nch));
+  post(make_op(OP_OUTL, oj, p.nch));
   FinalizeJob fj{hdr_d, hdrc_d, out, R[p.L], (uint32_t)na, off_anchors, bmap,
                  p.nblocks, off_bmap, lbits, p.nch, off_chw, tsyms, tlens, ctl};
-  ops.push_back(make_op(OP_FINAL, fj, finalize_blocks((uint32_t)na, p.nch, sms)));
-  ops.push_back(make_op(OP_RESULT, ResultJob{ctl, nullptr, 0, 0, d_size, d_status, 0}));
+  post(make_op(OP_FINAL, fj, finalize_blocks((uint32_t)na, p.nch, sms)));
+  post(make_op(OP_RESULT, ResultJob{ctl, nullptr, 0, 0, d_size, d_status, 0}));
   return HPEZ_OK;
 }
 
@@ -321,9 +467,12 @@ int plan_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
     if (!base) return HPEZ_OK;
     Ctl* ctl = reinterpret_cast<Ctl*>(base + o_ctl);
     ops.push_back(make_op(OP_INIT, InitJob{ctl}));
+    ops.back().key = 0;
     ops.push_back(make_op(OP_FILL, FillJob{d_out, (uint32_t)si.N, si.const_value},
                           grid_blocks(si.N, (unsigned)sms * 16)));
+    ops.back().key = 1;
     ops.push_back(make_op(OP_RESULT, ResultJob{ctl, nullptr, 0, 0, nullptr, d_status, 1}));
+    ops.back().key = kKeyPost;
     return HPEZ_OK;
   }
   Arena ar;
@@ -336,7 +485,7 @@ int plan_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   const size_t o_gkeys = ar.take<unsigned long long>(65536);
   size_t o_R[kMaxLevels + 1];
   for (int g = 1; g < p.L; ++g) o_R[g] = ar.take<float>(p.gsize[g]);
-  const size_t o_codes = ar.take<uint16_t>(si.N);
+  const size_t o_codes = ar.take<uint16_t>(si.N + 2);  // 2 spare: 4-byte code reads
   const size_t o_zc = ar.take<uint32_t>(p.nch);
   const size_t o_zoff = ar.take<unsigned long long>(p.nch);
   const size_t o_woff = ar.take<unsigned long long>(p.nch);
@@ -363,7 +512,9 @@ int plan_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   R[0] = d_out;
   R[p.L] = const_cast<float*>(reinterpret_cast<const float*>(in + si.oa));
 
-  ops.push_back(make_op(OP_INIT, InitJob{ctl}));
+  uint32_t kpre = 0;
+  auto pre = [&](Op o) { o.key = kpre++; ops.push_back(std::move(o)); };
+  pre(make_op(OP_INIT, InitJob{ctl}));
   ParamsJob pj;
   pj.ctl = ctl;
   pj.eb_mode = HPEZ_EB_ABS;
@@ -372,13 +523,13 @@ int plan_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   pj.alpha = cfg.alpha;
   pj.beta = cfg.beta;
   pj.x = d_out;
-  ops.push_back(make_op(OP_PARAMS, pj));
+  pre(make_op(OP_PARAMS, pj));
   const uint8_t* lbits_stream = in + si.ocw;
-  ops.push_back(make_op(OP_CWORDS, ChunkWordsJob{lbits_stream, p.nch, dchw},
-                        chunk_words_blocks(p.nch, sms)));
-  ops.push_back(make_op(OP_SCAN, ScanJob{dchw, woff, p.nch, &tot[0], ctl}));
-  ops.push_back(make_op(OP_DECTAB, DecTablesJob{in, si.nused, si.ot, lut, cnt,
-                                                first, offs, sorted, gkeys, ctl}));
+  pre(make_op(OP_CWORDS, ChunkWordsJob{lbits_stream, p.nch, dchw},
+              chunk_words_blocks(p.nch, sms)));
+  pre(make_op(OP_SCAN, ScanJob{dchw, woff, p.nch, &tot[0], ctl}));
+  pre(make_op(OP_DECTAB,
+              DecTablesJob{in, si.nused, si.ot, lut, cnt, first, offs, sorted, gkeys, ctl}));
   DecodeJob dj;
   dj.stream = in;
   dj.off_bits = si.ob;
@@ -398,8 +549,8 @@ int plan_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   dj.codes = codes;
   dj.zc = zc;
   dj.ctl = ctl;
-  ops.push_back(make_op(OP_DECODE, dj, decode_blocks(p.nch, sms)));
-  ops.push_back(make_op(OP_SCAN, ScanJob{zc, zoff, p.nch, &tot[1], ctl}));
+  pre(make_op(OP_DECODE, dj, decode_blocks(p.nch, sms)));
+  pre(make_op(OP_SCAN, ScanJob{zc, zoff, p.nch, &tot[1], ctl}));
   OutlierJob oj;
   oj.codes = codes;
   oj.N = p.N;
@@ -413,7 +564,7 @@ int plan_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   oj.max_out = si.nout;
   oj.ctl = ctl;
   oj.gather = 0;
-  ops.push_back(make_op(OP_OUTL, oj, p.nch));
+  pre(make_op(OP_OUTL, oj, p.nch));
   SweepBufs sb;
   std::memset(&sb, 0, sizeof(sb));
   sb.codes_full = codes;
@@ -429,29 +580,11 @@ int plan_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
     sb.R = R[g];
     sb.kind = cfg.interp[l - 1];
     sb.same = cfg.same_level[l - 1];
-    FusedLevel F;
-    Level3D F3;
-    if (ctx->fused_levels && plan_level3d(ctx, p, cfg, l, true, F3)) {
-      Level3DJob j{F3, nullptr, codes, d_out, R[l], nullptr, R[g], nullptr, ctl};
-      ops.push_back(make_op(OP_L3D_D + sb.kind, j, (uint32_t)(F3.nt0 * F3.nt1),
-                            (uint32_t)level3d_smem_bytes(F3, true)));
-    } else if (ctx->fused_levels && plan_fused(ctx, p, cfg, l, true, F)) {
-      LevelJob j{F, sb, R[l], nullptr, R[g], nullptr};
-      ops.push_back(make_op(OP_LVL_D + level_kind(sb), j, F.ntiles,
-                            (uint32_t)fused_smem_bytes(F, true)));
-    } else {
-      ops.push_back(make_op(OP_UPS,
-                            UpsampleJob{p.grid[l], p.gsize[l], p.grid[g], R[l],
-                                        nullptr, R[g], nullptr, ctl},
-                            grid_blocks(p.gsize[l], 65535)));
-      for (const Launch& L : level_schedule(p, cfg, l))
-        if (L.pb.total)
-          ops.push_back(make_op(OP_PASS_D, PassJob{p.grid[g], L.pb, sb},
-                                pass_blocks(L.pb.total, sms)));
-    }
+    add_level_ops(ctx, p, cfg, l, true, sb, R[l], nullptr, R[g], nullptr, codes, ctl, ops);
   }
   ops.push_back(make_op(OP_RESULT, ResultJob{ctl, tot, si.twords, si.nout,
                                              nullptr, d_status, 1}));
+  ops.back().key = kKeyPost;
   return HPEZ_OK;
 }
 
@@ -504,28 +637,42 @@ void build_tick(const std::vector<const Op*>& ops, std::vector<unsigned char>& t
   }
 }
 
-void launch_entry(const Entry& e, const unsigned char* d_tab, cudaStream_t s) {
+// Level ops run as persistent launches of at most max_ctas CTAs (0: the
+// CTAs resident on the GPU at once).
+void launch_entry(const Entry& e, const unsigned char* d_tab, int sms, int max_ctas,
+                  cudaStream_t s) {
   const void* J = d_tab + e.jobs_off;
   const uint32_t* off = reinterpret_cast<const uint32_t*>(d_tab + e.off_off);
   const int t = e.type;
   if (t >= OP_L3D_C && t < OP_L3D_C + 3) {
     launch_level3d_batch(false, t - OP_L3D_C, (const Level3DJob*)J, off, e.nj,
-                         e.nblk, e.smem, s);
+                         e.nblk, e.smem, sms, max_ctas, s);
     return;
   }
   if (t >= OP_L3D_D && t < OP_L3D_D + 3) {
     launch_level3d_batch(true, t - OP_L3D_D, (const Level3DJob*)J, off, e.nj,
-                         e.nblk, e.smem, s);
+                         e.nblk, e.smem, sms, max_ctas, s);
     return;
   }
   if (t >= OP_LVL_C && t < OP_LVL_C + 4) {
     launch_level_batch(false, t - OP_LVL_C, (const LevelJob*)J, off, e.nj, e.nblk,
-                       e.smem, s);
+                       e.smem, sms, max_ctas, s);
     return;
   }
   if (t >= OP_LVL_D && t < OP_LVL_D + 4) {
     launch_level_batch(true, t - OP_LVL_D, (const LevelJob*)J, off, e.nj, e.nblk,
-                       e.smem, s);
+                       e.smem, sms, max_ctas, s);
+    return;
+  }
+  if (t >= OP_MD3E_C && t < OP_MD3W_C) {
+    const int u = t - OP_MD3E_C;  // (odd, decomp, kind)
+    launch_md3_batch((u / 3) % 2 == 1, u >= 6, u % 3, (const MD3Job*)J, off, e.nj, e.nblk,
+                     e.smem, sms, max_ctas, s);
+    return;
+  }
+  if (t >= OP_MD3W_C && t < OP_COUNT) {
+    const int u = t - OP_MD3W_C;
+    launch_md3w_batch(u >= 3, u % 3, (const MD3WJob*)J, off, e.nj, e.nblk, sms, max_ctas, s);
     return;
   }
   switch (t) {
@@ -582,19 +729,19 @@ struct TickStreams {
   }
 };
 
-void enqueue_tick(const std::vector<Entry>& es, const unsigned char* d_tab,
-                  cudaStream_t s, TickStreams& ts) {
+void enqueue_tick(const std::vector<Entry>& es, const unsigned char* d_tab, int sms,
+                  int max_ctas, cudaStream_t s, TickStreams& ts) {
   const int n = (int)es.size();
   const int nside = std::min(kSide, n - 1);
   if (nside <= 0 || !ts.fork) {
-    for (const Entry& e : es) launch_entry(e, d_tab, s);
+    for (const Entry& e : es) launch_entry(e, d_tab, sms, max_ctas, s);
     return;
   }
   cudaEventRecord(ts.fork, s);
   for (int i = 0; i < nside; ++i) cudaStreamWaitEvent(ts.side[i], ts.fork, 0);
   for (int i = 0; i < n; ++i) {
     const int k = i % (nside + 1);
-    launch_entry(es[i], d_tab, k == 0 ? s : ts.side[k - 1]);
+    launch_entry(es[i], d_tab, sms, max_ctas, k == 0 ? s : ts.side[k - 1]);
   }
   for (int i = 0; i < nside; ++i) {
     cudaEventRecord(ts.join[i], ts.side[i]);
@@ -624,6 +771,7 @@ struct hpez_batch {
   unsigned long long* d_sizes = nullptr;
   int* d_status = nullptr;
   std::vector<std::vector<Entry>> ticks;
+  std::vector<uint32_t> tick_keys;  // the op key of each tick
   uint64_t launches = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -683,18 +831,19 @@ int batch_create(hpez_ctx* ctx, int n, int decomp, const void* descs,
       return rc;
     }
   }
-  // the tick sequence: every request advances by one operation per tick
-  std::vector<size_t> cur(n, 0);
+  // the tick sequence: one tick per op key, in key order (a request's keys
+  // increase along its ops), so every field's level l shares the launches
+  // of that level
+  std::map<uint32_t, std::vector<const Op*>> by_key;
+  for (int i = 0; i < n; ++i)
+    for (const Op& o : reqs[i].ops) by_key[o.key].push_back(&o);
   std::vector<unsigned char> tab;
-  for (;;) {
-    std::vector<const Op*> now;
-    for (int i = 0; i < n; ++i)
-      if (cur[i] < reqs[i].ops.size()) now.push_back(&reqs[i].ops[cur[i]++]);
-    if (now.empty()) break;
+  for (auto& kv : by_key) {
     std::vector<Entry> es;
-    build_tick(now, tab, es);
+    build_tick(kv.second, tab, es);
     b->launches += es.size();
     b->ticks.push_back(std::move(es));
+    b->tick_keys.push_back(kv.first);
   }
   if (b->ts.create()) {
     cudaGetLastError();
@@ -717,7 +866,8 @@ int batch_create(hpez_ctx* ctx, int n, int decomp, const void* descs,
 }
 
 void batch_enqueue(hpez_batch* b, cudaStream_t s) {
-  for (const auto& es : b->ticks) enqueue_tick(es, b->d_tab, s, b->ts);
+  for (const auto& es : b->ticks)
+    enqueue_tick(es, b->d_tab, b->ctx->num_sms, b->ctx->batch_ctas, s, b->ts);
 }
 
 }  // namespace
@@ -806,6 +956,223 @@ int hpez_batch_destroy(hpez_batch* b) {
 }
 
 }  // extern "C"
+
+// =====================================================================
+// offline search of level schedules
+// =====================================================================
+namespace {
+
+// The candidate schedules of the search: every family with tile shapes or
+// chunk counts from a fixed list (slot extents slowest first).
+std::vector<hpez_level_sched> sched_candidates(int ndim) {
+  std::vector<hpez_level_sched> c;
+  auto add = [&](int fam, int t0, int t1, int t2, int chunks) {
+    hpez_level_sched v;
+    v.family = fam;
+    v.tile[0] = t0;
+    v.tile[1] = t1;
+    v.tile[2] = t2;
+    v.chunks = chunks;
+    v.time_us = 0.f;
+    c.push_back(v);
+  };
+  if (ndim == 3) {
+    for (int e1 : {2, 4, 8, 16, 32}) add(HPEZ_FAM_LEVEL3D, 0, e1, 0, 0);
+    for (int ch : {1, 2, 4, 8, 16, 0}) add(HPEZ_FAM_MD3W, 0, 0, 0, ch);
+    for (int e1 : {2, 4, 8, 16, 32}) add(HPEZ_FAM_MD3, 0, e1, 0, 0);
+    const int f3[][3] = {{1, 2, 512}, {1, 4, 256}, {1, 8, 128}, {2, 8, 128},
+                         {2, 4, 256}, {1, 16, 64}, {2, 16, 64}, {4, 8, 64}};
+    for (const auto& f : f3) add(HPEZ_FAM_FUSED, f[0], f[1], f[2], 0);
+  } else {
+    const int f2[][2] = {{2, 512}, {4, 256}, {8, 128}, {16, 64},
+                         {8, 256}, {16, 128}, {32, 64}, {4, 512}};
+    for (const auto& f : f2) add(HPEZ_FAM_FUSED, 1, f[0], f[1], 0);
+  }
+  add(HPEZ_FAM_PASS, 0, 0, 0, 0);
+  return c;
+}
+
+int level_of_key(uint32_t key) {
+  if (key < kKeyLevel || key >= kKeyPost) return 0;
+  return (int)(kMaxLevels + 1) - (int)((key - kKeyLevel) >> 8);
+}
+
+// One run of the batch with an event before every tick and after the last;
+// per level l (1..kMaxLevels) the milliseconds of its ticks, added to ms[l].
+int timed_run(hpez_batch* b, cudaStream_t s, std::vector<double>& ms) {
+  const size_t n = b->ticks.size();
+  std::vector<cudaEvent_t> ev(n + 1, nullptr);
+  int rc = HPEZ_OK;
+  for (size_t i = 0; i <= n && !rc; ++i) rc = cuda_check(cudaEventCreate(&ev[i]));
+  if (!rc) {
+    for (size_t i = 0; i < n; ++i) {
+      cudaEventRecord(ev[i], s);
+      enqueue_tick(b->ticks[i], b->d_tab, b->ctx->num_sms, b->ctx->batch_ctas, s, b->ts);
+    }
+    cudaEventRecord(ev[n], s);
+    rc = cuda_check(cudaStreamSynchronize(s));
+  }
+  ms.assign(kMaxLevels + 1, 0.0);
+  for (size_t i = 0; i < n && !rc; ++i) {
+    float t = 0.f;
+    rc = cuda_check(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+    const int l = level_of_key(b->tick_keys[i]);
+    if (l >= 1 && l <= kMaxLevels) ms[l] += t;
+  }
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  return rc;
+}
+
+// The median over `reps` timed runs (after one warm-up run) of each
+// level's time, in microseconds.
+int time_levels(hpez_batch* b, cudaStream_t s, int reps, std::vector<double>& us) {
+  std::vector<double> ms;
+  int rc = timed_run(b, s, ms);
+  std::vector<std::vector<double>> all(kMaxLevels + 1);
+  for (int r = 0; r < reps && !rc; ++r) {
+    rc = timed_run(b, s, ms);
+    for (int l = 1; l <= kMaxLevels; ++l) all[l].push_back(ms[l]);
+  }
+  us.assign(kMaxLevels + 1, 0.0);
+  for (int l = 1; l <= kMaxLevels && !rc; ++l) {
+    std::sort(all[l].begin(), all[l].end());
+    us[l] = all[l].empty() ? 0.0 : 1000.0 * all[l][all[l].size() / 2];
+  }
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int hpez_tuning_search(hpez_ctx* ctx, hpez_tuning* t, const float* d_x, int ndim,
+                                  const uint64_t* dims, int eb_mode, double eb,
+                                  const hpez_config* cfg_in, int copies, int reps,
+                                  void* stream) {
+  if (!ctx || !t || !d_x || !dims || ndim < 1 || ndim > 3) return HPEZ_ERR_INVALID_ARG;
+  if (copies < 0 || copies > 1024 || reps < 1 || reps > 100) return HPEZ_ERR_INVALID_ARG;
+  hpez_config cfg;
+  if (cfg_in)
+    cfg = *cfg_in;
+  else
+    default_config(ndim, &cfg);
+  Plan p;
+  int rc = plan_geometry(p, ndim, dims, cfg.anchor_stride, cfg.frozen_dim);
+  if (rc) return rc;
+  if ((rc = check_config(p, cfg))) return rc;
+  if (cfg.blockwise && !cfg.h_blockmap) return HPEZ_ERR_INVALID_ARG;
+  if (cfg.predictor) return HPEZ_ERR_UNSUPPORTED;
+  plan_chunks_blocks(p, cfg);
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (copies == 0) copies = (int)std::max<uint64_t>(1, std::min<uint64_t>(64, (1ull << 25) / p.N));
+  uint64_t bound = 0;
+  if ((rc = hpez_compress_bound(ndim, dims, &bound))) return rc;
+  bound = (bound + 255) & ~255ull;
+  const uint64_t out_f = ((uint64_t)p.N * 4 + 255) & ~255ull;
+  char* buf = nullptr;
+  if (cudaMalloc(&buf, (size_t)copies * (bound + out_f)) != cudaSuccess) {
+    cudaGetLastError();
+    return HPEZ_ERR_NO_MEMORY;
+  }
+  const hpez_config sc = sweep_config(cfg, cfg.h_blockmap, p.nblocks);
+  // every level key of this field in both directions (compress plans the
+  // sweep config, decompress the header's config)
+  std::vector<std::array<int32_t, 8>> keys[2];
+  for (int dir = 0; dir < 2; ++dir)
+    for (int l = 1; l <= p.L; ++l) keys[dir].push_back(sched_key(p, dir ? cfg : sc, l, dir != 0));
+  const hpez_tuning saved = ctx->sched;
+  // best[dir][l]: the fastest feasible candidate so far
+  std::vector<hpez_level_sched> best[2];
+  for (int dir = 0; dir < 2; ++dir) {
+    best[dir].assign(p.L + 1, hpez_level_sched());
+    for (auto& v : best[dir]) {
+      v.family = 0;
+      v.time_us = INFINITY;
+    }
+  }
+  std::vector<hpez_field_desc> fd(copies);
+  std::vector<hpez_stream_desc> sd(copies);
+  std::vector<uint64_t> sizes(copies);
+  std::vector<int32_t> status(copies);
+  std::vector<uint8_t> hdr(kHeaderBytes);
+  for (const hpez_level_sched& c : sched_candidates(ndim)) {
+    if (rc) break;
+    ctx->sched.m.clear();
+    for (int dir = 0; dir < 2; ++dir)
+      for (const auto& k : keys[dir]) ctx->sched.m[k] = c;
+    // the levels that run this candidate
+    bool feas[2][kMaxLevels + 1] = {};
+    bool any = false;
+    for (int dir = 0; dir < 2; ++dir)
+      for (int l = 1; l <= p.L; ++l) {
+        LevelPick k;
+        const void* in = dir ? reinterpret_cast<const void*>((uintptr_t)256) : d_x;
+        const void* rs = reinterpret_cast<const void*>((uintptr_t)(buf + (size_t)copies * bound));
+        feas[dir][l] = pick_family(ctx, p, dir ? cfg : sc, l, dir != 0, in, rs, c.family,
+                                   c.tile, c.chunks, k);
+        any = any || feas[dir][l];
+      }
+    if (!any) continue;
+    for (int i = 0; i < copies; ++i) {
+      hpez_field_desc& f = fd[i];
+      std::memset(&f, 0, sizeof(f));
+      f.d_in = d_x;
+      f.ndim = ndim;
+      f.eb_mode = eb_mode;
+      for (int d = 0; d < ndim; ++d) f.dims[d] = dims[d];
+      f.eb = eb;
+      f.cfg = &cfg;
+      f.d_out = buf + (size_t)i * bound;
+      f.out_cap = bound;
+    }
+    hpez_batch* bc = nullptr;
+    rc = batch_create(ctx, copies, 0, fd.data(), &bc);
+    if (rc) break;
+    std::vector<double> us;
+    rc = time_levels(bc, s, reps, us);
+    if (!rc) rc = hpez_batch_results(bc, s, sizes.data(), status.data());
+    hpez_batch_destroy(bc);
+    for (int i = 0; i < copies && !rc; ++i)
+      if (status[i]) rc = status[i];
+    if (rc) break;
+    for (int l = 1; l <= p.L; ++l)
+      if (feas[0][l] && us[l] < best[0][l].time_us) {
+        best[0][l] = c;
+        best[0][l].time_us = (float)us[l];
+      }
+    rc = cuda_check(cudaMemcpy(hdr.data(), buf, kHeaderBytes, cudaMemcpyDeviceToHost));
+    if (rc) break;
+    for (int i = 0; i < copies; ++i) {
+      hpez_stream_desc& d = sd[i];
+      d.d_in = buf + (size_t)i * bound;
+      d.in_size = sizes[i];
+      d.h_header = hdr.data();
+      d.d_out = reinterpret_cast<float*>(buf + (size_t)copies * bound + (size_t)i * out_f);
+      d.out_cap_elems = p.N;
+    }
+    hpez_batch* bd = nullptr;
+    rc = batch_create(ctx, copies, 1, sd.data(), &bd);
+    if (rc) break;
+    rc = time_levels(bd, s, reps, us);
+    if (!rc) rc = hpez_batch_results(bd, s, nullptr, status.data());
+    hpez_batch_destroy(bd);
+    for (int i = 0; i < copies && !rc; ++i)
+      if (status[i]) rc = status[i];
+    if (rc) break;
+    for (int l = 1; l <= p.L; ++l)
+      if (feas[1][l] && us[l] < best[1][l].time_us) {
+        best[1][l] = c;
+        best[1][l].time_us = (float)us[l];
+      }
+  }
+  ctx->sched = saved;
+  cudaFree(buf);
+  if (rc) return rc;
+  for (int dir = 0; dir < 2; ++dir)
+    for (int l = 1; l <= p.L; ++l)
+      if (best[dir][l].family) t->m[keys[dir][l - 1]] = best[dir][l];
+  return HPEZ_OK;
+}
 
 // =====================================================================
 // served form
@@ -1199,7 +1566,7 @@ int hpez_server_step(hpez_server* S) {
   cudaMemcpyAsync(S->d_tab, S->h_tab[k], tab.size(), cudaMemcpyHostToDevice, s);
   cudaEventRecord(S->tab_ev[k], s);
   S->tab_used[k] = true;
-  enqueue_tick(es, S->d_tab, s, S->ts);
+  enqueue_tick(es, S->d_tab, S->ctx->num_sms, S->ctx->batch_ctas, s, S->ts);
   S->launches += es.size();
   S->ctx->launches += es.size();
   ++S->ticks;

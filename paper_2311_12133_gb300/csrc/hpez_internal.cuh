@@ -388,15 +388,35 @@ struct TuneGeom {
 // blockIdx.x - off[j] plays the role the block index plays in the
 // single-field launch.  Single-CTA stages run one block per job.
 // ---------------------------------------------------------------------
-__device__ __forceinline__ int batch_job(const uint32_t* __restrict__ off,
-                                         int nj) {
+__device__ __forceinline__ int batch_job_of(const uint32_t* __restrict__ off,
+                                            int nj, uint32_t b) {
   int lo = 0, hi = nj - 1;
-  const uint32_t b = blockIdx.x;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (__ldg(off + mid) <= b) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+__device__ __forceinline__ int batch_job(const uint32_t* __restrict__ off,
+                                         int nj) {
+  return batch_job_of(off, nj, blockIdx.x);
+}
+
+// Persistent batched launch: the grid holds at most the CTAs resident on
+// the GPU at once, and CTA c walks the launch's virtual blocks c,
+// c + gridDim.x, ... (job j owns virtual blocks [off[j], off[j+1])).  The
+// barrier between two virtual blocks keeps the next one from overwriting
+// shared memory the previous one still reads; every thread of a CTA walks
+// the same sequence, so the barrier is reached by all.
+template <class Body>
+__device__ __forceinline__ void for_each_batch_block(const uint32_t* __restrict__ off,
+                                                     int nj, Body body) {
+  const uint32_t total = __ldg(off + nj);
+  for (uint32_t v = blockIdx.x; v < total; v += gridDim.x) {
+    if (v != blockIdx.x) __syncthreads();
+    const int j = batch_job_of(off, nj, v);
+    body(j, v - __ldg(off + j));
+  }
 }
 
 struct InitJob { Ctl* ctl; };
@@ -428,6 +448,19 @@ struct Level3DJob {
 struct LevelJob {
   FusedLevel P; SweepBufs B; const float* Rc; const uint16_t* Cc; float* Rs;
   uint16_t* Cs;
+};
+// a 3D multi-dimensional level: even planes, then odd planes, in tiles of
+// E1 rows (nt1 tiles per plane)
+struct MD3Job {
+  LevelMD P; int E1, nt1; const float* X; const uint16_t* codes_full;
+  const float* outl_full; const float* Rc; const uint16_t* Cc; float* Rs;
+  uint16_t* Cs; const Ctl* ctl;
+};
+// the finest 3D multi-dimensional level as warp strips: n1 x n2 strips per
+// chunk of K even planes
+struct MD3WJob {
+  LevelMD P; int n1, n2, K; const void* in; const float* outl; const float* Rc;
+  const uint16_t* Cc; float* Rs; uint16_t* Cs; const Ctl* ctl;
 };
 struct HistJob {
   const uint16_t* codes; uint32_t N, C, nch; uint32_t* hist; uint32_t* zc;

@@ -8,6 +8,25 @@
 
 namespace hpez {
 
+// Grid of a persistent batched launch: the CTAs of `kernel` resident on
+// num_sms SMs at once (at most max_ctas when > 0), never more than the
+// launch's nblk virtual blocks.
+template <class K>
+unsigned persistent_grid(K kernel, int threads, size_t smem, uint32_t nblk, int num_sms,
+                         int max_ctas) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  if (per_sm < 1) per_sm = 1;
+  uint64_t g = (uint64_t)per_sm * (uint64_t)(num_sms > 0 ? num_sms : 1);
+  if (max_ctas > 0 && (uint64_t)max_ctas < g) g = (uint64_t)max_ctas;
+  if (g > nblk) g = nblk;
+  return (unsigned)(g ? g : 1);
+}
+
 // k_sweep.cu
 void launch_init_ctl(Ctl* ctl, cudaStream_t s);
 void launch_fill(float* out, uint32_t N, float v, int num_sms,
@@ -133,12 +152,20 @@ void launch_anchor_batch(const AnchorJob* J, const uint32_t* off, int nj,
                          uint32_t nblk, cudaStream_t s);
 void launch_fill_batch(const FillJob* J, const uint32_t* off, int nj,
                        uint32_t nblk, cudaStream_t s);
+// persistent level launches (at most max_ctas CTAs when > 0)
 void launch_level3d_batch(bool decomp, int kind, const Level3DJob* J,
                           const uint32_t* off, int nj, uint32_t nblk,
-                          size_t smem, cudaStream_t s);
+                          size_t smem, int num_sms, int max_ctas, cudaStream_t s);
 void launch_level_batch(bool decomp, int kind, const LevelJob* J,
                         const uint32_t* off, int nj, uint32_t nblk, size_t smem,
-                        cudaStream_t s);
+                        int num_sms, int max_ctas, cudaStream_t s);
+void launch_md3_batch(bool decomp, bool odd, int kind, const MD3Job* J, const uint32_t* off,
+                      int nj, uint32_t nblk, size_t smem, int num_sms, int max_ctas,
+                      cudaStream_t s);
+void md3w_geometry(bool decomp, int kind, const LevelMD& P, int num_sms, int chunks, int* n1,
+                   int* n2, int* K, uint32_t* ctas);
+void launch_md3w_batch(bool decomp, int kind, const MD3WJob* J, const uint32_t* off, int nj,
+                       uint32_t nblk, int num_sms, int max_ctas, cudaStream_t s);
 int level_kind(const SweepBufs& B);
 uint32_t hist_blocks(uint32_t nch, int num_sms);
 uint32_t enc_blocks(uint32_t nch, int num_sms);

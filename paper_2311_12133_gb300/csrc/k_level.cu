@@ -439,14 +439,15 @@ __global__ void __launch_bounds__(256)
   level_body<kDecomp, KIND>(P, B, Rc, Cc, Rs, Cs, blockIdx.x);
 }
 
-// batched: job j owns tiles [off[j], off[j+1]) of the launch
+// batched, persistent: job j owns tiles [off[j], off[j+1]) of the launch
 template <bool kDecomp, int KIND>
 __global__ void __launch_bounds__(256)
     k_level_batch(const LevelJob* __restrict__ J, const uint32_t* __restrict__ off,
                   int nj) {
-  const int j = batch_job(off, nj);
-  const LevelJob& q = J[j];
-  level_body<kDecomp, KIND>(q.P, q.B, q.Rc, q.Cc, q.Rs, q.Cs, blockIdx.x - off[j]);
+  for_each_batch_block(off, nj, [&](int j, uint32_t t) {
+    const LevelJob& q = J[j];
+    level_body<kDecomp, KIND>(q.P, q.B, q.Rc, q.Cc, q.Rs, q.Cs, t);
+  });
 }
 
 size_t fused_smem_bytes(const FusedLevel& P, bool decomp) {
@@ -495,35 +496,39 @@ void launch_level(bool decomp, const FusedLevel& P, const SweepBufs& B,
 
 template <bool kDecomp, int KIND>
 static void launch_kind_b(const LevelJob* J, const uint32_t* off, int nj,
-                          uint32_t nblk, size_t smem, cudaStream_t s) {
+                          uint32_t nblk, size_t smem, int num_sms, int max_ctas,
+                          cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_level_batch<kDecomp, KIND>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  k_level_batch<kDecomp, KIND><<<nblk, 256, smem, s>>>(J, off, nj);
+  const unsigned grid =
+      persistent_grid(k_level_batch<kDecomp, KIND>, 256, smem, nblk, num_sms, max_ctas);
+  k_level_batch<kDecomp, KIND><<<grid, 256, smem, s>>>(J, off, nj);
 }
 
 // kind: the interpolator of every job, or 3 for the per-point path (block
 // map or same-level), the value level_kind() returns
 void launch_level_batch(bool decomp, int kind, const LevelJob* J,
                         const uint32_t* off, int nj, uint32_t nblk, size_t smem,
-                        cudaStream_t s) {
+                        int num_sms, int max_ctas, cudaStream_t s) {
   if (!nblk) return;
+  const int k = kind == LINEAR || kind == CUBIC_NAK || kind == CUBIC_NAT ? kind : 3;
   if (decomp) {
-    switch (kind) {
-      case LINEAR: launch_kind_b<true, LINEAR>(J, off, nj, nblk, smem, s); break;
-      case CUBIC_NAK: launch_kind_b<true, CUBIC_NAK>(J, off, nj, nblk, smem, s); break;
-      case CUBIC_NAT: launch_kind_b<true, CUBIC_NAT>(J, off, nj, nblk, smem, s); break;
-      default: launch_kind_b<true, 3>(J, off, nj, nblk, smem, s); break;
+    switch (k) {
+      case LINEAR: launch_kind_b<true, LINEAR>(J, off, nj, nblk, smem, num_sms, max_ctas, s); break;
+      case CUBIC_NAK: launch_kind_b<true, CUBIC_NAK>(J, off, nj, nblk, smem, num_sms, max_ctas, s); break;
+      case CUBIC_NAT: launch_kind_b<true, CUBIC_NAT>(J, off, nj, nblk, smem, num_sms, max_ctas, s); break;
+      default: launch_kind_b<true, 3>(J, off, nj, nblk, smem, num_sms, max_ctas, s); break;
     }
   } else {
-    switch (kind) {
-      case LINEAR: launch_kind_b<false, LINEAR>(J, off, nj, nblk, smem, s); break;
-      case CUBIC_NAK: launch_kind_b<false, CUBIC_NAK>(J, off, nj, nblk, smem, s); break;
-      case CUBIC_NAT: launch_kind_b<false, CUBIC_NAT>(J, off, nj, nblk, smem, s); break;
-      default: launch_kind_b<false, 3>(J, off, nj, nblk, smem, s); break;
+    switch (k) {
+      case LINEAR: launch_kind_b<false, LINEAR>(J, off, nj, nblk, smem, num_sms, max_ctas, s); break;
+      case CUBIC_NAK: launch_kind_b<false, CUBIC_NAK>(J, off, nj, nblk, smem, num_sms, max_ctas, s); break;
+      case CUBIC_NAT: launch_kind_b<false, CUBIC_NAT>(J, off, nj, nblk, smem, num_sms, max_ctas, s); break;
+      default: launch_kind_b<false, 3>(J, off, nj, nblk, smem, num_sms, max_ctas, s); break;
     }
   }
 }

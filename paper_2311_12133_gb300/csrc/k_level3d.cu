@@ -338,16 +338,17 @@ __global__ void __launch_bounds__(256)
                               blockIdx.x);
 }
 
-// batched: job j owns tiles [off[j], off[j+1]) of the launch
+// batched, persistent: job j owns tiles [off[j], off[j+1]) of the launch
 template <bool kDecomp, int KIND>
 __global__ void __launch_bounds__(256)
     k_level3d_batch(const Level3DJob* __restrict__ J,
                     const uint32_t* __restrict__ off, int nj) {
-  const int j = batch_job(off, nj);
-  const Level3DJob& q = J[j];
-  const Level3D P = q.P;
-  level3d_body<kDecomp, KIND>(P, q.X, q.codes_full, q.outl_full, q.Rc, q.Cc,
-                              q.Rs, q.Cs, q.ctl, blockIdx.x - off[j]);
+  for_each_batch_block(off, nj, [&](int j, uint32_t t) {
+    const Level3DJob& q = J[j];
+    const Level3D P = q.P;
+    level3d_body<kDecomp, KIND>(P, q.X, q.codes_full, q.outl_full, q.Rc, q.Cc,
+                                q.Rs, q.Cs, q.ctl, t);
+  });
 }
 
 size_t level3d_smem_bytes(const Level3D& P, bool decomp) {
@@ -387,28 +388,33 @@ void launch_level3d(bool decomp, const Level3D& P, const SweepBufs& B,
 
 template <bool kDecomp, int KIND>
 static void launch3b(const Level3DJob* J, const uint32_t* off, int nj,
-                     uint32_t nblk, size_t smem, cudaStream_t s) {
+                     uint32_t nblk, size_t smem, int num_sms, int max_ctas,
+                     cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_level3d_batch<kDecomp, KIND>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  k_level3d_batch<kDecomp, KIND><<<nblk, 256, smem, s>>>(J, off, nj);
+  const unsigned grid =
+      persistent_grid(k_level3d_batch<kDecomp, KIND>, 256, smem, nblk, num_sms, max_ctas);
+  k_level3d_batch<kDecomp, KIND><<<grid, 256, smem, s>>>(J, off, nj);
 }
 
 void launch_level3d_batch(bool decomp, int kind, const Level3DJob* J,
                           const uint32_t* off, int nj, uint32_t nblk,
-                          size_t smem, cudaStream_t s) {
+                          size_t smem, int num_sms, int max_ctas, cudaStream_t s) {
   if (!nblk) return;
   if (decomp) {
-    if (kind == LINEAR) launch3b<true, LINEAR>(J, off, nj, nblk, smem, s);
-    else if (kind == CUBIC_NAK) launch3b<true, CUBIC_NAK>(J, off, nj, nblk, smem, s);
-    else launch3b<true, CUBIC_NAT>(J, off, nj, nblk, smem, s);
+    if (kind == LINEAR) launch3b<true, LINEAR>(J, off, nj, nblk, smem, num_sms, max_ctas, s);
+    else if (kind == CUBIC_NAK)
+      launch3b<true, CUBIC_NAK>(J, off, nj, nblk, smem, num_sms, max_ctas, s);
+    else launch3b<true, CUBIC_NAT>(J, off, nj, nblk, smem, num_sms, max_ctas, s);
   } else {
-    if (kind == LINEAR) launch3b<false, LINEAR>(J, off, nj, nblk, smem, s);
-    else if (kind == CUBIC_NAK) launch3b<false, CUBIC_NAK>(J, off, nj, nblk, smem, s);
-    else launch3b<false, CUBIC_NAT>(J, off, nj, nblk, smem, s);
+    if (kind == LINEAR) launch3b<false, LINEAR>(J, off, nj, nblk, smem, num_sms, max_ctas, s);
+    else if (kind == CUBIC_NAK)
+      launch3b<false, CUBIC_NAK>(J, off, nj, nblk, smem, num_sms, max_ctas, s);
+    else launch3b<false, CUBIC_NAT>(J, off, nj, nblk, smem, num_sms, max_ctas, s);
   }
 }
 

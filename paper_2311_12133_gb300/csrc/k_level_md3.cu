@@ -116,19 +116,18 @@ __device__ __forceinline__ void finish(const LevelMD& P, const Tile& T, int r,
 // even planes: coarse copy, (0,1,0), (0,0,1), (0,1,1)
 // ---------------------------------------------------------------------
 template <bool kDecomp, int KIND>
-__global__ void __launch_bounds__(256)
-    k_md3_even(LevelMD P, int E1, int nt1, const float* __restrict__ X,
-               const uint16_t* __restrict__ codes_full,
-               const float* __restrict__ outl_full, const float* __restrict__ Rc,
-               const uint16_t* __restrict__ Cc, float* __restrict__ Rs,
-               uint16_t* __restrict__ Cs, const Ctl* __restrict__ ctl) {
+__device__ __forceinline__ void md3_even_body(
+    const LevelMD& P, int E1, int nt1, const float* __restrict__ X,
+    const uint16_t* __restrict__ codes_full, const float* __restrict__ outl_full,
+    const float* __restrict__ Rc, const uint16_t* __restrict__ Cc, float* __restrict__ Rs,
+    uint16_t* __restrict__ Cs, const Ctl* __restrict__ ctl, unsigned bid) {
   if (ctl->status || ctl->is_const) return;
   extern __shared__ float sm[];
   const int li = P.level - 1;
   const float el = ctl->el[li], inv2 = ctl->inv2[li], twoe = ctl->twoe[li];
   const LevelGeom& g = P.g;
-  const int c0 = (int)(blockIdx.x / (unsigned)nt1);
-  const Tile T = make_tile(P, 2 * c0, (int)(blockIdx.x % (unsigned)nt1), E1);
+  const int c0 = (int)(bid / (unsigned)nt1);
+  const Tile T = make_tile(P, 2 * c0, (int)(bid % (unsigned)nt1), E1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int m1 = (int)g.m[1], m2 = (int)g.m[2];
   // even planes hold every value the odd planes read along dim 0
@@ -187,19 +186,18 @@ __global__ void __launch_bounds__(256)
 // odd planes: (1,0,0), (1,0,1), (1,1,0), (1,1,1)
 // ---------------------------------------------------------------------
 template <bool kDecomp, int KIND>
-__global__ void __launch_bounds__(256)
-    k_md3_odd(LevelMD P, int E1, int nt1, const float* __restrict__ X,
-              const uint16_t* __restrict__ codes_full,
-              const float* __restrict__ outl_full, const float* __restrict__ Rc,
-              float* __restrict__ Rs, uint16_t* __restrict__ Cs,
-              const Ctl* __restrict__ ctl) {
+__device__ __forceinline__ void md3_odd_body(
+    const LevelMD& P, int E1, int nt1, const float* __restrict__ X,
+    const uint16_t* __restrict__ codes_full, const float* __restrict__ outl_full,
+    const float* __restrict__ Rc, float* __restrict__ Rs, uint16_t* __restrict__ Cs,
+    const Ctl* __restrict__ ctl, unsigned bid) {
   if (ctl->status || ctl->is_const) return;
   extern __shared__ float sm[];
   const int li = P.level - 1;
   const float el = ctl->el[li], inv2 = ctl->inv2[li], twoe = ctl->twoe[li];
   const LevelGeom& g = P.g;
-  const int c0 = (int)(blockIdx.x / (unsigned)nt1);
-  const Tile T = make_tile(P, 2 * c0 + 1, (int)(blockIdx.x % (unsigned)nt1), E1);
+  const int c0 = (int)(bid / (unsigned)nt1);
+  const Tile T = make_tile(P, 2 * c0 + 1, (int)(bid % (unsigned)nt1), E1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int m0 = (int)g.m[0], m1 = (int)g.m[1], m2 = (int)g.m[2];
   const bool keep = kDecomp || P.write_recon;
@@ -266,6 +264,58 @@ __global__ void __launch_bounds__(256)
                       inv2, twoe, keep);
     }
   }
+}
+
+template <bool kDecomp, int KIND>
+__global__ void __launch_bounds__(256)
+    k_md3_even(LevelMD P, int E1, int nt1, const float* __restrict__ X,
+               const uint16_t* __restrict__ codes_full,
+               const float* __restrict__ outl_full, const float* __restrict__ Rc,
+               const uint16_t* __restrict__ Cc, float* __restrict__ Rs,
+               uint16_t* __restrict__ Cs, const Ctl* __restrict__ ctl) {
+  md3_even_body<kDecomp, KIND>(P, E1, nt1, X, codes_full, outl_full, Rc, Cc, Rs, Cs, ctl,
+                               blockIdx.x);
+}
+
+template <bool kDecomp, int KIND>
+__global__ void __launch_bounds__(256)
+    k_md3_odd(LevelMD P, int E1, int nt1, const float* __restrict__ X,
+              const uint16_t* __restrict__ codes_full,
+              const float* __restrict__ outl_full, const float* __restrict__ Rc,
+              float* __restrict__ Rs, uint16_t* __restrict__ Cs,
+              const Ctl* __restrict__ ctl) {
+  md3_odd_body<kDecomp, KIND>(P, E1, nt1, X, codes_full, outl_full, Rc, Rs, Cs, ctl,
+                              blockIdx.x);
+}
+
+// batched, persistent: job j owns the tiles [off[j], off[j+1]) of the
+// launch (even planes in one launch, odd planes in the next)
+template <bool kDecomp, int KIND, bool kOdd>
+__global__ void __launch_bounds__(256)
+    k_md3_batch(const MD3Job* __restrict__ J, const uint32_t* __restrict__ off, int nj) {
+  for_each_batch_block(off, nj, [&](int j, uint32_t t) {
+    const MD3Job& q = J[j];
+    if (kOdd)
+      md3_odd_body<kDecomp, KIND>(q.P, q.E1, q.nt1, q.X, q.codes_full, q.outl_full, q.Rc,
+                                  q.Rs, q.Cs, q.ctl, t);
+    else
+      md3_even_body<kDecomp, KIND>(q.P, q.E1, q.nt1, q.X, q.codes_full, q.outl_full, q.Rc,
+                                   q.Cc, q.Rs, q.Cs, q.ctl, t);
+  });
+}
+
+template <bool kDecomp, int KIND, bool kOdd>
+void launch_md3_b(const MD3Job* J, const uint32_t* off, int nj, uint32_t nblk, size_t smem,
+                  int num_sms, int max_ctas, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_md3_batch<kDecomp, KIND, kOdd>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  const unsigned grid =
+      persistent_grid(k_md3_batch<kDecomp, KIND, kOdd>, 256, smem, nblk, num_sms, max_ctas);
+  k_md3_batch<kDecomp, KIND, kOdd><<<grid, 256, smem, s>>>(J, off, nj);
 }
 
 template <bool kDecomp, int KIND>
@@ -912,6 +962,35 @@ bool md3s_supported(const LevelMD& P, bool decomp, const void* in, const float* 
 
 // Returns the chunks along dim 0 (0 when the tensor maps could not be
 // made; nothing was launched then).
+void launch_md3_batch(bool decomp, bool odd, int kind, const MD3Job* J, const uint32_t* off,
+                      int nj, uint32_t nblk, size_t smem, int num_sms, int max_ctas,
+                      cudaStream_t s) {
+  if (!nblk) return;
+#define HPEZ_MD3B(D, K, O) launch_md3_b<D, K, O>(J, off, nj, nblk, smem, num_sms, max_ctas, s)
+  if (decomp) {
+    if (odd) {
+      if (kind == LINEAR) HPEZ_MD3B(true, LINEAR, true);
+      else if (kind == CUBIC_NAK) HPEZ_MD3B(true, CUBIC_NAK, true);
+      else HPEZ_MD3B(true, CUBIC_NAT, true);
+    } else {
+      if (kind == LINEAR) HPEZ_MD3B(true, LINEAR, false);
+      else if (kind == CUBIC_NAK) HPEZ_MD3B(true, CUBIC_NAK, false);
+      else HPEZ_MD3B(true, CUBIC_NAT, false);
+    }
+  } else {
+    if (odd) {
+      if (kind == LINEAR) HPEZ_MD3B(false, LINEAR, true);
+      else if (kind == CUBIC_NAK) HPEZ_MD3B(false, CUBIC_NAK, true);
+      else HPEZ_MD3B(false, CUBIC_NAT, true);
+    } else {
+      if (kind == LINEAR) HPEZ_MD3B(false, LINEAR, false);
+      else if (kind == CUBIC_NAK) HPEZ_MD3B(false, CUBIC_NAK, false);
+      else HPEZ_MD3B(false, CUBIC_NAT, false);
+    }
+  }
+#undef HPEZ_MD3B
+}
+
 int launch_level_md3s(bool decomp, int kind, const LevelMD& P, const SweepBufs& B,
                       const float* Rc, const uint16_t* Cc, float* Rs, uint16_t* Cs,
                       Ctl* ctl, int num_sms, int drop_copy, int chunks, cudaStream_t s) {

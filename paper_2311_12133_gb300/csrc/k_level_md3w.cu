@@ -450,17 +450,19 @@ __device__ __forceinline__ void w_group(const WConst& K, const WStrip& S, const 
 }
 
 template <bool kDecomp, int KIND>
-__global__ void __launch_bounds__(32 * kWWarps, kDecomp ? 7 : 5)
-    k_md3w(LevelMD P, int n1, int n2, int K, const void* __restrict__ in,
-           const float* __restrict__ outl, const float* __restrict__ Rc,
-           const uint16_t* __restrict__ Cc, float* __restrict__ Rs, uint16_t* __restrict__ Cs,
-           const Ctl* __restrict__ ctl) {
+__device__ __forceinline__ void md3w_body(const LevelMD& P, int n1, int n2, int K,
+                                          const void* __restrict__ in,
+                                          const float* __restrict__ outl,
+                                          const float* __restrict__ Rc,
+                                          const uint16_t* __restrict__ Cc,
+                                          float* __restrict__ Rs, uint16_t* __restrict__ Cs,
+                                          const Ctl* __restrict__ ctl, unsigned bid) {
   using W = WK<KIND>;
   constexpr int kWD = wdepth<kDecomp>();
   if (ctl->status || ctl->is_const) return;
   extern __shared__ __align__(16) unsigned char wsm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int wid = blockIdx.x * kWWarps + warp;
+  const int wid = (int)bid * kWWarps + warp;
   const int s2 = wid % n2, s1 = (wid / n2) % n1, chunk = wid / (n1 * n2);
   WStrip S;
   S.m0 = (int)P.g.m[0];
@@ -588,6 +590,58 @@ __global__ void __launch_bounds__(32 * kWWarps, kDecomp ? 7 : 5)
 }
 
 template <bool kDecomp, int KIND>
+__global__ void __launch_bounds__(32 * kWWarps, kDecomp ? 7 : 5)
+    k_md3w(LevelMD P, int n1, int n2, int K, const void* __restrict__ in,
+           const float* __restrict__ outl, const float* __restrict__ Rc,
+           const uint16_t* __restrict__ Cc, float* __restrict__ Rs, uint16_t* __restrict__ Cs,
+           const Ctl* __restrict__ ctl) {
+  md3w_body<kDecomp, KIND>(P, n1, n2, K, in, outl, Rc, Cc, Rs, Cs, ctl, blockIdx.x);
+}
+
+// batched: job j owns the CTAs (groups of kWWarps strips) [off[j], off[j+1])
+// of the launch.  The kernel is persistent by construction: each warp
+// streams the K even planes of its chunk (and the odd planes between them)
+// through its own staging slots, and the planner sizes the chunks so that
+// the launch holds about the CTAs resident at once.
+template <bool kDecomp, int KIND>
+__global__ void __launch_bounds__(32 * kWWarps, kDecomp ? 7 : 5)
+    k_md3w_batch(const MD3WJob* __restrict__ J, const uint32_t* __restrict__ off, int nj) {
+  const int j = batch_job(off, nj);
+  const MD3WJob& q = J[j];
+  md3w_body<kDecomp, KIND>(q.P, q.n1, q.n2, q.K, q.in, q.outl, q.Rc, q.Cc, q.Rs, q.Cs, q.ctl,
+                           blockIdx.x - __ldg(off + j));
+}
+
+template <bool kDecomp, int KIND>
+void launch_md3w_b(const MD3WJob* J, const uint32_t* off, int nj, uint32_t nblk,
+                   int num_sms, int max_ctas, cudaStream_t s) {
+  const int smem = kWWarps * wsmem_per_warp<kDecomp, KIND>();
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_md3w_batch<kDecomp, KIND>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  (void)num_sms;
+  (void)max_ctas;
+  k_md3w_batch<kDecomp, KIND><<<nblk, 32 * kWWarps, smem, s>>>(J, off, nj);
+}
+
+template <bool kDecomp, int KIND>
+int md3w_occupancy() {
+  const int smem = kWWarps * wsmem_per_warp<kDecomp, KIND>();
+  static int per_sm = 0;
+  if (!per_sm) {
+    cudaFuncSetAttribute(k_md3w<kDecomp, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_md3w<kDecomp, KIND>,
+                                                  32 * kWWarps, smem);
+    if (per_sm < 1) per_sm = 1;
+  }
+  return per_sm;
+}
+
+template <bool kDecomp, int KIND>
 int launch_md3w_k(const LevelMD& P, const void* in, const float* outl, const float* Rc,
                   const uint16_t* Cc, float* Rs, uint16_t* Cs, const Ctl* ctl, int num_sms,
                   int chunks, cudaStream_t s) {
@@ -659,6 +713,53 @@ int launch_level_md3w(bool decomp, int kind, const LevelMD& P, const SweepBufs& 
   if (kind == CUBIC_NAK)
     return launch_md3w_k<false, CUBIC_NAK>(P, in, outl, Rc, Cc, Rs, Cs, ctl, num_sms, chunks, s);
   return launch_md3w_k<false, CUBIC_NAT>(P, in, outl, Rc, Cc, Rs, Cs, ctl, num_sms, chunks, s);
+}
+
+// The geometry of a warp-strip level: strips per chunk (n1 x n2), even
+// planes per chunk K, CTAs.  chunks <= 0: as many chunks as fill the GPU
+// with this field alone.
+void md3w_geometry(bool decomp, int kind, const LevelMD& P, int num_sms, int chunks, int* n1,
+                   int* n2, int* K, uint32_t* ctas) {
+  int per_sm;
+  int wc;
+  if (decomp) {
+    per_sm = kind == LINEAR ? md3w_occupancy<true, LINEAR>()
+                            : (kind == CUBIC_NAK ? md3w_occupancy<true, CUBIC_NAK>()
+                                                 : md3w_occupancy<true, CUBIC_NAT>());
+  } else {
+    per_sm = kind == LINEAR ? md3w_occupancy<false, LINEAR>()
+                            : (kind == CUBIC_NAK ? md3w_occupancy<false, CUBIC_NAK>()
+                                                 : md3w_occupancy<false, CUBIC_NAT>());
+  }
+  wc = kind == LINEAR ? wcols<LINEAR>()
+                      : (kind == CUBIC_NAK ? wcols<CUBIC_NAK>() : wcols<CUBIC_NAT>());
+  const int m0 = (int)P.g.m[0], m1 = (int)P.g.m[1], m2 = (int)P.g.m[2];
+  *n1 = (m1 + kWRows - 1) / kWRows;
+  *n2 = (m2 + wc - 1) / wc;
+  const int ke = (m0 + 1) / 2;
+  const int strips = *n1 * *n2;
+  int nch = chunks > 0 ? chunks : (num_sms * per_sm * kWWarps) / strips;
+  nch = std::max(1, std::min(nch, ke));
+  *K = (ke + nch - 1) / nch;
+  nch = (ke + *K - 1) / *K;
+  const long long warps = (long long)strips * nch;
+  *ctas = (uint32_t)((warps + kWWarps - 1) / kWWarps);
+}
+
+void launch_md3w_batch(bool decomp, int kind, const MD3WJob* J, const uint32_t* off, int nj,
+                       uint32_t nblk, int num_sms, int max_ctas, cudaStream_t s) {
+  if (!nblk) return;
+  if (decomp) {
+    if (kind == LINEAR) launch_md3w_b<true, LINEAR>(J, off, nj, nblk, num_sms, max_ctas, s);
+    else if (kind == CUBIC_NAK)
+      launch_md3w_b<true, CUBIC_NAK>(J, off, nj, nblk, num_sms, max_ctas, s);
+    else launch_md3w_b<true, CUBIC_NAT>(J, off, nj, nblk, num_sms, max_ctas, s);
+  } else {
+    if (kind == LINEAR) launch_md3w_b<false, LINEAR>(J, off, nj, nblk, num_sms, max_ctas, s);
+    else if (kind == CUBIC_NAK)
+      launch_md3w_b<false, CUBIC_NAK>(J, off, nj, nblk, num_sms, max_ctas, s);
+    else launch_md3w_b<false, CUBIC_NAT>(J, off, nj, nblk, num_sms, max_ctas, s);
+  }
 }
 
 }  // namespace hpez

@@ -107,6 +107,26 @@ class hpez_stream_desc(ctypes.Structure):
     ]
 
 
+class hpez_level_key(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("cls", ctypes.c_int32 * 3),
+                ("stride", ctypes.c_int32), ("interp", ctypes.c_int32),
+                ("paradigm", ctypes.c_int32), ("decomp", ctypes.c_int32)]
+
+    def astuple(self):
+        return (self.ndim, *self.cls, self.stride, self.interp, self.paradigm, self.decomp)
+
+
+class hpez_level_sched(ctypes.Structure):
+    _fields_ = [("family", ctypes.c_int32), ("tile", ctypes.c_int32 * 3),
+                ("chunks", ctypes.c_int32), ("time_us", ctypes.c_float)]
+
+    def astuple(self):
+        return (self.family, *self.tile, self.chunks)
+
+
+HPEZ_FAM_LEVEL3D, HPEZ_FAM_MD3W, HPEZ_FAM_MD3, HPEZ_FAM_FUSED, HPEZ_FAM_PASS = 1, 2, 3, 4, 5
+
+
 class hpez_request(ctypes.Structure):
     _fields_ = [
         ("op", ctypes.c_int32),
@@ -224,6 +244,23 @@ def _load():
                                                  ctypes.POINTER(ctypes.c_int), u64p,
                                                  u64p, u64p]),
             "hpez_server_destroy": (ctypes.c_int, [vp]),
+            "hpez_tuning_create": (ctypes.c_int, [ctypes.POINTER(vp)]),
+            "hpez_tuning_destroy": (ctypes.c_int, [vp]),
+            "hpez_tuning_set": (ctypes.c_int, [vp, ctypes.POINTER(hpez_level_key),
+                                               ctypes.POINTER(hpez_level_sched)]),
+            "hpez_tuning_get": (ctypes.c_int, [vp, ctypes.POINTER(hpez_level_key),
+                                               ctypes.POINTER(hpez_level_sched),
+                                               ctypes.POINTER(ctypes.c_int)]),
+            "hpez_tuning_count": (ctypes.c_int, [vp, u64p]),
+            "hpez_tuning_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
+            "hpez_tuning_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
+            "hpez_level_key_of": (ctypes.c_int, [ctypes.c_int, u64p, cfgp, ctypes.c_int,
+                                                 ctypes.c_int,
+                                                 ctypes.POINTER(hpez_level_key)]),
+            "hpez_use_tuning": (ctypes.c_int, [vp, vp]),
+            "hpez_tuning_search": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, u64p, ctypes.c_int,
+                                                  ctypes.c_double, cfgp, ctypes.c_int,
+                                                  ctypes.c_int, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -246,7 +283,13 @@ def exported_symbols() -> list[str]:
             "hpez_batch_create_decompress", "hpez_batch_run", "hpez_batch_run_graph",
             "hpez_batch_results", "hpez_batch_launch_count", "hpez_batch_destroy",
             "hpez_server_create", "hpez_server_submit", "hpez_server_step",
-            "hpez_server_poll", "hpez_server_stats", "hpez_server_destroy"]
+            "hpez_server_poll", "hpez_server_stats", "hpez_server_destroy",
+            "hpez_psnr", "hpez_compress_psnr", "hpez_compress_typed",
+            "hpez_decompress_typed", "hpez_lossless_encode", "hpez_lossless_decode",
+            "hpez_tuning_create", "hpez_tuning_destroy", "hpez_tuning_set",
+            "hpez_tuning_get", "hpez_tuning_count", "hpez_tuning_save",
+            "hpez_tuning_load", "hpez_level_key_of", "hpez_use_tuning",
+            "hpez_tuning_search"]
 
 
 def _check(rc: int, what: str):
@@ -303,6 +346,84 @@ def hpez_decompress(ctx, d_in: int, in_size: int, d_out: int,
                     out_cap_elems: int, stream: int = 0) -> None:
     _check(_load().hpez_decompress(ctx, d_in, in_size, d_out, out_cap_elems,
                                    stream or None), "hpez_decompress")
+
+
+def hpez_level_key_of(shape, cfg: hpez_config | None, level: int, decomp: bool) -> tuple:
+    k = hpez_level_key()
+    _check(_load().hpez_level_key_of(len(shape), _dims(shape), _cfg_ptr(cfg), level,
+                                     int(bool(decomp)), ctypes.byref(k)), "hpez_level_key_of")
+    return k.astuple()
+
+
+def hpez_use_tuning(ctx, tuning) -> None:
+    _check(_load().hpez_use_tuning(ctx, tuning.handle if tuning is not None else None),
+           "hpez_use_tuning")
+
+
+class Tuning:
+    """A table of level schedules of the batched and served forms (host
+    memory): keys are tuples (ndim, cls0, cls1, cls2, stride, interp,
+    paradigm, decomp), values (family, tile0, tile1, tile2, chunks)."""
+
+    def __init__(self, path: str | None = None):
+        h = ctypes.c_void_p(0)
+        _check(_load().hpez_tuning_create(ctypes.byref(h)), "hpez_tuning_create")
+        self.handle = h.value
+        if path is not None:
+            self.load(path)
+
+    @staticmethod
+    def _key(key):
+        k = hpez_level_key()
+        k.ndim, k.cls[0], k.cls[1], k.cls[2], k.stride, k.interp, k.paradigm, k.decomp = key
+        return k
+
+    def set(self, key, family: int, tile=(0, 0, 0), chunks: int = 0, time_us: float = 0.0):
+        v = hpez_level_sched()
+        v.family = family
+        v.tile[0], v.tile[1], v.tile[2] = tile
+        v.chunks = chunks
+        v.time_us = time_us
+        _check(_load().hpez_tuning_set(self.handle, ctypes.byref(self._key(key)),
+                                       ctypes.byref(v)), "hpez_tuning_set")
+
+    def get(self, key):
+        v = hpez_level_sched()
+        found = ctypes.c_int(0)
+        _check(_load().hpez_tuning_get(self.handle, ctypes.byref(self._key(key)),
+                                       ctypes.byref(v), ctypes.byref(found)), "hpez_tuning_get")
+        return v if found.value else None
+
+    def __len__(self):
+        n = ctypes.c_uint64(0)
+        _check(_load().hpez_tuning_count(self.handle, ctypes.byref(n)), "hpez_tuning_count")
+        return n.value
+
+    def save(self, path: str):
+        _check(_load().hpez_tuning_save(self.handle, os.fsencode(path)), "hpez_tuning_save")
+
+    def load(self, path: str):
+        _check(_load().hpez_tuning_load(self.handle, os.fsencode(path)), "hpez_tuning_load")
+
+    def search(self, ctx, x, eb: float, eb_mode: int = 1, cfg: hpez_config | None = None,
+               copies: int = 0, reps: int = 3, stream=None):
+        """The offline search for the class of device field `x` (float32,
+        contiguous): the fastest schedule of each level and direction."""
+        _check(_load().hpez_tuning_search(ctx.handle if hasattr(ctx, "handle") else ctx,
+                                          self.handle, x.data_ptr(), x.dim(), _dims(x.shape),
+                                          eb_mode, float(eb), _cfg_ptr(cfg), copies, reps,
+                                          Context._stream(stream)), "hpez_tuning_search")
+
+    def close(self):
+        if self.handle:
+            _load().hpez_tuning_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 HPEZ_NOALLOC_MAX_POINTS = 2097152
@@ -377,6 +498,7 @@ HPEZ_OPT_TILE_E2, HPEZ_OPT_FUSED_SMEM, HPEZ_OPT_LEVEL3D = 4, 5, 6
 HPEZ_OPT_STREAM_LEVELS = 7
 HPEZ_OPT_DROP_COPY = 8
 HPEZ_OPT_STREAM_CHUNKS, HPEZ_OPT_LORENZO_CTAS, HPEZ_OPT_WARP_LEVELS = 9, 10, 11
+HPEZ_OPT_BATCH_CTAS = 12
 
 
 def hpez_set_option(ctx, option: int, value: int) -> None:

@@ -107,6 +107,89 @@ def test_batch_compress_equals_single_and_oracle(gpu, oracle):
     d.close()
 
 
+def _md_mix():
+    """Fields whose levels run the multi-dimensional kernels of the batched
+    form: warp strips at the finest level (rows of an even length), the
+    even/odd-plane launches elsewhere, every interpolator."""
+    from paper_2311_12133_gb300 import fields
+    return [
+        (fields.make("grf", (40, 48, 64), 11), 1e-3, 1, dict(paradigm=1, interp=0)),
+        (fields.make("bumps", (30, 34, 50), 12), 1e-3, 1, dict(paradigm=1, interp=1)),
+        (fields.make("lognormal", (26, 31, 44), 13), 1e-2, 1, dict(paradigm=1, interp=2)),
+        (fields.make("grf", (65, 20, 36), 14), 1e-4, 1, dict(paradigm=1, interp=0)),
+        (fields.make("grf", (33, 40, 47), 6), 1e-3, 1, dict(paradigm=1, interp=2)),
+        (fields.make("bumps", (40, 36, 33), 1), 1e-3, 1, None),
+        (fields.make("climate2d", (90, 130), 3), 1e-3, 1, None),
+    ]
+
+
+@pytest.mark.parametrize("warp_levels,batch_ctas", [(1, 0), (0, 5), (1, 3)])
+def test_batch_md_levels_and_persistent_walk(gpu, oracle, warp_levels, batch_ctas):
+    """Multi-dimensional levels in the batch, and persistent level launches
+    capped at a few CTAs so each walks many tiles of several fields: the
+    streams and fields equal the oracle's."""
+    import torch
+    from paper_2311_12133_gb300 import hpez
+    hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_WARP_LEVELS, warp_levels)
+    hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_BATCH_CTAS, batch_ctas)
+    try:
+        mix = _md_mix()
+        xs, fields_arg, ocfgs = [], [], []
+        for x, eb, mode, kw in mix:
+            g, o = _cfgs(x, kw)
+            xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+            xs.append(xd)
+            fields_arg.append((xd, eb, mode, g))
+            ocfgs.append(o)
+        b = hpez.Batch(gpu, fields=fields_arg)
+        b.run(graph=True)
+        sizes, status = b.results()
+        assert status == [0] * len(mix)
+        streams = []
+        for i, (x, eb, mode, kw) in enumerate(mix):
+            got = b.outs[i][:sizes[i]].cpu().numpy().tobytes()
+            want, _, _, recon = oracle.compress(x, eb, mode, ocfgs[i], want_recon=True)
+            assert got == want, i
+            streams.append((got, recon))
+        b.close()
+        bufs = [torch.from_numpy(np.frombuffer(s_, np.uint8).copy()).cuda()
+                for s_, _ in streams]
+        d = hpez.Batch(gpu, streams=[(bufs[i], len(streams[i][0]), streams[i][0][:512])
+                                     for i in range(len(streams))])
+        d.run(graph=True)
+        _, st = d.results()
+        assert st == [0] * len(streams)
+        for i in range(len(streams)):
+            assert d.outs[i].cpu().numpy().tobytes() == streams[i][1].tobytes(), i
+        d.close()
+    finally:
+        hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_WARP_LEVELS, 1)
+        hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_BATCH_CTAS, 0)
+
+
+def test_batch_levels_share_launches(gpu):
+    """Fields with different numbers of levels run each level in the same
+    launches: the ticks are the distinct op keys, fewer than the ops of the
+    longest request plus the extra levels of the others."""
+    import torch
+    from paper_2311_12133_gb300 import fields, hpez
+    shapes = [(40, 48, 64), (100, 90, 80), (20, 24, 28), (130, 150)]
+    xs = [torch.from_numpy(fields.make("grf", sh, i)).cuda() for i, sh in enumerate(shapes)]
+    b = hpez.Batch(gpu, fields=[(x, 1e-3, 1, None) for x in xs])
+    b.run()
+    sizes, st = b.results()
+    assert st == [0] * len(xs)
+    launches, ticks = b.launch_count()
+    # 4 ops before the sweep, one op per level (5 levels at the 3D anchor
+    # stride 32, 6 at the 2D stride 64: the level ticks are the 2D field's),
+    # 11 ops after the sweep
+    assert ticks == 4 + 6 + 11
+    for i, x in enumerate(xs):
+        buf, size = gpu.compress(x, 1e-3)
+        assert b.outs[i][:sizes[i]].cpu().numpy().tobytes() == buf[:size].cpu().numpy().tobytes()
+    b.close()
+
+
 def test_batch_errors(gpu):
     import torch
     from paper_2311_12133_gb300 import hpez

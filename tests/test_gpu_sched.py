@@ -1,0 +1,135 @@
+"""Level schedules of the batched form: the offline search, and batches run
+under searched and forced schedule tables.  A schedule changes how the GPU
+runs a level, never what it computes, so every stream and field must equal
+the oracle's under any table."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_12133_gb300 import build as B
+    B.build()
+    from paper_2311_12133_gb300 import hpez
+    ctx = hpez.Context(0)
+    yield ctx
+    hpez.hpez_use_tuning(ctx.handle, None)
+    ctx.close()
+
+
+def _mix():
+    from paper_2311_12133_gb300 import fields
+    return [
+        (fields.make("grf", (40, 48, 64), 1), 1e-3, None),
+        (fields.make("bumps", (36, 40, 44), 2), 1e-3, dict(paradigm=1, interp=0)),
+        (fields.make("lognormal", (30, 34, 50), 3), 1e-2, dict(paradigm=1, interp=1)),
+        (fields.make("climate2d", (90, 130), 4), 1e-3, None),
+        (fields.make("grf", (33, 20, 47), 5), 1e-4, dict(interp=2)),
+    ]
+
+
+@pytest.fixture(scope="module")
+def expected(oracle):
+    from oracle import oracle as O
+    out = []
+    for x, eb, kw in _mix():
+        ocfg = O.make_config(x.ndim, **kw) if kw else None
+        s, _, _, recon = oracle.compress(x, eb, 1, ocfg, want_recon=True)
+        out.append((s, recon))
+    return out
+
+
+def _levels(hpez, shape, cfg):
+    """The level count of a field (key_of refuses a level beyond it)."""
+    L = 0
+    while True:
+        try:
+            hpez.hpez_level_key_of(shape, cfg, L + 1, False)
+        except hpez.HpezError:
+            return L
+        L += 1
+
+
+def _table_for(hpez, fam, tile=(0, 0, 0), chunks=0):
+    """A table mapping every level of every field of the mix (both
+    directions) to one schedule."""
+    t = hpez.Tuning()
+    for x, eb, kw in _mix():
+        cfg = hpez.make_config(x.ndim, **kw) if kw else None
+        for l in range(1, _levels(hpez, x.shape, cfg) + 1):
+            for d in (False, True):
+                t.set(hpez.hpez_level_key_of(x.shape, cfg, l, d), fam, tile, chunks)
+    return t
+
+
+def _run_and_check(gpu, expected):
+    import torch
+    from paper_2311_12133_gb300 import hpez
+    mix = _mix()
+    xs = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x, _, _ in mix]
+    cfgs = [hpez.make_config(x.ndim, **kw) if kw else None for x, _, kw in mix]
+    b = hpez.Batch(gpu, fields=[(xs[i], mix[i][1], 1, cfgs[i]) for i in range(len(mix))])
+    b.run(graph=True)
+    sizes, st = b.results()
+    assert st == [0] * len(mix)
+    for i in range(len(mix)):
+        assert b.outs[i][:sizes[i]].cpu().numpy().tobytes() == expected[i][0], i
+    b.close()
+    bufs = [torch.from_numpy(np.frombuffer(s, np.uint8).copy()).cuda() for s, _ in expected]
+    d = hpez.Batch(gpu, streams=[(bufs[i], len(expected[i][0]), expected[i][0][:512])
+                                 for i in range(len(mix))])
+    d.run()
+    _, st = d.results()
+    assert st == [0] * len(mix)
+    for i in range(len(mix)):
+        assert d.outs[i].cpu().numpy().tobytes() == expected[i][1].tobytes(), i
+    d.close()
+
+
+@pytest.mark.parametrize("sched", [
+    ("LEVEL3D", (0, 2, 0), 0), ("LEVEL3D", (0, 32, 0), 0),
+    ("MD3W", (0, 0, 0), 1), ("MD3W", (0, 0, 0), 3),
+    ("MD3", (0, 2, 0), 0), ("MD3", (0, 32, 0), 0),
+    ("FUSED", (4, 8, 64), 0), ("FUSED", (1, 2, 512), 0), ("FUSED", (1, 32, 64), 0),
+    ("PASS", (0, 0, 0), 0)])
+def test_forced_schedules_equal_oracle(gpu, expected, sched):
+    """Every level of every field forced to one schedule (levels that cannot
+    run it keep the fixed rules)."""
+    from paper_2311_12133_gb300 import hpez
+    fam, tile, chunks = sched
+    t = _table_for(hpez, getattr(hpez, "HPEZ_FAM_" + fam), tile, chunks)
+    hpez.hpez_use_tuning(gpu.handle, t)
+    try:
+        _run_and_check(gpu, expected)
+    finally:
+        hpez.hpez_use_tuning(gpu.handle, None)
+
+
+def test_search_then_tuned_batch(gpu, expected, tmp_path):
+    """The search fills an entry for every level and direction of each
+    searched class; a batch under the saved and reloaded table equals the
+    oracle."""
+    import torch
+    from paper_2311_12133_gb300 import hpez
+    t = hpez.Tuning()
+    for x, eb, kw in _mix():
+        cfg = hpez.make_config(x.ndim, **kw) if kw else None
+        xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        t.search(gpu, xd, eb, 1, cfg, copies=2, reps=1)
+        for l in range(1, _levels(hpez, x.shape, cfg) + 1):
+            for d in (False, True):
+                v = t.get(hpez.hpez_level_key_of(x.shape, cfg, l, d))
+                assert v is not None and v.time_us > 0
+                assert 1 <= v.family <= 5
+    path = str(tmp_path / "levels.txt")
+    t.save(path)
+    hpez.hpez_use_tuning(gpu.handle, hpez.Tuning(path))
+    try:
+        _run_and_check(gpu, expected)
+    finally:
+        hpez.hpez_use_tuning(gpu.handle, None)
