@@ -216,8 +216,10 @@ typedef struct hpez_batch hpez_batch;
 /* Plan n fields (streams) into one batch.  The device pointers are bound
  * to the batch: every run reads and writes the same buffers.  Errors:
  * INVALID_ARG / CORRUPT_STREAM / OUT_TOO_SMALL for the first bad entry,
- * UNSUPPORTED (a Lorenzo-predictor config or stream), NO_MEMORY, CUDA.
- * Synchronizes the device once (the uploads). */
+ * UNSUPPORTED (a global natural-spline level, or a Lorenzo-predictor
+ * geometry the Lorenzo kernel does not take), NO_MEMORY, CUDA.  A
+ * Lorenzo-predictor field (Sec. 6.5) runs its pass in the finest level's
+ * tick.  Synchronizes the device once (the uploads). */
 HPEZ_API int hpez_batch_create_compress(hpez_ctx* ctx, int n,
                                         const hpez_field_desc* fields,
                                         hpez_batch** out);
@@ -351,7 +353,7 @@ HPEZ_API int hpez_server_create(hpez_ctx* ctx, uint64_t budget_bytes,
                                 hpez_server** out);
 /* Queue a request; *id identifies it in hpez_server_poll.  Errors:
  * INVALID_ARG / CORRUPT_STREAM (checked now), TOO_LARGE (it can never fit
- * the budget), UNSUPPORTED (a Lorenzo-predictor config or stream). */
+ * the budget), UNSUPPORTED (as hpez_batch_create_compress). */
 HPEZ_API int hpez_server_submit(hpez_server* s, const hpez_request* req,
                                 uint64_t* id);
 /* One step: retire, admit, one tick.  Never waits for the GPU except to

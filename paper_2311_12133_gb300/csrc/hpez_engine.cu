@@ -50,7 +50,8 @@ enum OpType : int {
   OP_MD3O_D = OP_MD3O_C + 3,
   OP_MD3W_C = OP_MD3O_D + 3,  // finest level as warp strips
   OP_MD3W_D = OP_MD3W_C + 3,
-  OP_COUNT = OP_MD3W_D + 3
+  OP_LOR = OP_MD3W_D + 3,     // + variant: the Lorenzo pass (Sec. 6.5)
+  OP_COUNT = OP_LOR + kLorVariants
 };
 
 // The batched form runs ops of equal key in one tick: the ops before the
@@ -279,8 +280,16 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   if (rc) return rc;
   if ((rc = check_config(p, cfg))) return rc;
   if (cfg.blockwise && !cfg.h_blockmap) return HPEZ_ERR_INVALID_ARG;
-  if (cfg.predictor) return HPEZ_ERR_UNSUPPORTED;  // Lorenzo: hpez_compress
-  for (int l = 0; l < p.L; ++l)  // global spline: hpez_compress
+  const bool lor = cfg.predictor != 0;
+  LorenzoJob lj;
+  int lor_var = 0;
+  uint32_t lor_ctas = 0;
+  size_t lor_smem = 0;
+  if (lor && !lorenzo_batch_job(false, cfg.predictor, p.n, p.fst, p.off, p.A,
+                                (reinterpret_cast<uintptr_t>(d_in) & 15u) == 0, ctx->num_sms,
+                                ctx->lorenzo_ctas, &lj.G, &lor_var, &lor_ctas, &lor_smem))
+    return HPEZ_ERR_UNSUPPORTED;
+  for (int l = 0; l < p.L && !lor; ++l)  // global spline: hpez_compress
     if (cfg.interp[l] == HPEZ_SPLINE_GLOBAL) return HPEZ_ERR_UNSUPPORTED;
   plan_chunks_blocks(p, cfg);
   r.decomp = 0;
@@ -291,8 +300,9 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   ctx->x_aligned16 = (reinterpret_cast<uintptr_t>(d_in) & 15u) == 0;
   // the finest level's fused kernels write no reconstruction in compress:
   // its grid is then not allocated
-  const LevelPick pick1 = pick_level(ctx, p, sc, 1, false, d_in, nullptr);
-  const bool need_r0 = pick1.fam == FAM_MD3 || pick1.fam == FAM_PASS;
+  // the Lorenzo pass needs the finest code array only
+  const LevelPick pick1 = lor ? LevelPick() : pick_level(ctx, p, sc, 1, false, d_in, nullptr);
+  const bool need_r0 = !lor && (pick1.fam == FAM_MD3 || pick1.fam == FAM_PASS);
 
   Arena ar;
   const size_t o_ctl = ar.take<Ctl>(1);
@@ -306,10 +316,10 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   const size_t o_gpar = ar.take<uint32_t>(131072);
   size_t o_R[kMaxLevels + 1], o_C[kMaxLevels + 1];
   for (int g = 0; g <= p.L; ++g) {
-    o_R[g] = (g > 0 || need_r0) ? ar.take<float>(p.gsize[g]) : 0;
+    o_R[g] = ((g > 0 && !lor) || need_r0) ? ar.take<float>(p.gsize[g]) : 0;
     // two spare codes: kernels may read a code as the aligned 4-byte word
     // that holds it
-    o_C[g] = ar.take<uint16_t>(p.gsize[g] + 2);
+    o_C[g] = (g == 0 || !lor) ? ar.take<uint16_t>(p.gsize[g] + 2) : 0;
   }
   const size_t o_zc = ar.take<uint32_t>(p.nch);
   const size_t o_zoff = ar.take<unsigned long long>(p.nch);
@@ -334,8 +344,8 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   float* R[kMaxLevels + 1];
   uint16_t* Cg[kMaxLevels + 1];
   for (int g = 0; g <= p.L; ++g) {
-    R[g] = (g > 0 || need_r0) ? reinterpret_cast<float*>(base + o_R[g]) : nullptr;
-    Cg[g] = reinterpret_cast<uint16_t*>(base + o_C[g]);
+    R[g] = ((g > 0 && !lor) || need_r0) ? reinterpret_cast<float*>(base + o_R[g]) : nullptr;
+    Cg[g] = (g == 0 || !lor) ? reinterpret_cast<uint16_t*>(base + o_C[g]) : nullptr;
   }
   uint32_t* zc = reinterpret_cast<uint32_t*>(base + o_zc);
   unsigned long long* zoff = reinterpret_cast<unsigned long long*>(base + o_zoff);
@@ -346,7 +356,7 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   uint8_t* hdr_d = reinterpret_cast<uint8_t*>(base + o_hdr);
   uint8_t* hdrc_d = reinterpret_cast<uint8_t*>(base + o_hdrc);
 
-  const uint64_t na = n_anchors(p);
+  const uint64_t na = lor ? 0 : n_anchors(p);
   const uint64_t off_anchors = kHeaderBytes;
   const uint64_t off_bmap = a16(off_anchors + 4 * na);
   const uint64_t off_chw = a16(off_bmap + p.nblocks);
@@ -388,8 +398,19 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   pj.beta = cfg.beta;
   pj.x = d_in;
   pre(make_op(OP_PARAMS, pj));
-  pre(make_op(OP_ANCHOR, AnchorJob{d_in, p.grid[p.L], p.gsize[p.L], R[p.L], Cg[p.L], ctl},
-              grid_blocks(p.gsize[p.L], 65535)));
+  if (lor) {
+    // the Lorenzo pass in the place of the sweep (at level 1's tick)
+    lj.x = d_in;
+    lj.codes = Cg[0];
+    lj.out = nullptr;
+    lj.ctl = ctl;
+    Op o = make_op(OP_LOR + lor_var, lj, lor_ctas, (uint32_t)lor_smem);
+    o.key = level_key(1, 0);
+    ops.push_back(std::move(o));
+  } else {
+    pre(make_op(OP_ANCHOR, AnchorJob{d_in, p.grid[p.L], p.gsize[p.L], R[p.L], Cg[p.L], ctl},
+                grid_blocks(p.gsize[p.L], 65535)));
+  }
   SweepBufs sb;
   std::memset(&sb, 0, sizeof(sb));
   sb.x = d_in;
@@ -397,7 +418,7 @@ int plan_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   sb.bs = (uint32_t)(cfg.block_size > 0 ? cfg.block_size : 1);
   for (int s3 = 0; s3 < 3; ++s3) sb.nb[s3] = p.nb[s3];
   sb.ctl = ctl;
-  for (int l = p.L; l >= 1; --l) {
+  for (int l = lor ? 0 : p.L; l >= 1; --l) {
     const int g = l - 1;
     sb.R = R[g];
     sb.C = Cg[g];
@@ -449,8 +470,16 @@ int plan_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   int rc = parse_stream_header(static_cast<const uint8_t*>(h_header), in_size, si);
   if (rc) return rc;
   if (si.N > out_cap_elems) return HPEZ_ERR_OUT_TOO_SMALL;
-  if (!si.is_const && si.cfg.predictor) return HPEZ_ERR_UNSUPPORTED;
-  if (!si.is_const)
+  const bool lor = !si.is_const && si.cfg.predictor != 0;
+  LorenzoJob lj;
+  int lor_var = 0;
+  uint32_t lor_ctas = 0;
+  size_t lor_smem = 0;
+  if (lor && !lorenzo_batch_job(true, si.cfg.predictor, si.p.n, si.p.fst, si.p.off, si.p.A,
+                                (reinterpret_cast<uintptr_t>(d_out) & 15u) == 0, ctx->num_sms,
+                                ctx->lorenzo_ctas, &lj.G, &lor_var, &lor_ctas, &lor_smem))
+    return HPEZ_ERR_UNSUPPORTED;
+  if (!si.is_const && !lor)
     for (int l = 0; l < si.p.L; ++l)
       if (si.cfg.interp[l] == HPEZ_SPLINE_GLOBAL) return HPEZ_ERR_UNSUPPORTED;
   r.decomp = 1;
@@ -484,7 +513,7 @@ int plan_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   const size_t o_sorted = ar.take<uint16_t>(65536);
   const size_t o_gkeys = ar.take<unsigned long long>(65536);
   size_t o_R[kMaxLevels + 1];
-  for (int g = 1; g < p.L; ++g) o_R[g] = ar.take<float>(p.gsize[g]);
+  for (int g = 1; g < p.L; ++g) o_R[g] = lor ? 0 : ar.take<float>(p.gsize[g]);
   const size_t o_codes = ar.take<uint16_t>(si.N + 2);  // 2 spare: 4-byte code reads
   const size_t o_zc = ar.take<uint32_t>(p.nch);
   const size_t o_zoff = ar.take<unsigned long long>(p.nch);
@@ -508,7 +537,7 @@ int plan_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   uint32_t* dchw = reinterpret_cast<uint32_t*>(base + o_dchw);
   unsigned long long* tot = reinterpret_cast<unsigned long long*>(base + o_tot);
   float* R[kMaxLevels + 1];
-  for (int g = 1; g < p.L; ++g) R[g] = reinterpret_cast<float*>(base + o_R[g]);
+  for (int g = 1; g < p.L; ++g) R[g] = lor ? nullptr : reinterpret_cast<float*>(base + o_R[g]);
   R[0] = d_out;
   R[p.L] = const_cast<float*>(reinterpret_cast<const float*>(in + si.oa));
 
@@ -575,7 +604,18 @@ int plan_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   sb.ctl = ctl;
   ctx->out_aligned16 = (reinterpret_cast<uintptr_t>(d_out) & 15u) == 0;
   ctx->codes_aligned16 = true;
-  for (int l = p.L; l >= 1; --l) {
+  if (lor) {
+    // the Lorenzo recurrence over the decoded codes; the escaped values
+    // are already in place
+    lj.x = nullptr;
+    lj.codes = codes;
+    lj.out = d_out;
+    lj.ctl = ctl;
+    Op o = make_op(OP_LOR + lor_var, lj, lor_ctas, (uint32_t)lor_smem);
+    o.key = level_key(1, 0);
+    ops.push_back(std::move(o));
+  }
+  for (int l = lor ? 0 : p.L; l >= 1; --l) {
     const int g = l - 1;
     sb.R = R[g];
     sb.kind = cfg.interp[l - 1];
@@ -670,9 +710,13 @@ void launch_entry(const Entry& e, const unsigned char* d_tab, int sms, int max_c
                      e.smem, sms, max_ctas, s);
     return;
   }
-  if (t >= OP_MD3W_C && t < OP_COUNT) {
+  if (t >= OP_MD3W_C && t < OP_LOR) {
     const int u = t - OP_MD3W_C;
     launch_md3w_batch(u >= 3, u % 3, (const MD3WJob*)J, off, e.nj, e.nblk, sms, max_ctas, s);
+    return;
+  }
+  if (t >= OP_LOR && t < OP_COUNT) {
+    launch_lorenzo_batch(t - OP_LOR, (const LorenzoJob*)J, off, e.nj, e.nblk, e.smem, s);
     return;
   }
   switch (t) {

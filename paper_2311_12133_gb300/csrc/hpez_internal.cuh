@@ -456,6 +456,21 @@ struct MD3Job {
   const float* outl_full; const float* Rc; const uint16_t* Cc; float* Rs;
   uint16_t* Cs; const Ctl* ctl;
 };
+// the Lorenzo pass (Sec. 6.5) over one field of blocks of side A
+struct LorGeom {
+  uint32_t n[3];     // field extents per slot (padded slots 1)
+  uint32_t st[3];    // field strides
+  uint32_t B[3];     // block side per slot (1 on padded slots)
+  uint32_t nb[3];    // blocks per slot
+  uint32_t nblocks;  // nb[0] nb[1] nb[2]
+  uint32_t g[3];     // the grid size in the radix of nb
+  uint32_t W;        // ring row width in floats (B[1] + 2 padded for banks)
+  uint32_t slot;     // floats per ring slot: (B[0] + 2) W
+  int logP;          // log2 B[2]
+};
+struct LorenzoJob {
+  LorGeom G; const float* x; uint16_t* codes; float* out; const Ctl* ctl;
+};
 // the finest 3D multi-dimensional level as warp strips: n1 x n2 strips per
 // chunk of K even planes
 struct MD3WJob {

@@ -91,6 +91,15 @@ int launch_lorenzo(bool decomp, int order, const uint32_t n[3], const uint32_t f
                    const Ctl* ctl, int num_sms, int drop_copy, int max_ctas,
                    cudaStream_t s);
 
+// batched Lorenzo pass: the job's geometry (G.g for its CTA count), op
+// variant, CTA count and shared memory; false for geometries the kernel does
+// not take
+constexpr int kLorVariants = 2 * 2 * 3 * 2 * 2 * 6;
+bool lorenzo_batch_job(bool decomp, int order, const uint32_t n[3], const uint32_t fst[3],
+                       int off, int A, bool vec, int num_sms, int max_ctas, LorGeom* G,
+                       int* variant, uint32_t* ctas, size_t* smem);
+void launch_lorenzo_batch(int variant, const LorenzoJob* J, const uint32_t* off, int nj,
+                          uint32_t nblk, size_t smem, cudaStream_t s);
 // k_huffman.cu
 void launch_hist(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,
                  uint32_t* hist, uint32_t* zc, const Ctl* ctl, int num_sms,

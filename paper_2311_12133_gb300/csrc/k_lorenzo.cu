@@ -44,17 +44,6 @@ namespace {
 
 constexpr int kSeg = 8;  // input / output segment along i2
 
-struct LorGeom {
-  uint32_t n[3];     // field extents per slot (padded slots 1)
-  uint32_t st[3];    // field strides
-  uint32_t B[3];     // block side per slot (1 on padded slots)
-  uint32_t nb[3];    // blocks per slot
-  uint32_t nblocks;  // nb[0] nb[1] nb[2]
-  uint32_t g[3];     // the grid size in the radix of nb
-  uint32_t W;        // ring row width in floats (B[1] + 2 padded for banks)
-  uint32_t slot;     // floats per ring slot: (B[0] + 2) W
-  int logP;          // log2 B[2]
-};
 
 template <int ORDER>
 __host__ __device__ constexpr int lor_ring() { return ORDER == 1 ? 4 : 8; }
@@ -91,8 +80,8 @@ struct Walk {
   uint32_t b0, b1, b2;
 };
 
-__device__ __forceinline__ Walk walk_start(const LorGeom& G) {
-  uint32_t b = blockIdx.x;
+__device__ __forceinline__ Walk walk_start(const LorGeom& G, uint32_t bid) {
+  uint32_t b = bid;
   Walk w;
   w.b2 = b % G.nb[2];
   b /= G.nb[2];
@@ -312,10 +301,13 @@ __device__ __forceinline__ void lor_zero(float (&h)[L0 + 1][L1 + 1][ORDER]) {
       for (int c = 0; c < ORDER; ++c) h[a][b][c] = 0.0f;
 }
 
+// A CTA of the Lorenzo pass: block index bid of a grid of `grid` CTAs over
+// the field of G (G.g: that grid size in the radix of G.nb).
 template <bool kDecomp, int ORDER, int NDR, bool kVec, bool kSkew>
-__global__ void __launch_bounds__(1024, 1)
-    k_lorenzo(LorGeom G, const float* __restrict__ x, uint16_t* __restrict__ codes,
-              float* __restrict__ out, const Ctl* __restrict__ ctl) {
+__device__ __forceinline__ void lor_body(const LorGeom& G, const float* __restrict__ x,
+                                         uint16_t* __restrict__ codes, float* __restrict__ out,
+                                         const Ctl* __restrict__ ctl, uint32_t bid,
+                                         uint32_t grid) {
   if (ctl->status || ctl->is_const) return;
   constexpr int RING = lor_ring<ORDER>();
   constexpr int L0 = NDR >= 3 ? ORDER : 0;  // stencil reach along slot 0
@@ -336,7 +328,7 @@ __global__ void __launch_bounds__(1024, 1)
   }
   const int P = (int)G.B[2];
   const int sl = kVec ? kSeg : min(kSeg, P);
-  const uint32_t J = (G.nblocks - 1u - blockIdx.x) / gridDim.x + 1u;
+  const uint32_t J = (G.nblocks - 1u - bid) / grid + 1u;
   const int span = P * (int)J;  // steps a column is busy
   const int T = span + (int)G.B[0] + B1 - 2;
   const int W = (int)G.W;
@@ -358,7 +350,7 @@ __global__ void __launch_bounds__(1024, 1)
   // ahead (cA), of the next segment (cB, whose escaped values are being
   // prefetched into L1) and of the current one (cc); ov collects the
   // reconstructions of the segment for one vector store.
-  Walk wk = walk_start(G);
+  Walk wk = walk_start(G, bid);
   ColGeo cg = col_geo(G, wk, i0, i1);
   ColGeo gB = cg, gA = cg;
   float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
@@ -497,7 +489,24 @@ __global__ void __launch_bounds__(1024, 1)
   }
 }
 
+template <bool kDecomp, int ORDER, int NDR, bool kVec, bool kSkew>
+__global__ void __launch_bounds__(1024, 1)
+    k_lorenzo(LorGeom G, const float* __restrict__ x, uint16_t* __restrict__ codes,
+              float* __restrict__ out, const Ctl* __restrict__ ctl) {
+  lor_body<kDecomp, ORDER, NDR, kVec, kSkew>(G, x, codes, out, ctl, blockIdx.x, gridDim.x);
+}
 
+// batched: job j owns the persistent CTAs [off[j], off[j+1]) of the launch
+// (its G.g is that CTA count in the radix of its blocks)
+template <bool kDecomp, int ORDER, int NDR, bool kVec, bool kSkew>
+__global__ void __launch_bounds__(1024, 1)
+    k_lorenzo_batch(const LorenzoJob* __restrict__ J, const uint32_t* __restrict__ off, int nj) {
+  const int j = batch_job(off, nj);
+  const LorenzoJob& q = J[j];
+  const uint32_t o = __ldg(off + j);
+  lor_body<kDecomp, ORDER, NDR, kVec, kSkew>(q.G, q.x, q.codes, q.out, q.ctl, blockIdx.x - o,
+                                             __ldg(off + j + 1) - o);
+}
 
 // The 3D, A = 32 form fed by TMA.  Warp w owns the columns (w, 0..31) of
 // its CTA's blocks (lane l: i1 = l, so s = w + l) and reads its input from
@@ -560,7 +569,7 @@ __global__ void __launch_bounds__(1024, 1)
   const float inv2 = s_inv2;
 
   // the warp's box walk (block of the next segment to fetch)
-  Walk wb = walk_start(G);
+  Walk wb = walk_start(G, blockIdx.x);
   const uint32_t lane_off = (uint32_t)i0 * G.st[0] + (uint32_t)i1 * G.st[1];
   ColGeo cg;
   cg.col = 0u;
@@ -888,6 +897,127 @@ int launch_lorenzo(bool decomp, int order, const uint32_t n[3], const uint32_t f
                       : launch_lor_nd<true, 2>(ndr, vec, G, smem, threads, num_sms, max_ctas, x, codes, out, ctl, drop_copy, s);
   return order == 1 ? launch_lor_nd<false, 1>(ndr, vec, G, smem, threads, num_sms, max_ctas, x, codes, out, ctl, drop_copy, s)
                     : launch_lor_nd<false, 2>(ndr, vec, G, smem, threads, num_sms, max_ctas, x, codes, out, ctl, drop_copy, s);
+}
+
+// ---------------------------------------------------------------------
+// batched form: the register-fed kernel with one job table per launch.  A
+// launch's jobs share the template (direction, order, real dimensions, row
+// vectors, skewed lane map) and the CTA size, which the op variant encodes:
+// variant = ((((decomp 2 + order - 1) 3 + ndr - 1) 2 + vec) 2 + skew) 6 +
+// log2(threads / 32).
+// ---------------------------------------------------------------------
+namespace {
+
+template <class F>
+struct LorDispatch {
+  template <bool D, int O>
+  static void by_shape(int ndr, bool vec, bool skew, F& f) {
+    if (ndr == 3 && skew) {
+      if (vec) f.template run<D, O, 3, true, true>(); else f.template run<D, O, 3, false, true>();
+    } else if (ndr == 3) {
+      if (vec) f.template run<D, O, 3, true, false>(); else f.template run<D, O, 3, false, false>();
+    } else if (ndr == 2) {
+      if (vec) f.template run<D, O, 2, true, false>(); else f.template run<D, O, 2, false, false>();
+    } else {
+      if (vec) f.template run<D, O, 1, true, false>(); else f.template run<D, O, 1, false, false>();
+    }
+  }
+  static void go(bool decomp, int order, int ndr, bool vec, bool skew, F& f) {
+    if (decomp) {
+      if (order == 1) by_shape<true, 1>(ndr, vec, skew, f); else by_shape<true, 2>(ndr, vec, skew, f);
+    } else {
+      if (order == 1) by_shape<false, 1>(ndr, vec, skew, f); else by_shape<false, 2>(ndr, vec, skew, f);
+    }
+  }
+};
+
+struct LorOcc {
+  unsigned threads;
+  size_t smem;
+  int per_sm = 0;
+  template <bool D, int O, int N, bool V, bool S>
+  void run() {
+    auto k = k_lorenzo_batch<D, O, N, V, S>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, (int)threads, smem) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 0;
+    }
+  }
+};
+
+struct LorLaunch {
+  const LorenzoJob* J;
+  const uint32_t* off;
+  int nj;
+  uint32_t nblk;
+  unsigned threads;
+  size_t smem;
+  cudaStream_t s;
+  template <bool D, int O, int N, bool V, bool S>
+  void run() {
+    auto k = k_lorenzo_batch<D, O, N, V, S>;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr = true;
+    }
+    k<<<nblk, threads, smem, s>>>(J, off, nj);
+  }
+};
+
+}  // namespace
+
+bool lorenzo_batch_job(bool decomp, int order, const uint32_t n[3], const uint32_t fst[3],
+                       int off, int A, bool vec, int num_sms, int max_ctas, LorGeom* Gout,
+                       int* variant, uint32_t* ctas, size_t* smem_out) {
+  LorGeom G;
+  size_t smem;
+  unsigned threads;
+  if (order < 1 || order > 2 || !lor_geom(n, fst, off, A, order, G, smem, threads)) return false;
+  vec = vec && (n[2] % kSeg) == 0 && A >= kSeg;
+  const int ndr = 3 - off;
+  const bool skew = ndr == 3 && G.B[0] == 32 && G.B[1] == 32;
+  LorOcc occ;
+  occ.threads = threads;
+  occ.smem = smem;
+  LorDispatch<LorOcc>::go(decomp, order, ndr, vec, skew, occ);
+  if (occ.per_sm < 1) return false;
+  uint64_t cap = (uint64_t)occ.per_sm * (uint64_t)(num_sms > 0 ? num_sms : 1);
+  if (max_ctas > 0 && cap > (uint64_t)max_ctas) cap = (uint64_t)max_ctas;
+  uint64_t grid = G.nblocks < cap ? G.nblocks : cap;
+  const uint64_t J = (G.nblocks + grid - 1) / grid;
+  grid = (G.nblocks + J - 1) / J;
+  G.g[2] = (uint32_t)(grid % G.nb[2]);
+  G.g[1] = (uint32_t)(grid / G.nb[2] % G.nb[1]);
+  G.g[0] = (uint32_t)(grid / G.nb[2] / G.nb[1]);
+  int tcls = 0;
+  while ((32u << tcls) < threads) ++tcls;
+  *Gout = G;
+  *variant = (((((decomp ? 1 : 0) * 2 + order - 1) * 3 + ndr - 1) * 2 + (vec ? 1 : 0)) * 2 +
+              (skew ? 1 : 0)) * 6 + tcls;
+  *ctas = (uint32_t)grid;
+  *smem_out = smem;
+  return true;
+}
+
+void launch_lorenzo_batch(int variant, const LorenzoJob* J, const uint32_t* off, int nj,
+                          uint32_t nblk, size_t smem, cudaStream_t s) {
+  if (!nblk || variant < 0 || variant >= kLorVariants) return;
+  int v = variant;
+  const int tcls = v % 6;
+  v /= 6;
+  const bool skew = v % 2;
+  v /= 2;
+  const bool vec = v % 2;
+  v /= 2;
+  const int ndr = v % 3 + 1;
+  v /= 3;
+  const int order = v % 2 + 1;
+  const bool decomp = v / 2;
+  LorLaunch L{J, off, nj, nblk, 32u << tcls, smem, s};
+  LorDispatch<LorLaunch>::go(decomp, order, ndr, vec, skew, L);
 }
 
 }  // namespace hpez

@@ -167,6 +167,52 @@ def test_batch_md_levels_and_persistent_walk(gpu, oracle, warp_levels, batch_cta
         hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_BATCH_CTAS, 0)
 
 
+@pytest.mark.parametrize("lorenzo_ctas", [0, 4])
+def test_batch_lorenzo_fields_equal_oracle(gpu, oracle, lorenzo_ctas):
+    """Lorenzo-predictor fields (Sec. 6.5) of order 1 and 2, 1D to 3D, in a
+    batch with interpolation fields: streams and fields equal the oracle's
+    (with few CTAs, each streams many blocks)."""
+    import torch
+    from paper_2311_12133_gb300 import fields, hpez
+    mix = [
+        (fields.make("grf", (64, 64, 64), 21), 1e-3, dict(predictor=1)),
+        (fields.make("bumps", (40, 50, 36), 22), 1e-3, dict(predictor=2)),
+        (fields.make("climate2d", (130, 200), 23), 1e-3, dict(predictor=1)),
+        (fields.make("grf", (70, 90, 100), 24), 1e-4, dict(predictor=2)),
+        (np.cumsum(np.random.default_rng(5).normal(0, 1, 5000)).astype(np.float32), 1e-3,
+         dict(predictor=1)),
+        (fields.make("grf", (40, 48, 64), 25), 1e-3, None),
+    ]
+    hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_LORENZO_CTAS, lorenzo_ctas)
+    try:
+        xs, args, want = [], [], []
+        for x, eb, kw in mix:
+            xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+            xs.append(xd)
+            args.append((xd, eb, 1, hpez.make_config(x.ndim, **kw) if kw else None))
+            ocfg = oracle.make_config(x.ndim, **kw) if kw else None
+            st, _, _, recon = oracle.compress(x, eb, 1, ocfg, want_recon=True)
+            want.append((st, recon))
+        b = hpez.Batch(gpu, fields=args)
+        b.run(graph=True)
+        sizes, status = b.results()
+        assert status == [0] * len(mix)
+        for i in range(len(mix)):
+            assert b.outs[i][:sizes[i]].cpu().numpy().tobytes() == want[i][0], i
+        b.close()
+        bufs = [torch.from_numpy(np.frombuffer(w, np.uint8).copy()).cuda() for w, _ in want]
+        d = hpez.Batch(gpu, streams=[(bufs[i], len(want[i][0]), want[i][0][:512])
+                                     for i in range(len(mix))])
+        d.run()
+        _, st = d.results()
+        assert st == [0] * len(mix)
+        for i in range(len(mix)):
+            assert d.outs[i].cpu().numpy().tobytes() == want[i][1].tobytes(), i
+        d.close()
+    finally:
+        hpez.hpez_set_option(gpu.handle, hpez.HPEZ_OPT_LORENZO_CTAS, 0)
+
+
 def test_batch_levels_share_launches(gpu):
     """Fields with different numbers of levels run each level in the same
     launches: the ticks are the distinct op keys, fewer than the ops of the

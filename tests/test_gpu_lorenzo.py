@@ -100,8 +100,9 @@ def test_lorenzo_frozen_and_constant(gpu, oracle):
 
 
 def test_lorenzo_unsupported_forms(gpu):
-    """Blocks whose columns do not fit a CTA, a block-wise map with the
-    Lorenzo predictor, and the engine's request paths are refused."""
+    """Blocks whose columns do not fit a CTA and a block-wise map with the
+    Lorenzo predictor are refused; the batched and served forms take the
+    Lorenzo predictor with the same results as the single call."""
     import torch
     from paper_2311_12133_gb300 import hpez
     x = torch.rand((70, 70, 70), device="cuda")
@@ -118,21 +119,31 @@ def test_lorenzo_unsupported_forms(gpu):
         gpu.compress(x, 1e-3, 1, cfg)
     assert e.value.code == -1
     with pytest.raises(hpez.HpezError) as e:
-        hpez.Batch(gpu, fields=[(x, 1e-3, 1, hpez.make_config(3, predictor=1))])
+        hpez.Batch(gpu, fields=[(x, 1e-3, 1, hpez.make_config(3, predictor=1,
+                                                              anchor_stride=64))])
     assert e.value.code == -8
-    # a Lorenzo stream: the served form refuses it (so does the
-    # no-allocation decompressor, tested with it), hpez_decompress takes it
+    # a Lorenzo field through the served form: the stream and the field of
+    # the single call (the no-allocation decompressor refuses the stream,
+    # tested with it)
     small = torch.rand((40, 40, 40), device="cuda")
-    buf, size = gpu.compress(small, 1e-3, 1, hpez.make_config(3, predictor=1))
-    srv = hpez.Server(gpu, 1 << 28, 4)
-    with pytest.raises(hpez.HpezError) as e:
-        srv.submit_compress(small.cpu().numpy(), 1e-3, 1, hpez.make_config(3, predictor=2))
-    assert e.value.code == -8
-    with pytest.raises(hpez.HpezError) as e:
-        srv.submit_decompress(buf[:size].cpu().numpy(), size)
-    assert e.value.code == -8
-    srv.close()
+    cfg2 = hpez.make_config(3, predictor=2)
+    buf, size = gpu.compress(small, 1e-3, 1, cfg2)
+    want = buf[:size].cpu().numpy()
     y = gpu.decompress(buf, size)
+    srv = hpez.Server(gpu, 1 << 28, 4)
+    rc, hc = srv.submit_compress(small.cpu().numpy(), 1e-3, 1, cfg2)
+    rd, hd = srv.submit_decompress(want.copy(), size)
+    done = {}
+    for _ in range(10000):
+        srv.step()
+        for rid, st, sz, _ in srv.poll():
+            done[rid] = (st, sz)
+        if len(done) == 2:
+            break
+    srv.close()
+    assert done[rc] == (0, size) and done[rd][0] == 0
+    assert hc[:size].tobytes() == want.tobytes()
+    assert hd.tobytes() == y.cpu().numpy().tobytes()
     assert (y - small).abs().max().item() <= 1e-3 * (small.max() - small.min()).item()
 
 
