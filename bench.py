@@ -398,14 +398,18 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 def bench_batched(ctx, steps, warmup):
     """64 fields of uneven shapes (32^3 .. 256x384x384, 2D and 3D, per-field
-    relative eb), compress + decompress: one graph-captured batched run
-    against 64 sequential single-field calls on the same GPU."""
+    relative eb), compress + decompress: graph-captured batched runs (level
+    schedules from the fixed rules, then from the searched table shipped
+    with the package) against 64 sequential single-field calls on the same
+    GPU; then the same mix with the multi-dimensional linear configuration
+    the tuner picks for these fields."""
     import torch
-    from paper_2311_12133_gb300 import fields, hpez
+    from paper_2311_12133_gb300 import autotune, fields, hpez
     mix = fields.batch_mix(64, seed=0)
     xs = [(fields.make_torch(k, sh, sd), eb) for k, sh, sd, eb in mix]
     nbytes = sum(a.numel() * 4 for a, _ in xs)
     s = torch.cuda.Stream()
+    table = hpez.Tuning(autotune.SHIPPED) if os.path.exists(autotune.SHIPPED) else None
 
     def timed(fn):
         for _ in range(max(3, warmup)):
@@ -420,52 +424,76 @@ def bench_batched(ctx, steps, warmup):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / steps
 
-    with torch.cuda.stream(s):
-        outs = [torch.empty(hpez.hpez_compress_bound(a.shape), dtype=torch.uint8,
-                            device="cuda") for a, _ in xs]
-        ys = [torch.empty_like(a) for a, _ in xs]
-        sizes = [0] * len(xs)
+    def one_config(cfg_kw, tables):
+        cfgs = [hpez.make_config(a.dim(), **cfg_kw) if cfg_kw else None for a, _ in xs]
+        with torch.cuda.stream(s):
+            outs = [torch.empty(hpez.hpez_compress_bound(a.shape), dtype=torch.uint8,
+                                device="cuda") for a, _ in xs]
+            ys = [torch.empty_like(a) for a, _ in xs]
+            sizes = [0] * len(xs)
 
-        def plain():
-            for i, (a, eb) in enumerate(xs):
-                sizes[i] = ctx.compress(a, eb, hpez.HPEZ_EB_REL, None, out=outs[i],
-                                        stream=s)[1]
-            for i in range(len(xs)):
-                ctx.decompress(outs[i], sizes[i], out=ys[i], shape=tuple(xs[i][0].shape),
-                               stream=s)
+            def plain():
+                for i, (a, eb) in enumerate(xs):
+                    sizes[i] = ctx.compress(a, eb, hpez.HPEZ_EB_REL, cfgs[i], out=outs[i],
+                                            stream=s)[1]
+                for i in range(len(xs)):
+                    ctx.decompress(outs[i], sizes[i], out=ys[i], shape=tuple(xs[i][0].shape),
+                                   stream=s)
 
-        plain_ms = timed(plain)
-        bc = hpez.Batch(ctx, fields=[(a, eb, hpez.HPEZ_EB_REL, None) for a, eb in xs])
-        bc.run(stream=s)
-        bsz, bst = bc.results(stream=s)
-        assert bst == [0] * len(xs) and bsz == sizes, "batched compress differs"
-        hdrs = [bc.outs[i][:512].cpu().numpy().tobytes() for i in range(len(xs))]
-        bd = hpez.Batch(ctx, streams=[(bc.outs[i], bsz[i], hdrs[i]) for i in range(len(xs))])
+            plain_ms = timed(plain)
+            res = {"plain_value": round(nbytes / (plain_ms / 1e3) / 1e9, 3),
+                   "plain_ms_per_step": round(plain_ms, 3)}
+            for name, tab in tables:
+                hpez.hpez_use_tuning(ctx.handle, tab)
+                bc = hpez.Batch(ctx, fields=[(a, eb, hpez.HPEZ_EB_REL, cfgs[i])
+                                             for i, (a, eb) in enumerate(xs)])
+                bc.run(stream=s)
+                bsz, bst = bc.results(stream=s)
+                assert bst == [0] * len(xs) and bsz == sizes, "batched compress differs"
+                for i in range(len(xs)):
+                    assert torch.equal(bc.outs[i][:sizes[i]], outs[i][:sizes[i]]), \
+                        "batched stream differs"
+                hdrs = [bc.outs[i][:512].cpu().numpy().tobytes() for i in range(len(xs))]
+                bd = hpez.Batch(ctx, streams=[(bc.outs[i], bsz[i], hdrs[i])
+                                              for i in range(len(xs))])
 
-        def batched():
-            bc.run(stream=s, graph=True)
-            bd.run(stream=s, graph=True)
+                def batched():
+                    bc.run(stream=s, graph=True)
+                    bd.run(stream=s, graph=True)
 
-        batch_ms = timed(batched)
-        _, dst = bd.results(stream=s)
-        assert dst == [0] * len(xs)
-        for i in range(len(xs)):
-            assert torch.equal(bd.outs[i].view(-1), ys[i].view(-1)), "batched decompress differs"
-        la, ta = bc.launch_count()
-        lb, tb = bd.launch_count()
-        bc.close()
-        bd.close()
+                batch_ms = timed(batched)
+                _, dst = bd.results(stream=s)
+                assert dst == [0] * len(xs)
+                for i in range(len(xs)):
+                    assert torch.equal(bd.outs[i].view(-1), ys[i].view(-1)), \
+                        "batched decompress differs"
+                la, ta = bc.launch_count()
+                lb, tb = bd.launch_count()
+                bc.close()
+                bd.close()
+                res[name] = {"value": round(nbytes / (batch_ms / 1e3) / 1e9, 3),
+                             "ms_per_step": round(batch_ms, 3),
+                             "speedup_vs_plain": round(plain_ms / batch_ms, 3),
+                             "launches_per_step": la + lb, "ticks_per_step": ta + tb}
+            hpez.hpez_use_tuning(ctx.handle, None)
+        return res
+
+    tables = [("fixed_rules", None)] + ([("searched", table)] if table is not None else [])
+    dflt = one_config(None, tables)
+    md = one_config({"paradigm": hpez.HPEZ_PARADIGM_MD, "interp": hpez.HPEZ_LINEAR}, tables)
+    best = dflt[tables[-1][0]]
     return {"workload": "64 fields, log-uniform 32^3 .. 256x384x384 points, ~1/3 2D, "
                         "bumps/grf/lognormal/aniso/climate2d, rel eb per field in "
                         "{1e-2,1e-3,1e-4}, compress+decompress",
             "input_MB": round(nbytes / 1e6, 1),
-            "value": round(nbytes / (batch_ms / 1e3) / 1e9, 3), "unit": "GB/s",
-            "ms_per_step": round(batch_ms, 3),
-            "plain_value": round(nbytes / (plain_ms / 1e3) / 1e9, 3),
-            "plain_ms_per_step": round(plain_ms, 3),
-            "speedup_vs_plain": round(plain_ms / batch_ms, 3),
-            "launches_per_step": la + lb, "ticks_per_step": ta + tb,
-            "graph": True}
+            "value": best["value"], "unit": "GB/s", "ms_per_step": best["ms_per_step"],
+            "plain_value": dflt["plain_value"], "plain_ms_per_step": dflt["plain_ms_per_step"],
+            "speedup_vs_plain": best["speedup_vs_plain"],
+            "launches_per_step": best["launches_per_step"],
+            "ticks_per_step": best["ticks_per_step"],
+            "schedules": tables[-1][0], "default_config": dflt,
+            "md_linear_config": md, "graph": True,
+            "persistent_level_launches": True}
 
 
 def bench_lorenzo(ctx, x, shape, eb, cbuf, cap, y, stream, steps, peak):

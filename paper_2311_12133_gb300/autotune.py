@@ -28,9 +28,10 @@ def class_of(shape, cfg_kw):
     return key[:4], tuple(sorted((cfg_kw or {}).items()))
 
 
-def search_workload(ctx, specs, copies=0, reps=3, tuning=None, log=None):
+def search_workload(ctx, specs, copies=0, reps=3, tuning=None, log=None, save=None):
     """specs: (kind, shape, seed, rel eb, config kwargs or None) per field.
-    Returns the table (a new one unless `tuning` is given)."""
+    Returns the table (a new one unless `tuning` is given); with `save`, the
+    table is written there after every class."""
     t = tuning if tuning is not None else hpez.Tuning()
     seen = set()
     for kind, shape, seed, eb, kw in specs:
@@ -42,8 +43,10 @@ def search_workload(ctx, specs, copies=0, reps=3, tuning=None, log=None):
         cfg = hpez.make_config(len(shape), **kw) if kw else None
         t.search(ctx, x, eb, hpez.HPEZ_EB_REL, cfg, copies=copies, reps=reps)
         del x
+        if save:
+            t.save(save)
         if log:
-            log(f"searched class {c[0]} {dict(c[1])}: {len(t)} entries")
+            log(f"searched class {c[0]} {dict(c[1])}: {len(t)} entries", flush=True)
     return t
 
 
@@ -64,8 +67,9 @@ def main():
     ap.add_argument("--copies", type=int, default=0)
     a = ap.parse_args()
     ctx = hpez.Context(0)
-    t = search_workload(ctx, mix_specs(a.fields), copies=a.copies, reps=a.reps, log=print)
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
+    t = search_workload(ctx, mix_specs(a.fields), copies=a.copies, reps=a.reps, log=print,
+                        save=a.out)
     t.save(a.out)
     print(f"{len(t)} entries -> {a.out}")
     ctx.close()

@@ -133,3 +133,47 @@ def test_search_then_tuned_batch(gpu, expected, tmp_path):
         _run_and_check(gpu, expected)
     finally:
         hpez.hpez_use_tuning(gpu.handle, None)
+
+
+def test_shipped_table_batch_equals_oracle(gpu, oracle):
+    """The searched table shipped with the package, on the smallest fields
+    of the 64-field benchmark mix (both configurations it was searched
+    for): streams and fields equal the oracle's."""
+    import os
+    import torch
+    from oracle import oracle as O
+    from paper_2311_12133_gb300 import autotune, fields, hpez
+    if not os.path.exists(autotune.SHIPPED):
+        pytest.skip("no shipped table")
+    t = hpez.Tuning(autotune.SHIPPED)
+    specs = sorted(autotune.mix_specs(), key=lambda s: int(np.prod(s[1])))[:8]
+    hpez.hpez_use_tuning(gpu.handle, t)
+    try:
+        xs, args, want = [], [], []
+        for kind, shape, seed, eb, kw in specs:
+            x = fields.make(kind, shape, seed)
+            xd = torch.from_numpy(x).cuda()
+            xs.append(xd)
+            args.append((xd, eb, 1, hpez.make_config(x.ndim, **kw) if kw else None))
+            st, _, _, recon = oracle.compress(x, eb, 1, O.make_config(x.ndim, **kw) if kw
+                                              else None, want_recon=True)
+            want.append((st, recon))
+            assert t.get(hpez.hpez_level_key_of(shape, args[-1][3], 1, False)) is not None
+        b = hpez.Batch(gpu, fields=args)
+        b.run(graph=True)
+        sizes, status = b.results()
+        assert status == [0] * len(specs)
+        for i in range(len(specs)):
+            assert b.outs[i][:sizes[i]].cpu().numpy().tobytes() == want[i][0], i
+        b.close()
+        bufs = [torch.from_numpy(np.frombuffer(w, np.uint8).copy()).cuda() for w, _ in want]
+        d = hpez.Batch(gpu, streams=[(bufs[i], len(want[i][0]), want[i][0][:512])
+                                     for i in range(len(specs))])
+        d.run(graph=True)
+        _, st = d.results()
+        assert st == [0] * len(specs)
+        for i in range(len(specs)):
+            assert d.outs[i].cpu().numpy().tobytes() == want[i][1].tobytes(), i
+        d.close()
+    finally:
+        hpez.hpez_use_tuning(gpu.handle, None)
