@@ -350,13 +350,35 @@ int tune_globals(Call& k, std::vector<Variant>& vs, hpez_tune_report* rep,
     grid.push_back({vs[0].cfg.alpha, vs[0].cfg.beta});
   }
   const int ng = (int)grid.size();
-  const int nh = ng * nv;
+  // Pairs whose level factors min(alpha^(l-1), beta) (Eq. 15, the double
+  // products the device forms) agree at every level the tests run give the
+  // same level bounds, hence the same test: each distinct one runs once.
+  const int Lt = std::max(vs[0].g.L, vs[nv - 1].g.L);
+  std::vector<int> uniq_of(ng), reps;
+  std::vector<std::vector<double>> facs;
+  for (int v = 0; v < ng; ++v) {
+    std::vector<double> f(Lt);
+    for (int l = 1; l <= Lt; ++l) {
+      double ap = 1.0;
+      for (int i = 1; i < l; ++i) ap = ap * grid[v].first;
+      f[l - 1] = ap < grid[v].second ? ap : grid[v].second;
+    }
+    int u = 0;
+    while (u < (int)facs.size() && facs[u] != f) ++u;
+    if (u == (int)facs.size()) {
+      facs.push_back(f);
+      reps.push_back(v);
+    }
+    uniq_of[v] = u;
+  }
+  const int nu = (int)reps.size();
+  const int nh = nu * nv;
   for (int i = 0; i < nv; ++i)
-    for (int v = 0; v < ng; ++v) {
+    for (int u = 0; u < nu; ++u) {
       hpez_config c2 = vs[i].cfg;
-      c2.alpha = grid[v].first;
-      c2.beta = grid[v].second;
-      host[i * ng + v] = to_device(vs[i].p, c2);
+      c2.alpha = grid[reps[u]].first;
+      c2.beta = grid[reps[u]].second;
+      host[i * nu + u] = to_device(vs[i].p, c2);
     }
   prof.begin(HPEZ_PH_TUNE_EB, k.s);
   cudaMemcpyAsync(k.b.cfgs, host.data(), sizeof(TuneCfg) * nh,
@@ -365,7 +387,7 @@ int tune_globals(Call& k, std::vector<Variant>& vs, hpez_tune_report* rep,
   cudaMemsetAsync(k.b.hists, 0, sizeof(uint32_t) * 65536 * nh, k.s);
   cudaMemsetAsync(k.b.nout, 0, sizeof(unsigned long long) * nh, k.s);
   cudaMemsetAsync(k.b.score, 0, sizeof(unsigned long long) * nh, k.s);
-  launch_tune_test(k.x, vs[0].g, vs[nv - 1].g, ng, k.b.cfgs, nh, vs[0].nblk, 1,
+  launch_tune_test(k.x, vs[0].g, vs[nv - 1].g, nu, k.b.cfgs, nh, vs[0].nblk, 1,
                    true, k.b.score, k.b.hists, k.b.nout, nullptr, k.s);
   nl += 2;
   // the codebooks of these histograms and of the extra ones (the Lorenzo
@@ -391,7 +413,8 @@ int tune_globals(Call& k, std::vector<Variant>& vs, hpez_tune_report* rep,
     int best = 0;
     uint64_t best_bits = 0;
     for (int v = 0; v < ng; ++v) {
-      const uint64_t b = cost[i * ng + v] + 32ull * nout[i * ng + v] + 32ull * na;
+      const int h = i * nu + uniq_of[v];
+      const uint64_t b = cost[h] + 32ull * nout[h] + 32ull * na;
       if (v == 0 || b < best_bits) {
         best_bits = b;
         best = v;
