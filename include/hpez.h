@@ -81,8 +81,7 @@ typedef struct {
                             anchor_stride, not with blockwise.  A block's
                             columns must fit one CTA: A <= 32 in 3D, <= 1024
                             in 2D, else hpez_compress returns UNSUPPORTED;
-                            the batched and served forms and
-                            hpez_decompress_noalloc take interpolation
+                            hpez_decompress_noalloc takes interpolation
                             streams only (UNSUPPORTED) */
   double alpha, beta;    /* Eq. 15 level bounds, both >= 1 */
   double md_inv_var[3];  /* 1/sigma_d^2 for the Eq. 14 weights, > 0 */
@@ -134,6 +133,34 @@ HPEZ_API int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
  * Errors: CORRUPT_STREAM, OUT_TOO_SMALL, INVALID_ARG, NO_MEMORY, CUDA. */
 HPEZ_API int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
                     float* d_out, uint64_t out_cap_elems, void* stream);
+
+/* The same compress and decompress, enqueued on `stream` with no host
+ * synchronization (the launch sequences of hpez_compress / hpez_decompress,
+ * so the streams and fields are the same byte for byte).  The outcome is
+ * written on the device by the last kernel:
+ *   d_size    device u64: the stream size (0 on error)
+ *   d_status  device int32: 0 or a negative HPEZ_ERR_* (NONFINITE_INPUT,
+ *             OUT_TOO_SMALL, CORRUPT_STREAM, TIMEOUT)
+ *   h_header  host copy of the stream's first 512 bytes (decompress): the
+ *             launches are planned from it, so it must be the header of the
+ *             stream at d_in when the work runs
+ * The returned code covers only what the host checks before enqueueing
+ * (arguments, the header, capacities), as in the synchronous calls.  A call
+ * on a field larger than the context's scratch grows it first (cudaMalloc
+ * after a device synchronization); a call that needs no growth makes no
+ * allocation and no host read, so it can be captured in a CUDA graph
+ * (the capture replays the same pointers, sizes, bound and header).
+ * Refused (UNSUPPORTED): a config with a block map (compress reads the map
+ * from host memory) and a stream that went through the lossless stage
+ * (undoing it sizes a buffer on the host).  Block maps inside a stream are
+ * read on the device. */
+HPEZ_API int hpez_compress_async(hpez_ctx* ctx, const float* d_in, int ndim,
+                                 const uint64_t* dims, int eb_mode, double eb,
+                                 const hpez_config* cfg, void* d_out, uint64_t out_cap,
+                                 uint64_t* d_size, int32_t* d_status, void* stream);
+HPEZ_API int hpez_decompress_async(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
+                                   const void* h_header, float* d_out,
+                                   uint64_t out_cap_elems, int32_t* d_status, void* stream);
 
 /* Decompression that allocates nothing -- no counterpart in the paper; it
  * exists for callers that may not allocate memory: code running under a

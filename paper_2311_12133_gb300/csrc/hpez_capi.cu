@@ -847,11 +847,14 @@ int hpez_compress_bound(int ndim, const uint64_t* dims, uint64_t* out_bytes) {
   return HPEZ_OK;
 }
 
-int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
-                  const uint64_t* dims, int eb_mode, double eb,
-                  const hpez_config* cfg_in, void* d_out, uint64_t out_cap,
-                  uint64_t* h_out_size, void* stream) {
-  if (!ctx || !d_in || !d_out || !h_out_size) return HPEZ_ERR_INVALID_ARG;
+// The compress launch sequence.  Synchronous (d_status null): the size
+// comes back in *h_out_size.  Asynchronous: a last kernel writes the size
+// and the status to *d_size / *d_status and nothing waits.
+static int compress_impl(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
+                         int eb_mode, double eb, const hpez_config* cfg_in, void* d_out,
+                         uint64_t out_cap, uint64_t* h_out_size, unsigned long long* d_size,
+                         int* d_status, void* stream) {
+  if (!ctx || !d_in || !d_out || (!h_out_size && !d_status)) return HPEZ_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(d_out) & 15u) != 0) return HPEZ_ERR_INVALID_ARG;
   if (eb_mode != HPEZ_EB_ABS && eb_mode != HPEZ_EB_REL) return HPEZ_ERR_INVALID_ARG;
   if (!(eb > 0.0) || !std::isfinite(eb)) return HPEZ_ERR_INVALID_ARG;
@@ -870,6 +873,8 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   if (cfg.blockwise && !cfg.h_blockmap) return HPEZ_ERR_INVALID_ARG;
   if (cfg.predictor && !lorenzo_supported(p.n, p.fst, p.off, p.A))
     return HPEZ_ERR_UNSUPPORTED;
+  // the asynchronous form takes no host memory but the arguments
+  if (d_status && cfg.blockwise) return HPEZ_ERR_UNSUPPORTED;
   plan_chunks_blocks(p, cfg);
   cudaSetDevice(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1060,6 +1065,11 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
                   b.ctl, ctx->num_sms, s);
   pf.end(s);
   nl += 10;
+  if (d_status) {
+    launch_result_one(ResultJob{b.ctl, nullptr, 0, 0, d_size, d_status, 0}, s);
+    ++nl;
+    return cuda_check(cudaGetLastError());
+  }
   rc = cuda_check(cudaGetLastError());
   if (rc) return rc;
   rc = cuda_check(cudaMemcpyAsync(ctx->h_ctl, b.ctl, sizeof(Ctl),
@@ -1071,6 +1081,22 @@ int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim,
   if (ctx->h_ctl->status) return map_status(ctx->h_ctl->status);
   *h_out_size = ctx->h_ctl->total_size;
   return HPEZ_OK;
+}
+
+int hpez_compress(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
+                  int eb_mode, double eb, const hpez_config* cfg_in, void* d_out,
+                  uint64_t out_cap, uint64_t* h_out_size, void* stream) {
+  if (!h_out_size) return HPEZ_ERR_INVALID_ARG;
+  return compress_impl(ctx, d_in, ndim, dims, eb_mode, eb, cfg_in, d_out, out_cap, h_out_size,
+                       nullptr, nullptr, stream);
+}
+
+int hpez_compress_async(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
+                        int eb_mode, double eb, const hpez_config* cfg, void* d_out,
+                        uint64_t out_cap, uint64_t* d_size, int32_t* d_status, void* stream) {
+  if (!d_size || !d_status) return HPEZ_ERR_INVALID_ARG;
+  return compress_impl(ctx, d_in, ndim, dims, eb_mode, eb, cfg, d_out, out_cap, nullptr,
+                       reinterpret_cast<unsigned long long*>(d_size), d_status, stream);
 }
 
 int hpez_inspect(const void* h_header, uint64_t n, int* ndim, uint64_t* dims,
@@ -1088,22 +1114,36 @@ int hpez_inspect(const void* h_header, uint64_t n, int* ndim, uint64_t* dims,
   return HPEZ_OK;
 }
 
-int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
-                    float* d_out, uint64_t out_cap_elems, void* stream) {
+// The decompress launch sequence.  Synchronous (d_status null): the
+// header is read back first.  Asynchronous: the caller's host copy of the
+// header plans the launches, the one-symbol table's symbol and a block map
+// are read on the device, and a last kernel writes the status.
+static int decompress_impl(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
+                           const void* h_header, float* d_out, uint64_t out_cap_elems,
+                           int* d_status, void* stream) {
   if (!ctx || !d_in || !d_out) return HPEZ_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(d_in) & 15u) != 0) return HPEZ_ERR_INVALID_ARG;
   if (in_size < (uint64_t)kHeaderBytes) return HPEZ_ERR_CORRUPT_STREAM;
   if ((reinterpret_cast<uintptr_t>(d_out) & 3u) != 0) return HPEZ_ERR_INVALID_ARG;
+  if (d_status && !h_header) return HPEZ_ERR_INVALID_ARG;
   ctx->out_aligned16 = (reinterpret_cast<uintptr_t>(d_out) & 15u) == 0;
   cudaSetDevice(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int rc = cuda_check(cudaMemcpyAsync(ctx->h_hdr, d_in, kHeaderBytes,
-                                      cudaMemcpyDeviceToHost, s));
-  if (rc) return rc;
-  rc = cuda_check(cudaStreamSynchronize(s));
-  if (rc) return rc;
+  int rc;
+  uint8_t hdr_local[kHeaderBytes];
+  const uint8_t* hh = hdr_local;
+  if (d_status) {
+    std::memcpy(hdr_local, h_header, kHeaderBytes);
+  } else {
+    rc = cuda_check(cudaMemcpyAsync(ctx->h_hdr, d_in, kHeaderBytes, cudaMemcpyDeviceToHost, s));
+    if (rc) return rc;
+    rc = cuda_check(cudaStreamSynchronize(s));
+    if (rc) return rc;
+    hh = ctx->h_hdr;
+  }
   uint64_t raw = 0;
-  if (lossless_flagged(ctx->h_hdr, &raw)) {
+  if (lossless_flagged(hh, &raw)) {
+    if (d_status) return HPEZ_ERR_UNSUPPORTED;  // undoing the stage needs its sizes
     // the lossless stage (Sec. 4, Step 5) first, into the context's buffer
     if (raw < (uint64_t)kHeaderBytes || raw > (1ull << 40)) return HPEZ_ERR_CORRUPT_STREAM;
     if ((rc = ensure_io(&ctx->lz_stream, &ctx->lz_stream_cap, raw))) return rc;
@@ -1113,13 +1153,18 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
     return hpez_decompress(ctx, ctx->lz_stream, got, d_out, out_cap_elems, stream);
   }
   StreamInfo si;
-  rc = parse_stream_header(ctx->h_hdr, in_size, si);
+  rc = parse_stream_header(hh, in_size, si);
   if (rc) return rc;
   const uint64_t N = si.N;
   if (N > out_cap_elems) return HPEZ_ERR_OUT_TOO_SMALL;
   const uint8_t* in = static_cast<const uint8_t*>(d_in);
   if (si.is_const) {
     launch_fill(d_out, (uint32_t)N, si.const_value, ctx->num_sms, s);
+    if (d_status) {
+      rc = cuda_check(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+      if (rc) return rc;
+      return cuda_check(cudaGetLastError());
+    }
     rc = cuda_check(cudaGetLastError());
     if (rc) return rc;
     return cuda_check(cudaStreamSynchronize(s));
@@ -1132,7 +1177,7 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   const uint64_t oa = si.oa, ocw = si.ocw, ot = si.ot, oo = si.oo, ob = si.ob,
                  obm = si.obm;
   uint16_t single_sym = 0;
-  if (nused == 1) {
+  if (nused == 1 && !d_status) {
     // the lone symbol of a single-symbol code table
     rc = cuda_check(cudaMemcpyAsync(ctx->h_hdr, in + ot, 2,
                                     cudaMemcpyDeviceToHost, s));
@@ -1195,7 +1240,7 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   pf.begin(HPEZ_PH_DECODE, s);
   launch_decode(in, ob, twords, lbits_stream, woff, p.N, p.C, p.nch, nused,
                 single_sym, lut, cnt, first, offs, sorted, codes, zc, ctl,
-                ctx->num_sms, s);
+                ctx->num_sms, s, d_status && nused == 1 ? in + ot : nullptr);
   pf.end(s);
   pf.begin(HPEZ_PH_SCATTER, s);
   launch_scan(zc, zoff, p.nch, &tot[1], ctl, s);
@@ -1217,7 +1262,7 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   }
   // a uniform block map runs as its interpolator (the map is read back)
   std::vector<uint8_t> hmap;
-  if (cfg.blockwise) {
+  if (cfg.blockwise && !d_status) {
     hmap.resize(p.nblocks);
     rc = cuda_check(cudaMemcpyAsync(hmap.data(), in + obm, p.nblocks,
                                     cudaMemcpyDeviceToHost, s));
@@ -1282,6 +1327,11 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
     }
     pf.end(s);
   }
+  if (d_status) {
+    launch_result_one(ResultJob{ctl, tot, twords, nout, nullptr, d_status, 1}, s);
+    ++nl;
+    return cuda_check(cudaGetLastError());
+  }
   rc = cuda_check(cudaGetLastError());
   if (rc) return rc;
   unsigned long long h_tot[2];
@@ -1297,6 +1347,18 @@ int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   if (ctx->h_ctl->status) return map_status(ctx->h_ctl->status);
   if (h_tot[0] != twords || h_tot[1] != nout) return HPEZ_ERR_CORRUPT_STREAM;
   return HPEZ_OK;
+}
+
+int hpez_decompress(hpez_ctx* ctx, const void* d_in, uint64_t in_size, float* d_out,
+                    uint64_t out_cap_elems, void* stream) {
+  return decompress_impl(ctx, d_in, in_size, nullptr, d_out, out_cap_elems, nullptr, stream);
+}
+
+int hpez_decompress_async(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
+                          const void* h_header, float* d_out, uint64_t out_cap_elems,
+                          int32_t* d_status, void* stream) {
+  if (!d_status || !h_header) return HPEZ_ERR_INVALID_ARG;
+  return decompress_impl(ctx, d_in, in_size, h_header, d_out, out_cap_elems, d_status, stream);
 }
 
 

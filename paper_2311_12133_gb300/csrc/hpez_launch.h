@@ -135,7 +135,8 @@ void launch_decode(const uint8_t* stream, uint64_t off_bits,
                    const uint32_t* lut, const uint32_t* cnt,
                    const unsigned long long* first, const uint32_t* offs,
                    const uint16_t* sorted, uint16_t* codes, uint32_t* zc,
-                   Ctl* ctl, int num_sms, cudaStream_t s);
+                   Ctl* ctl, int num_sms, cudaStream_t s,
+                   const uint8_t* single_src = nullptr);
 
 // k_stream.cu
 void launch_scan(const uint32_t* in, unsigned long long* out, uint32_t n,
@@ -202,6 +203,8 @@ void launch_layout_batch(const LayoutJob* J, int nj, cudaStream_t s);
 void launch_finalize_batch(const FinalizeJob* J, const uint32_t* off, int nj,
                            uint32_t nblk, cudaStream_t s);
 void launch_result_batch(const ResultJob* J, int nj, cudaStream_t s);
+// one request's outcome (the job by value)
+void launch_result_one(const ResultJob& J, cudaStream_t s);
 void launch_upsample_batch(const UpsampleJob* J, const uint32_t* off, int nj,
                            uint32_t nblk, cudaStream_t s);
 void launch_pass_batch(bool decomp, const PassJob* J, const uint32_t* off,

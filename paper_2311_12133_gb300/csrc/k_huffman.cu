@@ -859,13 +859,19 @@ __device__ __forceinline__ void decode_body(
         nbuf = 32 - sh;
         ++wi;
       }
+      // the lane's next two words are loaded ahead, so a refill takes a
+      // word that has arrived while earlier symbols were decoded (word wi
+      // and wi + 1 of the lane, 0 past the chunk's words)
+      uint32_t nx0 = wi < nw ? __ldg(words + wi) : 0u;
+      uint32_t nx1 = wi + 1 < nw ? __ldg(words + wi + 1) : 0u;
       uint32_t left = mybits;  // bits of this lane not consumed yet
       for (uint32_t j = lane; j < nc; j += 32) {
         while (nbuf <= 32) {
-          const uint32_t w = wi < nw ? __ldg(words + wi) : 0u;
-          buf |= (unsigned long long)w << (32 - nbuf);
+          buf |= (unsigned long long)nx0 << (32 - nbuf);
           nbuf += 32;
           ++wi;
+          nx0 = nx1;
+          nx1 = wi + 1 < nw ? __ldg(words + wi + 1) : 0u;
         }
         const uint32_t e = lut[(uint32_t)(buf >> (64 - kLutBits))];
         uint32_t sym = 0, len = 0;
@@ -910,9 +916,13 @@ __global__ void __launch_bounds__(256)
              const unsigned long long* __restrict__ g_first,
              const uint32_t* __restrict__ g_offs,
              const uint16_t* __restrict__ sorted, uint16_t* __restrict__ codes,
-             uint32_t* __restrict__ zc, Ctl* ctl) {
+             uint32_t* __restrict__ zc, Ctl* ctl, const uint8_t* __restrict__ single_src) {
+  // single_src: the lone symbol of a one-symbol table read from the stream
+  // here (no host read), else single_sym as given
+  const uint16_t sym =
+      single_src ? (uint16_t)(single_src[0] | (single_src[1] << 8)) : single_sym;
   decode_body(stream, off_bits, total_words, lanebits_bytes, woff, N, C, nch,
-              n_used, single_sym, g_lut, g_cnt, g_first, g_offs, sorted, codes,
+              n_used, sym, g_lut, g_cnt, g_first, g_offs, sorted, codes,
               zc, ctl, blockIdx.x, gridDim.x);
 }
 
@@ -1095,10 +1105,10 @@ void launch_decode(const uint8_t* stream, uint64_t off_bits,
                    const uint32_t* lut, const uint32_t* cnt,
                    const unsigned long long* first, const uint32_t* offs,
                    const uint16_t* sorted, uint16_t* codes, uint32_t* zc,
-                   Ctl* ctl, int num_sms, cudaStream_t s) {
+                   Ctl* ctl, int num_sms, cudaStream_t s, const uint8_t* single_src) {
   k_decode<<<warps_grid(nch, num_sms * 2), 256, 0, s>>>(
       stream, off_bits, total_words, lanebits_bytes, woff, N, C, nch, n_used,
-      single_sym, lut, cnt, first, offs, sorted, codes, zc, ctl);
+      single_sym, lut, cnt, first, offs, sorted, codes, zc, ctl, single_src);
 }
 
 // ---------------------------------------------------------------------

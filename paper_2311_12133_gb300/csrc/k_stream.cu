@@ -200,10 +200,7 @@ __global__ void k_finalize(HeaderImage hdr, HeaderImage hdr_const,
 // Per request: the device status (its values equal the C-ABI error codes)
 // and, for compress, the stream size; decompress also checks that the
 // decoded word and outlier counts match the header.
-__global__ void k_result_batch(const ResultJob* __restrict__ J, int nj) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nj) return;
-  const ResultJob& q = J[j];
+__device__ __forceinline__ void result_body(const ResultJob& q) {
   int st = q.ctl->status;
   unsigned long long size = 0;
   if (!q.decomp) {
@@ -214,6 +211,14 @@ __global__ void k_result_batch(const ResultJob* __restrict__ J, int nj) {
   if (q.size_out) *q.size_out = size;
   if (q.status_out) *q.status_out = st;
 }
+
+__global__ void k_result_batch(const ResultJob* __restrict__ J, int nj) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nj) return;
+  result_body(J[j]);
+}
+
+__global__ void k_result_one(ResultJob q) { result_body(q); }
 
 __global__ void __launch_bounds__(1024) k_scan_batch(const ScanJob* __restrict__ J) {
   const ScanJob& q = J[blockIdx.x];
@@ -270,6 +275,8 @@ void launch_finalize(const uint8_t* hdr, const uint8_t* hdr_const,
 void launch_result_batch(const ResultJob* J, int nj, cudaStream_t s) {
   if (nj > 0) k_result_batch<<<(nj + 127) / 128, 128, 0, s>>>(J, nj);
 }
+
+void launch_result_one(const ResultJob& J, cudaStream_t s) { k_result_one<<<1, 1, 0, s>>>(J); }
 
 void launch_scan_batch(const ScanJob* J, int nj, cudaStream_t s) {
   if (nj > 0) k_scan_batch<<<nj, 1024, 0, s>>>(J);

@@ -175,6 +175,10 @@ def _load():
                                              ctypes.c_int, ctypes.c_double,
                                              cfgp, vp, u64, u64p, vp]),
             "hpez_decompress": (ctypes.c_int, [vp, vp, u64, vp, u64, vp]),
+            "hpez_compress_async": (ctypes.c_int, [vp, vp, ctypes.c_int, u64p,
+                                                   ctypes.c_int, ctypes.c_double,
+                                                   cfgp, vp, u64, vp, vp, vp]),
+            "hpez_decompress_async": (ctypes.c_int, [vp, vp, u64, vp, vp, u64, vp, vp]),
             "hpez_compress_host": (ctypes.c_int, [vp, vp, ctypes.c_int, u64p,
                                                   ctypes.c_int, ctypes.c_double,
                                                   cfgp, vp, u64, u64p, vp]),
@@ -289,7 +293,7 @@ def exported_symbols() -> list[str]:
             "hpez_tuning_create", "hpez_tuning_destroy", "hpez_tuning_set",
             "hpez_tuning_get", "hpez_tuning_count", "hpez_tuning_save",
             "hpez_tuning_load", "hpez_level_key_of", "hpez_use_tuning",
-            "hpez_tuning_search"]
+            "hpez_tuning_search", "hpez_compress_async", "hpez_decompress_async"]
 
 
 def _check(rc: int, what: str):
@@ -424,6 +428,26 @@ class Tuning:
             self.close()
         except Exception:
             pass
+
+
+def hpez_compress_async(ctx, d_in: int, shape, eb_mode: int, eb: float,
+                        cfg: hpez_config | None, d_out: int, out_cap: int, d_size: int,
+                        d_status: int, stream: int = 0) -> None:
+    """Enqueue a compress; the size (u64) and status (int32) land at the
+    device addresses d_size / d_status."""
+    _check(_load().hpez_compress_async(ctx, d_in, len(shape), _dims(shape), eb_mode, float(eb),
+                                       ctypes.byref(cfg) if cfg is not None else None, d_out,
+                                       out_cap, d_size, d_status, stream or None),
+           "hpez_compress_async")
+
+
+def hpez_decompress_async(ctx, d_in: int, in_size: int, header: bytes, d_out: int,
+                          out_cap_elems: int, d_status: int, stream: int = 0) -> None:
+    """Enqueue a decompress planned from `header` (the stream's first 512
+    bytes); the status (int32) lands at the device address d_status."""
+    hb = ctypes.create_string_buffer(bytes(header[:HPEZ_HEADER_BYTES]), HPEZ_HEADER_BYTES)
+    _check(_load().hpez_decompress_async(ctx, d_in, in_size, hb, d_out, out_cap_elems,
+                                         d_status, stream or None), "hpez_decompress_async")
 
 
 HPEZ_NOALLOC_MAX_POINTS = 2097152
