@@ -79,6 +79,9 @@ def parse():
                          "log-normal, anisotropic and 2D fields)")
     ap.add_argument("--served-seconds", type=float, default=60.0,
                     help="length of the Poisson request stream of the served section")
+    ap.add_argument("--schedules", choices=["searched", "fixed"], default="searched",
+                    help="level schedules: the searched table shipped with the package "
+                         "(the library's autotuner output) or the fixed rules")
     ap.add_argument("--fused", type=int, default=1,
                     help="1: one kernel per level (1D-style); 0: one per pass")
     ap.add_argument("--tile", default="",
@@ -986,6 +989,11 @@ def main():
     A = 32 if len(shape) == 3 else (64 if len(shape) == 2 else 128)
     x = fields.grf_torch(shape, seed=replica_seed(rank), device=f"cuda:{local}")
     ctx = hpez.Context(local)
+    from paper_2311_12133_gb300 import autotune
+    sched_table = None
+    if args.schedules == "searched" and os.path.exists(autotune.SHIPPED):
+        sched_table = hpez.Tuning(autotune.SHIPPED)
+        hpez.hpez_use_tuning(ctx.handle, sched_table)
     hpez.hpez_set_option(ctx.handle, hpez.HPEZ_OPT_FUSED_LEVELS, args.fused)
     if args.tile:
         for o, e in zip((hpez.HPEZ_OPT_TILE_E0, hpez.HPEZ_OPT_TILE_E1,
@@ -1218,6 +1226,7 @@ def main():
     batched = served = None
     if rank == 0 and world == 1 and not args.no_batched:
         batched = bench_batched(ctx, max(3, args.steps // 2), args.warmup)
+        hpez.hpez_use_tuning(ctx.handle, sched_table)
     if rank == 0 and world == 1 and not args.no_served:
         served = bench_served(ctx, seconds=args.served_seconds)
 
@@ -1238,7 +1247,9 @@ def main():
                                        "full auto-tuning + compress (hpez_compress_auto)")
                                    + " + decompress",
                        "global_batch": world, "parallelism": f"replicas{world}",
-                       "l2": f"input {4 * N / 1e6:.0f} MB > L2 {L2_BYTES / 1e6:.0f} MB, no flush"},
+                       "l2": f"input {4 * N / 1e6:.0f} MB > L2 {L2_BYTES / 1e6:.0f} MB, no flush",
+                       "level_schedules": "searched table (autotune.SHIPPED)"
+                       if sched_table is not None else "fixed rules"},
             "compress_gbps": round(world * 4 * N / (comp_ms / args.steps / 1e3) / 1e9, 3),
             "decompress_gbps": round(world * 4 * N / (dec_ms / args.steps / 1e3) / 1e9, 3),
             "compression_ratio": round(4 * N / size, 3), "psnr_db": round(psnr, 3),

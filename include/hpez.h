@@ -281,8 +281,9 @@ HPEZ_API int hpez_batch_destroy(hpez_batch* b);
  * back to the fixed rules. */
 typedef struct {
   int32_t ndim;      /* 1..3 */
-  int32_t cls[3];    /* ceil(log2(n)) of each slot of the field seen as 3D,
-                        slowest first (leading slots 0 for 1D and 2D) */
+  int32_t cls[3];    /* floor(2 log2 n) (half-octave class) of each slot
+                        of the field seen as 3D, slowest first (0 for the
+                        leading slots of 1D and 2D fields) */
   int32_t stride;    /* s = 2^(l-1) */
   int32_t interp;    /* HPEZ_LINEAR..HPEZ_CUBIC_NAT, or 3: a block map or
                         same-level halves (the per-point interpolator) */

@@ -847,6 +847,29 @@ int hpez_compress_bound(int ndim, const uint64_t* dims, uint64_t* out_bytes) {
   return HPEZ_OK;
 }
 
+// A level's chunk count for the warp-strip kernel from the context's
+// schedule table (searched offline), unless HPEZ_OPT_STREAM_CHUNKS is set.
+// The single-field calls take only that from the table: the batched
+// form's persistent launches of the other families favour other tile
+// shapes than one CTA per tile.  A decompress level without a warp-strip
+// entry takes the compress level's.
+struct LevelSchedScope {
+  int chunks;
+  LevelSchedScope(const hpez_ctx* c, const Plan& p, const hpez_config& kc, int l, bool decomp)
+      : chunks(c->stream_chunks) {
+    if (c->stream_chunks || c->sched.m.empty()) return;
+    for (int d = decomp ? 1 : 0; d >= 0; --d) {
+      std::array<int32_t, 8> k = sched_key(p, kc, l, decomp);
+      k[7] = d;
+      const auto it = c->sched.m.find(k);
+      if (it != c->sched.m.end() && it->second.family == HPEZ_FAM_MD3W) {
+        chunks = it->second.chunks;
+        return;
+      }
+    }
+  }
+};
+
 // The compress launch sequence.  Synchronous (d_status null): the size
 // comes back in *h_out_size.  Asynchronous: a last kernel writes the size
 // and the status to *d_size / *d_status and nothing waits.
@@ -984,6 +1007,7 @@ static int compress_impl(hpez_ctx* ctx, const float* d_in, int ndim, const uint6
   sb.ctl = b.ctl;
   for (int l = p.L; l >= 1; --l) {
     const int g = l - 1;
+    const LevelSchedScope ls(ctx, p, sc, l, false);
     pf.begin(HPEZ_PH_LEVEL + g, s);
     sb.R = b.R[g];
     sb.C = b.Cg[g];
@@ -1001,7 +1025,7 @@ static int compress_impl(hpez_ctx* ctx, const float* d_in, int ndim, const uint6
       if (ctx->warp_levels &&
           md3w_supported(FM, false, d_in, b.R[l], b.Cg[l], b.R[g], b.Cg[g])) {
         launch_level_md3w(false, sb.kind, FM, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g], b.ctl,
-                          ctx->num_sms, ctx->stream_chunks, s);
+                          ctx->num_sms, ls.chunks, s);
         ++nl;
       } else if (ctx->stream_levels && md3s_supported(FM, false, d_in, b.R[l], b.Cg[l]) &&
           launch_level_md3s(false, sb.kind, FM, sb, b.R[l], b.Cg[l], b.R[g], b.Cg[g],
@@ -1280,6 +1304,9 @@ static int decompress_impl(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
   sb.ctl = ctl;
   for (int l = cfg.predictor ? 0 : p.L; l >= 1; --l) {
     const int g = l - 1;
+    // keyed by the config this sweep runs (a uniform block map read back
+    // is its interpolator)
+    const LevelSchedScope ls(ctx, p, sc, l, true);
     pf.begin(HPEZ_PH_DLEVEL + g, s);
     sb.R = R[g];
     sb.kind = sc.interp[l - 1];
@@ -1295,7 +1322,7 @@ static int decompress_impl(hpez_ctx* ctx, const void* d_in, uint64_t in_size,
     } else if (!spline && plan_md3(ctx, p, sc, l, true, FM, E1)) {
       if (ctx->warp_levels && md3w_supported(FM, true, codes, R[l], nullptr, R[g], nullptr)) {
         launch_level_md3w(true, sb.kind, FM, sb, R[l], nullptr, R[g], nullptr, ctl,
-                          ctx->num_sms, ctx->stream_chunks, s);
+                          ctx->num_sms, ls.chunks, s);
         ++nl;
       } else if (ctx->stream_levels && md3s_supported(FM, true, codes, R[l], nullptr) &&
           launch_level_md3s(true, sb.kind, FM, sb, R[l], nullptr, R[g], nullptr, ctl,

@@ -1008,7 +1008,7 @@ namespace {
 
 // The candidate schedules of the search: every family with tile shapes or
 // chunk counts from a fixed list (slot extents slowest first).
-std::vector<hpez_level_sched> sched_candidates(int ndim) {
+std::vector<hpez_level_sched> sched_candidates(int ndim, int ke1) {
   std::vector<hpez_level_sched> c;
   auto add = [&](int fam, int t0, int t1, int t2, int chunks) {
     hpez_level_sched v;
@@ -1022,7 +1022,14 @@ std::vector<hpez_level_sched> sched_candidates(int ndim) {
   };
   if (ndim == 3) {
     for (int e1 : {2, 4, 8, 16, 32}) add(HPEZ_FAM_LEVEL3D, 0, e1, 0, 0);
-    for (int ch : {1, 2, 4, 8, 16, 0}) add(HPEZ_FAM_MD3W, 0, 0, 0, ch);
+    // warp strips: chunks of K even planes of the finest level
+    add(HPEZ_FAM_MD3W, 0, 0, 0, 0);
+    int last = -1;
+    for (int K : {2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 16, 24}) {
+      const int ch = (ke1 + K - 1) / K;
+      if (ch >= 1 && ch != last) add(HPEZ_FAM_MD3W, 0, 0, 0, ch);
+      last = ch;
+    }
     for (int e1 : {2, 4, 8, 16, 32}) add(HPEZ_FAM_MD3, 0, e1, 0, 0);
     const int f3[][3] = {{1, 2, 512}, {1, 4, 256}, {1, 8, 128}, {2, 8, 128},
                          {2, 4, 256}, {1, 16, 64}, {2, 16, 64}, {4, 8, 64}};
@@ -1139,7 +1146,7 @@ extern "C" int hpez_tuning_search(hpez_ctx* ctx, hpez_tuning* t, const float* d_
   std::vector<uint64_t> sizes(copies);
   std::vector<int32_t> status(copies);
   std::vector<uint8_t> hdr(kHeaderBytes);
-  for (const hpez_level_sched& c : sched_candidates(ndim)) {
+  for (const hpez_level_sched& c : sched_candidates(ndim, (int)(p.grid[0].m[0] + 1) / 2)) {
     if (rc) break;
     ctx->sched.m.clear();
     for (int dir = 0; dir < 2; ++dir)

@@ -19,9 +19,11 @@ using namespace hpez::host;
 
 namespace {
 
-int ceil_log2(uint32_t n) {
+// half-octave class of an extent: floor(2 log2 n) = floor(log2 n^2)
+int half_octave(uint32_t n) {
+  const unsigned long long sq = (unsigned long long)n * n;
   int c = 0;
-  while ((1ull << c) < (unsigned long long)n) ++c;
+  while (c < 63 && (sq >> (c + 1)) != 0) ++c;
   return c;
 }
 
@@ -45,7 +47,7 @@ hpez_level_key from_array(const std::array<int32_t, 8>& a) {
 bool key_ok(const hpez_level_key& k) {
   if (k.ndim < 1 || k.ndim > 3) return false;
   for (int s = 0; s < 3; ++s)
-    if (k.cls[s] < 0 || k.cls[s] > 32) return false;
+    if (k.cls[s] < 0 || k.cls[s] > 64) return false;
   if (k.stride < 1 || k.stride > (1 << 20) || (k.stride & (k.stride - 1))) return false;
   if (k.interp < 0 || k.interp > 3) return false;
   if (k.paradigm < 0 || k.paradigm > 1) return false;
@@ -68,9 +70,9 @@ namespace host {
 std::array<int32_t, 8> sched_key(const Plan& p, const hpez_config& sc, int l, bool decomp) {
   const bool per_point = sc.blockwise || sc.same_level[l - 1];
   return {p.ndim,
-          ceil_log2(p.n[0]),
-          ceil_log2(p.n[1]),
-          ceil_log2(p.n[2]),
+          half_octave(p.n[0]),
+          half_octave(p.n[1]),
+          half_octave(p.n[2]),
           1 << (l - 1),
           per_point ? 3 : (int32_t)sc.interp[l - 1],
           (int32_t)sc.paradigm[l - 1],

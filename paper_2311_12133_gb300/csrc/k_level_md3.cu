@@ -293,13 +293,21 @@ __global__ void __launch_bounds__(256)
 template <bool kDecomp, int KIND, bool kOdd>
 __global__ void __launch_bounds__(256)
     k_md3_batch(const MD3Job* __restrict__ J, const uint32_t* __restrict__ off, int nj) {
+  // the job's level geometry, read in every inner loop, in shared memory
+  // (the single-field kernel reads it from its parameters)
+  __shared__ LevelMD sP;
+  static_assert(sizeof(LevelMD) % 4 == 0, "word copy");
   for_each_batch_block(off, nj, [&](int j, uint32_t t) {
     const MD3Job& q = J[j];
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&q.P);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sP);
+    for (int i = threadIdx.x; i < (int)(sizeof(LevelMD) / 4); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
     if (kOdd)
-      md3_odd_body<kDecomp, KIND>(q.P, q.E1, q.nt1, q.X, q.codes_full, q.outl_full, q.Rc,
+      md3_odd_body<kDecomp, KIND>(sP, q.E1, q.nt1, q.X, q.codes_full, q.outl_full, q.Rc,
                                   q.Rs, q.Cs, q.ctl, t);
     else
-      md3_even_body<kDecomp, KIND>(q.P, q.E1, q.nt1, q.X, q.codes_full, q.outl_full, q.Rc,
+      md3_even_body<kDecomp, KIND>(sP, q.E1, q.nt1, q.X, q.codes_full, q.outl_full, q.Rc,
                                    q.Cc, q.Rs, q.Cs, q.ctl, t);
   });
 }

@@ -177,3 +177,42 @@ def test_shipped_table_batch_equals_oracle(gpu, oracle):
         d.close()
     finally:
         hpez.hpez_use_tuning(gpu.handle, None)
+
+
+@pytest.mark.parametrize("chunks", [1, 3, 7])
+def test_single_calls_follow_the_table(gpu, oracle, chunks):
+    """The single-field calls take a level's tile shape and chunk count from
+    the table: the warp-strip level with several chunk counts, the 3D and
+    fused level kernels with other tiles; streams and fields equal the
+    oracle's."""
+    import torch
+    from oracle import oracle as O
+    from paper_2311_12133_gb300 import fields, hpez
+    cases = [(fields.make("grf", (40, 48, 64), 31), dict(paradigm=1, interp=0)),
+             (fields.make("bumps", (36, 40, 44), 32), None),
+             (fields.make("climate2d", (90, 130), 33), None)]
+    t = hpez.Tuning()
+    for x, kw in cases:
+        cfg = hpez.make_config(x.ndim, **kw) if kw else None
+        for l in range(1, _levels(hpez, x.shape, cfg) + 1):
+            for d in (False, True):
+                k = hpez.hpez_level_key_of(x.shape, cfg, l, d)
+                if kw:
+                    t.set(k, hpez.HPEZ_FAM_MD3W if l == 1 else hpez.HPEZ_FAM_MD3,
+                          (0, 4, 0), chunks)
+                elif x.ndim == 3:
+                    t.set(k, hpez.HPEZ_FAM_LEVEL3D, (0, 2 * chunks, 0))
+                else:
+                    t.set(k, hpez.HPEZ_FAM_FUSED, (1, 2 * chunks, 64))
+    hpez.hpez_use_tuning(gpu.handle, t)
+    try:
+        for x, kw in cases:
+            cfg = hpez.make_config(x.ndim, **kw) if kw else None
+            want, _, _, _ = oracle.compress(x, 1e-3, 1, O.make_config(x.ndim, **kw) if kw
+                                            else None)
+            buf, size = gpu.compress(torch.from_numpy(x).cuda(), 1e-3, 1, cfg)
+            assert buf[:size].cpu().numpy().tobytes() == want
+            y = gpu.decompress(buf, size).cpu().numpy()
+            assert y.tobytes() == oracle.decompress(want).tobytes()
+    finally:
+        hpez.hpez_use_tuning(gpu.handle, None)

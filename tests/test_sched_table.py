@@ -14,13 +14,18 @@ def lib():
 
 
 def test_level_keys():
-    # (ndim, ceil log2 of each slot, stride, interp, paradigm, decomp)
+    # (ndim, floor(2 log2 n) of each slot, stride, interp, paradigm, decomp)
     k = hpez.hpez_level_key_of((100, 500, 500), None, 1, False)
-    assert k == (3, 7, 9, 9, 1, hpez.HPEZ_CUBIC_NAK, 0, 0)
+    assert k == (3, 13, 17, 17, 1, hpez.HPEZ_CUBIC_NAK, 0, 0)
     k = hpez.hpez_level_key_of((128, 128, 128), None, 3, True)
-    assert k == (3, 7, 7, 7, 4, hpez.HPEZ_CUBIC_NAK, 0, 1)
+    assert k == (3, 14, 14, 14, 4, hpez.HPEZ_CUBIC_NAK, 0, 1)
     k = hpez.hpez_level_key_of((1800, 3600), None, 2, False)
-    assert k == (2, 0, 11, 12, 2, hpez.HPEZ_CUBIC_NAK, 0, 0)
+    assert k == (2, 0, 21, 23, 2, hpez.HPEZ_CUBIC_NAK, 0, 0)
+    # half-octaves: 335 and 512 (or 362 and 363) fall in different classes
+    import math
+    for n in (1, 2, 3, 181, 182, 335, 362, 363, 384, 511, 512, 513, 3600):
+        want = math.floor(2 * math.log2(n) + 1e-12)
+        assert hpez.hpez_level_key_of((n, 8), None, 1, False)[2] == want, n
     cfg = hpez.make_config(3, paradigm=1, interp=0)
     assert hpez.hpez_level_key_of((64, 64, 64), cfg, 1, False)[5:7] == (0, 1)
     # same-level halves and block maps take the per-point interpolator
