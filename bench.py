@@ -257,9 +257,11 @@ def phase_bytes(name: str, shape, A, comp_size: int, lorenzo: bool = False) -> i
         l = int(name[6:])
         n_s, n_c = gs[l - 1], gs[l]
         return 2 * (n_s - n_c) + 4 * n_c + 4 * n_s
-    if name in ("hist", "encode_len"):
+    if name == "hist":
         return 2 * N
     if name == "pack":
+        # the one-pass encode: lane bit counts, chunk offsets and packing
+        # (the codes once, the bit stream once)
         return 2 * N + comp_size
     if name == "decode":
         return comp_size + 2 * N

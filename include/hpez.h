@@ -267,6 +267,8 @@ HPEZ_API int hpez_batch_results(hpez_batch* b, void* stream, uint64_t* h_sizes,
 /* Kernel launches and ticks of one run. */
 HPEZ_API int hpez_batch_launch_count(hpez_batch* b, uint64_t* launches,
                                      uint64_t* ticks);
+/* Frees the batch's device memory.  Batches and servers belong to the
+ * context they were made on: destroy them before that context. */
 HPEZ_API int hpez_batch_destroy(hpez_batch* b);
 
 /* ---- level schedules of the batched and served forms (no counterpart in

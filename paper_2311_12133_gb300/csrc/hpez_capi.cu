@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -424,6 +425,9 @@ int map_status(int st) {
 
 int cuda_check(cudaError_t e) {
   if (e == cudaSuccess) return HPEZ_OK;
+  // HPEZ_DEBUG_CUDA=1 in the environment names the runtime error on stderr
+  static const bool dbg = std::getenv("HPEZ_DEBUG_CUDA") != nullptr;
+  if (dbg) std::fprintf(stderr, "hpez: CUDA runtime error %s\n", cudaGetErrorName(e));
   if (e == cudaErrorMemoryAllocation) return HPEZ_ERR_NO_MEMORY;
   return HPEZ_ERR_CUDA;
 }
@@ -578,6 +582,7 @@ struct CompressBufs {
   unsigned long long* woff;
   uint16_t* lbits;
   uint8_t* bmap;
+  unsigned long long* flags;  // the one-pass encode's chunk flags + counter
 };
 
 
@@ -927,6 +932,7 @@ static int compress_impl(hpez_ctx* ctx, const float* d_in, int ndim, const uint6
   const size_t o_woff = ar.take<unsigned long long>(p.nch);
   const size_t o_lbits = ar.take<uint16_t>((size_t)p.nch * 32);
   const size_t o_bmap = ar.take<uint8_t>(p.nblocks + 1);
+  const size_t o_flags = ar.take<unsigned long long>((size_t)p.nch + 1);
   rc = ensure_scratch(ctx, ar.off);
   if (rc) return rc;
   char* S = ctx->scratch;
@@ -950,6 +956,7 @@ static int compress_impl(hpez_ctx* ctx, const float* d_in, int ndim, const uint6
   b.woff = reinterpret_cast<unsigned long long*>(S + o_woff);
   b.lbits = reinterpret_cast<uint16_t*>(S + o_lbits);
   b.bmap = reinterpret_cast<uint8_t*>(S + o_bmap);
+  b.flags = reinterpret_cast<unsigned long long*>(S + o_flags);
 
   // stream layout (static part)
   const uint64_t na = cfg.predictor ? 0 : n_anchors(p);
@@ -1068,16 +1075,15 @@ static int compress_impl(hpez_ctx* ctx, const float* d_in, int ndim, const uint6
   launch_codebook(b.hist, b.enc, b.tsyms, b.tlens, b.gkeys, b.giw, b.gpar,
                   b.lens_by_sym, b.ctl, s);
   pf.end(s);
+  // the stream's section offsets (their capacity check comes with the
+  // bit count, inside the one-pass encode)
   pf.begin(HPEZ_PH_ENCODE, s);
-  launch_enc_len(codes, p.N, p.C, p.nch, b.enc, b.lbits, b.chw, b.ctl,
-                 ctx->num_sms, s);
-  launch_scan(b.chw, b.woff, p.nch, &b.ctl->total_words, b.ctl, s);
-  launch_layout(b.ctl, off_table, out_cap, s);
+  launch_layout(b.ctl, off_table, ~0ull, s);
   pf.end(s);
   uint8_t* out = static_cast<uint8_t*>(d_out);
   pf.begin(HPEZ_PH_PACK, s);
-  launch_pack(codes, p.N, p.C, p.nch, b.enc, b.lbits, b.chw, b.woff, out,
-              b.ctl, ctx->num_sms, s);
+  launch_encode(codes, p.N, p.C, p.nch, b.enc, b.lbits, b.flags, out, b.ctl, out_cap,
+                ctx->num_sms, s);
   pf.end(s);
   pf.begin(HPEZ_PH_OUTLIERS, s);
   launch_outliers(true, codes, p.N, p.C, p.nch, b.zc, b.zoff, d_in, nullptr,

@@ -808,6 +808,7 @@ int upload(const Request& r) {
 // =====================================================================
 struct hpez_batch {
   hpez_ctx* ctx = nullptr;
+  int device = 0;  // the context's device, kept for destroy
   int n = 0;
   int decomp = 0;
   char* ws = nullptr;             // request workspaces + results
@@ -857,6 +858,7 @@ int batch_create(hpez_ctx* ctx, int n, int decomp, const void* descs,
   total += al256(sizeof(int) * n);
   hpez_batch* b = new hpez_batch();
   b->ctx = ctx;
+  b->device = ctx->device;
   b->n = n;
   b->decomp = decomp;
   if (cudaMalloc(&b->ws, total) != cudaSuccess) {
@@ -988,7 +990,7 @@ int hpez_batch_launch_count(hpez_batch* b, uint64_t* launches, uint64_t* ticks) 
 
 int hpez_batch_destroy(hpez_batch* b) {
   if (!b) return HPEZ_OK;
-  cudaSetDevice(b->ctx->device);
+  cudaSetDevice(b->device);
   cudaDeviceSynchronize();
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
@@ -1308,6 +1310,7 @@ constexpr int kRing = 8;
 
 struct hpez_server {
   hpez_ctx* ctx = nullptr;
+  int device = 0;  // the context's device, kept for destroy
   cudaStream_t s = nullptr;      // kernels (the caller's stream)
   cudaStream_t s_in = nullptr;   // host -> device copies
   cudaStream_t s_out = nullptr;  // device -> host copies
@@ -1399,6 +1402,7 @@ int hpez_server_create(hpez_ctx* ctx, uint64_t budget_bytes, int max_slots,
   cudaSetDevice(ctx->device);
   hpez_server* S = new hpez_server();
   S->ctx = ctx;
+  S->device = ctx->device;
   S->s = static_cast<cudaStream_t>(stream);
   S->budget = budget_bytes;
   S->max_slots = max_slots;
@@ -1666,7 +1670,7 @@ int hpez_server_stats(hpez_server* S, int* active, int* queued,
 
 int hpez_server_destroy(hpez_server* S) {
   if (!S) return HPEZ_OK;
-  cudaSetDevice(S->ctx->device);
+  cudaSetDevice(S->device);
   cudaDeviceSynchronize();
   for (SrvReq* q : S->queue) delete q;
   for (SrvReq* q : S->active) {

@@ -118,6 +118,13 @@ void launch_pack(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,
                  uint8_t* out, const Ctl* ctl, int num_sms, cudaStream_t s);
 void launch_chunk_words(const uint8_t* lanebits_bytes, uint32_t nch,
                         uint32_t* chw, int num_sms, cudaStream_t s);
+// lane bit counts, chunk offsets (decoupled look-back) and packing in one
+// kernel; flags: nch + 1 words of scratch; the stream layout's offsets
+// must be set, its capacity check happens here
+void launch_encode(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,
+                   const unsigned long long* enc, uint16_t* lanebits,
+                   unsigned long long* flags, uint8_t* out, Ctl* ctl,
+                   unsigned long long cap, int num_sms, cudaStream_t s);
 void launch_outliers(bool gather, const uint16_t* codes, uint32_t N,
                      uint32_t C, uint32_t nch, const uint32_t* zc,
                      const unsigned long long* zoff, const float* src,

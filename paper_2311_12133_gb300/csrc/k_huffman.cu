@@ -561,24 +561,14 @@ struct BitWriter {
   }
 };
 
-__device__ __forceinline__ void pack_body(
-    const uint16_t* __restrict__ codes, uint32_t N, uint32_t C, uint32_t nch,
-    const unsigned long long* __restrict__ enc,
-    const uint16_t* __restrict__ lanebits, const uint32_t* __restrict__ chw,
-    const unsigned long long* __restrict__ woff, uint8_t* out,
-    const Ctl* __restrict__ ctl, unsigned bid, unsigned nblk) {
-  if (ctl->status || ctl->is_const) return;
-  const int lane = threadIdx.x & 31;
-  const uint32_t warp = (bid * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (nblk * blockDim.x) >> 5;
-  uint32_t* bits = reinterpret_cast<uint32_t*>(out + ctl->off_bits);
-  for (uint32_t c = warp; c < nch; c += nwarps) {
-    const uint32_t beg = c * C, nc = min(C, N - beg);
-    uint32_t* words = bits + woff[c];
-    const uint32_t nw = chw[c];
+// one chunk's packing by its warp: the chunk's nw words at `words`, lane
+// `lane` holding mybits bits of the chunk's codes beg + lane + 32 k
+__device__ __forceinline__ void pack_chunk(const uint16_t* __restrict__ codes, uint32_t beg,
+                                           uint32_t nc, const unsigned long long* __restrict__ enc,
+                                           uint32_t mybits, uint32_t* words, uint32_t nw,
+                                           int lane) {
     for (uint32_t i = lane; i < nw; i += 32) words[i] = 0u;
     __syncwarp();
-    const uint32_t mybits = lanebits[(size_t)c * 32 + lane];
     uint32_t off = mybits;
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, off, o);
@@ -599,12 +589,134 @@ __device__ __forceinline__ void pack_body(
       unsigned long long e[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) e[k] = __ldg(enc + cd[k]);
+      // two consecutive codes of the lane whose lengths add up to at most
+      // 32 bits go out as one word fragment (the same bits, fewer steps)
 #pragma unroll
-      for (int k = 0; k < 8; ++k) bw.put_code(e[k]);
+      for (int k = 0; k < 8; k += 2) {
+        const int l0 = (int)(e[k] >> 56), l1 = (int)(e[k + 1] >> 56);
+        if (l0 + l1 <= 32) {
+          const unsigned long long v =
+              ((e[k] & ((1ull << 56) - 1)) << l1) | (e[k + 1] & ((1ull << 56) - 1));
+          bw.put((uint32_t)v, l0 + l1);
+        } else {
+          bw.put_code(e[k]);
+          bw.put_code(e[k + 1]);
+        }
+      }
     }
     for (; j < nc; j += 32) bw.put_code(enc[codes[beg + j]]);
     bw.flush();
     __syncwarp();
+}
+
+__device__ __forceinline__ void pack_body(
+    const uint16_t* __restrict__ codes, uint32_t N, uint32_t C, uint32_t nch,
+    const unsigned long long* __restrict__ enc,
+    const uint16_t* __restrict__ lanebits, const uint32_t* __restrict__ chw,
+    const unsigned long long* __restrict__ woff, uint8_t* out,
+    const Ctl* __restrict__ ctl, unsigned bid, unsigned nblk) {
+  if (ctl->status || ctl->is_const) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp = (bid * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (nblk * blockDim.x) >> 5;
+  uint32_t* bits = reinterpret_cast<uint32_t*>(out + ctl->off_bits);
+  for (uint32_t c = warp; c < nch; c += nwarps) {
+    const uint32_t beg = c * C, nc = min(C, N - beg);
+    pack_chunk(codes, beg, nc, enc, lanebits[(size_t)c * 32 + lane], bits + woff[c], chw[c],
+               lane);
+  }
+}
+
+// ---------------------------------------------------------------------
+// encode in one pass (single field): a warp takes the chunks in order from
+// a counter; per chunk it counts its lanes' bits, publishes the chunk's
+// word count, finds the chunk's word offset by a decoupled look-back over
+// the flags of the chunks before it (a flag holds a count: status 1 = this
+// chunk's words, 2 = the words of every chunk up to it), publishes that
+// inclusive count and packs the chunk.  Chunks are taken in order, so every
+// chunk a look-back waits for is held by a running warp.  The waits are
+// bounded: on expiry the call fails with a timeout.
+// ---------------------------------------------------------------------
+constexpr unsigned long long kEncWaitPolls = 1ull << 22;
+
+__device__ __forceinline__ unsigned long long load_flag(const unsigned long long* f) {
+  return *reinterpret_cast<const volatile unsigned long long*>(f);
+}
+
+__global__ void __launch_bounds__(256)
+    k_encode(const uint16_t* __restrict__ codes, uint32_t N, uint32_t C, uint32_t nch,
+             const unsigned long long* __restrict__ enc, uint16_t* __restrict__ lanebits,
+             unsigned long long* flags, uint32_t* counter, uint8_t* out, Ctl* ctl,
+             unsigned long long cap) {
+  if (ctl->status || ctl->is_const) return;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long off_bits = ctl->off_bits;
+  uint32_t* bits = reinterpret_cast<uint32_t*>(out + off_bits);
+  for (;;) {
+    uint32_t c = 0;
+    if (lane == 0) c = atomicAdd(counter, 1u);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c >= nch) return;
+    const uint32_t beg = c * C, nc = min(C, N - beg);
+    // the lane's bits
+    uint32_t mybits = 0;
+    {
+      uint32_t j = lane;
+      for (; j + 7 * 32 < nc; j += 8 * 32) {
+        unsigned cd[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) cd[k] = codes[beg + j + 32 * k];
+        unsigned long long e[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) e[k] = __ldg(enc + cd[k]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) mybits += (uint32_t)(e[k] >> 56);
+      }
+      for (; j < nc; j += 32) mybits += (uint32_t)(enc[codes[beg + j]] >> 56);
+    }
+    lanebits[(size_t)c * 32 + lane] = (uint16_t)mybits;
+    uint32_t tot = mybits;
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    const unsigned long long nw = (tot + 31) >> 5;
+    // publish the aggregate, then look back
+    if (lane == 0) atomicExch(flags + c, (nw << 2) | 1ull);
+    unsigned long long prefix = 0;
+    bool timed_out = false;
+    for (long long j = (long long)c - 1; j >= 0;) {
+      const long long jj = j - lane;
+      unsigned long long f = jj >= 0 ? load_flag(flags + jj) : 2ull;  // before chunk 0: 0 words
+      unsigned long long polls = 0;
+      while (__any_sync(0xffffffffu, (f & 3ull) == 0ull)) {
+        if (++polls > kEncWaitPolls) {
+          timed_out = true;
+          break;
+        }
+        __nanosleep(64);
+        if ((f & 3ull) == 0ull) f = load_flag(flags + jj);
+      }
+      if (timed_out) break;
+      const unsigned inc = __ballot_sync(0xffffffffu, (f & 3ull) == 2ull);
+      // lanes up to the first inclusive count (or all 32) add up
+      const int upto = inc ? __ffs(inc) - 1 : 31;
+      unsigned long long v = lane <= upto ? (f >> 2) : 0ull;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      prefix += v;
+      if (inc) break;
+      j -= 32;
+    }
+    if (timed_out) {
+      if (lane == 0) atomicCAS(&ctl->status, 0, ST_TIMEOUT);
+      return;
+    }
+    if (lane == 0) atomicExch(flags + c, ((prefix + nw) << 2) | 2ull);
+    if (c + 1 == nch && lane == 0) {
+      ctl->total_words = prefix + nw;
+      ctl->total_size = off_bits + 4ull * (prefix + nw);
+      if (ctl->total_size > cap) atomicCAS(&ctl->status, 0, ST_OUT_TOO_SMALL);
+    }
+    // nothing written past the output's capacity
+    if (off_bits + 4ull * (prefix + nw) > cap) continue;
+    pack_chunk(codes, beg, nc, enc, mybits, bits + prefix, (uint32_t)nw, lane);
   }
 }
 
@@ -1062,6 +1174,17 @@ void launch_pack(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,
                  uint8_t* out, const Ctl* ctl, int num_sms, cudaStream_t s) {
   k_pack<<<warps_grid(nch, num_sms), 256, 0, s>>>(codes, N, C, nch, enc,
                                                   lanebits, chw, woff, out, ctl);
+}
+
+void launch_encode(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,
+                   const unsigned long long* enc, uint16_t* lanebits,
+                   unsigned long long* flags, uint8_t* out, Ctl* ctl,
+                   unsigned long long cap, int num_sms, cudaStream_t s) {
+  // flags[0, nch) and the chunk counter (the word after them) start at 0
+  cudaMemsetAsync(flags, 0, sizeof(unsigned long long) * ((size_t)nch + 1), s);
+  k_encode<<<warps_grid(nch, num_sms), 256, 0, s>>>(
+      codes, N, C, nch, enc, lanebits, flags, reinterpret_cast<uint32_t*>(flags + nch), out,
+      ctl, cap);
 }
 
 void launch_chunk_words(const uint8_t* lanebits_bytes, uint32_t nch,

@@ -35,6 +35,9 @@
 // Order 1 on rows of 16-byte multiples takes k_lorenzo_tma instead: the
 // input of a warp's 32 columns arrives as one TMA tensor box per segment.
 #include <cuda.h>
+
+#include <cstdio>
+#include <cstdlib>
 #include "hpez.h"
 #include "hpez_internal.cuh"
 #include "hpez_launch.h"
@@ -785,10 +788,14 @@ int launch_lor_k(const LorGeom& G, size_t smem, unsigned threads, int num_sms,
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)threads, smem) !=
-          cudaSuccess ||
-      per_sm < 1)
+  const cudaError_t oe =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)threads, smem);
+  if (oe != cudaSuccess || per_sm < 1) {
+    if (std::getenv("HPEZ_DEBUG_CUDA"))
+      std::fprintf(stderr, "hpez: Lorenzo occupancy %s, %d CTAs per SM (%u threads, %zu B)\n",
+                   cudaGetErrorName(oe), per_sm, threads, smem);
     return HPEZ_ERR_CUDA;
+  }
   // persistent CTAs, the blocks dealt round robin; the grid shrunk to the
   // fewest CTAs that keep the most loaded one's block count
   uint64_t cap = (uint64_t)per_sm * (uint64_t)(num_sms > 0 ? num_sms : 1);

@@ -710,11 +710,16 @@ class Context:
     """Owns one hpez_ctx on a CUDA device."""
 
     def __init__(self, device: int = 0):
+        import weakref
         self.device = device
         self.handle = hpez_create(device)
+        # batches and servers planned on this context: destroyed before it
+        self._children = weakref.WeakSet()
 
     def close(self):
         if self.handle:
+            for c in list(self._children):
+                c.close()
             hpez_destroy(self.handle)
             self.handle = 0
 
@@ -782,6 +787,8 @@ class Batch:
     def __init__(self, ctx: Context, fields=None, streams=None):
         import torch
         self.ctx = ctx
+        self.handle = 0
+        ctx._children.add(self)
         self._keep = []
         h = ctypes.c_void_p(0)
         if fields is not None:
@@ -871,6 +878,8 @@ class Server:
                  stream=None):
         import torch
         self.ctx = ctx
+        self.handle = 0
+        ctx._children.add(self)
         self.stream = stream if stream is not None else torch.cuda.Stream()
         h = ctypes.c_void_p(0)
         _check(_load().hpez_server_create(ctx.handle, int(budget_bytes), max_slots,

@@ -261,6 +261,28 @@ def test_batch_errors(gpu):
     d.run()
     _, st = d.results()
     assert st[0] == 0 and st[2] == 0 and st[1] == -4
+    b.close()
+    d.close()
+
+
+def test_context_closes_its_batches_first(gpu):
+    """Closing a context destroys the batches and servers made on it first,
+    and leaves no CUDA error behind for the next call on another context."""
+    import torch
+    from paper_2311_12133_gb300 import hpez
+    c2 = hpez.Context(0)
+    x = torch.rand((30, 40, 50), device="cuda")
+    b = hpez.Batch(c2, fields=[(x, 1e-3, 1, None)])
+    b.run()
+    srv = hpez.Server(c2, 1 << 26, 2)
+    c2.close()
+    assert b.handle == 0 and srv.handle == 0
+    del b, srv
+    import gc
+    gc.collect()
+    buf, size = gpu.compress(x, 1e-3)
+    y = gpu.decompress(buf, size)
+    assert (y - x).abs().max().item() <= 1e-3 * (x.max() - x.min()).item()
 
 
 def _served_mix(gpu, oracle, mix, budget, slots, seed):
