@@ -582,10 +582,20 @@ __device__ __forceinline__ void pack_chunk(const uint16_t* __restrict__ codes, u
     bw.acc = 0;
     bw.shared_first = bw.nacc != 0;
     uint32_t j = lane;
+    // the codes of the next batch are loaded while this one is packed
+    unsigned nx[8];
+    if (j + 7 * 32 < nc) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) nx[k] = codes[beg + j + 32 * k];
+    }
     for (; j + 7 * 32 < nc; j += 8 * 32) {
       unsigned cd[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) cd[k] = codes[beg + j + 32 * k];
+      for (int k = 0; k < 8; ++k) cd[k] = nx[k];
+      if (j + 15 * 32 < nc) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) nx[k] = codes[beg + j + 256 + 32 * k];
+      }
       unsigned long long e[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) e[k] = __ldg(enc + cd[k]);
@@ -658,19 +668,16 @@ __global__ void __launch_bounds__(256)
     c = __shfl_sync(0xffffffffu, c, 0);
     if (c >= nch) return;
     const uint32_t beg = c * C, nc = min(C, N - beg);
-    // the lane's bits
+    // the lane's bits (16 code loads in flight: the pass waits on memory)
     uint32_t mybits = 0;
     {
       uint32_t j = lane;
-      for (; j + 7 * 32 < nc; j += 8 * 32) {
-        unsigned cd[8];
+      for (; j + 15 * 32 < nc; j += 16 * 32) {
+        unsigned cd[16];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) cd[k] = codes[beg + j + 32 * k];
-        unsigned long long e[8];
+        for (int k = 0; k < 16; ++k) cd[k] = codes[beg + j + 32 * k];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) e[k] = __ldg(enc + cd[k]);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) mybits += (uint32_t)(e[k] >> 56);
+        for (int k = 0; k < 16; ++k) mybits += (uint32_t)(__ldg(enc + cd[k]) >> 56);
       }
       for (; j < nc; j += 32) mybits += (uint32_t)(enc[codes[beg + j]] >> 56);
     }
