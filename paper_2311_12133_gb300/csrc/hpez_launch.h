@@ -256,7 +256,7 @@ void launch_tune_advance(const float* x, const TuneGeom& g0, const TuneGeom& g1,
 void launch_tune_lorenzo(const float* x, const TuneGeom& g, int nblk,
                          const Ctl* ctl, uint32_t* hists,
                          unsigned long long* nout, cudaStream_t s);
-void launch_tune_blockwise(const float* x, const TuneGeom& g, int bs, int Q,
+int launch_tune_blockwise(const float* x, const TuneGeom& g, int bs, int Q,
                            int frozen_slot, const uint32_t nb[3],
                            uint32_t nblocks, const TuneCfg* base,
                            unsigned allow, unsigned long long* scores,

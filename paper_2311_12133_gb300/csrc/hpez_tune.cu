@@ -712,10 +712,9 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
     cudaMemcpyAsync(k.b.cfgs, &host, sizeof(TuneCfg), cudaMemcpyHostToDevice, s);
     launch_tune_params(k.b.cfgs, 1, kMaxLevels, k.b.ctl, s);
     const unsigned allow = (tp.allow_natural ? 1u : 0u) | (tp.allow_same_level ? 2u : 0u);
-    launch_tune_blockwise(d_in, g, bsz, Q,
-                          out.frozen_dim < 0 ? -1 : out.frozen_dim + p.off, nb,
-                          (uint32_t)nbm, k.b.cfgs, allow, k.b.bscore, k.b.bmap, s);
-    nl += 5;
+    nl += 1 + launch_tune_blockwise(d_in, g, bsz, Q,
+                                    out.frozen_dim < 0 ? -1 : out.frozen_dim + p.off, nb,
+                                    (uint32_t)nbm, k.b.cfgs, allow, k.b.bscore, k.b.bmap, s);
     prof.end(s);
     cudaMemcpyAsync(h_blockmap, k.b.bmap, nbm, cudaMemcpyDeviceToHost, s);
     if ((rc = sync_check(k))) return rc;

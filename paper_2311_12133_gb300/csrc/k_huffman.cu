@@ -14,15 +14,18 @@
 
 namespace hpez {
 
-constexpr int kHistWin = 2048;              // bins per warp-private window
+constexpr int kHistWin = 1024;              // bins per warp-private window
 constexpr int kHistLo = kRadius - kHistWin / 2;
 constexpr int kHistWarps = 8;
 
 // ---------------------------------------------------------------------
 // histogram of the 65536 code symbols + per-chunk count of code 0.  Each
 // warp owns a private window of bins in shared memory (contention only
-// between lanes of one warp); the three central bins are counted in
-// registers; bins outside the window go straight to global atomics.
+// between lanes of one warp) and counts the zero-error code in a register;
+// a code outside the window (rare: large errors and outliers, code 0
+// among them) goes to a global atomic on a path taken only when one of a
+// lane's 8 codes needs it, so the common code costs a window test and one
+// shared atomic.
 // ---------------------------------------------------------------------
 __device__ __forceinline__ void hist_body(const uint16_t* __restrict__ codes,
                                           uint32_t N, uint32_t C, uint32_t nch,
@@ -38,63 +41,66 @@ __device__ __forceinline__ void hist_body(const uint16_t* __restrict__ codes,
   uint32_t* sh = shw + (threadIdx.x >> 5) * kHistWin;
   const uint32_t warp = (bid * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (nblk * blockDim.x) >> 5;
-  uint32_t cm1 = 0, c0 = 0, cp1 = 0;  // the three central bins in registers
-  auto add = [&](unsigned v) {
-    cm1 += (v == kRadius - 1);
-    c0 += (v == kRadius);
-    cp1 += (v == kRadius + 1);
-    if (v < kRadius - 1 || v > kRadius + 1) {
-      const int o = (int)v - kHistLo;
-      if (o >= 0 && o < kHistWin)
-        atomicAdd(&sh[o], 1u);
-      else
-        atomicAdd(&hist[v], 1u);
+  uint32_t c0 = 0;  // the zero-error code
+  // one code into the window or the centre register; false: outside
+  auto add_win = [&](unsigned v) -> bool {
+    const unsigned o = v - (unsigned)kHistLo;
+    c0 += (v == (unsigned)kRadius);
+    if (o < (unsigned)kHistWin) {
+      if (v != (unsigned)kRadius) atomicAdd(&sh[o], 1u);
+      return true;
+    }
+    return false;
+  };
+  auto add_far = [&](unsigned v, uint32_t& zeros) {
+    if (v - (unsigned)kHistLo >= (unsigned)kHistWin) {
+      atomicAdd(&hist[v], 1u);
+      zeros += (v == 0u);
     }
   };
   for (uint32_t c = warp; c < nch; c += nwarps) {
     const uint32_t beg = c * C;
     const uint32_t end = min(beg + C, N);
     uint32_t zeros = 0;
-    if (end - beg == C) {
+    if (end - beg == C && (C & 7u) == 0u) {
       const uint4* p = reinterpret_cast<const uint4*>(codes + beg);
-      for (uint32_t i = lane; i < C / 8; i += 64) {
-        uint4 v[2];
-        v[0] = __ldcs(p + i);
-        v[1] = i + 32 < C / 8 ? __ldcs(p + i + 32) : make_uint4(kRadius | (kRadius << 16), kRadius | (kRadius << 16), kRadius | (kRadius << 16), kRadius | (kRadius << 16));
-        const bool two = i + 32 < C / 8;
+      const uint32_t nq = C / 8;
+      for (uint32_t i = lane; i < nq; i += 128) {
+        uint4 v[4];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (h == 1 && !two) break;
+        for (int h = 0; h < 4; ++h)
+          if (i + 32u * h < nq) v[h] = __ldcs(p + i + 32u * h);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          if (i + 32u * h >= nq) break;
           const unsigned w[4] = {v[h].x, v[h].y, v[h].z, v[h].w};
+          bool in = true;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            const unsigned lo = w[k] & 0xFFFFu, hi = w[k] >> 16;
-            add(lo);
-            add(hi);
-            zeros += (lo == 0) + (hi == 0);
+            in &= add_win(w[k] & 0xFFFFu);
+            in &= add_win(w[k] >> 16);
+          }
+          if (!in) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              add_far(w[k] & 0xFFFFu, zeros);
+              add_far(w[k] >> 16, zeros);
+            }
           }
         }
       }
     } else {
       for (uint32_t i = beg + lane; i < end; i += 32) {
         const unsigned v = codes[i];
-        add(v);
-        zeros += (v == 0);
+        if (!add_win(v)) add_far(v, zeros);
       }
     }
     for (int o = 16; o > 0; o >>= 1) zeros += __shfl_xor_sync(0xffffffffu, zeros, o);
     if (lane == 0) zc[c] = zeros;
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    cm1 += __shfl_xor_sync(0xffffffffu, cm1, o);
-    c0 += __shfl_xor_sync(0xffffffffu, c0, o);
-    cp1 += __shfl_xor_sync(0xffffffffu, cp1, o);
-  }
-  if (lane == 0) {
-    sh[kRadius - 1 - kHistLo] += cm1;
-    sh[kRadius - kHistLo] += c0;
-    sh[kRadius + 1 - kHistLo] += cp1;
-  }
+  for (int o = 16; o > 0; o >>= 1) c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+  __syncwarp();
+  if (lane == 0) sh[kRadius - kHistLo] += c0;
   __syncthreads();
   for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) {
     uint32_t t = 0;

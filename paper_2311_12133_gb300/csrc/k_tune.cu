@@ -23,7 +23,7 @@ constexpr int kTestThreads = 512;
 // block-map codes of the block-wise candidates, in test order: linear,
 // not-a-knot, not-a-knot + same-level, natural, natural + same-level
 __constant__ uint8_t kBlockCodes[5] = {0, 1, 5, 2, 6};
-constexpr int kBlockThreads = 32;  // one warp per (block, candidate)
+constexpr int kBlockThreads = 64;  // two warps per (block, group of candidates)
 constexpr size_t kTuneSmemMax = 200 * 1024;
 
 // floor(min(|d| * (1/e_l), 2^24 - 1) * 256) in binary32: the per-point
@@ -548,17 +548,18 @@ __device__ void sweep_level_k(float* R, const Sub& f, const int interp[3],
 }
 
 // The same sweep for small sub-fields (the block-wise tests, one warp
-// each): the boxes of a pass in one enumeration, each same-level half
-// skipping the other half's points -- fewer partial iterations than a loop
-// per box when the boxes hold a few points each.  The points of one pass
-// (or same-level half) of a level, specialized on the interpolator and the
-// paradigm, which are uniform within a level.
-template <int KIND, bool MD, int PS, bool kHist>
-__device__ void sweep_pass_skip(float* R, const Sub& f, const Box* bx, int nb,
-                           int tot, int half, bool same, int sh,
-                           const int line[3], const TuneCfg& c, int l,
-                           bool score_on, unsigned long long& score,
-                           const HistSink& hist, unsigned long long& nout) {
+// each), for NK interpolators K0, K1, K2 at once: their passes have the
+// same points (one paradigm and order per level, from the global theta;
+// same-level halves for all of them or none), so the enumeration, the
+// input value and the index are shared and only the prediction, the
+// quantization and the score are per interpolator, each on its own
+// reconstruction (R + k * vol).  The boxes of a pass are one enumeration;
+// a same-level half skips the other half's points -- fewer partial
+// iterations than a loop per box when the boxes hold a few points each.
+template <int NK, int K0, int K1, int K2, bool SAME, bool MD, int PS>
+__device__ void sweep_pass_multi(float* R, int vol, const Sub& f, const Box* bx, int nb,
+                                 int tot, int half, int sh, const int line[3],
+                                 const TuneCfg& c, int l, unsigned long long (&score)[NK]) {
   const int s = 1 << sh;
   const float el = c.el[l - 1], inv2 = c.inv2[l - 1], twoe = c.twoe[l - 1];
   const float inv_el = c.inv_el[l - 1];
@@ -574,7 +575,7 @@ __device__ void sweep_pass_skip(float* R, const Sub& f, const Box* bx, int nb,
     cc[0] = B.a[0] + B.b[0] * (int)r0;
     const unsigned S = B.S;
     bool in_b = false;
-    if (KIND != LINEAR && same) {
+    if (SAME) {
       unsigned par = 0;
 #pragma unroll
       for (int d = 0; d < 3; ++d)
@@ -584,39 +585,41 @@ __device__ void sweep_pass_skip(float* R, const Sub& f, const Box* bx, int nb,
     }
     const int i = cc[0] * f.st[0] + cc[1] * f.st[1] + cc[2];
     const float xv = xval(f, cc);
-    float p;
-    if (!MD) {
-      p = predict_smem(R, i, s * f.st[PS], cc[PS] >> sh, line[PS], KIND, in_b);
-    } else {
-      float acc = 0.0f;
-      bool first = true;
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        if (!(S & (1u << d))) continue;
-        const float pd = predict_smem(R, i, s * f.st[d], cc[d] >> sh, line[d],
-                                      KIND, in_b);
-        const float tw = __fmul_rn(c.mdw[S][d], pd);
-        acc = first ? tw : __fadd_rn(acc, tw);
-        first = false;
+    for (int k = 0; k < NK; ++k) {
+      const int kind = k == 0 ? K0 : (k == 1 ? K1 : K2);
+      float* Rk = R + k * vol;
+      float p;
+      if (!MD) {
+        p = predict_smem(Rk, i, s * f.st[PS], cc[PS] >> sh, line[PS], kind, in_b);
+      } else {
+        float acc = 0.0f;
+        bool first = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          if (!(S & (1u << d))) continue;
+          const float pd = predict_smem(Rk, i, s * f.st[d], cc[d] >> sh, line[d], kind, in_b);
+          const float tw = __fmul_rn(c.mdw[S][d], pd);
+          acc = first ? tw : __fadd_rn(acc, tw);
+          first = false;
+        }
+        p = acc;
       }
-      p = acc;
+      float rv;
+      quantize_t(xv, p, el, inv2, twoe, rv);
+      Rk[i] = rv;
+      score[k] += err_fixed(__fsub_rn(xv, p), inv_el);
     }
-    float rv;
-    const unsigned code = quantize_t(xv, p, el, inv2, twoe, rv);
-    R[i] = rv;
-    if (score_on) score += err_fixed(__fsub_rn(xv, p), inv_el);
-    if (kHist) hist.add(code);
-    if (code == 0u) ++nout;
   }
 }
 
-// KIND < 0: the level's interpolator read from the config; KIND >= 0:
-// fixed (the config's value is that kind)
-template <int KIND, bool kHist>
-__device__ void sweep_level_skip(float* R, const Sub& f, const int interp[3],
-                              int k, int l, const TuneCfg& c, bool score_on,
-                              unsigned long long& score, const HistSink& hist,
-                              unsigned long long& nout, Box* bx) {
+// One level of the block-wise sweep for the NK interpolators of
+// sweep_pass_multi: passes (and same-level halves) in the compressor's
+// order, a barrier after each.
+template <int NK, int K0, int K1, int K2, bool SAME>
+__device__ void sweep_level_multi(float* R, int vol, const Sub& f, const int interp[3],
+                                  int k, int l, const TuneCfg& c,
+                                  unsigned long long (&score)[NK], Box* bx) {
   const int sh = l - 1, s = 1 << sh;
   int line[3];
   unsigned imask = 0;
@@ -625,9 +628,7 @@ __device__ void sweep_level_skip(float* R, const Sub& f, const int interp[3],
     line[d] = (f.n[d] - 1) / s + 1;
     if (interp[d]) imask |= 1u << d;
   }
-  const int kind = c.kind[l - 1];
   const bool md = c.md[l - 1] != 0;
-  const bool same = c.same[l - 1] != 0 && kind != LINEAR;
   for (int pj = 0; pj < k; ++pj) {
     // the pass's boxes (at most 3) in shared memory, one thread each
     BoxDesc bd[3];
@@ -647,30 +648,18 @@ __device__ void sweep_level_skip(float* R, const Sub& f, const int interp[3],
     __syncthreads();
     int tot = 0;
     for (int q = 0; q < nb; ++q) tot += bx[q].total;
-    for (int half = 0; half < (same ? 2 : 1); ++half) {
-#define HPEZ_SWEEP(K, M, P)                                                   \
-  sweep_pass_skip<K, M, P, kHist>(R, f, bx, nb, tot, half, same, sh, line, c, l,   \
-                             score_on, score, hist, nout)
-#define HPEZ_SWEEP_1D(K)                                                      \
-  do {                                                                        \
-    const int ps = c.ord[l - 1][pj];                                          \
-    if (ps == 0) HPEZ_SWEEP(K, false, 0);                                     \
-    else if (ps == 1) HPEZ_SWEEP(K, false, 1);                                \
-    else HPEZ_SWEEP(K, false, 2);                                             \
-  } while (0)
-      if (KIND >= 0) {
-        if (md) HPEZ_SWEEP(KIND < 0 ? 0 : KIND, true, 0);
-        else HPEZ_SWEEP_1D(KIND < 0 ? 0 : KIND);
-      } else if (md) {
-        if (kind == LINEAR) HPEZ_SWEEP(LINEAR, true, 0);
-        else if (kind == CUBIC_NAK) HPEZ_SWEEP(CUBIC_NAK, true, 0);
-        else HPEZ_SWEEP(CUBIC_NAT, true, 0);
+    for (int half = 0; half < (SAME ? 2 : 1); ++half) {
+#define HPEZ_SWEEP(M, P)                                                      \
+  sweep_pass_multi<NK, K0, K1, K2, SAME, M, P>(R, vol, f, bx, nb, tot, half, sh, line, c, \
+                                               l, score)
+      if (md) {
+        HPEZ_SWEEP(true, 0);
       } else {
-        if (kind == LINEAR) HPEZ_SWEEP_1D(LINEAR);
-        else if (kind == CUBIC_NAK) HPEZ_SWEEP_1D(CUBIC_NAK);
-        else HPEZ_SWEEP_1D(CUBIC_NAT);
+        const int ps = c.ord[l - 1][pj];
+        if (ps == 0) HPEZ_SWEEP(false, 0);
+        else if (ps == 1) HPEZ_SWEEP(false, 1);
+        else HPEZ_SWEEP(false, 2);
       }
-#undef HPEZ_SWEEP_1D
 #undef HPEZ_SWEEP
       __syncthreads();
     }
@@ -962,26 +951,19 @@ struct BlockGeom {
   int bs, Q, frozen_slot;
 };
 
-// CTA (field block, candidate j): the summed level score of the centred
-// sub-block with candidate j at every level; ~0 for a candidate not allowed
-// one launch per interpolator kind: candidate j of the launch is
-// kBlockCodes[j0 + j]
-template <int KIND>
+// CTA (field block) of one launch: the summed level scores of the centred
+// sub-block with each of the launch's NK interpolators at every level,
+// written to the candidates' slots (kBlockCodes[j] for j in slots, 8 bits
+// each)
+template <int NK, int K0, int K1, int K2, bool SAME>
 __global__ void __launch_bounds__(kBlockThreads)
     k_tune_blockwise(const float* __restrict__ x, TuneGeom g, BlockGeom bg,
-                     const TuneCfg* __restrict__ base, unsigned allow, int j0,
+                     const TuneCfg* __restrict__ base, uint32_t slots,
                      unsigned long long* scores) {
   extern __shared__ float R[];
   __shared__ TuneCfg c;
   __shared__ unsigned long long red[32];
   __shared__ Box sbx[3];
-  const int jj = j0 + (int)blockIdx.y;
-  const uint8_t v = kBlockCodes[jj];
-  unsigned long long* out = scores + (size_t)blockIdx.x * 5 + jj;
-  if (((v & 3) == CUBIC_NAT && !(allow & 1u)) || ((v & 4) && !(allow & 2u))) {
-    if (threadIdx.x == 0) *out = ~0ull;
-    return;
-  }
   load_cfg(&c, base);
   unsigned b = blockIdx.x;
   Sub f;
@@ -1004,33 +986,58 @@ __global__ void __launch_bounds__(kBlockThreads)
   }
   f.x = x + off;
   set_strides(f);
+  const int vol = f.n[0] * f.n[1] * f.n[2];
   int As = 2;
   const int lim = qmin > 1 ? qmin - 1 : 1;
   while (As * 2 <= lim) As *= 2;
   int L = 0;
   while ((1 << L) < As) ++L;
-  if (threadIdx.x < kMaxLevels) {
-    c.kind[threadIdx.x] = v & 3;
-    c.same[threadIdx.x] = (v >> 2) & 1;
+  // the anchors, in every interpolator's copy
+  {
+    int m[3], st[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      st[d] = g.interp[d] ? As : 1;
+      m[d] = (f.n[d] + st[d] - 1) / st[d];
+    }
+    const int tot = m[0] * m[1] * m[2];
+    for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+      int cc[3];
+      cc[2] = (q % m[2]) * st[2];
+      const int r = q / m[2];
+      cc[1] = (r % m[1]) * st[1];
+      cc[0] = (r / m[1]) * st[0];
+      const int i = cc[0] * f.st[0] + cc[1] * f.st[1] + cc[2];
+      const float v = xval(f, cc);
+#pragma unroll
+      for (int k = 0; k < NK; ++k) R[k * vol + i] = v;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  init_anchors(R, f, g.interp, As);
-  unsigned long long sc = 0, no = 0;
-  const HistSink none{nullptr, nullptr};
+  unsigned long long sc[NK];
+#pragma unroll
+  for (int k = 0; k < NK; ++k) sc[k] = 0;
   for (int l = L; l >= 1; --l)
-    sweep_level_skip<KIND, false>(R, f, g.interp, g.k, l, c, true, sc, none, no, sbx);
-  sc = block_sum(sc, red);
-  if (threadIdx.x == 0) *out = sc;
+    sweep_level_multi<NK, K0, K1, K2, SAME>(R, vol, f, g.interp, g.k, l, c, sc, sbx);
+#pragma unroll
+  for (int k = 0; k < NK; ++k) {
+    const unsigned long long t = block_sum(sc[k], red);
+    if (threadIdx.x == 0)
+      scores[(size_t)blockIdx.x * 5 + ((slots >> (8 * k)) & 0xFFu)] = t;
+    __syncthreads();
+  }
 }
 
 // the block map: per block the first candidate with the smallest score
+// among the allowed ones (natural: slots 3, 4; same-level: slots 2, 4)
 __global__ void k_tune_block_argmin(const unsigned long long* __restrict__ scores,
-                                    uint32_t nblocks, uint8_t* bmap) {
+                                    uint32_t nblocks, unsigned allow, uint8_t* bmap) {
   const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nblocks) return;
   unsigned long long best = scores[(size_t)b * 5];
   int bj = 0;
   for (int j = 1; j < 5; ++j) {
+    if ((j >= 3 && !(allow & 1u)) || ((j == 2 || j == 4) && !(allow & 2u))) continue;
     const unsigned long long v = scores[(size_t)b * 5 + j];
     if (v < best) {
       best = v;
@@ -1055,15 +1062,18 @@ void set_smem_attr() {
   cudaFuncSetAttribute(k_tune_advance,
                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)kTuneSmemMax);
-  cudaFuncSetAttribute(k_tune_blockwise<LINEAR>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)kTuneSmemMax);
-  cudaFuncSetAttribute(k_tune_blockwise<CUBIC_NAK>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)kTuneSmemMax);
-  cudaFuncSetAttribute(k_tune_blockwise<CUBIC_NAT>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)kTuneSmemMax);
+#define HPEZ_BW_ATTR(...)                                                     \
+  cudaFuncSetAttribute(k_tune_blockwise<__VA_ARGS__>,                         \
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTuneSmemMax)
+  HPEZ_BW_ATTR(3, LINEAR, CUBIC_NAK, CUBIC_NAT, false);
+  HPEZ_BW_ATTR(2, LINEAR, CUBIC_NAK, 0, false);
+  HPEZ_BW_ATTR(2, CUBIC_NAK, CUBIC_NAT, 0, true);
+  HPEZ_BW_ATTR(1, LINEAR, 0, 0, false);
+  HPEZ_BW_ATTR(1, CUBIC_NAK, 0, 0, false);
+  HPEZ_BW_ATTR(1, CUBIC_NAT, 0, 0, false);
+  HPEZ_BW_ATTR(1, CUBIC_NAK, 0, 0, true);
+  HPEZ_BW_ATTR(1, CUBIC_NAT, 0, 0, true);
+#undef HPEZ_BW_ATTR
   done = true;
 }
 
@@ -1172,7 +1182,7 @@ void launch_tune_lorenzo(const float* x, const TuneGeom& g, int nblk,
       x, g, ctl, hists, nout);
 }
 
-void launch_tune_blockwise(const float* x, const TuneGeom& g, int bs, int Q,
+int launch_tune_blockwise(const float* x, const TuneGeom& g, int bs, int Q,
                            int frozen_slot, const uint32_t nb[3],
                            uint32_t nblocks, const TuneCfg* base,
                            unsigned allow, unsigned long long* scores,
@@ -1187,14 +1197,42 @@ void launch_tune_blockwise(const float* x, const TuneGeom& g, int bs, int Q,
   bg.bs = bs;
   bg.Q = Q;
   bg.frozen_slot = frozen_slot;
-  // codes 0 | 1, 5 | 2, 6: linear, not-a-knot, natural
-  k_tune_blockwise<LINEAR><<<dim3(nblocks, 1), kBlockThreads, vol * sizeof(float), s>>>(
-      x, g, bg, base, allow, 0, scores);
-  k_tune_blockwise<CUBIC_NAK><<<dim3(nblocks, 2), kBlockThreads, vol * sizeof(float), s>>>(
-      x, g, bg, base, allow, 1, scores);
-  k_tune_blockwise<CUBIC_NAT><<<dim3(nblocks, 2), kBlockThreads, vol * sizeof(float), s>>>(
-      x, g, bg, base, allow, 3, scores);
-  k_tune_block_argmin<<<(nblocks + 255) / 256, 256, 0, s>>>(scores, nblocks, bmap);
+  // slots j (kBlockCodes[j]): 0 linear, 1 not-a-knot, 2 not-a-knot with
+  // same-level halves, 3 natural, 4 natural with same-level halves.  A
+  // launch scores the interpolators whose passes have the same points, as
+  // many as fit next to each other in shared memory.
+  const size_t bytes = vol * sizeof(float);
+  const int per = (int)(kTuneSmemMax / bytes);  // >= 1 (checked by the caller)
+  const bool nat = (allow & 1u) != 0, sl = (allow & 2u) != 0;
+  const dim3 grid(nblocks);
+  int n = 1;
+#define HPEZ_BW(NK, K0, K1, K2, SAME, SLOTS)                                  \
+  do {                                                                        \
+    ++n;                                                                      \
+    k_tune_blockwise<NK, K0, K1, K2, SAME><<<grid, kBlockThreads, NK * bytes, s>>>( \
+        x, g, bg, base, SLOTS, scores);                                       \
+  } while (0)
+  if (nat && per >= 3) {
+    HPEZ_BW(3, LINEAR, CUBIC_NAK, CUBIC_NAT, false, 0u | (1u << 8) | (3u << 16));
+  } else if (per >= 2) {
+    HPEZ_BW(2, LINEAR, CUBIC_NAK, 0, false, 0u | (1u << 8));
+    if (nat) HPEZ_BW(1, CUBIC_NAT, 0, 0, false, 3u);
+  } else {
+    HPEZ_BW(1, LINEAR, 0, 0, false, 0u);
+    HPEZ_BW(1, CUBIC_NAK, 0, 0, false, 1u);
+    if (nat) HPEZ_BW(1, CUBIC_NAT, 0, 0, false, 3u);
+  }
+  if (sl) {
+    if (nat && per >= 2) {
+      HPEZ_BW(2, CUBIC_NAK, CUBIC_NAT, 0, true, 2u | (4u << 8));
+    } else {
+      HPEZ_BW(1, CUBIC_NAK, 0, 0, true, 2u);
+      if (nat) HPEZ_BW(1, CUBIC_NAT, 0, 0, true, 4u);
+    }
+  }
+#undef HPEZ_BW
+  k_tune_block_argmin<<<(nblocks + 255) / 256, 256, 0, s>>>(scores, nblocks, allow, bmap);
+  return n;
 }
 
 

@@ -96,6 +96,11 @@ def test_tune_matches_oracle(gpu, oracle, kind, shape, eb):
     dict(tune_levels=0, tune_eb=0),
     dict(tune_freeze=0, tune_blockwise=0, sample_rate=0.01),
     dict(anchor_stride=4, block_rate=0.05, sub_frac=0.1),
+    # sub-blocks of 27^3 and 32^3: two and one block-wise candidates per
+    # launch (their reconstructions side by side in shared memory)
+    dict(anchor_stride=8, sub_frac=0.6),
+    dict(anchor_stride=8, sub_frac=1.0),
+    dict(anchor_stride=8, sub_frac=0.6, allow_natural=0),
 ])
 def test_tune_options(gpu, oracle, kw):
     from paper_2311_12133_gb300 import fields
