@@ -260,6 +260,7 @@ int launch_tune_blockwise(const float* x, const TuneGeom& g, int bs, int Q,
                            int frozen_slot, const uint32_t nb[3],
                            uint32_t nblocks, const TuneCfg* base,
                            unsigned allow, unsigned long long* scores,
-                           uint8_t* bmap, cudaStream_t s);
+                           uint8_t* bmap, cudaStream_t s, cudaStream_t s2,
+                           cudaEvent_t fork, cudaEvent_t join);
 
 }  // namespace hpez

@@ -312,7 +312,7 @@ int tune_globals(Call& k, std::vector<Variant>& vs, hpez_tune_report* rep,
       // every variant's candidates in one launch (escapes unused here),
       // from the blocks' state after the levels above l
       launch_tune_test(k.x, vs[0].g, vs[nv - 1].g, n0, k.b.cfgs, n0 + n1, vs[0].nblk, l,
-                       false, k.b.score, nullptr, k.b.nout + kMaxHists, k.b.state, k.s);
+                       false, k.b.score, nullptr, nullptr, k.b.state, k.s);
       launch_tune_select(k.b.score, k.b.cands, n0, n1, nv, l, k.b.base, k.b.choice,
                          k.b.best, k.s);
       nl += 3;
@@ -425,6 +425,19 @@ int tune_globals(Call& k, std::vector<Variant>& vs, hpez_tune_report* rep,
     vs[i].bits = best_bits;
     if (rep) rep->bits[vs[i].slot] = best_bits;
   }
+  return HPEZ_OK;
+}
+
+// the side stream and its two events (created on first use)
+int ensure_aux(hpez_ctx* ctx) {
+  int rc;
+  if (!ctx->aux_stream &&
+      (rc = cuda_check(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking))))
+    return rc;
+  if (!ctx->aux_ev[0] &&
+      ((rc = cuda_check(cudaEventCreateWithFlags(&ctx->aux_ev[0], cudaEventDisableTiming))) ||
+       (rc = cuda_check(cudaEventCreateWithFlags(&ctx->aux_ev[1], cudaEventDisableTiming)))))
+    return rc;
   return HPEZ_OK;
 }
 
@@ -630,15 +643,8 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
   // Sec. 6.5: order-1 and order-2 Lorenzo tests on the same sample blocks,
   // on a side stream, overlapping the candidate tests
   std::vector<int> lor_slots;
+  if ((tp.tune_lorenzo || tp.tune_blockwise) && (rc = ensure_aux(ctx))) return rc;
   if (tp.tune_lorenzo) {
-    if (!ctx->aux_stream &&
-        (rc = cuda_check(cudaStreamCreateWithFlags(&ctx->aux_stream,
-                                                   cudaStreamNonBlocking))))
-      return rc;
-    if (!ctx->aux_ev[0] &&
-        ((rc = cuda_check(cudaEventCreateWithFlags(&ctx->aux_ev[0], cudaEventDisableTiming))) ||
-         (rc = cuda_check(cudaEventCreateWithFlags(&ctx->aux_ev[1], cudaEventDisableTiming)))))
-      return rc;
     cudaStream_t s2 = ctx->aux_stream;
     cudaEventRecord(ctx->aux_ev[0], s);
     cudaStreamWaitEvent(s2, ctx->aux_ev[0], 0);
@@ -714,7 +720,8 @@ int hpez_tune(hpez_ctx* ctx, const float* d_in, int ndim, const uint64_t* dims,
     const unsigned allow = (tp.allow_natural ? 1u : 0u) | (tp.allow_same_level ? 2u : 0u);
     nl += 1 + launch_tune_blockwise(d_in, g, bsz, Q,
                                     out.frozen_dim < 0 ? -1 : out.frozen_dim + p.off, nb,
-                                    (uint32_t)nbm, k.b.cfgs, allow, k.b.bscore, k.b.bmap, s);
+                                    (uint32_t)nbm, k.b.cfgs, allow, k.b.bscore, k.b.bmap, s,
+                                    ctx->aux_stream, ctx->aux_ev[0], ctx->aux_ev[1]);
     prof.end(s);
     cudaMemcpyAsync(h_blockmap, k.b.bmap, nbm, cudaMemcpyDeviceToHost, s);
     if ((rc = sync_check(k))) return rc;

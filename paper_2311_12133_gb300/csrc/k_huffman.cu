@@ -17,6 +17,11 @@ namespace hpez {
 constexpr int kHistWin = 1024;              // bins per warp-private window
 constexpr int kHistLo = kRadius - kHistWin / 2;
 constexpr int kHistWarps = 8;
+// the codes of the first chunks (this many bytes) are read with the normal
+// cache policy and the rest as streaming loads, so that the start of the
+// code array is still in L2 when the encoder (which takes the chunks in
+// order) reads it
+constexpr uint64_t kHistKeepBytes = 64ull << 20;
 
 // ---------------------------------------------------------------------
 // histogram of the 65536 code symbols + per-chunk count of code 0.  Each
@@ -65,11 +70,12 @@ __device__ __forceinline__ void hist_body(const uint16_t* __restrict__ codes,
     if (end - beg == C && (C & 7u) == 0u) {
       const uint4* p = reinterpret_cast<const uint4*>(codes + beg);
       const uint32_t nq = C / 8;
+      const bool keep = (uint64_t)beg * sizeof(uint16_t) < kHistKeepBytes;
       for (uint32_t i = lane; i < nq; i += 128) {
         uint4 v[4];
 #pragma unroll
         for (int h = 0; h < 4; ++h)
-          if (i + 32u * h < nq) v[h] = __ldcs(p + i + 32u * h);
+          if (i + 32u * h < nq) v[h] = keep ? __ldg(p + i + 32u * h) : __ldcs(p + i + 32u * h);
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
           if (i + 32u * h >= nq) break;
@@ -733,6 +739,181 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ---------------------------------------------------------------------
+// The same one-pass encode with a CTA of kEncWarps warps per chunk and the
+// chunk's codes staged in shared memory by 16-byte loads, so both passes
+// read them there (the codes leave DRAM once).  Warp w counts and packs
+// part w of every lane's codes (lane l: codes l + 32 k, k in the part's
+// range), so four warps pack one chunk: a part starts at its lane's bit
+// offset plus the bits of the lane's earlier parts, and shares at most its
+// first and last word with the neighbouring parts (atomicOr, as between
+// lanes).  Warp 0 publishes the chunk and looks back as above.
+// ---------------------------------------------------------------------
+constexpr int kEncWarps = 4;
+constexpr uint32_t kEncStageMax = 32768;  // codes per chunk staged in shared memory
+
+// part [k0, k1) of lane `lane`'s codes in a staged chunk of nc codes, from
+// bit `off` of the chunk's words
+__device__ __forceinline__ void pack_part(const uint16_t* sc, uint32_t nc, int lane,
+                                          uint32_t k0, uint32_t k1,
+                                          const unsigned long long* __restrict__ enc,
+                                          uint32_t* words, uint32_t off) {
+  BitWriter bw;
+  bw.words = words;
+  bw.wi = off >> 5;
+  bw.nacc = (int)(off & 31);
+  bw.acc = 0;
+  bw.shared_first = bw.nacc != 0;
+  if (k1 > k0 && lane + 32 * (k1 - 1) >= nc) --k1;  // the lane's last code may be missing
+  uint32_t k = k0;
+  for (; k + 8 <= k1; k += 8) {
+    unsigned long long e[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) e[u] = __ldg(enc + sc[lane + 32 * (k + u)]);
+    // two codes whose lengths add up to at most 32 bits go out as one
+    // word fragment (the same bits, fewer steps)
+#pragma unroll
+    for (int u = 0; u < 8; u += 2) {
+      const int l0 = (int)(e[u] >> 56), l1 = (int)(e[u + 1] >> 56);
+      if (l0 + l1 <= 32) {
+        const unsigned long long v =
+            ((e[u] & ((1ull << 56) - 1)) << l1) | (e[u + 1] & ((1ull << 56) - 1));
+        bw.put((uint32_t)v, l0 + l1);
+      } else {
+        bw.put_code(e[u]);
+        bw.put_code(e[u + 1]);
+      }
+    }
+  }
+  for (; k < k1; ++k) bw.put_code(__ldg(enc + sc[lane + 32 * k]));
+  bw.flush();
+}
+
+__global__ void __launch_bounds__(kEncWarps * 32)
+    k_encode_staged(const uint16_t* __restrict__ codes, uint32_t N, uint32_t C, uint32_t nch,
+                    const unsigned long long* __restrict__ enc, uint16_t* __restrict__ lanebits,
+                    unsigned long long* flags, uint32_t* counter, uint8_t* out, Ctl* ctl,
+                    unsigned long long cap) {
+  if (ctl->status || ctl->is_const) return;
+  extern __shared__ uint4 sc4[];  // the chunk's codes
+  const uint16_t* sc = reinterpret_cast<const uint16_t*>(sc4);
+  __shared__ uint32_t cnt[kEncWarps][32];  // bits per (part, lane)
+  __shared__ uint32_t laneoff[32];         // lane bit offsets in the chunk
+  __shared__ uint32_t s_c, s_nw;
+  __shared__ unsigned long long s_prefix;
+  __shared__ int s_state;  // 0 pack, 1 past the capacity, 2 timed out
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned long long off_bits = ctl->off_bits;
+  uint32_t* bits = reinterpret_cast<uint32_t*>(out + off_bits);
+  for (;;) {
+    if (threadIdx.x == 0) s_c = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t c = s_c;
+    if (c >= nch) return;
+    const uint32_t beg = c * C, nc = min(C, N - beg);
+    // stage: 16-byte loads, 8 in flight per thread
+    {
+      const uint32_t n8 = nc / 8;
+      const uint4* src = reinterpret_cast<const uint4*>(codes + beg);
+      for (uint32_t i0 = threadIdx.x; i0 < n8; i0 += 8 * blockDim.x) {
+        uint4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (i0 + u * blockDim.x < n8) v[u] = __ldcs(src + i0 + u * blockDim.x);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (i0 + u * blockDim.x < n8) sc4[i0 + u * blockDim.x] = v[u];
+      }
+      uint16_t* sct = reinterpret_cast<uint16_t*>(sc4);
+      for (uint32_t i = 8 * n8 + threadIdx.x; i < nc; i += blockDim.x) sct[i] = codes[beg + i];
+    }
+    __syncthreads();
+    // part w of the lane's codes: k in [k0, k1)
+    const uint32_t kmax = (nc + 31) / 32;
+    const uint32_t k0 = (uint32_t)((uint64_t)kmax * w / kEncWarps);
+    const uint32_t k1 = (uint32_t)((uint64_t)kmax * (w + 1) / kEncWarps);
+    {
+      uint32_t pb = 0;
+      uint32_t k = k0;
+      for (; k + 8 <= k1 && lane + 32 * (k + 7) < nc; k += 8) {
+        unsigned long long e[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) e[u] = __ldg(enc + sc[lane + 32 * (k + u)]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) pb += (uint32_t)(e[u] >> 56);
+      }
+      for (; k < k1; ++k)
+        if (lane + 32 * k < nc) pb += (uint32_t)(__ldg(enc + sc[lane + 32 * k]) >> 56);
+      cnt[w][lane] = pb;
+    }
+    __syncthreads();
+    if (w == 0) {
+      uint32_t mybits = 0;
+#pragma unroll
+      for (int q = 0; q < kEncWarps; ++q) mybits += cnt[q][lane];
+      lanebits[(size_t)c * 32 + lane] = (uint16_t)mybits;
+      uint32_t incl = mybits;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      laneoff[lane] = incl - mybits;
+      const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+      const unsigned long long nw = (tot + 31) >> 5;
+      if (lane == 0) atomicExch(flags + c, (nw << 2) | 1ull);
+      unsigned long long prefix = 0;
+      bool timed_out = false;
+      for (long long j = (long long)c - 1; j >= 0;) {
+        const long long jj = j - lane;
+        unsigned long long f = jj >= 0 ? load_flag(flags + jj) : 2ull;
+        unsigned long long polls = 0;
+        while (__any_sync(0xffffffffu, (f & 3ull) == 0ull)) {
+          if (++polls > kEncWaitPolls) {
+            timed_out = true;
+            break;
+          }
+          __nanosleep(64);
+          if ((f & 3ull) == 0ull) f = load_flag(flags + jj);
+        }
+        if (timed_out) break;
+        const unsigned inc = __ballot_sync(0xffffffffu, (f & 3ull) == 2ull);
+        const int upto = inc ? __ffs(inc) - 1 : 31;
+        unsigned long long v = lane <= upto ? (f >> 2) : 0ull;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        prefix += v;
+        if (inc) break;
+        j -= 32;
+      }
+      if (lane == 0) {
+        if (timed_out) {
+          atomicCAS(&ctl->status, 0, ST_TIMEOUT);
+          s_state = 2;
+        } else {
+          atomicExch(flags + c, ((prefix + nw) << 2) | 2ull);
+          if (c + 1 == nch) {
+            ctl->total_words = prefix + nw;
+            ctl->total_size = off_bits + 4ull * (prefix + nw);
+            if (ctl->total_size > cap) atomicCAS(&ctl->status, 0, ST_OUT_TOO_SMALL);
+          }
+          // nothing written past the output's capacity
+          s_state = off_bits + 4ull * (prefix + nw) > cap ? 1 : 0;
+          s_prefix = prefix;
+          s_nw = (uint32_t)nw;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_state == 2) return;
+    if (s_state == 1) continue;
+    uint32_t* words = bits + s_prefix;
+    for (uint32_t i = threadIdx.x; i < s_nw; i += blockDim.x) words[i] = 0u;
+    __syncthreads();
+    uint32_t off = laneoff[lane];
+    for (int q = 0; q < w; ++q) off += cnt[q][lane];
+    pack_part(sc, nc, lane, k0, k1, enc, words, off);
+  }
+}
+
 __global__ void __launch_bounds__(256)
     k_pack(const uint16_t* __restrict__ codes, uint32_t N, uint32_t C,
            uint32_t nch, const unsigned long long* __restrict__ enc,
@@ -1195,9 +1376,28 @@ void launch_encode(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,
                    unsigned long long cap, int num_sms, cudaStream_t s) {
   // flags[0, nch) and the chunk counter (the word after them) start at 0
   cudaMemsetAsync(flags, 0, sizeof(unsigned long long) * ((size_t)nch + 1), s);
-  k_encode<<<warps_grid(nch, num_sms), 256, 0, s>>>(
-      codes, N, C, nch, enc, lanebits, flags, reinterpret_cast<uint32_t*>(flags + nch), out,
-      ctl, cap);
+  uint32_t* counter = reinterpret_cast<uint32_t*>(flags + nch);
+  if (C <= kEncStageMax && (C & 7u) == 0 && (reinterpret_cast<uintptr_t>(codes) & 15u) == 0) {
+    // a CTA per chunk with the codes in shared memory: as many CTAs as fit
+    const int smem = (int)(C * sizeof(uint16_t));
+    static int attr_smem = 0;
+    if (smem > 48 * 1024 && smem > attr_smem) {
+      cudaFuncSetAttribute(k_encode_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      attr_smem = smem;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_encode_staged, kEncWarps * 32,
+                                                  smem);
+    if (per_sm < 1) per_sm = 1;
+    uint64_t g = (uint64_t)per_sm * num_sms;
+    if (g > nch) g = nch;
+    if (g < 1) g = 1;
+    k_encode_staged<<<(unsigned)g, kEncWarps * 32, smem, s>>>(codes, N, C, nch, enc, lanebits,
+                                                              flags, counter, out, ctl, cap);
+    return;
+  }
+  k_encode<<<warps_grid(nch, num_sms), 256, 0, s>>>(codes, N, C, nch, enc, lanebits, flags,
+                                                    counter, out, ctl, cap);
 }
 
 void launch_chunk_words(const uint8_t* lanebits_bytes, uint32_t nch,

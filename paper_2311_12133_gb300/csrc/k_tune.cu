@@ -240,6 +240,37 @@ __device__ void init_anchors(float* R, const Sub& f, const int interp[3],
   __syncthreads();
 }
 
+// Every point of a sub-field with a dense shared layout (set_strides) from
+// the input, four loads in flight per thread.  The sweeps then read a
+// point's input value from its own entry, just before they overwrite it
+// with the reconstruction: a pass reads only points of earlier passes (or
+// of its own half A), never one it has still to visit, so an entry holds
+// the input until its point is visited.
+__device__ void fill_x(float* R, const Sub& f) {
+  const unsigned n2 = (unsigned)f.n[2], n1 = (unsigned)f.n[1];
+  const unsigned mg2 = fdiv_magic(n2), mg1 = fdiv_magic(n1);
+  const int tot = f.n[0] * f.n[1] * f.n[2];
+  constexpr int U = 4;
+  for (int q0 = threadIdx.x; q0 < tot; q0 += U * blockDim.x) {
+    float v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int q = q0 + u * (int)blockDim.x;
+      if (q < tot) {
+        const unsigned r1 = fdiv((unsigned)q, mg2), c2 = (unsigned)q - r1 * n2;
+        const unsigned c0 = fdiv(r1, mg1), c1 = r1 - c0 * n1;
+        v[u] = f.x[c0 * f.xst[0] + c1 * f.xst[1] + c2 * f.xst[2]];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int q = q0 + u * (int)blockDim.x;
+      if (q < tot) R[q] = v[u];
+    }
+  }
+  __syncthreads();
+}
+
 // prediction along one slot from shared memory (same stencil choice and
 // operation order as the compressor)
 __device__ __forceinline__ float predict_smem(const float* R, int i, int st,
@@ -424,7 +455,10 @@ __device__ __forceinline__ float predict_t(const float* R, int i, int st, int u,
 // The points of one box of a pass (or same-level half), specialized on the
 // interpolator and the paradigm, which are uniform within a level; hb: the
 // box is in half B of a same-level pass.
-template <int KIND, bool MD, int PS, bool kHist>
+// REC false: the points' reconstructions are never read again (the last
+// pass, or its same-level half B, of a score-only test): only the
+// prediction and its score are needed, so the point is not quantized.
+template <int KIND, bool MD, int PS, bool kHist, bool REC>
 __device__ __forceinline__ void sweep_box(float* R, const Sub& f, const Box B, bool hb,
                                           int sh, const int line[3], const TuneCfg& c,
                                           int l, bool score_on, unsigned long long& score,
@@ -448,7 +482,7 @@ __device__ __forceinline__ void sweep_box(float* R, const Sub& f, const Box B, b
     cc[1] = B.a[1] + B.b[1] * ((int)r1 - (int)r0 * B.cnt[1]);
     cc[0] = B.a[0] + B.b[0] * (int)r0;
     const int i = cc[0] * f.st[0] + cc[1] * f.st[1] + cc[2];
-    const float xv = xval(f, cc);
+    const float xv = R[i];  // the input, until the point is visited
     float p;
     if (!MD) {
       p = predict_t<KIND>(R, i, sst[PS], cc[PS] >> sh, line[PS], hb);
@@ -465,12 +499,14 @@ __device__ __forceinline__ void sweep_box(float* R, const Sub& f, const Box B, b
       }
       p = acc;
     }
-    float rv;
-    const unsigned code = quantize_t(xv, p, el, inv2, twoe, rv);
-    R[i] = rv;
+    if (REC) {
+      float rv;
+      const unsigned code = quantize_t(xv, p, el, inv2, twoe, rv);
+      R[i] = rv;
+      if (kHist) hist.add(code);
+      if (code == 0u) ++nout;
+    }
     if (score_on) score += err_fixed(__fsub_rn(xv, p), inv_el);
-    if (kHist) hist.add(code);
-    if (code == 0u) ++nout;
   }
 }
 
@@ -480,11 +516,14 @@ __device__ __forceinline__ void sweep_box(float* R, const Sub& f, const Box B, b
 // one thread
 // sh: the level's stride as a shift in the coordinates of f (l - 1 on the
 // sample block, 0 on its compact level-l grid)
+// free_last: a score-only test of this level alone (no histogram, the
+// level's state not kept), whose last pass (its half B with same-level
+// halves) is not quantized
 template <int KIND, bool kHist>
 __device__ void sweep_level_k(float* R, const Sub& f, const int interp[3],
                               int k, int l, int sh, const TuneCfg& c, bool score_on,
                               unsigned long long& score, const HistSink& hist,
-                              unsigned long long& nout, Box* sbox) {
+                              unsigned long long& nout, Box* sbox, bool free_last) {
   const int s = 1 << sh;
   int line[3];
   unsigned imask = 0;
@@ -514,12 +553,19 @@ __device__ void sweep_level_k(float* R, const Sub& f, const int interp[3],
       }
       __syncthreads();
       const bool hb = half == 1;
+      const bool rec = kHist || !free_last || pj != k - 1 || (same && half == 0);
       for (int q = 0; q < nb; ++q) {
         const Box B = sbox[q];
         if (B.total == 0) continue;
 #define HPEZ_SWEEP(K, M, P)                                                   \
-  sweep_box<K, M, P, kHist>(R, f, B, hb, sh, line, c, l, score_on, score,     \
-                            hist, nout)
+  do {                                                                        \
+    if (rec)                                                                  \
+      sweep_box<K, M, P, kHist, true>(R, f, B, hb, sh, line, c, l, score_on,  \
+                                      score, hist, nout);                    \
+    else                                                                      \
+      sweep_box<K, M, P, kHist, false>(R, f, B, hb, sh, line, c, l, score_on, \
+                                       score, hist, nout);                   \
+  } while (0)
 #define HPEZ_SWEEP_1D(K)                                                      \
   do {                                                                        \
     const int ps = c.ord[l - 1][pj];                                          \
@@ -553,10 +599,11 @@ __device__ void sweep_level_k(float* R, const Sub& f, const int interp[3],
 // same-level halves for all of them or none), so the enumeration, the
 // input value and the index are shared and only the prediction, the
 // quantization and the score are per interpolator, each on its own
-// reconstruction (R + k * vol).  The boxes of a pass are one enumeration;
-// a same-level half skips the other half's points -- fewer partial
-// iterations than a loop per box when the boxes hold a few points each.
-template <int NK, int K0, int K1, int K2, bool SAME, bool MD, int PS>
+// reconstruction (R + k * vol).  The boxes of a pass (or of a same-level
+// half: boxes of step 4s along the odd directions, one per parity pattern)
+// are one enumeration -- fewer partial iterations than a loop per box when
+// the boxes hold a few points each.
+template <int NK, int K0, int K1, int K2, bool SAME, bool MD, int PS, bool REC>
 __device__ void sweep_pass_multi(float* R, int vol, const Sub& f, const Box* bx, int nb,
                                  int tot, int half, int sh, const int line[3],
                                  const TuneCfg& c, int l, unsigned long long (&score)[NK]) {
@@ -574,17 +621,9 @@ __device__ void sweep_pass_multi(float* R, int vol, const Sub& f, const Box* bx,
     cc[1] = B.a[1] + B.b[1] * ((int)r1 - (int)r0 * B.cnt[1]);
     cc[0] = B.a[0] + B.b[0] * (int)r0;
     const unsigned S = B.S;
-    bool in_b = false;
-    if (SAME) {
-      unsigned par = 0;
-#pragma unroll
-      for (int d = 0; d < 3; ++d)
-        if (S & (1u << d)) par += (unsigned)(((cc[d] >> sh) - 1) >> 1);
-      in_b = (par & 1u) != 0;
-      if ((int)in_b != half) continue;
-    }
+    const bool in_b = SAME && half == 1;
     const int i = cc[0] * f.st[0] + cc[1] * f.st[1] + cc[2];
-    const float xv = xval(f, cc);
+    const float xv = R[i];  // copy 0 holds the input until the point is visited
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
       const int kind = k == 0 ? K0 : (k == 1 ? K1 : K2);
@@ -605,9 +644,11 @@ __device__ void sweep_pass_multi(float* R, int vol, const Sub& f, const Box* bx,
         }
         p = acc;
       }
-      float rv;
-      quantize_t(xv, p, el, inv2, twoe, rv);
-      Rk[i] = rv;
+      if (REC) {
+        float rv;
+        quantize_t(xv, p, el, inv2, twoe, rv);
+        Rk[i] = rv;
+      }
       score[k] += err_fixed(__fsub_rn(xv, p), inv_el);
     }
   }
@@ -630,28 +671,38 @@ __device__ void sweep_level_multi(float* R, int vol, const Sub& f, const int int
   }
   const bool md = c.md[l - 1] != 0;
   for (int pj = 0; pj < k; ++pj) {
-    // the pass's boxes (at most 3) in shared memory, one thread each
-    BoxDesc bd[3];
-    int nb = 0;
-    if (!md) {
-      unsigned any = 0;  // directions earlier in the order: any parity
-      for (int q = 0; q < pj; ++q) any |= 1u << c.ord[l - 1][q];
-      bd[nb++] = BoxDesc{1u << c.ord[l - 1][pj], any, 0u};
-    } else {
-      for (unsigned S = 1; S < 8; ++S)
-        if ((S & imask) == S && __popc(S) == pj + 1) bd[nb++] = BoxDesc{S, 0u, 0u};
-    }
-    __syncthreads();  // the previous pass is done with bx
-    if ((int)threadIdx.x < nb)
-      make_box(bx[threadIdx.x], f, interp, s, bd[threadIdx.x].S, bd[threadIdx.x].any, false,
-               0u);
-    __syncthreads();
-    int tot = 0;
-    for (int q = 0; q < nb; ++q) tot += bx[q].total;
     for (int half = 0; half < (SAME ? 2 : 1); ++half) {
+      // the boxes of the pass or half (at most 6) in shared memory, one
+      // thread each
+      BoxDesc bd[6];
+      int nb = 0;
+      if (!md) {
+        unsigned any = 0;  // directions earlier in the order: any parity
+        for (int q = 0; q < pj; ++q) any |= 1u << c.ord[l - 1][q];
+        add_boxes(bd, nb, 1u << c.ord[l - 1][pj], any, SAME, half);
+      } else {
+        for (unsigned S = 1; S < 8; ++S)
+          if ((S & imask) == S && __popc(S) == pj + 1) add_boxes(bd, nb, S, 0u, SAME, half);
+      }
+      __syncthreads();  // the previous pass or half is done with bx
+      if ((int)threadIdx.x < nb)
+        make_box(bx[threadIdx.x], f, interp, s, bd[threadIdx.x].S, bd[threadIdx.x].any, SAME,
+                 bd[threadIdx.x].par);
+      __syncthreads();
+      int tot = 0;
+      for (int q = 0; q < nb; ++q) tot += bx[q].total;
+      // the finest level's last pass (half B with same-level halves) is
+      // read by nothing: scored, not quantized
+      const bool rec = l != 1 || pj != k - 1 || (SAME && half == 0);
 #define HPEZ_SWEEP(M, P)                                                      \
-  sweep_pass_multi<NK, K0, K1, K2, SAME, M, P>(R, vol, f, bx, nb, tot, half, sh, line, c, \
-                                               l, score)
+  do {                                                                        \
+    if (rec)                                                                  \
+      sweep_pass_multi<NK, K0, K1, K2, SAME, M, P, true>(R, vol, f, bx, nb, tot, half, sh, \
+                                                         line, c, l, score);  \
+    else                                                                      \
+      sweep_pass_multi<NK, K0, K1, K2, SAME, M, P, false>(R, vol, f, bx, nb, tot, half, \
+                                                          sh, line, c, l, score); \
+  } while (0)
       if (md) {
         HPEZ_SWEEP(true, 0);
       } else {
@@ -673,8 +724,9 @@ __device__ __forceinline__ void sweep_level(float* R, const Sub& f,
                                             unsigned long long& score,
                                             const HistSink& hist,
                                             unsigned long long& nout, Box* sbox,
-                                            int sh) {
-  sweep_level_k<-1, kHist>(R, f, interp, k, l, sh, c, score_on, score, hist, nout, sbox);
+                                            int sh, bool free_last = false) {
+  sweep_level_k<-1, kHist>(R, f, interp, k, l, sh, c, score_on, score, hist, nout, sbox,
+                           free_last);
 }
 
 __device__ __forceinline__ void load_cfg(TuneCfg* dst, const TuneCfg* src) {
@@ -792,14 +844,13 @@ __global__ void __launch_bounds__(kTestThreads, 1)
     // the levels above it (the anchors at the coarsest level)
     const int s = 1 << (l_stop - 1);
     const Sub fc = compact_sub(f, g.interp, s);
+    fill_x(R, fc);  // the input everywhere (the anchors at the coarsest level)
     if (l_stop < g.L)
       load_state_compact(R, state + ((size_t)(second ? 1 : 0) * gridDim.x + blockIdx.x) * vol,
                          f, fc, g.interp, s);
-    else
-      init_anchors(R, fc, g.interp, 2);
-    sweep_level<kHist>(R, fc, g.interp, g.k, l_stop, c, true, sc, h, no, sbox, 0);
+    sweep_level<kHist>(R, fc, g.interp, g.k, l_stop, c, true, sc, h, no, sbox, 0, !kHist);
   } else {
-    init_anchors(R, f, g.interp, g.A);
+    fill_x(R, f);  // the input everywhere, the anchors among it
     for (int l = g.L; l >= l_stop; --l)
       sweep_level<kHist>(R, f, g.interp, g.k, l, c, l == l_stop, sc, h, no, sbox, l - 1);
   }
@@ -808,8 +859,10 @@ __global__ void __launch_bounds__(kTestThreads, 1)
       if (win[i]) atomicAdd(h.glob + (kRadius - kWin / 2) + i, win[i]);
   sc = block_sum(sc, red);
   if (threadIdx.x == 0 && sc) atomicAdd(score + v, sc);
-  no = block_sum(no, red);
-  if (threadIdx.x == 0 && no) atomicAdd(nout + v, no);
+  if (nout) {  // escapes: counted by the (alpha, beta) tests only
+    no = block_sum(no, red);
+    if (threadIdx.x == 0 && no) atomicAdd(nout + v, no);
+  }
 }
 
 // After level l's choice: CTA (sample block, variant w) runs level l with
@@ -827,10 +880,10 @@ __global__ void __launch_bounds__(kTestThreads, 1)
   load_cfg(&c, cfgs + w);
   const Sub f = sample_block(x, g, blockIdx.x);
   float* st = state + ((size_t)w * gridDim.x + blockIdx.x) * vol;
-  if (l == g.L)
-    init_anchors(R, f, g.interp, g.A);
-  else
-    copy_lattice<true>(R, st, f, g.interp, 2 << (l - 1));
+  // the input on the level's lattice (the anchors at the coarsest level),
+  // then the coarser points' reconstruction over it
+  init_anchors(R, f, g.interp, 1 << (l - 1));
+  if (l < g.L) copy_lattice<true>(R, st, f, g.interp, 2 << (l - 1));
   unsigned long long sc = 0, no = 0;
   const HistSink none{nullptr, nullptr};
   sweep_level<false>(R, f, g.interp, g.k, l, c, false, sc, none, no, sbox, l - 1);
@@ -963,7 +1016,7 @@ __global__ void __launch_bounds__(kBlockThreads)
   extern __shared__ float R[];
   __shared__ TuneCfg c;
   __shared__ unsigned long long red[32];
-  __shared__ Box sbx[3];
+  __shared__ Box sbx[6];
   load_cfg(&c, base);
   unsigned b = blockIdx.x;
   Sub f;
@@ -992,8 +1045,9 @@ __global__ void __launch_bounds__(kBlockThreads)
   while (As * 2 <= lim) As *= 2;
   int L = 0;
   while ((1 << L) < As) ++L;
-  // the anchors, in every interpolator's copy
-  {
+  // the input everywhere in copy 0, the anchors in the others
+  fill_x(R, f);
+  if (NK > 1) {
     int m[3], st[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -1010,7 +1064,7 @@ __global__ void __launch_bounds__(kBlockThreads)
       const int i = cc[0] * f.st[0] + cc[1] * f.st[1] + cc[2];
       const float v = xval(f, cc);
 #pragma unroll
-      for (int k = 0; k < NK; ++k) R[k * vol + i] = v;
+      for (int k = 1; k < NK; ++k) R[k * vol + i] = v;
     }
     __syncthreads();
   }
@@ -1186,7 +1240,8 @@ int launch_tune_blockwise(const float* x, const TuneGeom& g, int bs, int Q,
                            int frozen_slot, const uint32_t nb[3],
                            uint32_t nblocks, const TuneCfg* base,
                            unsigned allow, unsigned long long* scores,
-                           uint8_t* bmap, cudaStream_t s) {
+                           uint8_t* bmap, cudaStream_t s, cudaStream_t s2,
+                           cudaEvent_t fork, cudaEvent_t join) {
   set_smem_attr();
   BlockGeom bg;
   size_t vol = 1;
@@ -1223,12 +1278,21 @@ int launch_tune_blockwise(const float* x, const TuneGeom& g, int bs, int Q,
     if (nat) HPEZ_BW(1, CUBIC_NAT, 0, 0, false, 3u);
   }
   if (sl) {
+    // the same-level candidates on the second stream, so that their CTAs
+    // fill the SMs the first launch's last wave leaves idle
+    cudaEventRecord(fork, s);
+    cudaStreamWaitEvent(s2, fork, 0);
+    cudaStream_t s1 = s;
+    s = s2;
     if (nat && per >= 2) {
       HPEZ_BW(2, CUBIC_NAK, CUBIC_NAT, 0, true, 2u | (4u << 8));
     } else {
       HPEZ_BW(1, CUBIC_NAK, 0, 0, true, 2u);
       if (nat) HPEZ_BW(1, CUBIC_NAT, 0, 0, true, 4u);
     }
+    cudaEventRecord(join, s2);
+    s = s1;
+    cudaStreamWaitEvent(s, join, 0);
   }
 #undef HPEZ_BW
   k_tune_block_argmin<<<(nblocks + 255) / 256, 256, 0, s>>>(scores, nblocks, allow, bmap);
