@@ -741,16 +741,25 @@ __global__ void __launch_bounds__(256)
 
 // ---------------------------------------------------------------------
 // The same one-pass encode with a CTA of kEncWarps warps per chunk and the
-// chunk's codes staged in shared memory by 16-byte loads, so both passes
-// read them there (the codes leave DRAM once).  Warp w counts and packs
-// part w of every lane's codes (lane l: codes l + 32 k, k in the part's
-// range), so four warps pack one chunk: a part starts at its lane's bit
+// chunk's codes staged in shared memory by asynchronous 16-byte copies, so
+// both passes read them there (the codes leave DRAM once).  Warp w counts
+// and packs part w of every lane's codes (lane l: codes l + 32 k, k in the
+// part's range), so eight warps pack one chunk: a part starts at its lane's bit
 // offset plus the bits of the lane's earlier parts, and shares at most its
 // first and last word with the neighbouring parts (atomicOr, as between
 // lanes).  Warp 0 publishes the chunk and looks back as above.
 // ---------------------------------------------------------------------
-constexpr int kEncWarps = 4;
+constexpr int kEncWarps = 8;
 constexpr uint32_t kEncStageMax = 32768;  // codes per chunk staged in shared memory
+
+// 16 bytes global -> shared without registers (both 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
 
 // part [k0, k1) of lane `lane`'s codes in a staged chunk of nc codes, from
 // bit `off` of the chunk's words
@@ -811,19 +820,13 @@ __global__ void __launch_bounds__(kEncWarps * 32)
     const uint32_t c = s_c;
     if (c >= nch) return;
     const uint32_t beg = c * C, nc = min(C, N - beg);
-    // stage: 16-byte loads, 8 in flight per thread
+    // stage: asynchronous 16-byte copies straight into shared memory, all
+    // of the chunk in flight at once
     {
       const uint32_t n8 = nc / 8;
       const uint4* src = reinterpret_cast<const uint4*>(codes + beg);
-      for (uint32_t i0 = threadIdx.x; i0 < n8; i0 += 8 * blockDim.x) {
-        uint4 v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (i0 + u * blockDim.x < n8) v[u] = __ldcs(src + i0 + u * blockDim.x);
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (i0 + u * blockDim.x < n8) sc4[i0 + u * blockDim.x] = v[u];
-      }
+      for (uint32_t i = threadIdx.x; i < n8; i += blockDim.x) cp_async16(sc4 + i, src + i);
+      cp_async_wait_all();
       uint16_t* sct = reinterpret_cast<uint16_t*>(sc4);
       for (uint32_t i = 8 * n8 + threadIdx.x; i < nc; i += blockDim.x) sct[i] = codes[beg + i];
     }
@@ -1108,6 +1111,10 @@ __global__ void __launch_bounds__(1024)
 // ---------------------------------------------------------------------
 // decode: one warp per chunk, lane l decodes its own bit range
 // ---------------------------------------------------------------------
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
+}
+
 __device__ __forceinline__ void decode_body(
     const uint8_t* __restrict__ stream, uint64_t off_bits, uint64_t total_words,
     const uint8_t* __restrict__ lanebits_bytes,
@@ -1178,6 +1185,9 @@ __device__ __forceinline__ void decode_body(
           ++wi;
           nx0 = nx1;
           nx1 = wi + 1 < nw ? __ldg(words + wi + 1) : 0u;
+          // every eighth word (a 32-byte sector's worth) the lane's word 16
+          // ahead is requested into L2, so its refills wait on L2, not DRAM
+          if ((wi & 7u) == 0 && wi + 16 < nw) prefetch_l2(words + wi + 16);
         }
         const uint32_t e = lut[(uint32_t)(buf >> (64 - kLutBits))];
         uint32_t sym = 0, len = 0;

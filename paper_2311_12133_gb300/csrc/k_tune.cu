@@ -241,16 +241,21 @@ __device__ void init_anchors(float* R, const Sub& f, const int interp[3],
 }
 
 // Every point of a sub-field with a dense shared layout (set_strides) from
-// the input, four loads in flight per thread.  The sweeps then read a
-// point's input value from its own entry, just before they overwrite it
-// with the reconstruction: a pass reads only points of earlier passes (or
-// of its own half A), never one it has still to visit, so an entry holds
-// the input until its point is visited.
-__device__ void fill_x(float* R, const Sub& f) {
+// the input -- or, with a state buffer, the points whose interpolation
+// coordinates are all even (the coarser levels' lattice of a compact
+// level grid) from the state, in the sample-block layout of f0 at stride s
+// -- with sixteen loads in flight per thread (a CTA alone on its SM has
+// nothing else to overlap them with).  The sweeps then read a point's
+// input value from its own entry, just before they overwrite it with the
+// reconstruction: a pass reads only points of earlier passes (or of its
+// own half A), never one it has still to visit, so an entry holds the
+// input until its point is visited.
+__device__ void fill_x(float* R, const Sub& f, const float* __restrict__ state = nullptr,
+                       const Sub* f0 = nullptr, const int* interp = nullptr, int s = 1) {
   const unsigned n2 = (unsigned)f.n[2], n1 = (unsigned)f.n[1];
   const unsigned mg2 = fdiv_magic(n2), mg1 = fdiv_magic(n1);
   const int tot = f.n[0] * f.n[1] * f.n[2];
-  constexpr int U = 4;
+  constexpr int U = 16;
   for (int q0 = threadIdx.x; q0 < tot; q0 += U * blockDim.x) {
     float v[U];
 #pragma unroll
@@ -259,7 +264,23 @@ __device__ void fill_x(float* R, const Sub& f) {
       if (q < tot) {
         const unsigned r1 = fdiv((unsigned)q, mg2), c2 = (unsigned)q - r1 * n2;
         const unsigned c0 = fdiv(r1, mg1), c1 = r1 - c0 * n1;
-        v[u] = f.x[c0 * f.xst[0] + c1 * f.xst[1] + c2 * f.xst[2]];
+        bool coarse = state != nullptr;
+        if (coarse) {
+          const unsigned cc[3] = {c0, c1, c2};
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+            if (interp[d] && (cc[d] & 1u)) coarse = false;
+        }
+        if (coarse) {
+          const unsigned cc[3] = {c0, c1, c2};
+          unsigned full = 0;
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+            full += cc[d] * (unsigned)(interp[d] ? s : 1) * (unsigned)f0->st[d];
+          v[u] = state[full];
+        } else {
+          v[u] = f.x[c0 * f.xst[0] + c1 * f.xst[1] + c2 * f.xst[2]];
+        }
       }
     }
 #pragma unroll
@@ -519,11 +540,18 @@ __device__ __forceinline__ void sweep_box(float* R, const Sub& f, const Box B, b
 // free_last: a score-only test of this level alone (no histogram, the
 // level's state not kept), whose last pass (its half B with same-level
 // halves) is not quantized
+// the boxes of every pass and same-level half of one level: slot
+// pj * halves + half holds nb[slot] boxes at b[6 * slot]
+struct LevelBoxes {
+  Box b[36];
+  int nb[6];
+};
+
 template <int KIND, bool kHist>
 __device__ void sweep_level_k(float* R, const Sub& f, const int interp[3],
                               int k, int l, int sh, const TuneCfg& c, bool score_on,
                               unsigned long long& score, const HistSink& hist,
-                              unsigned long long& nout, Box* sbox, bool free_last) {
+                              unsigned long long& nout, LevelBoxes* lb, bool free_last) {
   const int s = 1 << sh;
   int line[3];
   unsigned imask = 0;
@@ -535,23 +563,31 @@ __device__ void sweep_level_k(float* R, const Sub& f, const int interp[3],
   const int kind = c.kind[l - 1];
   const bool md = c.md[l - 1] != 0;
   const bool same = c.same[l - 1] != 0 && kind != LINEAR;
+  const int halves = same ? 2 : 1;
+  // every box of the level at once, one thread each (the barrier that
+  // ended the previous level's last pass freed the array)
+  if ((int)threadIdx.x < 6 * k * halves) {
+    const int slot = (int)threadIdx.x / 6, q = (int)threadIdx.x % 6;
+    const int pj = slot / halves, half = slot % halves;
+    BoxDesc bd[6];
+    int nb = 0;
+    if (!md) {
+      unsigned any = 0;  // directions earlier in the order: any parity
+      for (int r = 0; r < pj; ++r) any |= 1u << c.ord[l - 1][r];
+      add_boxes(bd, nb, 1u << c.ord[l - 1][pj], any, same, half);
+    } else {
+      for (unsigned S = 1; S < 8; ++S)
+        if ((S & imask) == S && __popc(S) == pj + 1) add_boxes(bd, nb, S, 0u, same, half);
+    }
+    if (q < nb) make_box(lb->b[6 * slot + q], f, interp, s, bd[q].S, bd[q].any, same, bd[q].par);
+    if (q == 0) lb->nb[slot] = nb;
+  }
+  __syncthreads();
   for (int pj = 0; pj < k; ++pj) {
-    for (int half = 0; half < (same ? 2 : 1); ++half) {
-      BoxDesc bd[6];
-      int nb = 0;
-      if (!md) {
-        unsigned any = 0;  // directions earlier in the order: any parity
-        for (int q = 0; q < pj; ++q) any |= 1u << c.ord[l - 1][q];
-        add_boxes(bd, nb, 1u << c.ord[l - 1][pj], any, same, half);
-      } else {
-        for (unsigned S = 1; S < 8; ++S)
-          if ((S & imask) == S && __popc(S) == pj + 1) add_boxes(bd, nb, S, 0u, same, half);
-      }
-      if ((int)threadIdx.x < nb) {
-        const BoxDesc d = bd[threadIdx.x];
-        make_box(sbox[threadIdx.x], f, interp, s, d.S, d.any, same, d.par);
-      }
-      __syncthreads();
+    for (int half = 0; half < halves; ++half) {
+      const int slot = pj * halves + half;
+      const int nb = lb->nb[slot];
+      const Box* sbox = lb->b + 6 * slot;
       const bool hb = half == 1;
       const bool rec = kHist || !free_last || pj != k - 1 || (same && half == 0);
       for (int q = 0; q < nb; ++q) {
@@ -723,9 +759,9 @@ __device__ __forceinline__ void sweep_level(float* R, const Sub& f,
                                             const TuneCfg& c, bool score_on,
                                             unsigned long long& score,
                                             const HistSink& hist,
-                                            unsigned long long& nout, Box* sbox,
+                                            unsigned long long& nout, LevelBoxes* lb,
                                             int sh, bool free_last = false) {
-  sweep_level_k<-1, kHist>(R, f, interp, k, l, sh, c, score_on, score, hist, nout, sbox,
+  sweep_level_k<-1, kHist>(R, f, interp, k, l, sh, c, score_on, score, hist, nout, lb,
                            free_last);
 }
 
@@ -785,34 +821,6 @@ __device__ __forceinline__ Sub compact_sub(const Sub& f, const int interp[3], in
   return c;
 }
 
-// the state's stride-2s lattice (sample-block layout) into the compact
-// level-s grid (its points at even compact coordinates)
-__device__ void load_state_compact(float* R, const float* __restrict__ state, const Sub& f,
-                                   const Sub& fc, const int interp[3], int s) {
-  int m[3], sp[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    sp[d] = interp[d] ? 2 : 1;
-    m[d] = (fc.n[d] + sp[d] - 1) / sp[d];
-  }
-  const unsigned mg2 = fdiv_magic((unsigned)m[2]), mg1 = fdiv_magic((unsigned)m[1]);
-  const int tot = m[0] * m[1] * m[2];
-  for (int q = threadIdx.x; q < tot; q += blockDim.x) {
-    const unsigned r1 = fdiv((unsigned)q, mg2);
-    const unsigned r0 = fdiv(r1, mg1);
-    const int c[3] = {(int)r0 * sp[0], ((int)r1 - (int)r0 * m[1]) * sp[1],
-                      (q - (int)r1 * m[2]) * sp[2]};
-    int full = 0, comp = 0;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      full += c[d] * (interp[d] ? s : 1) * f.st[d];
-      comp += c[d] * fc.st[d];
-    }
-    R[comp] = state[full];
-  }
-  __syncthreads();
-}
-
 // Variants y < ny0 use geometry g0, the others g1 (two frozen-dimension
 // choices in one launch).  With a state buffer (candidate tests of level
 // l_stop), a CTA starts from its block's reconstruction after the coarser
@@ -831,7 +839,7 @@ __global__ void __launch_bounds__(kTestThreads, 1)
   __shared__ TuneCfg c;
   __shared__ unsigned long long red[32];
   __shared__ uint32_t win[kHist ? kWin : 1];
-  __shared__ Box sbox[6];
+  __shared__ LevelBoxes sbox;
   const int v = blockIdx.y;
   if (kHist)
     for (int i = threadIdx.x; i < kWin; i += blockDim.x) win[i] = 0;
@@ -844,15 +852,18 @@ __global__ void __launch_bounds__(kTestThreads, 1)
     // the levels above it (the anchors at the coarsest level)
     const int s = 1 << (l_stop - 1);
     const Sub fc = compact_sub(f, g.interp, s);
-    fill_x(R, fc);  // the input everywhere (the anchors at the coarsest level)
+    // the input at the level's points, the coarser levels' reconstruction
+    // at the others (the anchors, from the input, at the coarsest level)
     if (l_stop < g.L)
-      load_state_compact(R, state + ((size_t)(second ? 1 : 0) * gridDim.x + blockIdx.x) * vol,
-                         f, fc, g.interp, s);
-    sweep_level<kHist>(R, fc, g.interp, g.k, l_stop, c, true, sc, h, no, sbox, 0, !kHist);
+      fill_x(R, fc, state + ((size_t)(second ? 1 : 0) * gridDim.x + blockIdx.x) * vol, &f,
+             g.interp, s);
+    else
+      fill_x(R, fc);
+    sweep_level<kHist>(R, fc, g.interp, g.k, l_stop, c, true, sc, h, no, &sbox, 0, !kHist);
   } else {
     fill_x(R, f);  // the input everywhere, the anchors among it
     for (int l = g.L; l >= l_stop; --l)
-      sweep_level<kHist>(R, f, g.interp, g.k, l, c, l == l_stop, sc, h, no, sbox, l - 1);
+      sweep_level<kHist>(R, f, g.interp, g.k, l, c, l == l_stop, sc, h, no, &sbox, l - 1);
   }
   if (kHist)
     for (int i = threadIdx.x; i < kWin; i += blockDim.x)
@@ -876,7 +887,7 @@ __global__ void __launch_bounds__(kTestThreads, 1)
   const TuneGeom& g = w ? g1 : g0;
   extern __shared__ float R[];
   __shared__ TuneCfg c;
-  __shared__ Box sbox[6];
+  __shared__ LevelBoxes sbox;
   load_cfg(&c, cfgs + w);
   const Sub f = sample_block(x, g, blockIdx.x);
   float* st = state + ((size_t)w * gridDim.x + blockIdx.x) * vol;
@@ -886,7 +897,7 @@ __global__ void __launch_bounds__(kTestThreads, 1)
   if (l < g.L) copy_lattice<true>(R, st, f, g.interp, 2 << (l - 1));
   unsigned long long sc = 0, no = 0;
   const HistSink none{nullptr, nullptr};
-  sweep_level<false>(R, f, g.interp, g.k, l, c, false, sc, none, no, sbox, l - 1);
+  sweep_level<false>(R, f, g.interp, g.k, l, c, false, sc, none, no, &sbox, l - 1);
   copy_lattice<false>(R, st, f, g.interp, 1 << (l - 1));
 }
 
