@@ -650,14 +650,21 @@ __device__ __forceinline__ void pack_body(
 }
 
 // ---------------------------------------------------------------------
-// encode in one pass (single field): a warp takes the chunks in order from
-// a counter; per chunk it counts its lanes' bits, publishes the chunk's
-// word count, finds the chunk's word offset by a decoupled look-back over
-// the flags of the chunks before it (a flag holds a count: status 1 = this
-// chunk's words, 2 = the words of every chunk up to it), publishes that
-// inclusive count and packs the chunk.  Chunks are taken in order, so every
-// chunk a look-back waits for is held by a running warp.  The waits are
-// bounded: on expiry the call fails with a timeout.
+// encode in one pass (single field): a CTA of kEncWarps warps takes the
+// chunks in order from a counter.  Per chunk it stages the chunk's codes in
+// shared memory by asynchronous 16-byte copies (the codes leave DRAM once;
+// both passes read them there), counts its lanes' bits, publishes the
+// chunk's word count, finds the chunk's word offset by a decoupled
+// look-back over the flags of the chunks before it (a flag holds a count:
+// status 1 = this chunk's words, 2 = the words of every chunk up to it),
+// publishes that inclusive count and packs the chunk.  Warp w counts and
+// packs part w of every lane's codes (lane l: codes l + 32 k, k in the
+// part's range): a part starts at its lane's bit offset plus the bits of
+// the lane's earlier parts and shares at most its first and last word with
+// the neighbouring parts (atomicOr, as between lanes).  Warp 0 publishes
+// and looks back.  Chunks are taken in order, so every chunk a look-back
+// waits for is held by a running CTA.  The waits are bounded: on expiry
+// the call fails with a timeout.
 // ---------------------------------------------------------------------
 constexpr unsigned long long kEncWaitPolls = 1ull << 22;
 
@@ -665,90 +672,6 @@ __device__ __forceinline__ unsigned long long load_flag(const unsigned long long
   return *reinterpret_cast<const volatile unsigned long long*>(f);
 }
 
-__global__ void __launch_bounds__(256)
-    k_encode(const uint16_t* __restrict__ codes, uint32_t N, uint32_t C, uint32_t nch,
-             const unsigned long long* __restrict__ enc, uint16_t* __restrict__ lanebits,
-             unsigned long long* flags, uint32_t* counter, uint8_t* out, Ctl* ctl,
-             unsigned long long cap) {
-  if (ctl->status || ctl->is_const) return;
-  const int lane = threadIdx.x & 31;
-  const unsigned long long off_bits = ctl->off_bits;
-  uint32_t* bits = reinterpret_cast<uint32_t*>(out + off_bits);
-  for (;;) {
-    uint32_t c = 0;
-    if (lane == 0) c = atomicAdd(counter, 1u);
-    c = __shfl_sync(0xffffffffu, c, 0);
-    if (c >= nch) return;
-    const uint32_t beg = c * C, nc = min(C, N - beg);
-    // the lane's bits (16 code loads in flight: the pass waits on memory)
-    uint32_t mybits = 0;
-    {
-      uint32_t j = lane;
-      for (; j + 15 * 32 < nc; j += 16 * 32) {
-        unsigned cd[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) cd[k] = codes[beg + j + 32 * k];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) mybits += (uint32_t)(__ldg(enc + cd[k]) >> 56);
-      }
-      for (; j < nc; j += 32) mybits += (uint32_t)(enc[codes[beg + j]] >> 56);
-    }
-    lanebits[(size_t)c * 32 + lane] = (uint16_t)mybits;
-    uint32_t tot = mybits;
-    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    const unsigned long long nw = (tot + 31) >> 5;
-    // publish the aggregate, then look back
-    if (lane == 0) atomicExch(flags + c, (nw << 2) | 1ull);
-    unsigned long long prefix = 0;
-    bool timed_out = false;
-    for (long long j = (long long)c - 1; j >= 0;) {
-      const long long jj = j - lane;
-      unsigned long long f = jj >= 0 ? load_flag(flags + jj) : 2ull;  // before chunk 0: 0 words
-      unsigned long long polls = 0;
-      while (__any_sync(0xffffffffu, (f & 3ull) == 0ull)) {
-        if (++polls > kEncWaitPolls) {
-          timed_out = true;
-          break;
-        }
-        __nanosleep(64);
-        if ((f & 3ull) == 0ull) f = load_flag(flags + jj);
-      }
-      if (timed_out) break;
-      const unsigned inc = __ballot_sync(0xffffffffu, (f & 3ull) == 2ull);
-      // lanes up to the first inclusive count (or all 32) add up
-      const int upto = inc ? __ffs(inc) - 1 : 31;
-      unsigned long long v = lane <= upto ? (f >> 2) : 0ull;
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      prefix += v;
-      if (inc) break;
-      j -= 32;
-    }
-    if (timed_out) {
-      if (lane == 0) atomicCAS(&ctl->status, 0, ST_TIMEOUT);
-      return;
-    }
-    if (lane == 0) atomicExch(flags + c, ((prefix + nw) << 2) | 2ull);
-    if (c + 1 == nch && lane == 0) {
-      ctl->total_words = prefix + nw;
-      ctl->total_size = off_bits + 4ull * (prefix + nw);
-      if (ctl->total_size > cap) atomicCAS(&ctl->status, 0, ST_OUT_TOO_SMALL);
-    }
-    // nothing written past the output's capacity
-    if (off_bits + 4ull * (prefix + nw) > cap) continue;
-    pack_chunk(codes, beg, nc, enc, mybits, bits + prefix, (uint32_t)nw, lane);
-  }
-}
-
-// ---------------------------------------------------------------------
-// The same one-pass encode with a CTA of kEncWarps warps per chunk and the
-// chunk's codes staged in shared memory by asynchronous 16-byte copies, so
-// both passes read them there (the codes leave DRAM once).  Warp w counts
-// and packs part w of every lane's codes (lane l: codes l + 32 k, k in the
-// part's range), so eight warps pack one chunk: a part starts at its lane's bit
-// offset plus the bits of the lane's earlier parts, and shares at most its
-// first and last word with the neighbouring parts (atomicOr, as between
-// lanes).  Warp 0 publishes the chunk and looks back as above.
-// ---------------------------------------------------------------------
 constexpr int kEncWarps = 8;
 constexpr uint32_t kEncStageMax = 32768;  // codes per chunk staged in shared memory
 
@@ -1387,27 +1310,24 @@ void launch_encode(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,
   // flags[0, nch) and the chunk counter (the word after them) start at 0
   cudaMemsetAsync(flags, 0, sizeof(unsigned long long) * ((size_t)nch + 1), s);
   uint32_t* counter = reinterpret_cast<uint32_t*>(flags + nch);
-  if (C <= kEncStageMax && (C & 7u) == 0 && (reinterpret_cast<uintptr_t>(codes) & 15u) == 0) {
-    // a CTA per chunk with the codes in shared memory: as many CTAs as fit
-    const int smem = (int)(C * sizeof(uint16_t));
-    static int attr_smem = 0;
-    if (smem > 48 * 1024 && smem > attr_smem) {
-      cudaFuncSetAttribute(k_encode_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      attr_smem = smem;
-    }
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_encode_staged, kEncWarps * 32,
-                                                  smem);
-    if (per_sm < 1) per_sm = 1;
-    uint64_t g = (uint64_t)per_sm * num_sms;
-    if (g > nch) g = nch;
-    if (g < 1) g = 1;
-    k_encode_staged<<<(unsigned)g, kEncWarps * 32, smem, s>>>(codes, N, C, nch, enc, lanebits,
-                                                              flags, counter, out, ctl, cap);
-    return;
+  // a CTA per chunk with the codes in shared memory, as many CTAs as fit;
+  // C is a power of two in [256, kEncStageMax] (checked with the config)
+  // and the code array starts on a 256-byte boundary, so every chunk starts
+  // on a 16-byte one
+  const int smem = (int)(C * sizeof(uint16_t));
+  static int attr_smem = 0;
+  if (smem > 48 * 1024 && smem > attr_smem) {
+    cudaFuncSetAttribute(k_encode_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr_smem = smem;
   }
-  k_encode<<<warps_grid(nch, num_sms), 256, 0, s>>>(codes, N, C, nch, enc, lanebits, flags,
-                                                    counter, out, ctl, cap);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_encode_staged, kEncWarps * 32, smem);
+  if (per_sm < 1) per_sm = 1;
+  uint64_t g = (uint64_t)per_sm * num_sms;
+  if (g > nch) g = nch;
+  if (g < 1) g = 1;
+  k_encode_staged<<<(unsigned)g, kEncWarps * 32, smem, s>>>(codes, N, C, nch, enc, lanebits,
+                                                            flags, counter, out, ctl, cap);
 }
 
 void launch_chunk_words(const uint8_t* lanebits_bytes, uint32_t nch,

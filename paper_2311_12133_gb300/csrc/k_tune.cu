@@ -241,17 +241,13 @@ __device__ void init_anchors(float* R, const Sub& f, const int interp[3],
 }
 
 // Every point of a sub-field with a dense shared layout (set_strides) from
-// the input -- or, with a state buffer, the points whose interpolation
-// coordinates are all even (the coarser levels' lattice of a compact
-// level grid) from the state, in the sample-block layout of f0 at stride s
-// -- with sixteen loads in flight per thread (a CTA alone on its SM has
+// the input, sixteen loads in flight per thread (a CTA alone on its SM has
 // nothing else to overlap them with).  The sweeps then read a point's
 // input value from its own entry, just before they overwrite it with the
 // reconstruction: a pass reads only points of earlier passes (or of its
 // own half A), never one it has still to visit, so an entry holds the
 // input until its point is visited.
-__device__ void fill_x(float* R, const Sub& f, const float* __restrict__ state = nullptr,
-                       const Sub* f0 = nullptr, const int* interp = nullptr, int s = 1) {
+__device__ void fill_x(float* R, const Sub& f) {
   const unsigned n2 = (unsigned)f.n[2], n1 = (unsigned)f.n[1];
   const unsigned mg2 = fdiv_magic(n2), mg1 = fdiv_magic(n1);
   const int tot = f.n[0] * f.n[1] * f.n[2];
@@ -264,23 +260,7 @@ __device__ void fill_x(float* R, const Sub& f, const float* __restrict__ state =
       if (q < tot) {
         const unsigned r1 = fdiv((unsigned)q, mg2), c2 = (unsigned)q - r1 * n2;
         const unsigned c0 = fdiv(r1, mg1), c1 = r1 - c0 * n1;
-        bool coarse = state != nullptr;
-        if (coarse) {
-          const unsigned cc[3] = {c0, c1, c2};
-#pragma unroll
-          for (int d = 0; d < 3; ++d)
-            if (interp[d] && (cc[d] & 1u)) coarse = false;
-        }
-        if (coarse) {
-          const unsigned cc[3] = {c0, c1, c2};
-          unsigned full = 0;
-#pragma unroll
-          for (int d = 0; d < 3; ++d)
-            full += cc[d] * (unsigned)(interp[d] ? s : 1) * (unsigned)f0->st[d];
-          v[u] = state[full];
-        } else {
-          v[u] = f.x[c0 * f.xst[0] + c1 * f.xst[1] + c2 * f.xst[2]];
-        }
+        v[u] = f.x[c0 * f.xst[0] + c1 * f.xst[1] + c2 * f.xst[2]];
       }
     }
 #pragma unroll
@@ -288,6 +268,50 @@ __device__ void fill_x(float* R, const Sub& f, const float* __restrict__ state =
       const int q = q0 + u * (int)blockDim.x;
       if (q < tot) R[q] = v[u];
     }
+  }
+  __syncthreads();
+}
+
+// Over the inputs of a compact level-s grid fc: the coarser levels'
+// reconstruction at its points with even interpolation coordinates, from
+// the state (the sample-block layout of f), eight loads in flight per
+// thread.
+__device__ void overlay_state(float* R, const float* __restrict__ state, const Sub& f,
+                              const Sub& fc, const int interp[3], int s) {
+  int m[3], sp[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    sp[d] = interp[d] ? 2 : 1;
+    m[d] = (fc.n[d] + sp[d] - 1) / sp[d];
+  }
+  const unsigned mg2 = fdiv_magic((unsigned)m[2]), mg1 = fdiv_magic((unsigned)m[1]);
+  const int tot = m[0] * m[1] * m[2];
+  constexpr int U = 8;
+  for (int q0 = threadIdx.x; q0 < tot; q0 += U * blockDim.x) {
+    float v[U];
+    int dst[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int q = q0 + u * (int)blockDim.x;
+      dst[u] = -1;
+      if (q < tot) {
+        const unsigned r1 = fdiv((unsigned)q, mg2);
+        const unsigned r0 = fdiv(r1, mg1);
+        const int c[3] = {(int)r0 * sp[0], ((int)r1 - (int)r0 * m[1]) * sp[1],
+                          (q - (int)r1 * m[2]) * sp[2]};
+        int full = 0, comp = 0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          full += c[d] * (interp[d] ? s : 1) * f.st[d];
+          comp += c[d] * fc.st[d];
+        }
+        v[u] = state[full];
+        dst[u] = comp;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (dst[u] >= 0) R[dst[u]] = v[u];
   }
   __syncthreads();
 }
@@ -854,11 +878,10 @@ __global__ void __launch_bounds__(kTestThreads, 1)
     const Sub fc = compact_sub(f, g.interp, s);
     // the input at the level's points, the coarser levels' reconstruction
     // at the others (the anchors, from the input, at the coarsest level)
+    fill_x(R, fc);
     if (l_stop < g.L)
-      fill_x(R, fc, state + ((size_t)(second ? 1 : 0) * gridDim.x + blockIdx.x) * vol, &f,
-             g.interp, s);
-    else
-      fill_x(R, fc);
+      overlay_state(R, state + ((size_t)(second ? 1 : 0) * gridDim.x + blockIdx.x) * vol, f,
+                    fc, g.interp, s);
     sweep_level<kHist>(R, fc, g.interp, g.k, l_stop, c, true, sc, h, no, &sbox, 0, !kHist);
   } else {
     fill_x(R, f);  // the input everywhere, the anchors among it
