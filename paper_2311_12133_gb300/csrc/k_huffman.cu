@@ -14,7 +14,7 @@
 
 namespace hpez {
 
-constexpr int kHistWin = 1024;              // bins per warp-private window
+constexpr int kHistWin = 2048;              // bins per warp-private window
 constexpr int kHistLo = kRadius - kHistWin / 2;
 constexpr int kHistWarps = 8;
 // the codes of the first chunks (this many bytes) are read with the normal
@@ -1034,10 +1034,6 @@ __global__ void __launch_bounds__(1024)
 // ---------------------------------------------------------------------
 // decode: one warp per chunk, lane l decodes its own bit range
 // ---------------------------------------------------------------------
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
-}
-
 __device__ __forceinline__ void decode_body(
     const uint8_t* __restrict__ stream, uint64_t off_bits, uint64_t total_words,
     const uint8_t* __restrict__ lanebits_bytes,
@@ -1108,9 +1104,6 @@ __device__ __forceinline__ void decode_body(
           ++wi;
           nx0 = nx1;
           nx1 = wi + 1 < nw ? __ldg(words + wi + 1) : 0u;
-          // every eighth word (a 32-byte sector's worth) the lane's word 16
-          // ahead is requested into L2, so its refills wait on L2, not DRAM
-          if ((wi & 7u) == 0 && wi + 16 < nw) prefetch_l2(words + wi + 16);
         }
         const uint32_t e = lut[(uint32_t)(buf >> (64 - kLutBits))];
         uint32_t sym = 0, len = 0;
