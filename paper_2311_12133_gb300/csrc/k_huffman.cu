@@ -726,7 +726,6 @@ __global__ void __launch_bounds__(kEncWarps * 32)
                     const unsigned long long* __restrict__ enc, uint16_t* __restrict__ lanebits,
                     unsigned long long* flags, uint32_t* counter, uint8_t* out, Ctl* ctl,
                     unsigned long long cap) {
-  if (ctl->status || ctl->is_const) return;
   extern __shared__ uint4 sc4[];  // the chunk's codes
   const uint16_t* sc = reinterpret_cast<const uint16_t*>(sc4);
   __shared__ uint32_t cnt[kEncWarps][32];  // bits per (part, lane)
@@ -734,6 +733,11 @@ __global__ void __launch_bounds__(kEncWarps * 32)
   __shared__ uint32_t s_c, s_nw;
   __shared__ unsigned long long s_prefix;
   __shared__ int s_state;  // 0 pack, 1 past the capacity, 2 timed out
+  // one reading of the status for the whole CTA (other CTAs of this launch
+  // may set it while this one starts; its warps meet at barriers)
+  if (threadIdx.x == 0) s_state = (ctl->status || ctl->is_const) ? 2 : 0;
+  __syncthreads();
+  if (s_state == 2) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned long long off_bits = ctl->off_bits;
   uint32_t* bits = reinterpret_cast<uint32_t*>(out + off_bits);
