@@ -673,7 +673,6 @@ __device__ __forceinline__ unsigned long long load_flag(const unsigned long long
 }
 
 constexpr int kEncWarps = 8;
-constexpr uint32_t kEncStageMax = 32768;  // codes per chunk staged in shared memory
 
 // 16 bytes global -> shared without registers (both 16-byte aligned)
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -1307,10 +1306,10 @@ void launch_encode(const uint16_t* codes, uint32_t N, uint32_t C, uint32_t nch,
   // flags[0, nch) and the chunk counter (the word after them) start at 0
   cudaMemsetAsync(flags, 0, sizeof(unsigned long long) * ((size_t)nch + 1), s);
   uint32_t* counter = reinterpret_cast<uint32_t*>(flags + nch);
-  // a CTA per chunk with the codes in shared memory, as many CTAs as fit;
-  // C is a power of two in [256, kEncStageMax] (checked with the config)
-  // and the code array starts on a 256-byte boundary, so every chunk starts
-  // on a 16-byte one
+  // a CTA per chunk with the codes in shared memory, as many CTAs as fit.
+  // C is a power of two in [256, 32768] (checked with the config: at most
+  // 64 KB of codes to stage) and the code array starts on a 256-byte
+  // boundary, so every chunk starts on a 16-byte one
   const int smem = (int)(C * sizeof(uint16_t));
   static int attr_smem = 0;
   if (smem > 48 * 1024 && smem > attr_smem) {
